@@ -710,7 +710,9 @@ int orc_reference_entry(const double *a9, const double *b9, int op, double k, in
  *  - a cluster with more than leaf_size triangles is split along the
  *    longest box axis (lowest axis on ties) at the median of the triangle
  *    centroids ((v0 + v1) + v2) / 3, ties broken by triangle index; the
- *    first floor(n/2) triangles form the left child. */
+ *    first floor(n/2) triangles form the left child;
+ *  - inside a leaf the triangles are in increasing index order, so the
+ *    permutation depends only on the cluster sets. */
 static const double *g_cent; /* centroid coordinate array for qsort */
 static int g_axis;
 
@@ -720,6 +722,12 @@ static int cmp_centroid(const void *pa, const void *pb)
     double ca = g_cent[3 * (int64_t)a + g_axis], cb = g_cent[3 * (int64_t)b + g_axis];
     if (ca < cb) return -1;
     if (ca > cb) return 1;
+    return (a > b) - (a < b);
+}
+
+static int cmp_index(const void *pa, const void *pb)
+{
+    int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
     return (a > b) - (a < b);
 }
 
@@ -761,7 +769,11 @@ int orc_cluster_tree(const double *V, const int32_t *Tr, int64_t nt, int leaf_si
         int64_t b = cl_begin[c], e = cl_end[c], n = e - b;
         cluster_bbox(V, Tr, perm, b, e, cl_box + 6 * c);
         cl_left[c] = cl_right[c] = -1;
-        if (n <= leaf_size) continue;
+        if (n <= leaf_size) {
+            /* leaf: its triangles in increasing index order */
+            qsort(perm + b, (size_t)n, sizeof(int32_t), cmp_index);
+            continue;
+        }
         double *box = cl_box + 6 * c;
         int axis = 0;
         double ext = box[3] - box[0];
