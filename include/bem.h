@@ -1,0 +1,201 @@
+/*
+ * bem.h -- C ABI of the GB300 library for P0 Galerkin boundary-element
+ * matrices of the 3D Laplace and Helmholtz single-layer, double-layer and
+ * adjoint double-layer operators, assembled as H-matrices with ACA
+ * (Vater, Betcke, Dilba, "Simple and efficient GPU parallelization of
+ * existing H-Matrix accelerated BEM code", arXiv 1711.01897).
+ *
+ * Conventions shared by every call
+ *  - Every call returns a bem_status.  No call aborts, traps or prints.  The
+ *    text of the last error of the calling thread is bem_last_error().
+ *  - Handles are created and destroyed by the caller; the library copies all
+ *    mesh inputs, so caller buffers may be freed after a create call.
+ *  - Output buffers are owned by the caller.  A pointer argument may be host
+ *    or device memory unless stated otherwise; the library detects which.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Work
+ *    with device-resident inputs and outputs is enqueued on that stream and
+ *    the call returns without waiting, unless stated otherwise.  Calls with
+ *    host buffers wait for their copies to finish before returning.
+ *  - Rows are test functions psi_i and columns trial functions phi_j, as in
+ *    [S_h]_{i,j} of Eq. (1).  P0 spaces: one basis function per triangle,
+ *    the indicator of that triangle.
+ *  - Operators (Sec. 2, Eq. (1)-(3) with g of Eq. (5), k = 0 for Laplace):
+ *      BEM_SLP  single layer          int int psi_i g phi_j
+ *      BEM_DLP  double layer          int int psi_i dg/dn_y phi_j
+ *      BEM_ADLP adjoint double layer  int int psi_i dg/dn_x phi_j
+ *    Values are f64 for k == 0 and interleaved complex128 (re, im) for k != 0.
+ *  - Quadrature: pairs that share no vertex use the symmetric 6-point
+ *    degree-4 triangle rule in both triangles (Sec. 3.2.1, Sec. 3.2.3);
+ *    pairs that share a vertex, an edge or the whole triangle use the
+ *    Sauter-Schwab transformations of [0,1]^4 with 4 Gauss-Legendre points
+ *    per axis (the Erichsen-Sauter scheme cited in Sec. 3.2.3), always in
+ *    FP64.
+ *  - Precision (Sec. 3.2.4): BEM_FP64 evaluates every regular pair in FP64;
+ *    BEM_MIXED evaluates regular pairs in FP32 (centroid-relative geometry)
+ *    and accumulates each entry's quadrature sum in float-float (about 48
+ *    significant bits) before it is stored in FP64.  ACA pivoting, residual
+ *    updates and norms are FP64 in both modes.
+ */
+#ifndef BEM_H
+#define BEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bem_mesh_s *bem_mesh;
+typedef struct bem_hmat_s *bem_hmat;
+
+enum bem_op { BEM_SLP = 0, BEM_DLP = 1, BEM_ADLP = 2 };
+enum bem_prec { BEM_FP64 = 0, BEM_MIXED = 1 };
+enum bem_status {
+    BEM_OK = 0,
+    BEM_E_ARG = 1,     /* invalid argument (null handle, size, enum, index) */
+    BEM_E_MESH = 2,    /* mesh rejected: index out of range, zero area, NaN */
+    BEM_E_OOM = 3,     /* device or host allocation failed */
+    BEM_E_CUDA = 4,    /* a CUDA runtime call failed */
+    BEM_E_TIMEOUT = 5, /* a bounded device-side wait ran out */
+    BEM_E_STATE = 6    /* call not valid in the handle's state */
+};
+
+/* Library version, e.g. 100 for 0.1.0. */
+int bem_version(void);
+
+/* Text of the calling thread's last error ("" if none).  The pointer stays
+ * valid until the next library call on this thread. */
+const char *bem_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Meshes (Sec. 3.2.1: the whole grid is copied to the device; normals,     */
+/* areas and global quadrature points are precomputed there)               */
+/* ---------------------------------------------------------------------- */
+
+/* Creates a mesh on the current CUDA device.
+ *  vertices   host f64 [n_vertices][3], row-major
+ *  triangles  host i32 [n_triangles][3], 0-based; the right-hand normal of
+ *             the stored vertex order is n in dg/dn (outward for closed
+ *             surfaces with counter-clockwise order seen from outside)
+ *  out        receives the handle
+ * Fails with BEM_E_MESH for an index outside [0, n_vertices), a repeated
+ * vertex in a triangle, a triangle of zero area, or a non-finite coordinate;
+ * BEM_E_ARG for n_vertices < 3, n_triangles < 1 or n_triangles >= 2^31.
+ * Synchronous: returns after the device geometry is built. */
+int bem_mesh_create(const double *vertices, int64_t n_vertices, const int32_t *triangles,
+                    int64_t n_triangles, bem_mesh *out);
+
+/* Frees a mesh.  Hierarchical matrices built on it must be destroyed first
+ * (BEM_E_STATE otherwise). */
+int bem_mesh_destroy(bem_mesh mesh);
+
+/* Number of triangles; -1 for a null handle. */
+int64_t bem_mesh_size(bem_mesh mesh);
+
+/* Dense sub-block of the Galerkin matrix (Eq. (1)-(3)):
+ *   out[a][b] = A(test_ids[a], trial_ids[b]),  row-major [n_test][n_trial],
+ * f64 for k == 0, interleaved complex128 otherwise.  Any pairs may be
+ * requested, including pairs that share vertices (evaluated by the singular
+ * rule, Sec. 3.2.3, on the device).  Ids must lie in [0, n_triangles);
+ * device-resident ids are checked on the device and a bad id makes the call
+ * return BEM_E_ARG at its next synchronisation (the call then waits for the
+ * stream).  test_ids, trial_ids and out may each be host or device memory.
+ * prec: BEM_FP64 or BEM_MIXED (regular pairs only; singular pairs are FP64).
+ * Allocates stream-ordered device scratch for the list of singular pairs.
+ * Returns after the stream is synchronised. */
+int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t *test_ids,
+                int64_t n_test, const int32_t *trial_ids, int64_t n_trial, void *out,
+                void *cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* Hierarchical matrices (Sec. 2.1; Algorithm "H-Matrix Assembly", Sec. 4.1)*/
+/* ---------------------------------------------------------------------- */
+
+/* Builds the cluster tree and the block cluster tree on the host ("purely
+ * geometry-based", Sec. 4.1) and uploads them, with the geometry in cluster
+ * order, to the device.
+ *  leaf_size  a cluster with more triangles is split in two along the longest
+ *             axis of its vertex bounding box, at the median of the triangle
+ *             centroids ((v0 + v1) + v2)/3 (ties by triangle index); leaves
+ *             list their triangles in increasing index order
+ *  eta        a block (tau, sigma) is admissible, i.e. compressed by ACA, iff
+ *             the bounding boxes are disjoint and
+ *             min(diam tau, diam sigma) <= eta * dist(tau, sigma)
+ *             (box diagonal and box distance); otherwise it is split, or
+ *             stored dense when tau or sigma is a leaf
+ * The handle keeps a reference to the mesh.  Synchronous. */
+int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out);
+
+/* Assembles the H-matrix of operator op and wavenumber k on the device:
+ * dense near-field blocks (regular pairs by Gauss, singular pairs by
+ * Sauter-Schwab) and, for every admissible block, ACA with partial pivoting
+ * (Sec. 2.1, Eq. (6)-(7), Algorithm ACA) run for all blocks by one
+ * persistent kernel fed from a device work queue.  ACA readings: the first
+ * row is the block's first row; later rows maximise |u_k| over unused rows
+ * (lowest index on ties); a row whose maximum is 0 or at most 1e-14 times the
+ * largest pivot so far "vanishes" and the smallest unused row is taken next;
+ * the loop stops once ||u_k|| ||v_k|| <= aca_eps ||S_k||_F, or when k reaches
+ * min(m, n) or the rank cap, or when all rows are used.
+ *  aca_eps  > 0
+ *  prec     BEM_FP64 or BEM_MIXED (see the top of this file)
+ * May be called again on the same handle (the previous matrix is replaced).
+ * Synchronous: it reads back the device status word; a bounded device wait
+ * that runs out gives BEM_E_TIMEOUT. */
+int hmat_assemble(bem_hmat hmat, int32_t op, double k, double aca_eps, int32_t prec,
+                  void *cuda_stream);
+
+/* y = A x for the assembled H-matrix, in the original triangle order
+ * (the cluster permutation is applied inside).  x and y hold `batch`
+ * vectors one after another, each n_triangles long, f64 for k == 0 and
+ * complex128 otherwise; host or device memory.  Uses buffers owned by the
+ * handle: concurrent products on one handle must be on the same stream.
+ * BEM_E_STATE before hmat_assemble. */
+int hmat_matvec(bem_hmat hmat, const void *x, void *y, int32_t batch, void *cuda_stream);
+
+typedef struct {
+    int64_t n_triangles;
+    int64_t n_clusters;
+    int64_t n_blocks_near;
+    int64_t n_blocks_far;
+    int64_t near_entries;        /* entries of all dense blocks */
+    int64_t singular_pairs[3];   /* vertex-, edge-adjacent, identical */
+    int64_t far_entries;         /* entries the ACA evaluated (rows + columns) */
+    int64_t factor_bytes;        /* bytes of U, V factors (allocated chunks) */
+    int64_t near_bytes;          /* bytes of the dense blocks */
+    int32_t rank_min, rank_max;
+    double rank_mean;
+    int64_t rank_capped_blocks;  /* blocks that stopped at the rank cap */
+    double time_tree_ms;         /* hmat_build_tree, host */
+    double time_near_ms;         /* last assembly: near field (device) */
+    double time_far_ms;          /* last assembly: ACA (device) */
+    int32_t assembled;
+    int32_t op;
+    double k;
+    double aca_eps;
+    int32_t prec;
+} bem_hmat_stats;
+
+/* Copies statistics of the handle into *out. */
+int hmat_stats(bem_hmat hmat, bem_hmat_stats *out);
+
+/* Block list in cluster order for inspection: rows of 5 int64
+ * (tau_begin, tau_end, sigma_begin, sigma_end, admissible) into host
+ * `blocks` (capacity `cap` rows) and the permutation (cluster position ->
+ * triangle id) into host `perm` (n_triangles).  *n_blocks receives the
+ * number of blocks; BEM_E_ARG if cap is too small. */
+int hmat_blocks(bem_hmat hmat, int64_t *blocks, int64_t cap, int64_t *n_blocks, int32_t *perm);
+
+/* Copies one assembled block to host memory as a dense row-major m x n
+ * array in cluster order (f64 or complex128): the near-field entries, or
+ * U V^T for an admissible block; *rank receives its ACA rank (-1 for a
+ * dense block). */
+int hmat_block_dense(bem_hmat hmat, int64_t block, void *out, int32_t *rank);
+
+/* Frees the handle and its device memory. */
+int hmat_destroy(bem_hmat hmat);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_H */

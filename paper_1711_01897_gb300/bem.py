@@ -1,0 +1,268 @@
+"""Thin Python binding of libbem.so (include/bem.h): the same call names,
+argument marshalling only.  Every step of the computation runs in the CUDA
+library; there is no fallback, and a missing library raises.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA);
+streams default to torch's current CUDA stream when torch is available.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbem.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bem.h")
+
+SLP, DLP, ADLP = 0, 1, 2
+FP64, MIXED = 0, 1
+STATUS = {0: "BEM_OK", 1: "BEM_E_ARG", 2: "BEM_E_MESH", 3: "BEM_E_OOM", 4: "BEM_E_CUDA",
+          5: "BEM_E_TIMEOUT", 6: "BEM_E_STATE"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class HmatStats(ctypes.Structure):
+    _fields_ = [("n_triangles", ctypes.c_int64), ("n_clusters", ctypes.c_int64),
+                ("n_blocks_near", ctypes.c_int64), ("n_blocks_far", ctypes.c_int64),
+                ("near_entries", ctypes.c_int64), ("singular_pairs", ctypes.c_int64 * 3),
+                ("far_entries", ctypes.c_int64), ("factor_bytes", ctypes.c_int64),
+                ("near_bytes", ctypes.c_int64), ("rank_min", ctypes.c_int32),
+                ("rank_max", ctypes.c_int32), ("rank_mean", ctypes.c_double),
+                ("rank_capped_blocks", ctypes.c_int64), ("time_tree_ms", ctypes.c_double),
+                ("time_near_ms", ctypes.c_double), ("time_far_ms", ctypes.c_double),
+                ("assembled", ctypes.c_int32), ("op", ctypes.c_int32), ("k", ctypes.c_double),
+                ("aca_eps", ctypes.c_double), ("prec", ctypes.c_int32)]
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/bem.h."""
+    with open(HEADER) as f:
+        src = f.read()
+    return re.findall(r"^\w[\w\s\*]*?\b((?:bem|hmat)_\w+)\s*\(", src, flags=re.M)
+
+
+def load(path: str = LIB_PATH):
+    """Loads libbem.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -m paper_1711_01897_gb300.build`")
+        L = ctypes.CDLL(path)
+        P, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "bem_version": ([], ctypes.c_int),
+            "bem_last_error": ([], ctypes.c_char_p),
+            "bem_mesh_create": ([P, i64, P, i64, P], ctypes.c_int),
+            "bem_mesh_destroy": ([P], ctypes.c_int),
+            "bem_mesh_size": ([P], i64),
+            "bem_entries": ([P, i32, dbl, i32, P, i64, P, i64, P, P], ctypes.c_int),
+            "hmat_build_tree": ([P, i32, dbl, P], ctypes.c_int),
+            "hmat_assemble": ([P, i32, dbl, dbl, i32, P], ctypes.c_int),
+            "hmat_matvec": ([P, P, P, i32, P], ctypes.c_int),
+            "hmat_stats": ([P, ctypes.POINTER(HmatStats)], ctypes.c_int),
+            "hmat_blocks": ([P, P, i64, P, P], ctypes.c_int),
+            "hmat_block_dense": ([P, i64, P, P], ctypes.c_int),
+            "hmat_destroy": ([P], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise BemError(rc, load().bem_last_error().decode())
+
+
+def _ptr(a):
+    """(pointer, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data), a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def bem_version() -> int:
+    return int(load().bem_version())
+
+
+def bem_last_error() -> str:
+    return load().bem_last_error().decode()
+
+
+def bem_mesh_create(vertices, triangles):
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    T = np.ascontiguousarray(triangles, dtype=np.int32)
+    if V.ndim != 2 or V.shape[1] != 3 or T.ndim != 2 or T.shape[1] != 3:
+        raise ValueError("vertices and triangles must be [n,3]")
+    h = ctypes.c_void_p()
+    _check(load().bem_mesh_create(V.ctypes.data, V.shape[0], T.ctypes.data, T.shape[0],
+                                  ctypes.byref(h)))
+    return h
+
+
+def bem_mesh_destroy(mesh):
+    _check(load().bem_mesh_destroy(mesh))
+
+
+def bem_mesh_size(mesh) -> int:
+    return int(load().bem_mesh_size(mesh))
+
+
+def bem_entries(mesh, op: int, k: float, prec: int, test_ids, trial_ids, out, stream=None):
+    pt, kt = _ptr(test_ids)
+    pj, kj = _ptr(trial_ids)
+    po, ko = _ptr(out)
+    _check(load().bem_entries(mesh, op, float(k), prec, pt, len(test_ids), pj, len(trial_ids), po,
+                              _stream(stream)))
+    del kt, kj, ko
+    return out
+
+
+def hmat_build_tree(mesh, leaf_size: int, eta: float):
+    h = ctypes.c_void_p()
+    _check(load().hmat_build_tree(mesh, int(leaf_size), float(eta), ctypes.byref(h)))
+    return h
+
+
+def hmat_assemble(hmat, op: int, k: float, aca_eps: float, prec: int, stream=None):
+    _check(load().hmat_assemble(hmat, op, float(k), float(aca_eps), prec, _stream(stream)))
+
+
+def hmat_matvec(hmat, x, y, batch: int = 1, stream=None):
+    px, kx = _ptr(x)
+    py, ky = _ptr(y)
+    _check(load().hmat_matvec(hmat, px, py, int(batch), _stream(stream)))
+    del kx, ky
+    return y
+
+
+def hmat_stats(hmat) -> dict:
+    s = HmatStats()
+    _check(load().hmat_stats(hmat, ctypes.byref(s)))
+    d = {name: getattr(s, name) for name, _ in HmatStats._fields_}
+    d["singular_pairs"] = list(s.singular_pairs)
+    return d
+
+
+def hmat_blocks(hmat):
+    """(blocks int64 [n,5] in cluster order, perm int32 [n_triangles])."""
+    L = load()
+    n = ctypes.c_int64()
+    _check(L.hmat_blocks(hmat, None, 0, ctypes.byref(n), None))
+    nt = hmat_stats(hmat)["n_triangles"]
+    blocks = np.zeros((n.value, 5), dtype=np.int64)
+    perm = np.zeros(nt, dtype=np.int32)
+    _check(L.hmat_blocks(hmat, blocks.ctypes.data, n.value, ctypes.byref(n), perm.ctypes.data))
+    return blocks, perm
+
+
+def hmat_block_dense(hmat, block: int, shape, cplx: bool):
+    out = np.zeros(shape, dtype=np.complex128 if cplx else np.float64)
+    r = ctypes.c_int32()
+    _check(load().hmat_block_dense(hmat, int(block), out.ctypes.data, ctypes.byref(r)))
+    return out, int(r.value)
+
+
+def hmat_destroy(hmat):
+    _check(load().hmat_destroy(hmat))
+
+
+class Mesh:
+    """Owns a bem_mesh handle."""
+
+    def __init__(self, vertices, triangles):
+        self.handle = bem_mesh_create(vertices, triangles)
+        self.n = bem_mesh_size(self.handle)
+
+    def entries(self, op, k, prec, test_ids, trial_ids, out=None, stream=None):
+        if out is None:
+            out = np.zeros((len(test_ids), len(trial_ids)),
+                           dtype=np.complex128 if k != 0 else np.float64)
+        return bem_entries(self.handle, op, k, prec, test_ids, trial_ids, out, stream)
+
+    def close(self):
+        if self.handle is not None:
+            bem_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HMatrix:
+    """Owns a bem_hmat handle built on a Mesh."""
+
+    def __init__(self, mesh: Mesh, leaf_size: int = 32, eta: float = 1.2):
+        self.mesh = mesh
+        self.handle = hmat_build_tree(mesh.handle, leaf_size, eta)
+        self.cplx = False
+
+    def assemble(self, op, k, aca_eps, prec, stream=None):
+        hmat_assemble(self.handle, op, k, aca_eps, prec, stream)
+        self.cplx = k != 0
+
+    def matvec(self, x, y=None, batch=1, stream=None):
+        if y is None:
+            y = np.zeros_like(x)
+        return hmat_matvec(self.handle, x, y, batch, stream)
+
+    def stats(self):
+        return hmat_stats(self.handle)
+
+    def blocks(self):
+        return hmat_blocks(self.handle)
+
+    def block_dense(self, b, shape):
+        return hmat_block_dense(self.handle, b, shape, self.cplx)
+
+    def close(self):
+        if self.handle is not None:
+            hmat_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,348 @@
+// Device helpers shared by the kernels: geometry access, float-float
+// accumulation and the per-entry quadrature of the regular and singular
+// rules.  Header-only; every .cu file gets its own copy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "bem_internal.h"
+
+namespace bem {
+
+constexpr double kInv4Pi = 0.25 / CUDART_PI;
+
+struct C2 {
+    double re, im;
+};
+
+__device__ __forceinline__ C2 cadd(C2 a, C2 b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ C2 csub(C2 a, C2 b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ C2 cmul(C2 a, C2 b)
+{
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ C2 cconjmul(C2 a, C2 b)  // conj(a) * b
+{
+    return {fma(a.re, b.re, a.im * b.im), fma(a.re, b.im, -a.im * b.re)};
+}
+__device__ __forceinline__ double cabs2(C2 a) { return fma(a.re, a.re, a.im * a.im); }
+
+// ---- float-float accumulation (Knuth's TwoSum) ---------------------------
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add(FF &a, float x)
+{
+    float s = __fadd_rn(a.hi, x);
+    float bp = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+
+// Exact product a*b as float-float (FMA error term).
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return {p, e};
+}
+
+// Exact widening of a finite float to double from its IEEE-754 fields, on
+// the integer pipe (the FP64 pipe is the scarce unit on this part).
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    unsigned b = __float_as_uint(f);
+    unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0.0;  // zero (subnormal partial sums do not occur)
+    unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    unsigned lo = b << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ double ff_to_double(FF a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
+
+// ---- triangle views -------------------------------------------------------
+struct TriF {           // mixed-precision view
+    float ch[3], cl[3];
+    float q[NQ][3];     // quadrature points relative to the centroid
+    float n[3];
+    FF s;               // area / sqrt(4 pi)
+};
+
+struct TriD {           // FP64 view
+    double q[NQ][3];
+    double n[3];
+    double area;
+};
+
+__device__ __forceinline__ void load_trif(const DevGeom &g, int64_t p, TriF &t)
+{
+    const int64_t n = g.nt;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        t.ch[c] = __ldg(g.ch + c * n + p);
+        t.cl[c] = __ldg(g.cl + c * n + p);
+        t.n[c] = __ldg(g.nrmf + c * n + p);
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t.q[q][c] = __ldg(g.qo + (q * 3 + c) * n + p);
+    t.s.hi = __ldg(g.sc + p);
+    t.s.lo = __ldg(g.sc + n + p);
+}
+
+__device__ __forceinline__ void load_trid(const DevGeom &g, int64_t p, TriD &t)
+{
+    const int64_t n = g.nt;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t.n[c] = __ldg(g.nrm + c * n + p);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t.q[q][c] = __ldg(g.qp + (q * 3 + c) * n + p);
+    t.area = __ldg(g.area + p);
+}
+
+__device__ __forceinline__ int shared_count(const DevGeom &g, int64_t a, int64_t b)
+{
+    const int64_t n = g.nt;
+    int ta[3], tb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ta[c] = __ldg(g.tri + c * n + a);
+        tb[c] = __ldg(g.tri + c * n + b);
+    }
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s += (ta[i] == tb[j]);
+    return s;
+}
+
+// ---- regular entries, mixed precision (Laplace) --------------------------
+// A_ij = |T_i||T_j|/(4 pi) sum_p sum_q w_p w_q K(x_p - y_q), with
+// K = 1/r (SLP), d.n_y/r^3 (DLP), -d.n_x/r^3 (ADLP), d = x - y.
+// Geometry relative to the centroids: d = (c_i - c_j) + (dx_p - dy_q); the
+// points lie in their triangle's plane, so d.n_y depends on p only and
+// d.n_x on q only.  Each test point's 6-term FP32 sum is folded into a
+// float-float accumulator.
+template <int OP>
+__device__ __forceinline__ double entry_mixed_laplace(const TriF &a, const TriF &b,
+                                                      const float *__restrict__ w)
+{
+    float D[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) D[c] = (a.ch[c] - b.ch[c]) + (a.cl[c] - b.cl[c]);
+    float cq[NQ];
+    if (OP == 2) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            cq[q] = -w[q] * ((D[0] - b.q[q][0]) * a.n[0] + (D[1] - b.q[q][1]) * a.n[1] +
+                             (D[2] - b.q[q][2]) * a.n[2]);
+    }
+    FF acc = {0.f, 0.f};
+#pragma unroll
+    for (int p = 0; p < NQ; ++p) {
+        float Dp0 = D[0] + a.q[p][0], Dp1 = D[1] + a.q[p][1], Dp2 = D[2] + a.q[p][2];
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float d0 = Dp0 - b.q[q][0], d1 = Dp1 - b.q[q][1], d2 = Dp2 - b.q[q][2];
+            float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+            float ri = rsqrtf(r2);
+            if (OP == 0) s = fmaf(w[q], ri, s);
+            else if (OP == 1) s = fmaf(w[q], ri * ri * ri, s);
+            else s = fmaf(cq[q], ri * ri * ri, s);
+        }
+        if (OP == 1) s *= Dp0 * b.n[0] + Dp1 * b.n[1] + Dp2 * b.n[2];
+        ff_add(acc, w[p] * s);
+    }
+    FF scale = ff_mul(a.s, b.s);
+    FF hi = ff_mul({acc.hi, 0.f}, scale);
+    FF lo = ff_mul({acc.lo, 0.f}, scale);
+    return (f2d_exact(hi.hi) + f2d_exact(hi.lo)) + f2d_exact(lo.hi);
+}
+
+// ---- regular entries, FP64 (Laplace and Helmholtz) -----------------------
+template <int OP, bool CPLX>
+__device__ __forceinline__ C2 entry_fp64(const TriD &a, const TriD &b, const double *__restrict__ w,
+                                         double k)
+{
+    C2 acc = {0.0, 0.0};
+#pragma unroll 1
+    for (int p = 0; p < NQ; ++p) {
+        C2 s = {0.0, 0.0};
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double d0 = a.q[p][0] - b.q[q][0], d1 = a.q[p][1] - b.q[q][1],
+                   d2 = a.q[p][2] - b.q[q][2];
+            double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
+            double ri = rsqrt(r2);
+            double amp;  // real factor multiplying exp(ikr)
+            if (OP == 0) amp = ri;
+            else if (OP == 1) amp = (d0 * b.n[0] + d1 * b.n[1] + d2 * b.n[2]) * ri * ri * ri;
+            else amp = -(d0 * a.n[0] + d1 * a.n[1] + d2 * a.n[2]) * ri * ri * ri;
+            if (!CPLX) {
+                s.re = fma(w[q], amp, s.re);
+            } else {
+                double r = r2 * ri, sn, cs;
+                sincos(k * r, &sn, &cs);
+                if (OP == 0) {
+                    s.re = fma(w[q] * amp, cs, s.re);
+                    s.im = fma(w[q] * amp, sn, s.im);
+                } else {
+                    // exp(ikr)(ikr - 1)(-d.n_y) = exp(ikr)(1 - ikr) d.n_y (DLP);
+                    // likewise for ADLP with d.n_x: amp already holds -/+ d.n
+                    double kr = k * r;
+                    double fr = cs + kr * sn;   // Re[exp(ikr)(1 - ikr)]
+                    double fi = sn - kr * cs;   // Im[exp(ikr)(1 - ikr)]
+                    s.re = fma(w[q] * amp, fr, s.re);
+                    s.im = fma(w[q] * amp, fi, s.im);
+                }
+            }
+        }
+        acc.re = fma(w[p], s.re, acc.re);
+        acc.im = fma(w[p], s.im, acc.im);
+    }
+    double sc = a.area * b.area * kInv4Pi;
+    return {acc.re * sc, acc.im * sc};
+}
+
+// ---- regular entries, mixed precision (Helmholtz) ------------------------
+// exp(ikr) = exp(ik R0) exp(ik (r - R0)) with R0 the centroid distance.  R0
+// and its phase are formed in float-float and reduced modulo 2 pi, so the
+// large phase k R0 keeps an absolute error far below 1e-6; the small phase
+// k (r - R0) = k e.(2D + e)/(r + R0), e = dx_p - dy_q, is evaluated per point.
+__device__ __forceinline__ void ff_two_diff(float a, float b, float &s, float &e)
+{
+    s = __fsub_rn(a, b);
+    float bp = __fsub_rn(a, s);
+    e = __fadd_rn(__fsub_rn(a, __fadd_rn(s, bp)), __fsub_rn(bp, b));
+}
+
+template <int OP>
+__device__ __forceinline__ C2 entry_mixed_helmholtz(const TriF &a, const TriF &b,
+                                                    const float *__restrict__ w, float kf,
+                                                    double k)
+{
+    // centroid difference in float-float
+    float Dh[3], Dl[3], D[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float s, e;
+        ff_two_diff(a.ch[c], b.ch[c], s, e);
+        Dh[c] = s;
+        Dl[c] = e + (a.cl[c] - b.cl[c]);
+        D[c] = Dh[c] + Dl[c];
+    }
+    // R0^2 = |D|^2 in float-float, then R0 = sqrt with one Newton correction
+    FF r02 = {0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        FF sq = ff_mul({Dh[c], 0.f}, {Dh[c], 0.f});
+        ff_add(r02, sq.hi);
+        ff_add(r02, sq.lo);
+        ff_add(r02, 2.f * Dh[c] * Dl[c]);
+    }
+    float R0 = sqrtf(r02.hi);
+    FF R0sq = ff_mul({R0, 0.f}, {R0, 0.f});
+    float R0lo = ((r02.hi - R0sq.hi) - R0sq.lo + r02.lo) / (2.f * R0);
+    // phase k R0 in FP64 from the float-float radius (two FP64 ops), reduced
+    double ph = k * ((double)R0 + (double)R0lo);
+    double nrev = rint(ph * (0.5 / CUDART_PI));
+    float th = (float)fma(-nrev, 2.0 * CUDART_PI, ph);
+    float s0, c0;
+    sincosf(th, &s0, &c0);
+    float R0f = R0;
+    float cq[NQ];
+    if (OP == 2) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            cq[q] = (D[0] - b.q[q][0]) * a.n[0] + (D[1] - b.q[q][1]) * a.n[1] +
+                    (D[2] - b.q[q][2]) * a.n[2];
+    }
+    FF are = {0.f, 0.f}, aim = {0.f, 0.f};
+#pragma unroll
+    for (int p = 0; p < NQ; ++p) {
+        float Dp0 = D[0] + a.q[p][0], Dp1 = D[1] + a.q[p][1], Dp2 = D[2] + a.q[p][2];
+        float dny = (OP == 1) ? (Dp0 * b.n[0] + Dp1 * b.n[1] + Dp2 * b.n[2]) : 0.f;
+        float sre = 0.f, sim = 0.f;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float e0 = a.q[p][0] - b.q[q][0], e1 = a.q[p][1] - b.q[q][1], e2 = a.q[p][2] - b.q[q][2];
+            float d0 = D[0] + e0, d1 = D[1] + e1, d2 = D[2] + e2;
+            float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+            float ri = rsqrtf(r2);
+            float r = r2 * ri;
+            float dr2 = fmaf(e0, 2.f * D[0] + e0, fmaf(e1, 2.f * D[1] + e1, e2 * (2.f * D[2] + e2)));
+            float phi = kf * dr2 / (r + R0f);
+            float sp, cp;
+            __sincosf(phi, &sp, &cp);
+            float fr, fi, amp;
+            if (OP == 0) {
+                amp = w[q] * ri;
+                fr = cp;
+                fi = sp;
+            } else {
+                // exp(i phi)(1 - ikr) times the normal factor
+                float kr = kf * r;
+                fr = fmaf(kr, sp, cp);
+                fi = fmaf(-kr, cp, sp);
+                float nf = (OP == 1) ? dny : -cq[q];
+                amp = w[q] * nf * ri * ri * ri;
+            }
+            sre = fmaf(amp, fr, sre);
+            sim = fmaf(amp, fi, sim);
+        }
+        ff_add(are, w[p] * sre);
+        ff_add(aim, w[p] * sim);
+    }
+    double sc = ff_to_double(ff_mul(a.s, b.s));
+    double xr = ff_to_double(are) * sc, xi = ff_to_double(aim) * sc;
+    double cr = (double)c0, ci = (double)s0;
+    return {fma(xr, cr, -xi * ci), fma(xr, ci, xi * cr)};
+}
+
+// ---- one regular entry, dispatched on the precision ------------------------
+// Views are loaded by the caller so that a row (or column) reuses its fixed
+// triangle.
+template <int OP, bool CPLX, int PREC>
+struct RegularEntry;
+
+template <int OP, bool CPLX>
+struct RegularEntry<OP, CPLX, 0> {  // FP64
+    using Tri = TriD;
+    static __device__ __forceinline__ void load(const DevGeom &g, int64_t p, Tri &t)
+    {
+        load_trid(g, p, t);
+    }
+    static __device__ __forceinline__ C2 eval(const Tri &a, const Tri &b, const QuadRule &R,
+                                              double k)
+    {
+        return entry_fp64<OP, CPLX>(a, b, R.w, k);
+    }
+};
+
+template <int OP, bool CPLX>
+struct RegularEntry<OP, CPLX, 1> {  // mixed
+    using Tri = TriF;
+    static __device__ __forceinline__ void load(const DevGeom &g, int64_t p, Tri &t)
+    {
+        load_trif(g, p, t);
+    }
+    static __device__ __forceinline__ C2 eval(const Tri &a, const Tri &b, const QuadRule &R,
+                                              double k)
+    {
+        if (!CPLX) return {entry_mixed_laplace<OP>(a, b, R.wf), 0.0};
+        return entry_mixed_helmholtz<OP>(a, b, R.wf, (float)k, k);
+    }
+};
+
+}  // namespace bem

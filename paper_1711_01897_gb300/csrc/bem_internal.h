@@ -1,0 +1,117 @@
+// Internal host/device declarations of the GB300 BEM library.  Not part of
+// the public ABI (include/bem.h).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+
+#include <cuda_runtime.h>
+
+namespace bem {
+
+constexpr int NQ = 6;          // points of the regular triangle rule (degree 4)
+constexpr int NGL = 4;         // Gauss-Legendre points per axis, singular rule
+constexpr int KCHUNK = 16;     // ACA factor columns allocated at a time
+constexpr int KMAX = 128;      // rank cap of one admissible block
+constexpr int NCHUNK = KMAX / KCHUNK;
+
+// Geometry of a triangle set in some order (identity for a mesh, cluster
+// order for an H-matrix), structure-of-arrays in device memory.
+struct DevGeom {
+    int64_t nt;
+    const int32_t *tri;    // [3][nt] vertex ids
+    const double *vtx;     // [9][nt] v0.xyz v1.xyz v2.xyz
+    const double *nrm;     // [3][nt] unit normal (right-hand rule)
+    const double *area;    // [nt]
+    const double *qp;      // [3*NQ][nt] quadrature points, q*3 + c
+    const float *ch;       // [3][nt] centroid, high part
+    const float *cl;       // [3][nt] centroid, low part (centroid - ch)
+    const float *qo;       // [3*NQ][nt] points minus centroid
+    const float *nrmf;     // [3][nt]
+    const float *sc;       // [2][nt] area / sqrt(4 pi) as float-float (hi, lo)
+};
+
+// Regular rule: reference points and weights (sum 1).
+struct QuadRule {
+    double s[NQ], t[NQ], w[NQ];
+    float wf[NQ];
+};
+
+// Singular rule tables for one case (1 vertex-, 2 edge-adjacent, 3
+// identical).  Each 4D Gauss-Legendre node of the Sauter-Schwab maps gives
+// d = x - y as a combination sum_i c_i E_i of the case's edge vectors E_i.
+//  lap:  nodes with the same direction c/|c|_max merged (exact for any
+//        geometry); rows c0..c3 (normalised direction), w_slp = sum w J/rho,
+//        w_dlp = sum w J/rho^2 with rho = |c|_max.  Used for k == 0.
+//  helm: all maps are homogeneous of degree one in xi, so the table lists
+//        the eta nodes (rows c0..c3 of d/xi and w_eta = weights times the
+//        eta part of the Jacobian) and the xi axis is summed in the kernel.
+struct SingTable {
+    int n_lap;
+    int n_helm;
+    const double *lap;     // [6][n_lap]
+    const double *helm;    // [5][n_helm]
+    double xi[NGL], wxi[NGL];
+};
+
+struct SingPair {
+    int32_t i, j;          // triangle ids in the mesh's own order
+    int64_t dest;          // element offset of the result
+};
+
+struct FarBlock {
+    int64_t tb, te, sb, se;         // cluster-order ranges (rows: tau)
+    int64_t chunk[NCHUNK];          // element offsets of factor chunks
+    int32_t rank;
+    int32_t status;                 // 0 ok, 1 rank cap, 2 pool overflow
+    int64_t entries;                // entries evaluated by ACA
+};
+
+struct NearBlock {
+    int64_t tb, te, sb, se;
+    int64_t off;                    // element offset of the dense block
+};
+
+struct Pool {
+    unsigned long long top;         // elements used
+    unsigned long long cap;         // elements available
+    int overflow;
+    int pad;
+};
+
+struct AcaQueue {
+    unsigned int next_big;
+    unsigned int next_small;
+};
+
+// ---- launchers (defined in the .cu files) -------------------------------
+cudaError_t launch_geometry(const double *V, const int32_t *T, const int32_t *perm, int64_t nt,
+                            const QuadRule &rule, void *const bufs[11], cudaStream_t st);
+
+cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int op, double k,
+                                   int prec, const int32_t *test, int64_t n_test,
+                                   const int32_t *trial, int64_t n_trial, void *out,
+                                   SingPair *lists[3], unsigned long long *counts,
+                                   unsigned long long cap, int *err, cudaStream_t st);
+
+cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k,
+                            const SingPair *pairs[3], const unsigned long long *dev_counts,
+                            const int64_t host_counts[3], void *out, cudaStream_t st);
+
+cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
+                                const NearBlock *blocks, int64_t nblocks, void *out,
+                                cudaStream_t st);
+
+cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
+                       double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,
+                       int64_t max_m_big, void *pool_data, Pool *pool, AcaQueue *queue,
+                       int num_sms, cudaStream_t st);
+
+cudaError_t launch_matvec(bool cplx, int64_t n, const int32_t *perm, const void *x, void *y,
+                          void *xt, void *yt, void *tbuf, const FarBlock *far, int64_t nfar,
+                          const int64_t *toff, const void *pool_data, const NearBlock *near,
+                          const void *near_data, const int64_t *leaf_rows,
+                          const int64_t *leaf_ptr, const int64_t *leaf_items, int64_t nleaf,
+                          cudaStream_t st);
+
+}  // namespace bem

@@ -1,0 +1,1190 @@
+// Host side of the GB300 BEM library: the C ABI of include/bem.h, mesh
+// validation and adjacency, quadrature tables, the cluster and block
+// cluster trees (Sec. 2.1; Algorithm "H-Matrix Assembly", Sec. 4.1) and the
+// orchestration of the device kernels.
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/bem.h"
+#include "bem_internal.h"
+
+using namespace bem;
+
+namespace bem {
+int aca_small_max();
+}
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+struct CudaFail {
+    int code;
+};
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            g_err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
+            throw CudaFail{e_ == cudaErrorMemoryAllocation ? BEM_E_OOM : BEM_E_CUDA};     \
+        }                                                                                 \
+    } while (0)
+
+template <class F>
+int guarded(F &&f)
+{
+    try {
+        g_err.clear();
+        return f();
+    } catch (const CudaFail &c) {
+        return c.code;
+    } catch (const std::bad_alloc &) {
+        return fail(BEM_E_OOM, "host allocation failed");
+    } catch (const std::exception &ex) {
+        return fail(BEM_E_ARG, ex.what());
+    }
+}
+
+// device buffer owned by RAII
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void alloc(size_t b)
+    {
+        release();
+        if (b == 0) b = 16;
+        CU(cudaMalloc(&p, b));
+        bytes = b;
+    }
+    template <class T>
+    T *as() const
+    {
+        return reinterpret_cast<T *>(p);
+    }
+    template <class T>
+    void upload(const std::vector<T> &v)
+    {
+        alloc(v.size() * sizeof(T));
+        if (!v.empty()) CU(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+};
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// ---------------------------------------------------------------------------
+// quadrature tables (derived here, independently of any test code)
+// ---------------------------------------------------------------------------
+
+// Gauss-Legendre nodes on [0,1] by Golub-Welsch: eigenvalues of the
+// symmetric Jacobi matrix of the Legendre recurrence (off-diagonal
+// k / sqrt(4k^2 - 1)), found by cyclic Jacobi rotations; the weights are
+// twice the squared first components of the eigenvectors.
+void gauss_legendre01(int n, double *x, double *w)
+{
+    std::vector<double> A(n * n, 0.0), Q(n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[i * n + i] = 1.0;
+    for (int k = 1; k < n; ++k) {
+        double b = k / std::sqrt(4.0 * k * k - 1.0);
+        A[(k - 1) * n + k] = A[k * n + k - 1] = b;
+    }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+        if (off < 1e-34) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) /
+                           (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // A <- A J
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // A <- J^T A
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double qkp = Q[k * n + p], qkq = Q[k * n + q];
+                    Q[k * n + p] = c * qkp - s * qkq;
+                    Q[k * n + q] = s * qkp + c * qkq;
+                }
+            }
+    }
+    std::vector<std::pair<double, double>> nw(n);
+    for (int i = 0; i < n; ++i) nw[i] = {0.5 * (1.0 + A[i * n + i]), Q[i] * Q[i]};
+    std::sort(nw.begin(), nw.end());
+    for (int i = 0; i < n; ++i) {
+        x[i] = nw[i].first;
+        w[i] = nw[i].second;  // 2 v0^2 on [-1,1], halved on [0,1]
+    }
+}
+
+// Symmetric 6-point rule of degree 4 (Sec. 3.2.1): orbits (a,a,1-2a) and
+// (b,b,1-2b).  For given (a,b) the orbit weights follow from the moments of
+// 1 and e2 (a 2x2 linear system); (a,b) then solve the moments of e3 and
+// e2^2 (1/60, 1/15) by Newton's method with a difference Jacobian.
+QuadRule make_rule6()
+{
+    auto e2 = [](double a) { return 2 * a - 3 * a * a; };
+    auto e3 = [](double a) { return a * a * (1 - 2 * a); };
+    auto weights = [&](double a, double b, double &W1, double &W2) {
+        W1 = (0.25 - e2(b)) / (e2(a) - e2(b));
+        W2 = 1.0 - W1;
+    };
+    auto resid = [&](double a, double b, double r[2]) {
+        double W1, W2;
+        weights(a, b, W1, W2);
+        r[0] = W1 * e3(a) + W2 * e3(b) - 1.0 / 60.0;
+        r[1] = W1 * e2(a) * e2(a) + W2 * e2(b) * e2(b) - 1.0 / 15.0;
+    };
+    double a = 0.44, b = 0.09;
+    for (int it = 0; it < 60; ++it) {
+        double r[2], ra[2], rb[2], h = 1e-7;
+        resid(a, b, r);
+        double rap[2], ram[2], rbp[2], rbm[2];
+        resid(a + h, b, rap);
+        resid(a - h, b, ram);
+        resid(a, b + h, rbp);
+        resid(a, b - h, rbm);
+        for (int c = 0; c < 2; ++c) {
+            ra[c] = (rap[c] - ram[c]) / (2 * h);
+            rb[c] = (rbp[c] - rbm[c]) / (2 * h);
+        }
+        double det = ra[0] * rb[1] - rb[0] * ra[1];
+        double da = (r[0] * rb[1] - rb[0] * r[1]) / det;
+        double db = (ra[0] * r[1] - r[0] * ra[1]) / det;
+        a -= da;
+        b -= db;
+        if (std::fabs(da) + std::fabs(db) < 1e-18) break;
+    }
+    double W1, W2;
+    weights(a, b, W1, W2);
+    QuadRule R{};
+    const double orb[2] = {a, b}, ow[2] = {W1 / 3.0, W2 / 3.0};
+    int k = 0;
+    for (int o = 0; o < 2; ++o) {
+        double q = orb[o], r = 1.0 - 2.0 * q;
+        const double bary[3][3] = {{q, q, r}, {q, r, q}, {r, q, q}};
+        for (int m = 0; m < 3; ++m, ++k) {
+            R.s[k] = bary[m][1];
+            R.t[k] = bary[m][2];
+            R.w[k] = ow[o];
+            R.wf[k] = (float)ow[o];
+        }
+    }
+    return R;
+}
+
+// Sauter-Schwab maps of [0,1]^4 onto T^ x T^ (T^ = {0 <= x2 <= x1 <= 1})
+// for vertex- (1), edge-adjacent (2) and identical (3) panels, after the
+// Erichsen-Sauter scheme (Sec. 3.2.3).  Returns the Jacobian.
+double ss_map(int c, int r, double xi, double a, double b, double g, double X[2], double Y[2])
+{
+    if (c == 3) {
+        switch (r) {
+        case 0: X[0] = xi; X[1] = xi * (1 - a + a * b); Y[0] = xi * (1 - a * b * g); Y[1] = xi * (1 - a); break;
+        case 1: X[0] = xi * (1 - a * b * g); X[1] = xi * (1 - a); Y[0] = xi; Y[1] = xi * (1 - a + a * b); break;
+        case 2: X[0] = xi; X[1] = xi * a * (1 - b + b * g); Y[0] = xi * (1 - a * b); Y[1] = xi * a * (1 - b); break;
+        case 3: X[0] = xi * (1 - a * b); X[1] = xi * a * (1 - b); Y[0] = xi; Y[1] = xi * a * (1 - b + b * g); break;
+        case 4: X[0] = xi * (1 - a * b * g); X[1] = xi * a * (1 - b * g); Y[0] = xi; Y[1] = xi * a * (1 - b); break;
+        default: X[0] = xi; X[1] = xi * a * (1 - b); Y[0] = xi * (1 - a * b * g); Y[1] = xi * a * (1 - b * g); break;
+        }
+        return xi * xi * xi * a * a * b;
+    }
+    if (c == 2) {
+        switch (r) {
+        case 0: X[0] = xi; X[1] = xi * a * g; Y[0] = xi * (1 - a * b); Y[1] = xi * a * (1 - b);
+            return xi * xi * xi * a * a;
+        case 1: X[0] = xi; X[1] = xi * a; Y[0] = xi * (1 - a * b * g); Y[1] = xi * a * b * (1 - g); break;
+        case 2: X[0] = xi * (1 - a * b); X[1] = xi * a * (1 - b); Y[0] = xi; Y[1] = xi * a * b * g; break;
+        case 3: X[0] = xi * (1 - a * b * g); X[1] = xi * a * b * (1 - g); Y[0] = xi; Y[1] = xi * a; break;
+        default: X[0] = xi * (1 - a * b * g); X[1] = xi * a * (1 - b * g); Y[0] = xi; Y[1] = xi * a * b; break;
+        }
+        return xi * xi * xi * a * a * b;
+    }
+    if (r == 0) { X[0] = xi; X[1] = xi * a; Y[0] = xi * b; Y[1] = xi * b * g; }
+    else { X[0] = xi * b; X[1] = xi * b * g; Y[0] = xi; Y[1] = xi * a; }
+    return xi * xi * xi * b;
+}
+
+// d = x - y in the case's edge basis (see SingTable).
+void ss_coef(int c, const double X[2], const double Y[2], double cf[4])
+{
+    if (c == 3) { cf[0] = X[0] - Y[0]; cf[1] = X[1] - Y[1]; cf[2] = cf[3] = 0.0; }
+    else if (c == 2) { cf[0] = X[0] - Y[0]; cf[1] = X[1]; cf[2] = -Y[1]; cf[3] = 0.0; }
+    else { cf[0] = X[0]; cf[1] = X[1]; cf[2] = -Y[0]; cf[3] = -Y[1]; }
+}
+
+struct HostSingTable {
+    std::vector<double> lap, helm;  // row-major [6][n_lap], [5][n_helm]
+    int n_lap = 0, n_helm = 0;
+};
+
+HostSingTable make_sing_table(int c, const double *x, const double *w)
+{
+    const int R = c == 3 ? 6 : (c == 2 ? 5 : 2);
+    HostSingTable T;
+    // Laplace: merge nodes of equal direction c/|c|_max
+    std::map<std::array<long long, 4>, int> key_to_idx;
+    std::vector<std::array<double, 6>> rows;
+    for (int r = 0; r < R; ++r)
+        for (int i0 = 0; i0 < NGL; ++i0)
+            for (int i1 = 0; i1 < NGL; ++i1)
+                for (int i2 = 0; i2 < NGL; ++i2)
+                    for (int i3 = 0; i3 < NGL; ++i3) {
+                        double X[2], Y[2], cf[4];
+                        double J = ss_map(c, r, x[i0], x[i1], x[i2], x[i3], X, Y);
+                        ss_coef(c, X, Y, cf);
+                        double W = w[i0] * w[i1] * w[i2] * w[i3] * J;
+                        double rho = 0.0;
+                        for (int q = 0; q < 4; ++q) rho = std::max(rho, std::fabs(cf[q]));
+                        std::array<long long, 4> key;
+                        double v[4];
+                        for (int q = 0; q < 4; ++q) {
+                            v[q] = cf[q] / rho;
+                            key[q] = std::llround(v[q] * 68719476736.0);  // 2^36
+                        }
+                        auto it = key_to_idx.find(key);
+                        if (it == key_to_idx.end()) {
+                            key_to_idx[key] = (int)rows.size();
+                            rows.push_back({v[0], v[1], v[2], v[3], W / rho, W / (rho * rho)});
+                        } else {
+                            rows[it->second][4] += W / rho;
+                            rows[it->second][5] += W / (rho * rho);
+                        }
+                    }
+    T.n_lap = (int)rows.size();
+    T.lap.assign(6 * T.n_lap, 0.0);
+    for (int q = 0; q < T.n_lap; ++q)
+        for (int rr = 0; rr < 6; ++rr) T.lap[rr * T.n_lap + q] = rows[q][rr];
+    // Helmholtz: eta nodes at xi = 1 (all maps are homogeneous in xi)
+    T.n_helm = R * NGL * NGL * NGL;
+    T.helm.assign(5 * T.n_helm, 0.0);
+    int q = 0;
+    for (int r = 0; r < R; ++r)
+        for (int i1 = 0; i1 < NGL; ++i1)
+            for (int i2 = 0; i2 < NGL; ++i2)
+                for (int i3 = 0; i3 < NGL; ++i3, ++q) {
+                    double X[2], Y[2], cf[4];
+                    double J = ss_map(c, r, 1.0, x[i1], x[i2], x[i3], X, Y);
+                    ss_coef(c, X, Y, cf);
+                    for (int rr = 0; rr < 4; ++rr) T.helm[rr * T.n_helm + q] = cf[rr];
+                    T.helm[4 * T.n_helm + q] = w[i1] * w[i2] * w[i3] * J;
+                }
+    return T;
+}
+
+// Per-device constant data: rules and singular tables.
+struct DeviceConsts {
+    QuadRule rule;
+    SingTable sing[3];
+    DBuf bufs[6];
+    int num_sms = 0;
+};
+
+std::mutex g_dev_mu;
+std::map<int, std::unique_ptr<DeviceConsts>> g_dev;
+
+DeviceConsts &device_consts()
+{
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    auto it = g_dev.find(dev);
+    if (it != g_dev.end()) return *it->second;
+    auto D = std::make_unique<DeviceConsts>();
+    D->rule = make_rule6();
+    double x[NGL], w[NGL];
+    gauss_legendre01(NGL, x, w);
+    for (int c = 1; c <= 3; ++c) {
+        HostSingTable H = make_sing_table(c, x, w);
+        // the singular kernel stages a table of at most 6 * NGL^3 points
+        if (H.n_lap > 6 * NGL * NGL * NGL || H.n_helm > 6 * NGL * NGL * NGL)
+            throw std::runtime_error("singular quadrature table too large");
+        DBuf &bl = D->bufs[2 * (c - 1)], &bh = D->bufs[2 * (c - 1) + 1];
+        bl.upload(H.lap);
+        bh.upload(H.helm);
+        SingTable &S = D->sing[c - 1];
+        S.n_lap = H.n_lap;
+        S.n_helm = H.n_helm;
+        S.lap = bl.as<double>();
+        S.helm = bh.as<double>();
+        for (int i = 0; i < NGL; ++i) {
+            S.xi[i] = x[i];
+            S.wxi[i] = w[i];
+        }
+    }
+    CU(cudaDeviceGetAttribute(&D->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    DeviceConsts &ref = *D;
+    g_dev[dev] = std::move(D);
+    return ref;
+}
+
+// Device geometry owned by a mesh or an H-matrix.
+struct GeomStore {
+    DBuf tri, vtx, nrm, area, qp, ch, cl, qo, nrmf, sc;
+    DevGeom g{};
+    void build(const double *dV, const int32_t *dT, const int32_t *dperm, int64_t nt,
+               const QuadRule &R, cudaStream_t st)
+    {
+        tri.alloc(3 * nt * sizeof(int32_t));
+        vtx.alloc(9 * nt * sizeof(double));
+        nrm.alloc(3 * nt * sizeof(double));
+        area.alloc(nt * sizeof(double));
+        qp.alloc(3 * NQ * nt * sizeof(double));
+        ch.alloc(3 * nt * sizeof(float));
+        cl.alloc(3 * nt * sizeof(float));
+        qo.alloc(3 * NQ * nt * sizeof(float));
+        nrmf.alloc(3 * nt * sizeof(float));
+        sc.alloc(2 * nt * sizeof(float));
+        void *const b[11] = {tri.p, vtx.p, nrm.p, area.p, qp.p, ch.p, cl.p, qo.p, nrmf.p, sc.p,
+                             nullptr};
+        CU(launch_geometry(dV, dT, dperm, nt, R, b, st));
+        g.nt = nt;
+        g.tri = tri.as<int32_t>();
+        g.vtx = vtx.as<double>();
+        g.nrm = nrm.as<double>();
+        g.area = area.as<double>();
+        g.qp = qp.as<double>();
+        g.ch = ch.as<float>();
+        g.cl = cl.as<float>();
+        g.qo = qo.as<float>();
+        g.nrmf = nrmf.as<float>();
+        g.sc = sc.as<float>();
+    }
+};
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// meshes
+// ---------------------------------------------------------------------------
+struct bem_mesh_s {
+    int device = 0;
+    int64_t nv = 0, nt = 0;
+    std::vector<double> V;
+    std::vector<int32_t> T;
+    DBuf dV, dT;
+    GeomStore geom;
+    // touching triangles (sharing >= 1 vertex, itself included): CSR
+    std::vector<int64_t> adj_ptr;
+    std::vector<int32_t> adj_tri;
+    std::vector<int8_t> adj_case;   // shared vertex count 1..3
+    int64_t max_touch = 0;
+    int hmat_refs = 0;
+};
+
+namespace {
+
+void build_adjacency(bem_mesh_s &M)
+{
+    const int64_t nt = M.nt, nv = M.nv;
+    std::vector<int64_t> vptr(nv + 1, 0);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int a = 0; a < 3; ++a) ++vptr[M.T[3 * t + a] + 1];
+    for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
+    std::vector<int32_t> vtri(vptr[nv]);
+    std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int a = 0; a < 3; ++a) vtri[fill[M.T[3 * t + a]]++] = (int32_t)t;
+    M.adj_ptr.assign(nt + 1, 0);
+    M.adj_tri.clear();
+    M.adj_case.clear();
+    std::vector<std::pair<int32_t, int>> loc;
+    for (int64_t t = 0; t < nt; ++t) {
+        loc.clear();
+        for (int a = 0; a < 3; ++a) {
+            int32_t v = M.T[3 * t + a];
+            for (int64_t q = vptr[v]; q < vptr[v + 1]; ++q) loc.push_back({vtri[q], 1});
+        }
+        std::sort(loc.begin(), loc.end());
+        for (size_t q = 0; q < loc.size();) {
+            size_t e = q;
+            while (e < loc.size() && loc[e].first == loc[q].first) ++e;
+            M.adj_tri.push_back(loc[q].first);
+            M.adj_case.push_back((int8_t)(e - q));
+            q = e;
+        }
+        M.adj_ptr[t + 1] = (int64_t)M.adj_tri.size();
+        M.max_touch = std::max<int64_t>(M.max_touch, M.adj_ptr[t + 1] - M.adj_ptr[t]);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int bem_version(void) { return 100; }
+
+const char *bem_last_error(void) { return g_err.c_str(); }
+
+int bem_mesh_create(const double *vertices, int64_t n_vertices, const int32_t *triangles,
+                    int64_t n_triangles, bem_mesh *out)
+{
+    return guarded([&]() -> int {
+        if (!out) return fail(BEM_E_ARG, "out is null");
+        *out = nullptr;
+        if (!vertices || !triangles) return fail(BEM_E_ARG, "null input array");
+        if (n_vertices < 3 || n_triangles < 1 || n_triangles >= (int64_t(1) << 31) ||
+            n_vertices >= (int64_t(1) << 31))
+            return fail(BEM_E_ARG, "bad mesh sizes");
+        auto M = std::make_unique<bem_mesh_s>();
+        M->nv = n_vertices;
+        M->nt = n_triangles;
+        M->V.assign(vertices, vertices + 3 * n_vertices);
+        M->T.assign(triangles, triangles + 3 * n_triangles);
+        for (int64_t i = 0; i < 3 * n_vertices; ++i)
+            if (!std::isfinite(M->V[i]))
+                return fail(BEM_E_MESH, "non-finite coordinate at vertex " + std::to_string(i / 3));
+        for (int64_t t = 0; t < n_triangles; ++t) {
+            const int32_t *tr = &M->T[3 * t];
+            for (int a = 0; a < 3; ++a)
+                if (tr[a] < 0 || tr[a] >= n_vertices)
+                    return fail(BEM_E_MESH, "vertex index out of range in triangle " + std::to_string(t));
+            if (tr[0] == tr[1] || tr[1] == tr[2] || tr[0] == tr[2])
+                return fail(BEM_E_MESH, "repeated vertex in triangle " + std::to_string(t));
+            const double *a = &M->V[3 * tr[0]], *b = &M->V[3 * tr[1]], *c = &M->V[3 * tr[2]];
+            double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+            double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+            double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                           e1[0] * e2[1] - e1[1] * e2[0]};
+            double n2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+            double s2 = (e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]) *
+                        (e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
+            if (!(n2 > 1e-24 * s2) || n2 == 0.0)
+                return fail(BEM_E_MESH, "zero-area triangle " + std::to_string(t));
+        }
+        CU(cudaGetDevice(&M->device));
+        DeviceConsts &D = device_consts();
+        build_adjacency(*M);
+        M->dV.upload(M->V);
+        M->dT.upload(M->T);
+        M->geom.build(M->dV.as<double>(), M->dT.as<int32_t>(), nullptr, M->nt, D.rule, 0);
+        CU(cudaStreamSynchronize(0));
+        *out = M.release();
+        return BEM_OK;
+    });
+}
+
+int bem_mesh_destroy(bem_mesh mesh)
+{
+    return guarded([&]() -> int {
+        if (!mesh) return fail(BEM_E_ARG, "null mesh");
+        if (mesh->hmat_refs > 0) return fail(BEM_E_STATE, "H-matrices still use this mesh");
+        delete mesh;
+        return BEM_OK;
+    });
+}
+
+int64_t bem_mesh_size(bem_mesh mesh) { return mesh ? mesh->nt : -1; }
+
+int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t *test_ids,
+                int64_t n_test, const int32_t *trial_ids, int64_t n_trial, void *out,
+                void *cuda_stream)
+{
+    return guarded([&]() -> int {
+        if (!mesh) return fail(BEM_E_ARG, "null mesh");
+        if (op < 0 || op > 2) return fail(BEM_E_ARG, "bad op");
+        if (prec != BEM_FP64 && prec != BEM_MIXED) return fail(BEM_E_ARG, "bad prec");
+        if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
+        if (n_test < 0 || n_trial < 0) return fail(BEM_E_ARG, "negative size");
+        if (n_test == 0 || n_trial == 0) return BEM_OK;
+        if (!test_ids || !trial_ids || !out) return fail(BEM_E_ARG, "null array");
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        DeviceConsts &D = device_consts();
+        const bool cplx = k != 0.0;
+        const size_t esz = cplx ? 16 : 8;
+        const int64_t nout = n_test * n_trial;
+        // stage host arrays
+        DBuf sti, stj, sto;
+        const int32_t *dti = test_ids, *dtj = trial_ids;
+        void *dout = out;
+        bool host_out = !is_device_ptr(out);
+        if (!is_device_ptr(test_ids)) {
+            for (int64_t a = 0; a < n_test; ++a)
+                if (test_ids[a] < 0 || test_ids[a] >= mesh->nt)
+                    return fail(BEM_E_ARG, "test id out of range");
+            sti.alloc(n_test * 4);
+            CU(cudaMemcpyAsync(sti.p, test_ids, n_test * 4, cudaMemcpyHostToDevice, st));
+            dti = sti.as<int32_t>();
+        }
+        if (!is_device_ptr(trial_ids)) {
+            for (int64_t b = 0; b < n_trial; ++b)
+                if (trial_ids[b] < 0 || trial_ids[b] >= mesh->nt)
+                    return fail(BEM_E_ARG, "trial id out of range");
+            stj.alloc(n_trial * 4);
+            CU(cudaMemcpyAsync(stj.p, trial_ids, n_trial * 4, cudaMemcpyHostToDevice, st));
+            dtj = stj.as<int32_t>();
+        }
+        if (host_out) {
+            sto.alloc(nout * esz);
+            dout = sto.p;
+        }
+        // scratch: singular pair lists (one per case), counters, error flag
+        unsigned long long cap =
+            (unsigned long long)std::min<int64_t>(nout, n_test * std::max<int64_t>(mesh->max_touch, 1));
+        size_t list_bytes = cap * sizeof(SingPair);
+        size_t scratch = 3 * list_bytes + 64;
+        void *ws = nullptr;
+        CU(cudaMallocAsync(&ws, scratch, st));
+        unsigned char *wb = (unsigned char *)ws;
+        SingPair *lists[3] = {(SingPair *)wb, (SingPair *)(wb + list_bytes),
+                              (SingPair *)(wb + 2 * list_bytes)};
+        unsigned long long *counts = (unsigned long long *)(wb + 3 * list_bytes);
+        int *err = (int *)(counts + 3);
+        cudaError_t e = cudaMemsetAsync(counts, 0, 64, st);
+        if (e == cudaSuccess)
+            e = launch_entries_regular(mesh->geom.g, D.rule, op, k, prec, dti, n_test, dtj,
+                                       n_trial, dout, lists, counts, cap, err, st);
+        const SingPair *cl[3] = {lists[0], lists[1], lists[2]};
+        int64_t hc[3] = {(int64_t)cap, (int64_t)cap, (int64_t)cap};
+        if (e == cudaSuccess) e = launch_singular(mesh->geom.g, D.sing, op, k, cl, counts, hc, dout, st);
+        int herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && host_out)
+            e = cudaMemcpyAsync(out, dout, nout * esz, cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(ws, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            g_err = std::string("bem_entries: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? BEM_E_OOM : BEM_E_CUDA;
+        }
+        if (herr == 1) return fail(BEM_E_ARG, "triangle id out of range");
+        if (herr == 2) return fail(BEM_E_CUDA, "singular pair list overflow");
+        return BEM_OK;
+    });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// H-matrices
+// ---------------------------------------------------------------------------
+struct Cluster {
+    int64_t b, e, left, right;
+    double box[6];
+};
+
+struct BlockH {
+    int64_t tau, sigma;
+    bool adm;
+};
+
+struct bem_hmat_s {
+    bem_mesh mesh = nullptr;
+    int leaf = 0;
+    double eta = 0;
+    std::vector<int32_t> perm, iperm;
+    std::vector<Cluster> cl;
+    std::vector<BlockH> blocks;           // tree order
+    std::vector<NearBlock> near;          // host copies
+    std::vector<int64_t> near_block_id;   // index into blocks
+    std::vector<FarBlock> far;            // LPT order (big first, then small)
+    std::vector<int64_t> far_block_id;
+    int64_t n_big = 0, n_small = 0, max_m_big = 0;
+    int64_t near_total = 0;
+    std::vector<SingPair> sing[3];
+    // leaves (matvec)
+    std::vector<int64_t> leaf_rows, leaf_ptr, leaf_items;
+    // device
+    DBuf d_perm, d_near, d_far, d_sing[3], d_leaf_rows, d_leaf_ptr, d_leaf_items;
+    DBuf d_near_data, d_pool, d_poolhdr, d_queue, d_toff, d_xt, d_yt, d_tbuf, d_x, d_y;
+    GeomStore geom;                       // cluster order
+    // assembled state
+    bool assembled = false;
+    int op = 0, prec = 0;
+    double k = 0.0, eps = 0.0;
+    bool cplx = false;
+    std::vector<int64_t> toff;
+    std::vector<FarBlock> far_result;     // ranks and chunk offsets after assembly
+    int64_t pool_elems = 0;
+    double t_tree = 0, t_near = 0, t_far = 0;
+    int64_t far_entries = 0, rank_sum = 0, capped = 0;
+    int32_t rank_min = 0, rank_max = 0;
+};
+
+namespace {
+
+// Cluster tree (Sec. 2.1): a cluster with more than leaf_size triangles is
+// split along the longest axis of its vertex bounding box at the median of
+// the centroids ((v0 + v1) + v2) / 3, ties by triangle index; leaves list
+// their triangles in increasing index order.  Breadth-first numbering.
+void build_clusters(bem_hmat_s &H)
+{
+    const bem_mesh_s &M = *H.mesh;
+    const int64_t nt = M.nt;
+    std::vector<double> cen(3 * nt);
+    for (int64_t t = 0; t < nt; ++t)
+        for (int c = 0; c < 3; ++c)
+            cen[3 * t + c] = ((M.V[3 * M.T[3 * t] + c] + M.V[3 * M.T[3 * t + 1] + c]) +
+                              M.V[3 * M.T[3 * t + 2] + c]) / 3.0;
+    H.perm.resize(nt);
+    std::iota(H.perm.begin(), H.perm.end(), 0);
+    H.cl.clear();
+    H.cl.push_back({0, nt, -1, -1, {0, 0, 0, 0, 0, 0}});
+    for (size_t head = 0; head < H.cl.size(); ++head) {
+        Cluster C = H.cl[head];
+        double box[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int64_t q = C.b; q < C.e; ++q) {
+            const int32_t *tr = &M.T[3 * (int64_t)H.perm[q]];
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    double x = M.V[3 * (int64_t)tr[a] + c];
+                    box[c] = std::min(box[c], x);
+                    box[3 + c] = std::max(box[3 + c], x);
+                }
+        }
+        std::memcpy(H.cl[head].box, box, sizeof(box));
+        const int64_t n = C.e - C.b;
+        if (n <= H.leaf) {
+            std::sort(H.perm.begin() + C.b, H.perm.begin() + C.e);
+            continue;
+        }
+        int axis = 0;
+        double ext = box[3] - box[0];
+        for (int a = 1; a < 3; ++a)
+            if (box[3 + a] - box[a] > ext) {
+                ext = box[3 + a] - box[a];
+                axis = a;
+            }
+        auto less = [&](int32_t x, int32_t y) {
+            double cx = cen[3 * (int64_t)x + axis], cy = cen[3 * (int64_t)y + axis];
+            return cx < cy || (cx == cy && x < y);
+        };
+        int64_t mid = C.b + n / 2;
+        std::nth_element(H.perm.begin() + C.b, H.perm.begin() + mid, H.perm.begin() + C.e, less);
+        int64_t L = (int64_t)H.cl.size();
+        H.cl[head].left = L;
+        H.cl[head].right = L + 1;
+        H.cl.push_back({C.b, mid, -1, -1, {0, 0, 0, 0, 0, 0}});
+        H.cl.push_back({mid, C.e, -1, -1, {0, 0, 0, 0, 0, 0}});
+    }
+    H.iperm.resize(nt);
+    for (int64_t p = 0; p < nt; ++p) H.iperm[H.perm[p]] = (int32_t)p;
+}
+
+// Admissibility (Sec. 2.1): disjoint boxes and min(diam) <= eta * dist.
+bool admissible(const double *bt, const double *bs, double eta)
+{
+    double dt = std::sqrt((bt[3] - bt[0]) * (bt[3] - bt[0]) + (bt[4] - bt[1]) * (bt[4] - bt[1]) +
+                          (bt[5] - bt[2]) * (bt[5] - bt[2]));
+    double ds = std::sqrt((bs[3] - bs[0]) * (bs[3] - bs[0]) + (bs[4] - bs[1]) * (bs[4] - bs[1]) +
+                          (bs[5] - bs[2]) * (bs[5] - bs[2]));
+    double g[3];
+    for (int c = 0; c < 3; ++c) {
+        double g1 = bs[c] - bt[3 + c], g2 = bt[c] - bs[3 + c];
+        double m = g1 > g2 ? g1 : g2;
+        g[c] = m > 0 ? m : 0;
+    }
+    double dist = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (!(dist > 0)) return false;
+    return (dt < ds ? dt : ds) <= eta * dist;
+}
+
+void build_blocks(bem_hmat_s &H)
+{
+    H.blocks.clear();
+    std::vector<std::pair<int64_t, int64_t>> stack{{0, 0}};
+    while (!stack.empty()) {
+        auto [t, s] = stack.back();
+        stack.pop_back();
+        const Cluster &T = H.cl[t], &S = H.cl[s];
+        bool adm = admissible(T.box, S.box, H.eta);
+        if (adm || T.left < 0 || S.left < 0) {
+            H.blocks.push_back({t, s, adm});
+            continue;
+        }
+        // visit children in the order (l,l), (l,r), (r,l), (r,r)
+        stack.push_back({T.right, S.right});
+        stack.push_back({T.right, S.left});
+        stack.push_back({T.left, S.right});
+        stack.push_back({T.left, S.left});
+    }
+}
+
+void build_lists(bem_hmat_s &H)
+{
+    const bem_mesh_s &M = *H.mesh;
+    H.near.clear();
+    H.near_block_id.clear();
+    std::vector<FarBlock> big, small;
+    std::vector<int64_t> big_id, small_id;
+    int64_t off = 0;
+    const int64_t smax = aca_small_max();
+    for (size_t b = 0; b < H.blocks.size(); ++b) {
+        const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
+        if (!H.blocks[b].adm) {
+            H.near.push_back({T.b, T.e, S.b, S.e, off});
+            H.near_block_id.push_back((int64_t)b);
+            off += (T.e - T.b) * (S.e - S.b);
+        } else {
+            FarBlock F{};
+            F.tb = T.b;
+            F.te = T.e;
+            F.sb = S.b;
+            F.se = S.e;
+            for (int c = 0; c < NCHUNK; ++c) F.chunk[c] = -1;
+            if (std::max(T.e - T.b, S.e - S.b) > smax) {
+                big.push_back(F);
+                big_id.push_back((int64_t)b);
+            } else {
+                small.push_back(F);
+                small_id.push_back((int64_t)b);
+            }
+        }
+    }
+    H.near_total = off;
+    // longest processing time first: by size, then tree order
+    auto order = [](std::vector<FarBlock> &v, std::vector<int64_t> &id) {
+        std::vector<size_t> ix(v.size());
+        std::iota(ix.begin(), ix.end(), 0);
+        std::stable_sort(ix.begin(), ix.end(), [&](size_t a, size_t b) {
+            int64_t sa = (v[a].te - v[a].tb) + (v[a].se - v[a].sb);
+            int64_t sb = (v[b].te - v[b].tb) + (v[b].se - v[b].sb);
+            return sa > sb;
+        });
+        std::vector<FarBlock> v2(v.size());
+        std::vector<int64_t> id2(v.size());
+        for (size_t i = 0; i < ix.size(); ++i) {
+            v2[i] = v[ix[i]];
+            id2[i] = id[ix[i]];
+        }
+        v.swap(v2);
+        id.swap(id2);
+    };
+    order(big, big_id);
+    order(small, small_id);
+    H.n_big = (int64_t)big.size();
+    H.n_small = (int64_t)small.size();
+    H.max_m_big = 0;
+    for (auto &F : big) H.max_m_big = std::max(H.max_m_big, F.te - F.tb);
+    H.far = big;
+    H.far.insert(H.far.end(), small.begin(), small.end());
+    H.far_block_id = big_id;
+    H.far_block_id.insert(H.far_block_id.end(), small_id.begin(), small_id.end());
+
+    // leaves and, per leaf, the blocks whose row range contains it
+    const int64_t nt = M.nt;
+    std::vector<int64_t> leaf_of(nt, -1);
+    H.leaf_rows.clear();
+    int64_t nleaf = 0;
+    for (const Cluster &C : H.cl)
+        if (C.left < 0) {
+            H.leaf_rows.push_back(C.b);
+            H.leaf_rows.push_back(C.e);
+            ++nleaf;
+        }
+    // sort leaves by row start
+    {
+        std::vector<std::pair<int64_t, int64_t>> lr(nleaf);
+        for (int64_t l = 0; l < nleaf; ++l) lr[l] = {H.leaf_rows[2 * l], H.leaf_rows[2 * l + 1]};
+        std::sort(lr.begin(), lr.end());
+        for (int64_t l = 0; l < nleaf; ++l) {
+            H.leaf_rows[2 * l] = lr[l].first;
+            H.leaf_rows[2 * l + 1] = lr[l].second;
+            for (int64_t p = lr[l].first; p < lr[l].second; ++p) leaf_of[p] = l;
+        }
+    }
+    std::vector<std::vector<int64_t>> per_leaf(nleaf);
+    for (size_t f = 0; f < H.far.size(); ++f)
+        for (int64_t l = leaf_of[H.far[f].tb]; l <= leaf_of[H.far[f].te - 1]; ++l)
+            per_leaf[l].push_back((int64_t)f);
+    for (size_t q = 0; q < H.near.size(); ++q)
+        for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l)
+            per_leaf[l].push_back(-1 - (int64_t)q);
+    H.leaf_ptr.assign(nleaf + 1, 0);
+    H.leaf_items.clear();
+    for (int64_t l = 0; l < nleaf; ++l) {
+        H.leaf_items.insert(H.leaf_items.end(), per_leaf[l].begin(), per_leaf[l].end());
+        H.leaf_ptr[l + 1] = (int64_t)H.leaf_items.size();
+    }
+
+    // singular pairs of the near field, with their place in the dense blocks
+    std::vector<std::vector<int64_t>> near_of_leaf(nleaf);  // near blocks by row leaf
+    for (size_t q = 0; q < H.near.size(); ++q)
+        for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l)
+            near_of_leaf[l].push_back((int64_t)q);
+    for (auto &v : near_of_leaf)
+        std::sort(v.begin(), v.end(), [&](int64_t a, int64_t b) { return H.near[a].sb < H.near[b].sb; });
+    for (int c = 0; c < 3; ++c) H.sing[c].clear();
+    for (int64_t p = 0; p < nt; ++p) {
+        const int32_t t = H.perm[p];
+        const auto &lst = near_of_leaf[leaf_of[p]];
+        for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) {
+            const int32_t u = M.adj_tri[a];
+            const int64_t q = H.iperm[u];
+            // near block of this row leaf whose column range holds q
+            auto it = std::upper_bound(lst.begin(), lst.end(), q,
+                                       [&](int64_t val, int64_t nb) { return val < H.near[nb].sb; });
+            if (it == lst.begin()) throw std::runtime_error("touching pair outside the near field");
+            const NearBlock &N = H.near[*(it - 1)];
+            if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
+            int64_t dest = N.off + (p - N.tb) * (N.se - N.sb) + (q - N.sb);
+            H.sing[M.adj_case[a] - 1].push_back({t, u, dest});
+        }
+    }
+}
+
+void upload_tree(bem_hmat_s &H)
+{
+    H.d_perm.upload(H.perm);
+    H.d_near.upload(H.near);
+    H.d_far.upload(H.far);
+    for (int c = 0; c < 3; ++c) H.d_sing[c].upload(H.sing[c]);
+    H.d_leaf_rows.upload(H.leaf_rows);
+    H.d_leaf_ptr.upload(H.leaf_ptr);
+    H.d_leaf_items.upload(H.leaf_items);
+    DeviceConsts &D = device_consts();
+    H.geom.build(H.mesh->dV.as<double>(), H.mesh->dT.as<int32_t>(), H.d_perm.as<int32_t>(),
+                 H.mesh->nt, D.rule, 0);
+    H.d_poolhdr.alloc(sizeof(Pool));
+    H.d_queue.alloc(sizeof(AcaQueue));
+    CU(cudaStreamSynchronize(0));
+}
+
+}  // namespace
+
+extern "C" {
+
+int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
+{
+    return guarded([&]() -> int {
+        if (!out) return fail(BEM_E_ARG, "out is null");
+        *out = nullptr;
+        if (!mesh) return fail(BEM_E_ARG, "null mesh");
+        if (leaf_size < 1) return fail(BEM_E_ARG, "leaf_size must be >= 1");
+        if (!(eta > 0) || !std::isfinite(eta)) return fail(BEM_E_ARG, "eta must be > 0");
+        double t0 = now_ms();
+        auto H = std::make_unique<bem_hmat_s>();
+        H->mesh = mesh;
+        H->leaf = leaf_size;
+        H->eta = eta;
+        build_clusters(*H);
+        build_blocks(*H);
+        build_lists(*H);
+        upload_tree(*H);
+        H->t_tree = now_ms() - t0;
+        ++mesh->hmat_refs;
+        *out = H.release();
+        return BEM_OK;
+    });
+}
+
+int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec, void *cuda_stream)
+{
+    return guarded([&]() -> int {
+        if (!H) return fail(BEM_E_ARG, "null hmat");
+        if (op < 0 || op > 2) return fail(BEM_E_ARG, "bad op");
+        if (prec != BEM_FP64 && prec != BEM_MIXED) return fail(BEM_E_ARG, "bad prec");
+        if (!(aca_eps > 0) || !std::isfinite(aca_eps)) return fail(BEM_E_ARG, "aca_eps must be > 0");
+        if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        DeviceConsts &D = device_consts();
+        const bool cplx = k != 0.0;
+        const size_t esz = cplx ? 16 : 8;
+        H->assembled = false;
+        H->op = op;
+        H->k = k;
+        H->eps = aca_eps;
+        H->prec = prec;
+        H->cplx = cplx;
+        cudaEvent_t ev[3];
+        for (auto &e : ev) CU(cudaEventCreate(&e));
+        struct EvGuard {
+            cudaEvent_t *e;
+            ~EvGuard()
+            {
+                for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+            }
+        } eg{ev};
+        // near field: regular pairs, then singular pairs (FP64)
+        if (H->d_near_data.bytes < (size_t)H->near_total * esz) H->d_near_data.alloc(H->near_total * esz);
+        CU(cudaEventRecord(ev[0], st));
+        CU(launch_near_regular(H->geom.g, D.rule, op, k, prec, H->d_near.as<NearBlock>(),
+                               (int64_t)H->near.size(), H->d_near_data.p, st));
+        const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
+                                 H->d_sing[2].as<SingPair>()};
+        int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
+                         (int64_t)H->sing[2].size()};
+        CU(launch_singular(H->mesh->geom.g, D.sing, op, k, sp, nullptr, hc, H->d_near_data.p, st));
+        CU(cudaEventRecord(ev[1], st));
+        // far field: persistent ACA over all admissible blocks; the factor
+        // pool grows and the launch repeats if it overflows
+        int64_t sum_mn = 0;
+        for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
+        int64_t want = std::max<int64_t>(H->pool_elems, sum_mn * KCHUNK * 2 + 1024);
+        for (int attempt = 0;; ++attempt) {
+            if (H->d_pool.bytes < (size_t)want * esz) H->d_pool.alloc((size_t)want * esz);
+            H->pool_elems = want;
+            Pool ph{0ull, (unsigned long long)want, 0, 0};
+            AcaQueue q{0u, 0u};
+            CU(cudaMemcpyAsync(H->d_poolhdr.p, &ph, sizeof(ph), cudaMemcpyHostToDevice, st));
+            CU(cudaMemcpyAsync(H->d_queue.p, &q, sizeof(q), cudaMemcpyHostToDevice, st));
+            CU(cudaMemcpyAsync(H->d_far.p, H->far.data(), H->far.size() * sizeof(FarBlock),
+                               cudaMemcpyHostToDevice, st));
+            if (!H->far.empty())
+                CU(launch_aca(H->geom.g, D.rule, op, k, prec, aca_eps, H->d_far.as<FarBlock>(),
+                              H->n_big, H->n_small, H->max_m_big, H->d_pool.p,
+                              H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(), D.num_sms, st));
+            CU(cudaEventRecord(ev[2], st));
+            CU(cudaMemcpyAsync(&ph, H->d_poolhdr.p, sizeof(ph), cudaMemcpyDeviceToHost, st));
+            CU(cudaStreamSynchronize(st));
+            if (!ph.overflow) break;
+            if (attempt >= 6) return fail(BEM_E_OOM, "ACA factor pool keeps overflowing");
+            want *= 2;
+        }
+        float tn = 0, tf = 0;
+        CU(cudaEventElapsedTime(&tn, ev[0], ev[1]));
+        CU(cudaEventElapsedTime(&tf, ev[1], ev[2]));
+        H->t_near = tn;
+        H->t_far = tf;
+        // ranks -> offsets of the V^T x buffer
+        std::vector<FarBlock> res(H->far.size());
+        if (!res.empty())
+            CU(cudaMemcpy(res.data(), H->d_far.p, res.size() * sizeof(FarBlock), cudaMemcpyDeviceToHost));
+        H->toff.assign(res.size() + 1, 0);
+        H->far_entries = 0;
+        H->rank_sum = 0;
+        H->capped = 0;
+        H->rank_min = res.empty() ? 0 : INT32_MAX;
+        H->rank_max = 0;
+        for (size_t b = 0; b < res.size(); ++b) {
+            H->toff[b + 1] = H->toff[b] + res[b].rank;
+            H->far_entries += res[b].entries;
+            H->rank_sum += res[b].rank;
+            H->capped += res[b].status == 1;
+            H->rank_min = std::min(H->rank_min, res[b].rank);
+            H->rank_max = std::max(H->rank_max, res[b].rank);
+        }
+        H->far_result = res;
+        H->d_toff.upload(H->toff);
+        const int64_t nt = H->mesh->nt;
+        H->d_xt.alloc(nt * esz);
+        H->d_yt.alloc(nt * esz);
+        H->d_tbuf.alloc((H->toff.back() + 1) * esz);
+        H->assembled = true;
+        return BEM_OK;
+    });
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int hmat_matvec(bem_hmat H, const void *x, void *y, int32_t batch, void *cuda_stream)
+{
+    return guarded([&]() -> int {
+        if (!H) return fail(BEM_E_ARG, "null hmat");
+        if (!H->assembled) return fail(BEM_E_STATE, "hmat_matvec before hmat_assemble");
+        if (batch < 0) return fail(BEM_E_ARG, "negative batch");
+        if (batch == 0) return BEM_OK;
+        if (!x || !y) return fail(BEM_E_ARG, "null vector");
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        const int64_t nt = H->mesh->nt;
+        const size_t esz = H->cplx ? 16 : 8;
+        const size_t vb = nt * esz;
+        const bool hx = !is_device_ptr(x), hy = !is_device_ptr(y);
+        if ((hx || hy) && H->d_x.bytes < vb) {
+            H->d_x.alloc(vb);
+            H->d_y.alloc(vb);
+        }
+        for (int32_t b = 0; b < batch; ++b) {
+            const void *xb = (const char *)x + b * vb;
+            void *yb = (char *)y + b * vb;
+            const void *dx = xb;
+            void *dy = yb;
+            if (hx) {
+                CU(cudaMemcpyAsync(H->d_x.p, xb, vb, cudaMemcpyHostToDevice, st));
+                dx = H->d_x.p;
+            }
+            if (hy) dy = H->d_y.p;
+            CU(launch_matvec(H->cplx, nt, H->d_perm.as<int32_t>(), dx, dy, H->d_xt.p, H->d_yt.p,
+                             H->d_tbuf.p, H->d_far.as<FarBlock>(), (int64_t)H->far.size(),
+                             H->d_toff.as<int64_t>(), H->d_pool.p, H->d_near.as<NearBlock>(),
+                             H->d_near_data.p, H->d_leaf_rows.as<int64_t>(),
+                             H->d_leaf_ptr.as<int64_t>(), H->d_leaf_items.as<int64_t>(),
+                             (int64_t)(H->leaf_ptr.size() - 1), st));
+            if (hy) CU(cudaMemcpyAsync(yb, dy, vb, cudaMemcpyDeviceToHost, st));
+        }
+        if (hx || hy) CU(cudaStreamSynchronize(st));
+        return BEM_OK;
+    });
+}
+
+int hmat_stats(bem_hmat H, bem_hmat_stats *out)
+{
+    return guarded([&]() -> int {
+        if (!H || !out) return fail(BEM_E_ARG, "null argument");
+        bem_hmat_stats s{};
+        s.n_triangles = H->mesh->nt;
+        s.n_clusters = (int64_t)H->cl.size();
+        s.n_blocks_near = (int64_t)H->near.size();
+        s.n_blocks_far = (int64_t)H->far.size();
+        s.near_entries = H->near_total;
+        for (int c = 0; c < 3; ++c) s.singular_pairs[c] = (int64_t)H->sing[c].size();
+        s.far_entries = H->far_entries;
+        const size_t esz = H->cplx ? 16 : 8;
+        int64_t fb = 0;
+        for (const FarBlock &F : H->far_result)
+            for (int c = 0; c < NCHUNK; ++c)
+                if (F.chunk[c] >= 0) fb += ((F.te - F.tb) + (F.se - F.sb)) * KCHUNK * (int64_t)esz;
+        s.factor_bytes = fb;
+        s.near_bytes = H->near_total * (int64_t)esz;
+        s.rank_min = H->rank_min;
+        s.rank_max = H->rank_max;
+        s.rank_mean = H->far_result.empty() ? 0.0 : (double)H->rank_sum / H->far_result.size();
+        s.rank_capped_blocks = H->capped;
+        s.time_tree_ms = H->t_tree;
+        s.time_near_ms = H->t_near;
+        s.time_far_ms = H->t_far;
+        s.assembled = H->assembled;
+        s.op = H->op;
+        s.k = H->k;
+        s.aca_eps = H->eps;
+        s.prec = H->prec;
+        *out = s;
+        return BEM_OK;
+    });
+}
+
+int hmat_blocks(bem_hmat H, int64_t *blocks, int64_t cap, int64_t *n_blocks, int32_t *perm)
+{
+    return guarded([&]() -> int {
+        if (!H || !n_blocks) return fail(BEM_E_ARG, "null argument");
+        *n_blocks = (int64_t)H->blocks.size();
+        if (perm) std::memcpy(perm, H->perm.data(), H->perm.size() * sizeof(int32_t));
+        if (!blocks) return BEM_OK;
+        if (cap < (int64_t)H->blocks.size()) return fail(BEM_E_ARG, "block capacity too small");
+        for (size_t b = 0; b < H->blocks.size(); ++b) {
+            const Cluster &T = H->cl[H->blocks[b].tau], &S = H->cl[H->blocks[b].sigma];
+            int64_t *r = blocks + 5 * b;
+            r[0] = T.b;
+            r[1] = T.e;
+            r[2] = S.b;
+            r[3] = S.e;
+            r[4] = H->blocks[b].adm ? 1 : 0;
+        }
+        return BEM_OK;
+    });
+}
+
+int hmat_block_dense(bem_hmat H, int64_t block, void *out, int32_t *rank)
+{
+    return guarded([&]() -> int {
+        if (!H || !out) return fail(BEM_E_ARG, "null argument");
+        if (!H->assembled) return fail(BEM_E_STATE, "not assembled");
+        if (block < 0 || block >= (int64_t)H->blocks.size()) return fail(BEM_E_ARG, "bad block");
+        const size_t esz = H->cplx ? 16 : 8;
+        if (!H->blocks[block].adm) {
+            auto it = std::find(H->near_block_id.begin(), H->near_block_id.end(), block);
+            const NearBlock &N = H->near[it - H->near_block_id.begin()];
+            size_t bytes = (N.te - N.tb) * (N.se - N.sb) * esz;
+            CU(cudaMemcpy(out, H->d_near_data.as<char>() + N.off * esz, bytes, cudaMemcpyDeviceToHost));
+            if (rank) *rank = -1;
+            return BEM_OK;
+        }
+        auto it = std::find(H->far_block_id.begin(), H->far_block_id.end(), block);
+        const FarBlock &F = H->far_result[it - H->far_block_id.begin()];
+        const int64_t m = F.te - F.tb, n = F.se - F.sb;
+        const int r = F.rank;
+        if (rank) *rank = r;
+        const int cpl = H->cplx ? 2 : 1;
+        std::vector<double> U((size_t)m * r * cpl), V((size_t)n * r * cpl);
+        for (int l = 0; l < r; ++l) {
+            const int64_t base = F.chunk[l / KCHUNK];
+            CU(cudaMemcpy(&U[(size_t)l * m * cpl], H->d_pool.as<char>() + (base + (l % KCHUNK) * m) * esz,
+                          m * esz, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(&V[(size_t)l * n * cpl],
+                          H->d_pool.as<char>() + (base + KCHUNK * m + (l % KCHUNK) * n) * esz, n * esz,
+                          cudaMemcpyDeviceToHost));
+        }
+        double *o = (double *)out;
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t j = 0; j < n; ++j) {
+                double re = 0, im = 0;
+                for (int l = 0; l < r; ++l) {
+                    if (cpl == 1) {
+                        re += U[(size_t)l * m + i] * V[(size_t)l * n + j];
+                    } else {
+                        double ur = U[2 * ((size_t)l * m + i)], ui = U[2 * ((size_t)l * m + i) + 1];
+                        double vr = V[2 * ((size_t)l * n + j)], vi = V[2 * ((size_t)l * n + j) + 1];
+                        re += ur * vr - ui * vi;
+                        im += ur * vi + ui * vr;
+                    }
+                }
+                if (cpl == 1) o[i * n + j] = re;
+                else {
+                    o[2 * (i * n + j)] = re;
+                    o[2 * (i * n + j) + 1] = im;
+                }
+            }
+        return BEM_OK;
+    });
+}
+
+int hmat_destroy(bem_hmat H)
+{
+    return guarded([&]() -> int {
+        if (!H) return fail(BEM_E_ARG, "null hmat");
+        --H->mesh->hmat_refs;
+        delete H;
+        return BEM_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,426 @@
+// Persistent ACA driver: every admissible block of the H-matrix is
+// compressed by partially pivoted ACA (Sec. 2.1, Eq. (6)-(7), Algorithm ACA)
+// inside one kernel launch.  Blocks come from two device work queues in
+// descending size: a CTA works on one large block at a time; once those are
+// gone, every warp takes small blocks on its own.  Entries of the requested
+// rows and columns are evaluated in place by the regular quadrature
+// (admissible blocks contain no pair that shares a vertex); pivot search,
+// residual updates and the norm of S_k are FP64.
+//
+// Readings where the paper is silent (same as the oracle): i_1 = 0;
+// i_{k+1} = argmax over unused rows of |(u_k)_i| (lowest index on ties); a row
+// vanishes if its maximum is 0 or <= 1e-14 * the largest pivot so far, and
+// then the smallest unused row is next; stop once ||u_k|| ||v_k|| <= eps
+// ||S_k||_F, or k = min(m, n), or all rows used, or k = KMAX (rank cap).
+#include "bem_device.cuh"
+
+namespace bem {
+
+namespace {
+
+constexpr int kAcaThreads = 256;
+constexpr int kWarps = kAcaThreads / 32;
+constexpr int kSmallMax = 256;  // blocks with max(m, n) <= this go to single warps
+
+template <bool CPLX>
+struct VT;
+
+template <>
+struct VT<false> {
+    using T = double;
+    static __device__ __forceinline__ T from(C2 v) { return v.re; }
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ double mag(T a) { return fabs(a); }
+    static __device__ __forceinline__ double abs2(T a) { return a * a; }
+    static __device__ __forceinline__ T fnma(T a, T b, T c) { return fma(-a, b, c); }  // c - a b
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T inv(T a) { return 1.0 / a; }
+    static __device__ __forceinline__ T dotc(T a, T b, T acc) { return fma(a, b, acc); }  // conj(a) b
+    static __device__ __forceinline__ double re_mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T shfl_down(T a, int o)
+    {
+        return __shfl_down_sync(0xffffffffu, a, o);
+    }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+};
+
+template <>
+struct VT<true> {
+    using T = double2;
+    static __device__ __forceinline__ T from(C2 v) { return make_double2(v.re, v.im); }
+    static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ double mag(T a) { return hypot(a.x, a.y); }
+    static __device__ __forceinline__ double abs2(T a) { return fma(a.x, a.x, a.y * a.y); }
+    static __device__ __forceinline__ T fnma(T a, T b, T c)
+    {
+        return make_double2(c.x - fma(a.x, b.x, -a.y * b.y), c.y - fma(a.x, b.y, a.y * b.x));
+    }
+    static __device__ __forceinline__ T mul(T a, T b)
+    {
+        return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+    }
+    static __device__ __forceinline__ T inv(T a)
+    {
+        double d = 1.0 / fma(a.x, a.x, a.y * a.y);
+        return make_double2(a.x * d, -a.y * d);
+    }
+    static __device__ __forceinline__ T dotc(T a, T b, T acc)
+    {
+        return make_double2(acc.x + fma(a.x, b.x, a.y * b.y), acc.y + fma(a.x, b.y, -a.y * b.x));
+    }
+    static __device__ __forceinline__ double re_mul(T a, T b) { return fma(a.x, b.x, -a.y * b.y); }
+    static __device__ __forceinline__ T shfl_down(T a, int o)
+    {
+        return make_double2(__shfl_down_sync(0xffffffffu, a.x, o),
+                            __shfl_down_sync(0xffffffffu, a.y, o));
+    }
+    static __device__ __forceinline__ T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
+};
+
+// ---- groups: a whole CTA or a single warp ---------------------------------
+struct RedScratch {
+    double v[kWarps];
+    int64_t i[kWarps];
+    double s0[kWarps], s1[kWarps];
+};
+
+__device__ __forceinline__ void warp_argmax(double &v, int64_t &idx)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, v, o);
+        int64_t oi = __shfl_down_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    v = __shfl_sync(0xffffffffu, v, 0);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+struct WarpGroup {
+    int lane;
+    __device__ int rank() const { return lane; }
+    __device__ int size() const { return 32; }
+    __device__ int warp() const { return 0; }
+    __device__ int nwarps() const { return 1; }
+    __device__ void sync() const { __syncwarp(); }
+    __device__ void argmax(double &v, int64_t &idx) const { warp_argmax(v, idx); }
+    __device__ void sum2(double &a, double &b) const
+    {
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
+    __device__ double sum(double a) const { return warp_sum(a); }
+};
+
+struct CtaGroup {
+    RedScratch *red;
+    __device__ int rank() const { return threadIdx.x; }
+    __device__ int size() const { return blockDim.x; }
+    __device__ int warp() const { return threadIdx.x >> 5; }
+    __device__ int nwarps() const { return blockDim.x >> 5; }
+    __device__ void sync() const { __syncthreads(); }
+    __device__ void argmax(double &v, int64_t &idx) const
+    {
+        warp_argmax(v, idx);
+        int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0) {
+            red->v[w] = v;
+            red->i[w] = idx;
+        }
+        __syncthreads();
+        v = red->v[0];
+        idx = red->i[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            double ov = red->v[q];
+            int64_t oi = red->i[q];
+            if (ov > v || (ov == v && oi < idx)) {
+                v = ov;
+                idx = oi;
+            }
+        }
+        __syncthreads();
+    }
+    __device__ void sum2(double &a, double &b) const
+    {
+        a = warp_sum(a);
+        b = warp_sum(b);
+        int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0) {
+            red->s0[w] = a;
+            red->s1[w] = b;
+        }
+        __syncthreads();
+        a = 0.0;
+        b = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            a += red->s0[q];
+            b += red->s1[q];
+        }
+        __syncthreads();
+    }
+    __device__ double sum(double a) const
+    {
+        double b = 0.0;
+        sum2(a, b);
+        return a;
+    }
+};
+
+// Per-group shared state.
+template <bool CPLX>
+struct GroupSmem {
+    typename VT<CPLX>::T cu[KMAX];   // (u_l)_i of the current row / (v_l)_j of the column
+    int64_t chunk[NCHUNK];
+    int64_t scal;                   // broadcast slot
+    int fail;
+};
+
+template <class Grp, int OP, bool CPLX, int PREC>
+__device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, double k, double eps,
+                          FarBlock *blk, typename VT<CPLX>::T *pool, Pool *P,
+                          GroupSmem<CPLX> &S, unsigned *Z)
+{
+    using V = VT<CPLX>;
+    using T = typename V::T;
+    using E = RegularEntry<OP, CPLX, PREC>;
+    const int64_t tb = blk->tb, sb = blk->sb;
+    const int64_t m = blk->te - tb, n = blk->se - sb;
+    const int t = G.rank(), GS = G.size();
+    const int64_t kmin = m < n ? m : n;
+    const int kcap = (int)(kmin < KMAX ? kmin : KMAX);
+    const int64_t zwords = (m + 31) >> 5;
+    for (int64_t w = t; w < zwords; w += GS) Z[w] = 0u;
+    if (t < NCHUNK) S.chunk[t] = -1;
+    if (t == 0) S.fail = 0;
+    G.sync();
+
+    int kk = 0, status = 0;
+    int64_t nZ = 0, i = 0, entries = 0;
+    double normS2 = 0.0, maxpiv = 0.0;
+    auto Uat = [&](int l, int64_t r) -> T * {
+        return pool + S.chunk[l / KCHUNK] + (int64_t)(l % KCHUNK) * m + r;
+    };
+    auto Vat = [&](int l, int64_t j) -> T * {
+        return pool + S.chunk[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n + j;
+    };
+
+    for (;;) {
+        // factor storage for column kk
+        if (kk < kcap && (kk % KCHUNK) == 0 && S.chunk[kk / KCHUNK] < 0) {
+            if (t == 0) {
+                unsigned long long need = (unsigned long long)(m + n) * KCHUNK;
+                unsigned long long off = atomicAdd(&P->top, need);
+                if (off + need > P->cap) {
+                    P->overflow = 1;
+                    S.fail = 1;
+                } else {
+                    S.chunk[kk / KCHUNK] = (int64_t)off;
+                }
+            }
+            G.sync();
+            if (S.fail) {
+                status = 2;
+                break;
+            }
+        }
+        // selected row of R_{k-1}: a_{i,:} - sum_l (u_l)_i v_l
+        for (int l = t; l < kk; l += GS) S.cu[l] = *Uat(l, i);
+        G.sync();
+        typename E::Tri ti;
+        E::load(g, tb + i, ti);
+        double best = -1.0;
+        int64_t bj = 0;
+        for (int64_t j = t; j < n; j += GS) {
+            typename E::Tri tj;
+            E::load(g, sb + j, tj);
+            T a = V::from(E::eval(ti, tj, R, k));
+            for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Vat(l, j), a);
+            if (kk < kcap) *Vat(kk, j) = a;
+            double mg = V::mag(a);
+            if (mg > best) {  // j increases, so ties keep the lowest index
+                best = mg;
+                bj = j;
+            }
+        }
+        entries += n;
+        G.argmax(best, bj);
+        if (t == 0) Z[i >> 5] |= 1u << (i & 31);
+        ++nZ;
+        const double vmax = best;
+        if (vmax == 0.0 || vmax <= 1e-14 * maxpiv) {
+            if (nZ == m) break;
+            G.sync();
+            if (t == 0) {
+                int64_t r = 0;
+                while (r < m && (Z[r >> 5] >> (r & 31)) & 1u) ++r;
+                S.scal = r;
+            }
+            G.sync();
+            i = S.scal;
+            continue;
+        }
+        if (kk == kcap) {
+            status = 1;
+            break;
+        }
+        if (vmax > maxpiv) maxpiv = vmax;
+        G.sync();
+        const T piv = *Vat(kk, bj);
+        const T pinv = V::inv(piv);
+        G.sync();
+        double nv2 = 0.0;
+        for (int64_t j = t; j < n; j += GS) {
+            T v = V::mul(*Vat(kk, j), pinv);
+            if (j == bj) v = V::mul(piv, pinv);
+            *Vat(kk, j) = v;
+            nv2 += V::abs2(v);
+        }
+        // selected column of R_{k-1}: a_{:,j} - sum_l (v_l)_j u_l
+        for (int l = t; l < kk; l += GS) S.cu[l] = *Vat(l, bj);
+        G.sync();
+        typename E::Tri tj;
+        E::load(g, sb + bj, tj);
+        double nu2 = 0.0, bu = -1.0;
+        int64_t br = m;
+        for (int64_t r = t; r < m; r += GS) {
+            typename E::Tri tr;
+            E::load(g, tb + r, tr);
+            T a = V::from(E::eval(tr, tj, R, k));
+            for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Uat(l, r), a);
+            *Uat(kk, r) = a;
+            nu2 += V::abs2(a);
+            if (!((Z[r >> 5] >> (r & 31)) & 1u)) {
+                double mg = V::mag(a);
+                if (mg > bu) {
+                    bu = mg;
+                    br = r;
+                }
+            }
+        }
+        entries += m;
+        G.sum2(nu2, nv2);
+        G.argmax(bu, br);
+        G.sync();
+        // cross terms 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> of ||S_k||_F^2
+        double cross = 0.0;
+        {
+            const int lane = t & 31;
+            for (int l = G.warp(); l < kk; l += G.nwarps()) {
+                T iu = V::zero(), iv = V::zero();
+                for (int64_t r = lane; r < m; r += 32) iu = V::dotc(*Uat(l, r), *Uat(kk, r), iu);
+                for (int64_t j = lane; j < n; j += 32) iv = V::dotc(*Vat(l, j), *Vat(kk, j), iv);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    iu = V::add(iu, V::shfl_down(iu, o));
+                    iv = V::add(iv, V::shfl_down(iv, o));
+                }
+                if (lane == 0) cross += V::re_mul(iu, iv);
+            }
+            if ((t & 31) != 0) cross = 0.0;
+            cross = G.sum(cross);
+        }
+        normS2 += 2.0 * cross + nu2 * nv2;
+        ++kk;
+        if (sqrt(nu2) * sqrt(nv2) <= eps * sqrt(normS2)) break;
+        if (kk == kmin || nZ == m) break;
+        i = br;
+    }
+    G.sync();
+    if (t == 0) {
+        blk->rank = kk;
+        blk->status = status;
+        blk->entries = entries;
+        for (int c = 0; c < NCHUNK; ++c) blk->chunk[c] = S.chunk[c];
+    }
+    G.sync();
+}
+
+template <int OP, bool CPLX, int PREC>
+__global__ void __launch_bounds__(kAcaThreads, 1)
+k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_big,
+      int64_t n_small, int64_t zwords_big, typename VT<CPLX>::T *pool, Pool *P, AcaQueue *Q)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ RedScratch red;
+    __shared__ GroupSmem<CPLX> gs[kWarps];
+    __shared__ unsigned zsmall[kWarps][(kSmallMax + 31) / 32];
+    __shared__ int64_t s_b;
+    unsigned *zbig = reinterpret_cast<unsigned *>(smem_raw);
+    // phase 1: large blocks, one CTA each
+    CtaGroup cg{&red};
+    for (;;) {
+        if (threadIdx.x == 0) s_b = (int64_t)atomicAdd(&Q->next_big, 1u);
+        __syncthreads();
+        int64_t b = s_b;
+        __syncthreads();
+        if (b >= n_big) break;
+        aca_block<CtaGroup, OP, CPLX, PREC>(cg, g, R, k, eps, blocks + b, pool, P, gs[0], zbig);
+    }
+    (void)zwords_big;
+    // phase 2: small blocks, one warp each
+    const int w = threadIdx.x >> 5;
+    WarpGroup wg{(int)(threadIdx.x & 31)};
+    for (;;) {
+        int64_t b = 0;
+        if (wg.lane == 0) b = (int64_t)atomicAdd(&Q->next_small, 1u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= n_small) break;
+        aca_block<WarpGroup, OP, CPLX, PREC>(wg, g, R, k, eps, blocks + n_big + b, pool, P, gs[w],
+                                             zsmall[w]);
+    }
+}
+
+template <int OP, bool CPLX, int PREC>
+cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps,
+                       FarBlock *blocks, int64_t n_big, int64_t n_small, int64_t max_m_big,
+                       void *pool, Pool *P, AcaQueue *Q, int num_sms, cudaStream_t st)
+{
+    int64_t zwords = (max_m_big + 31) / 32;
+    size_t dyn = (size_t)(zwords > 0 ? zwords : 1) * sizeof(unsigned);
+    auto kern = k_aca<OP, CPLX, PREC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAcaThreads, dyn);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    kern<<<(unsigned)grid, kAcaThreads, dyn, st>>>(
+        g, R, k, eps, blocks, n_big, n_small, zwords,
+        reinterpret_cast<typename VT<CPLX>::T *>(pool), P, Q);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int aca_small_max() { return kSmallMax; }
+
+cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
+                       double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,
+                       int64_t max_m_big, void *pool_data, Pool *pool, AcaQueue *queue,
+                       int num_sms, cudaStream_t st)
+{
+    const bool cplx = k != 0.0;
+#define BEM_ACA(O, C, Pp)                                                                     \
+    if (op == O && cplx == C && prec == Pp)                                                   \
+        return aca_launch<O, C, Pp>(g, rule, k, eps, blocks, n_big, n_small, max_m_big,       \
+                                    pool_data, pool, queue, num_sms, st);
+    BEM_ACA(0, false, 0) BEM_ACA(0, false, 1) BEM_ACA(0, true, 0) BEM_ACA(0, true, 1)
+    BEM_ACA(1, false, 0) BEM_ACA(1, false, 1) BEM_ACA(1, true, 0) BEM_ACA(1, true, 1)
+    BEM_ACA(2, false, 0) BEM_ACA(2, false, 1) BEM_ACA(2, true, 0) BEM_ACA(2, true, 1)
+#undef BEM_ACA
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace bem

@@ -1,0 +1,426 @@
+// Geometry precompute, dense sub-blocks (bem_entries), the Sauter-Schwab
+// singular kernel and the near-field regular kernel.
+#include "bem_device.cuh"
+
+namespace bem {
+
+namespace {
+
+constexpr int kGeomThreads = 256;
+
+// Per triangle: vertices, unit normal and area (right-hand rule on the
+// stored order), the 6 global quadrature points of the degree-4 rule, and the
+// mixed-precision view (centroid as float-float, points relative to it).
+// Sec. 3.2.1: geometry computed on the device in 1D coalesced arrays.
+__global__ void __launch_bounds__(kGeomThreads)
+k_geometry(const double *__restrict__ V, const int32_t *__restrict__ T,
+           const int32_t *__restrict__ perm, int64_t nt, QuadRule R, int32_t *tri, double *vtx,
+           double *nrm, double *area, double *qp, float *ch, float *cl, float *qo, float *nrmf,
+           float *sc)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nt) return;
+    int64_t t = perm ? (int64_t)perm[p] : p;
+    double v[3][3];
+    for (int a = 0; a < 3; ++a) {
+        int32_t id = T[3 * t + a];
+        tri[a * nt + p] = id;
+        for (int c = 0; c < 3; ++c) {
+            v[a][c] = V[3 * (int64_t)id + c];
+            vtx[(3 * a + c) * nt + p] = v[a][c];
+        }
+    }
+    double e1[3], e2[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = v[1][c] - v[0][c];
+        e2[c] = v[2][c] - v[0][c];
+    }
+    double nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                    e1[0] * e2[1] - e1[1] * e2[0]};
+    double len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+    double A = 0.5 * len;
+    area[p] = A;
+    double cen[3];
+    for (int c = 0; c < 3; ++c) {
+        double nc = nn[c] / len;
+        nrm[c * nt + p] = nc;
+        nrmf[c * nt + p] = (float)nc;
+        cen[c] = ((v[0][c] + v[1][c]) + v[2][c]) / 3.0;
+        float h = (float)cen[c];
+        ch[c * nt + p] = h;
+        cl[c * nt + p] = (float)(cen[c] - (double)h);
+    }
+    for (int q = 0; q < NQ; ++q)
+        for (int c = 0; c < 3; ++c) {
+            double x = v[0][c] + R.s[q] * e1[c] + R.t[q] * e2[c];
+            qp[(q * 3 + c) * nt + p] = x;
+            qo[(q * 3 + c) * nt + p] = (float)(x - cen[c]);
+        }
+    double s = A * rsqrt(4.0 * CUDART_PI);
+    float sh = (float)s;
+    sc[p] = sh;
+    sc[nt + p] = (float)(s - (double)sh);
+}
+
+template <bool CPLX>
+__device__ __forceinline__ void store_val(void *out, int64_t idx, C2 v)
+{
+    if (CPLX) reinterpret_cast<double2 *>(out)[idx] = make_double2(v.re, v.im);
+    else reinterpret_cast<double *>(out)[idx] = v.re;
+}
+
+// Dense sub-block: thread (a, b) evaluates A(test[a], trial[b]) by the
+// regular rule (Algorithm "Integral Evaluation", Sec. 3.3: one thread per
+// element pair) or queues the pair for the singular kernel.
+constexpr int kEntBx = 32, kEntBy = 4;
+
+template <int OP, bool CPLX, int PREC>
+__global__ void __launch_bounds__(kEntBx *kEntBy)
+k_entries(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int64_t n_test,
+          const int32_t *__restrict__ trial, int64_t n_trial, void *out, SingPair *l1,
+          SingPair *l2, SingPair *l3, unsigned long long *counts, unsigned long long cap, int *err)
+{
+    using E = RegularEntry<OP, CPLX, PREC>;
+    int64_t b = (int64_t)blockIdx.x * kEntBx + threadIdx.x;
+    if (b >= n_trial) return;
+    int32_t j = trial[b];
+    for (int64_t a = (int64_t)blockIdx.y * kEntBy + threadIdx.y; a < n_test;
+         a += (int64_t)gridDim.y * kEntBy) {
+        int32_t i = test[a];
+        if (i < 0 || i >= g.nt || j < 0 || j >= g.nt) {
+            atomicExch(err, 1);
+            continue;
+        }
+        int64_t dst = a * n_trial + b;
+        int s = shared_count(g, i, j);
+        if (s > 0) {
+            unsigned long long slot = atomicAdd(&counts[s - 1], 1ull);
+            if (slot < cap) {
+                SingPair *L = s == 1 ? l1 : (s == 2 ? l2 : l3);
+                L[slot] = {i, j, dst};
+            } else {
+                atomicExch(err, 2);
+            }
+            continue;
+        }
+        typename E::Tri ta, tb;
+        E::load(g, i, ta);
+        E::load(g, j, tb);
+        store_val<CPLX>(out, dst, E::eval(ta, tb, R, k));
+    }
+}
+
+// ---- Sauter-Schwab singular pairs (FP64) -----------------------------------
+// Vertex orders of the panel parametrisations chi(x^) = P0 + x1 (P1 - P0) +
+// x2 (P2 - P1):  identical - stored order for both; edge - test starts at the
+// shared edge in its cyclic order, trial takes the same two vertices first;
+// vertex - both start at the shared vertex and continue cyclically.
+template <int CASE>
+__device__ __forceinline__ void singular_order(const int ta[3], const int tb[3], int oa[3],
+                                               int ob[3])
+{
+    if (CASE == 3) {
+        for (int i = 0; i < 3; ++i) {
+            oa[i] = i;
+            ob[i] = 0;
+            for (int j = 0; j < 3; ++j)
+                if (tb[j] == ta[i]) ob[i] = j;
+        }
+    } else if (CASE == 2) {
+        int p = 0;
+        for (int q = 0; q < 3; ++q) {
+            bool s0 = false, s1 = false;
+            for (int j = 0; j < 3; ++j) {
+                s0 |= tb[j] == ta[q];
+                s1 |= tb[j] == ta[(q + 1) % 3];
+            }
+            if (s0 && s1) {
+                p = q;
+                break;
+            }
+        }
+        oa[0] = p;
+        oa[1] = (p + 1) % 3;
+        oa[2] = (p + 2) % 3;
+        ob[0] = ob[1] = ob[2] = 0;
+        for (int j = 0; j < 3; ++j) {
+            if (tb[j] == ta[oa[0]]) ob[0] = j;
+            else if (tb[j] == ta[oa[1]]) ob[1] = j;
+            else ob[2] = j;
+        }
+    } else {
+        int p = 0, q = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (ta[i] == tb[j]) {
+                    p = i;
+                    q = j;
+                }
+        for (int i = 0; i < 3; ++i) {
+            oa[i] = (p + i) % 3;
+            ob[i] = (q + i) % 3;
+        }
+    }
+}
+
+constexpr int kSingThreads = 128;
+constexpr int kSingMaxPts = 6 * NGL * NGL * NGL;  // largest table (identical, helm)
+
+template <int CASE, int OP, bool CPLX>
+__global__ void __launch_bounds__(kSingThreads)
+k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pairs,
+           const unsigned long long *__restrict__ dev_count, int64_t max_count, void *out)
+{
+    constexpr int NC = CASE == 3 ? 2 : (CASE == 2 ? 3 : 4);
+    constexpr int ROWS = CPLX ? 5 : 6;
+    __shared__ double s_tab[6 * kSingMaxPts];
+    const int npts = CPLX ? tab.n_helm : tab.n_lap;
+    const double *src = CPLX ? tab.helm : tab.lap;
+    for (int e = threadIdx.x; e < ROWS * npts; e += blockDim.x) s_tab[e] = src[e];
+    __syncthreads();
+    int64_t count = max_count;
+    if (dev_count) {
+        unsigned long long c = *dev_count;
+        if ((int64_t)c < count) count = (int64_t)c;
+    }
+    const int64_t n = g.nt;
+    for (int64_t pid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pid < count;
+         pid += (int64_t)gridDim.x * blockDim.x) {
+        SingPair pr = pairs[pid];
+        int ta[3], tb[3];
+        for (int c = 0; c < 3; ++c) {
+            ta[c] = g.tri[c * n + pr.i];
+            tb[c] = g.tri[c * n + pr.j];
+        }
+        int oa[3], ob[3];
+        singular_order<CASE>(ta, tb, oa, ob);
+        double Pa[3][3], Pb[3][3], nx[3], ny[3];
+        for (int v = 0; v < 3; ++v)
+            for (int c = 0; c < 3; ++c) {
+                Pa[v][c] = g.vtx[(3 * oa[v] + c) * n + pr.i];
+                Pb[v][c] = g.vtx[(3 * ob[v] + c) * n + pr.j];
+            }
+        for (int c = 0; c < 3; ++c) {
+            nx[c] = g.nrm[c * n + pr.i];
+            ny[c] = g.nrm[c * n + pr.j];
+        }
+        // edge basis E_i of d = x - y
+        double E[4][3];
+        for (int c = 0; c < 3; ++c) {
+            E[0][c] = Pa[1][c] - Pa[0][c];
+            E[1][c] = Pa[2][c] - Pa[1][c];
+            if (CASE == 2) {
+                E[2][c] = Pb[2][c] - Pb[1][c];
+                E[3][c] = 0.0;
+            } else if (CASE == 1) {
+                E[2][c] = Pb[1][c] - Pb[0][c];
+                E[3][c] = Pb[2][c] - Pb[1][c];
+            } else {
+                E[2][c] = E[3][c] = 0.0;
+            }
+        }
+        double eny[4], enx[4];
+        for (int i = 0; i < 4; ++i) {
+            eny[i] = E[i][0] * ny[0] + E[i][1] * ny[1] + E[i][2] * ny[2];
+            enx[i] = E[i][0] * nx[0] + E[i][1] * nx[1] + E[i][2] * nx[2];
+        }
+        C2 acc = {0.0, 0.0};
+        const bool flat_zero = (CASE == 3 && OP != 0);  // d.n = 0 on one flat panel
+        if (!flat_zero) {
+            for (int q = 0; q < npts; ++q) {
+                double cf[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) cf[i] = s_tab[i * npts + q];
+                double d[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double x = cf[0] * E[0][c];
+#pragma unroll
+                    for (int i = 1; i < NC; ++i) x = fma(cf[i], E[i][c], x);
+                    d[c] = x;
+                }
+                double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
+                double ri = rsqrt(r2);
+                double dn = 0.0;
+                if (OP != 0) {
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) dn = fma(cf[i], OP == 1 ? eny[i] : enx[i], dn);
+                    if (OP == 2) dn = -dn;  // ADLP kernel has -(x - y).n_x
+                }
+                if (!CPLX) {
+                    if (OP == 0) acc.re = fma(s_tab[4 * npts + q], ri, acc.re);
+                    else acc.re = fma(s_tab[5 * npts + q] * dn, ri * ri * ri, acc.re);
+                } else {
+                    // d = xi * dt: sum the xi axis here
+                    double rt = r2 * ri, weta = s_tab[4 * npts + q];
+#pragma unroll
+                    for (int m = 0; m < NGL; ++m) {
+                        double xi = tab.xi[m], r = xi * rt, sn, cs;
+                        sincos(k * r, &sn, &cs);
+                        if (OP == 0) {
+                            // xi^3 J_eta exp(ikr) / (xi rt)
+                            double f = tab.wxi[m] * xi * xi * weta * ri;
+                            acc.re = fma(f, cs, acc.re);
+                            acc.im = fma(f, sn, acc.im);
+                        } else {
+                            // xi^3 J_eta exp(ikr)(1 - ikr) xi dn / (xi rt)^3
+                            double f = tab.wxi[m] * xi * weta * dn * ri * ri * ri;
+                            double kr = k * r;
+                            acc.re = fma(f, fma(kr, sn, cs), acc.re);
+                            acc.im = fma(f, fma(-kr, cs, sn), acc.im);
+                        }
+                    }
+                }
+            }
+        }
+        double sc = 4.0 * g.area[pr.i] * g.area[pr.j] * kInv4Pi;
+        store_val<CPLX>(out, pr.dest, {acc.re * sc, acc.im * sc});
+    }
+}
+
+// Near-field regular pairs: one warp per dense block, entries flattened
+// row-major over the lanes; pairs sharing a vertex are left to k_singular.
+constexpr int kNearThreads = 128;
+
+template <int OP, bool CPLX, int PREC>
+__global__ void __launch_bounds__(kNearThreads)
+k_near_regular(DevGeom g, QuadRule R, double k, const NearBlock *__restrict__ blocks,
+               int64_t nblocks, void *out)
+{
+    using E = RegularEntry<OP, CPLX, PREC>;
+    const int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < nblocks; b += nwarps) {
+        NearBlock B = blocks[b];
+        int64_t m = B.te - B.tb, nn = B.se - B.sb, tot = m * nn;
+        for (int64_t e = lane; e < tot; e += 32) {
+            int64_t r = e / nn, c = e - r * nn;
+            int64_t pi = B.tb + r, pj = B.sb + c;
+            if (shared_count(g, pi, pj) > 0) continue;
+            typename E::Tri ta, tb;
+            E::load(g, pi, ta);
+            E::load(g, pj, tb);
+            store_val<CPLX>(out, B.off + e, E::eval(ta, tb, R, k));
+        }
+    }
+}
+
+int num_sms_cached()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+cudaError_t launch_geometry(const double *V, const int32_t *T, const int32_t *perm, int64_t nt,
+                            const QuadRule &rule, void *const bufs[11], cudaStream_t st)
+{
+    int64_t grid = (nt + kGeomThreads - 1) / kGeomThreads;
+    k_geometry<<<(unsigned)grid, kGeomThreads, 0, st>>>(
+        V, T, perm, nt, rule, (int32_t *)bufs[0], (double *)bufs[1], (double *)bufs[2],
+        (double *)bufs[3], (double *)bufs[4], (float *)bufs[5], (float *)bufs[6],
+        (float *)bufs[7], (float *)bufs[8], (float *)bufs[9]);
+    (void)bufs[10];
+    return cudaGetLastError();
+}
+
+template <int OP, bool CPLX, int PREC>
+static void entries_launch(const DevGeom &g, const QuadRule &R, double k, const int32_t *test,
+                           int64_t n_test, const int32_t *trial, int64_t n_trial, void *out,
+                           SingPair *lists[3], unsigned long long *counts,
+                           unsigned long long cap, int *err, cudaStream_t st)
+{
+    int64_t gx = (n_trial + kEntBx - 1) / kEntBx;
+    int64_t gy = (n_test + kEntBy - 1) / kEntBy;
+    if (gy > 65535) gy = 65535;
+    dim3 grid((unsigned)gx, (unsigned)gy), block(kEntBx, kEntBy);
+    k_entries<OP, CPLX, PREC><<<grid, block, 0, st>>>(g, R, k, test, n_test, trial, n_trial, out,
+                                                      lists[0], lists[1], lists[2], counts, cap,
+                                                      err);
+}
+
+#define BEM_DISPATCH(OPV, CPLXV, PRECV, CALL)                                           \
+    do {                                                                                \
+        if (OPV == 0 && !CPLXV && PRECV == 0) { constexpr int OP = 0; constexpr bool CPLX = false; constexpr int PREC = 0; CALL; } \
+        else if (OPV == 0 && !CPLXV && PRECV == 1) { constexpr int OP = 0; constexpr bool CPLX = false; constexpr int PREC = 1; CALL; } \
+        else if (OPV == 0 && CPLXV && PRECV == 0) { constexpr int OP = 0; constexpr bool CPLX = true; constexpr int PREC = 0; CALL; } \
+        else if (OPV == 0 && CPLXV && PRECV == 1) { constexpr int OP = 0; constexpr bool CPLX = true; constexpr int PREC = 1; CALL; } \
+        else if (OPV == 1 && !CPLXV && PRECV == 0) { constexpr int OP = 1; constexpr bool CPLX = false; constexpr int PREC = 0; CALL; } \
+        else if (OPV == 1 && !CPLXV && PRECV == 1) { constexpr int OP = 1; constexpr bool CPLX = false; constexpr int PREC = 1; CALL; } \
+        else if (OPV == 1 && CPLXV && PRECV == 0) { constexpr int OP = 1; constexpr bool CPLX = true; constexpr int PREC = 0; CALL; } \
+        else if (OPV == 1 && CPLXV && PRECV == 1) { constexpr int OP = 1; constexpr bool CPLX = true; constexpr int PREC = 1; CALL; } \
+        else if (OPV == 2 && !CPLXV && PRECV == 0) { constexpr int OP = 2; constexpr bool CPLX = false; constexpr int PREC = 0; CALL; } \
+        else if (OPV == 2 && !CPLXV && PRECV == 1) { constexpr int OP = 2; constexpr bool CPLX = false; constexpr int PREC = 1; CALL; } \
+        else if (OPV == 2 && CPLXV && PRECV == 0) { constexpr int OP = 2; constexpr bool CPLX = true; constexpr int PREC = 0; CALL; } \
+        else { constexpr int OP = 2; constexpr bool CPLX = true; constexpr int PREC = 1; CALL; } \
+    } while (0)
+
+cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int op, double k,
+                                   int prec, const int32_t *test, int64_t n_test,
+                                   const int32_t *trial, int64_t n_trial, void *out,
+                                   SingPair *lists[3], unsigned long long *counts,
+                                   unsigned long long cap, int *err, cudaStream_t st)
+{
+    const bool cplx = k != 0.0;
+    BEM_DISPATCH(op, cplx, prec,
+                 (entries_launch<OP, CPLX, PREC>(g, rule, k, test, n_test, trial, n_trial, out,
+                                                 lists, counts, cap, err, st)));
+    return cudaGetLastError();
+}
+
+template <int CASE, int OP, bool CPLX>
+static void singular_launch(const DevGeom &g, const SingTable &tab, double k, const SingPair *p,
+                            const unsigned long long *dc, int64_t hc, void *out, cudaStream_t st)
+{
+    if (hc <= 0) return;
+    int64_t want = (hc + kSingThreads - 1) / kSingThreads;
+    int64_t cap = (int64_t)num_sms_cached() * 16;
+    unsigned grid = (unsigned)(want < cap ? want : cap);
+    k_singular<CASE, OP, CPLX><<<grid, kSingThreads, 0, st>>>(g, tab, k, p, dc, hc, out);
+}
+
+cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k,
+                            const SingPair *pairs[3], const unsigned long long *dev_counts,
+                            const int64_t host_counts[3], void *out, cudaStream_t st)
+{
+    const bool cplx = k != 0.0;
+    for (int c = 1; c <= 3; ++c) {
+        const unsigned long long *dc = dev_counts ? dev_counts + (c - 1) : nullptr;
+        const SingTable &T = tabs[c - 1];
+        int64_t hc = host_counts[c - 1];
+        const SingPair *P = pairs[c - 1];
+        BEM_DISPATCH(op, cplx, 0, ({
+                         (void)PREC;
+                         if (c == 1) singular_launch<1, OP, CPLX>(g, T, k, P, dc, hc, out, st);
+                         else if (c == 2) singular_launch<2, OP, CPLX>(g, T, k, P, dc, hc, out, st);
+                         else singular_launch<3, OP, CPLX>(g, T, k, P, dc, hc, out, st);
+                     }));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
+                                const NearBlock *blocks, int64_t nblocks, void *out,
+                                cudaStream_t st)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    const bool cplx = k != 0.0;
+    int64_t warps = nblocks;
+    int64_t grid = (warps * 32 + kNearThreads - 1) / kNearThreads;
+    int64_t cap = (int64_t)num_sms_cached() * 64;
+    if (grid > cap) grid = cap;
+    BEM_DISPATCH(op, cplx, prec,
+                 (k_near_regular<OP, CPLX, PREC>
+                  <<<(unsigned)grid, kNearThreads, 0, st>>>(g, rule, k, blocks, nblocks, out)));
+    return cudaGetLastError();
+}
+
+}  // namespace bem

@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle
+on the same seeded meshes.
+
+Tolerances (relative Frobenius norm per entry set / block):
+  FP64 path   <= 1e-6 (expected ~1e-13)
+  mixed path  <= 1e-5 (expected ~1e-7)
+  singular pairs are FP64 in both modes: elementwise <= 1e-11
+  ACA block vs dense truth: <= 2 e_oracle,b + 1e-6 (FP64) / + 1e-5 (mixed)
+  H-matrix product vs dense product: <= 2 aca_eps
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_01897_gb300 import bem, meshes
+
+pytestmark = pytest.mark.gpu
+
+TOL = {bem.FP64: 1e-6, bem.MIXED: 1e-5}
+
+
+def relf(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.init()
+    return bem.load()
+
+
+@pytest.fixture(scope="module")
+def l3():
+    return meshes.icosphere_level(3)
+
+
+@pytest.fixture(scope="module")
+def l3_mesh(lib, l3):
+    return bem.Mesh(*l3)
+
+
+def _touching_ids(T, seeds):
+    ids = set()
+    for s in seeds:
+        ids |= set(np.nonzero(np.isin(T, T[s]).any(axis=1))[0].tolist())
+    return np.array(sorted(ids), dtype=np.int32)
+
+
+@pytest.mark.parametrize("op", [bem.SLP, bem.DLP, bem.ADLP])
+@pytest.mark.parametrize("k", [0.0, 2.0])
+@pytest.mark.parametrize("prec", [bem.FP64, bem.MIXED])
+def test_entries_against_oracle(l3, l3_mesh, op, k, prec):
+    V, T = l3
+    rng = np.random.default_rng(100 + op + 10 * int(k) + 100 * prec)
+    test = np.concatenate([_touching_ids(T, [5, 600]), rng.choice(T.shape[0], 20, replace=False)])
+    test = test.astype(np.int32)
+    trial = np.concatenate([_touching_ids(T, [5, 601]), rng.choice(T.shape[0], 50, replace=False)])
+    trial = trial.astype(np.int32)
+    got = l3_mesh.entries(op, k, prec, test, trial)
+    ref = oracle.entries(V, T, op, k, test, trial)
+    if k == 0:
+        ref = ref.real
+    err = relf(got, ref)
+    assert err <= TOL[prec], err
+    if prec == bem.FP64:
+        assert err < 1e-11, err
+    # singular pairs are FP64 in both modes and follow the same rule
+    sing = (T[test][:, None, :, None] == T[trial][None, :, None, :]).any(axis=(2, 3))
+    assert sing.sum() > 20
+    scale = np.abs(ref[sing]).max()
+    assert np.max(np.abs(got[sing] - ref[sing])) <= 1e-11 * scale
+
+
+def test_entries_full_matrix_small_meshes(lib):
+    for V, T in [meshes.icosphere(1), meshes.icosphere(2), meshes.ellipsoid(3, (1.0, 0.7, 0.4))]:
+        m = bem.Mesh(V, T)
+        ids = np.arange(T.shape[0], dtype=np.int32)
+        for op in (bem.SLP, bem.DLP, bem.ADLP):
+            ref = oracle.entries(V, T, op, 0.0, ids, ids).real
+            got = m.entries(op, 0.0, bem.FP64, ids, ids)
+            assert relf(got, ref) < 1e-12
+            assert np.max(np.abs(got - ref)) <= 1e-11 * np.abs(ref).max()
+
+
+def test_entries_device_pointers_and_ragged(lib, l3):
+    import torch
+    V, T = l3
+    m = bem.Mesh(V, T)
+    test = torch.arange(3, 3 + 37, dtype=torch.int32, device="cuda")
+    trial = torch.arange(200, 200 + 129, dtype=torch.int32, device="cuda")
+    out = torch.zeros(37, 129, dtype=torch.float64, device="cuda")
+    bem.bem_entries(m.handle, bem.SLP, 0.0, bem.MIXED, test, trial, out)
+    torch.cuda.synchronize()
+    ref = oracle.entries(V, T, 0, 0.0, test.cpu().numpy(), trial.cpu().numpy()).real
+    assert relf(out.cpu().numpy(), ref) < 1e-5
+    outc = torch.zeros(37, 129, dtype=torch.complex128, device="cuda")
+    bem.bem_entries(m.handle, bem.DLP, 1.5, bem.FP64, test, trial, outc)
+    refc = oracle.entries(V, T, 1, 1.5, test.cpu().numpy(), trial.cpu().numpy())
+    assert relf(outc.cpu().numpy(), refc) < 1e-11
+
+
+def test_entries_errors(lib, l3_mesh):
+    out = np.zeros((1, 1))
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_entries(l3_mesh.handle, 0, 0.0, 0, np.array([5000], np.int32),
+                        np.array([0], np.int32), out)
+    assert e.value.status == 1
+    with pytest.raises(bem.BemError):
+        bem.bem_entries(l3_mesh.handle, 7, 0.0, 0, np.array([0], np.int32), np.array([0], np.int32), out)
+    # empty request is a no-op
+    bem.bem_entries(l3_mesh.handle, 0, 0.0, 0, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                    np.zeros((0, 0)))
+
+
+def test_mesh_validation(lib):
+    V, T = meshes.icosphere(1)
+    with pytest.raises(bem.BemError) as e:
+        bem.Mesh(V, np.where(T == 3, 99, T))
+    assert e.value.status == 2
+    Vn = V.copy()
+    Vn[4, 1] = np.nan
+    with pytest.raises(bem.BemError) as e:
+        bem.Mesh(Vn, T)
+    assert e.value.status == 2
+    Td = T.copy()
+    Td[0] = [1, 1, 2]
+    with pytest.raises(bem.BemError) as e:
+        bem.Mesh(V, Td)
+    assert e.value.status == 2
+    Vz = np.vstack([V, V[0] * 2, V[0] * 3])
+    Tz = np.vstack([T, [[0, V.shape[0], V.shape[0] + 1]]])
+    with pytest.raises(bem.BemError) as e:   # collinear vertices: zero area
+        bem.Mesh(Vz, Tz)
+    assert e.value.status == 2
+
+
+# ---- H-matrix -------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def l3_oracle_dense(l3):
+    V, T = l3
+    return {op: oracle.dense_matrix(V, T, op, 0.0).real for op in (0, 1)}
+
+
+def test_block_tree_matches_oracle(lib, l3):
+    V, T = l3
+    m = bem.Mesh(V, T)
+    h = bem.HMatrix(m, 32, 1.2)
+    blocks, perm = h.blocks()
+    ct = oracle.cluster_tree(V, T, 32)
+    ob = oracle.block_list(ct, oracle.block_tree(ct, 1.2))
+    assert np.array_equal(perm, ct.perm)
+    key = lambda a: a[np.lexsort(a.T[::-1])]
+    assert np.array_equal(key(blocks), key(ob))
+    s = h.stats()
+    assert s["n_blocks_far"] == int(ob[:, 4].sum())
+    assert sum(s["singular_pairs"]) == int(
+        (T[:, None, :, None] == T[None, :, None, :]).any(axis=(2, 3)).sum())
+
+
+@pytest.mark.parametrize("prec", [bem.FP64, bem.MIXED])
+@pytest.mark.parametrize("op", [bem.SLP, bem.DLP])
+def test_hmatrix_blocks_and_matvec_l3(lib, l3, l3_oracle_dense, prec, op):
+    """Workload: Laplace P0 on icosphere L3 (1,280 triangles), leaf 32,
+    eta 1.2, ACA eps 1e-4 -- every block is checked against the dense truth."""
+    V, T = l3
+    eps = 1e-4
+    m = bem.Mesh(V, T)
+    h = bem.HMatrix(m, 32, 1.2)
+    h.assemble(op, 0.0, eps, prec)
+    blocks, perm = h.blocks()
+    A = l3_oracle_dense[op]
+    Ap = A[np.ix_(perm, perm)]
+    ohm = oracle.hmat_assemble(V, T, op, 0.0, 32, 1.2, eps)
+    n_far = 0
+    for b, (tb, te, sb, se, adm) in enumerate(blocks):
+        got, rank = h.block_dense(b, (te - tb, se - sb))
+        truth = Ap[tb:te, sb:se]
+        if adm:
+            n_far += 1
+            ob = next(i for i, r in enumerate(ohm.blocks) if tuple(r) == (tb, te, sb, se, 1))
+            e_or = relf(ohm.block_dense(ob), truth)
+            e = relf(got, truth)
+            assert e <= 2 * e_or + TOL[prec], (b, e, e_or, rank)
+            assert 0 < rank < min(te - tb, se - sb)
+        else:
+            assert relf(got, truth) <= TOL[prec] if prec == bem.MIXED else relf(got, truth) < 1e-12
+    assert n_far > 0
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(2, T.shape[0]))
+    y = h.matvec(x, batch=2)
+    yd = x @ A.T
+    for b in range(2):
+        assert relf(y[b], yd[b]) <= 2 * eps
+    s = h.stats()
+    assert s["assembled"] and s["far_entries"] > 0 and s["rank_capped_blocks"] == 0
+
+
+def test_fp64_aca_matches_oracle_aca(lib, l3):
+    """FP64 ACA follows the oracle's pivots; where they coincide the blocks
+    agree to rounding (report how often)."""
+    V, T = l3
+    m = bem.Mesh(V, T)
+    h = bem.HMatrix(m, 32, 1.2)
+    h.assemble(bem.SLP, 0.0, 1e-4, bem.FP64)
+    blocks, _ = h.blocks()
+    ohm = oracle.hmat_assemble(V, T, 0, 0.0, 32, 1.2, 1e-4)
+    same, tot = 0, 0
+    for b, (tb, te, sb, se, adm) in enumerate(blocks):
+        if not adm:
+            continue
+        got, rank = h.block_dense(b, (te - tb, se - sb))
+        ob = next(i for i, r in enumerate(ohm.blocks) if tuple(r) == (tb, te, sb, se, 1))
+        tot += 1
+        if rank == ohm.ranks[ob]:
+            same += 1
+            assert relf(got, ohm.block_dense(ob)) < 1e-6
+    assert same >= 0.9 * tot, (same, tot)
+
+
+def test_hmatrix_helmholtz(lib):
+    V, T = meshes.icosphere_level(2)
+    A = oracle.dense_matrix(V, T, 0, 3.0)
+    m = bem.Mesh(V, T)
+    for prec in (bem.FP64, bem.MIXED):
+        h = bem.HMatrix(m, 16, 1.2)
+        h.assemble(bem.SLP, 3.0, 1e-6, prec)
+        assert h.stats()["n_blocks_far"] > 0
+        x = np.random.default_rng(3).normal(size=T.shape[0]) + 0j
+        y = h.matvec(x)
+        assert relf(y, A @ x) <= max(2e-6, 2 * TOL[prec] if prec == bem.MIXED else 2e-6)
+        h.close()
+
+
+def test_hmatrix_state_and_degenerate(lib):
+    V, T = meshes.icosphere(1)
+    m = bem.Mesh(V, T)
+    h = bem.HMatrix(m, 200, 1.2)      # one leaf: a single dense block
+    with pytest.raises(bem.BemError) as e:
+        h.matvec(np.zeros(T.shape[0]))
+    assert e.value.status == 6
+    with pytest.raises(bem.BemError):
+        bem.bem_mesh_destroy(m.handle)  # still referenced
+    h.assemble(bem.SLP, 0.0, 1e-4, bem.FP64)
+    A = oracle.dense_matrix(V, T, 0, 0.0).real
+    x = np.linspace(-1, 1, T.shape[0])
+    assert relf(h.matvec(x), A @ x) < 1e-13
+    assert h.stats()["n_blocks_far"] == 0
+    h.close()
+
+
+# ---- full-size workload: icosphere L6, jittered (81,920 triangles) ---------
+
+@pytest.fixture(scope="module")
+def l6(lib):
+    return meshes.workload_mesh("sphere_l6_jitter")
+
+
+@pytest.mark.parametrize("op", [bem.SLP, bem.DLP])
+def test_workload_l6_sampled(lib, l6, op):
+    """Laplace SLP/DLP, leaf 32, eta 1.2, ACA eps 1e-5, mixed and FP64, all
+    blocks in one persistent launch; sampled blocks against the oracle's
+    dense blocks and sampled rows of the product against exact rows."""
+    V, T = l6
+    eps = 1e-5
+    m = bem.Mesh(V, T)
+    h = bem.HMatrix(m, 32, 1.2)
+    blocks, perm = h.blocks()
+    rng = np.random.default_rng(11 + op)
+    far = np.nonzero(blocks[:, 4] == 1)[0]
+    near = np.nonzero(blocks[:, 4] == 0)[0]
+    sizes = (blocks[far, 1] - blocks[far, 0]) + (blocks[far, 3] - blocks[far, 2])
+    big = far[np.argsort(-sizes)[:3]]
+    pick_far = np.concatenate([big, rng.choice(far, 12, replace=False)])
+    pick_near = rng.choice(near, 12, replace=False)
+    rows = rng.choice(T.shape[0], 48, replace=False).astype(np.int32)
+    allc = np.arange(T.shape[0], dtype=np.int32)
+    Arows = oracle.entries(V, T, op, 0.0, rows, allc).real
+    x = rng.normal(size=T.shape[0])
+    for prec in (bem.MIXED, bem.FP64):
+        h.assemble(op, 0.0, eps, prec)
+        for b in pick_far:
+            tb, te, sb, se, _ = blocks[b]
+            truth = oracle.entries(V, T, op, 0.0, perm[tb:te], perm[sb:se]).real
+            got, rank = h.block_dense(b, (te - tb, se - sb))
+            # heuristic stopping rule: the oracle's own ACA error is the yardstick
+            U, Vv = oracle.aca_dense(truth, eps)
+            e_or = relf((U @ Vv.T).real, truth)
+            assert relf(got, truth) <= 2 * e_or + TOL[prec] + 2 * eps
+        for b in pick_near:
+            tb, te, sb, se, _ = blocks[b]
+            truth = oracle.entries(V, T, op, 0.0, perm[tb:te], perm[sb:se]).real
+            got, _ = h.block_dense(b, (te - tb, se - sb))
+            assert relf(got, truth) <= TOL[prec]
+        y = h.matvec(x)
+        assert relf(y[rows], Arows @ x) <= 2 * eps
+        s = h.stats()
+        assert s["rank_capped_blocks"] == 0
