@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the H-matrix BEM hot path on GB300.
+
+Workload (default): Laplace single- and double-layer P0 on the icosphere of
+level 6 (81,920 triangles), vertices jittered by 5% of the mean edge length
+(uniform, seeded), cluster leaf 32, eta 1.2, ACA eps 1e-5, FP32 quadrature
+with FP64 accumulation ("mixed"), all admissible blocks in one persistent
+launch per operator.
+
+One step = for both operators: hmat_assemble (near field: regular pairs +
+Sauter-Schwab singular pairs; far field: persistent ACA) and one hmat_matvec
+with a seeded N(0,1) vector.  The mesh geometry and the block tree are built
+once per mesh before the timed region (they do not depend on the operator);
+the end-to-end figure `e2e` rebuilds everything from host arrays every step.
+
+Metric: Galerkin integrals/s = entries evaluated per step (all near-field
+entries + every entry the ACA requested) / step time.  The FP64 path of the
+same step is timed after the run for the mixed-vs-FP64 comparison.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Galerkin integrals/s & H-assembly time; p50/p99 latency; mixed vs FP64 at tol"
+UNIT = "integrals/s"
+WORKLOAD = {"workload": "laplace_slp_dlp_p0_icosphere_l6_jitter5pct", "n_triangles": 81920,
+            "leaf_size": 32, "eta": 1.2, "aca_eps": 1e-5, "operators": ["SLP", "DLP"],
+            "quadrature": "6-pt degree-4 regular, Sauter-Schwab 4^4 GL singular",
+            "precision": "mixed (FP32 quadrature, float-float accumulation, FP64 ACA)",
+            "l2": "flushed between timed steps (256 MiB write)"}
+LEAF, ETA, EPS = 32, 1.2, 1e-5
+
+# GB300 unit counts and the maximum SM clock (profiling recipe)
+N_SM, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, SM_MAX_MHZ = 152, 16, 128, 2070.0
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_gpu{gpu}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arm (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7):
+    """Times the oracle's H-matrix assembly (Algorithm "H-Matrix Assembly":
+    dense near blocks + ACA blocks, SLP and DLP) on a seeded sample of the
+    workload's leaf blocks; returns integrals/s, threads, description."""
+    import oracle
+    ct = oracle.cluster_tree(V, T, LEAF)
+    bl = oracle.block_list(ct, oracle.block_tree(ct, ETA))
+    rng = np.random.default_rng(seed)
+    far = np.nonzero(bl[:, 4] == 1)[0]
+    near = np.nonzero(bl[:, 4] == 0)[0]
+    # stratified: the same fraction of near and far blocks, growing until the
+    # sample takes about seconds_target
+    frac, total_entries, total_t = 0.002, 0, 0.0
+    used = 0
+    while True:
+        nf = max(1, int(frac * far.size))
+        nn = max(1, int(frac * near.size))
+        ids = np.concatenate([rng.choice(far, nf, replace=False), rng.choice(near, nn, replace=False)])
+        t0 = time.perf_counter()
+        ent = 0
+        for op in (oracle.SLP, oracle.DLP):
+            hm = oracle.hmat_assemble(V, T, op, 0.0, LEAF, ETA, EPS, block_ids=ids)
+            ent += hm.entries_evaluated
+        dt = time.perf_counter() - t0
+        total_entries += ent
+        total_t += dt
+        used += ids.size
+        if total_t >= seconds_target or frac >= 0.5:
+            break
+        frac = min(0.5, frac * max(2.0, seconds_target / max(dt, 1e-3) * 0.7))
+    return (total_entries / total_t, oracle.num_threads(),
+            f"{used} of {bl.shape[0]} leaf blocks (near and admissible, seeded stratified sample), "
+            f"SLP+DLP, FP64 oracle, {total_entries} integrals in {total_t:.1f} s")
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1711_01897_gb300 import meshes
+    V, T = meshes.workload_mesh("sphere_l6_jitter")
+    times, vals = [], []
+    for s in range(args.warmup + args.steps):
+        rate, cores, sample = oracle_sample_rate(V, T, seconds_target=args.ref_seconds, seed=100 + s)
+        if s >= args.warmup:
+            vals.append(rate)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": WORKLOAD,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    from paper_1711_01897_gb300 import bem, meshes
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    torch.cuda.init()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    # independent problems per rank: same workload, rank-dependent jitter seed
+    V, T = meshes.icosphere_level(6)
+    V = meshes.jitter(V, T, 0.05, 1001 + 7919 * rank)
+    n = T.shape[0]
+    mesh = bem.Mesh(V, T)
+    hs = {op: bem.HMatrix(mesh, LEAF, ETA) for op in (bem.SLP, bem.DLP)}
+    rng = np.random.default_rng(5 + rank)
+    x_host = rng.normal(size=n)
+    x = torch.from_numpy(x_host).to(dev)
+    ys = {op: torch.zeros(n, dtype=torch.float64, device=dev) for op in hs}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(prec):
+        ent = 0
+        for op, h in hs.items():
+            bem.hmat_assemble(h.handle, op, 0.0, EPS, prec, sptr)
+            bem.hmat_matvec(h.handle, x, ys[op], 1, sptr)
+        for op, h in hs.items():
+            st = h.stats()
+            ent += st["near_entries"] + st["far_entries"]
+        return ent
+
+    for _ in range(args.warmup):
+        step(bem.MIXED)
+        flush.fill_(1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    phase = {"near_regular": 0.0, "singular": 0.0, "aca": 0.0}
+    launches0 = bem.bem_kernel_launches()
+    ents = 0
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.fill_(s & 0xff)
+        ev[s][0].record(stream)
+        ents += step(bem.MIXED)
+        ev[s][1].record(stream)
+        for h in hs.values():
+            st = h.stats()
+            phase["near_regular"] += st["time_near_regular_ms"]
+            phase["singular"] += st["time_singular_ms"]
+            phase["aca"] += st["time_far_ms"]
+    torch.cuda.synchronize()
+    launches = bem.bem_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        e = torch.tensor([ents], device=dev, dtype=torch.float64)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        ents_all = float(e.item())
+    else:
+        ents_all = float(ents)
+    value = ents_all / (total_ms * 1e-3)
+    st_slp, st_dlp = hs[bem.SLP].stats(), hs[bem.DLP].stats()
+    y_mixed = {op: ys[op].cpu().numpy().copy() for op in hs}
+
+    # FP64 path of the same step (after the timed region)
+    fp64_ms = []
+    for r in range(2):
+        flush.fill_(7)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(bem.FP64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms.append(a.elapsed_time(b))
+    y_fp64 = {op: ys[op].cpu().numpy().copy() for op in hs}
+    mixed_vs_fp64 = {
+        "fp64_ms_per_step": float(np.min(fp64_ms)),
+        "mixed_ms_per_step": float(np.median(step_ms)),
+        "speedup": float(np.min(fp64_ms) / np.median(step_ms)),
+        "matvec_rel_diff": {("SLP" if op == 0 else "DLP"): float(
+            np.linalg.norm(y_mixed[op] - y_fp64[op]) / np.linalg.norm(y_fp64[op])) for op in hs},
+        "tolerance": 2 * EPS}
+
+    # end to end through the C ABI from host buffers
+    e2e_ms = []
+    h2d = V.nbytes + T.astype(np.int32).nbytes + 2 * x_host.nbytes
+    d2h = 2 * x_host.nbytes
+    for r in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = bem.Mesh(V, T)
+        ent2 = 0
+        for op in (bem.SLP, bem.DLP):
+            h2 = bem.HMatrix(m2, LEAF, ETA)
+            h2.assemble(op, 0.0, EPS, bem.MIXED, sptr)
+            yh = np.zeros(n)
+            bem.hmat_matvec(h2.handle, x_host, yh, 1, sptr)
+            s2 = h2.stats()
+            ent2 += s2["near_entries"] + s2["far_entries"]
+            h2.close()
+        m2.close()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = ent2 / (np.median(e2e_ms) * 1e-3) * ws
+
+    # roofline of the dominant kernel (device time share over the timed steps)
+    steps = args.steps
+    f_clk = (clk.get("sm_mhz") or SM_MAX_MHZ) * 1e6
+    evals_far = 36.0 * (st_slp["far_entries"] + st_dlp["far_entries"])
+    sing = [st_slp["singular_pairs"][c] + st_dlp["singular_pairs"][c] for c in range(3)]
+    near_reg = st_slp["near_entries"] + st_dlp["near_entries"] - sum(sing)
+    per_step = {k: v / steps for k, v in phase.items()}
+    dom = max(per_step, key=per_step.get)
+    if dom == "aca" or dom == "near_regular":
+        evals = evals_far if dom == "aca" else 36.0 * near_reg
+        achieved = evals / (per_step[dom] * 1e-3) / 1e9
+        peak = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+        roof = {"kernel": "k_aca (persistent ACA + far-field quadrature)" if dom == "aca"
+                else "k_near_regular", "bound": "alu", "pipe": "MUFU (one rsqrt per Green's function evaluation)",
+                "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+                "traffic": None}
+    else:
+        # FP64 singular kernel: DFMA-equivalents per pair from the table sizes
+        per_pair = [128 * 22, 80 * 18, 24 * 15]
+        ops = sum(s * p for s, p in zip(sing, per_pair)) / 2 * 2  # both operators counted in sing
+        achieved = ops / (per_step[dom] * 1e-3) / 1e9
+        peak = FP64_TFLOPS_NOMINAL * 1e12 / 2 / 1e9
+        roof = {"kernel": "k_singular (Sauter-Schwab, FP64)", "bound": "alu", "pipe": "FP64",
+                "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+                "traffic": None}
+    roof["peak_source"] = "derived from unit counts x max SM clock (no ALU peak in MEASURED_PEAKS.json)"
+    roof["phase_ms_per_step"] = per_step
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, sample = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic (seeded jittered icosphere)", "config": WORKLOAD,
+                "integrals_per_step": ents_all / args.steps,
+                "h_assembly_ms": {"SLP": st_slp["time_near_ms"] + st_slp["time_far_ms"],
+                                  "DLP": st_dlp["time_near_ms"] + st_dlp["time_far_ms"]},
+                "tree_ms": st_slp["time_tree_ms"],
+                "ranks": {"SLP": [st_slp["rank_min"], st_slp["rank_mean"], st_slp["rank_max"]],
+                          "DLP": [st_dlp["rank_min"], st_dlp["rank_mean"], st_dlp["rank_max"]]},
+                "mixed_vs_fp64": mixed_vs_fp64,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.median(e2e_ms))},
+                "gpu_launches": int(launches), "step_ms": step_ms}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -63,6 +63,10 @@ enum bem_status {
 /* Library version, e.g. 100 for 0.1.0. */
 int bem_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all handles); a monotone counter for launch accounting. */
+int64_t bem_kernel_launches(void);
+
 /* Text of the calling thread's last error ("" if none).  The pointer stays
  * valid until the next library call on this thread. */
 const char *bem_last_error(void);
@@ -168,6 +172,8 @@ typedef struct {
     double time_tree_ms;         /* hmat_build_tree, host */
     double time_near_ms;         /* last assembly: near field (device) */
     double time_far_ms;          /* last assembly: ACA (device) */
+    double time_near_regular_ms; /* part of time_near_ms: regular pairs */
+    double time_singular_ms;     /* part of time_near_ms: singular pairs */
     int32_t assembled;
     int32_t op;
     double k;

@@ -42,6 +42,7 @@ class HmatStats(ctypes.Structure):
                 ("rank_max", ctypes.c_int32), ("rank_mean", ctypes.c_double),
                 ("rank_capped_blocks", ctypes.c_int64), ("time_tree_ms", ctypes.c_double),
                 ("time_near_ms", ctypes.c_double), ("time_far_ms", ctypes.c_double),
+                ("time_near_regular_ms", ctypes.c_double), ("time_singular_ms", ctypes.c_double),
                 ("assembled", ctypes.c_int32), ("op", ctypes.c_int32), ("k", ctypes.c_double),
                 ("aca_eps", ctypes.c_double), ("prec", ctypes.c_int32)]
 
@@ -66,6 +67,7 @@ def load(path: str = LIB_PATH):
         P, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         sig = {
             "bem_version": ([], ctypes.c_int),
+            "bem_kernel_launches": ([], ctypes.c_int64),
             "bem_last_error": ([], ctypes.c_char_p),
             "bem_mesh_create": ([P, i64, P, i64, P], ctypes.c_int),
             "bem_mesh_destroy": ([P], ctypes.c_int),
@@ -121,6 +123,10 @@ def _stream(stream):
 
 def bem_version() -> int:
     return int(load().bem_version())
+
+
+def bem_kernel_launches() -> int:
+    return int(load().bem_kernel_launches())
 
 
 def bem_last_error() -> str:

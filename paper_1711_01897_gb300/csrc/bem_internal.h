@@ -84,6 +84,10 @@ struct AcaQueue {
     unsigned int next_small;
 };
 
+// Process-wide count of kernel launches (launch accounting).
+void count_launches(int64_t n);
+int64_t launches_total();
+
 // ---- launchers (defined in the .cu files) -------------------------------
 cudaError_t launch_geometry(const double *V, const int32_t *T, const int32_t *perm, int64_t nt,
                             const QuadRule &rule, void *const bufs[11], cudaStream_t st);

@@ -19,10 +19,16 @@
 #include "../../include/bem.h"
 #include "bem_internal.h"
 
+#include <atomic>
+
 using namespace bem;
 
 namespace bem {
 int aca_small_max();
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 }
 
 // ---------------------------------------------------------------------------
@@ -471,6 +477,8 @@ extern "C" {
 
 int bem_version(void) { return 100; }
 
+int64_t bem_kernel_launches(void) { return launches_total(); }
+
 const char *bem_last_error(void) { return g_err.c_str(); }
 
 int bem_mesh_create(const double *vertices, int64_t n_vertices, const int32_t *triangles,
@@ -653,7 +661,7 @@ struct bem_hmat_s {
     std::vector<int64_t> toff;
     std::vector<FarBlock> far_result;     // ranks and chunk offsets after assembly
     int64_t pool_elems = 0;
-    double t_tree = 0, t_near = 0, t_far = 0;
+    double t_tree = 0, t_near = 0, t_far = 0, t_near_reg = 0;
     int64_t far_entries = 0, rank_sum = 0, capped = 0;
     int32_t rank_min = 0, rank_max = 0;
 };
@@ -943,13 +951,13 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         H->eps = aca_eps;
         H->prec = prec;
         H->cplx = cplx;
-        cudaEvent_t ev[3];
+        cudaEvent_t ev[4];
         for (auto &e : ev) CU(cudaEventCreate(&e));
         struct EvGuard {
             cudaEvent_t *e;
             ~EvGuard()
             {
-                for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+                for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
             }
         } eg{ev};
         // near field: regular pairs, then singular pairs (FP64)
@@ -957,6 +965,7 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         CU(cudaEventRecord(ev[0], st));
         CU(launch_near_regular(H->geom.g, D.rule, op, k, prec, H->d_near.as<NearBlock>(),
                                (int64_t)H->near.size(), H->d_near_data.p, st));
+        CU(cudaEventRecord(ev[3], st));
         const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
                                  H->d_sing[2].as<SingPair>()};
         int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
@@ -988,11 +997,13 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             if (attempt >= 6) return fail(BEM_E_OOM, "ACA factor pool keeps overflowing");
             want *= 2;
         }
-        float tn = 0, tf = 0;
+        float tn = 0, tf = 0, tr = 0;
         CU(cudaEventElapsedTime(&tn, ev[0], ev[1]));
         CU(cudaEventElapsedTime(&tf, ev[1], ev[2]));
+        CU(cudaEventElapsedTime(&tr, ev[0], ev[3]));
         H->t_near = tn;
         H->t_far = tf;
+        H->t_near_reg = tr;
         // ranks -> offsets of the V^T x buffer
         std::vector<FarBlock> res(H->far.size());
         if (!res.empty())
@@ -1092,6 +1103,8 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         s.time_tree_ms = H->t_tree;
         s.time_near_ms = H->t_near;
         s.time_far_ms = H->t_far;
+        s.time_near_regular_ms = H->t_near_reg;
+        s.time_singular_ms = H->t_near - H->t_near_reg;
         s.assembled = H->assembled;
         s.op = H->op;
         s.k = H->k;

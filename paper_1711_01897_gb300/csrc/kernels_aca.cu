@@ -399,6 +399,7 @@ cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps
     kern<<<(unsigned)grid, kAcaThreads, dyn, st>>>(
         g, R, k, eps, blocks, n_big, n_small, zwords,
         reinterpret_cast<typename VT<CPLX>::T *>(pool), P, Q);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -328,6 +328,7 @@ cudaError_t launch_geometry(const double *V, const int32_t *T, const int32_t *pe
         V, T, perm, nt, rule, (int32_t *)bufs[0], (double *)bufs[1], (double *)bufs[2],
         (double *)bufs[3], (double *)bufs[4], (float *)bufs[5], (float *)bufs[6],
         (float *)bufs[7], (float *)bufs[8], (float *)bufs[9]);
+    count_launches(1);
     (void)bufs[10];
     return cudaGetLastError();
 }
@@ -345,6 +346,7 @@ static void entries_launch(const DevGeom &g, const QuadRule &R, double k, const 
     k_entries<OP, CPLX, PREC><<<grid, block, 0, st>>>(g, R, k, test, n_test, trial, n_trial, out,
                                                       lists[0], lists[1], lists[2], counts, cap,
                                                       err);
+    count_launches(1);
 }
 
 #define BEM_DISPATCH(OPV, CPLXV, PRECV, CALL)                                           \
@@ -385,6 +387,7 @@ static void singular_launch(const DevGeom &g, const SingTable &tab, double k, co
     int64_t cap = (int64_t)num_sms_cached() * 16;
     unsigned grid = (unsigned)(want < cap ? want : cap);
     k_singular<CASE, OP, CPLX><<<grid, kSingThreads, 0, st>>>(g, tab, k, p, dc, hc, out);
+    count_launches(1);
 }
 
 cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k,
@@ -420,6 +423,7 @@ cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, 
     BEM_DISPATCH(op, cplx, prec,
                  (k_near_regular<OP, CPLX, PREC>
                   <<<(unsigned)grid, kNearThreads, 0, st>>>(g, rule, k, blocks, nblocks, out)));
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -114,18 +114,23 @@ cudaError_t matvec_t(int64_t n, const int32_t *perm, const T *x, T *y, T *xt, T 
 {
     unsigned g1 = (unsigned)((n + kMvThreads - 1) / kMvThreads);
     k_gather<T><<<g1, kMvThreads, 0, st>>>(n, perm, x, xt);
+    count_launches(1);
     if (nfar > 0) {
         int64_t g = (nfar * 32 + kMvThreads - 1) / kMvThreads;
         if (g > 65535) g = 65535;
         k_far_vtx<T><<<(unsigned)g, kMvThreads, 0, st>>>(far, nfar, toff, pool, xt, tbuf);
+        count_launches(1);
     }
     int64_t g2 = (nleaf * 32 + kMvThreads - 1) / kMvThreads;
     if (g2 > 65535) g2 = 65535;
-    if (g2 > 0)
+    if (g2 > 0) {
         k_leaf_rows<T><<<(unsigned)g2, kMvThreads, 0, st>>>(leaf_rows, leaf_ptr, leaf_items, nleaf,
                                                             far, toff, pool, tbuf, near, near_data,
                                                             xt, yt);
+        count_launches(1);
+    }
     k_scatter<T><<<g1, kMvThreads, 0, st>>>(n, perm, yt, y);
+    count_launches(1);
     return cudaGetLastError();
 }
 
