@@ -111,6 +111,33 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
                 int64_t n_test, const int32_t *trial_ids, int64_t n_trial, void *out,
                 void *cuda_stream);
 
+/* The same dense sub-block as bem_entries, for callers that cannot allocate
+ * device memory while they run: a process whose device memory is entirely
+ * reserved by its own pool allocator (an allocation from inside this library
+ * would fail or fragment that pool), or a loop where the latency or failure
+ * of an allocation is not acceptable.  The paper has no counterpart; this is
+ * an interface of this library only.
+ *  - Allocates nothing: no cudaMalloc, cudaMallocAsync, cudaFree or
+ *    allocating library routine.  The list of singular pairs lives in one
+ *    file-scope device array of the library, 12 MiB plus counters, which
+ *    every GPU that loads the library holds until the process exits.
+ *  - test_ids, trial_ids and out must be device memory on the mesh's device,
+ *    which must be current (BEM_E_ARG / BEM_E_STATE otherwise).
+ *  - Maximum size: the request may hold at most 262,144 singular pairs of
+ *    each kind, counted as min(n_test * n_trial, n_test * T) with T the
+ *    largest number of triangles that touch one triangle; larger requests
+ *    return BEM_E_ARG without launching anything (use bem_entries).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and clears its counters first; the array
+ *    keeps the last call's contents.  Calls whose work overlaps on the GPU
+ *    (different streams or threads) race on it: serialise them.
+ *  - Returns after the stream is synchronised, like bem_entries. */
+int bem_entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec,
+                        const int32_t *test_ids, int64_t n_test, const int32_t *trial_ids,
+                        int64_t n_trial, void *out, void *cuda_stream);
+
 /* ---------------------------------------------------------------------- */
 /* Hierarchical matrices (Sec. 2.1; Algorithm "H-Matrix Assembly", Sec. 4.1)*/
 /* ---------------------------------------------------------------------- */

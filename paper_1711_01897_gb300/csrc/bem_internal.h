@@ -84,6 +84,19 @@ struct AcaQueue {
     unsigned int next_small;
 };
 
+// Read-only view of a mesh and of already-initialised per-device constants,
+// for entry points that must not allocate.  mesh_view fails (returns false)
+// for a null mesh; consts_peek returns false if the device has none yet.
+struct MeshView {
+    DevGeom g;
+    int device;
+    int64_t nt;
+    int64_t max_touch;
+};
+bool mesh_view(const void *mesh, MeshView *out);
+bool consts_peek(int device, QuadRule *rule, const SingTable **sing);
+void set_last_error(const char *msg);
+
 // Process-wide count of kernel launches (launch accounting).
 void count_launches(int64_t n);
 int64_t launches_total();

@@ -473,6 +473,33 @@ void build_adjacency(bem_mesh_s &M)
 
 }  // namespace
 
+namespace bem {
+
+bool mesh_view(const void *mesh, MeshView *out)
+{
+    if (!mesh || !out) return false;
+    const bem_mesh_s *M = static_cast<const bem_mesh_s *>(mesh);
+    out->g = M->geom.g;
+    out->device = M->device;
+    out->nt = M->nt;
+    out->max_touch = M->max_touch;
+    return true;
+}
+
+bool consts_peek(int device, QuadRule *rule, const SingTable **sing)
+{
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    auto it = g_dev.find(device);
+    if (it == g_dev.end()) return false;
+    *rule = it->second->rule;
+    *sing = it->second->sing;
+    return true;
+}
+
+void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
+}  // namespace bem
+
 extern "C" {
 
 int bem_version(void) { return 100; }
