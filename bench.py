@@ -198,7 +198,7 @@ def run_gpu(args):
     sptr = stream.cuda_stream
 
     # independent problems per rank: same workload, rank-dependent jitter seed
-    V, T = meshes.icosphere_level(6)
+    V, T = meshes.icosphere_level(args.level)
     V = meshes.jitter(V, T, 0.05, 1001 + 7919 * rank)
     n = T.shape[0]
     mesh = bem.Mesh(V, T)
@@ -341,6 +341,9 @@ def run_gpu(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic (seeded jittered icosphere)", "config": WORKLOAD,
                 "integrals_per_step": ents_all / args.steps,
+                "entries": {"near": st_slp["near_entries"], "far_SLP": st_slp["far_entries"],
+                            "far_DLP": st_dlp["far_entries"], "singular_pairs": st_slp["singular_pairs"],
+                            "far_blocks": st_slp["n_blocks_far"], "near_blocks": st_slp["n_blocks_near"]},
                 "h_assembly_ms": {"SLP": st_slp["time_near_ms"] + st_slp["time_far_ms"],
                                   "DLP": st_dlp["time_near_ms"] + st_dlp["time_far_ms"]},
                 "tree_ms": st_slp["time_tree_ms"],
@@ -367,9 +370,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--level", type=int, default=6,
+                    help="icosphere level of the mesh (6 = the workload; smaller for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.level != 6:
+        WORKLOAD["workload"] = f"laplace_slp_dlp_p0_icosphere_l{args.level}_jitter5pct (profiling size)"
+        WORKLOAD["n_triangles"] = 20 * 4 ** args.level
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
