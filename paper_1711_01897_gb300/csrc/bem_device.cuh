@@ -164,10 +164,10 @@ __device__ __forceinline__ double entry_mixed_laplace(const TriF &a, const TriF 
         if (OP == 1) s *= Dp0 * b.n[0] + Dp1 * b.n[1] + Dp2 * b.n[2];
         ff_add(acc, w[p] * s);
     }
-    FF scale = ff_mul(a.s, b.s);
-    FF hi = ff_mul({acc.hi, 0.f}, scale);
-    FF lo = ff_mul({acc.lo, 0.f}, scale);
-    return (f2d_exact(hi.hi) + f2d_exact(hi.lo)) + f2d_exact(lo.hi);
+    // (acc.hi + acc.lo) * |T_i||T_j|/(4 pi) in float-float, widened with one
+    // FP64 addition
+    FF r = ff_mul(acc, ff_mul(a.s, b.s));
+    return f2d_exact(r.hi) + f2d_exact(r.lo);
 }
 
 // ---- regular entries, FP64 (Laplace and Helmholtz) -----------------------

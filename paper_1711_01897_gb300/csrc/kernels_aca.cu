@@ -188,7 +188,7 @@ struct GroupSmem {
 template <class Grp, int OP, bool CPLX, int PREC>
 __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, double k, double eps,
                           FarBlock *blk, typename VT<CPLX>::T *pool, Pool *P,
-                          GroupSmem<CPLX> &S, unsigned *Z)
+                          GroupSmem<CPLX> &S, unsigned *Z, typename VT<CPLX>::T *part)
 {
     using V = VT<CPLX>;
     using T = typename V::T;
@@ -205,6 +205,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
     G.sync();
 
     int kk = 0, status = 0;
+    int nalloc = 0;  // chunks allocated so far (same value in every thread)
     int64_t nZ = 0, i = 0, entries = 0;
     double normS2 = 0.0, maxpiv = 0.0;
     auto Uat = [&](int l, int64_t r) -> T * {
@@ -215,8 +216,9 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
     };
 
     for (;;) {
-        // factor storage for column kk
-        if (kk < kcap && (kk % KCHUNK) == 0 && S.chunk[kk / KCHUNK] < 0) {
+        // factor storage for column kk; the decision uses only values that
+        // every thread of the group holds, so the barrier below is uniform
+        if (kk < kcap && kk / KCHUNK >= nalloc) {
             if (t == 0) {
                 unsigned long long need = (unsigned long long)(m + n) * KCHUNK;
                 unsigned long long off = atomicAdd(&P->top, need);
@@ -232,6 +234,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 status = 2;
                 break;
             }
+            ++nalloc;
         }
         // selected row of R_{k-1}: a_{i,:} - sum_l (u_l)_i v_l
         for (int l = t; l < kk; l += GS) S.cu[l] = *Uat(l, i);
@@ -311,24 +314,39 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         G.sum2(nu2, nv2);
         G.argmax(bu, br);
         G.sync();
-        // cross terms 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> of ||S_k||_F^2
+        // cross terms 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> of ||S_k||_F^2: every
+        // thread forms the dot products of one column l over one segment of
+        // the rows (and of v_l over one segment of the columns); the segments
+        // of each l are then combined in shared memory.  FP64 work is
+        // k (m + n) multiply-adds plus k * segments additions.
         double cross = 0.0;
-        {
-            const int lane = t & 31;
-            for (int l = G.warp(); l < kk; l += G.nwarps()) {
-                T iu = V::zero(), iv = V::zero();
-                for (int64_t r = lane; r < m; r += 32) iu = V::dotc(*Uat(l, r), *Uat(kk, r), iu);
-                for (int64_t j = lane; j < n; j += 32) iv = V::dotc(*Vat(l, j), *Vat(kk, j), iv);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    iu = V::add(iu, V::shfl_down(iu, o));
-                    iv = V::add(iv, V::shfl_down(iv, o));
-                }
-                if (lane == 0) cross += V::re_mul(iu, iv);
+        for (int l0 = 0; l0 < kk; l0 += GS) {
+            const int kc = (kk - l0) < GS ? (kk - l0) : GS;
+            const int nseg = GS / kc;
+            T iu = V::zero(), iv = V::zero();
+            if (t < kc * nseg) {
+                const int l = l0 + t % kc, sgi = t / kc;
+                const T *ul = Uat(l, 0), *uk = Uat(kk, 0);
+                const T *vl = Vat(l, 0), *vk = Vat(kk, 0);
+                for (int64_t r = (m * sgi) / nseg, r1 = (m * (sgi + 1)) / nseg; r < r1; ++r)
+                    iu = V::dotc(ul[r], uk[r], iu);
+                for (int64_t j = (n * sgi) / nseg, j1 = (n * (sgi + 1)) / nseg; j < j1; ++j)
+                    iv = V::dotc(vl[j], vk[j], iv);
             }
-            if ((t & 31) != 0) cross = 0.0;
-            cross = G.sum(cross);
+            part[t] = iu;
+            part[GS + t] = iv;
+            G.sync();
+            if (t < kc) {
+                T su = part[t], sv = part[GS + t];
+                for (int q = 1; q < nseg; ++q) {
+                    su = V::add(su, part[q * kc + t]);
+                    sv = V::add(sv, part[GS + q * kc + t]);
+                }
+                cross += V::re_mul(su, sv);
+            }
+            G.sync();
         }
+        cross = G.sum(cross);
         normS2 += 2.0 * cross + nu2 * nv2;
         ++kk;
         if (sqrt(nu2) * sqrt(nv2) <= eps * sqrt(normS2)) break;
@@ -346,7 +364,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
 }
 
 template <int OP, bool CPLX, int PREC>
-__global__ void __launch_bounds__(kAcaThreads, 1)
+__global__ void __launch_bounds__(kAcaThreads, 2)
 k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_big,
       int64_t n_small, int64_t zwords_big, typename VT<CPLX>::T *pool, Pool *P, AcaQueue *Q)
 {
@@ -354,6 +372,7 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_b
     __shared__ RedScratch red;
     __shared__ GroupSmem<CPLX> gs[kWarps];
     __shared__ unsigned zsmall[kWarps][(kSmallMax + 31) / 32];
+    __shared__ typename VT<CPLX>::T part[2 * kAcaThreads];
     __shared__ int64_t s_b;
     unsigned *zbig = reinterpret_cast<unsigned *>(smem_raw);
     // phase 1: large blocks, one CTA each
@@ -364,7 +383,7 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_b
         int64_t b = s_b;
         __syncthreads();
         if (b >= n_big) break;
-        aca_block<CtaGroup, OP, CPLX, PREC>(cg, g, R, k, eps, blocks + b, pool, P, gs[0], zbig);
+        aca_block<CtaGroup, OP, CPLX, PREC>(cg, g, R, k, eps, blocks + b, pool, P, gs[0], zbig, part);
     }
     (void)zwords_big;
     // phase 2: small blocks, one warp each
@@ -376,7 +395,7 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_b
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= n_small) break;
         aca_block<WarpGroup, OP, CPLX, PREC>(wg, g, R, k, eps, blocks + n_big + b, pool, P, gs[w],
-                                             zsmall[w]);
+                                             zsmall[w], part + 64 * w);
     }
 }
 
