@@ -31,6 +31,12 @@ struct VT<false> {
     static __device__ __forceinline__ T from(C2 v) { return v.re; }
     static __device__ __forceinline__ T zero() { return 0.0; }
     static __device__ __forceinline__ double mag(T a) { return fabs(a); }
+    // key ordered like |a|; mag_of_key recovers |a|
+    static __device__ __forceinline__ long long key(T a) { return __double_as_longlong(fabs(a)); }
+    static __device__ __forceinline__ double mag_of_key(long long k)
+    {
+        return __longlong_as_double(k);
+    }
     static __device__ __forceinline__ double abs2(T a) { return a * a; }
     static __device__ __forceinline__ T fnma(T a, T b, T c) { return fma(-a, b, c); }  // c - a b
     static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
@@ -50,6 +56,14 @@ struct VT<true> {
     static __device__ __forceinline__ T from(C2 v) { return make_double2(v.re, v.im); }
     static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
     static __device__ __forceinline__ double mag(T a) { return hypot(a.x, a.y); }
+    static __device__ __forceinline__ long long key(T a)
+    {
+        return __double_as_longlong(fma(a.x, a.x, a.y * a.y));
+    }
+    static __device__ __forceinline__ double mag_of_key(long long k)
+    {
+        return sqrt(__longlong_as_double(k));
+    }
     static __device__ __forceinline__ double abs2(T a) { return fma(a.x, a.x, a.y * a.y); }
     static __device__ __forceinline__ T fnma(T a, T b, T c)
     {
@@ -80,6 +94,7 @@ struct VT<true> {
 // ---- groups: a whole CTA or a single warp ---------------------------------
 struct RedScratch {
     double v[kWarps];
+    long long k[kWarps];
     int64_t i[kWarps];
     double s0[kWarps], s1[kWarps];
 };
@@ -106,6 +121,23 @@ __device__ __forceinline__ double warp_sum(double v)
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
+// argmax on integer keys: for non-negative doubles the IEEE bit pattern
+// orders like the value, so the comparisons stay off the FP64 pipe
+__device__ __forceinline__ void warp_argmax_key(long long &key, int64_t &idx)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        long long ok = __shfl_down_sync(0xffffffffu, key, o);
+        int64_t oi = __shfl_down_sync(0xffffffffu, idx, o);
+        if (ok > key || (ok == key && oi < idx)) {
+            key = ok;
+            idx = oi;
+        }
+    }
+    key = __shfl_sync(0xffffffffu, key, 0);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+}
+
 struct WarpGroup {
     int lane;
     __device__ int rank() const { return lane; }
@@ -114,6 +146,7 @@ struct WarpGroup {
     __device__ int nwarps() const { return 1; }
     __device__ void sync() const { __syncwarp(); }
     __device__ void argmax(double &v, int64_t &idx) const { warp_argmax(v, idx); }
+    __device__ void argmax_key(long long &key, int64_t &idx) const { warp_argmax_key(key, idx); }
     __device__ void sum2(double &a, double &b) const
     {
         a = warp_sum(a);
@@ -145,6 +178,27 @@ struct CtaGroup {
             int64_t oi = red->i[q];
             if (ov > v || (ov == v && oi < idx)) {
                 v = ov;
+                idx = oi;
+            }
+        }
+        __syncthreads();
+    }
+    __device__ void argmax_key(long long &key, int64_t &idx) const
+    {
+        warp_argmax_key(key, idx);
+        int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0) {
+            red->k[w] = key;
+            red->i[w] = idx;
+        }
+        __syncthreads();
+        key = red->k[0];
+        idx = red->i[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            long long ok = red->k[q];
+            int64_t oi = red->i[q];
+            if (ok > key || (ok == key && oi < idx)) {
+                key = ok;
                 idx = oi;
             }
         }
@@ -182,6 +236,7 @@ struct GroupSmem {
     typename VT<CPLX>::T cu[KMAX];   // (u_l)_i of the current row / (v_l)_j of the column
     int64_t chunk[NCHUNK];
     int64_t scal;                   // broadcast slot
+    double uv2;                     // ||u_k||^2 ||v_k||^2 of the current step
     int fail;
 };
 
@@ -241,7 +296,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         G.sync();
         typename E::Tri ti;
         E::load(g, tb + i, ti);
-        double best = -1.0;
+        long long bkey = -1;
         int64_t bj = 0;
         for (int64_t j = t; j < n; j += GS) {
             typename E::Tri tj;
@@ -249,17 +304,17 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             T a = V::from(E::eval(ti, tj, R, k));
             for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Vat(l, j), a);
             if (kk < kcap) *Vat(kk, j) = a;
-            double mg = V::mag(a);
-            if (mg > best) {  // j increases, so ties keep the lowest index
-                best = mg;
+            long long ky = V::key(a);
+            if (ky > bkey) {  // j increases, so ties keep the lowest index
+                bkey = ky;
                 bj = j;
             }
         }
         entries += n;
-        G.argmax(best, bj);
+        G.argmax_key(bkey, bj);
         if (t == 0) Z[i >> 5] |= 1u << (i & 31);
         ++nZ;
-        const double vmax = best;
+        const double vmax = bkey < 0 ? -1.0 : V::mag_of_key(bkey);
         if (vmax == 0.0 || vmax <= 1e-14 * maxpiv) {
             if (nZ == m) break;
             G.sync();
@@ -281,19 +336,13 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         const T piv = *Vat(kk, bj);
         const T pinv = V::inv(piv);
         G.sync();
-        double nv2 = 0.0;
-        for (int64_t j = t; j < n; j += GS) {
-            T v = V::mul(*Vat(kk, j), pinv);
-            if (j == bj) v = V::mul(piv, pinv);
-            *Vat(kk, j) = v;
-            nv2 += V::abs2(v);
-        }
+        for (int64_t j = t; j < n; j += GS) *Vat(kk, j) = V::mul(*Vat(kk, j), pinv);
         // selected column of R_{k-1}: a_{:,j} - sum_l (v_l)_j u_l
         for (int l = t; l < kk; l += GS) S.cu[l] = *Vat(l, bj);
         G.sync();
         typename E::Tri tj;
         E::load(g, sb + bj, tj);
-        double nu2 = 0.0, bu = -1.0;
+        long long ukey = -1;
         int64_t br = m;
         for (int64_t r = t; r < m; r += GS) {
             typename E::Tri tr;
@@ -301,27 +350,27 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             T a = V::from(E::eval(tr, tj, R, k));
             for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Uat(l, r), a);
             *Uat(kk, r) = a;
-            nu2 += V::abs2(a);
             if (!((Z[r >> 5] >> (r & 31)) & 1u)) {
-                double mg = V::mag(a);
-                if (mg > bu) {
-                    bu = mg;
+                long long ky = V::key(a);
+                if (ky > ukey) {
+                    ukey = ky;
                     br = r;
                 }
             }
         }
         entries += m;
-        G.sum2(nu2, nv2);
-        G.argmax(bu, br);
+        G.argmax_key(ukey, br);
         G.sync();
-        // cross terms 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> of ||S_k||_F^2: every
-        // thread forms the dot products of one column l over one segment of
-        // the rows (and of v_l over one segment of the columns); the segments
-        // of each l are then combined in shared memory.  FP64 work is
-        // k (m + n) multiply-adds plus k * segments additions.
-        double cross = 0.0;
-        for (int l0 = 0; l0 < kk; l0 += GS) {
-            const int kc = (kk - l0) < GS ? (kk - l0) : GS;
+        // ||S_k||_F^2 grows by 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> + ||u_k||^2 ||v_k||^2.
+        // Every thread forms the dot products of one column l <= k over one
+        // segment of the rows (and of v_l over one segment of the columns);
+        // the segments of each l are combined in shared memory, and one group
+        // sum gives the increment.  FP64 work: (k+1)(m+n) multiply-adds plus
+        // (k+1) * segments additions.
+        double incr = 0.0;
+        const int ncol = kk + 1;
+        for (int l0 = 0; l0 < ncol; l0 += GS) {
+            const int kc = (ncol - l0) < GS ? (ncol - l0) : GS;
             const int nseg = GS / kc;
             T iu = V::zero(), iv = V::zero();
             if (t < kc * nseg) {
@@ -342,14 +391,21 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                     su = V::add(su, part[q * kc + t]);
                     sv = V::add(sv, part[GS + q * kc + t]);
                 }
-                cross += V::re_mul(su, sv);
+                const double pr = V::re_mul(su, sv);
+                if (l0 + t == kk) {
+                    incr += pr;          // ||u_k||^2 ||v_k||^2
+                    S.uv2 = pr;
+                } else {
+                    incr += 2.0 * pr;
+                }
             }
             G.sync();
         }
-        cross = G.sum(cross);
-        normS2 += 2.0 * cross + nu2 * nv2;
+        incr = G.sum(incr);
+        const double uv2 = S.uv2;  // written before the last barrier above
+        normS2 += incr;
         ++kk;
-        if (sqrt(nu2) * sqrt(nv2) <= eps * sqrt(normS2)) break;
+        if (sqrt(uv2) <= eps * sqrt(normS2)) break;
         if (kk == kmin || nZ == m) break;
         i = br;
     }
