@@ -79,6 +79,15 @@ struct Pool {
     int pad;
 };
 
+// Totals of one ACA launch, reduced on the device.
+struct AcaStats {
+    unsigned long long entries;       // entries evaluated by all blocks
+    unsigned long long rank_sum;      // = total length of the V^T x buffer
+    unsigned long long factor_elems;  // elements of all allocated chunks
+    int rank_min, rank_max;
+    int capped, failed;
+};
+
 struct AcaQueue {
     unsigned int next_big;
     unsigned int next_small;
@@ -123,6 +132,12 @@ cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k,
                        double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,
                        int64_t max_m_big, void *pool_data, Pool *pool, AcaQueue *queue,
                        int num_sms, cudaStream_t st);
+
+// After an ACA launch: toff[b] = sum of ranks of blocks < b (toff[n] = total)
+// and the totals in *st.  tile_sums needs aca_finish_tiles(n) entries.
+int64_t aca_finish_tiles(int64_t nfar);
+cudaError_t launch_aca_finish(const FarBlock *far, int64_t nfar, int64_t *toff,
+                              int64_t *tile_sums, AcaStats *st, cudaStream_t st_);
 
 cudaError_t launch_matvec(bool cplx, int64_t n, const int32_t *perm, const void *x, void *y,
                           void *xt, void *yt, void *tbuf, const FarBlock *far, int64_t nfar,

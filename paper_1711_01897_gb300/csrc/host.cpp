@@ -686,7 +686,10 @@ struct bem_hmat_s {
     double k = 0.0, eps = 0.0;
     bool cplx = false;
     std::vector<int64_t> toff;
-    std::vector<FarBlock> far_result;     // ranks and chunk offsets after assembly
+    std::vector<FarBlock> far_result;     // host copy of the factor descriptors, fetched lazily
+    bool far_result_valid = false;
+    int64_t factor_elems = 0;
+    DBuf d_tiles, d_acastats;
     int64_t pool_elems = 0;
     double t_tree = 0, t_near = 0, t_far = 0, t_near_reg = 0;
     int64_t far_entries = 0, rank_sum = 0, capped = 0;
@@ -929,6 +932,9 @@ void upload_tree(bem_hmat_s &H)
                  H.mesh->nt, D.rule, 0);
     H.d_poolhdr.alloc(sizeof(Pool));
     H.d_queue.alloc(sizeof(AcaQueue));
+    H.d_toff.alloc((H.far.size() + 1) * sizeof(int64_t));
+    H.d_tiles.alloc(aca_finish_tiles((int64_t)H.far.size()) * sizeof(int64_t));
+    H.d_acastats.alloc(sizeof(AcaStats));
     CU(cudaStreamSynchronize(0));
 }
 
@@ -1004,6 +1010,7 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         int64_t sum_mn = 0;
         for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
         int64_t want = std::max<int64_t>(H->pool_elems, sum_mn * KCHUNK * 2 + 1024);
+        AcaStats ast{};
         for (int attempt = 0;; ++attempt) {
             if (H->d_pool.bytes < (size_t)want * esz) H->d_pool.alloc((size_t)want * esz);
             H->pool_elems = want;
@@ -1011,14 +1018,17 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             AcaQueue q{0u, 0u};
             CU(cudaMemcpyAsync(H->d_poolhdr.p, &ph, sizeof(ph), cudaMemcpyHostToDevice, st));
             CU(cudaMemcpyAsync(H->d_queue.p, &q, sizeof(q), cudaMemcpyHostToDevice, st));
-            CU(cudaMemcpyAsync(H->d_far.p, H->far.data(), H->far.size() * sizeof(FarBlock),
-                               cudaMemcpyHostToDevice, st));
             if (!H->far.empty())
                 CU(launch_aca(H->geom.g, D.rule, op, k, prec, aca_eps, H->d_far.as<FarBlock>(),
                               H->n_big, H->n_small, H->max_m_big, H->d_pool.p,
                               H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(), D.num_sms, st));
             CU(cudaEventRecord(ev[2], st));
+            // ranks -> offsets of the V^T x buffer, and totals, on the device
+            CU(launch_aca_finish(H->d_far.as<FarBlock>(), (int64_t)H->far.size(),
+                                 H->d_toff.as<int64_t>(), H->d_tiles.as<int64_t>(),
+                                 H->d_acastats.as<AcaStats>(), st));
             CU(cudaMemcpyAsync(&ph, H->d_poolhdr.p, sizeof(ph), cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(&ast, H->d_acastats.p, sizeof(ast), cudaMemcpyDeviceToHost, st));
             CU(cudaStreamSynchronize(st));
             if (!ph.overflow) break;
             if (attempt >= 6) return fail(BEM_E_OOM, "ACA factor pool keeps overflowing");
@@ -1031,30 +1041,20 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         H->t_near = tn;
         H->t_far = tf;
         H->t_near_reg = tr;
-        // ranks -> offsets of the V^T x buffer
-        std::vector<FarBlock> res(H->far.size());
-        if (!res.empty())
-            CU(cudaMemcpy(res.data(), H->d_far.p, res.size() * sizeof(FarBlock), cudaMemcpyDeviceToHost));
-        H->toff.assign(res.size() + 1, 0);
-        H->far_entries = 0;
-        H->rank_sum = 0;
-        H->capped = 0;
-        H->rank_min = res.empty() ? 0 : INT32_MAX;
-        H->rank_max = 0;
-        for (size_t b = 0; b < res.size(); ++b) {
-            H->toff[b + 1] = H->toff[b] + res[b].rank;
-            H->far_entries += res[b].entries;
-            H->rank_sum += res[b].rank;
-            H->capped += res[b].status == 1;
-            H->rank_min = std::min(H->rank_min, res[b].rank);
-            H->rank_max = std::max(H->rank_max, res[b].rank);
-        }
-        H->far_result = res;
-        H->d_toff.upload(H->toff);
+        H->far_entries = (int64_t)ast.entries;
+        H->rank_sum = (int64_t)ast.rank_sum;
+        H->capped = ast.capped;
+        H->rank_min = H->far.empty() ? 0 : ast.rank_min;
+        H->rank_max = ast.rank_max;
+        H->factor_elems = (int64_t)ast.factor_elems;
+        H->far_result_valid = false;
         const int64_t nt = H->mesh->nt;
-        H->d_xt.alloc(nt * esz);
-        H->d_yt.alloc(nt * esz);
-        H->d_tbuf.alloc((H->toff.back() + 1) * esz);
+        if (H->d_xt.bytes < nt * esz) {
+            H->d_xt.alloc(nt * esz);
+            H->d_yt.alloc(nt * esz);
+        }
+        if (H->d_tbuf.bytes < (size_t)(H->rank_sum + 1) * esz)
+            H->d_tbuf.alloc((size_t)(H->rank_sum + 1) * esz * 5 / 4);
         H->assembled = true;
         return BEM_OK;
     });
@@ -1117,15 +1117,11 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         for (int c = 0; c < 3; ++c) s.singular_pairs[c] = (int64_t)H->sing[c].size();
         s.far_entries = H->far_entries;
         const size_t esz = H->cplx ? 16 : 8;
-        int64_t fb = 0;
-        for (const FarBlock &F : H->far_result)
-            for (int c = 0; c < NCHUNK; ++c)
-                if (F.chunk[c] >= 0) fb += ((F.te - F.tb) + (F.se - F.sb)) * KCHUNK * (int64_t)esz;
-        s.factor_bytes = fb;
+        s.factor_bytes = H->factor_elems * (int64_t)esz;
         s.near_bytes = H->near_total * (int64_t)esz;
         s.rank_min = H->rank_min;
         s.rank_max = H->rank_max;
-        s.rank_mean = H->far_result.empty() ? 0.0 : (double)H->rank_sum / H->far_result.size();
+        s.rank_mean = H->far.empty() ? 0.0 : (double)H->rank_sum / H->far.size();
         s.rank_capped_blocks = H->capped;
         s.time_tree_ms = H->t_tree;
         s.time_near_ms = H->t_near;
@@ -1177,6 +1173,12 @@ int hmat_block_dense(bem_hmat H, int64_t block, void *out, int32_t *rank)
             CU(cudaMemcpy(out, H->d_near_data.as<char>() + N.off * esz, bytes, cudaMemcpyDeviceToHost));
             if (rank) *rank = -1;
             return BEM_OK;
+        }
+        if (!H->far_result_valid) {
+            H->far_result.resize(H->far.size());
+            CU(cudaMemcpy(H->far_result.data(), H->d_far.p, H->far.size() * sizeof(FarBlock),
+                          cudaMemcpyDeviceToHost));
+            H->far_result_valid = true;
         }
         auto it = std::find(H->far_block_id.begin(), H->far_block_id.end(), block);
         const FarBlock &F = H->far_result[it - H->far_block_id.begin()];

@@ -377,9 +377,11 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 const int l = l0 + t % kc, sgi = t / kc;
                 const T *ul = Uat(l, 0), *uk = Uat(kk, 0);
                 const T *vl = Vat(l, 0), *vk = Vat(kk, 0);
-                for (int64_t r = (m * sgi) / nseg, r1 = (m * (sgi + 1)) / nseg; r < r1; ++r)
+                // segment bounds in 32-bit arithmetic (m, n < 2^31 / GS)
+                const int mi = (int)m, ni = (int)n;
+                for (int r = (mi * sgi) / nseg, r1 = (mi * (sgi + 1)) / nseg; r < r1; ++r)
                     iu = V::dotc(ul[r], uk[r], iu);
-                for (int64_t j = (n * sgi) / nseg, j1 = (n * (sgi + 1)) / nseg; j < j1; ++j)
+                for (int j = (ni * sgi) / nseg, j1 = (ni * (sgi + 1)) / nseg; j < j1; ++j)
                     iv = V::dotc(vl[j], vk[j], iv);
             }
             part[t] = iu;
@@ -481,6 +483,132 @@ cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps
 }  // namespace
 
 int aca_small_max() { return kSmallMax; }
+
+// ---- after the launch: prefix sums of the ranks and device-side totals ----
+namespace {
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *warp_tot, int64_t &total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    total = warp_tot[(blockDim.x >> 5) - 1];
+    int64_t before = w > 0 ? warp_tot[w - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_rank_tiles(const FarBlock *__restrict__ far, int64_t n, int64_t *tile_sums, AcaStats *st)
+{
+    __shared__ int64_t wt[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int64_t sum = 0, ent = 0, fe = 0;
+    int rmin = 0x7fffffff, rmax = 0, capped = 0, failed = 0;
+    for (int q = 0; q < kScanPer; ++q) {
+        int64_t b = base + q;
+        if (b < n) {
+            const FarBlock &F = far[b];
+            sum += F.rank;
+            ent += F.entries;
+            rmin = min(rmin, F.rank);
+            rmax = max(rmax, F.rank);
+            capped += F.status == 1;
+            failed += F.status == 2;
+            for (int c = 0; c < NCHUNK; ++c)
+                if (F.chunk[c] >= 0) fe += ((F.te - F.tb) + (F.se - F.sb)) * KCHUNK;
+        }
+    }
+    int64_t tot = 0;
+    block_exclusive_scan(sum, wt, tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+    atomicAdd(&st->entries, (unsigned long long)ent);
+    atomicAdd(&st->rank_sum, (unsigned long long)sum);
+    atomicAdd(&st->factor_elems, (unsigned long long)fe);
+    atomicMin(&st->rank_min, rmin);
+    atomicMax(&st->rank_max, rmax);
+    if (capped) atomicAdd(&st->capped, capped);
+    if (failed) atomicAdd(&st->failed, failed);
+}
+
+// exclusive scan of the tile sums in place, one CTA
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile_sums(int64_t *tile_sums, int64_t ntiles)
+{
+    __shared__ int64_t wt[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < ntiles; b0 += kScanThreads) {
+        int64_t b = b0 + threadIdx.x;
+        int64_t v = b < ntiles ? tile_sums[b] : 0;
+        int64_t tot = 0;
+        int64_t ex = block_exclusive_scan(v, wt, tot);
+        int64_t c = carry;
+        if (b < ntiles) tile_sums[b] = c + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_rank_scan(const FarBlock *__restrict__ far, int64_t n, const int64_t *__restrict__ tile_off,
+            int64_t *__restrict__ toff)
+{
+    __shared__ int64_t wt[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int r[kScanPer];
+    int64_t sum = 0;
+    for (int q = 0; q < kScanPer; ++q) {
+        r[q] = base + q < n ? far[base + q].rank : 0;
+        sum += r[q];
+    }
+    int64_t tot = 0;
+    int64_t ex = block_exclusive_scan(sum, wt, tot) + tile_off[blockIdx.x];
+    for (int q = 0; q < kScanPer; ++q) {
+        if (base + q < n) toff[base + q] = ex;
+        if (base + q == n - 1) toff[n] = ex + r[q];
+        ex += r[q];
+    }
+}
+}  // namespace
+
+int64_t aca_finish_tiles(int64_t nfar) { return (nfar + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t launch_aca_finish(const FarBlock *far, int64_t nfar, int64_t *toff,
+                              int64_t *tile_sums, AcaStats *st, cudaStream_t s)
+{
+    AcaStats init{};
+    init.rank_min = 0x7fffffff;
+    cudaError_t e = cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (nfar <= 0) return cudaMemsetAsync(toff, 0, sizeof(int64_t), s);
+    int64_t tiles = (nfar + kScanTile - 1) / kScanTile;
+    k_rank_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(far, nfar, tile_sums, st);
+    count_launches(1);
+    k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tile_sums, tiles);
+    count_launches(1);
+    k_rank_scan<<<(unsigned)tiles, kScanThreads, 0, s>>>(far, nfar, tile_sums, toff);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                        double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,

@@ -226,7 +226,54 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
         }
         C2 acc = {0.0, 0.0};
         const bool flat_zero = (CASE == 3 && OP != 0);  // d.n = 0 on one flat panel
-        if (!flat_zero) {
+        if (CASE == 1 && !CPLX) {
+            // Vertex-adjacent Laplace pair, factorised.  Region 0 maps to
+            // x - y = xi (u(eta1) - eta2 u'(eta3)), region 1 to
+            // x - y = xi (eta2 u(eta3) - u'(eta1)), with u(t) = E0 + t E1 and
+            // u'(t) = E2 + t E3; J = xi^3 eta2.  So |x - y|^2 / xi^2 is a
+            // quadratic in eta2 with coefficients |u_a|^2, u_a.u'_b, |u'_b|^2 over
+            // the 4 x 4 node pairs, and the xi sums (of xi^2 for the single
+            // layer, xi for the double layers) are taken once.
+            double u[NGL][3], up[NGL][3], A[NGL], Cc[NGL], B[NGL][NGL], uny[NGL], upnx[NGL];
+            double sx1 = 0.0, sx2 = 0.0;
+            for (int a = 0; a < NGL; ++a) {
+                const double xa = tab.xi[a];
+                sx1 = fma(tab.wxi[a], xa, sx1);
+                sx2 = fma(tab.wxi[a] * xa, xa, sx2);
+                for (int c = 0; c < 3; ++c) {
+                    u[a][c] = fma(xa, E[1][c], E[0][c]);
+                    up[a][c] = fma(xa, E[3][c], E[2][c]);
+                }
+                A[a] = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
+                Cc[a] = up[a][0] * up[a][0] + up[a][1] * up[a][1] + up[a][2] * up[a][2];
+                uny[a] = u[a][0] * ny[0] + u[a][1] * ny[1] + u[a][2] * ny[2];
+                upnx[a] = up[a][0] * nx[0] + up[a][1] * nx[1] + up[a][2] * nx[2];
+            }
+            for (int a = 0; a < NGL; ++a)
+                for (int b = 0; b < NGL; ++b)
+                    B[a][b] = u[a][0] * up[b][0] + u[a][1] * up[b][1] + u[a][2] * up[b][2];
+            double s = 0.0;
+            for (int c = 0; c < NGL; ++c) {
+                const double e2 = tab.xi[c], m2 = -2.0 * e2, q2 = e2 * e2;
+                for (int a = 0; a < NGL; ++a)      // eta1 node
+                    for (int b = 0; b < NGL; ++b) {  // eta3 node
+                        const double w = tab.wxi[a] * tab.wxi[b] * tab.wxi[c] * e2;
+                        const double q0 = fma(q2, Cc[b], fma(m2, B[a][b], A[a]));
+                        const double q1 = fma(q2, A[b], fma(m2, B[b][a], Cc[a]));
+                        const double r0 = rsqrt(q0), r1 = rsqrt(q1);
+                        if (OP == 0) {
+                            s = fma(w, r0 + r1, s);
+                        } else if (OP == 1) {
+                            // d.n_y / r^3: region 0 xi u_a.n_y, region 1 xi eta2 u_b.n_y
+                            s = fma(w, uny[a] * r0 * r0 * r0 + e2 * uny[b] * r1 * r1 * r1, s);
+                        } else {
+                            // -d.n_x / r^3: region 0 xi eta2 u'_b.n_x, region 1 xi u'_a.n_x
+                            s = fma(w, e2 * upnx[b] * r0 * r0 * r0 + upnx[a] * r1 * r1 * r1, s);
+                        }
+                    }
+            }
+            acc.re = s * (OP == 0 ? sx2 : sx1);
+        } else if (!flat_zero) {
             for (int q = 0; q < npts; ++q) {
                 double cf[NC];
 #pragma unroll
