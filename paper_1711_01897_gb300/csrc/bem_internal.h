@@ -130,8 +130,8 @@ cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, 
 
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                        double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,
-                       int64_t max_m_big, void *pool_data, Pool *pool, AcaQueue *queue,
-                       int num_sms, cudaStream_t st);
+                       int64_t max_m_big, int64_t max_m_small, void *pool_data, Pool *pool,
+                       AcaQueue *queue, int num_sms, cudaStream_t st);
 
 // After an ACA launch: toff[b] = sum of ranks of blocks < b (toff[n] = total)
 // and the totals in *st.  tile_sums needs aca_finish_tiles(n) entries.

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -24,7 +25,7 @@
 using namespace bem;
 
 namespace bem {
-int aca_small_max();
+int aca_small_cap();
 
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -664,6 +665,7 @@ struct bem_hmat_s {
     bem_mesh mesh = nullptr;
     int leaf = 0;
     double eta = 0;
+    int64_t small_max = 8192;             // blocks with max(m, n) <= this run on one warp
     std::vector<int32_t> perm, iperm;
     std::vector<Cluster> cl;
     std::vector<BlockH> blocks;           // tree order
@@ -671,7 +673,7 @@ struct bem_hmat_s {
     std::vector<int64_t> near_block_id;   // index into blocks
     std::vector<FarBlock> far;            // LPT order (big first, then small)
     std::vector<int64_t> far_block_id;
-    int64_t n_big = 0, n_small = 0, max_m_big = 0;
+    int64_t n_big = 0, n_small = 0, max_m_big = 0, max_m_small = 0;
     int64_t near_total = 0;
     std::vector<SingPair> sing[3];
     // leaves (matvec)
@@ -803,7 +805,7 @@ void build_lists(bem_hmat_s &H)
     std::vector<FarBlock> big, small;
     std::vector<int64_t> big_id, small_id;
     int64_t off = 0;
-    const int64_t smax = aca_small_max();
+    const int64_t smax = H.small_max;
     for (size_t b = 0; b < H.blocks.size(); ++b) {
         const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
         if (!H.blocks[b].adm) {
@@ -851,6 +853,8 @@ void build_lists(bem_hmat_s &H)
     H.n_small = (int64_t)small.size();
     H.max_m_big = 0;
     for (auto &F : big) H.max_m_big = std::max(H.max_m_big, F.te - F.tb);
+    H.max_m_small = 0;
+    for (auto &F : small) H.max_m_small = std::max(H.max_m_small, F.te - F.tb);
     H.far = big;
     H.far.insert(H.far.end(), small.begin(), small.end());
     H.far_block_id = big_id;
@@ -955,6 +959,10 @@ int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
         H->mesh = mesh;
         H->leaf = leaf_size;
         H->eta = eta;
+        if (const char *ev = std::getenv("BEM_ACA_SMALL_MAX")) {
+            long v = std::strtol(ev, nullptr, 10);
+            if (v >= 0) H->small_max = std::min<int64_t>(v, aca_small_cap());
+        }
         build_clusters(*H);
         build_blocks(*H);
         build_lists(*H);
@@ -1020,7 +1028,7 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             CU(cudaMemcpyAsync(H->d_queue.p, &q, sizeof(q), cudaMemcpyHostToDevice, st));
             if (!H->far.empty())
                 CU(launch_aca(H->geom.g, D.rule, op, k, prec, aca_eps, H->d_far.as<FarBlock>(),
-                              H->n_big, H->n_small, H->max_m_big, H->d_pool.p,
+                              H->n_big, H->n_small, H->max_m_big, H->max_m_small, H->d_pool.p,
                               H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(), D.num_sms, st));
             CU(cudaEventRecord(ev[2], st));
             // ranks -> offsets of the V^T x buffer, and totals, on the device

@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kAcaThreads = 256;
 constexpr int kWarps = kAcaThreads / 32;
-constexpr int kSmallMax = 256;  // blocks with max(m, n) <= this go to single warps
+constexpr int kSmallCap = 8192;  // largest max(m, n) a single warp may take
 
 template <bool CPLX>
 struct VT;
@@ -424,14 +424,15 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
 template <int OP, bool CPLX, int PREC>
 __global__ void __launch_bounds__(kAcaThreads, 2)
 k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_big,
-      int64_t n_small, int64_t zwords_big, typename VT<CPLX>::T *pool, Pool *P, AcaQueue *Q)
+      int64_t n_small, int zwords_small, typename VT<CPLX>::T *pool, Pool *P, AcaQueue *Q)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ RedScratch red;
     __shared__ GroupSmem<CPLX> gs[kWarps];
-    __shared__ unsigned zsmall[kWarps][(kSmallMax + 31) / 32];
     __shared__ typename VT<CPLX>::T part[2 * kAcaThreads];
     __shared__ int64_t s_b;
+    // row bitmasks: the whole region for a CTA-wide block, then one slice of
+    // zwords_small words per warp for the small blocks
     unsigned *zbig = reinterpret_cast<unsigned *>(smem_raw);
     // phase 1: large blocks, one CTA each
     CtaGroup cg{&red};
@@ -443,7 +444,6 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_b
         if (b >= n_big) break;
         aca_block<CtaGroup, OP, CPLX, PREC>(cg, g, R, k, eps, blocks + b, pool, P, gs[0], zbig, part);
     }
-    (void)zwords_big;
     // phase 2: small blocks, one warp each
     const int w = threadIdx.x >> 5;
     WarpGroup wg{(int)(threadIdx.x & 31)};
@@ -453,17 +453,19 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_b
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= n_small) break;
         aca_block<WarpGroup, OP, CPLX, PREC>(wg, g, R, k, eps, blocks + n_big + b, pool, P, gs[w],
-                                             zsmall[w], part + 64 * w);
+                                             zbig + (int64_t)w * zwords_small, part + 64 * w);
     }
 }
 
 template <int OP, bool CPLX, int PREC>
 cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps,
                        FarBlock *blocks, int64_t n_big, int64_t n_small, int64_t max_m_big,
-                       void *pool, Pool *P, AcaQueue *Q, int num_sms, cudaStream_t st)
+                       int64_t max_m_small, void *pool, Pool *P, AcaQueue *Q, int num_sms,
+                       cudaStream_t st)
 {
-    int64_t zwords = (max_m_big + 31) / 32;
-    size_t dyn = (size_t)(zwords > 0 ? zwords : 1) * sizeof(unsigned);
+    const int64_t zw_big = (max_m_big + 31) / 32, zw_small = (max_m_small + 31) / 32;
+    int64_t words = zw_big > kWarps * zw_small ? zw_big : kWarps * zw_small;
+    size_t dyn = (size_t)(words > 0 ? words : 1) * sizeof(unsigned);
     auto kern = k_aca<OP, CPLX, PREC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dyn);
@@ -474,7 +476,7 @@ cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
     kern<<<(unsigned)grid, kAcaThreads, dyn, st>>>(
-        g, R, k, eps, blocks, n_big, n_small, zwords,
+        g, R, k, eps, blocks, n_big, n_small, (int)zw_small,
         reinterpret_cast<typename VT<CPLX>::T *>(pool), P, Q);
     count_launches(1);
     return cudaGetLastError();
@@ -482,7 +484,7 @@ cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps
 
 }  // namespace
 
-int aca_small_max() { return kSmallMax; }
+int aca_small_cap() { return kSmallCap; }
 
 // ---- after the launch: prefix sums of the ranks and device-side totals ----
 namespace {
@@ -612,14 +614,14 @@ cudaError_t launch_aca_finish(const FarBlock *far, int64_t nfar, int64_t *toff,
 
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                        double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,
-                       int64_t max_m_big, void *pool_data, Pool *pool, AcaQueue *queue,
-                       int num_sms, cudaStream_t st)
+                       int64_t max_m_big, int64_t max_m_small, void *pool_data, Pool *pool,
+                       AcaQueue *queue, int num_sms, cudaStream_t st)
 {
     const bool cplx = k != 0.0;
 #define BEM_ACA(O, C, Pp)                                                                     \
     if (op == O && cplx == C && prec == Pp)                                                   \
         return aca_launch<O, C, Pp>(g, rule, k, eps, blocks, n_big, n_small, max_m_big,       \
-                                    pool_data, pool, queue, num_sms, st);
+                                    max_m_small, pool_data, pool, queue, num_sms, st);
     BEM_ACA(0, false, 0) BEM_ACA(0, false, 1) BEM_ACA(0, true, 0) BEM_ACA(0, true, 1)
     BEM_ACA(1, false, 0) BEM_ACA(1, false, 1) BEM_ACA(1, true, 0) BEM_ACA(1, true, 1)
     BEM_ACA(2, false, 0) BEM_ACA(2, false, 1) BEM_ACA(2, true, 0) BEM_ACA(2, true, 1)
