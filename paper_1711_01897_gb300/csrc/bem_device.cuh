@@ -80,6 +80,8 @@ struct TriD {           // FP64 view
     double area;
 };
 
+// structure-of-arrays load: coalesced when neighbouring lanes read
+// neighbouring triangles
 __device__ __forceinline__ void load_trif(const DevGeom &g, int64_t p, TriF &t)
 {
     const int64_t n = g.nt;
@@ -95,6 +97,34 @@ __device__ __forceinline__ void load_trif(const DevGeom &g, int64_t p, TriF &t)
         for (int c = 0; c < 3; ++c) t.q[q][c] = __ldg(g.qo + (q * 3 + c) * n + p);
     t.s.hi = __ldg(g.sc + p);
     t.s.lo = __ldg(g.sc + n + p);
+}
+
+// array-of-structures load: one 128-byte line per triangle, for lanes that
+// read unrelated triangles
+__device__ __forceinline__ void load_trif_aos(const DevGeom &g, int64_t p, TriF &t)
+{
+    float f[32];
+    const float4 *src = g.tf + 8 * p;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        float4 x = __ldg(src + v);
+        f[4 * v] = x.x;
+        f[4 * v + 1] = x.y;
+        f[4 * v + 2] = x.z;
+        f[4 * v + 3] = x.w;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        t.ch[c] = f[c];
+        t.cl[c] = f[3 + c];
+        t.n[c] = f[24 + c];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t.q[q][c] = f[6 + 3 * q + c];
+    t.s.hi = f[27];
+    t.s.lo = f[28];
 }
 
 __device__ __forceinline__ void load_trid(const DevGeom &g, int64_t p, TriD &t)
@@ -323,6 +353,10 @@ struct RegularEntry<OP, CPLX, 0> {  // FP64
     {
         load_trid(g, p, t);
     }
+    static __device__ __forceinline__ void load_scattered(const DevGeom &g, int64_t p, Tri &t)
+    {
+        load_trid(g, p, t);
+    }
     static __device__ __forceinline__ C2 eval(const Tri &a, const Tri &b, const QuadRule &R,
                                               double k)
     {
@@ -336,6 +370,10 @@ struct RegularEntry<OP, CPLX, 1> {  // mixed
     static __device__ __forceinline__ void load(const DevGeom &g, int64_t p, Tri &t)
     {
         load_trif(g, p, t);
+    }
+    static __device__ __forceinline__ void load_scattered(const DevGeom &g, int64_t p, Tri &t)
+    {
+        load_trif_aos(g, p, t);
     }
     static __device__ __forceinline__ C2 eval(const Tri &a, const Tri &b, const QuadRule &R,
                                               double k)

@@ -29,6 +29,9 @@ struct DevGeom {
     const float *qo;       // [3*NQ][nt] points minus centroid
     const float *nrmf;     // [3][nt]
     const float *sc;       // [2][nt] area / sqrt(4 pi) as float-float (hi, lo)
+    // the mixed-precision view again, 128 bytes per triangle (array of
+    // structures): centroid hi[3] lo[3], points[18], normal[3], scale hi lo, pad
+    const float4 *tf;      // [8 * nt]
 };
 
 // Regular rule: reference points and weights (sum 1).
@@ -91,6 +94,8 @@ struct AcaStats {
 struct AcaQueue {
     unsigned int next_big;
     unsigned int next_small;
+    unsigned int next_tiny;
+    unsigned int pad;
 };
 
 // Read-only view of a mesh and of already-initialised per-device constants,
@@ -112,7 +117,7 @@ int64_t launches_total();
 
 // ---- launchers (defined in the .cu files) -------------------------------
 cudaError_t launch_geometry(const double *V, const int32_t *T, const int32_t *perm, int64_t nt,
-                            const QuadRule &rule, void *const bufs[11], cudaStream_t st);
+                            const QuadRule &rule, void *const bufs[12], cudaStream_t st);
 
 cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int op, double k,
                                    int prec, const int32_t *test, int64_t n_test,
@@ -130,8 +135,8 @@ cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, 
 
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                        double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,
-                       int64_t max_m_big, int64_t max_m_small, void *pool_data, Pool *pool,
-                       AcaQueue *queue, int num_sms, cudaStream_t st);
+                       int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
+                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st);
 
 // After an ACA launch: toff[b] = sum of ranks of blocks < b (toff[n] = total)
 // and the totals in *st.  tile_sums needs aca_finish_tiles(n) entries.

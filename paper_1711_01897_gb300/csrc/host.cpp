@@ -26,6 +26,7 @@ using namespace bem;
 
 namespace bem {
 int aca_small_cap();
+int aca_tiny_max();
 
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -372,7 +373,7 @@ DeviceConsts &device_consts()
 
 // Device geometry owned by a mesh or an H-matrix.
 struct GeomStore {
-    DBuf tri, vtx, nrm, area, qp, ch, cl, qo, nrmf, sc;
+    DBuf tri, vtx, nrm, area, qp, ch, cl, qo, nrmf, sc, tf;
     DevGeom g{};
     void build(const double *dV, const int32_t *dT, const int32_t *dperm, int64_t nt,
                const QuadRule &R, cudaStream_t st)
@@ -387,8 +388,9 @@ struct GeomStore {
         qo.alloc(3 * NQ * nt * sizeof(float));
         nrmf.alloc(3 * nt * sizeof(float));
         sc.alloc(2 * nt * sizeof(float));
-        void *const b[11] = {tri.p, vtx.p, nrm.p, area.p, qp.p, ch.p, cl.p, qo.p, nrmf.p, sc.p,
-                             nullptr};
+        tf.alloc(8 * nt * sizeof(float4));
+        void *const b[12] = {tri.p, vtx.p, nrm.p, area.p, qp.p, ch.p, cl.p, qo.p, nrmf.p, sc.p,
+                             tf.p, nullptr};
         CU(launch_geometry(dV, dT, dperm, nt, R, b, st));
         g.nt = nt;
         g.tri = tri.as<int32_t>();
@@ -401,6 +403,7 @@ struct GeomStore {
         g.qo = qo.as<float>();
         g.nrmf = nrmf.as<float>();
         g.sc = sc.as<float>();
+        g.tf = tf.as<float4>();
     }
 };
 
@@ -666,6 +669,7 @@ struct bem_hmat_s {
     int leaf = 0;
     double eta = 0;
     int64_t small_max = 8192;             // blocks with max(m, n) <= this run on one warp
+    int64_t tiny_max = 0;                 // ... and with max(m, n) <= this on one lane
     std::vector<int32_t> perm, iperm;
     std::vector<Cluster> cl;
     std::vector<BlockH> blocks;           // tree order
@@ -673,7 +677,7 @@ struct bem_hmat_s {
     std::vector<int64_t> near_block_id;   // index into blocks
     std::vector<FarBlock> far;            // LPT order (big first, then small)
     std::vector<int64_t> far_block_id;
-    int64_t n_big = 0, n_small = 0, max_m_big = 0, max_m_small = 0;
+    int64_t n_big = 0, n_small = 0, n_tiny = 0, max_m_big = 0, max_m_small = 0;
     int64_t near_total = 0;
     std::vector<SingPair> sing[3];
     // leaves (matvec)
@@ -802,8 +806,8 @@ void build_lists(bem_hmat_s &H)
     const bem_mesh_s &M = *H.mesh;
     H.near.clear();
     H.near_block_id.clear();
-    std::vector<FarBlock> big, small;
-    std::vector<int64_t> big_id, small_id;
+    std::vector<FarBlock> big, small, tiny;
+    std::vector<int64_t> big_id, small_id, tiny_id;
     int64_t off = 0;
     const int64_t smax = H.small_max;
     for (size_t b = 0; b < H.blocks.size(); ++b) {
@@ -819,12 +823,16 @@ void build_lists(bem_hmat_s &H)
             F.sb = S.b;
             F.se = S.e;
             for (int c = 0; c < NCHUNK; ++c) F.chunk[c] = -1;
-            if (std::max(T.e - T.b, S.e - S.b) > smax) {
+            const int64_t mx = std::max(T.e - T.b, S.e - S.b);
+            if (mx > smax) {
                 big.push_back(F);
                 big_id.push_back((int64_t)b);
-            } else {
+            } else if (mx > H.tiny_max) {
                 small.push_back(F);
                 small_id.push_back((int64_t)b);
+            } else {
+                tiny.push_back(F);
+                tiny_id.push_back((int64_t)b);
             }
         }
     }
@@ -849,16 +857,20 @@ void build_lists(bem_hmat_s &H)
     };
     order(big, big_id);
     order(small, small_id);
+    order(tiny, tiny_id);
     H.n_big = (int64_t)big.size();
     H.n_small = (int64_t)small.size();
+    H.n_tiny = (int64_t)tiny.size();
     H.max_m_big = 0;
     for (auto &F : big) H.max_m_big = std::max(H.max_m_big, F.te - F.tb);
     H.max_m_small = 0;
     for (auto &F : small) H.max_m_small = std::max(H.max_m_small, F.te - F.tb);
     H.far = big;
     H.far.insert(H.far.end(), small.begin(), small.end());
+    H.far.insert(H.far.end(), tiny.begin(), tiny.end());
     H.far_block_id = big_id;
     H.far_block_id.insert(H.far_block_id.end(), small_id.begin(), small_id.end());
+    H.far_block_id.insert(H.far_block_id.end(), tiny_id.begin(), tiny_id.end());
 
     // leaves and, per leaf, the blocks whose row range contains it
     const int64_t nt = M.nt;
@@ -963,6 +975,11 @@ int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
             long v = std::strtol(ev, nullptr, 10);
             if (v >= 0) H->small_max = std::min<int64_t>(v, aca_small_cap());
         }
+        H->tiny_max = 0;  // the one-block-per-lane path is off unless asked for
+        if (const char *ev = std::getenv("BEM_ACA_TINY_MAX")) {
+            long v = std::strtol(ev, nullptr, 10);
+            if (v >= 0) H->tiny_max = std::min<int64_t>(v, aca_tiny_max());
+        }
         build_clusters(*H);
         build_blocks(*H);
         build_lists(*H);
@@ -1023,12 +1040,13 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             if (H->d_pool.bytes < (size_t)want * esz) H->d_pool.alloc((size_t)want * esz);
             H->pool_elems = want;
             Pool ph{0ull, (unsigned long long)want, 0, 0};
-            AcaQueue q{0u, 0u};
+            AcaQueue q{0u, 0u, 0u, 0u};
             CU(cudaMemcpyAsync(H->d_poolhdr.p, &ph, sizeof(ph), cudaMemcpyHostToDevice, st));
             CU(cudaMemcpyAsync(H->d_queue.p, &q, sizeof(q), cudaMemcpyHostToDevice, st));
             if (!H->far.empty())
                 CU(launch_aca(H->geom.g, D.rule, op, k, prec, aca_eps, H->d_far.as<FarBlock>(),
-                              H->n_big, H->n_small, H->max_m_big, H->max_m_small, H->d_pool.p,
+                              H->n_big, H->n_small, H->n_tiny, H->max_m_big, H->max_m_small,
+                              H->d_pool.p,
                               H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(), D.num_sms, st));
             CU(cudaEventRecord(ev[2], st));
             // ranks -> offsets of the V^T x buffer, and totals, on the device

@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(kGeomThreads)
 k_geometry(const double *__restrict__ V, const int32_t *__restrict__ T,
            const int32_t *__restrict__ perm, int64_t nt, QuadRule R, int32_t *tri, double *vtx,
            double *nrm, double *area, double *qp, float *ch, float *cl, float *qo, float *nrmf,
-           float *sc)
+           float *sc, float4 *tf)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nt) return;
@@ -60,6 +60,17 @@ k_geometry(const double *__restrict__ V, const int32_t *__restrict__ T,
     float sh = (float)s;
     sc[p] = sh;
     sc[nt + p] = (float)(s - (double)sh);
+    float f[32];
+    for (int c = 0; c < 3; ++c) {
+        f[c] = ch[c * nt + p];
+        f[3 + c] = cl[c * nt + p];
+        f[24 + c] = nrmf[c * nt + p];
+    }
+    for (int q = 0; q < 3 * NQ; ++q) f[6 + q] = qo[q * nt + p];
+    f[27] = sh;
+    f[28] = sc[nt + p];
+    f[29] = f[30] = f[31] = 0.f;
+    for (int v = 0; v < 8; ++v) tf[8 * p + v] = make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
 }
 
 template <bool CPLX>
@@ -368,15 +379,14 @@ int num_sms_cached()
 }  // namespace
 
 cudaError_t launch_geometry(const double *V, const int32_t *T, const int32_t *perm, int64_t nt,
-                            const QuadRule &rule, void *const bufs[11], cudaStream_t st)
+                            const QuadRule &rule, void *const bufs[12], cudaStream_t st)
 {
     int64_t grid = (nt + kGeomThreads - 1) / kGeomThreads;
     k_geometry<<<(unsigned)grid, kGeomThreads, 0, st>>>(
         V, T, perm, nt, rule, (int32_t *)bufs[0], (double *)bufs[1], (double *)bufs[2],
         (double *)bufs[3], (double *)bufs[4], (float *)bufs[5], (float *)bufs[6],
-        (float *)bufs[7], (float *)bufs[8], (float *)bufs[9]);
+        (float *)bufs[7], (float *)bufs[8], (float *)bufs[9], (float4 *)bufs[10]);
     count_launches(1);
-    (void)bufs[10];
     return cudaGetLastError();
 }
 
