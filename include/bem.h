@@ -201,6 +201,8 @@ typedef struct {
     double time_far_ms;          /* last assembly: ACA (device) */
     double time_near_regular_ms; /* part of time_near_ms: regular pairs */
     double time_singular_ms;     /* part of time_near_ms: singular pairs */
+    int64_t aca_fp64_fma;        /* sum over admissible blocks of rank^2 (m + n): the FP64
+                                    multiply-adds of the ACA residual updates and norms */
     int32_t assembled;
     int32_t op;
     double k;
@@ -226,6 +228,89 @@ int hmat_block_dense(bem_hmat hmat, int64_t block, void *out, int32_t *rank);
 
 /* Frees the handle and its device memory. */
 int hmat_destroy(bem_hmat hmat);
+
+/* ---------------------------------------------------------------------- */
+/* Request server: assembly-and-product requests for meshes of different    */
+/* sizes and wavenumbers arrive over time; each is admitted when the HBM     */
+/* budget allows and runs on its own stream, so admitted requests overlap on */
+/* the device.  (The paper runs one problem at a time; this is the library's */
+/* serving interface.)                                                       */
+/* ---------------------------------------------------------------------- */
+
+typedef struct bem_server_s *bem_server;
+
+enum bem_server_flags { BEM_SERVER_DRY_RUN = 1 };  /* no device work (host logic only) */
+enum bem_request_state {
+    BEM_REQ_QUEUED = 0, BEM_REQ_PREPARING = 1, BEM_REQ_RUNNING = 2, BEM_REQ_DONE = 3,
+    BEM_REQ_FAILED = 4, BEM_REQ_CANCELLED = 5
+};
+
+/* One request: mesh (copied at submit), operator, ACA settings and the host
+ * vector x of the product (n_triangles f64 for k == 0, complex128 otherwise). */
+typedef struct {
+    const double *vertices;
+    int64_t n_vertices;
+    const int32_t *triangles;
+    int64_t n_triangles;
+    int32_t op;
+    double k;
+    double aca_eps;
+    int32_t prec;
+    int32_t leaf_size;
+    double eta;
+    const void *x;
+    double dry_run_ms;   /* duration of the simulated device work (dry-run servers) */
+} bem_request;
+
+typedef struct {
+    int32_t state;              /* bem_request_state */
+    int32_t status;             /* bem_status of the request (BEM_OK while pending) */
+    double t_submit_ms;         /* steady-clock times in ms */
+    double t_admit_ms;
+    double t_done_ms;
+    int64_t reserved_bytes;     /* HBM reserved for the request while it ran */
+    int64_t integrals;          /* entries evaluated: near field + ACA requests */
+    double assembly_ms;         /* device time of the assembly */
+} bem_request_info;
+
+typedef struct {
+    int64_t submitted, completed, failed, cancelled;
+    int64_t queued, running;
+    int64_t reserved_bytes;      /* currently reserved */
+    int64_t peak_reserved_bytes; /* never above the budget */
+    int64_t budget_bytes;
+} bem_server_stats;
+
+/* Creates a server on the current device with `max_slots` worker threads
+ * (1..64), each with its own CUDA stream.  A request is admitted, in arrival
+ * order, once its device bytes (geometry, tree, dense blocks, factor pool of
+ * one 16-column chunk per admissible block, vectors) fit next to the
+ * requests already running; one that alone exceeds the budget fails with
+ * BEM_E_OOM.  flags: BEM_SERVER_DRY_RUN runs the host logic only (no CUDA
+ * call; reserved bytes = 1024 per triangle; y = x after dry_run_ms). */
+int bem_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t flags,
+                      bem_server *out);
+
+/* Queues a request (inputs are copied) and returns its id. */
+int bem_server_submit(bem_server server, const bem_request *req, int64_t *req_id);
+
+/* State and times of a request that has not been collected yet. */
+int bem_server_poll(bem_server server, int64_t req_id, bem_request_info *info);
+
+/* Waits up to timeout_ms (< 0: no limit) for a request to finish.  When it
+ * has finished, copies its product into host `y` (may be NULL), fills *info,
+ * releases the request and returns its status; otherwise returns
+ * BEM_E_TIMEOUT and keeps it. */
+int bem_server_wait(bem_server server, int64_t req_id, int64_t timeout_ms,
+                    bem_request_info *info, void *y);
+
+/* Cancels a request that is still queued (BEM_E_STATE once it has started). */
+int bem_server_cancel(bem_server server, int64_t req_id);
+
+int bem_server_stats_get(bem_server server, bem_server_stats *out);
+
+/* Cancels queued requests, waits for running ones, joins the workers. */
+int bem_server_destroy(bem_server server);
 
 #ifdef __cplusplus
 }

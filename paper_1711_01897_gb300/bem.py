@@ -43,8 +43,34 @@ class HmatStats(ctypes.Structure):
                 ("rank_capped_blocks", ctypes.c_int64), ("time_tree_ms", ctypes.c_double),
                 ("time_near_ms", ctypes.c_double), ("time_far_ms", ctypes.c_double),
                 ("time_near_regular_ms", ctypes.c_double), ("time_singular_ms", ctypes.c_double),
+                ("aca_fp64_fma", ctypes.c_int64),
                 ("assembled", ctypes.c_int32), ("op", ctypes.c_int32), ("k", ctypes.c_double),
                 ("aca_eps", ctypes.c_double), ("prec", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.c_void_p), ("n_vertices", ctypes.c_int64),
+                ("triangles", ctypes.c_void_p), ("n_triangles", ctypes.c_int64),
+                ("op", ctypes.c_int32), ("k", ctypes.c_double), ("aca_eps", ctypes.c_double),
+                ("prec", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("eta", ctypes.c_double),
+                ("x", ctypes.c_void_p), ("dry_run_ms", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("reserved_bytes", ctypes.c_int64),
+                ("integrals", ctypes.c_int64), ("assembly_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("submitted", "completed", "failed", "cancelled", "queued", "running",
+                 "reserved_bytes", "peak_reserved_bytes", "budget_bytes")]
+
+
+QUEUED, PREPARING, RUNNING, DONE, FAILED, CANCELLED = range(6)
+SERVER_DRY_RUN = 1
 
 
 def header_functions() -> list[str]:
@@ -80,6 +106,13 @@ def load(path: str = LIB_PATH):
             "hmat_blocks": ([P, P, i64, P, P], ctypes.c_int),
             "hmat_block_dense": ([P, i64, P, P], ctypes.c_int),
             "hmat_destroy": ([P], ctypes.c_int),
+            "bem_server_create": ([i64, i32, i32, P], ctypes.c_int),
+            "bem_server_submit": ([P, ctypes.POINTER(Request), P], ctypes.c_int),
+            "bem_server_poll": ([P, i64, ctypes.POINTER(RequestInfo)], ctypes.c_int),
+            "bem_server_wait": ([P, i64, i64, ctypes.POINTER(RequestInfo), P], ctypes.c_int),
+            "bem_server_cancel": ([P, i64], ctypes.c_int),
+            "bem_server_stats_get": ([P, ctypes.POINTER(ServerStats)], ctypes.c_int),
+            "bem_server_destroy": ([P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -265,6 +298,63 @@ class HMatrix:
     def close(self):
         if self.handle is not None:
             hmat_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns a bem_server: submit requests, wait for their products."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4, dry_run: bool = False):
+        self.handle = ctypes.c_void_p()
+        _check(load().bem_server_create(int(hbm_budget_bytes), int(max_slots),
+                                        SERVER_DRY_RUN if dry_run else 0, ctypes.byref(self.handle)))
+        self._keep = {}
+
+    def submit(self, vertices, triangles, x, op=SLP, k=0.0, aca_eps=1e-4, prec=MIXED,
+               leaf_size=32, eta=1.2, dry_run_ms=0.0) -> int:
+        V = np.ascontiguousarray(vertices, dtype=np.float64)
+        T = np.ascontiguousarray(triangles, dtype=np.int32)
+        X = np.ascontiguousarray(x, dtype=np.complex128 if k != 0 else np.float64)
+        q = Request(V.ctypes.data, V.shape[0], T.ctypes.data, T.shape[0], op, float(k),
+                    float(aca_eps), prec, leaf_size, float(eta), X.ctypes.data, float(dry_run_ms))
+        rid = ctypes.c_int64()
+        _check(load().bem_server_submit(self.handle, ctypes.byref(q), ctypes.byref(rid)))
+        self._keep[rid.value] = (T.shape[0], k != 0)
+        return rid.value
+
+    def poll(self, rid: int) -> RequestInfo:
+        info = RequestInfo()
+        _check(load().bem_server_poll(self.handle, rid, ctypes.byref(info)))
+        return info
+
+    def wait(self, rid: int, timeout_ms: int = -1):
+        """(status, info, y); status BEM_E_TIMEOUT (5) keeps the request."""
+        nt, cplx = self._keep[rid]
+        y = np.zeros(nt, dtype=np.complex128 if cplx else np.float64)
+        info = RequestInfo()
+        rc = load().bem_server_wait(self.handle, rid, int(timeout_ms), ctypes.byref(info),
+                                    y.ctypes.data)
+        if rc != 5:
+            self._keep.pop(rid, None)
+        return rc, info, y
+
+    def cancel(self, rid: int) -> int:
+        return load().bem_server_cancel(self.handle, rid)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().bem_server_stats_get(self.handle, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            load().bem_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -87,6 +87,8 @@ struct AcaStats {
     unsigned long long entries;       // entries evaluated by all blocks
     unsigned long long rank_sum;      // = total length of the V^T x buffer
     unsigned long long factor_elems;  // elements of all allocated chunks
+    unsigned long long k2mn;          // sum over blocks of rank^2 (m + n): FP64 multiply-adds
+                                      // of the residual updates and norm terms
     int rank_min, rank_max;
     int capped, failed;
 };
@@ -110,6 +112,9 @@ struct MeshView {
 bool mesh_view(const void *mesh, MeshView *out);
 bool consts_peek(int device, QuadRule *rule, const SingTable **sing);
 void set_last_error(const char *msg);
+
+// Stream value meaning "host part only" for the staged create functions.
+inline cudaStream_t const kHostOnly = reinterpret_cast<cudaStream_t>(~uintptr_t(0));
 
 // Process-wide count of kernel launches (launch accounting).
 void count_launches(int64_t n);

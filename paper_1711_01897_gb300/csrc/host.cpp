@@ -74,25 +74,28 @@ int guarded(F &&f)
     }
 }
 
-// device buffer owned by RAII
+// Device buffer owned by RAII, allocated stream-ordered on its home stream
+// and freed on that stream.
 struct DBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t home = 0;
     DBuf() = default;
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
     ~DBuf() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, home);
         p = nullptr;
         bytes = 0;
     }
-    void alloc(size_t b)
+    void alloc(size_t b, cudaStream_t st = 0)
     {
         release();
         if (b == 0) b = 16;
-        CU(cudaMalloc(&p, b));
+        home = st;
+        CU(cudaMallocAsync(&p, b, st));
         bytes = b;
     }
     template <class T>
@@ -101,10 +104,11 @@ struct DBuf {
         return reinterpret_cast<T *>(p);
     }
     template <class T>
-    void upload(const std::vector<T> &v)
+    void upload(const std::vector<T> &v, cudaStream_t st = 0)
     {
-        alloc(v.size() * sizeof(T));
-        if (!v.empty()) CU(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        alloc(v.size() * sizeof(T), st);
+        if (!v.empty())
+            CU(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
     }
 };
 
@@ -355,6 +359,7 @@ DeviceConsts &device_consts()
         DBuf &bl = D->bufs[2 * (c - 1)], &bh = D->bufs[2 * (c - 1) + 1];
         bl.upload(H.lap);
         bh.upload(H.helm);
+        CU(cudaStreamSynchronize(0));
         SingTable &S = D->sing[c - 1];
         S.n_lap = H.n_lap;
         S.n_helm = H.n_helm;
@@ -378,17 +383,17 @@ struct GeomStore {
     void build(const double *dV, const int32_t *dT, const int32_t *dperm, int64_t nt,
                const QuadRule &R, cudaStream_t st)
     {
-        tri.alloc(3 * nt * sizeof(int32_t));
-        vtx.alloc(9 * nt * sizeof(double));
-        nrm.alloc(3 * nt * sizeof(double));
-        area.alloc(nt * sizeof(double));
-        qp.alloc(3 * NQ * nt * sizeof(double));
-        ch.alloc(3 * nt * sizeof(float));
-        cl.alloc(3 * nt * sizeof(float));
-        qo.alloc(3 * NQ * nt * sizeof(float));
-        nrmf.alloc(3 * nt * sizeof(float));
-        sc.alloc(2 * nt * sizeof(float));
-        tf.alloc(8 * nt * sizeof(float4));
+        tri.alloc(3 * nt * sizeof(int32_t), st);
+        vtx.alloc(9 * nt * sizeof(double), st);
+        nrm.alloc(3 * nt * sizeof(double), st);
+        area.alloc(nt * sizeof(double), st);
+        qp.alloc(3 * NQ * nt * sizeof(double), st);
+        ch.alloc(3 * nt * sizeof(float), st);
+        cl.alloc(3 * nt * sizeof(float), st);
+        qo.alloc(3 * NQ * nt * sizeof(float), st);
+        nrmf.alloc(3 * nt * sizeof(float), st);
+        sc.alloc(2 * nt * sizeof(float), st);
+        tf.alloc(8 * nt * sizeof(float4), st);
         void *const b[12] = {tri.p, vtx.p, nrm.p, area.p, qp.p, ch.p, cl.p, qo.p, nrmf.p, sc.p,
                              tf.p, nullptr};
         CU(launch_geometry(dV, dT, dperm, nt, R, b, st));
@@ -512,8 +517,16 @@ int64_t bem_kernel_launches(void) { return launches_total(); }
 
 const char *bem_last_error(void) { return g_err.c_str(); }
 
-int bem_mesh_create(const double *vertices, int64_t n_vertices, const int32_t *triangles,
-                    int64_t n_triangles, bem_mesh *out)
+}  // extern "C"
+
+namespace bem {
+
+int mesh_upload(bem_mesh M, cudaStream_t st);
+
+// Mesh creation with all device work on stream st (synchronised before return);
+// st == kHostOnly stops after the host part (validation and adjacency).
+int mesh_create_impl(const double *vertices, int64_t n_vertices, const int32_t *triangles,
+                     int64_t n_triangles, cudaStream_t st, bem_mesh *out)
 {
     return guarded([&]() -> int {
         if (!out) return fail(BEM_E_ARG, "out is null");
@@ -548,16 +561,41 @@ int bem_mesh_create(const double *vertices, int64_t n_vertices, const int32_t *t
             if (!(n2 > 1e-24 * s2) || n2 == 0.0)
                 return fail(BEM_E_MESH, "zero-area triangle " + std::to_string(t));
         }
-        CU(cudaGetDevice(&M->device));
-        DeviceConsts &D = device_consts();
         build_adjacency(*M);
-        M->dV.upload(M->V);
-        M->dT.upload(M->T);
-        M->geom.build(M->dV.as<double>(), M->dT.as<int32_t>(), nullptr, M->nt, D.rule, 0);
-        CU(cudaStreamSynchronize(0));
+        if (st != kHostOnly) {
+            int rc = mesh_upload(M.get(), st);
+            if (rc) return rc;
+        }
         *out = M.release();
         return BEM_OK;
     });
+}
+
+// Device part of a mesh: geometry on stream st (synchronised).
+int mesh_upload(bem_mesh M, cudaStream_t st)
+{
+    return guarded([&]() -> int {
+        CU(cudaGetDevice(&M->device));
+        DeviceConsts &D = device_consts();
+        M->dV.upload(M->V, st);
+        M->dT.upload(M->T, st);
+        M->geom.build(M->dV.as<double>(), M->dT.as<int32_t>(), nullptr, M->nt, D.rule, st);
+        CU(cudaStreamSynchronize(st));
+        return BEM_OK;
+    });
+}
+
+// Frees a mesh whose streams have all been synchronised by the caller.
+void mesh_free_synced(bem_mesh M) { delete M; }
+
+}  // namespace bem
+
+extern "C" {
+
+int bem_mesh_create(const double *vertices, int64_t n_vertices, const int32_t *triangles,
+                    int64_t n_triangles, bem_mesh *out)
+{
+    return mesh_create_impl(vertices, n_vertices, triangles, n_triangles, 0, out);
 }
 
 int bem_mesh_destroy(bem_mesh mesh)
@@ -565,6 +603,7 @@ int bem_mesh_destroy(bem_mesh mesh)
     return guarded([&]() -> int {
         if (!mesh) return fail(BEM_E_ARG, "null mesh");
         if (mesh->hmat_refs > 0) return fail(BEM_E_STATE, "H-matrices still use this mesh");
+        cudaDeviceSynchronize();  // work of any stream may still read the mesh
         delete mesh;
         return BEM_OK;
     });
@@ -598,7 +637,7 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
             for (int64_t a = 0; a < n_test; ++a)
                 if (test_ids[a] < 0 || test_ids[a] >= mesh->nt)
                     return fail(BEM_E_ARG, "test id out of range");
-            sti.alloc(n_test * 4);
+            sti.alloc(n_test * 4, st);
             CU(cudaMemcpyAsync(sti.p, test_ids, n_test * 4, cudaMemcpyHostToDevice, st));
             dti = sti.as<int32_t>();
         }
@@ -606,12 +645,12 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
             for (int64_t b = 0; b < n_trial; ++b)
                 if (trial_ids[b] < 0 || trial_ids[b] >= mesh->nt)
                     return fail(BEM_E_ARG, "trial id out of range");
-            stj.alloc(n_trial * 4);
+            stj.alloc(n_trial * 4, st);
             CU(cudaMemcpyAsync(stj.p, trial_ids, n_trial * 4, cudaMemcpyHostToDevice, st));
             dtj = stj.as<int32_t>();
         }
         if (host_out) {
-            sto.alloc(nout * esz);
+            sto.alloc(nout * esz, st);
             dout = sto.p;
         }
         // scratch: singular pair lists (one per case), counters, error flag
@@ -694,7 +733,7 @@ struct bem_hmat_s {
     std::vector<int64_t> toff;
     std::vector<FarBlock> far_result;     // host copy of the factor descriptors, fetched lazily
     bool far_result_valid = false;
-    int64_t factor_elems = 0;
+    int64_t factor_elems = 0, k2mn = 0;
     DBuf d_tiles, d_acastats;
     int64_t pool_elems = 0;
     double t_tree = 0, t_near = 0, t_far = 0, t_near_reg = 0;
@@ -934,31 +973,38 @@ void build_lists(bem_hmat_s &H)
     }
 }
 
-void upload_tree(bem_hmat_s &H)
+void upload_tree(bem_hmat_s &H, cudaStream_t st)
 {
-    H.d_perm.upload(H.perm);
-    H.d_near.upload(H.near);
-    H.d_far.upload(H.far);
-    for (int c = 0; c < 3; ++c) H.d_sing[c].upload(H.sing[c]);
-    H.d_leaf_rows.upload(H.leaf_rows);
-    H.d_leaf_ptr.upload(H.leaf_ptr);
-    H.d_leaf_items.upload(H.leaf_items);
+    H.d_perm.upload(H.perm, st);
+    H.d_near.upload(H.near, st);
+    H.d_far.upload(H.far, st);
+    for (int c = 0; c < 3; ++c) H.d_sing[c].upload(H.sing[c], st);
+    H.d_leaf_rows.upload(H.leaf_rows, st);
+    H.d_leaf_ptr.upload(H.leaf_ptr, st);
+    H.d_leaf_items.upload(H.leaf_items, st);
     DeviceConsts &D = device_consts();
     H.geom.build(H.mesh->dV.as<double>(), H.mesh->dT.as<int32_t>(), H.d_perm.as<int32_t>(),
-                 H.mesh->nt, D.rule, 0);
-    H.d_poolhdr.alloc(sizeof(Pool));
-    H.d_queue.alloc(sizeof(AcaQueue));
-    H.d_toff.alloc((H.far.size() + 1) * sizeof(int64_t));
-    H.d_tiles.alloc(aca_finish_tiles((int64_t)H.far.size()) * sizeof(int64_t));
-    H.d_acastats.alloc(sizeof(AcaStats));
-    CU(cudaStreamSynchronize(0));
+                 H.mesh->nt, D.rule, st);
+    H.d_poolhdr.alloc(sizeof(Pool), st);
+    H.d_queue.alloc(sizeof(AcaQueue), st);
+    H.d_toff.alloc((H.far.size() + 1) * sizeof(int64_t), st);
+    H.d_tiles.alloc(aca_finish_tiles((int64_t)H.far.size()) * sizeof(int64_t), st);
+    H.d_acastats.alloc(sizeof(AcaStats), st);
+    CU(cudaStreamSynchronize(st));
 }
 
 }  // namespace
 
 extern "C" {
 
-int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
+}  // extern "C"
+
+namespace bem {
+
+// Tree build on the host, uploads and geometry on stream st (none for
+// st == kHostOnly).
+int hmat_build_tree_impl(bem_mesh mesh, int32_t leaf_size, double eta, cudaStream_t st,
+                         bem_hmat *out)
 {
     return guarded([&]() -> int {
         if (!out) return fail(BEM_E_ARG, "out is null");
@@ -983,12 +1029,54 @@ int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
         build_clusters(*H);
         build_blocks(*H);
         build_lists(*H);
-        upload_tree(*H);
+        if (st != kHostOnly) upload_tree(*H, st);
         H->t_tree = now_ms() - t0;
         ++mesh->hmat_refs;
         *out = H.release();
         return BEM_OK;
     });
+}
+
+// Device part of an H-matrix built with kHostOnly.
+int hmat_upload(bem_hmat H, cudaStream_t st)
+{
+    return guarded([&]() -> int {
+        upload_tree(*H, st);
+        return BEM_OK;
+    });
+}
+
+// Device bytes an assembly of this H-matrix holds (geometry, tree arrays,
+// dense blocks, factor pool of one 16-column chunk per admissible block, and
+// the product buffers), for admission control.
+int64_t hmat_device_bytes(bem_hmat H, bool cplx)
+{
+    const int64_t nt = H->mesh->nt, esz = cplx ? 16 : 8;
+    int64_t sum_mn = 0;
+    for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
+    int64_t geom = 2 * nt * (12 + 72 + 24 + 8 + 144 + 24 + 72 + 12 + 8 + 128);  // mesh + cluster order
+    int64_t tree = (int64_t)(H->near.size() * sizeof(NearBlock) + H->far.size() * sizeof(FarBlock)) +
+                   (int64_t)(H->sing[0].size() + H->sing[1].size() + H->sing[2].size()) * 16 +
+                   (int64_t)(H->leaf_items.size() + H->leaf_ptr.size() + H->leaf_rows.size()) * 8 +
+                   nt * 4 + (int64_t)H->far.size() * 8 * 2;
+    int64_t pool = (sum_mn * KCHUNK * 2 + 1024) * esz;
+    int64_t vecs = 5 * nt * esz;
+    return geom + tree + H->near_total * esz + pool + vecs;
+}
+
+void hmat_free_synced(bem_hmat H)
+{
+    --H->mesh->hmat_refs;
+    delete H;
+}
+
+}  // namespace bem
+
+extern "C" {
+
+int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
+{
+    return hmat_build_tree_impl(mesh, leaf_size, eta, 0, out);
 }
 
 int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec, void *cuda_stream)
@@ -1019,7 +1107,8 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             }
         } eg{ev};
         // near field: regular pairs, then singular pairs (FP64)
-        if (H->d_near_data.bytes < (size_t)H->near_total * esz) H->d_near_data.alloc(H->near_total * esz);
+        if (H->d_near_data.bytes < (size_t)H->near_total * esz)
+            H->d_near_data.alloc(H->near_total * esz, st);
         CU(cudaEventRecord(ev[0], st));
         CU(launch_near_regular(H->geom.g, D.rule, op, k, prec, H->d_near.as<NearBlock>(),
                                (int64_t)H->near.size(), H->d_near_data.p, st));
@@ -1037,7 +1126,7 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         int64_t want = std::max<int64_t>(H->pool_elems, sum_mn * KCHUNK * 2 + 1024);
         AcaStats ast{};
         for (int attempt = 0;; ++attempt) {
-            if (H->d_pool.bytes < (size_t)want * esz) H->d_pool.alloc((size_t)want * esz);
+            if (H->d_pool.bytes < (size_t)want * esz) H->d_pool.alloc((size_t)want * esz, st);
             H->pool_elems = want;
             Pool ph{0ull, (unsigned long long)want, 0, 0};
             AcaQueue q{0u, 0u, 0u, 0u};
@@ -1073,14 +1162,15 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         H->rank_min = H->far.empty() ? 0 : ast.rank_min;
         H->rank_max = ast.rank_max;
         H->factor_elems = (int64_t)ast.factor_elems;
+        H->k2mn = (int64_t)ast.k2mn;
         H->far_result_valid = false;
         const int64_t nt = H->mesh->nt;
         if (H->d_xt.bytes < nt * esz) {
-            H->d_xt.alloc(nt * esz);
-            H->d_yt.alloc(nt * esz);
+            H->d_xt.alloc(nt * esz, st);
+            H->d_yt.alloc(nt * esz, st);
         }
         if (H->d_tbuf.bytes < (size_t)(H->rank_sum + 1) * esz)
-            H->d_tbuf.alloc((size_t)(H->rank_sum + 1) * esz * 5 / 4);
+            H->d_tbuf.alloc((size_t)(H->rank_sum + 1) * esz * 5 / 4, st);
         H->assembled = true;
         return BEM_OK;
     });
@@ -1104,8 +1194,8 @@ int hmat_matvec(bem_hmat H, const void *x, void *y, int32_t batch, void *cuda_st
         const size_t vb = nt * esz;
         const bool hx = !is_device_ptr(x), hy = !is_device_ptr(y);
         if ((hx || hy) && H->d_x.bytes < vb) {
-            H->d_x.alloc(vb);
-            H->d_y.alloc(vb);
+            H->d_x.alloc(vb, st);
+            H->d_y.alloc(vb, st);
         }
         for (int32_t b = 0; b < batch; ++b) {
             const void *xb = (const char *)x + b * vb;
@@ -1154,6 +1244,7 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         s.time_far_ms = H->t_far;
         s.time_near_regular_ms = H->t_near_reg;
         s.time_singular_ms = H->t_near - H->t_near_reg;
+        s.aca_fp64_fma = H->k2mn;
         s.assembled = H->assembled;
         s.op = H->op;
         s.k = H->k;
@@ -1249,6 +1340,7 @@ int hmat_destroy(bem_hmat H)
 {
     return guarded([&]() -> int {
         if (!H) return fail(BEM_E_ARG, "null hmat");
+        cudaDeviceSynchronize();  // products on any stream may still read the factors
         --H->mesh->hmat_refs;
         delete H;
         return BEM_OK;

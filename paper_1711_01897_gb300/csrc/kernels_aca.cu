@@ -735,7 +735,7 @@ k_rank_tiles(const FarBlock *__restrict__ far, int64_t n, int64_t *tile_sums, Ac
 {
     __shared__ int64_t wt[32];
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    int64_t sum = 0, ent = 0, fe = 0;
+    int64_t sum = 0, ent = 0, fe = 0, k2 = 0;
     int rmin = 0x7fffffff, rmax = 0, capped = 0, failed = 0;
     for (int q = 0; q < kScanPer; ++q) {
         int64_t b = base + q;
@@ -743,6 +743,7 @@ k_rank_tiles(const FarBlock *__restrict__ far, int64_t n, int64_t *tile_sums, Ac
             const FarBlock &F = far[b];
             sum += F.rank;
             ent += F.entries;
+            k2 += (int64_t)F.rank * F.rank * ((F.te - F.tb) + (F.se - F.sb));
             rmin = min(rmin, F.rank);
             rmax = max(rmax, F.rank);
             capped += F.status == 1;
@@ -757,6 +758,7 @@ k_rank_tiles(const FarBlock *__restrict__ far, int64_t n, int64_t *tile_sums, Ac
     atomicAdd(&st->entries, (unsigned long long)ent);
     atomicAdd(&st->rank_sum, (unsigned long long)sum);
     atomicAdd(&st->factor_elems, (unsigned long long)fe);
+    atomicAdd(&st->k2mn, (unsigned long long)k2);
     atomicMin(&st->rank_min, rmin);
     atomicMax(&st->rank_max, rmax);
     if (capped) atomicAdd(&st->capped, capped);

@@ -1,0 +1,90 @@
+"""Host logic of the request server, run without a GPU (dry-run servers:
+no CUDA call, simulated device work, reserved bytes = 1024 per triangle)."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1711_01897_gb300 import bem, meshes
+from paper_1711_01897_gb300 import build as bem_build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    bem_build.build()
+    return bem.load()
+
+
+def _mesh(nu):
+    return meshes.icosphere(nu)
+
+
+def test_budget_never_exceeded_and_all_complete(lib):
+    budget = 3 * 1024 * 1280          # room for three L3-sized requests
+    srv = bem.Server(budget, max_slots=6, dry_run=True)
+    V, T = _mesh(8)                   # 1,280 triangles -> 1.25 MiB each
+    ids = [srv.submit(V, T, np.arange(T.shape[0], dtype=float), dry_run_ms=30) for _ in range(12)]
+    peak_running = 0
+    while srv.stats()["completed"] < len(ids):
+        peak_running = max(peak_running, srv.stats()["running"])
+        time.sleep(0.005)
+    st = srv.stats()
+    assert st["peak_reserved_bytes"] <= budget
+    assert st["peak_reserved_bytes"] == budget      # three ran together
+    assert peak_running <= 3
+    for i in ids:
+        rc, info, y = srv.wait(i)
+        assert rc == 0 and info.state == bem.DONE
+        assert np.array_equal(y, np.arange(T.shape[0], dtype=float))
+        assert info.t_submit_ms <= info.t_admit_ms <= info.t_done_ms
+    srv.close()
+
+
+def test_admission_in_arrival_order(lib):
+    V, T = _mesh(8)
+    srv = bem.Server(1024 * 1280, max_slots=4, dry_run=True)   # one at a time
+    ids = [srv.submit(V, T, np.zeros(T.shape[0]), dry_run_ms=10) for _ in range(6)]
+    infos = [srv.wait(i)[1] for i in ids]
+    admits = [inf.t_admit_ms for inf in infos]
+    assert admits == sorted(admits)
+    for a, b in zip(infos, infos[1:]):
+        assert b.t_admit_ms >= a.t_done_ms - 1e-6   # never two at once
+    srv.close()
+
+
+def test_oversized_request_fails_alone(lib):
+    V, T = _mesh(8)
+    srv = bem.Server(1024 * 100, max_slots=2, dry_run=True)
+    rid = srv.submit(V, T, np.zeros(T.shape[0]), dry_run_ms=1)
+    rc, info, _ = srv.wait(rid)
+    assert rc == 3 and info.state == bem.FAILED
+    srv.close()
+
+
+def test_cancel_timeout_and_shutdown(lib):
+    V, T = _mesh(8)
+    srv = bem.Server(1024 * 1280, max_slots=1, dry_run=True)
+    a = srv.submit(V, T, np.zeros(T.shape[0]), dry_run_ms=300)
+    b = srv.submit(V, T, np.zeros(T.shape[0]), dry_run_ms=1)
+    c = srv.submit(V, T, np.zeros(T.shape[0]), dry_run_ms=1)
+    time.sleep(0.05)
+    assert srv.cancel(b) == 0
+    rc, info, _ = srv.wait(a, timeout_ms=20)          # still running: bounded wait ends
+    assert rc == 5 and info.state in (bem.PREPARING, bem.RUNNING)
+    rc, info, _ = srv.wait(b)
+    assert info.state == bem.CANCELLED
+    assert srv.cancel(a) == 6                          # already started
+    rc, _, _ = srv.wait(a)
+    assert rc == 0
+    srv.close()                                        # c is done or cancelled, no hang
+    assert c > a
+
+
+def test_bad_requests_rejected(lib):
+    srv = bem.Server(1 << 20, max_slots=1, dry_run=True)
+    V, T = _mesh(2)
+    with pytest.raises(bem.BemError):
+        srv.submit(V, T, np.zeros(T.shape[0]), aca_eps=-1.0)
+    with pytest.raises(bem.BemError):
+        srv.submit(V, T, np.zeros(T.shape[0]), op=5)
+    srv.close()
