@@ -67,6 +67,25 @@ int bem_version(void);
  * devices, all handles); a monotone counter for launch accounting. */
 int64_t bem_kernel_launches(void);
 
+/* Process-wide tuning, read when a tree is built (row thresholds) and when
+ * an H-matrix is assembled (graphs).  The numerical results do not depend on
+ * it (up to ACA pivot near-ties, which rounding decides).
+ *  warp_max_rows  admissible blocks with max(m, n) <= this are compressed by
+ *                 one warp each, larger ones by a whole CTA (1..8192)
+ *  lane_max_rows  ... and those with max(m, n) <= this by one lane each,
+ *                 32 blocks per warp (0 = off, at most 64)
+ *  use_graphs     1: the kernel sequence of hmat_assemble is captured into a
+ *                 CUDA graph per handle and replayed while op, k, aca_eps,
+ *                 prec and the buffers stay the same */
+typedef struct {
+    int32_t warp_max_rows;
+    int32_t lane_max_rows;
+    int32_t use_graphs;
+} bem_tuning;
+
+int bem_set_tuning(const bem_tuning *t);
+int bem_get_tuning(bem_tuning *t);
+
 /* Text of the calling thread's last error ("" if none).  The pointer stays
  * valid until the next library call on this thread. */
 const char *bem_last_error(void);

@@ -48,6 +48,11 @@ class HmatStats(ctypes.Structure):
                 ("aca_eps", ctypes.c_double), ("prec", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("warp_max_rows", ctypes.c_int32), ("lane_max_rows", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32)]
+
+
 class Request(ctypes.Structure):
     _fields_ = [("vertices", ctypes.c_void_p), ("n_vertices", ctypes.c_int64),
                 ("triangles", ctypes.c_void_p), ("n_triangles", ctypes.c_int64),
@@ -94,6 +99,8 @@ def load(path: str = LIB_PATH):
         sig = {
             "bem_version": ([], ctypes.c_int),
             "bem_kernel_launches": ([], ctypes.c_int64),
+            "bem_set_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
+            "bem_get_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
             "bem_last_error": ([], ctypes.c_char_p),
             "bem_mesh_create": ([P, i64, P, i64, P], ctypes.c_int),
             "bem_mesh_destroy": ([P], ctypes.c_int),
@@ -119,7 +126,15 @@ def load(path: str = LIB_PATH):
             fn.argtypes = args
             fn.restype = res
         _lib = L
-        return L
+    # apply the autotuner's table, if one has been written
+    table = os.path.join(_HERE, "tuning.json")
+    if os.path.exists(table):
+        import json
+        with open(table) as f:
+            t = json.load(f)
+        tt = Tuning(int(t["warp_max_rows"]), int(t["lane_max_rows"]), int(t.get("use_graphs", 1)))
+        L.bem_set_tuning(ctypes.byref(tt))
+    return L
 
 
 def _check(rc: int):
@@ -160,6 +175,18 @@ def bem_version() -> int:
 
 def bem_kernel_launches() -> int:
     return int(load().bem_kernel_launches())
+
+
+def bem_set_tuning(warp_max_rows: int, lane_max_rows: int, use_graphs: int = 1):
+    t = Tuning(int(warp_max_rows), int(lane_max_rows), int(use_graphs))
+    _check(load().bem_set_tuning(ctypes.byref(t)))
+
+
+def bem_get_tuning() -> dict:
+    t = Tuning()
+    _check(load().bem_get_tuning(ctypes.byref(t)))
+    return {"warp_max_rows": t.warp_max_rows, "lane_max_rows": t.lane_max_rows,
+            "use_graphs": t.use_graphs}
 
 
 def bem_last_error() -> str:

@@ -146,6 +146,9 @@ cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k,
 // After an ACA launch: toff[b] = sum of ranks of blocks < b (toff[n] = total)
 // and the totals in *st.  tile_sums needs aca_finish_tiles(n) entries.
 int64_t aca_finish_tiles(int64_t nfar);
+// Zeroes the pool header (capacity cap), the work queues and the totals.
+cudaError_t launch_aca_reset(Pool *P, unsigned long long cap, AcaQueue *Q, AcaStats *st,
+                             cudaStream_t s);
 cudaError_t launch_aca_finish(const FarBlock *far, int64_t nfar, int64_t *toff,
                               int64_t *tile_sums, AcaStats *st, cudaStream_t st_);
 

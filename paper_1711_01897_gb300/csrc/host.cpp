@@ -28,6 +28,9 @@ namespace bem {
 int aca_small_cap();
 int aca_tiny_max();
 
+static std::mutex g_tune_mu;
+static bem_tuning g_tuning{8192, 0, 1};
+
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
@@ -515,6 +518,27 @@ int bem_version(void) { return 100; }
 
 int64_t bem_kernel_launches(void) { return launches_total(); }
 
+int bem_set_tuning(const bem_tuning *t)
+{
+    if (!t || t->warp_max_rows < 1 || t->warp_max_rows > aca_small_cap() || t->lane_max_rows < 0 ||
+        t->lane_max_rows > aca_tiny_max() || t->lane_max_rows > t->warp_max_rows ||
+        (t->use_graphs != 0 && t->use_graphs != 1)) {
+        set_last_error("bad tuning values");
+        return BEM_E_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuning = *t;
+    return BEM_OK;
+}
+
+int bem_get_tuning(bem_tuning *t)
+{
+    if (!t) return BEM_E_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *t = g_tuning;
+    return BEM_OK;
+}
+
 const char *bem_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
@@ -737,6 +761,23 @@ struct bem_hmat_s {
     DBuf d_tiles, d_acastats;
     int64_t pool_elems = 0;
     double t_tree = 0, t_near = 0, t_far = 0, t_near_reg = 0;
+    // CUDA graph of the assembly sequence and what it was captured for
+    cudaGraphExec_t graph = nullptr;
+    int g_op = -1, g_prec = -1;
+    double g_k = 0, g_eps = 0;
+    void *g_pool = nullptr, *g_near = nullptr;
+    int64_t g_nodes = 0, g_pool_elems = -1;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    Pool *pin_pool = nullptr;       // pinned readback slots
+    AcaStats *pin_stats = nullptr;
+    ~bem_hmat_s()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        if (pin_pool) cudaFreeHost(pin_pool);
+        if (pin_stats) cudaFreeHost(pin_stats);
+    }
     int64_t far_entries = 0, rank_sum = 0, capped = 0;
     int32_t rank_min = 0, rank_max = 0;
 };
@@ -1017,14 +1058,10 @@ int hmat_build_tree_impl(bem_mesh mesh, int32_t leaf_size, double eta, cudaStrea
         H->mesh = mesh;
         H->leaf = leaf_size;
         H->eta = eta;
-        if (const char *ev = std::getenv("BEM_ACA_SMALL_MAX")) {
-            long v = std::strtol(ev, nullptr, 10);
-            if (v >= 0) H->small_max = std::min<int64_t>(v, aca_small_cap());
-        }
-        H->tiny_max = 0;  // the one-block-per-lane path is off unless asked for
-        if (const char *ev = std::getenv("BEM_ACA_TINY_MAX")) {
-            long v = std::strtol(ev, nullptr, 10);
-            if (v >= 0) H->tiny_max = std::min<int64_t>(v, aca_tiny_max());
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            H->small_max = g_tuning.warp_max_rows;
+            H->tiny_max = g_tuning.lane_max_rows;
         }
         build_clusters(*H);
         build_blocks(*H);
@@ -1097,58 +1134,102 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         H->eps = aca_eps;
         H->prec = prec;
         H->cplx = cplx;
-        cudaEvent_t ev[4];
-        for (auto &e : ev) CU(cudaEventCreate(&e));
-        struct EvGuard {
-            cudaEvent_t *e;
-            ~EvGuard()
-            {
-                for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
-            }
-        } eg{ev};
-        // near field: regular pairs, then singular pairs (FP64)
+        if (!H->ev[0])
+            for (auto &e : H->ev) CU(cudaEventCreate(&e));
+        if (!H->pin_pool) {
+            CU(cudaMallocHost(&H->pin_pool, sizeof(Pool)));
+            CU(cudaMallocHost(&H->pin_stats, sizeof(AcaStats)));
+        }
+        cudaEvent_t *ev = H->ev;
+        bool use_graphs;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            use_graphs = g_tuning.use_graphs != 0;
+        }
         if (H->d_near_data.bytes < (size_t)H->near_total * esz)
             H->d_near_data.alloc(H->near_total * esz, st);
-        CU(cudaEventRecord(ev[0], st));
-        CU(launch_near_regular(H->geom.g, D.rule, op, k, prec, H->d_near.as<NearBlock>(),
-                               (int64_t)H->near.size(), H->d_near_data.p, st));
-        CU(cudaEventRecord(ev[3], st));
-        const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
-                                 H->d_sing[2].as<SingPair>()};
-        int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
-                         (int64_t)H->sing[2].size()};
-        CU(launch_singular(H->mesh->geom.g, D.sing, op, k, sp, nullptr, hc, H->d_near_data.p, st));
-        CU(cudaEventRecord(ev[1], st));
-        // far field: persistent ACA over all admissible blocks; the factor
-        // pool grows and the launch repeats if it overflows
         int64_t sum_mn = 0;
         for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
         int64_t want = std::max<int64_t>(H->pool_elems, sum_mn * KCHUNK * 2 + 1024);
-        AcaStats ast{};
-        for (int attempt = 0;; ++attempt) {
-            if (H->d_pool.bytes < (size_t)want * esz) H->d_pool.alloc((size_t)want * esz, st);
-            H->pool_elems = want;
-            Pool ph{0ull, (unsigned long long)want, 0, 0};
-            AcaQueue q{0u, 0u, 0u, 0u};
-            CU(cudaMemcpyAsync(H->d_poolhdr.p, &ph, sizeof(ph), cudaMemcpyHostToDevice, st));
-            CU(cudaMemcpyAsync(H->d_queue.p, &q, sizeof(q), cudaMemcpyHostToDevice, st));
+        // the whole sequence: near field (regular, then singular pairs, FP64),
+        // then the persistent ACA over all admissible blocks and its totals
+        auto enqueue = [&]() {
+            CU(cudaEventRecord(ev[0], st));
+            CU(launch_aca_reset(H->d_poolhdr.as<Pool>(), (unsigned long long)H->pool_elems,
+                                H->d_queue.as<AcaQueue>(), H->d_acastats.as<AcaStats>(), st));
+            CU(launch_near_regular(H->geom.g, D.rule, op, k, prec, H->d_near.as<NearBlock>(),
+                                   (int64_t)H->near.size(), H->d_near_data.p, st));
+            CU(cudaEventRecord(ev[3], st));
+            const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
+                                     H->d_sing[2].as<SingPair>()};
+            int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
+                             (int64_t)H->sing[2].size()};
+            CU(launch_singular(H->mesh->geom.g, D.sing, op, k, sp, nullptr, hc, H->d_near_data.p,
+                               st));
+            CU(cudaEventRecord(ev[1], st));
             if (!H->far.empty())
                 CU(launch_aca(H->geom.g, D.rule, op, k, prec, aca_eps, H->d_far.as<FarBlock>(),
                               H->n_big, H->n_small, H->n_tiny, H->max_m_big, H->max_m_small,
-                              H->d_pool.p,
-                              H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(), D.num_sms, st));
+                              H->d_pool.p, H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(),
+                              D.num_sms, st));
             CU(cudaEventRecord(ev[2], st));
-            // ranks -> offsets of the V^T x buffer, and totals, on the device
             CU(launch_aca_finish(H->d_far.as<FarBlock>(), (int64_t)H->far.size(),
                                  H->d_toff.as<int64_t>(), H->d_tiles.as<int64_t>(),
                                  H->d_acastats.as<AcaStats>(), st));
-            CU(cudaMemcpyAsync(&ph, H->d_poolhdr.p, sizeof(ph), cudaMemcpyDeviceToHost, st));
-            CU(cudaMemcpyAsync(&ast, H->d_acastats.p, sizeof(ast), cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(H->pin_pool, H->d_poolhdr.p, sizeof(Pool), cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(H->pin_stats, H->d_acastats.p, sizeof(AcaStats),
+                               cudaMemcpyDeviceToHost, st));
+        };
+        for (int attempt = 0;; ++attempt) {
+            if (H->d_pool.bytes < (size_t)want * esz) H->d_pool.alloc((size_t)want * esz, st);
+            H->pool_elems = want;
+            // the first assembly with a given key runs eagerly; the second
+            // captures the sequence into a graph, later ones replay it
+            const bool same = H->g_op == op && H->g_prec == prec && H->g_k == k &&
+                              H->g_eps == aca_eps && H->g_pool == H->d_pool.p &&
+                              H->g_near == H->d_near_data.p && H->g_pool_elems == H->pool_elems;
+            if (!use_graphs || !same) {
+                if (H->graph) {
+                    cudaGraphExecDestroy(H->graph);
+                    H->graph = nullptr;
+                }
+                enqueue();
+                H->g_op = op;
+                H->g_prec = prec;
+                H->g_k = k;
+                H->g_eps = aca_eps;
+                H->g_pool = H->d_pool.p;
+                H->g_near = H->d_near_data.p;
+                H->g_pool_elems = H->pool_elems;
+            } else {
+                if (!H->graph) {
+                    CU(cudaStreamSynchronize(st));
+                    const int64_t before = launches_total();
+                    cudaGraph_t gr = nullptr;
+                    CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                    try {
+                        enqueue();
+                    } catch (...) {
+                        cudaStreamEndCapture(st, &gr);
+                        if (gr) cudaGraphDestroy(gr);
+                        throw;
+                    }
+                    CU(cudaStreamEndCapture(st, &gr));
+                    cudaError_t ie = cudaGraphInstantiate(&H->graph, gr, 0);
+                    cudaGraphDestroy(gr);
+                    CU(ie);
+                    H->g_nodes = launches_total() - before;
+                    count_launches(-H->g_nodes);  // captured, not launched
+                }
+                CU(cudaGraphLaunch(H->graph, st));
+                count_launches(H->g_nodes);
+            }
             CU(cudaStreamSynchronize(st));
-            if (!ph.overflow) break;
+            if (!H->pin_pool->overflow) break;
             if (attempt >= 6) return fail(BEM_E_OOM, "ACA factor pool keeps overflowing");
             want *= 2;
         }
+        const AcaStats ast = *H->pin_stats;
         float tn = 0, tf = 0, tr = 0;
         CU(cudaEventElapsedTime(&tn, ev[0], ev[1]));
         CU(cudaEventElapsedTime(&tf, ev[1], ev[2]));

@@ -809,13 +809,28 @@ k_rank_scan(const FarBlock *__restrict__ far, int64_t n, const int64_t *__restri
 
 int64_t aca_finish_tiles(int64_t nfar) { return (nfar + kScanTile - 1) / kScanTile + 1; }
 
+namespace {
+__global__ void k_aca_reset(Pool *P, unsigned long long cap, AcaQueue *Q, AcaStats *st)
+{
+    *P = Pool{0ull, cap, 0, 0};
+    *Q = AcaQueue{0u, 0u, 0u, 0u};
+    AcaStats z{};
+    z.rank_min = 0x7fffffff;
+    *st = z;
+}
+}  // namespace
+
+cudaError_t launch_aca_reset(Pool *P, unsigned long long cap, AcaQueue *Q, AcaStats *st,
+                             cudaStream_t s)
+{
+    k_aca_reset<<<1, 1, 0, s>>>(P, cap, Q, st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_aca_finish(const FarBlock *far, int64_t nfar, int64_t *toff,
                               int64_t *tile_sums, AcaStats *st, cudaStream_t s)
 {
-    AcaStats init{};
-    init.rank_min = 0x7fffffff;
-    cudaError_t e = cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
     if (nfar <= 0) return cudaMemsetAsync(toff, 0, sizeof(int64_t), s);
     int64_t tiles = (nfar + kScanTile - 1) / kScanTile;
     k_rank_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(far, nfar, tile_sums, st);
