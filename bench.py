@@ -463,6 +463,91 @@ def run_serving(args):
     return 0
 
 
+LARGE = {
+    "c3": {"mesh": "ellipsoid_nu158", "op": 0, "helmholtz": True, "eps": 1e-4, "matvecs": 1,
+           "workload": "helmholtz_slp_p0_ellipsoid_10x1x1_nu158 (499,280 triangles, "
+                       "k = 2 pi / (10 h), h mean longest edge)"},
+    "c4": {"mesh": "sphere_l9", "op": 0, "helmholtz": False, "eps": 1e-4, "matvecs": 100,
+           "workload": "laplace_slp_p0_icosphere_l9 (5,242,880 triangles), then 100 matvecs"},
+}
+
+
+def run_large(args, spec):
+    """Helmholtz ellipsoid (C3) and level-9 sphere (C4): one step = one mixed
+    assembly (all blocks in one persistent launch) plus the products; sampled
+    exact rows of the matrix (oracle) check the product."""
+    import torch
+    from paper_1711_01897_gb300 import bem, meshes
+    torch.cuda.set_device(0)
+    torch.cuda.init()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    V, T = meshes.workload_mesh(spec["mesh"])
+    n = T.shape[0]
+    k = meshes.helmholtz_k_10_per_wavelength(V, T) if spec["helmholtz"] else 0.0
+    t0 = time.perf_counter()
+    mesh = bem.Mesh(V, T)
+    h = bem.HMatrix(mesh, LEAF, ETA)
+    setup_s = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    xh = rng.normal(size=n) + (1j * rng.normal(size=n) if k else 0)
+    x = torch.from_numpy(xh).to(dev)
+    y = torch.zeros_like(x)
+    clk = Clocks(0)
+    asm_ms, mv_ms, ents = [], [], 0
+    for s in range(args.warmup + args.steps):
+        if s == args.warmup:
+            clk.start()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bem.hmat_assemble(h.handle, spec["op"], k, spec["eps"], bem.MIXED, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        st = h.stats()
+        mvs = []
+        for _ in range(spec["matvecs"]):
+            c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c.record(stream)
+            bem.hmat_matvec(h.handle, x, y, 1, stream.cuda_stream)
+            d.record(stream)
+            d.synchronize()
+            mvs.append(c.elapsed_time(d))
+        if s >= args.warmup:
+            asm_ms.append(a.elapsed_time(b))
+            mv_ms.extend(mvs)
+            ents += st["near_entries"] + st["far_entries"]
+    clocks = clk.stop()
+    # sampled exact rows of A (oracle, FP64) against the product
+    import oracle
+    rows = np.sort(rng.choice(n, 16, replace=False)).astype(np.int32)
+    t1 = time.perf_counter()
+    A = oracle.entries(V, T, 0, k, rows, np.arange(n, dtype=np.int32))
+    ref = A @ xh
+    t_or = time.perf_counter() - t1
+    got = y.cpu().numpy()[rows]
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    tot_ms = float(np.sum(asm_ms))
+    line = {"metric": METRIC, "value": ents / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot_ms / args.steps + float(np.sum(mv_ms)) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "config": {"workload": spec["workload"], "n_triangles": n, "k": k,
+                                           "aca_eps": spec["eps"], "leaf_size": LEAF, "eta": ETA},
+            "h_assembly_ms": float(np.median(asm_ms)), "tree_and_upload_s": setup_s,
+            "integrals_per_assembly": ents / args.steps,
+            "phase_ms": {"near": st["time_near_ms"], "singular": st["time_singular_ms"],
+                         "aca": st["time_far_ms"]},
+            "ranks": [st["rank_min"], st["rank_mean"], st["rank_max"]],
+            "memory_gb": {"near": st["near_bytes"] / 2**30, "factors": st["factor_bytes"] / 2**30},
+            "matvec_ms": {"mean": float(np.mean(mv_ms)), "p50": float(np.percentile(mv_ms, 50)),
+                          "p99": float(np.percentile(mv_ms, 99)), "count": len(mv_ms)},
+            "matvec_gbs": (st["near_bytes"] + st["factor_bytes"]) / (np.median(mv_ms) * 1e-3) / 1e9,
+            "sampled_rows_rel_err": err, "tolerance": 2 * spec["eps"],
+            "oracle_rows_s": t_or, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,7 +557,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "serving"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serving"])
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--slots", type=int, default=6)
     ap.add_argument("--hbm-budget-gb", type=float, default=96.0)
@@ -490,6 +575,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload in LARGE:
+        return run_large(args, LARGE[args.workload])
     return run_gpu(args)
 
 

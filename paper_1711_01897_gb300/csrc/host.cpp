@@ -1084,7 +1084,7 @@ int hmat_upload(bem_hmat H, cudaStream_t st)
 }
 
 // Device bytes an assembly of this H-matrix holds (geometry, tree arrays,
-// dense blocks, factor pool of one 16-column chunk per admissible block, and
+// dense blocks, factor pool of four 8-column chunks per admissible block, and
 // the product buffers), for admission control.
 int64_t hmat_device_bytes(bem_hmat H, bool cplx)
 {
@@ -1096,7 +1096,7 @@ int64_t hmat_device_bytes(bem_hmat H, bool cplx)
                    (int64_t)(H->sing[0].size() + H->sing[1].size() + H->sing[2].size()) * 16 +
                    (int64_t)(H->leaf_items.size() + H->leaf_ptr.size() + H->leaf_rows.size()) * 8 +
                    nt * 4 + (int64_t)H->far.size() * 8 * 2;
-    int64_t pool = (sum_mn * KCHUNK * 2 + 1024) * esz;
+    int64_t pool = (sum_mn * KCHUNK * 4 + 1024) * esz;
     int64_t vecs = 5 * nt * esz;
     return geom + tree + H->near_total * esz + pool + vecs;
 }
@@ -1150,7 +1150,17 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             H->d_near_data.alloc(H->near_total * esz, st);
         int64_t sum_mn = 0;
         for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
-        int64_t want = std::max<int64_t>(H->pool_elems, sum_mn * KCHUNK * 2 + 1024);
+        // factor pool: room for four chunks per admissible block, capped by
+        // what the device has free, never below one chunk per block
+        int64_t want = sum_mn * KCHUNK * 4 + 1024;
+        {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+                int64_t cap = (int64_t)((double)(fr + H->d_pool.bytes) * 0.7) / (int64_t)esz;
+                want = std::min(want, std::max<int64_t>(cap, sum_mn * KCHUNK + 1024));
+            }
+        }
+        want = std::max(want, H->pool_elems);
         // the whole sequence: near field (regular, then singular pairs, FP64),
         // then the persistent ACA over all admissible blocks and its totals
         auto enqueue = [&]() {
