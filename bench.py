@@ -566,7 +566,7 @@ def main():
     ap.add_argument("--level", type=int, default=6,
                     help="icosphere level of the mesh (6 = the workload; smaller for profiling)")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and args.workload == "c2":
         args.warmup = 3
     if args.level != 6:
         WORKLOAD["workload"] = f"laplace_slp_dlp_p0_icosphere_l{args.level}_jitter5pct (profiling size)"

@@ -768,11 +768,13 @@ struct bem_hmat_s {
     void *g_pool = nullptr, *g_near = nullptr;
     int64_t g_nodes = 0, g_pool_elems = -1;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
     Pool *pin_pool = nullptr;       // pinned readback slots
     AcaStats *pin_stats = nullptr;
     ~bem_hmat_s()
     {
         if (graph) cudaGraphExecDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
         if (pin_pool) cudaFreeHost(pin_pool);
@@ -1163,26 +1165,31 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         want = std::max(want, H->pool_elems);
         // the whole sequence: near field (regular, then singular pairs, FP64),
         // then the persistent ACA over all admissible blocks and its totals
-        auto enqueue = [&]() {
-            CU(cudaEventRecord(ev[0], st));
+        // timing events become event-record nodes when the sequence is captured
+        auto enqueue = [&](cudaStream_t st, bool capturing) {
+            auto rec = [&](cudaEvent_t e) {
+                if (capturing) CU(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+                else CU(cudaEventRecord(e, st));
+            };
+            rec(ev[0]);
             CU(launch_aca_reset(H->d_poolhdr.as<Pool>(), (unsigned long long)H->pool_elems,
                                 H->d_queue.as<AcaQueue>(), H->d_acastats.as<AcaStats>(), st));
             CU(launch_near_regular(H->geom.g, D.rule, op, k, prec, H->d_near.as<NearBlock>(),
                                    (int64_t)H->near.size(), H->d_near_data.p, st));
-            CU(cudaEventRecord(ev[3], st));
+            rec(ev[3]);
             const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
                                      H->d_sing[2].as<SingPair>()};
             int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
                              (int64_t)H->sing[2].size()};
             CU(launch_singular(H->mesh->geom.g, D.sing, op, k, sp, nullptr, hc, H->d_near_data.p,
                                st));
-            CU(cudaEventRecord(ev[1], st));
+            rec(ev[1]);
             if (!H->far.empty())
                 CU(launch_aca(H->geom.g, D.rule, op, k, prec, aca_eps, H->d_far.as<FarBlock>(),
                               H->n_big, H->n_small, H->n_tiny, H->max_m_big, H->max_m_small,
                               H->d_pool.p, H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(),
                               D.num_sms, st));
-            CU(cudaEventRecord(ev[2], st));
+            rec(ev[2]);
             CU(launch_aca_finish(H->d_far.as<FarBlock>(), (int64_t)H->far.size(),
                                  H->d_toff.as<int64_t>(), H->d_tiles.as<int64_t>(),
                                  H->d_acastats.as<AcaStats>(), st));
@@ -1203,7 +1210,7 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
                     cudaGraphExecDestroy(H->graph);
                     H->graph = nullptr;
                 }
-                enqueue();
+                enqueue(st, false);
                 H->g_op = op;
                 H->g_prec = prec;
                 H->g_k = k;
@@ -1213,18 +1220,23 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
                 H->g_pool_elems = H->pool_elems;
             } else {
                 if (!H->graph) {
+                    // capture on a private stream (the legacy default stream
+                    // cannot be captured); the graph is launched on st
                     CU(cudaStreamSynchronize(st));
+                    if (!H->cap_stream)
+                        CU(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+                    cudaStream_t cs = H->cap_stream;
                     const int64_t before = launches_total();
                     cudaGraph_t gr = nullptr;
-                    CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                    CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
                     try {
-                        enqueue();
+                        enqueue(cs, true);
                     } catch (...) {
-                        cudaStreamEndCapture(st, &gr);
+                        cudaStreamEndCapture(cs, &gr);
                         if (gr) cudaGraphDestroy(gr);
                         throw;
                     }
-                    CU(cudaStreamEndCapture(st, &gr));
+                    CU(cudaStreamEndCapture(cs, &gr));
                     cudaError_t ie = cudaGraphInstantiate(&H->graph, gr, 0);
                     cudaGraphDestroy(gr);
                     CU(ie);
