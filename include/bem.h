@@ -210,7 +210,7 @@ typedef struct {
     int64_t near_entries;        /* entries of all dense blocks */
     int64_t singular_pairs[3];   /* vertex-, edge-adjacent, identical */
     int64_t far_entries;         /* entries the ACA evaluated (rows + columns) */
-    int64_t factor_bytes;        /* bytes of U, V factors (allocated 8-column chunks) */
+    int64_t factor_bytes;        /* bytes of U, V factors (allocated 4-column chunks) */
     int64_t near_bytes;          /* bytes of the dense blocks */
     int32_t rank_min, rank_max;
     double rank_mean;
@@ -303,7 +303,7 @@ typedef struct {
 /* Creates a server on the current device with `max_slots` worker threads
  * (1..64), each with its own CUDA stream.  A request is admitted, in arrival
  * order, once its device bytes (geometry, tree, dense blocks, factor pool of
- * four 8-column chunks per admissible block, vectors) fit next to the
+ * four 4-column chunks per admissible block, vectors) fit next to the
  * requests already running; one that alone exceeds the budget fails with
  * BEM_E_OOM.  flags: BEM_SERVER_DRY_RUN runs the host logic only (no CUDA
  * call; reserved bytes = 1024 per triangle; y = x after dry_run_ms). */

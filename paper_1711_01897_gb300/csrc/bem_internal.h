@@ -11,7 +11,7 @@ namespace bem {
 
 constexpr int NQ = 6;          // points of the regular triangle rule (degree 4)
 constexpr int NGL = 4;         // Gauss-Legendre points per axis, singular rule
-constexpr int KCHUNK = 8;      // ACA factor columns allocated at a time
+constexpr int KCHUNK = 4;      // ACA factor columns allocated at a time
 constexpr int KMAX = 128;      // rank cap of one admissible block
 constexpr int NCHUNK = KMAX / KCHUNK;
 

@@ -98,7 +98,13 @@ struct DBuf {
         release();
         if (b == 0) b = 16;
         home = st;
-        CU(cudaMallocAsync(&p, b, st));
+        cudaError_t e = cudaMallocAsync(&p, b, st);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            g_err = "device allocation of " + std::to_string(b) + " bytes failed: " +
+                    cudaGetErrorString(e);
+            throw CudaFail{e == cudaErrorMemoryAllocation ? BEM_E_OOM : BEM_E_CUDA};
+        }
         bytes = b;
     }
     template <class T>
@@ -1086,7 +1092,7 @@ int hmat_upload(bem_hmat H, cudaStream_t st)
 }
 
 // Device bytes an assembly of this H-matrix holds (geometry, tree arrays,
-// dense blocks, factor pool of four 8-column chunks per admissible block, and
+// dense blocks, factor pool of four 4-column chunks per admissible block, and
 // the product buffers), for admission control.
 int64_t hmat_device_bytes(bem_hmat H, bool cplx)
 {
@@ -1153,13 +1159,19 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         int64_t sum_mn = 0;
         for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
         // factor pool: room for four chunks per admissible block, capped by
-        // what the device has free, never below one chunk per block
+        // what the device has free (less a margin for the product buffers);
+        // one chunk per block is the least that can work
         int64_t want = sum_mn * KCHUNK * 4 + 1024;
         {
             size_t fr = 0, tot = 0;
             if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-                int64_t cap = (int64_t)((double)(fr + H->d_pool.bytes) * 0.7) / (int64_t)esz;
-                want = std::min(want, std::max<int64_t>(cap, sum_mn * KCHUNK + 1024));
+                const double margin = 4.0 * (1 << 30) + 5.0 * H->mesh->nt * esz;
+                const int64_t avail =
+                    (int64_t)(((double)fr + (double)H->d_pool.bytes - margin) / (double)esz);
+                want = std::min(want, avail);
+                if (want < sum_mn * KCHUNK + 1024)
+                    return fail(BEM_E_OOM, "not enough device memory for one " +
+                                               std::to_string(KCHUNK) + "-column chunk per block");
             }
         }
         want = std::max(want, H->pool_elems);
