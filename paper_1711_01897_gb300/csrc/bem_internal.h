@@ -157,6 +157,12 @@ cudaError_t launch_matvec(bool cplx, int64_t n, const int32_t *perm, const void 
                           const int64_t *toff, const void *pool_data, const NearBlock *near,
                           const void *near_data, const int64_t *leaf_rows,
                           const int64_t *leaf_ptr, const int64_t *leaf_items, int64_t nleaf,
+                          const int64_t *long_ids, int64_t nlong, int64_t *long_off,
                           cudaStream_t st);
+// After an assembly: prefix sum of the ranks of the long-column blocks.
+cudaError_t launch_long_offsets(const FarBlock *far, const int64_t *ids, int64_t nids,
+                                int64_t *loff, cudaStream_t st);
+// column length above which V^T x uses one warp per column
+constexpr int64_t kMatvecLongCol = 1024;
 
 }  // namespace bem

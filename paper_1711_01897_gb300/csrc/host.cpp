@@ -752,7 +752,8 @@ struct bem_hmat_s {
     // leaves (matvec)
     std::vector<int64_t> leaf_rows, leaf_ptr, leaf_items;
     // device
-    DBuf d_perm, d_near, d_far, d_sing[3], d_leaf_rows, d_leaf_ptr, d_leaf_items;
+    DBuf d_perm, d_near, d_far, d_sing[3], d_leaf_rows, d_leaf_ptr, d_leaf_items, d_long, d_long_off;
+    std::vector<int64_t> long_ids;        // admissible blocks with long columns (matvec)
     DBuf d_near_data, d_pool, d_poolhdr, d_queue, d_toff, d_xt, d_yt, d_tbuf, d_x, d_y;
     GeomStore geom;                       // cluster order
     // assembled state
@@ -1031,6 +1032,11 @@ void upload_tree(bem_hmat_s &H, cudaStream_t st)
     H.d_leaf_rows.upload(H.leaf_rows, st);
     H.d_leaf_ptr.upload(H.leaf_ptr, st);
     H.d_leaf_items.upload(H.leaf_items, st);
+    H.long_ids.clear();
+    for (size_t b = 0; b < H.far.size(); ++b)
+        if (H.far[b].se - H.far[b].sb > kMatvecLongCol) H.long_ids.push_back((int64_t)b);
+    H.d_long.upload(H.long_ids, st);
+    H.d_long_off.alloc((H.long_ids.size() + 1) * sizeof(int64_t), st);
     DeviceConsts &D = device_consts();
     H.geom.build(H.mesh->dV.as<double>(), H.mesh->dT.as<int32_t>(), H.d_perm.as<int32_t>(),
                  H.mesh->nt, D.rule, st);
@@ -1205,6 +1211,8 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             CU(launch_aca_finish(H->d_far.as<FarBlock>(), (int64_t)H->far.size(),
                                  H->d_toff.as<int64_t>(), H->d_tiles.as<int64_t>(),
                                  H->d_acastats.as<AcaStats>(), st));
+            CU(launch_long_offsets(H->d_far.as<FarBlock>(), H->d_long.as<int64_t>(),
+                                   (int64_t)H->long_ids.size(), H->d_long_off.as<int64_t>(), st));
             CU(cudaMemcpyAsync(H->pin_pool, H->d_poolhdr.p, sizeof(Pool), cudaMemcpyDeviceToHost, st));
             CU(cudaMemcpyAsync(H->pin_stats, H->d_acastats.p, sizeof(AcaStats),
                                cudaMemcpyDeviceToHost, st));
@@ -1327,7 +1335,8 @@ int hmat_matvec(bem_hmat H, const void *x, void *y, int32_t batch, void *cuda_st
                              H->d_toff.as<int64_t>(), H->d_pool.p, H->d_near.as<NearBlock>(),
                              H->d_near_data.p, H->d_leaf_rows.as<int64_t>(),
                              H->d_leaf_ptr.as<int64_t>(), H->d_leaf_items.as<int64_t>(),
-                             (int64_t)(H->leaf_ptr.size() - 1), st));
+                             (int64_t)(H->leaf_ptr.size() - 1), H->d_long.as<int64_t>(),
+                             (int64_t)H->long_ids.size(), H->d_long_off.as<int64_t>(), st));
             if (hy) CU(cudaMemcpyAsync(yb, dy, vb, cudaMemcpyDeviceToHost, st));
         }
         if (hx || hy) CU(cudaStreamSynchronize(st));

@@ -44,28 +44,112 @@ __device__ __forceinline__ double2 shdown(double2 v, int o)
 __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
-// t_b[l] = sum_j (v_l)_j x~_{sigma_b + j}; one warp per admissible block.
+// t_b[l] = sum_j (v_l)_j x~_{sigma_b + j}.  One lane per (block, column)
+// pair: the lane finds its block by binary search in the rank offsets and sums
+// the column sequentially, so every FP64 instruction of the warp is useful and
+// no reductions are needed.  Columns longer than kMatvecLongCol go to
+// k_far_vtx_long.  A block of rank 0 owns no item (it is skipped by the search).
+
 template <typename T>
 __global__ void k_far_vtx(const FarBlock *__restrict__ far, int64_t nfar,
                           const int64_t *__restrict__ toff, const T *__restrict__ pool,
                           const T *__restrict__ xt, T *__restrict__ tbuf)
 {
+    const int64_t total = toff[nfar];
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nfar - 1;  // last block with toff[b] <= it
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (toff[mid] <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const FarBlock &B = far[lo];
+        const int64_t m = B.te - B.tb, n = B.se - B.sb;
+        if (n > kMatvecLongCol) continue;
+        const int l = (int)(it - toff[lo]);
+        const T *v = pool + B.chunk[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n;
+        const T *x = xt + B.sb;
+        T s = zero_of(T{});
+        for (int64_t j = 0; j < n; ++j) s = madd(v[j], x[j], s);
+        tbuf[it] = s;
+    }
+}
+
+// Long columns: one warp per (block, column) of the blocks with
+// n > kMatvecLongCol; loff is the prefix sum of their ranks (loff[nids] total).
+template <typename T>
+__global__ void k_far_vtx_long(const FarBlock *__restrict__ far, const int64_t *__restrict__ ids,
+                               int64_t nids, const int64_t *__restrict__ loff,
+                               const int64_t *__restrict__ toff, const T *__restrict__ pool,
+                               const T *__restrict__ xt, T *__restrict__ tbuf)
+{
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = warp; b < nfar; b += nw) {
+    const int64_t total = loff[nids];
+    for (int64_t it = warp; it < total; it += nw) {
+        int64_t lo = 0, hi = nids - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (loff[mid] <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t b = ids[lo];
+        const int l = (int)(it - loff[lo]);
         const FarBlock &B = far[b];
         const int64_t m = B.te - B.tb, n = B.se - B.sb;
-        const int rank = B.rank;
-        for (int l = 0; l < rank; ++l) {
-            const T *v = pool + B.chunk[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n;
-            T s = zero_of(T{});
-            for (int64_t j = lane; j < n; j += 32) s = madd(v[j], xt[B.sb + j], s);
+        const T *v = pool + B.chunk[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n;
+        T s = zero_of(T{});
+        for (int64_t j = lane; j < n; j += 32) s = madd(v[j], xt[B.sb + j], s);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s = add(s, shdown(s, o));
-            if (lane == 0) tbuf[toff[b] + l] = s;
-        }
+        for (int o = 16; o > 0; o >>= 1) s = add(s, shdown(s, o));
+        if (lane == 0) tbuf[toff[b] + l] = s;
     }
+}
+
+// Prefix sum of the ranks of the long-column blocks: one CTA, chunks of
+// 1024 with a carried total.
+constexpr int kLongScan = 1024;
+
+__global__ void __launch_bounds__(kLongScan)
+k_long_offsets(const FarBlock *__restrict__ far, const int64_t *__restrict__ ids, int64_t nids,
+               int64_t *__restrict__ loff)
+{
+    __shared__ int64_t wt[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t q0 = 0; q0 < nids; q0 += kLongScan) {
+        const int64_t q = q0 + threadIdx.x;
+        const int64_t v = q < nids ? (int64_t)far[ids[q]].rank : 0;
+        int64_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wt[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int64_t t = wt[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wt[lane] = t;
+        }
+        __syncthreads();
+        const int64_t c = carry;
+        const int64_t ex = c + (w > 0 ? wt[w - 1] : 0) + x - v;
+        if (q < nids) loff[q] = ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + wt[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loff[nids] = carry;
 }
 
 // Rows of one leaf cluster: items >= 0 are admissible blocks, items < 0 are
@@ -110,16 +194,23 @@ cudaError_t matvec_t(int64_t n, const int32_t *perm, const T *x, T *y, T *xt, T 
                      const FarBlock *far, int64_t nfar, const int64_t *toff, const T *pool,
                      const NearBlock *near, const T *near_data, const int64_t *leaf_rows,
                      const int64_t *leaf_ptr, const int64_t *leaf_items, int64_t nleaf,
+                     const int64_t *long_ids, int64_t nlong, int64_t *long_off,
                      cudaStream_t st)
 {
     unsigned g1 = (unsigned)((n + kMvThreads - 1) / kMvThreads);
     k_gather<T><<<g1, kMvThreads, 0, st>>>(n, perm, x, xt);
     count_launches(1);
     if (nfar > 0) {
-        int64_t g = (nfar * 32 + kMvThreads - 1) / kMvThreads;
-        if (g > 65535) g = 65535;
-        k_far_vtx<T><<<(unsigned)g, kMvThreads, 0, st>>>(far, nfar, toff, pool, xt, tbuf);
+        int dev = 0, nsm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        k_far_vtx<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(far, nfar, toff, pool, xt, tbuf);
         count_launches(1);
+        if (nlong > 0) {
+            k_far_vtx_long<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(
+                far, long_ids, nlong, long_off, toff, pool, xt, tbuf);
+            count_launches(1);
+        }
     }
     int64_t g2 = (nleaf * 32 + kMvThreads - 1) / kMvThreads;
     if (g2 > 65535) g2 = 65535;
@@ -136,21 +227,33 @@ cudaError_t matvec_t(int64_t n, const int32_t *perm, const T *x, T *y, T *xt, T 
 
 }  // namespace
 
+cudaError_t launch_long_offsets(const FarBlock *far, const int64_t *ids, int64_t nids,
+                                int64_t *loff, cudaStream_t st)
+{
+    if (nids <= 0) return cudaSuccess;
+    k_long_offsets<<<1, kLongScan, 0, st>>>(far, ids, nids, loff);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_matvec(bool cplx, int64_t n, const int32_t *perm, const void *x, void *y,
                           void *xt, void *yt, void *tbuf, const FarBlock *far, int64_t nfar,
                           const int64_t *toff, const void *pool_data, const NearBlock *near,
                           const void *near_data, const int64_t *leaf_rows,
                           const int64_t *leaf_ptr, const int64_t *leaf_items, int64_t nleaf,
+                          const int64_t *long_ids, int64_t nlong, int64_t *long_off,
                           cudaStream_t st)
 {
     if (cplx)
         return matvec_t<double2>(n, perm, (const double2 *)x, (double2 *)y, (double2 *)xt,
                                  (double2 *)yt, (double2 *)tbuf, far, nfar, toff,
                                  (const double2 *)pool_data, near, (const double2 *)near_data,
-                                 leaf_rows, leaf_ptr, leaf_items, nleaf, st);
+                                 leaf_rows, leaf_ptr, leaf_items, nleaf, long_ids, nlong,
+                                 long_off, st);
     return matvec_t<double>(n, perm, (const double *)x, (double *)y, (double *)xt, (double *)yt,
                             (double *)tbuf, far, nfar, toff, (const double *)pool_data, near,
-                            (const double *)near_data, leaf_rows, leaf_ptr, leaf_items, nleaf, st);
+                            (const double *)near_data, leaf_rows, leaf_ptr, leaf_items, nleaf,
+                            long_ids, nlong, long_off, st);
 }
 
 }  // namespace bem
