@@ -64,10 +64,16 @@ struct SingPair {
 
 struct FarBlock {
     int64_t tb, te, sb, se;         // cluster-order ranges (rows: tau)
-    int64_t chunk[NCHUNK];          // element offsets of factor chunks
     int32_t rank;
     int32_t status;                 // 0 ok, 1 rank cap, 2 pool overflow
     int64_t entries;                // entries evaluated by ACA
+};
+
+// Element offsets of a block's factor chunks (-1: not allocated), written by
+// the ACA; an array parallel to the FarBlock list, kept apart so that the
+// host-built block descriptors stay small.
+struct FarChunks {
+    int64_t c[NCHUNK];
 };
 
 struct NearBlock {
@@ -139,8 +145,8 @@ cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, 
                                 cudaStream_t st);
 
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
-                       double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,
-                       int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
+                       double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
+                       int64_t n_small, int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
                        Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st);
 
 // After an ACA launch: toff[b] = sum of ranks of blocks < b (toff[n] = total)
@@ -149,11 +155,13 @@ int64_t aca_finish_tiles(int64_t nfar);
 // Zeroes the pool header (capacity cap), the work queues and the totals.
 cudaError_t launch_aca_reset(Pool *P, unsigned long long cap, AcaQueue *Q, AcaStats *st,
                              cudaStream_t s);
-cudaError_t launch_aca_finish(const FarBlock *far, int64_t nfar, int64_t *toff,
+cudaError_t launch_aca_finish(const FarBlock *far, const FarChunks *chunks, int64_t nfar,
+                              int64_t *toff,
                               int64_t *tile_sums, AcaStats *st, cudaStream_t st_);
 
 cudaError_t launch_matvec(bool cplx, int64_t n, const int32_t *perm, const void *x, void *y,
-                          void *xt, void *yt, void *tbuf, const FarBlock *far, int64_t nfar,
+                          void *xt, void *yt, void *tbuf, const FarBlock *far,
+                          const FarChunks *chunks, int64_t nfar,
                           const int64_t *toff, const void *pool_data, const NearBlock *near,
                           const void *near_data, const int64_t *leaf_rows,
                           const int64_t *leaf_ptr, const int64_t *leaf_items, int64_t nleaf,

@@ -752,7 +752,7 @@ struct bem_hmat_s {
     // leaves (matvec)
     std::vector<int64_t> leaf_rows, leaf_ptr, leaf_items;
     // device
-    DBuf d_perm, d_near, d_far, d_sing[3], d_leaf_rows, d_leaf_ptr, d_leaf_items, d_long, d_long_off;
+    DBuf d_perm, d_near, d_far, d_chunks, d_sing[3], d_leaf_rows, d_leaf_ptr, d_leaf_items, d_long, d_long_off;
     std::vector<int64_t> long_ids;        // admissible blocks with long columns (matvec)
     DBuf d_near_data, d_pool, d_poolhdr, d_queue, d_toff, d_xt, d_yt, d_tbuf, d_x, d_y;
     GeomStore geom;                       // cluster order
@@ -890,134 +890,130 @@ void build_blocks(bem_hmat_s &H)
     }
 }
 
+// Block lists.  Near-field blocks keep tree order and get consecutive dense
+// storage.  Admissible blocks are split into three classes by their longer
+// side (CTA, warp, lane ACA), each in longest-processing-time-first order
+// (m + n descending, tree order on ties); the order comes from one sort of
+// packed 64-bit keys so that each FarBlock is written once.
 void build_lists(bem_hmat_s &H)
 {
     const bem_mesh_s &M = *H.mesh;
+    const int64_t nb = (int64_t)H.blocks.size(), nt = M.nt;
+    if (nb >= (int64_t(1) << 32) || nt >= (int64_t(1) << 29))
+        throw std::runtime_error("problem too large for the block-list keys");
+    constexpr uint64_t kSizeMask = (uint64_t(1) << 30) - 1;
+    int64_t nnear = 0;
+    for (const BlockH &B : H.blocks) nnear += !B.adm;
     H.near.clear();
+    H.near.reserve(nnear);
     H.near_block_id.clear();
-    std::vector<FarBlock> big, small, tiny;
-    std::vector<int64_t> big_id, small_id, tiny_id;
-    int64_t off = 0;
-    const int64_t smax = H.small_max;
-    for (size_t b = 0; b < H.blocks.size(); ++b) {
+    H.near_block_id.reserve(nnear);
+    std::vector<uint64_t> key;
+    key.reserve(nb - nnear);
+    int64_t off = 0, ncls[3] = {0, 0, 0};
+    for (int64_t b = 0; b < nb; ++b) {
         const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
+        const int64_t m = T.e - T.b, n = S.e - S.b;
         if (!H.blocks[b].adm) {
             H.near.push_back({T.b, T.e, S.b, S.e, off});
-            H.near_block_id.push_back((int64_t)b);
-            off += (T.e - T.b) * (S.e - S.b);
+            H.near_block_id.push_back(b);
+            off += m * n;
         } else {
-            FarBlock F{};
-            F.tb = T.b;
-            F.te = T.e;
-            F.sb = S.b;
-            F.se = S.e;
-            for (int c = 0; c < NCHUNK; ++c) F.chunk[c] = -1;
-            const int64_t mx = std::max(T.e - T.b, S.e - S.b);
-            if (mx > smax) {
-                big.push_back(F);
-                big_id.push_back((int64_t)b);
-            } else if (mx > H.tiny_max) {
-                small.push_back(F);
-                small_id.push_back((int64_t)b);
-            } else {
-                tiny.push_back(F);
-                tiny_id.push_back((int64_t)b);
-            }
+            const int64_t mx = std::max(m, n);
+            const uint64_t cls = mx > H.small_max ? 0 : mx > H.tiny_max ? 1 : 2;
+            ++ncls[cls];
+            key.push_back(cls << 62 | (kSizeMask - (uint64_t)(m + n)) << 32 | (uint64_t)b);
         }
     }
     H.near_total = off;
-    // longest processing time first: by size, then tree order
-    auto order = [](std::vector<FarBlock> &v, std::vector<int64_t> &id) {
-        std::vector<size_t> ix(v.size());
-        std::iota(ix.begin(), ix.end(), 0);
-        std::stable_sort(ix.begin(), ix.end(), [&](size_t a, size_t b) {
-            int64_t sa = (v[a].te - v[a].tb) + (v[a].se - v[a].sb);
-            int64_t sb = (v[b].te - v[b].tb) + (v[b].se - v[b].sb);
-            return sa > sb;
-        });
-        std::vector<FarBlock> v2(v.size());
-        std::vector<int64_t> id2(v.size());
-        for (size_t i = 0; i < ix.size(); ++i) {
-            v2[i] = v[ix[i]];
-            id2[i] = id[ix[i]];
-        }
-        v.swap(v2);
-        id.swap(id2);
-    };
-    order(big, big_id);
-    order(small, small_id);
-    order(tiny, tiny_id);
-    H.n_big = (int64_t)big.size();
-    H.n_small = (int64_t)small.size();
-    H.n_tiny = (int64_t)tiny.size();
-    H.max_m_big = 0;
-    for (auto &F : big) H.max_m_big = std::max(H.max_m_big, F.te - F.tb);
-    H.max_m_small = 0;
-    for (auto &F : small) H.max_m_small = std::max(H.max_m_small, F.te - F.tb);
-    H.far = big;
-    H.far.insert(H.far.end(), small.begin(), small.end());
-    H.far.insert(H.far.end(), tiny.begin(), tiny.end());
-    H.far_block_id = big_id;
-    H.far_block_id.insert(H.far_block_id.end(), small_id.begin(), small_id.end());
-    H.far_block_id.insert(H.far_block_id.end(), tiny_id.begin(), tiny_id.end());
-
-    // leaves and, per leaf, the blocks whose row range contains it
-    const int64_t nt = M.nt;
-    std::vector<int64_t> leaf_of(nt, -1);
-    H.leaf_rows.clear();
-    int64_t nleaf = 0;
-    for (const Cluster &C : H.cl)
-        if (C.left < 0) {
-            H.leaf_rows.push_back(C.b);
-            H.leaf_rows.push_back(C.e);
-            ++nleaf;
-        }
-    // sort leaves by row start
-    {
-        std::vector<std::pair<int64_t, int64_t>> lr(nleaf);
-        for (int64_t l = 0; l < nleaf; ++l) lr[l] = {H.leaf_rows[2 * l], H.leaf_rows[2 * l + 1]};
-        std::sort(lr.begin(), lr.end());
-        for (int64_t l = 0; l < nleaf; ++l) {
-            H.leaf_rows[2 * l] = lr[l].first;
-            H.leaf_rows[2 * l + 1] = lr[l].second;
-            for (int64_t p = lr[l].first; p < lr[l].second; ++p) leaf_of[p] = l;
-        }
+    std::sort(key.begin(), key.end());
+    H.far.resize(key.size());
+    H.far_block_id.resize(key.size());
+    H.max_m_big = H.max_m_small = 0;
+    for (size_t f = 0; f < key.size(); ++f) {
+        const int64_t b = (int64_t)(key[f] & 0xffffffffu);
+        const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
+        FarBlock &F = H.far[f];
+        std::memset(&F, 0, sizeof(F));
+        F.tb = T.b;
+        F.te = T.e;
+        F.sb = S.b;
+        F.se = S.e;
+        H.far_block_id[f] = b;
+        if ((int64_t)f < ncls[0]) H.max_m_big = std::max(H.max_m_big, T.e - T.b);
+        else if ((int64_t)f < ncls[0] + ncls[1]) H.max_m_small = std::max(H.max_m_small, T.e - T.b);
     }
-    std::vector<std::vector<int64_t>> per_leaf(nleaf);
+    H.n_big = ncls[0];
+    H.n_small = ncls[1];
+    H.n_tiny = ncls[2];
+
+    // leaves sorted by row start, and the leaf of every cluster-order row
+    std::vector<std::pair<int64_t, int64_t>> lr;
+    for (const Cluster &C : H.cl)
+        if (C.left < 0) lr.push_back({C.b, C.e});
+    std::sort(lr.begin(), lr.end());
+    const int64_t nleaf = (int64_t)lr.size();
+    std::vector<int64_t> leaf_of(nt, -1);
+    H.leaf_rows.resize(2 * nleaf);
+    for (int64_t l = 0; l < nleaf; ++l) {
+        H.leaf_rows[2 * l] = lr[l].first;
+        H.leaf_rows[2 * l + 1] = lr[l].second;
+        for (int64_t p = lr[l].first; p < lr[l].second; ++p) leaf_of[p] = l;
+    }
+    // per leaf, the blocks whose row range contains it: far blocks in list
+    // order as f, then near blocks in tree order as -1 - q (CSR, two passes)
+    H.leaf_ptr.assign(nleaf + 1, 0);
+    for (const FarBlock &F : H.far)
+        for (int64_t l = leaf_of[F.tb]; l <= leaf_of[F.te - 1]; ++l) ++H.leaf_ptr[l + 1];
+    for (const NearBlock &N : H.near)
+        for (int64_t l = leaf_of[N.tb]; l <= leaf_of[N.te - 1]; ++l) ++H.leaf_ptr[l + 1];
+    for (int64_t l = 0; l < nleaf; ++l) H.leaf_ptr[l + 1] += H.leaf_ptr[l];
+    H.leaf_items.resize(H.leaf_ptr[nleaf]);
+    std::vector<int64_t> pos(H.leaf_ptr.begin(), H.leaf_ptr.end() - 1);
     for (size_t f = 0; f < H.far.size(); ++f)
         for (int64_t l = leaf_of[H.far[f].tb]; l <= leaf_of[H.far[f].te - 1]; ++l)
-            per_leaf[l].push_back((int64_t)f);
+            H.leaf_items[pos[l]++] = (int64_t)f;
+    // near blocks per row leaf, by column start (the columns of one leaf's
+    // blocks are disjoint, so the starts are distinct)
+    std::vector<int64_t> nptr(nleaf + 1, 0);
+    for (size_t q = 0; q < H.near.size(); ++q)
+        for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l) {
+            H.leaf_items[pos[l]++] = -1 - (int64_t)q;
+            ++nptr[l + 1];
+        }
+    for (int64_t l = 0; l < nleaf; ++l) nptr[l + 1] += nptr[l];
+    std::vector<int64_t> nq(nptr[nleaf]);
+    std::copy(nptr.begin(), nptr.end() - 1, pos.begin());
     for (size_t q = 0; q < H.near.size(); ++q)
         for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l)
-            per_leaf[l].push_back(-1 - (int64_t)q);
-    H.leaf_ptr.assign(nleaf + 1, 0);
-    H.leaf_items.clear();
+            nq[pos[l]++] = (int64_t)q;
+    std::vector<int64_t> nsb(nq.size());
     for (int64_t l = 0; l < nleaf; ++l) {
-        H.leaf_items.insert(H.leaf_items.end(), per_leaf[l].begin(), per_leaf[l].end());
-        H.leaf_ptr[l + 1] = (int64_t)H.leaf_items.size();
+        std::sort(nq.begin() + nptr[l], nq.begin() + nptr[l + 1],
+                  [&](int64_t a, int64_t b) { return H.near[a].sb < H.near[b].sb; });
+        for (int64_t i = nptr[l]; i < nptr[l + 1]; ++i) nsb[i] = H.near[nq[i]].sb;
     }
 
     // singular pairs of the near field, with their place in the dense blocks
-    std::vector<std::vector<int64_t>> near_of_leaf(nleaf);  // near blocks by row leaf
-    for (size_t q = 0; q < H.near.size(); ++q)
-        for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l)
-            near_of_leaf[l].push_back((int64_t)q);
-    for (auto &v : near_of_leaf)
-        std::sort(v.begin(), v.end(), [&](int64_t a, int64_t b) { return H.near[a].sb < H.near[b].sb; });
-    for (int c = 0; c < 3; ++c) H.sing[c].clear();
+    int64_t ncase[3] = {0, 0, 0};
+    for (int8_t c : M.adj_case) ++ncase[c - 1];
+    for (int c = 0; c < 3; ++c) {
+        H.sing[c].clear();
+        H.sing[c].reserve(ncase[c]);
+    }
     for (int64_t p = 0; p < nt; ++p) {
         const int32_t t = H.perm[p];
-        const auto &lst = near_of_leaf[leaf_of[p]];
+        const int64_t l = leaf_of[p];
+        const int64_t *b0 = nsb.data() + nptr[l], *b1 = nsb.data() + nptr[l + 1];
         for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) {
             const int32_t u = M.adj_tri[a];
             const int64_t q = H.iperm[u];
             // near block of this row leaf whose column range holds q
-            auto it = std::upper_bound(lst.begin(), lst.end(), q,
-                                       [&](int64_t val, int64_t nb) { return val < H.near[nb].sb; });
-            if (it == lst.begin()) throw std::runtime_error("touching pair outside the near field");
-            const NearBlock &N = H.near[*(it - 1)];
+            const int64_t *it = std::upper_bound(b0, b1, q);
+            if (it == b0) throw std::runtime_error("touching pair outside the near field");
+            const NearBlock &N = H.near[nq[nptr[l] + (it - 1 - b0)]];
             if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
-            int64_t dest = N.off + (p - N.tb) * (N.se - N.sb) + (q - N.sb);
+            const int64_t dest = N.off + (p - N.tb) * (N.se - N.sb) + (q - N.sb);
             H.sing[M.adj_case[a] - 1].push_back({t, u, dest});
         }
     }
@@ -1028,6 +1024,7 @@ void upload_tree(bem_hmat_s &H, cudaStream_t st)
     H.d_perm.upload(H.perm, st);
     H.d_near.upload(H.near, st);
     H.d_far.upload(H.far, st);
+    H.d_chunks.alloc(H.far.size() * sizeof(FarChunks), st);
     for (int c = 0; c < 3; ++c) H.d_sing[c].upload(H.sing[c], st);
     H.d_leaf_rows.upload(H.leaf_rows, st);
     H.d_leaf_ptr.upload(H.leaf_ptr, st);
@@ -1106,7 +1103,8 @@ int64_t hmat_device_bytes(bem_hmat H, bool cplx)
     int64_t sum_mn = 0;
     for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
     int64_t geom = 2 * nt * (12 + 72 + 24 + 8 + 144 + 24 + 72 + 12 + 8 + 128);  // mesh + cluster order
-    int64_t tree = (int64_t)(H->near.size() * sizeof(NearBlock) + H->far.size() * sizeof(FarBlock)) +
+    int64_t tree = (int64_t)(H->near.size() * sizeof(NearBlock) +
+                             H->far.size() * (sizeof(FarBlock) + sizeof(FarChunks))) +
                    (int64_t)(H->sing[0].size() + H->sing[1].size() + H->sing[2].size()) * 16 +
                    (int64_t)(H->leaf_items.size() + H->leaf_ptr.size() + H->leaf_rows.size()) * 8 +
                    nt * 4 + (int64_t)H->far.size() * 8 * 2;
@@ -1204,11 +1202,12 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             rec(ev[1]);
             if (!H->far.empty())
                 CU(launch_aca(H->geom.g, D.rule, op, k, prec, aca_eps, H->d_far.as<FarBlock>(),
-                              H->n_big, H->n_small, H->n_tiny, H->max_m_big, H->max_m_small,
+                              H->d_chunks.as<FarChunks>(), H->n_big, H->n_small, H->n_tiny, H->max_m_big, H->max_m_small,
                               H->d_pool.p, H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(),
                               D.num_sms, st));
             rec(ev[2]);
-            CU(launch_aca_finish(H->d_far.as<FarBlock>(), (int64_t)H->far.size(),
+            CU(launch_aca_finish(H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
+                                 (int64_t)H->far.size(),
                                  H->d_toff.as<int64_t>(), H->d_tiles.as<int64_t>(),
                                  H->d_acastats.as<AcaStats>(), st));
             CU(launch_long_offsets(H->d_far.as<FarBlock>(), H->d_long.as<int64_t>(),
@@ -1331,7 +1330,8 @@ int hmat_matvec(bem_hmat H, const void *x, void *y, int32_t batch, void *cuda_st
             }
             if (hy) dy = H->d_y.p;
             CU(launch_matvec(H->cplx, nt, H->d_perm.as<int32_t>(), dx, dy, H->d_xt.p, H->d_yt.p,
-                             H->d_tbuf.p, H->d_far.as<FarBlock>(), (int64_t)H->far.size(),
+                             H->d_tbuf.p, H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
+                             (int64_t)H->far.size(),
                              H->d_toff.as<int64_t>(), H->d_pool.p, H->d_near.as<NearBlock>(),
                              H->d_near_data.p, H->d_leaf_rows.as<int64_t>(),
                              H->d_leaf_ptr.as<int64_t>(), H->d_leaf_items.as<int64_t>(),
@@ -1422,14 +1422,17 @@ int hmat_block_dense(bem_hmat H, int64_t block, void *out, int32_t *rank)
             H->far_result_valid = true;
         }
         auto it = std::find(H->far_block_id.begin(), H->far_block_id.end(), block);
-        const FarBlock &F = H->far_result[it - H->far_block_id.begin()];
+        const int64_t f = it - H->far_block_id.begin();
+        const FarBlock &F = H->far_result[f];
+        FarChunks C;
+        CU(cudaMemcpy(&C, H->d_chunks.as<FarChunks>() + f, sizeof(FarChunks), cudaMemcpyDeviceToHost));
         const int64_t m = F.te - F.tb, n = F.se - F.sb;
         const int r = F.rank;
         if (rank) *rank = r;
         const int cpl = H->cplx ? 2 : 1;
         std::vector<double> U((size_t)m * r * cpl), V((size_t)n * r * cpl);
         for (int l = 0; l < r; ++l) {
-            const int64_t base = F.chunk[l / KCHUNK];
+            const int64_t base = C.c[l / KCHUNK];
             CU(cudaMemcpy(&U[(size_t)l * m * cpl], H->d_pool.as<char>() + (base + (l % KCHUNK) * m) * esz,
                           m * esz, cudaMemcpyDeviceToHost));
             CU(cudaMemcpy(&V[(size_t)l * n * cpl],

@@ -276,7 +276,7 @@ struct GroupSmem {
 
 template <class Grp, int OP, bool CPLX, int PREC>
 __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, double k, double eps,
-                          FarBlock *blk, typename VT<CPLX>::T *pool, Pool *P,
+                          FarBlock *blk, FarChunks *chk, typename VT<CPLX>::T *pool, Pool *P,
                           GroupSmem<CPLX> &S, unsigned *Z, typename VT<CPLX>::T *part)
 {
     using V = VT<CPLX>;
@@ -492,7 +492,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         blk->rank = kk;
         blk->status = status;
         blk->entries = entries;
-        for (int c = 0; c < NCHUNK; ++c) blk->chunk[c] = S.chunk[c];
+        for (int c = 0; c < NCHUNK; ++c) chk->c[c] = S.chunk[c];
     }
     G.sync();
 }
@@ -505,7 +505,7 @@ constexpr int kTinyMax = 64;
 
 template <int OP, bool CPLX, int PREC>
 __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double eps,
-                         FarBlock *blk, typename VT<CPLX>::T *pool, Pool *P)
+                         FarBlock *blk, FarChunks *chk, typename VT<CPLX>::T *pool, Pool *P)
 {
     using V = VT<CPLX>;
     using T = typename V::T;
@@ -618,12 +618,13 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
     blk->status = status;
     blk->entries = entries;
 #pragma unroll
-    for (int c = 0; c < NCHUNK; ++c) blk->chunk[c] = chunk[c];
+    for (int c = 0; c < NCHUNK; ++c) chk->c[c] = chunk[c];
 }
 
 template <int OP, bool CPLX, int PREC>
 __global__ void __launch_bounds__(kAcaThreads, 2)
-k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_big,
+k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, FarChunks *chunks,
+      int64_t n_big,
       int64_t n_small, int64_t n_tiny, int zwords_small, typename VT<CPLX>::T *pool, Pool *P,
       AcaQueue *Q)
 {
@@ -643,7 +644,8 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_b
         int64_t b = s_b;
         __syncthreads();
         if (b >= n_big) break;
-        aca_block<CtaGroup, OP, CPLX, PREC>(cg, g, R, k, eps, blocks + b, pool, P, gs[0], zbig, part);
+        aca_block<CtaGroup, OP, CPLX, PREC>(cg, g, R, k, eps, blocks + b, chunks + b, pool, P, gs[0],
+                                            zbig, part);
     }
     // phase 2: small blocks, one warp each
     const int w = threadIdx.x >> 5;
@@ -653,26 +655,29 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, int64_t n_b
         if (wg.lane == 0) b = (int64_t)atomicAdd(&Q->next_small, 1u);
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= n_small) break;
-        aca_block<WarpGroup, OP, CPLX, PREC>(wg, g, R, k, eps, blocks + n_big + b, pool, P, gs[w],
+        aca_block<WarpGroup, OP, CPLX, PREC>(wg, g, R, k, eps, blocks + n_big + b,
+                                             chunks + n_big + b, pool, P, gs[w],
                                              zbig + (int64_t)w * zwords_small, part + 64 * w);
     }
     // phase 3: tiny blocks, 32 per warp, one per lane
     FarBlock *tiny = blocks + n_big + n_small;
+    FarChunks *tiny_chk = chunks + n_big + n_small;
     for (;;) {
         int64_t b0 = 0;
         if (wg.lane == 0) b0 = (int64_t)atomicAdd(&Q->next_tiny, 32u);
         b0 = __shfl_sync(0xffffffffu, b0, 0);
         if (b0 >= n_tiny) break;
         const int64_t b = b0 + wg.lane;
-        if (b < n_tiny) aca_lane<OP, CPLX, PREC>(g, R, k, eps, tiny + b, pool, P);
+        if (b < n_tiny) aca_lane<OP, CPLX, PREC>(g, R, k, eps, tiny + b, tiny_chk + b, pool, P);
         __syncwarp();
     }
 }
 
 template <int OP, bool CPLX, int PREC>
 cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps,
-                       FarBlock *blocks, int64_t n_big, int64_t n_small, int64_t n_tiny,
-                       int64_t max_m_big, int64_t max_m_small, void *pool, Pool *P, AcaQueue *Q,
+                       FarBlock *blocks, FarChunks *chunks, int64_t n_big, int64_t n_small,
+                       int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool,
+                       Pool *P, AcaQueue *Q,
                        int num_sms, cudaStream_t st)
 {
     const int64_t zw_big = (max_m_big + 31) / 32, zw_small = (max_m_small + 31) / 32;
@@ -688,7 +693,7 @@ cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
     kern<<<(unsigned)grid, kAcaThreads, dyn, st>>>(
-        g, R, k, eps, blocks, n_big, n_small, n_tiny, (int)zw_small,
+        g, R, k, eps, blocks, chunks, n_big, n_small, n_tiny, (int)zw_small,
         reinterpret_cast<typename VT<CPLX>::T *>(pool), P, Q);
     count_launches(1);
     return cudaGetLastError();
@@ -731,7 +736,8 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *warp
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_rank_tiles(const FarBlock *__restrict__ far, int64_t n, int64_t *tile_sums, AcaStats *st)
+k_rank_tiles(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks, int64_t n,
+             int64_t *tile_sums, AcaStats *st)
 {
     __shared__ int64_t wt[32];
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
@@ -749,7 +755,7 @@ k_rank_tiles(const FarBlock *__restrict__ far, int64_t n, int64_t *tile_sums, Ac
             capped += F.status == 1;
             failed += F.status == 2;
             for (int c = 0; c < NCHUNK; ++c)
-                if (F.chunk[c] >= 0) fe += ((F.te - F.tb) + (F.se - F.sb)) * KCHUNK;
+                if (chunks[b].c[c] >= 0) fe += ((F.te - F.tb) + (F.se - F.sb)) * KCHUNK;
         }
     }
     int64_t tot = 0;
@@ -828,12 +834,13 @@ cudaError_t launch_aca_reset(Pool *P, unsigned long long cap, AcaQueue *Q, AcaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_aca_finish(const FarBlock *far, int64_t nfar, int64_t *toff,
+cudaError_t launch_aca_finish(const FarBlock *far, const FarChunks *chunks, int64_t nfar,
+                              int64_t *toff,
                               int64_t *tile_sums, AcaStats *st, cudaStream_t s)
 {
     if (nfar <= 0) return cudaMemsetAsync(toff, 0, sizeof(int64_t), s);
     int64_t tiles = (nfar + kScanTile - 1) / kScanTile;
-    k_rank_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(far, nfar, tile_sums, st);
+    k_rank_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(far, chunks, nfar, tile_sums, st);
     count_launches(1);
     k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tile_sums, tiles);
     count_launches(1);
@@ -843,14 +850,14 @@ cudaError_t launch_aca_finish(const FarBlock *far, int64_t nfar, int64_t *toff,
 }
 
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
-                       double eps, FarBlock *blocks, int64_t n_big, int64_t n_small,
-                       int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
+                       double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
+                       int64_t n_small, int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
                        Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st)
 {
     const bool cplx = k != 0.0;
 #define BEM_ACA(O, C, Pp)                                                                     \
     if (op == O && cplx == C && prec == Pp)                                                   \
-        return aca_launch<O, C, Pp>(g, rule, k, eps, blocks, n_big, n_small, n_tiny,          \
+        return aca_launch<O, C, Pp>(g, rule, k, eps, blocks, chunks, n_big, n_small, n_tiny,          \
                                     max_m_big, max_m_small, pool_data, pool, queue, num_sms, st);
     BEM_ACA(0, false, 0) BEM_ACA(0, false, 1) BEM_ACA(0, true, 0) BEM_ACA(0, true, 1)
     BEM_ACA(1, false, 0) BEM_ACA(1, false, 1) BEM_ACA(1, true, 0) BEM_ACA(1, true, 1)

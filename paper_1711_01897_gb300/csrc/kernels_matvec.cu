@@ -51,7 +51,8 @@ __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_doubl
 // k_far_vtx_long.  A block of rank 0 owns no item (it is skipped by the search).
 
 template <typename T>
-__global__ void k_far_vtx(const FarBlock *__restrict__ far, int64_t nfar,
+__global__ void k_far_vtx(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks,
+                          int64_t nfar,
                           const int64_t *__restrict__ toff, const T *__restrict__ pool,
                           const T *__restrict__ xt, T *__restrict__ tbuf)
 {
@@ -68,7 +69,7 @@ __global__ void k_far_vtx(const FarBlock *__restrict__ far, int64_t nfar,
         const int64_t m = B.te - B.tb, n = B.se - B.sb;
         if (n > kMatvecLongCol) continue;
         const int l = (int)(it - toff[lo]);
-        const T *v = pool + B.chunk[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n;
+        const T *v = pool + chunks[lo].c[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n;
         const T *x = xt + B.sb;
         T s = zero_of(T{});
         for (int64_t j = 0; j < n; ++j) s = madd(v[j], x[j], s);
@@ -79,7 +80,8 @@ __global__ void k_far_vtx(const FarBlock *__restrict__ far, int64_t nfar,
 // Long columns: one warp per (block, column) of the blocks with
 // n > kMatvecLongCol; loff is the prefix sum of their ranks (loff[nids] total).
 template <typename T>
-__global__ void k_far_vtx_long(const FarBlock *__restrict__ far, const int64_t *__restrict__ ids,
+__global__ void k_far_vtx_long(const FarBlock *__restrict__ far,
+                               const FarChunks *__restrict__ chunks, const int64_t *__restrict__ ids,
                                int64_t nids, const int64_t *__restrict__ loff,
                                const int64_t *__restrict__ toff, const T *__restrict__ pool,
                                const T *__restrict__ xt, T *__restrict__ tbuf)
@@ -99,7 +101,7 @@ __global__ void k_far_vtx_long(const FarBlock *__restrict__ far, const int64_t *
         const int l = (int)(it - loff[lo]);
         const FarBlock &B = far[b];
         const int64_t m = B.te - B.tb, n = B.se - B.sb;
-        const T *v = pool + B.chunk[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n;
+        const T *v = pool + chunks[b].c[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n;
         T s = zero_of(T{});
         for (int64_t j = lane; j < n; j += 32) s = madd(v[j], xt[B.sb + j], s);
 #pragma unroll
@@ -157,7 +159,8 @@ k_long_offsets(const FarBlock *__restrict__ far, const int64_t *__restrict__ ids
 template <typename T>
 __global__ void k_leaf_rows(const int64_t *__restrict__ leaf_rows, const int64_t *__restrict__ ptr,
                             const int64_t *__restrict__ items, int64_t nleaf,
-                            const FarBlock *__restrict__ far, const int64_t *__restrict__ toff,
+                            const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks,
+                            const int64_t *__restrict__ toff,
                             const T *__restrict__ pool, const T *__restrict__ tbuf,
                             const NearBlock *__restrict__ near, const T *__restrict__ near_data,
                             const T *__restrict__ xt, T *__restrict__ yt)
@@ -175,8 +178,9 @@ __global__ void k_leaf_rows(const int64_t *__restrict__ leaf_rows, const int64_t
                     const FarBlock &B = far[id];
                     const int64_t m = B.te - B.tb, rr = r - B.tb;
                     const T *t = tbuf + toff[id];
+                    const int64_t *ch = chunks[id].c;
                     for (int l = 0; l < B.rank; ++l)
-                        acc = madd(pool[B.chunk[l / KCHUNK] + (int64_t)(l % KCHUNK) * m + rr], t[l], acc);
+                        acc = madd(pool[ch[l / KCHUNK] + (int64_t)(l % KCHUNK) * m + rr], t[l], acc);
                 } else {
                     const NearBlock &N = near[-1 - id];
                     const int64_t nc = N.se - N.sb, rr = r - N.tb;
@@ -191,7 +195,8 @@ __global__ void k_leaf_rows(const int64_t *__restrict__ leaf_rows, const int64_t
 
 template <typename T>
 cudaError_t matvec_t(int64_t n, const int32_t *perm, const T *x, T *y, T *xt, T *yt, T *tbuf,
-                     const FarBlock *far, int64_t nfar, const int64_t *toff, const T *pool,
+                     const FarBlock *far, const FarChunks *chunks, int64_t nfar,
+                     const int64_t *toff, const T *pool,
                      const NearBlock *near, const T *near_data, const int64_t *leaf_rows,
                      const int64_t *leaf_ptr, const int64_t *leaf_items, int64_t nleaf,
                      const int64_t *long_ids, int64_t nlong, int64_t *long_off,
@@ -204,11 +209,11 @@ cudaError_t matvec_t(int64_t n, const int32_t *perm, const T *x, T *y, T *xt, T 
         int dev = 0, nsm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        k_far_vtx<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(far, nfar, toff, pool, xt, tbuf);
+        k_far_vtx<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(far, chunks, nfar, toff, pool, xt, tbuf);
         count_launches(1);
         if (nlong > 0) {
             k_far_vtx_long<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(
-                far, long_ids, nlong, long_off, toff, pool, xt, tbuf);
+                far, chunks, long_ids, nlong, long_off, toff, pool, xt, tbuf);
             count_launches(1);
         }
     }
@@ -216,7 +221,8 @@ cudaError_t matvec_t(int64_t n, const int32_t *perm, const T *x, T *y, T *xt, T 
     if (g2 > 65535) g2 = 65535;
     if (g2 > 0) {
         k_leaf_rows<T><<<(unsigned)g2, kMvThreads, 0, st>>>(leaf_rows, leaf_ptr, leaf_items, nleaf,
-                                                            far, toff, pool, tbuf, near, near_data,
+                                                            far, chunks, toff, pool, tbuf, near,
+                                                            near_data,
                                                             xt, yt);
         count_launches(1);
     }
@@ -237,7 +243,8 @@ cudaError_t launch_long_offsets(const FarBlock *far, const int64_t *ids, int64_t
 }
 
 cudaError_t launch_matvec(bool cplx, int64_t n, const int32_t *perm, const void *x, void *y,
-                          void *xt, void *yt, void *tbuf, const FarBlock *far, int64_t nfar,
+                          void *xt, void *yt, void *tbuf, const FarBlock *far,
+                          const FarChunks *chunks, int64_t nfar,
                           const int64_t *toff, const void *pool_data, const NearBlock *near,
                           const void *near_data, const int64_t *leaf_rows,
                           const int64_t *leaf_ptr, const int64_t *leaf_items, int64_t nleaf,
@@ -246,12 +253,12 @@ cudaError_t launch_matvec(bool cplx, int64_t n, const int32_t *perm, const void 
 {
     if (cplx)
         return matvec_t<double2>(n, perm, (const double2 *)x, (double2 *)y, (double2 *)xt,
-                                 (double2 *)yt, (double2 *)tbuf, far, nfar, toff,
+                                 (double2 *)yt, (double2 *)tbuf, far, chunks, nfar, toff,
                                  (const double2 *)pool_data, near, (const double2 *)near_data,
                                  leaf_rows, leaf_ptr, leaf_items, nleaf, long_ids, nlong,
                                  long_off, st);
     return matvec_t<double>(n, perm, (const double *)x, (double *)y, (double *)xt, (double *)yt,
-                            (double *)tbuf, far, nfar, toff, (const double *)pool_data, near,
+                            (double *)tbuf, far, chunks, nfar, toff, (const double *)pool_data, near,
                             (const double *)near_data, leaf_rows, leaf_ptr, leaf_items, nleaf,
                             long_ids, nlong, long_off, st);
 }
