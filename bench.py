@@ -115,6 +115,55 @@ def measured_peaks():
         return {}
 
 
+# Algorithmic FP32 instructions and MUFU operations per Green's function
+# evaluation of the regular quadrature (36 evaluations per entry):
+# SLP 3 FADD (x - y) + 3 FMUL/FFMA (r^2) + 1 FFMA (w / r) and one rsqrt;
+# DLP adds the normal product (3) and r^-3 (2).
+QUAD_FP32_PER_EVAL = {0: 7, 1: 12}
+
+
+def quadrature_roofline(bem, mesh, V, T, dev, stream, flush, reps: int = 3):
+    """A3 alone: one bem_entries call over two opposite caps of the sphere
+    (every pair regular and well separated), timed with CUDA events on the
+    launching stream, against the FP32 and MUFU pipe peaks."""
+    import torch
+    cen = V[T].mean(axis=1)
+    test = np.nonzero(cen[:, 2] > 0.5)[0].astype(np.int32)
+    trial = np.nonzero(cen[:, 2] < -0.5)[0].astype(np.int32)
+    ti = torch.from_numpy(test).to(dev)
+    tj = torch.from_numpy(trial).to(dev)
+    out = torch.empty(len(test) * len(trial), dtype=torch.float64, device=dev)
+    ents = float(len(test)) * len(trial)
+    f_fp32 = N_SM * FP32_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9   # Gop/s
+    f_mufu = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+    res = {"kernel": "k_entries (bem_entries, mixed precision, regular far pairs)",
+           "entries_per_launch": ents, "evals_per_entry": 36,
+           "timing": "CUDA events around one bem_entries call (one k_entries launch, "
+                     "3 empty singular launches); L2 flushed before each"}
+    for op, name in ((bem.SLP, "SLP"), (bem.DLP, "DLP")):
+        bem.bem_entries(mesh.handle, op, 0.0, bem.MIXED, ti, tj, out, stream.cuda_stream)  # warm-up
+        ms = []
+        for _ in range(reps):
+            flush.fill_(3)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bem.bem_entries(mesh.handle, op, 0.0, bem.MIXED, ti, tj, out, stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = float(np.median(ms)) * 1e-3
+        fp32 = ents * 36 * QUAD_FP32_PER_EVAL[op] / t / 1e9
+        mufu = ents * 36 / t / 1e9
+        fr32, frmu = fp32 / f_fp32, mufu / f_mufu
+        res[name] = {"ms": t * 1e3, "entries_per_s": ents / t,
+                     "fp32": {"achieved": fp32, "peak": f_fp32, "unit": "Gop/s", "frac": fr32},
+                     "mufu": {"achieved": mufu, "peak": f_mufu, "unit": "Gop/s", "frac": frmu},
+                     "binding": "fp32" if fr32 >= frmu else "mufu", "frac": max(fr32, frmu)}
+    del out
+    torch.cuda.empty_cache()
+    return res
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle arm (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -340,6 +389,8 @@ def run_gpu(args):
                            "max SM clock; MEASURED_PEAKS.json holds no ALU peak")
     roof["phase_ms_per_step"] = per_step
 
+    quad = quadrature_roofline(bem, mesh, V, T, dev, stream, flush)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds)
@@ -360,7 +411,7 @@ def run_gpu(args):
                 "ranks": {"SLP": [st_slp["rank_min"], st_slp["rank_mean"], st_slp["rank_max"]],
                           "DLP": [st_dlp["rank_min"], st_dlp["rank_mean"], st_dlp["rank_max"]]},
                 "mixed_vs_fp64": mixed_vs_fp64,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "roofline": roof, "quadrature_roofline": quad, "cpu_baseline": cpu, "clocks": clk,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.median(e2e_ms))},
                 "gpu_launches": int(launches), "step_ms": step_ms}

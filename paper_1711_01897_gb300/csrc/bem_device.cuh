@@ -28,6 +28,30 @@ __device__ __forceinline__ C2 cconjmul(C2 a, C2 b)  // conj(a) * b
 }
 __device__ __forceinline__ double cabs2(C2 a) { return fma(a.re, a.re, a.im * a.im); }
 
+// ---- single-instruction FP32 approximations (PTX ISA) ---------------------
+// The .ftz forms are one MUFU instruction each; the non-ftz library forms add
+// subnormal handling that no regular-pair quadrature operand needs (r^2 and
+// r + R0 are bounded away from zero).  PTX ISA bounds: rsqrt.approx and
+// rcp.approx have maximum relative error 2^-23 (rcp: 1 ulp); sin.approx and
+// cos.approx have maximum absolute error 2^-20.5 for |x| <= 100 pi.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void sincos_ftz(float x, float *s, float *c)
+{
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(x));
+}
+
 // ---- float-float accumulation (Knuth's TwoSum) ---------------------------
 struct FF {
     float hi, lo;
@@ -80,51 +104,36 @@ struct TriD {           // FP64 view
     double area;
 };
 
-// structure-of-arrays load: coalesced when neighbouring lanes read
-// neighbouring triangles
-__device__ __forceinline__ void load_trif(const DevGeom &g, int64_t p, TriF &t)
+// tiled load: field k of triangle p at a fixed offset 128 k bytes from one
+// address; coalesced when neighbouring lanes read neighbouring triangles and
+// a single line per field when all lanes read the same triangle
+__device__ __forceinline__ const float *tile_of(const DevGeom &g, int64_t p)
 {
-    const int64_t n = g.nt;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        t.ch[c] = __ldg(g.ch + c * n + p);
-        t.cl[c] = __ldg(g.cl + c * n + p);
-        t.n[c] = __ldg(g.nrmf + c * n + p);
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) t.q[q][c] = __ldg(g.qo + (q * 3 + c) * n + p);
-    t.s.hi = __ldg(g.sc + p);
-    t.s.lo = __ldg(g.sc + n + p);
+    return g.tq + ((p >> 5) << 10) + (p & 31);
 }
 
-// array-of-structures load: one 128-byte line per triangle, for lanes that
-// read unrelated triangles
-__device__ __forceinline__ void load_trif_aos(const DevGeom &g, int64_t p, TriF &t)
+__device__ __forceinline__ void load_trif(const DevGeom &g, int64_t p, TriF &t)
 {
-    float f[32];
-    const float4 *src = g.tf + 8 * p;
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-        float4 x = __ldg(src + v);
-        f[4 * v] = x.x;
-        f[4 * v + 1] = x.y;
-        f[4 * v + 2] = x.z;
-        f[4 * v + 3] = x.w;
-    }
+    const float *f = tile_of(g, p);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        t.ch[c] = f[c];
-        t.cl[c] = f[3 + c];
-        t.n[c] = f[24 + c];
+        t.ch[c] = __ldg(f + 32 * (kFCh + c));
+        t.cl[c] = __ldg(f + 32 * (kFCl + c));
+        t.n[c] = __ldg(f + 32 * (kFN + c));
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) t.q[q][c] = f[6 + 3 * q + c];
-    t.s.hi = f[27];
-    t.s.lo = f[28];
+        for (int c = 0; c < 3; ++c) t.q[q][c] = __ldg(f + 32 * (kFQ + 3 * q + c));
+    t.s.hi = __ldg(f + 32 * kFS);
+    t.s.lo = __ldg(f + 32 * (kFS + 1));
+}
+
+__device__ __forceinline__ void load_ids_tile(const DevGeom &g, int64_t p, int v[3])
+{
+    const float *f = tile_of(g, p);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = __float_as_int(__ldg(f + 32 * (kFId + c)));
 }
 
 __device__ __forceinline__ void load_trid(const DevGeom &g, int64_t p, TriD &t)
@@ -139,20 +148,20 @@ __device__ __forceinline__ void load_trid(const DevGeom &g, int64_t p, TriD &t)
     t.area = __ldg(g.area + p);
 }
 
-__device__ __forceinline__ int shared_count(const DevGeom &g, int64_t a, int64_t b)
+__device__ __forceinline__ void load_ids_soa(const DevGeom &g, int64_t p, int v[3])
 {
-    const int64_t n = g.nt;
-    int ta[3], tb[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        ta[c] = __ldg(g.tri + c * n + a);
-        tb[c] = __ldg(g.tri + c * n + b);
-    }
+    for (int c = 0; c < 3; ++c) v[c] = __ldg(g.tri + c * g.nt + p);
+}
+
+// number of vertices two triangles share
+__device__ __forceinline__ int count_shared(const int a[3], const int b[3])
+{
     int s = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) s += (ta[i] == tb[j]);
+        for (int j = 0; j < 3; ++j) s += (a[i] == b[j]);
     return s;
 }
 
@@ -186,7 +195,7 @@ __device__ __forceinline__ double entry_mixed_laplace(const TriF &a, const TriF 
         for (int q = 0; q < NQ; ++q) {
             float d0 = Dp0 - b.q[q][0], d1 = Dp1 - b.q[q][1], d2 = Dp2 - b.q[q][2];
             float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            float ri = rsqrtf(r2);
+            float ri = rsqrt_ftz(r2);
             if (OP == 0) s = fmaf(w[q], ri, s);
             else if (OP == 1) s = fmaf(w[q], ri * ri * ri, s);
             else s = fmaf(cq[q], ri * ri * ri, s);
@@ -309,12 +318,12 @@ __device__ __forceinline__ C2 entry_mixed_helmholtz(const TriF &a, const TriF &b
             float e0 = a.q[p][0] - b.q[q][0], e1 = a.q[p][1] - b.q[q][1], e2 = a.q[p][2] - b.q[q][2];
             float d0 = D[0] + e0, d1 = D[1] + e1, d2 = D[2] + e2;
             float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            float ri = rsqrtf(r2);
+            float ri = rsqrt_ftz(r2);
             float r = r2 * ri;
             float dr2 = fmaf(e0, 2.f * D[0] + e0, fmaf(e1, 2.f * D[1] + e1, e2 * (2.f * D[2] + e2)));
-            float phi = kf * dr2 / (r + R0f);
+            float phi = kf * dr2 * rcp_ftz(r + R0f);
             float sp, cp;
-            __sincosf(phi, &sp, &cp);
+            sincos_ftz(phi, &sp, &cp);
             float fr, fi, amp;
             if (OP == 0) {
                 amp = w[q] * ri;
@@ -357,6 +366,10 @@ struct RegularEntry<OP, CPLX, 0> {  // FP64
     {
         load_trid(g, p, t);
     }
+    static __device__ __forceinline__ void ids(const DevGeom &g, int64_t p, int v[3])
+    {
+        load_ids_soa(g, p, v);
+    }
     static __device__ __forceinline__ C2 eval(const Tri &a, const Tri &b, const QuadRule &R,
                                               double k)
     {
@@ -373,7 +386,11 @@ struct RegularEntry<OP, CPLX, 1> {  // mixed
     }
     static __device__ __forceinline__ void load_scattered(const DevGeom &g, int64_t p, Tri &t)
     {
-        load_trif_aos(g, p, t);
+        load_trif(g, p, t);
+    }
+    static __device__ __forceinline__ void ids(const DevGeom &g, int64_t p, int v[3])
+    {
+        load_ids_tile(g, p, v);
     }
     static __device__ __forceinline__ C2 eval(const Tri &a, const Tri &b, const QuadRule &R,
                                               double k)

@@ -24,15 +24,19 @@ struct DevGeom {
     const double *nrm;     // [3][nt] unit normal (right-hand rule)
     const double *area;    // [nt]
     const double *qp;      // [3*NQ][nt] quadrature points, q*3 + c
-    const float *ch;       // [3][nt] centroid, high part
-    const float *cl;       // [3][nt] centroid, low part (centroid - ch)
-    const float *qo;       // [3*NQ][nt] points minus centroid
-    const float *nrmf;     // [3][nt]
-    const float *sc;       // [2][nt] area / sqrt(4 pi) as float-float (hi, lo)
-    // the mixed-precision view again, 128 bytes per triangle (array of
-    // structures): centroid hi[3] lo[3], points[18], normal[3], scale hi lo, pad
-    const float4 *tf;      // [8 * nt]
+    // mixed-precision view in tiles of 32 triangles: tile t holds field f of
+    // triangle 32 t + l at tq[1024 t + 32 f + l], so that a warp reading 32
+    // consecutive triangles reads one 128-byte line per field and every field
+    // of a triangle sits at a fixed offset from one address
+    const float *tq;       // [ceil(nt / 32)][kTileFields][32]
 };
+
+// fields of a tile: centroid high part [3] and low part [3] (centroid - high),
+// quadrature points minus centroid [NQ][3], unit normal [3], area/sqrt(4 pi)
+// as float-float (hi, lo), vertex ids [3] stored as int bits
+constexpr int kTileFields = 32;
+constexpr int kFCh = 0, kFCl = 3, kFQ = 6, kFN = 6 + 3 * NQ, kFS = kFN + 3, kFId = kFS + 2;
+static_assert(kFId + 3 == kTileFields, "tile fields");
 
 // Regular rule: reference points and weights (sum 1).
 struct QuadRule {
@@ -128,7 +132,7 @@ int64_t launches_total();
 
 // ---- launchers (defined in the .cu files) -------------------------------
 cudaError_t launch_geometry(const double *V, const int32_t *T, const int32_t *perm, int64_t nt,
-                            const QuadRule &rule, void *const bufs[12], cudaStream_t st);
+                            const QuadRule &rule, void *const bufs[6], cudaStream_t st);
 
 cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int op, double k,
                                    int prec, const int32_t *test, int64_t n_test,

@@ -387,7 +387,7 @@ DeviceConsts &device_consts()
 
 // Device geometry owned by a mesh or an H-matrix.
 struct GeomStore {
-    DBuf tri, vtx, nrm, area, qp, ch, cl, qo, nrmf, sc, tf;
+    DBuf tri, vtx, nrm, area, qp, tq;
     DevGeom g{};
     void build(const double *dV, const int32_t *dT, const int32_t *dperm, int64_t nt,
                const QuadRule &R, cudaStream_t st)
@@ -397,14 +397,8 @@ struct GeomStore {
         nrm.alloc(3 * nt * sizeof(double), st);
         area.alloc(nt * sizeof(double), st);
         qp.alloc(3 * NQ * nt * sizeof(double), st);
-        ch.alloc(3 * nt * sizeof(float), st);
-        cl.alloc(3 * nt * sizeof(float), st);
-        qo.alloc(3 * NQ * nt * sizeof(float), st);
-        nrmf.alloc(3 * nt * sizeof(float), st);
-        sc.alloc(2 * nt * sizeof(float), st);
-        tf.alloc(8 * nt * sizeof(float4), st);
-        void *const b[12] = {tri.p, vtx.p, nrm.p, area.p, qp.p, ch.p, cl.p, qo.p, nrmf.p, sc.p,
-                             tf.p, nullptr};
+        tq.alloc((nt + 31) / 32 * 32 * kTileFields * sizeof(float), st);
+        void *const b[6] = {tri.p, vtx.p, nrm.p, area.p, qp.p, tq.p};
         CU(launch_geometry(dV, dT, dperm, nt, R, b, st));
         g.nt = nt;
         g.tri = tri.as<int32_t>();
@@ -412,12 +406,7 @@ struct GeomStore {
         g.nrm = nrm.as<double>();
         g.area = area.as<double>();
         g.qp = qp.as<double>();
-        g.ch = ch.as<float>();
-        g.cl = cl.as<float>();
-        g.qo = qo.as<float>();
-        g.nrmf = nrmf.as<float>();
-        g.sc = sc.as<float>();
-        g.tf = tf.as<float4>();
+        g.tq = tq.as<float>();
     }
 };
 
@@ -1102,7 +1091,7 @@ int64_t hmat_device_bytes(bem_hmat H, bool cplx)
     const int64_t nt = H->mesh->nt, esz = cplx ? 16 : 8;
     int64_t sum_mn = 0;
     for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
-    int64_t geom = 2 * nt * (12 + 72 + 24 + 8 + 144 + 24 + 72 + 12 + 8 + 128);  // mesh + cluster order
+    int64_t geom = 2 * (nt * (12 + 72 + 24 + 8 + 144) + (nt + 31) / 32 * 32 * 128);  // mesh + cluster order
     int64_t tree = (int64_t)(H->near.size() * sizeof(NearBlock) +
                              H->far.size() * (sizeof(FarBlock) + sizeof(FarChunks))) +
                    (int64_t)(H->sing[0].size() + H->sing[1].size() + H->sing[2].size()) * 16 +

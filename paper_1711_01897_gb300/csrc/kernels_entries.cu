@@ -15,8 +15,7 @@ constexpr int kGeomThreads = 256;
 __global__ void __launch_bounds__(kGeomThreads)
 k_geometry(const double *__restrict__ V, const int32_t *__restrict__ T,
            const int32_t *__restrict__ perm, int64_t nt, QuadRule R, int32_t *tri, double *vtx,
-           double *nrm, double *area, double *qp, float *ch, float *cl, float *qo, float *nrmf,
-           float *sc, float4 *tf)
+           double *nrm, double *area, double *qp, float *tq)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nt) return;
@@ -40,37 +39,28 @@ k_geometry(const double *__restrict__ V, const int32_t *__restrict__ T,
     double len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
     double A = 0.5 * len;
     area[p] = A;
+    float *f = tq + ((p >> 5) << 10) + (p & 31);  // field k at f[32 k]
     double cen[3];
     for (int c = 0; c < 3; ++c) {
         double nc = nn[c] / len;
         nrm[c * nt + p] = nc;
-        nrmf[c * nt + p] = (float)nc;
+        f[32 * (kFN + c)] = (float)nc;
         cen[c] = ((v[0][c] + v[1][c]) + v[2][c]) / 3.0;
         float h = (float)cen[c];
-        ch[c * nt + p] = h;
-        cl[c * nt + p] = (float)(cen[c] - (double)h);
+        f[32 * (kFCh + c)] = h;
+        f[32 * (kFCl + c)] = (float)(cen[c] - (double)h);
+        f[32 * (kFId + c)] = __int_as_float(T[3 * t + c]);
     }
     for (int q = 0; q < NQ; ++q)
         for (int c = 0; c < 3; ++c) {
             double x = v[0][c] + R.s[q] * e1[c] + R.t[q] * e2[c];
             qp[(q * 3 + c) * nt + p] = x;
-            qo[(q * 3 + c) * nt + p] = (float)(x - cen[c]);
+            f[32 * (kFQ + 3 * q + c)] = (float)(x - cen[c]);
         }
     double s = A * rsqrt(4.0 * CUDART_PI);
     float sh = (float)s;
-    sc[p] = sh;
-    sc[nt + p] = (float)(s - (double)sh);
-    float f[32];
-    for (int c = 0; c < 3; ++c) {
-        f[c] = ch[c * nt + p];
-        f[3 + c] = cl[c * nt + p];
-        f[24 + c] = nrmf[c * nt + p];
-    }
-    for (int q = 0; q < 3 * NQ; ++q) f[6 + q] = qo[q * nt + p];
-    f[27] = sh;
-    f[28] = sc[nt + p];
-    f[29] = f[30] = f[31] = 0.f;
-    for (int v = 0; v < 8; ++v) tf[8 * p + v] = make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+    f[32 * kFS] = sh;
+    f[32 * (kFS + 1)] = (float)(s - (double)sh);
 }
 
 template <bool CPLX>
@@ -94,16 +84,26 @@ k_entries(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int
     using E = RegularEntry<OP, CPLX, PREC>;
     int64_t b = (int64_t)blockIdx.x * kEntBx + threadIdx.x;
     if (b >= n_trial) return;
-    int32_t j = trial[b];
+    const int32_t j = trial[b];
+    if (j < 0 || j >= g.nt) {
+        atomicExch(err, 1);
+        return;
+    }
+    typename E::Tri tb;  // this thread's trial triangle, fixed over its rows
+    E::load(g, j, tb);
+    int vj[3];
+    E::ids(g, j, vj);
     for (int64_t a = (int64_t)blockIdx.y * kEntBy + threadIdx.y; a < n_test;
          a += (int64_t)gridDim.y * kEntBy) {
         int32_t i = test[a];
-        if (i < 0 || i >= g.nt || j < 0 || j >= g.nt) {
+        if (i < 0 || i >= g.nt) {
             atomicExch(err, 1);
             continue;
         }
         int64_t dst = a * n_trial + b;
-        int s = shared_count(g, i, j);
+        int vi[3];
+        E::ids(g, i, vi);
+        const int s = count_shared(vi, vj);
         if (s > 0) {
             unsigned long long slot = atomicAdd(&counts[s - 1], 1ull);
             if (slot < cap) {
@@ -114,9 +114,8 @@ k_entries(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int
             }
             continue;
         }
-        typename E::Tri ta, tb;
+        typename E::Tri ta;
         E::load(g, i, ta);
-        E::load(g, j, tb);
         store_val<CPLX>(out, dst, E::eval(ta, tb, R, k));
     }
 }
@@ -350,16 +349,25 @@ k_near_regular(DevGeom g, QuadRule R, double k, const NearBlock *__restrict__ bl
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t b = warp; b < nblocks; b += nwarps) {
-        NearBlock B = blocks[b];
-        int64_t m = B.te - B.tb, nn = B.se - B.sb, tot = m * nn;
+        const NearBlock B = blocks[b];
+        const int m = (int)(B.te - B.tb), nn = (int)(B.se - B.sb);
+        // entry e = r * nn + c of the block, stepped by 32 without division
+        int r = lane / nn, c = lane - r * nn;
+        const int dr = 32 / nn, dc = 32 - dr * nn;
+        const int64_t tot = (int64_t)m * nn;
         for (int64_t e = lane; e < tot; e += 32) {
-            int64_t r = e / nn, c = e - r * nn;
-            int64_t pi = B.tb + r, pj = B.sb + c;
-            if (shared_count(g, pi, pj) > 0) continue;
+            // pairs that share a vertex get a value here that the singular
+            // kernel, launched after this one on the same stream, overwrites
             typename E::Tri ta, tb;
-            E::load(g, pi, ta);
-            E::load(g, pj, tb);
+            E::load(g, B.tb + r, ta);
+            E::load(g, B.sb + c, tb);
             store_val<CPLX>(out, B.off + e, E::eval(ta, tb, R, k));
+            r += dr;
+            c += dc;
+            if (c >= nn) {
+                c -= nn;
+                ++r;
+            }
         }
     }
 }
@@ -379,13 +387,12 @@ int num_sms_cached()
 }  // namespace
 
 cudaError_t launch_geometry(const double *V, const int32_t *T, const int32_t *perm, int64_t nt,
-                            const QuadRule &rule, void *const bufs[12], cudaStream_t st)
+                            const QuadRule &rule, void *const bufs[6], cudaStream_t st)
 {
     int64_t grid = (nt + kGeomThreads - 1) / kGeomThreads;
     k_geometry<<<(unsigned)grid, kGeomThreads, 0, st>>>(
         V, T, perm, nt, rule, (int32_t *)bufs[0], (double *)bufs[1], (double *)bufs[2],
-        (double *)bufs[3], (double *)bufs[4], (float *)bufs[5], (float *)bufs[6],
-        (float *)bufs[7], (float *)bufs[8], (float *)bufs[9], (float4 *)bufs[10]);
+        (double *)bufs[3], (double *)bufs[4], (float *)bufs[5]);
     count_launches(1);
     return cudaGetLastError();
 }
