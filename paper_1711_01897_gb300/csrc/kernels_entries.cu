@@ -120,6 +120,111 @@ k_entries(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int
     }
 }
 
+// Mixed precision: persistent CTAs over tiles of kTileRows test rows x 32
+// trial columns.  The tile's test triangles are staged in shared memory (a
+// warp copies one triangle, a field per lane), each lane holds its trial
+// triangle in registers for the whole tile, and a warp evaluates one row at a
+// time, reading the row's triangle with eight broadcast 128-bit loads.
+constexpr int kTileThreads = 128, kTileRows = 64;
+
+__device__ __forceinline__ void push_singular(int s, int32_t i, int32_t j, int64_t dst,
+                                              SingPair *l1, SingPair *l2, SingPair *l3,
+                                              unsigned long long *counts, unsigned long long cap,
+                                              int *err)
+{
+    unsigned long long slot = atomicAdd(&counts[s - 1], 1ull);
+    if (slot < cap) {
+        SingPair *L = s == 1 ? l1 : (s == 2 ? l2 : l3);
+        L[slot] = {i, j, dst};
+    } else {
+        atomicExch(err, 2);
+    }
+}
+
+template <int OP, bool CPLX>
+__global__ void __launch_bounds__(kTileThreads)
+k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int64_t n_test,
+                const int32_t *__restrict__ trial, int64_t n_trial, void *out, SingPair *l1,
+                SingPair *l2, SingPair *l3, unsigned long long *counts, unsigned long long cap,
+                int *err)
+{
+    using E = RegularEntry<OP, CPLX, 1>;
+    __shared__ __align__(16) float rows_s[kTileRows][kTileFields];
+    __shared__ int32_t rid_s[kTileRows];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int nw = kTileThreads / 32;
+    const int64_t ncb = (n_trial + 31) / 32, nrb = (n_test + kTileRows - 1) / kTileRows;
+    const int64_t ntiles = ncb * nrb;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t cb = tile % ncb, rb = tile / ncb;
+        const int64_t a0 = rb * kTileRows;
+        const int nr = (int)((n_test - a0) < kTileRows ? (n_test - a0) : kTileRows);
+        __syncthreads();  // the previous tile's rows are no longer read
+        for (int r = w; r < nr; r += nw) {
+            const int32_t i = __ldg(test + a0 + r);
+            const bool ok = i >= 0 && i < g.nt;
+            rows_s[r][lane] = ok ? __ldg(tile_of(g, i) + 32 * lane) : 0.f;
+            if (lane == 0) {
+                rid_s[r] = ok ? i : -1;
+                if (!ok) atomicExch(err, 1);
+            }
+        }
+        const int64_t b = cb * 32 + lane;
+        int32_t j = -1;
+        if (b < n_trial) {
+            j = __ldg(trial + b);
+            if (j < 0 || j >= g.nt) {
+                atomicExch(err, 1);
+                j = -1;
+            }
+        }
+        TriF tb;
+        int vj[3] = {-1, -1, -1};
+        if (j >= 0) {
+            load_trif(g, j, tb);
+            load_ids_tile(g, j, vj);
+        }
+        __syncthreads();
+        if (j < 0) continue;
+        for (int r = w; r < nr; r += nw) {
+            const int32_t i = rid_s[r];
+            if (i < 0) continue;
+            float f[kTileFields];
+            const float4 *src = reinterpret_cast<const float4 *>(rows_s[r]);
+#pragma unroll
+            for (int v = 0; v < kTileFields / 4; ++v) {
+                const float4 x = src[v];
+                f[4 * v] = x.x;
+                f[4 * v + 1] = x.y;
+                f[4 * v + 2] = x.z;
+                f[4 * v + 3] = x.w;
+            }
+            const int vi[3] = {__float_as_int(f[kFId]), __float_as_int(f[kFId + 1]),
+                               __float_as_int(f[kFId + 2])};
+            const int64_t dst = (a0 + r) * n_trial + b;
+            const int s = count_shared(vi, vj);
+            if (s > 0) {
+                push_singular(s, i, j, dst, l1, l2, l3, counts, cap, err);
+                continue;
+            }
+            TriF ta;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ta.ch[c] = f[kFCh + c];
+                ta.cl[c] = f[kFCl + c];
+                ta.n[c] = f[kFN + c];
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ta.q[q][c] = f[kFQ + 3 * q + c];
+            ta.s.hi = f[kFS];
+            ta.s.lo = f[kFS + 1];
+            store_val<CPLX>(out, dst, E::eval(ta, tb, R, k));
+        }
+    }
+}
+
 // ---- Sauter-Schwab singular pairs (FP64) -----------------------------------
 // Vertex orders of the panel parametrisations chi(x^) = P0 + x1 (P1 - P0) +
 // x2 (P2 - P1):  identical - stored order for both; edge - test starts at the
@@ -403,14 +508,31 @@ static void entries_launch(const DevGeom &g, const QuadRule &R, double k, const 
                            SingPair *lists[3], unsigned long long *counts,
                            unsigned long long cap, int *err, cudaStream_t st)
 {
-    int64_t gx = (n_trial + kEntBx - 1) / kEntBx;
-    int64_t gy = (n_test + kEntBy - 1) / kEntBy;
-    if (gy > 65535) gy = 65535;
-    dim3 grid((unsigned)gx, (unsigned)gy), block(kEntBx, kEntBy);
-    k_entries<OP, CPLX, PREC><<<grid, block, 0, st>>>(g, R, k, test, n_test, trial, n_trial, out,
-                                                      lists[0], lists[1], lists[2], counts, cap,
-                                                      err);
-    count_launches(1);
+    if constexpr (PREC == 1) {
+        // persistent grid: every SM filled, tiles handed out round-robin
+        static int per_sm = 0;
+        if (!per_sm) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_entries_tiled<OP, CPLX>,
+                                                          kTileThreads, 0);
+            if (per_sm < 1) per_sm = 1;
+        }
+        const int64_t ntiles = (n_trial + 31) / 32 * ((n_test + kTileRows - 1) / kTileRows);
+        int64_t grid = (int64_t)num_sms_cached() * per_sm;
+        if (grid > ntiles) grid = ntiles;
+        k_entries_tiled<OP, CPLX><<<(unsigned)grid, kTileThreads, 0, st>>>(
+            g, R, k, test, n_test, trial, n_trial, out, lists[0], lists[1], lists[2], counts, cap,
+            err);
+        count_launches(1);
+    } else {
+        int64_t gx = (n_trial + kEntBx - 1) / kEntBx;
+        int64_t gy = (n_test + kEntBy - 1) / kEntBy;
+        if (gy > 65535) gy = 65535;
+        dim3 grid((unsigned)gx, (unsigned)gy), block(kEntBx, kEntBy);
+        k_entries<OP, CPLX, PREC><<<grid, block, 0, st>>>(g, R, k, test, n_test, trial, n_trial,
+                                                          out, lists[0], lists[1], lists[2],
+                                                          counts, cap, err);
+        count_launches(1);
+    }
 }
 
 #define BEM_DISPATCH(OPV, CPLXV, PRECV, CALL)                                           \

@@ -118,6 +118,34 @@ def test_entries_device_pointers_and_ragged(lib, l3):
     assert relf(outc.cpu().numpy(), refc) < 1e-11
 
 
+@pytest.mark.parametrize("op", [bem.SLP, bem.DLP, bem.ADLP])
+@pytest.mark.parametrize("k", [0.0, 2.0])
+def test_entries_mixed_tiles_ragged(lib, l3, l3_mesh, op, k):
+    """Mixed path over several 64-row x 32-column tiles with ragged tails in
+    both directions, repeated ids and touching pairs inside tiles."""
+    V, T = l3
+    rng = np.random.default_rng(7 + op + int(10 * k))
+    test = np.concatenate([_touching_ids(T, [11, 700, 1200]),
+                           rng.choice(T.shape[0], 200, replace=False), [3, 3]]).astype(np.int32)
+    trial = np.concatenate([rng.choice(T.shape[0], 150, replace=False),
+                            _touching_ids(T, [11, 701])]).astype(np.int32)
+    assert len(test) % 64 and len(trial) % 32 and len(test) > 3 * 64 and len(trial) > 5 * 32
+    got = l3_mesh.entries(op, k, bem.MIXED, test, trial)
+    ref = oracle.entries(V, T, op, k, test, trial)
+    if k == 0:
+        ref = ref.real
+    assert relf(got, ref) <= TOL[bem.MIXED]
+    sing = (T[test][:, None, :, None] == T[trial][None, :, None, :]).any(axis=(2, 3))
+    assert sing.sum() > 20
+    assert np.max(np.abs(got[sing] - ref[sing])) <= 1e-11 * np.abs(ref[sing]).max()
+    # a bad id inside a tile is reported, not evaluated
+    bad = test.copy()
+    bad[70] = T.shape[0] + 5
+    with pytest.raises(bem.BemError) as e:
+        l3_mesh.entries(op, k, bem.MIXED, bad, trial)
+    assert e.value.status == 1
+
+
 def test_entries_errors(lib, l3_mesh):
     out = np.zeros((1, 1))
     with pytest.raises(bem.BemError) as e:
