@@ -26,6 +26,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
 SLP, DLP, ADLP = 0, 1, 2
+P0, DP1, P1 = 0, 1, 2
 _lock = threading.Lock()
 _lib = None
 
@@ -66,8 +67,12 @@ def lib():
                                               ctypes.c_int, P, P]
             L.orc_cluster_tree.argtypes = [P, P, i64, ctypes.c_int, P, P, P, P, P, P, P]
             L.orc_block_tree.argtypes = [P, P, P, dbl, P, P, P, i64, P]
-            L.orc_aca_blocks.argtypes = [P, P, P, i64, P, P, P, P, ctypes.c_int, dbl, dbl, P, P,
-                                         P, P, P, P, P, P, ctypes.c_int]
+            L.orc_aca_blocks.argtypes = [P, P, P, ctypes.c_int, i64, P, P, P, P, ctypes.c_int, dbl,
+                                         dbl, P, P, P, P, P, P, P, P, ctypes.c_int]
+            L.orc_entries_dp1.argtypes = [P, P, i64, ctypes.c_int, dbl, P, i64, P, i64,
+                                          ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
+            L.orc_pair_local.argtypes = [P, P, P, P, ctypes.c_int, dbl, ctypes.c_int, ctypes.c_int,
+                                         P]
             L.orc_aca_dense.argtypes = [P, i64, i64, dbl, ctypes.c_int, P, P, P]
             L.orc_num_threads.restype = ctypes.c_int
             _lib = L
@@ -153,6 +158,127 @@ def pair_entry(a9, b9, ia, ib, op: int, k: float, n_gl: int = 4, regular_order: 
     lib().orc_pair_entry(_p(a9), _p(b9), _p(ia), _p(ib), op, float(k), n_gl, regular_order,
                          ctypes.byref(re), ctypes.byref(im))
     return complex(re.value, im.value)
+
+
+# --------------------------------------------------------------------------
+# Piecewise linear spaces (Sec. 3.3: local dofs of each element pair; Sec.
+# 3.2.3 "Global matrix assembly": contributions summed into global dofs)
+# --------------------------------------------------------------------------
+
+def entries_dp1(V, T, op: int, k: float, test_tris, trial_tris, n_gl: int = 4,
+                regular_order: int = 0, nthreads: int = 0) -> np.ndarray:
+    """DP1 sub-block (complex128, 3 n_test x 3 n_trial): row 3a + alpha, column
+    3b + beta holds the local entry (alpha, beta) of the pair (test_tris[a],
+    trial_tris[b]); local basis functions are the barycentric coordinates of
+    the stored vertices."""
+    V, T = _mesh_arrays(V, T)
+    ti = np.ascontiguousarray(test_tris, dtype=np.int32)
+    tj = np.ascontiguousarray(trial_tris, dtype=np.int32)
+    out = np.zeros((3 * ti.size, 3 * tj.size), dtype=np.complex128)
+    if ti.size and tj.size:
+        lib().orc_entries_dp1(_p(V), _p(T), T.shape[0], op, float(k), _p(ti), ti.size, _p(tj),
+                              tj.size, n_gl, regular_order, _p(out), nthreads)
+    return out
+
+
+def dense_matrix_dp1(V, T, op: int, k: float, **kw) -> np.ndarray:
+    n = np.asarray(T).shape[0]
+    ids = np.arange(n, dtype=np.int32)
+    return entries_dp1(V, T, op, k, ids, ids, **kw)
+
+
+def pair_local(a9, b9, ia, ib, op: int, k: float, n_gl: int = 4,
+               regular_order: int = 0) -> np.ndarray:
+    """3 x 3 local matrix of an explicit triangle pair."""
+    a9 = np.ascontiguousarray(a9, dtype=np.float64).reshape(9)
+    b9 = np.ascontiguousarray(b9, dtype=np.float64).reshape(9)
+    ia = np.ascontiguousarray(ia, dtype=np.int32)
+    ib = np.ascontiguousarray(ib, dtype=np.int32)
+    out = np.zeros(9, dtype=np.complex128)
+    lib().orc_pair_local(_p(a9), _p(b9), _p(ia), _p(ib), op, float(k), n_gl, regular_order,
+                         _p(out))
+    return out.reshape(3, 3)
+
+
+def assemble_p1(T, n_vertices: int, local: np.ndarray) -> np.ndarray:
+    """Global assembly of element-pair contributions into continuous P1 dofs:
+    A[u, v] = sum over pairs (i, j), local a, b with T[i, a] = u, T[j, b] = v
+    of local[3i + a, 3j + b] (Sec. 3.2.3, "Global matrix assembly": the raw
+    element results are added to the global degrees of freedom)."""
+    T = np.asarray(T)
+    dof = T.reshape(-1)
+    A = np.zeros((n_vertices, n_vertices), dtype=local.dtype)
+    for a in range(dof.size):
+        np.add.at(A[dof[a]], dof, local[a])
+    return A
+
+
+def dense_matrix_p1(V, T, op: int, k: float, **kw) -> np.ndarray:
+    """Continuous piecewise linear Galerkin matrix of op (Eq. (1)-(3) with
+    hat functions as test and trial basis)."""
+    return assemble_p1(T, np.asarray(V).shape[0], dense_matrix_dp1(V, T, op, k, **kw))
+
+
+def surface_curls(V, T) -> np.ndarray:
+    """curl_Gamma of each local basis function on its triangle, [nt, 3, 3]
+    (triangle, local vertex, component): n x grad_Gamma lambda_a, with the
+    surface gradient from the 2 x 2 metric of the edge vectors (the gradient
+    g in the plane with g.(v1 - v0) = lambda_a(v1) - lambda_a(v0) and
+    g.(v2 - v0) = lambda_a(v2) - lambda_a(v0))."""
+    V = np.asarray(V, dtype=np.float64)
+    T = np.asarray(T)
+    P = V[T]
+    E1, E2 = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
+    n = np.cross(E1, E2)
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    G = np.stack([np.einsum("ij,ij->i", E1, E1), np.einsum("ij,ij->i", E1, E2),
+                  np.einsum("ij,ij->i", E2, E1), np.einsum("ij,ij->i", E2, E2)], 1).reshape(-1, 2, 2)
+    Ginv = np.linalg.inv(G)
+    # differences lambda_a(v1) - lambda_a(v0), lambda_a(v2) - lambda_a(v0)
+    dl = np.array([[-1.0, -1.0], [1.0, 0.0], [0.0, 1.0]])
+    out = np.zeros((T.shape[0], 3, 3))
+    for a in range(3):
+        c = np.einsum("tij,j->ti", Ginv, dl[a])          # coefficients on E1, E2
+        grad = c[:, 0:1] * E1 + c[:, 1:2] * E2
+        out[:, a] = np.cross(n, grad)
+    return out
+
+
+def hypersingular_p1(V, T, k: float, **kw) -> np.ndarray:
+    """Hypersingular operator on continuous P1 by its weak form, Eq. (4):
+    D[u, v] = sum over element pairs of
+        curl phi_u . curl phi_v  int int g  -  k^2 n_x . n_y  int int phi_u g phi_v,
+    the first integral the P0 single-layer entry of the pair (the curls are
+    constant per triangle), the second the local P1 single-layer entry."""
+    V = np.asarray(V, dtype=np.float64)
+    T = np.asarray(T)
+    nt = T.shape[0]
+    ids = np.arange(nt, dtype=np.int32)
+    S0 = entries(V, T, SLP, k, ids, ids, **kw)                  # [nt, nt]
+    S1 = dense_matrix_dp1(V, T, SLP, k, **kw)                    # [3nt, 3nt]
+    C = surface_curls(V, T).reshape(3 * nt, 3)                   # row 3t + a
+    P = V[T]
+    n = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    tri = np.repeat(np.arange(nt), 3)
+    local = (C @ C.T) * S0[np.ix_(tri, tri)]
+    if k != 0.0:
+        local = local - k * k * (n[tri] @ n[tri].T) * S1
+    return assemble_p1(T, V.shape[0], local)
+
+
+def mass_p1(V, T) -> np.ndarray:
+    """P1 mass matrix M[u, v] = int phi_u phi_v (exact: |T|/12 (1 + delta_ab))."""
+    V = np.asarray(V, dtype=np.float64)
+    T = np.asarray(T)
+    P = V[T]
+    area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    M = np.zeros((V.shape[0], V.shape[0]))
+    loc = (np.ones((3, 3)) + np.eye(3)) / 12.0
+    for a in range(3):
+        for b in range(3):
+            np.add.at(M, (T[:, a], T[:, b]), area * loc[a, b])
+    return M
 
 
 def triangle_potential(tri9, x) -> float:
@@ -301,27 +427,44 @@ def block_list(ct: ClusterTree, bt: BlockTree) -> np.ndarray:
 
 def hmat_assemble(V, T, op: int, k: float, leaf_size: int, eta: float, eps: float,
                   n_gl: int = 4, kcap_max: int = 256, nthreads: int = 0,
-                  block_ids=None) -> HMatrix:
+                  block_ids=None, space: int = P0) -> HMatrix:
     """Algorithm "H-Matrix Assembly" (Sec. 4.1): generate the block cluster
     tree, evaluate inadmissible blocks densely, approximate admissible blocks
-    by ACA.  block_ids restricts the work to a subset of leaf blocks."""
+    by ACA.  block_ids restricts the work to a subset of leaf blocks.
+
+    space=DP1: the same triangle cluster and block trees, each triangle
+    carrying its three local dofs (cluster position t -> dofs 3t, 3t+1,
+    3t+2), so every block is the tripled dof block; ``perm`` and ``blocks``
+    are then in dof units."""
     V, T = _mesh_arrays(V, T)
     ct = cluster_tree(V, T, leaf_size)
     bt = block_tree(ct, eta)
     blocks = block_list(ct, bt)
-    hm = HMatrix(n=T.shape[0], perm=ct.perm, blocks=blocks)
-    sel = np.arange(blocks.shape[0]) if block_ids is None else np.asarray(block_ids)
     perm = ct.perm
+    if space == DP1:
+        dof_perm = (3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1).astype(np.int32)
+        dblocks = blocks.copy()
+        dblocks[:, :4] *= 3
+        hm = HMatrix(n=3 * T.shape[0], perm=dof_perm, blocks=dblocks)
+    else:
+        hm = HMatrix(n=T.shape[0], perm=perm, blocks=blocks)
+    sel = np.arange(blocks.shape[0]) if block_ids is None else np.asarray(block_ids)
     far_ids = [b for b in sel if blocks[b, 4]]
     near_ids = [b for b in sel if not blocks[b, 4]]
     for b in near_ids:
         tb, te, sb, se, _ = blocks[b]
-        hm.near[b] = entries(V, T, op, k, perm[tb:te], perm[sb:se], n_gl=n_gl, nthreads=nthreads)
-        hm.entries_evaluated += (te - tb) * (se - sb)
+        if space == DP1:
+            hm.near[b] = entries_dp1(V, T, op, k, perm[tb:te], perm[sb:se], n_gl=n_gl,
+                                     nthreads=nthreads)
+            hm.entries_evaluated += 9 * (te - tb) * (se - sb)
+        else:
+            hm.near[b] = entries(V, T, op, k, perm[tb:te], perm[sb:se], n_gl=n_gl,
+                                 nthreads=nthreads)
+            hm.entries_evaluated += (te - tb) * (se - sb)
     chunk = 2048
     for c0 in range(0, len(far_ids), chunk):
         ids = np.array(far_ids[c0:c0 + chunk], dtype=np.int64)
-        tb, te, sb, se = (np.ascontiguousarray(blocks[ids, c]) for c in range(4))
+        tb, te, sb, se = (np.ascontiguousarray(hm.blocks[ids, c]) for c in range(4))
         m, n = te - tb, se - sb
         kc = np.minimum(np.minimum(m, n), kcap_max).astype(np.int32)
         uoff = np.concatenate([[0], np.cumsum(m * kc)[:-1]]).astype(np.int64)
@@ -331,7 +474,7 @@ def hmat_assemble(V, T, op: int, k: float, leaf_size: int, eta: float, eps: floa
         rank = np.zeros(ids.size, dtype=np.int32)
         status = np.zeros(ids.size, dtype=np.int32)
         ev = np.zeros(ids.size, dtype=np.int64)
-        lib().orc_aca_blocks(_p(V), _p(T), _p(perm), ids.size, _p(tb), _p(te), _p(sb), _p(se), op,
+        lib().orc_aca_blocks(_p(V), _p(T), _p(perm), int(space), ids.size, _p(tb), _p(te), _p(sb), _p(se), op,
                              float(k), float(eps), _p(kc), _p(uoff), _p(voff), _p(U), _p(Vf),
                              _p(rank), _p(status), _p(ev), nthreads)
         if np.any(status == 3):

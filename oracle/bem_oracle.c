@@ -500,6 +500,153 @@ int orc_pair_entry(const double *a9, const double *b9, const int32_t *ia, const 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Piecewise linear spaces                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Local 3 x 3 matrix of an element pair for piecewise linear test and trial
+ * functions (Sec. 3.3, Algorithm "Integral Evaluation": the kernel values of
+ * all quadrature point pairs are combined with the basis function values of
+ * every pair of local dofs).  The local basis functions of a triangle are
+ * its barycentric coordinates lambda_a, a = stored vertex index; at the
+ * point x = v0 + s (v1 - v0) + t (v2 - v0):  lambda = (1 - s - t, s, t).
+ *   L[a][b] = int_Ti int_Tj lambda_a(x) G(x, y) lambda_b(y) dy dx.
+ * Regular pairs by the tensor Gauss rule. */
+static void local_regular(const otri *Ti, const otri *Tj, int op, double k, const orule *R,
+                          cplx L[3][3])
+{
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) L[a][b] = 0;
+    for (int p = 0; p < R->np; ++p) {
+        double x[3];
+        tri_point(Ti, R->s[p], R->t[p], x);
+        double la[3] = {1.0 - R->s[p] - R->t[p], R->s[p], R->t[p]};
+        for (int q = 0; q < R->np; ++q) {
+            double y[3];
+            tri_point(Tj, R->s[q], R->t[q], y);
+            double lb[3] = {1.0 - R->s[q] - R->t[q], R->s[q], R->t[q]};
+            cplx g = R->w[p] * R->w[q] * kernel(x, y, Ti->n, Tj->n, op, k);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) L[a][b] += la[a] * lb[b] * g;
+        }
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) L[a][b] *= Ti->area * Tj->area;
+}
+
+/* Singular pairs by the same Sauter-Schwab maps as entry_singular.  With the
+ * panel parametrisation chi(x^) = P0 + x1 (P1 - P0) + x2 (P2 - P1), the
+ * barycentric coordinates of the point with respect to (P0, P1, P2) are
+ * (1 - x1, x1 - x2, x2); P_i is stored vertex o[i], so lambda_{o[i]} takes
+ * the i-th of them. */
+static void local_singular(const otri *Ti, const otri *Tj, const int32_t *ta, const int32_t *tb,
+                           int ncase, int op, double k, int n, cplx L[3][3])
+{
+    int oa[3], ob[3];
+    singular_order(ta, tb, ncase, oa, ob);
+    double Pa[3][3], Pb[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) {
+            Pa[i][c] = Ti->v[oa[i]][c];
+            Pb[i][c] = Tj->v[ob[i]][c];
+        }
+    double x[128], g[128];
+    orc_gauss_legendre01(n, x, g);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) L[a][b] = 0;
+    for (int r = 0; r < ss_nregions(ncase); ++r)
+        for (int i0 = 0; i0 < n; ++i0)
+            for (int i1 = 0; i1 < n; ++i1)
+                for (int i2 = 0; i2 < n; ++i2)
+                    for (int i3 = 0; i3 < n; ++i3) {
+                        double xh[2], yh[2], px[3], py[3];
+                        double J = ss_map(ncase, r, x[i0], x[i1], x[i2], x[i3], xh, yh);
+                        chi(Pa, xh, px);
+                        chi(Pb, yh, py);
+                        cplx gv = g[i0] * g[i1] * g[i2] * g[i3] * J *
+                                  kernel(px, py, Ti->n, Tj->n, op, k);
+                        double ba[3] = {1.0 - xh[0], xh[0] - xh[1], xh[1]};
+                        double bb[3] = {1.0 - yh[0], yh[0] - yh[1], yh[1]};
+                        double la[3], lb[3];
+                        for (int i = 0; i < 3; ++i) {
+                            la[oa[i]] = ba[i];
+                            lb[ob[i]] = bb[i];
+                        }
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) L[a][b] += la[a] * lb[b] * gv;
+                    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) L[a][b] *= 4.0 * Ti->area * Tj->area;
+}
+
+static void local_ij(const double *V, const int32_t *Tr, int64_t i, int64_t j, int op, double k,
+                     int n_gl, const orule *R, cplx L[3][3])
+{
+    otri Ti, Tj;
+    tri_load(V, Tr, i, &Ti);
+    tri_load(V, Tr, j, &Tj);
+    int c = count_shared(Tr + 3 * i, Tr + 3 * j);
+    if (c == 0) local_regular(&Ti, &Tj, op, k, R, L);
+    else local_singular(&Ti, &Tj, Tr + 3 * i, Tr + 3 * j, c, op, k, n_gl, L);
+}
+
+/* Discontinuous piecewise linear (DP1) entry: dof 3 t + a is lambda_a on
+ * triangle t, so every entry belongs to exactly one element pair. */
+static cplx entry_dp1(const double *V, const int32_t *Tr, int64_t di, int64_t dj, int op,
+                      double k, int n_gl, const orule *R)
+{
+    cplx L[3][3];
+    local_ij(V, Tr, di / 3, dj / 3, op, k, n_gl, R, L);
+    return L[di % 3][dj % 3];
+}
+
+/* DP1 sub-block for triangle lists: out[3 a + alpha][3 b + beta] (row-major,
+ * 3 n_test x 3 n_trial, complex128) = L(test[a], trial[b])[alpha][beta]. */
+int orc_entries_dp1(const double *V, const int32_t *Tr, int64_t nt, int op, double k,
+                    const int32_t *test_ids, int64_t n_test, const int32_t *trial_ids,
+                    int64_t n_trial, int n_gl, int regular_order, cplx *out, int nthreads)
+{
+    (void)nt;
+    orule *R = (orule *)malloc(sizeof(orule));
+    if (!R) return 3;
+    rule_init(R, regular_order);
+    const int64_t ld = 3 * n_trial;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t a = 0; a < n_test; ++a)
+        for (int64_t b = 0; b < n_trial; ++b) {
+            cplx L[3][3];
+            local_ij(V, Tr, test_ids[a], trial_ids[b], op, k, n_gl, R, L);
+            for (int al = 0; al < 3; ++al)
+                for (int be = 0; be < 3; ++be) out[(3 * a + al) * ld + 3 * b + be] = L[al][be];
+        }
+    free(R);
+    return 0;
+}
+
+/* Local matrix of an explicit triangle pair (coordinates + vertex-index
+ * triples that classify it), for the pins. */
+int orc_pair_local(const double *a9, const double *b9, const int32_t *ia, const int32_t *ib, int op,
+                   double k, int n_gl, int regular_order, cplx *out9)
+{
+    otri Ti, Tj;
+    tri_from_pts(a9, a9 + 3, a9 + 6, &Ti);
+    tri_from_pts(b9, b9 + 3, b9 + 6, &Tj);
+    orule *R = (orule *)malloc(sizeof(orule));
+    if (!R) return 3;
+    rule_init(R, regular_order);
+    int c = count_shared(ia, ib);
+    cplx L[3][3];
+    if (c == 0) local_regular(&Ti, &Tj, op, k, R, L);
+    else local_singular(&Ti, &Tj, ia, ib, c, op, k, n_gl, L);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) out9[3 * a + b] = L[a][b];
+    free(R);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Closed forms used by the pins (not by the entry path above)               */
 /* ------------------------------------------------------------------------ */
 
@@ -856,6 +1003,18 @@ int orc_block_tree(const int64_t *cl_left, const int64_t *cl_right, const double
 /* ACA with partial pivoting (Sec. 2.1, Eq. (6)-(7), Algorithm ACA)          */
 /* ------------------------------------------------------------------------ */
 
+/* Entry (r, c) of a block in cluster order.  P0: dof = triangle.  DP1: the
+ * dofs of the triangle at cluster position t are 3 t, 3 t + 1, 3 t + 2 (its
+ * local basis functions), so a block of triangle ranges is the block of the
+ * tripled dof ranges. */
+static cplx block_entry(const double *V, const int32_t *Tr, const int32_t *perm, int space,
+                        int64_t r, int64_t c, int op, double k, const orule *R)
+{
+    if (space == 0) return entry_ij(V, Tr, perm[r], perm[c], op, k, 4, R);
+    return entry_dp1(V, Tr, 3 * (int64_t)perm[r / 3] + r % 3, 3 * (int64_t)perm[c / 3] + c % 3, op,
+                     k, 4, R);
+}
+
 /* Readings where the paper defers or is silent:
  *  row pivot:  i_1 = 0; afterwards i_{k+1} = argmax_{i not in Z} |(u_k)_i|,
  *              lowest index on ties;
@@ -865,12 +1024,13 @@ int orc_block_tree(const int64_t *cl_left, const int64_t *cl_right, const double
  *              with ||S_k||_F^2 = ||S_{k-1}||_F^2
  *                 + 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> + ||u_k||^2 ||v_k||^2,
  *              or when k = min(m, n), or when Z holds all m rows.
- * Block rows are the test cluster (perm[tb..te)), columns the trial cluster.
+ * Block rows are the test cluster, columns the trial cluster, as dof ranges
+ * in cluster order of the space (block_entry).
  * U is m x kcap column-major, V is n x kcap column-major.  *rank = k.
  * Returns 0, or 4 if kcap was reached before the criterion held. */
-int orc_aca_block(const double *V, const int32_t *Tr, const int32_t *perm, int64_t tb, int64_t te,
-                  int64_t sb, int64_t se, int op, double k, double eps, int kcap, cplx *U, cplx *Vf,
-                  int *rank, int64_t *entries_evaluated)
+int orc_aca_block(const double *V, const int32_t *Tr, const int32_t *perm, int space, int64_t tb,
+                  int64_t te, int64_t sb, int64_t se, int op, double k, double eps, int kcap,
+                  cplx *U, cplx *Vf, int *rank, int64_t *entries_evaluated)
 {
     int64_t m = te - tb, n = se - sb;
     orule *R = (orule *)malloc(sizeof(orule));
@@ -886,7 +1046,7 @@ int orc_aca_block(const double *V, const int32_t *Tr, const int32_t *perm, int64
     for (;;) {
         /* selected row of R_{k-1}: a_{i,:} - sum_l (u_l)_i v_l */
         for (int64_t j = 0; j < n; ++j) {
-            cplx a = entry_ij(V, Tr, perm[tb + i], perm[sb + j], op, k, 4, R);
+            cplx a = block_entry(V, Tr, perm, space, tb + i, sb + j, op, k, R);
             for (int l = 0; l < kk; ++l) a -= U[(int64_t)l * m + i] * Vf[(int64_t)l * n + j];
             row[j] = a;
         }
@@ -909,7 +1069,7 @@ int orc_aca_block(const double *V, const int32_t *Tr, const int32_t *perm, int64
         for (int64_t j = 0; j < n; ++j) vk[j] = row[j] / piv;
         /* selected column of R_{k-1}: a_{:,j} - sum_l (v_l)_j u_l */
         for (int64_t r = 0; r < m; ++r) {
-            cplx a = entry_ij(V, Tr, perm[tb + r], perm[sb + jk], op, k, 4, R);
+            cplx a = block_entry(V, Tr, perm, space, tb + r, sb + jk, op, k, R);
             for (int l = 0; l < kk; ++l) a -= Vf[(int64_t)l * n + jk] * U[(int64_t)l * m + r];
             col[r] = a;
             uk[r] = a;
@@ -945,7 +1105,7 @@ int orc_aca_block(const double *V, const int32_t *Tr, const int32_t *perm, int64
 
 /* ACA over a list of blocks; block b writes its factors at U + uoff[b],
  * V + voff[b] with capacity kcap[b] columns.  Parallel over blocks. */
-int orc_aca_blocks(const double *V, const int32_t *Tr, const int32_t *perm, int64_t nblk,
+int orc_aca_blocks(const double *V, const int32_t *Tr, const int32_t *perm, int space, int64_t nblk,
                    const int64_t *tb, const int64_t *te, const int64_t *sb, const int64_t *se,
                    int op, double k, double eps, const int32_t *kcap, const int64_t *uoff,
                    const int64_t *voff, cplx *U, cplx *Vf, int32_t *rank, int32_t *status,
@@ -958,7 +1118,7 @@ int orc_aca_blocks(const double *V, const int32_t *Tr, const int32_t *perm, int6
     for (int64_t b = 0; b < nblk; ++b) {
         int r = 0;
         int64_t ev = 0;
-        status[b] = orc_aca_block(V, Tr, perm, tb[b], te[b], sb[b], se[b], op, k, eps, kcap[b],
+        status[b] = orc_aca_block(V, Tr, perm, space, tb[b], te[b], sb[b], se[b], op, k, eps, kcap[b],
                                   U + uoff[b], Vf + voff[b], &r, &ev);
         rank[b] = r;
         entries[b] = ev;

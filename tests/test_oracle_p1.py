@@ -1,0 +1,181 @@
+"""Pins of the oracle's piecewise linear spaces (Sec. 3.3, local dofs of an
+element pair; Sec. 3.2.3, global assembly into continuous dofs) and of the
+hypersingular operator (Eq. (4)) against closed forms and identities of the
+exact integrals:
+
+- the three local basis functions sum to one, so the local matrix of a pair
+  sums to its P0 entry;
+- one level of midpoint refinement of both triangles reproduces the local
+  matrix (the parent's barycentric coordinates are linear on every child),
+  which ties every local index of the regular and singular rules;
+- on the unit sphere the interpolant of Y_1 = z is an approximate
+  eigenfunction: <A z, z> / <M z, z> tends at O(h^2) to 1/3 (single layer),
+  -1/6 (double layer and its adjoint), 2/3 (hypersingular), and for k != 0 to
+  i k j_1(k) h_1(k) and -i k^3 j_1'(k) h_1'(k);
+- symmetry of V and D, K' = K^T, D 1 = 0 for k = 0;
+- the surface curl of a hat function against its closed form;
+- the DP1 H-matrix against the dense DP1 matrix.
+"""
+import numpy as np
+import pytest
+from scipy.special import spherical_jn, spherical_yn
+
+import oracle
+from paper_1711_01897_gb300 import meshes
+
+
+def _h1(l, k, derivative=False):
+    return spherical_jn(l, k, derivative) + 1j * spherical_yn(l, k, derivative)
+
+
+@pytest.mark.parametrize("op", [oracle.SLP, oracle.DLP, oracle.ADLP])
+@pytest.mark.parametrize("k", [0.0, 2.0])
+def test_dp1_local_matrices_sum_to_p0_entries(op, k):
+    V, T = meshes.icosphere_level(1)
+    V = meshes.jitter(V, T, 0.05, 17)
+    nt = T.shape[0]
+    ids = np.arange(nt, dtype=np.int32)
+    A1 = oracle.entries_dp1(V, T, op, k, ids, ids)
+    A0 = oracle.entries(V, T, op, k, ids, ids)
+    S = A1.reshape(nt, 3, nt, 3).sum(axis=(1, 3))
+    assert np.abs(S - A0).max() <= 1e-13 * np.abs(A0).max()
+
+
+def _children(P, ids):
+    """Midpoint subdivision.  Midpoints get ids from their edge's end ids so
+    that triangles sharing an edge share its midpoint.  Returns (coords,
+    ids, bary) with bary[g] the parent barycentric coordinates of child
+    vertex g."""
+    B = np.eye(3)
+
+    def mid(a, b):
+        lo, hi = sorted((int(ids[a]), int(ids[b])))
+        return 1000 + 100 * lo + hi, 0.5 * (P[a] + P[b]), 0.5 * (B[a] + B[b])
+
+    v = [(int(ids[i]), P[i], B[i]) for i in range(3)]
+    m01, m12, m20 = mid(0, 1), mid(1, 2), mid(2, 0)
+    out = []
+    for c in ((v[0], m01, m20), (m01, v[1], m12), (m20, m12, v[2]), (m01, m12, m20)):
+        out.append((np.concatenate([x[1] for x in c]), np.array([x[0] for x in c], np.int32),
+                    np.array([x[2] for x in c])))
+    return out
+
+
+BASE = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.1], [0.2, 0.9, 0.0]])
+PAIRS = {
+    "identical": (BASE, [1, 2, 3], BASE, [1, 2, 3]),
+    "edge": (BASE, [1, 2, 3], np.array([[1.0, 0.0, 0.1], [0.0, 0.0, 0.0], [0.7, -0.8, 0.3]]),
+             [2, 1, 4]),
+    "vertex": (BASE, [1, 2, 3], np.array([[1.0, 0.0, 0.1], [1.8, 0.3, -0.2], [1.5, -0.7, 0.1]]),
+               [2, 5, 6]),
+    "regular": (BASE, [1, 2, 3], BASE + np.array([0.3, 0.2, 1.2]), [7, 8, 9]),
+}
+
+
+@pytest.mark.parametrize("case", list(PAIRS))
+@pytest.mark.parametrize("op", [oracle.SLP, oracle.DLP])
+def test_local_matrix_invariant_under_refinement(case, op):
+    Pa, ia, Pb, ib = PAIRS[case]
+    if case == "identical" and op == oracle.DLP:
+        pytest.skip("coplanar pair: the double layer vanishes at both levels")
+    ia, ib = np.array(ia, np.int32), np.array(ib, np.int32)
+    ngl = order = 10
+    L = oracle.pair_local(Pa.reshape(-1), Pb.reshape(-1), ia, ib, op, 0.0, ngl, order)
+    R = np.zeros((3, 3), dtype=complex)
+    for ca, ida, Ba in _children(Pa, ia):
+        for cb, idb, Bb in _children(Pb, ib):
+            R += Ba.T @ oracle.pair_local(ca, cb, ida, idb, op, 0.0, ngl, order) @ Bb
+    assert np.abs(L - R).max() <= 1e-9 * np.abs(L).max()
+    # a transposed local index would break it
+    assert np.abs(L.T - R).max() > 1e-6 * np.abs(L).max() or case == "identical"
+
+
+def test_surface_curl_closed_form():
+    V, T = meshes.icosphere_level(1)
+    V = meshes.jitter(V, T, 0.05, 3)
+    C = oracle.surface_curls(V, T)
+    P = V[T]
+    area2 = np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    for a in range(3):
+        expect = (P[:, (a + 1) % 3] - P[:, (a + 2) % 3]) / area2[:, None]
+        assert np.abs(C[:, a] - expect).max() < 1e-12
+    assert np.abs(C.sum(axis=1)).max() < 1e-12
+
+
+def _rayleigh(V, T, A):
+    z = V[:, 2]
+    return (z @ A @ z) / (z @ oracle.mass_p1(V, T) @ z)
+
+
+@pytest.mark.parametrize("name", ["V", "K", "Kp", "D", "Vk", "Dk"])
+def test_p1_sphere_eigenvalues_converge(name):
+    k = 2.0
+    pred = {"V": 1.0 / 3.0, "K": -1.0 / 6.0, "Kp": -1.0 / 6.0, "D": 2.0 / 3.0,
+            "Vk": 1j * k * spherical_jn(1, k) * _h1(1, k),
+            "Dk": -1j * k ** 3 * spherical_jn(1, k, True) * _h1(1, k, True)}[name]
+    errs = []
+    for L in (1, 2, 3):
+        V, T = meshes.icosphere_level(L)
+        if name == "D":
+            A = oracle.hypersingular_p1(V, T, 0.0)
+        elif name == "Dk":
+            A = oracle.hypersingular_p1(V, T, k)
+        else:
+            op = {"V": oracle.SLP, "Vk": oracle.SLP, "K": oracle.DLP, "Kp": oracle.ADLP}[name]
+            A = oracle.dense_matrix_p1(V, T, op, k if name == "Vk" else 0.0)
+        errs.append(abs(_rayleigh(V, T, A) - pred))
+    # O(h^2) at least: each halving of h divides the error by > 3
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3, errs
+    # the curl and k^2 parts of D_k are each O(1) and cancel to 0.086, so the
+    # final error is bounded in absolute terms
+    assert errs[2] < 0.01, errs
+
+
+def test_p1_symmetries_and_constants():
+    # The Sauter-Schwab maps are not symmetric in test and trial, so with
+    # linear basis functions the transposed pair differs by the singular
+    # rule's error: 10 points per axis make that negligible.
+    V, T = meshes.icosphere_level(1)
+    V = meshes.jitter(V, T, 0.05, 9)
+    kw = {"n_gl": 10}
+    S = oracle.dense_matrix_p1(V, T, oracle.SLP, 0.0, **kw)
+    K = oracle.dense_matrix_p1(V, T, oracle.DLP, 0.0, **kw)
+    Kp = oracle.dense_matrix_p1(V, T, oracle.ADLP, 0.0, **kw)
+    D = oracle.hypersingular_p1(V, T, 0.0, **kw)
+    Dk = oracle.hypersingular_p1(V, T, 1.5, **kw)
+    assert np.abs(S - S.T).max() < 1e-10 * np.abs(S).max()
+    assert np.abs(Kp - K.T).max() < 1e-10 * np.abs(K).max()
+    assert np.abs(D - D.T).max() < 1e-10 * np.abs(D).max()
+    assert np.abs(Dk - Dk.T).max() < 1e-10 * np.abs(Dk).max()
+    # at the production order the asymmetry is the rule's error, still small
+    S4 = oracle.dense_matrix_p1(V, T, oracle.SLP, 0.0)
+    assert np.abs(S4 - S4.T).max() < 1e-5 * np.abs(S4).max()
+    # D 1 = 0: the curl of a constant vanishes
+    D4 = oracle.hypersingular_p1(V, T, 0.0)
+    assert np.abs(D4 @ np.ones(V.shape[0])).max() < 1e-12 * np.abs(D4).max()
+    # Laplace hypersingular: positive semi-definite with the constants as kernel
+    ev = np.linalg.eigvalsh(0.5 * (D + D.T).real)
+    assert ev[0] > -1e-10 * ev[-1] and ev[1] > 1e-6 * ev[-1]
+
+
+def test_dp1_hmatrix_blocks_against_dense():
+    V, T = meshes.icosphere_level(2)
+    A = oracle.dense_matrix_dp1(V, T, oracle.SLP, 0.0)
+    hm = oracle.hmat_assemble(V, T, oracle.SLP, 0.0, 16, 1.2, 1e-6, space=oracle.DP1)
+    assert hm.n == 3 * T.shape[0]
+    Ap = A[np.ix_(hm.perm, hm.perm)]
+    n_far = 0
+    for b, (tb, te, sb, se, adm) in enumerate(hm.blocks):
+        ref = Ap[tb:te, sb:se]
+        got = hm.block_dense(b)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        if adm:
+            n_far += 1
+            assert err < 1e-4, (b, err)
+        else:
+            assert err < 1e-13, (b, err)
+    assert n_far > 0
+    x = np.random.default_rng(1).normal(size=hm.n)
+    y = hm.matvec(x)
+    ref = A @ x
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-6
