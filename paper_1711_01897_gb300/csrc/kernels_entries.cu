@@ -126,6 +126,19 @@ k_entries(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int
 // triangle in registers for the whole tile, and a warp evaluates one row at a
 // time, reading the row's triangle with eight broadcast 128-bit loads.
 constexpr int kTileThreads = 128, kTileRows = 64;
+constexpr int kRowsPerWarp = kTileRows / (kTileThreads / 32);
+static_assert(kTileRows % (kTileThreads / 32) == 0 && kRowsPerWarp <= 32, "rows per warp");
+
+// 4-byte asynchronous global -> shared copy (PTX cp.async, sm_80 and later)
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 __device__ __forceinline__ void push_singular(int s, int32_t i, int32_t j, int64_t dst,
                                               SingPair *l1, SingPair *l2, SingPair *l3,
@@ -160,15 +173,26 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
         const int64_t a0 = rb * kTileRows;
         const int nr = (int)((n_test - a0) < kTileRows ? (n_test - a0) : kTileRows);
         __syncthreads();  // the previous tile's rows are no longer read
-        for (int r = w; r < nr; r += nw) {
-            const int32_t i = __ldg(test + a0 + r);
-            const bool ok = i >= 0 && i < g.nt;
-            rows_s[r][lane] = ok ? __ldg(tile_of(g, i) + 32 * lane) : 0.f;
-            if (lane == 0) {
-                rid_s[r] = ok ? i : -1;
-                if (!ok) atomicExch(err, 1);
+        // A warp stages rows w, w + nw, ...: lane t loads the id of its t-th
+        // row, then the rows' fields are copied asynchronously, all in flight
+        // together (one field per lane and row).
+        int32_t my_id = -1;
+        if (lane < kRowsPerWarp && w + lane * nw < nr) my_id = __ldg(test + a0 + w + lane * nw);
+#pragma unroll 4
+        for (int t = 0; t < kRowsPerWarp; ++t) {
+            const int r = w + t * nw;
+            const int32_t i = __shfl_sync(0xffffffffu, my_id, t);
+            if (r < nr) {
+                const bool ok = i >= 0 && i < g.nt;
+                if (ok) cp_async4(&rows_s[r][lane], tile_of(g, i) + 32 * lane);
+                else rows_s[r][lane] = 0.f;
+                if (lane == 0) {
+                    rid_s[r] = ok ? i : -1;
+                    if (!ok) atomicExch(err, 1);
+                }
             }
         }
+        cp_async_wait_all();
         const int64_t b = cb * 32 + lane;
         int32_t j = -1;
         if (b < n_trial) {
