@@ -1,7 +1,8 @@
 /*
- * bem.h -- C ABI of the GB300 library for P0 Galerkin boundary-element
- * matrices of the 3D Laplace and Helmholtz single-layer, double-layer and
- * adjoint double-layer operators, assembled as H-matrices with ACA
+ * bem.h -- C ABI of the GB300 library for Galerkin boundary-element matrices
+ * (piecewise constant P0 and piecewise linear DP1 / P1 spaces) of the 3D
+ * Laplace and Helmholtz single-layer, double-layer, adjoint double-layer and
+ * hypersingular operators, assembled as H-matrices with ACA
  * (Vater, Betcke, Dilba, "Simple and efficient GPU parallelization of
  * existing H-Matrix accelerated BEM code", arXiv 1711.01897).
  *
@@ -17,12 +18,23 @@
  *    the call returns without waiting, unless stated otherwise.  Calls with
  *    host buffers wait for their copies to finish before returning.
  *  - Rows are test functions psi_i and columns trial functions phi_j, as in
- *    [S_h]_{i,j} of Eq. (1).  P0 spaces: one basis function per triangle,
- *    the indicator of that triangle.
+ *    [S_h]_{i,j} of Eq. (1).  Spaces (test and trial alike):
+ *      BEM_P0   one basis function per triangle, its indicator
+ *      BEM_DP1  three per triangle: dof 3 t + a is the barycentric coordinate
+ *               of stored vertex a on triangle t, zero elsewhere
+ *               (discontinuous piecewise linear)
+ *      BEM_P1   one per vertex, the continuous hat function; its matrix is
+ *               C^T A_DP1 C with C[3 t + a, v] = 1 where T[t][a] = v, i.e.
+ *               the global assembly of the element pairs' local matrices
+ *               (Sec. 3.2.3, "Global matrix assembly")
  *  - Operators (Sec. 2, Eq. (1)-(3) with g of Eq. (5), k = 0 for Laplace):
  *      BEM_SLP  single layer          int int psi_i g phi_j
  *      BEM_DLP  double layer          int int psi_i dg/dn_y phi_j
  *      BEM_ADLP adjoint double layer  int int psi_i dg/dn_x phi_j
+ *      BEM_HYPS hypersingular (Eq. (4)), P1 only, applied as
+ *               D = sum_j Q_j^T S Q_j - k^2 sum_j P_j^T S P_j with S the single
+ *               layer on DP1, Q_j the j-th component of the surface curl and
+ *               P_j the j-th normal component (Eq. (9), Sec. 5.1)
  *    Values are f64 for k == 0 and interleaved complex128 (re, im) for k != 0.
  *  - Quadrature: pairs that share no vertex use the symmetric 6-point
  *    degree-4 triangle rule in both triangles (Sec. 3.2.1, Sec. 3.2.3);
@@ -48,7 +60,8 @@ extern "C" {
 typedef struct bem_mesh_s *bem_mesh;
 typedef struct bem_hmat_s *bem_hmat;
 
-enum bem_op { BEM_SLP = 0, BEM_DLP = 1, BEM_ADLP = 2 };
+enum bem_op { BEM_SLP = 0, BEM_DLP = 1, BEM_ADLP = 2, BEM_HYPS = 3 };
+enum bem_space { BEM_P0 = 0, BEM_DP1 = 1, BEM_P1 = 2 };
 enum bem_prec { BEM_FP64 = 0, BEM_MIXED = 1 };
 enum bem_status {
     BEM_OK = 0,
@@ -157,6 +170,18 @@ int bem_entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec,
                         const int32_t *test_ids, int64_t n_test, const int32_t *trial_ids,
                         int64_t n_trial, void *out, void *cuda_stream);
 
+/* Dense DP1 sub-block for triangle lists (Sec. 3.3, Algorithm "Integral
+ * Evaluation": every combination of local dofs of an element pair):
+ *   out[3 a + alpha][3 b + beta] = int_{T_i} int_{T_j} lambda_alpha g' lambda_beta,
+ *   i = test_tris[a], j = trial_tris[b], row-major [3 n_test][3 n_trial],
+ * with lambda the barycentric coordinates of the stored vertices and g' the
+ * kernel of op (BEM_SLP, BEM_DLP or BEM_ADLP).  Same quadrature, precision,
+ * argument rules, scratch and synchronisation as bem_entries; touching pairs
+ * use the Sauter-Schwab rule with the basis functions at the mapped points. */
+int bem_entries_dp1(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t *test_tris,
+                    int64_t n_test, const int32_t *trial_tris, int64_t n_trial, void *out,
+                    void *cuda_stream);
+
 /* ---------------------------------------------------------------------- */
 /* Hierarchical matrices (Sec. 2.1; Algorithm "H-Matrix Assembly", Sec. 4.1)*/
 /* ---------------------------------------------------------------------- */
@@ -176,6 +201,19 @@ int bem_entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec,
  * The handle keeps a reference to the mesh.  Synchronous. */
 int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out);
 
+/* hmat_build_tree for a space (BEM_P0, BEM_DP1 or BEM_P1).  The piecewise
+ * linear spaces use the same cluster and block trees, every triangle carrying
+ * its three DP1 dofs: a block of triangle ranges is the block of the tripled
+ * dof ranges (dof 3 p + a of cluster position p), so leaf_size counts
+ * triangles.  BEM_P1 handles hold the DP1 matrix and apply C and C^T around
+ * it in hmat_matvec.  hmat_build_tree(...) == hmat_build_tree_space(..., BEM_P0). */
+int hmat_build_tree_space(bem_mesh mesh, int32_t leaf_size, double eta, int32_t space,
+                          bem_hmat *out);
+
+/* Length of the vectors of hmat_matvec: triangles (P0), 3 x triangles (DP1)
+ * or vertices (P1); -1 for a null handle. */
+int64_t hmat_dofs(bem_hmat hmat);
+
 /* Assembles the H-matrix of operator op and wavenumber k on the device:
  * dense near-field blocks (regular pairs by Gauss, singular pairs by
  * Sauter-Schwab) and, for every admissible block, ACA with partial pivoting
@@ -186,6 +224,8 @@ int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
  * largest pivot so far "vanishes" and the smallest unused row is taken next;
  * the loop stops once ||u_k|| ||v_k|| <= aca_eps ||S_k||_F, or when k reaches
  * min(m, n) or the rank cap, or when all rows are used.
+ *  op       BEM_SLP, BEM_DLP, BEM_ADLP; BEM_HYPS on BEM_P1 handles (the
+ *           single layer on DP1 is assembled, the rest is applied in products)
  *  aca_eps  > 0
  *  prec     BEM_FP64 or BEM_MIXED (see the top of this file)
  * May be called again on the same handle (the previous matrix is replaced).
@@ -194,11 +234,13 @@ int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
 int hmat_assemble(bem_hmat hmat, int32_t op, double k, double aca_eps, int32_t prec,
                   void *cuda_stream);
 
-/* y = A x for the assembled H-matrix, in the original triangle order
- * (the cluster permutation is applied inside).  x and y hold `batch`
- * vectors one after another, each n_triangles long, f64 for k == 0 and
- * complex128 otherwise; host or device memory.  Uses buffers owned by the
- * handle: concurrent products on one handle must be on the same stream.
+/* y = A x for the assembled H-matrix, in the original dof order (the
+ * cluster permutation is applied inside).  x and y hold `batch` vectors one
+ * after another, each hmat_dofs() long (triangles, DP1 dofs 3 t + a, or
+ * vertices), f64 for k == 0 and complex128 otherwise; host or device memory.
+ * P1: y = C^T A_DP1 C x; BEM_HYPS: D x by Eq. (9) with three DP1
+ * products for k = 0 and six otherwise.  Uses buffers owned by the handle:
+ * concurrent products on one handle must be on the same stream.
  * BEM_E_STATE before hmat_assemble. */
 int hmat_matvec(bem_hmat hmat, const void *x, void *y, int32_t batch, void *cuda_stream);
 
@@ -227,6 +269,8 @@ typedef struct {
     double k;
     double aca_eps;
     int32_t prec;
+    int32_t space;               /* BEM_P0, BEM_DP1, BEM_P1 */
+    int64_t n_dofs;              /* hmat_dofs() */
 } bem_hmat_stats;
 
 /* Copies statistics of the handle into *out. */
@@ -236,13 +280,14 @@ int hmat_stats(bem_hmat hmat, bem_hmat_stats *out);
  * (tau_begin, tau_end, sigma_begin, sigma_end, admissible) into host
  * `blocks` (capacity `cap` rows) and the permutation (cluster position ->
  * triangle id) into host `perm` (n_triangles).  *n_blocks receives the
- * number of blocks; BEM_E_ARG if cap is too small. */
+ * number of blocks; BEM_E_ARG if cap is too small.  For DP1 and P1 handles
+ * the ranges are DP1 dof ranges (three dofs per cluster position). */
 int hmat_blocks(bem_hmat hmat, int64_t *blocks, int64_t cap, int64_t *n_blocks, int32_t *perm);
 
 /* Copies one assembled block to host memory as a dense row-major m x n
  * array in cluster order (f64 or complex128): the near-field entries, or
  * U V^T for an admissible block; *rank receives its ACA rank (-1 for a
- * dense block). */
+ * dense block).  DP1 and P1 handles: DP1 dofs, as in hmat_blocks. */
 int hmat_block_dense(bem_hmat hmat, int64_t block, void *out, int32_t *rank);
 
 /* Frees the handle and its device memory. */

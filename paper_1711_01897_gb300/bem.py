@@ -18,8 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbem.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "bem.h")
 
-SLP, DLP, ADLP = 0, 1, 2
+SLP, DLP, ADLP, HYPS = 0, 1, 2, 3
 FP64, MIXED = 0, 1
+P0, DP1, P1 = 0, 1, 2
 STATUS = {0: "BEM_OK", 1: "BEM_E_ARG", 2: "BEM_E_MESH", 3: "BEM_E_OOM", 4: "BEM_E_CUDA",
           5: "BEM_E_TIMEOUT", 6: "BEM_E_STATE"}
 
@@ -45,7 +46,8 @@ class HmatStats(ctypes.Structure):
                 ("time_near_regular_ms", ctypes.c_double), ("time_singular_ms", ctypes.c_double),
                 ("aca_fp64_fma", ctypes.c_int64),
                 ("assembled", ctypes.c_int32), ("op", ctypes.c_int32), ("k", ctypes.c_double),
-                ("aca_eps", ctypes.c_double), ("prec", ctypes.c_int32)]
+                ("aca_eps", ctypes.c_double), ("prec", ctypes.c_int32),
+                ("space", ctypes.c_int32), ("n_dofs", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
@@ -106,7 +108,10 @@ def load(path: str = LIB_PATH):
             "bem_mesh_destroy": ([P], ctypes.c_int),
             "bem_mesh_size": ([P], i64),
             "bem_entries": ([P, i32, dbl, i32, P, i64, P, i64, P, P], ctypes.c_int),
+            "bem_entries_dp1": ([P, i32, dbl, i32, P, i64, P, i64, P, P], ctypes.c_int),
             "hmat_build_tree": ([P, i32, dbl, P], ctypes.c_int),
+            "hmat_build_tree_space": ([P, i32, dbl, i32, P], ctypes.c_int),
+            "hmat_dofs": ([P], i64),
             "hmat_assemble": ([P, i32, dbl, dbl, i32, P], ctypes.c_int),
             "hmat_matvec": ([P, P, P, i32, P], ctypes.c_int),
             "hmat_stats": ([P, ctypes.POINTER(HmatStats)], ctypes.c_int),
@@ -222,10 +227,31 @@ def bem_entries(mesh, op: int, k: float, prec: int, test_ids, trial_ids, out, st
     return out
 
 
+def bem_entries_dp1(mesh, op: int, k: float, prec: int, test_tris, trial_tris, out, stream=None):
+    pt, kt = _ptr(test_tris)
+    pj, kj = _ptr(trial_tris)
+    po, ko = _ptr(out)
+    _check(load().bem_entries_dp1(mesh, op, float(k), prec, pt, len(test_tris), pj,
+                                  len(trial_tris), po, _stream(stream)))
+    del kt, kj, ko
+    return out
+
+
 def hmat_build_tree(mesh, leaf_size: int, eta: float):
     h = ctypes.c_void_p()
     _check(load().hmat_build_tree(mesh, int(leaf_size), float(eta), ctypes.byref(h)))
     return h
+
+
+def hmat_build_tree_space(mesh, leaf_size: int, eta: float, space: int):
+    h = ctypes.c_void_p()
+    _check(load().hmat_build_tree_space(mesh, int(leaf_size), float(eta), int(space),
+                                        ctypes.byref(h)))
+    return h
+
+
+def hmat_dofs(hmat) -> int:
+    return int(load().hmat_dofs(hmat))
 
 
 def hmat_assemble(hmat, op: int, k: float, aca_eps: float, prec: int, stream=None):
@@ -284,6 +310,12 @@ class Mesh:
                            dtype=np.complex128 if k != 0 else np.float64)
         return bem_entries(self.handle, op, k, prec, test_ids, trial_ids, out, stream)
 
+    def entries_dp1(self, op, k, prec, test_tris, trial_tris, out=None, stream=None):
+        if out is None:
+            out = np.zeros((3 * len(test_tris), 3 * len(trial_tris)),
+                           dtype=np.complex128 if k != 0 else np.float64)
+        return bem_entries_dp1(self.handle, op, k, prec, test_tris, trial_tris, out, stream)
+
     def close(self):
         if self.handle is not None:
             bem_mesh_destroy(self.handle)
@@ -299,9 +331,14 @@ class Mesh:
 class HMatrix:
     """Owns a bem_hmat handle built on a Mesh."""
 
-    def __init__(self, mesh: Mesh, leaf_size: int = 32, eta: float = 1.2):
+    def __init__(self, mesh: Mesh, leaf_size: int = 32, eta: float = 1.2, space: int = P0):
         self.mesh = mesh
-        self.handle = hmat_build_tree(mesh.handle, leaf_size, eta)
+        self.space = space
+        if space == P0:
+            self.handle = hmat_build_tree(mesh.handle, leaf_size, eta)
+        else:
+            self.handle = hmat_build_tree_space(mesh.handle, leaf_size, eta, space)
+        self.n = hmat_dofs(self.handle)
         self.cplx = False
 
     def assemble(self, op, k, aca_eps, prec, stream=None):

@@ -38,10 +38,14 @@ constexpr int kTileFields = 32;
 constexpr int kFCh = 0, kFCl = 3, kFQ = 6, kFN = 6 + 3 * NQ, kFS = kFN + 3, kFId = kFS + 2;
 static_assert(kFId + 3 == kTileFields, "tile fields");
 
-// Regular rule: reference points and weights (sum 1).
+// Regular rule: reference points and weights (sum 1); wl[p][a] = w_p lambda_a(p)
+// with lambda = (1 - s - t, s, t) the barycentric coordinates of point p, the
+// weights of the piecewise linear local basis functions.
 struct QuadRule {
     double s[NQ], t[NQ], w[NQ];
     float wf[NQ];
+    double wl[NQ][3];
+    float wlf[NQ][3];
 };
 
 // Singular rule tables for one case (1 vertex-, 2 edge-adjacent, 3
@@ -53,17 +57,29 @@ struct QuadRule {
 //  helm: all maps are homogeneous of degree one in xi, so the table lists
 //        the eta nodes (rows c0..c3 of d/xi and w_eta = weights times the
 //        eta part of the Jacobian) and the xi axis is summed in the kernel.
+//  xy:   for the same eta nodes, the reference points divided by xi,
+//        rows X1, X2, Y1, Y2 (x^ = xi X, y^ = xi Y), for the linear basis
+//        functions of the piecewise linear spaces.
 struct SingTable {
     int n_lap;
     int n_helm;
     const double *lap;     // [6][n_lap]
     const double *helm;    // [5][n_helm]
+    const double *xy;      // [4][n_helm]
     double xi[NGL], wxi[NGL];
 };
 
 struct SingPair {
     int32_t i, j;          // triangle ids in the mesh's own order
     int64_t dest;          // element offset of the result
+};
+
+// A touching pair of a piecewise linear matrix: its 3 x 3 local matrix goes to
+// dest + alpha * ld + beta (alpha, beta: stored vertex indices).
+struct SingPairL {
+    int32_t i, j;
+    int64_t dest;
+    int64_t ld;
 };
 
 struct FarBlock {
@@ -148,10 +164,46 @@ cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, 
                                 const NearBlock *blocks, int64_t nblocks, void *out,
                                 cudaStream_t st);
 
+// Piecewise linear (DP1) counterparts: local 3 x 3 matrices of element pairs.
+// Entries of triangle lists: out is [3 n_test][3 n_trial].
+cudaError_t launch_entries_dp1(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
+                               const int32_t *test, int64_t n_test, const int32_t *trial,
+                               int64_t n_trial, void *out, SingPairL *lists[3],
+                               unsigned long long *counts, unsigned long long cap, int *err,
+                               cudaStream_t st);
+cudaError_t launch_singular_dp1(const DevGeom &g, const SingTable *tabs, int op, double k,
+                                const SingPairL *pairs[3], const unsigned long long *dev_counts,
+                                const int64_t host_counts[3], void *out, cudaStream_t st);
+// Continuous P1 around a DP1 matrix: x_dp1 = C x, y = C^T y_dp1; and the
+// hypersingular operator through the DP1 single layer, Eq. (9):
+// xs = (Q_1 x, Q_2 x, Q_3 x[, P_1 x, P_2 x, P_3 x]) (nvec = 3 for k = 0, else
+// 6), y = sum_j Q_j^T ys_j - k^2 sum_j P_j^T ys_{3+j}.  g in the mesh's order.
+cudaError_t launch_p1_gather(bool cplx, const int32_t *tri, int64_t nt, const void *x, void *xd,
+                             cudaStream_t st);
+cudaError_t launch_p1_scatter(bool cplx, const int64_t *vptr, const int32_t *vdof, int64_t nv,
+                              const void *yd, void *y, cudaStream_t st);
+cudaError_t launch_hyps_in(bool cplx, const DevGeom &g, const void *x, void *xs, int nvec,
+                           cudaStream_t st);
+cudaError_t launch_hyps_out(bool cplx, const int64_t *vptr, const int32_t *vdof, const DevGeom &g,
+                            int64_t nv, double k, const void *ys, int nvec, void *y,
+                            cudaStream_t st);
+// near-field blocks in dof units (ranges are three times the triangle ranges)
+cudaError_t launch_near_dp1(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
+                            const NearBlock *blocks, int64_t nblocks, void *out, cudaStream_t st);
+
+// dofs = 1: P0 (a dof per triangle); dofs = 3: DP1 (block ranges in dof
+// units, three local dofs per triangle)
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                        double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
                        int64_t n_small, int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
-                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st);
+                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st, int dofs = 1);
+
+// the DP1 instantiations (kernels_aca_dp1.cu); no tiny-block class
+cudaError_t launch_aca_dp1(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
+                           double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
+                           int64_t n_small, int64_t max_m_big, int64_t max_m_small,
+                           void *pool_data, Pool *pool, AcaQueue *queue, int num_sms,
+                           cudaStream_t st);
 
 // After an ACA launch: toff[b] = sum of ranks of blocks < b (toff[n] = total)
 // and the totals in *st.  tile_sums needs aca_finish_tiles(n) entries.

@@ -234,6 +234,10 @@ QuadRule make_rule6()
             R.t[k] = bary[m][2];
             R.w[k] = ow[o];
             R.wf[k] = (float)ow[o];
+            for (int a = 0; a < 3; ++a) {
+                R.wl[k][a] = ow[o] * bary[m][a];
+                R.wlf[k][a] = (float)R.wl[k][a];
+            }
         }
     }
     return R;
@@ -280,7 +284,7 @@ void ss_coef(int c, const double X[2], const double Y[2], double cf[4])
 }
 
 struct HostSingTable {
-    std::vector<double> lap, helm;  // row-major [6][n_lap], [5][n_helm]
+    std::vector<double> lap, helm, xy;  // row-major [6][n_lap], [5][n_helm], [4][n_helm]
     int n_lap = 0, n_helm = 0;
 };
 
@@ -324,6 +328,7 @@ HostSingTable make_sing_table(int c, const double *x, const double *w)
     // Helmholtz: eta nodes at xi = 1 (all maps are homogeneous in xi)
     T.n_helm = R * NGL * NGL * NGL;
     T.helm.assign(5 * T.n_helm, 0.0);
+    T.xy.assign(4 * T.n_helm, 0.0);
     int q = 0;
     for (int r = 0; r < R; ++r)
         for (int i1 = 0; i1 < NGL; ++i1)
@@ -334,6 +339,10 @@ HostSingTable make_sing_table(int c, const double *x, const double *w)
                     ss_coef(c, X, Y, cf);
                     for (int rr = 0; rr < 4; ++rr) T.helm[rr * T.n_helm + q] = cf[rr];
                     T.helm[4 * T.n_helm + q] = w[i1] * w[i2] * w[i3] * J;
+                    T.xy[0 * T.n_helm + q] = X[0];
+                    T.xy[1 * T.n_helm + q] = X[1];
+                    T.xy[2 * T.n_helm + q] = Y[0];
+                    T.xy[3 * T.n_helm + q] = Y[1];
                 }
     return T;
 }
@@ -342,7 +351,7 @@ HostSingTable make_sing_table(int c, const double *x, const double *w)
 struct DeviceConsts {
     QuadRule rule;
     SingTable sing[3];
-    DBuf bufs[6];
+    DBuf bufs[9];
     int num_sms = 0;
 };
 
@@ -365,15 +374,18 @@ DeviceConsts &device_consts()
         // the singular kernel stages a table of at most 6 * NGL^3 points
         if (H.n_lap > 6 * NGL * NGL * NGL || H.n_helm > 6 * NGL * NGL * NGL)
             throw std::runtime_error("singular quadrature table too large");
-        DBuf &bl = D->bufs[2 * (c - 1)], &bh = D->bufs[2 * (c - 1) + 1];
+        DBuf &bl = D->bufs[3 * (c - 1)], &bh = D->bufs[3 * (c - 1) + 1],
+             &bx = D->bufs[3 * (c - 1) + 2];
         bl.upload(H.lap);
         bh.upload(H.helm);
+        bx.upload(H.xy);
         CU(cudaStreamSynchronize(0));
         SingTable &S = D->sing[c - 1];
         S.n_lap = H.n_lap;
         S.n_helm = H.n_helm;
         S.lap = bl.as<double>();
         S.helm = bh.as<double>();
+        S.xy = bx.as<double>();
         for (int i = 0; i < NGL; ++i) {
             S.xi[i] = x[i];
             S.wxi[i] = w[i];
@@ -707,6 +719,82 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
     });
 }
 
+int bem_entries_dp1(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t *test_tris,
+                    int64_t n_test, const int32_t *trial_tris, int64_t n_trial, void *out,
+                    void *cuda_stream)
+{
+    return guarded([&]() -> int {
+        if (!mesh) return fail(BEM_E_ARG, "null mesh");
+        if (op < 0 || op > 2) return fail(BEM_E_ARG, "bad op");
+        if (prec != BEM_FP64 && prec != BEM_MIXED) return fail(BEM_E_ARG, "bad prec");
+        if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
+        if (n_test < 0 || n_trial < 0) return fail(BEM_E_ARG, "negative size");
+        if (n_test == 0 || n_trial == 0) return BEM_OK;
+        if (!test_tris || !trial_tris || !out) return fail(BEM_E_ARG, "null array");
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        DeviceConsts &D = device_consts();
+        const bool cplx = k != 0.0;
+        const size_t esz = cplx ? 16 : 8;
+        const int64_t nout = 9 * n_test * n_trial;
+        DBuf sti, stj, sto;
+        const int32_t *dti = test_tris, *dtj = trial_tris;
+        void *dout = out;
+        const bool host_out = !is_device_ptr(out);
+        if (!is_device_ptr(test_tris)) {
+            for (int64_t a = 0; a < n_test; ++a)
+                if (test_tris[a] < 0 || test_tris[a] >= mesh->nt)
+                    return fail(BEM_E_ARG, "test id out of range");
+            sti.alloc(n_test * 4, st);
+            CU(cudaMemcpyAsync(sti.p, test_tris, n_test * 4, cudaMemcpyHostToDevice, st));
+            dti = sti.as<int32_t>();
+        }
+        if (!is_device_ptr(trial_tris)) {
+            for (int64_t b = 0; b < n_trial; ++b)
+                if (trial_tris[b] < 0 || trial_tris[b] >= mesh->nt)
+                    return fail(BEM_E_ARG, "trial id out of range");
+            stj.alloc(n_trial * 4, st);
+            CU(cudaMemcpyAsync(stj.p, trial_tris, n_trial * 4, cudaMemcpyHostToDevice, st));
+            dtj = stj.as<int32_t>();
+        }
+        if (host_out) {
+            sto.alloc(nout * esz, st);
+            dout = sto.p;
+        }
+        // scratch: touching-pair lists (one per case), counters, error flag
+        const unsigned long long cap = (unsigned long long)std::min<int64_t>(
+            n_test * n_trial, n_test * std::max<int64_t>(mesh->max_touch, 1));
+        const size_t list_bytes = cap * sizeof(SingPairL);
+        void *ws = nullptr;
+        CU(cudaMallocAsync(&ws, 3 * list_bytes + 64, st));
+        unsigned char *wb = (unsigned char *)ws;
+        SingPairL *lists[3] = {(SingPairL *)wb, (SingPairL *)(wb + list_bytes),
+                               (SingPairL *)(wb + 2 * list_bytes)};
+        unsigned long long *counts = (unsigned long long *)(wb + 3 * list_bytes);
+        int *err = (int *)(counts + 3);
+        cudaError_t e = cudaMemsetAsync(counts, 0, 64, st);
+        if (e == cudaSuccess)
+            e = launch_entries_dp1(mesh->geom.g, D.rule, op, k, prec, dti, n_test, dtj, n_trial,
+                                   dout, lists, counts, cap, err, st);
+        const SingPairL *cl[3] = {lists[0], lists[1], lists[2]};
+        const int64_t hc[3] = {(int64_t)cap, (int64_t)cap, (int64_t)cap};
+        if (e == cudaSuccess)
+            e = launch_singular_dp1(mesh->geom.g, D.sing, op, k, cl, counts, hc, dout, st);
+        int herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && host_out)
+            e = cudaMemcpyAsync(out, dout, nout * esz, cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(ws, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            g_err = std::string("bem_entries_dp1: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? BEM_E_OOM : BEM_E_CUDA;
+        }
+        if (herr == 1) return fail(BEM_E_ARG, "triangle id out of range");
+        if (herr == 2) return fail(BEM_E_CUDA, "singular pair list overflow");
+        return BEM_OK;
+    });
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -726,6 +814,17 @@ struct bem_hmat_s {
     bem_mesh mesh = nullptr;
     int leaf = 0;
     double eta = 0;
+    // function space: BEM_P0 (a dof per triangle) or the piecewise linear
+    // spaces, held as DP1 (three local dofs per triangle: dof 3 t + a is the
+    // local basis function of vertex a of triangle t); BEM_P1 applies the
+    // continuous space's transforms around the DP1 matrix in products
+    int space = BEM_P0;
+    int dofs = 1;
+    int64_t ndof = 0;                     // length of the internal vectors
+    std::vector<int32_t> dperm;           // dof permutation (DP1): cluster dof -> mesh dof
+    std::vector<SingPairL> singl[3];      // touching pairs of the DP1 near field
+    std::vector<int64_t> vptr;            // P1: per vertex, its DP1 dofs (CSR, mesh order)
+    std::vector<int32_t> vdof;
     int64_t small_max = 8192;             // blocks with max(m, n) <= this run on one warp
     int64_t tiny_max = 0;                 // ... and with max(m, n) <= this on one lane
     std::vector<int32_t> perm, iperm;
@@ -744,6 +843,7 @@ struct bem_hmat_s {
     DBuf d_perm, d_near, d_far, d_chunks, d_sing[3], d_leaf_rows, d_leaf_ptr, d_leaf_items, d_long, d_long_off;
     std::vector<int64_t> long_ids;        // admissible blocks with long columns (matvec)
     DBuf d_near_data, d_pool, d_poolhdr, d_queue, d_toff, d_xt, d_yt, d_tbuf, d_x, d_y;
+    DBuf d_dperm, d_singl[3], d_vptr, d_vdof, d_xs, d_ys;
     GeomStore geom;                       // cluster order
     // assembled state
     bool assembled = false;
@@ -906,9 +1006,9 @@ void build_lists(bem_hmat_s &H)
         if (!H.blocks[b].adm) {
             H.near.push_back({T.b, T.e, S.b, S.e, off});
             H.near_block_id.push_back(b);
-            off += m * n;
+            off += m * n * H.dofs * H.dofs;
         } else {
-            const int64_t mx = std::max(m, n);
+            const int64_t mx = std::max(m, n) * H.dofs;
             const uint64_t cls = mx > H.small_max ? 0 : mx > H.tiny_max ? 1 : 2;
             ++ncls[cls];
             key.push_back(cls << 62 | (kSizeMask - (uint64_t)(m + n)) << 32 | (uint64_t)b);
@@ -988,7 +1088,9 @@ void build_lists(bem_hmat_s &H)
     for (int8_t c : M.adj_case) ++ncase[c - 1];
     for (int c = 0; c < 3; ++c) {
         H.sing[c].clear();
-        H.sing[c].reserve(ncase[c]);
+        H.singl[c].clear();
+        if (H.dofs == 1) H.sing[c].reserve(ncase[c]);
+        else H.singl[c].reserve(ncase[c]);
     }
     for (int64_t p = 0; p < nt; ++p) {
         const int32_t t = H.perm[p];
@@ -1002,9 +1104,48 @@ void build_lists(bem_hmat_s &H)
             if (it == b0) throw std::runtime_error("touching pair outside the near field");
             const NearBlock &N = H.near[nq[nptr[l] + (it - 1 - b0)]];
             if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
-            const int64_t dest = N.off + (p - N.tb) * (N.se - N.sb) + (q - N.sb);
-            H.sing[M.adj_case[a] - 1].push_back({t, u, dest});
+            if (H.dofs == 1) {
+                const int64_t dest = N.off + (p - N.tb) * (N.se - N.sb) + (q - N.sb);
+                H.sing[M.adj_case[a] - 1].push_back({t, u, dest});
+            } else {
+                // local (0, 0) of the pair in the block of 3m x 3n dofs
+                const int64_t ld = 3 * (N.se - N.sb);
+                const int64_t dest = N.off + 3 * (p - N.tb) * ld + 3 * (q - N.sb);
+                H.singl[M.adj_case[a] - 1].push_back({t, u, dest, ld});
+            }
         }
+    }
+    if (H.dofs == 3) {
+        // every list in dof units: ranges times three
+        for (NearBlock &N : H.near) {
+            N.tb *= 3;
+            N.te *= 3;
+            N.sb *= 3;
+            N.se *= 3;
+        }
+        for (FarBlock &F : H.far) {
+            F.tb *= 3;
+            F.te *= 3;
+            F.sb *= 3;
+            F.se *= 3;
+        }
+        for (int64_t &r : H.leaf_rows) r *= 3;
+        H.max_m_big *= 3;
+        H.max_m_small *= 3;
+        H.dperm.resize(3 * nt);
+        for (int64_t p = 0; p < nt; ++p)
+            for (int a = 0; a < 3; ++a) H.dperm[3 * p + a] = 3 * H.perm[p] + a;
+    }
+    H.ndof = H.dofs * nt;
+    if (H.space == BEM_P1) {
+        // vertex -> its DP1 dofs 3 t + a (T[t][a] = v), in increasing dof order
+        const int64_t nv = M.nv;
+        H.vptr.assign(nv + 1, 0);
+        for (int64_t q = 0; q < 3 * nt; ++q) ++H.vptr[M.T[q] + 1];
+        for (int64_t v = 0; v < nv; ++v) H.vptr[v + 1] += H.vptr[v];
+        H.vdof.resize(3 * nt);
+        std::vector<int64_t> fill(H.vptr.begin(), H.vptr.end() - 1);
+        for (int64_t q = 0; q < 3 * nt; ++q) H.vdof[fill[M.T[q]]++] = (int32_t)q;
     }
 }
 
@@ -1015,6 +1156,14 @@ void upload_tree(bem_hmat_s &H, cudaStream_t st)
     H.d_far.upload(H.far, st);
     H.d_chunks.alloc(H.far.size() * sizeof(FarChunks), st);
     for (int c = 0; c < 3; ++c) H.d_sing[c].upload(H.sing[c], st);
+    if (H.dofs == 3) {
+        H.d_dperm.upload(H.dperm, st);
+        for (int c = 0; c < 3; ++c) H.d_singl[c].upload(H.singl[c], st);
+    }
+    if (H.space == BEM_P1) {
+        H.d_vptr.upload(H.vptr, st);
+        H.d_vdof.upload(H.vdof, st);
+    }
     H.d_leaf_rows.upload(H.leaf_rows, st);
     H.d_leaf_ptr.upload(H.leaf_ptr, st);
     H.d_leaf_items.upload(H.leaf_items, st);
@@ -1045,7 +1194,7 @@ namespace bem {
 // Tree build on the host, uploads and geometry on stream st (none for
 // st == kHostOnly).
 int hmat_build_tree_impl(bem_mesh mesh, int32_t leaf_size, double eta, cudaStream_t st,
-                         bem_hmat *out)
+                         bem_hmat *out, int32_t space)
 {
     return guarded([&]() -> int {
         if (!out) return fail(BEM_E_ARG, "out is null");
@@ -1053,15 +1202,19 @@ int hmat_build_tree_impl(bem_mesh mesh, int32_t leaf_size, double eta, cudaStrea
         if (!mesh) return fail(BEM_E_ARG, "null mesh");
         if (leaf_size < 1) return fail(BEM_E_ARG, "leaf_size must be >= 1");
         if (!(eta > 0) || !std::isfinite(eta)) return fail(BEM_E_ARG, "eta must be > 0");
+        if (space != BEM_P0 && space != BEM_DP1 && space != BEM_P1)
+            return fail(BEM_E_ARG, "bad space");
         double t0 = now_ms();
         auto H = std::make_unique<bem_hmat_s>();
         H->mesh = mesh;
         H->leaf = leaf_size;
         H->eta = eta;
+        H->space = space;
+        H->dofs = space == BEM_P0 ? 1 : 3;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             H->small_max = g_tuning.warp_max_rows;
-            H->tiny_max = g_tuning.lane_max_rows;
+            H->tiny_max = H->dofs == 1 ? g_tuning.lane_max_rows : 0;
         }
         build_clusters(*H);
         build_blocks(*H);
@@ -1114,18 +1267,35 @@ extern "C" {
 
 int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
 {
-    return hmat_build_tree_impl(mesh, leaf_size, eta, 0, out);
+    return hmat_build_tree_impl(mesh, leaf_size, eta, 0, out, BEM_P0);
+}
+
+int hmat_build_tree_space(bem_mesh mesh, int32_t leaf_size, double eta, int32_t space,
+                          bem_hmat *out)
+{
+    return hmat_build_tree_impl(mesh, leaf_size, eta, 0, out, space);
+}
+
+int64_t hmat_dofs(bem_hmat H)
+{
+    if (!H) return -1;
+    return H->space == BEM_P1 ? H->mesh->nv : H->ndof;
 }
 
 int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec, void *cuda_stream)
 {
     return guarded([&]() -> int {
         if (!H) return fail(BEM_E_ARG, "null hmat");
-        if (op < 0 || op > 2) return fail(BEM_E_ARG, "bad op");
+        if (op < 0 || op > 3) return fail(BEM_E_ARG, "bad op");
+        if (op == BEM_HYPS && H->space != BEM_P1)
+            return fail(BEM_E_ARG, "the hypersingular operator needs a BEM_P1 handle");
         if (prec != BEM_FP64 && prec != BEM_MIXED) return fail(BEM_E_ARG, "bad prec");
         if (!(aca_eps > 0) || !std::isfinite(aca_eps)) return fail(BEM_E_ARG, "aca_eps must be > 0");
         if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
         cudaStream_t st = (cudaStream_t)cuda_stream;
+        // the hypersingular operator is applied through the single layer on
+        // DP1 (Eq. (9)): that is the matrix assembled here
+        const int aop = op == BEM_HYPS ? BEM_SLP : op;
         DeviceConsts &D = device_consts();
         const bool cplx = k != 0.0;
         const size_t esz = cplx ? 16 : 8;
@@ -1158,7 +1328,7 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         {
             size_t fr = 0, tot = 0;
             if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-                const double margin = 4.0 * (1 << 30) + 5.0 * H->mesh->nt * esz;
+                const double margin = 4.0 * (1 << 30) + 17.0 * H->ndof * esz;
                 const int64_t avail =
                     (int64_t)(((double)fr + (double)H->d_pool.bytes - margin) / (double)esz);
                 want = std::min(want, avail);
@@ -1179,21 +1349,34 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             rec(ev[0]);
             CU(launch_aca_reset(H->d_poolhdr.as<Pool>(), (unsigned long long)H->pool_elems,
                                 H->d_queue.as<AcaQueue>(), H->d_acastats.as<AcaStats>(), st));
-            CU(launch_near_regular(H->geom.g, D.rule, op, k, prec, H->d_near.as<NearBlock>(),
+            if (H->dofs == 1) {
+                CU(launch_near_regular(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
+                                       (int64_t)H->near.size(), H->d_near_data.p, st));
+                rec(ev[3]);
+                const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
+                                         H->d_sing[2].as<SingPair>()};
+                int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
+                                 (int64_t)H->sing[2].size()};
+                CU(launch_singular(H->mesh->geom.g, D.sing, aop, k, sp, nullptr, hc,
+                                   H->d_near_data.p, st));
+            } else {
+                CU(launch_near_dp1(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
                                    (int64_t)H->near.size(), H->d_near_data.p, st));
-            rec(ev[3]);
-            const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
-                                     H->d_sing[2].as<SingPair>()};
-            int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
-                             (int64_t)H->sing[2].size()};
-            CU(launch_singular(H->mesh->geom.g, D.sing, op, k, sp, nullptr, hc, H->d_near_data.p,
-                               st));
+                rec(ev[3]);
+                const SingPairL *sp[3] = {H->d_singl[0].as<SingPairL>(),
+                                          H->d_singl[1].as<SingPairL>(),
+                                          H->d_singl[2].as<SingPairL>()};
+                int64_t hc[3] = {(int64_t)H->singl[0].size(), (int64_t)H->singl[1].size(),
+                                 (int64_t)H->singl[2].size()};
+                CU(launch_singular_dp1(H->mesh->geom.g, D.sing, aop, k, sp, nullptr, hc,
+                                       H->d_near_data.p, st));
+            }
             rec(ev[1]);
             if (!H->far.empty())
-                CU(launch_aca(H->geom.g, D.rule, op, k, prec, aca_eps, H->d_far.as<FarBlock>(),
+                CU(launch_aca(H->geom.g, D.rule, aop, k, prec, aca_eps, H->d_far.as<FarBlock>(),
                               H->d_chunks.as<FarChunks>(), H->n_big, H->n_small, H->n_tiny, H->max_m_big, H->max_m_small,
                               H->d_pool.p, H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(),
-                              D.num_sms, st));
+                              D.num_sms, st, H->dofs));
             rec(ev[2]);
             CU(launch_aca_finish(H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
                                  (int64_t)H->far.size(),
@@ -1275,10 +1458,20 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         H->factor_elems = (int64_t)ast.factor_elems;
         H->k2mn = (int64_t)ast.k2mn;
         H->far_result_valid = false;
-        const int64_t nt = H->mesh->nt;
-        if (H->d_xt.bytes < nt * esz) {
-            H->d_xt.alloc(nt * esz, st);
-            H->d_yt.alloc(nt * esz, st);
+        const int64_t nd = H->ndof;
+        if (H->d_xt.bytes < nd * esz) {
+            H->d_xt.alloc(nd * esz, st);
+            H->d_yt.alloc(nd * esz, st);
+        }
+        if (H->space == BEM_P1) {
+            // transformed vectors of the products: six DP1 vectors in and out
+            // (three curl components and three normal components, Eq. (9));
+            // one of each for SLP, DLP and ADLP
+            const size_t want_v = (size_t)(op == BEM_HYPS ? 6 : 1) * nd * esz;
+            if (H->d_xs.bytes < want_v) {
+                H->d_xs.alloc(want_v, st);
+                H->d_ys.alloc(want_v, st);
+            }
         }
         if (H->d_tbuf.bytes < (size_t)(H->rank_sum + 1) * esz)
             H->d_tbuf.alloc((size_t)(H->rank_sum + 1) * esz * 5 / 4, st);
@@ -1300,14 +1493,29 @@ int hmat_matvec(bem_hmat H, const void *x, void *y, int32_t batch, void *cuda_st
         if (batch == 0) return BEM_OK;
         if (!x || !y) return fail(BEM_E_ARG, "null vector");
         cudaStream_t st = (cudaStream_t)cuda_stream;
-        const int64_t nt = H->mesh->nt;
+        const int64_t nd = H->ndof;
+        const bool p1 = H->space == BEM_P1;
+        const int64_t nio = p1 ? H->mesh->nv : nd;  // length of the caller's vectors
         const size_t esz = H->cplx ? 16 : 8;
-        const size_t vb = nt * esz;
+        const size_t vb = nio * esz;
         const bool hx = !is_device_ptr(x), hy = !is_device_ptr(y);
         if ((hx || hy) && H->d_x.bytes < vb) {
             H->d_x.alloc(vb, st);
             H->d_y.alloc(vb, st);
         }
+        const int32_t *perm = H->dofs == 1 ? H->d_perm.as<int32_t>() : H->d_dperm.as<int32_t>();
+        // the DP1 (or P0) product in the mesh's dof order
+        auto apply = [&](const void *xi, void *yo) {
+            CU(launch_matvec(H->cplx, nd, perm, xi, yo, H->d_xt.p, H->d_yt.p, H->d_tbuf.p,
+                             H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
+                             (int64_t)H->far.size(), H->d_toff.as<int64_t>(), H->d_pool.p,
+                             H->d_near.as<NearBlock>(), H->d_near_data.p,
+                             H->d_leaf_rows.as<int64_t>(), H->d_leaf_ptr.as<int64_t>(),
+                             H->d_leaf_items.as<int64_t>(), (int64_t)(H->leaf_ptr.size() - 1),
+                             H->d_long.as<int64_t>(), (int64_t)H->long_ids.size(),
+                             H->d_long_off.as<int64_t>(), st));
+        };
+        const DevGeom &mg = H->mesh->geom.g;
         for (int32_t b = 0; b < batch; ++b) {
             const void *xb = (const char *)x + b * vb;
             void *yb = (char *)y + b * vb;
@@ -1318,14 +1526,21 @@ int hmat_matvec(bem_hmat H, const void *x, void *y, int32_t batch, void *cuda_st
                 dx = H->d_x.p;
             }
             if (hy) dy = H->d_y.p;
-            CU(launch_matvec(H->cplx, nt, H->d_perm.as<int32_t>(), dx, dy, H->d_xt.p, H->d_yt.p,
-                             H->d_tbuf.p, H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
-                             (int64_t)H->far.size(),
-                             H->d_toff.as<int64_t>(), H->d_pool.p, H->d_near.as<NearBlock>(),
-                             H->d_near_data.p, H->d_leaf_rows.as<int64_t>(),
-                             H->d_leaf_ptr.as<int64_t>(), H->d_leaf_items.as<int64_t>(),
-                             (int64_t)(H->leaf_ptr.size() - 1), H->d_long.as<int64_t>(),
-                             (int64_t)H->long_ids.size(), H->d_long_off.as<int64_t>(), st));
+            if (!p1) {
+                apply(dx, dy);
+            } else if (H->op != BEM_HYPS) {
+                CU(launch_p1_gather(H->cplx, mg.tri, mg.nt, dx, H->d_xs.p, st));
+                apply(H->d_xs.p, H->d_ys.p);
+                CU(launch_p1_scatter(H->cplx, H->d_vptr.as<int64_t>(), H->d_vdof.as<int32_t>(),
+                                     nio, H->d_ys.p, dy, st));
+            } else {
+                const int nvec = H->k != 0.0 ? 6 : 3;
+                CU(launch_hyps_in(H->cplx, mg, dx, H->d_xs.p, nvec, st));
+                for (int j = 0; j < nvec; ++j)
+                    apply(H->d_xs.as<char>() + j * nd * esz, H->d_ys.as<char>() + j * nd * esz);
+                CU(launch_hyps_out(H->cplx, H->d_vptr.as<int64_t>(), H->d_vdof.as<int32_t>(), mg,
+                                   nio, H->k, H->d_ys.p, nvec, dy, st));
+            }
             if (hy) CU(cudaMemcpyAsync(yb, dy, vb, cudaMemcpyDeviceToHost, st));
         }
         if (hx || hy) CU(cudaStreamSynchronize(st));
@@ -1363,6 +1578,10 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         s.k = H->k;
         s.aca_eps = H->eps;
         s.prec = H->prec;
+        s.space = H->space;
+        s.n_dofs = H->space == BEM_P1 ? H->mesh->nv : H->ndof;
+        for (int c = 0; c < 3; ++c)
+            if (H->dofs == 3) s.singular_pairs[c] = (int64_t)H->singl[c].size();
         *out = s;
         return BEM_OK;
     });
@@ -1379,10 +1598,10 @@ int hmat_blocks(bem_hmat H, int64_t *blocks, int64_t cap, int64_t *n_blocks, int
         for (size_t b = 0; b < H->blocks.size(); ++b) {
             const Cluster &T = H->cl[H->blocks[b].tau], &S = H->cl[H->blocks[b].sigma];
             int64_t *r = blocks + 5 * b;
-            r[0] = T.b;
-            r[1] = T.e;
-            r[2] = S.b;
-            r[3] = S.e;
+            r[0] = T.b * H->dofs;
+            r[1] = T.e * H->dofs;
+            r[2] = S.b * H->dofs;
+            r[3] = S.e * H->dofs;
             r[4] = H->blocks[b].adm ? 1 : 0;
         }
         return BEM_OK;

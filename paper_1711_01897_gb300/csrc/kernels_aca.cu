@@ -12,693 +12,11 @@
 // vanishes if its maximum is 0 or <= 1e-14 * the largest pivot so far, and
 // then the smallest unused row is next; stop once ||u_k|| ||v_k|| <= eps
 // ||S_k||_F, or k = min(m, n), or all rows used, or k = KMAX (rank cap).
-#include <type_traits>
-
-#include "bem_device.cuh"
+#include "aca_kernel.cuh"
 
 namespace bem {
 
 namespace {
-
-constexpr int kAcaThreads = 256;
-constexpr int kWarps = kAcaThreads / 32;
-constexpr int kSmallCap = 8192;  // largest max(m, n) a single warp may take
-
-// 1/a by Newton-Raphson (r <- r + r (1 - a r)) from a single-precision
-// seed: the seed comes from the top 32 bits of a and the hardware's
-// approximate FP32 reciprocal, and two FP64 steps take its ~2^-20 relative
-// error to rounding level.  Four FP64 operations instead of a full division;
-// values outside the FP32 exponent range fall back to the division.
-__device__ __forceinline__ double recip(double a)
-{
-    const int hi = __double2hiint(a);
-    const int e = (hi >> 20) & 0x7ff;
-    if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / a;
-    const unsigned fb = ((unsigned)hi & 0x80000000u) | ((unsigned)(e - 896) << 23) |
-                        (((unsigned)hi & 0xfffffu) << 3);
-    float r0;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(__uint_as_float(fb)));
-    double r = f2d_exact(r0);
-    r = fma(r, fma(-a, r, 1.0), r);
-    r = fma(r, fma(-a, r, 1.0), r);
-    return r;
-}
-
-template <bool CPLX>
-struct VT;
-
-template <>
-struct VT<false> {
-    using T = double;
-    static __device__ __forceinline__ T from(C2 v) { return v.re; }
-    static __device__ __forceinline__ T zero() { return 0.0; }
-    static __device__ __forceinline__ double mag(T a) { return fabs(a); }
-    // key ordered like |a|; mag_of_key recovers |a|
-    static __device__ __forceinline__ long long key(T a)
-    {
-        return __double_as_longlong(a) & 0x7fffffffffffffffll;  // |a| without FP64 work
-    }
-    static __device__ __forceinline__ double mag_of_key(long long k)
-    {
-        return __longlong_as_double(k);
-    }
-    // key of 1e-14 * |pivot| for the vanishing test
-    static __device__ __forceinline__ long long vanish_key(long long maxkey)
-    {
-        return __double_as_longlong(1e-14 * __longlong_as_double(maxkey));
-    }
-    static __device__ __forceinline__ double abs2(T a) { return a * a; }
-    static __device__ __forceinline__ T fnma(T a, T b, T c) { return fma(-a, b, c); }  // c - a b
-    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
-    static __device__ __forceinline__ T inv(T a) { return recip(a); }
-    static __device__ __forceinline__ T dotc(T a, T b, T acc) { return fma(a, b, acc); }  // conj(a) b
-    static __device__ __forceinline__ double re_mul(T a, T b) { return a * b; }
-    static __device__ __forceinline__ T shfl_down(T a, int o)
-    {
-        return __shfl_down_sync(0xffffffffu, a, o);
-    }
-    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
-};
-
-template <>
-struct VT<true> {
-    using T = double2;
-    static __device__ __forceinline__ T from(C2 v) { return make_double2(v.re, v.im); }
-    static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
-    static __device__ __forceinline__ double mag(T a) { return hypot(a.x, a.y); }
-    static __device__ __forceinline__ long long key(T a)
-    {
-        return __double_as_longlong(fma(a.x, a.x, a.y * a.y));
-    }
-    static __device__ __forceinline__ double mag_of_key(long long k)
-    {
-        return sqrt(__longlong_as_double(k));
-    }
-    static __device__ __forceinline__ long long vanish_key(long long maxkey)
-    {
-        return __double_as_longlong(1e-28 * __longlong_as_double(maxkey));  // squares
-    }
-    static __device__ __forceinline__ double abs2(T a) { return fma(a.x, a.x, a.y * a.y); }
-    static __device__ __forceinline__ T fnma(T a, T b, T c)
-    {
-        return make_double2(c.x - fma(a.x, b.x, -a.y * b.y), c.y - fma(a.x, b.y, a.y * b.x));
-    }
-    static __device__ __forceinline__ T mul(T a, T b)
-    {
-        return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-    }
-    static __device__ __forceinline__ T inv(T a)
-    {
-        double d = recip(fma(a.x, a.x, a.y * a.y));
-        return make_double2(a.x * d, -a.y * d);
-    }
-    static __device__ __forceinline__ T dotc(T a, T b, T acc)
-    {
-        return make_double2(acc.x + fma(a.x, b.x, a.y * b.y), acc.y + fma(a.x, b.y, -a.y * b.x));
-    }
-    static __device__ __forceinline__ double re_mul(T a, T b) { return fma(a.x, b.x, -a.y * b.y); }
-    static __device__ __forceinline__ T shfl_down(T a, int o)
-    {
-        return make_double2(__shfl_down_sync(0xffffffffu, a.x, o),
-                            __shfl_down_sync(0xffffffffu, a.y, o));
-    }
-    static __device__ __forceinline__ T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
-};
-
-// ---- groups: a whole CTA or a single warp ---------------------------------
-struct RedScratch {
-    double v[kWarps];
-    long long k[kWarps];
-    int64_t i[kWarps];
-    double s0[kWarps], s1[kWarps];
-};
-
-__device__ __forceinline__ void warp_argmax(double &v, int64_t &idx)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, v, o);
-        int64_t oi = __shfl_down_sync(0xffffffffu, idx, o);
-        if (ov > v || (ov == v && oi < idx)) {
-            v = ov;
-            idx = oi;
-        }
-    }
-    v = __shfl_sync(0xffffffffu, v, 0);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return __shfl_sync(0xffffffffu, v, 0);
-}
-
-// argmax on integer keys: for non-negative doubles the IEEE bit pattern
-// orders like the value, so the comparisons stay off the FP64 pipe
-__device__ __forceinline__ void warp_argmax_key(long long &key, int64_t &idx)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        long long ok = __shfl_down_sync(0xffffffffu, key, o);
-        int64_t oi = __shfl_down_sync(0xffffffffu, idx, o);
-        if (ok > key || (ok == key && oi < idx)) {
-            key = ok;
-            idx = oi;
-        }
-    }
-    key = __shfl_sync(0xffffffffu, key, 0);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-}
-
-struct WarpGroup {
-    int lane;
-    __device__ int rank() const { return lane; }
-    __device__ int size() const { return 32; }
-    __device__ int warp() const { return 0; }
-    __device__ int nwarps() const { return 1; }
-    __device__ void sync() const { __syncwarp(); }
-    __device__ void argmax(double &v, int64_t &idx) const { warp_argmax(v, idx); }
-    __device__ void argmax_key(long long &key, int64_t &idx) const { warp_argmax_key(key, idx); }
-    __device__ void sum2(double &a, double &b) const
-    {
-        a = warp_sum(a);
-        b = warp_sum(b);
-    }
-    __device__ double sum(double a) const { return warp_sum(a); }
-};
-
-struct CtaGroup {
-    RedScratch *red;
-    __device__ int rank() const { return threadIdx.x; }
-    __device__ int size() const { return blockDim.x; }
-    __device__ int warp() const { return threadIdx.x >> 5; }
-    __device__ int nwarps() const { return blockDim.x >> 5; }
-    __device__ void sync() const { __syncthreads(); }
-    __device__ void argmax(double &v, int64_t &idx) const
-    {
-        warp_argmax(v, idx);
-        int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        if (l == 0) {
-            red->v[w] = v;
-            red->i[w] = idx;
-        }
-        __syncthreads();
-        v = red->v[0];
-        idx = red->i[0];
-        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
-            double ov = red->v[q];
-            int64_t oi = red->i[q];
-            if (ov > v || (ov == v && oi < idx)) {
-                v = ov;
-                idx = oi;
-            }
-        }
-        __syncthreads();
-    }
-    __device__ void argmax_key(long long &key, int64_t &idx) const
-    {
-        warp_argmax_key(key, idx);
-        int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        if (l == 0) {
-            red->k[w] = key;
-            red->i[w] = idx;
-        }
-        __syncthreads();
-        key = red->k[0];
-        idx = red->i[0];
-        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
-            long long ok = red->k[q];
-            int64_t oi = red->i[q];
-            if (ok > key || (ok == key && oi < idx)) {
-                key = ok;
-                idx = oi;
-            }
-        }
-        __syncthreads();
-    }
-    __device__ void sum2(double &a, double &b) const
-    {
-        a = warp_sum(a);
-        b = warp_sum(b);
-        int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        if (l == 0) {
-            red->s0[w] = a;
-            red->s1[w] = b;
-        }
-        __syncthreads();
-        a = 0.0;
-        b = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-            a += red->s0[q];
-            b += red->s1[q];
-        }
-        __syncthreads();
-    }
-    __device__ double sum(double a) const
-    {
-        double b = 0.0;
-        sum2(a, b);
-        return a;
-    }
-};
-
-// Per-group shared state.
-template <bool CPLX>
-struct GroupSmem {
-    typename VT<CPLX>::T cu[KMAX];   // (u_l)_i of the current row / (v_l)_j of the column
-    int64_t chunk[NCHUNK];
-    int64_t scal;                   // broadcast slot
-    double uv2;                     // ||u_k||^2 ||v_k||^2 of the current step
-    int fail;
-};
-
-template <class Grp, int OP, bool CPLX, int PREC>
-__device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, double k, double eps,
-                          FarBlock *blk, FarChunks *chk, typename VT<CPLX>::T *pool, Pool *P,
-                          GroupSmem<CPLX> &S, unsigned *Z, typename VT<CPLX>::T *part)
-{
-    using V = VT<CPLX>;
-    using T = typename V::T;
-    using E = RegularEntry<OP, CPLX, PREC>;
-    const int64_t tb = blk->tb, sb = blk->sb;
-    const int64_t m = blk->te - tb, n = blk->se - sb;
-    const int t = G.rank(), GS = G.size();
-    const int64_t kmin = m < n ? m : n;
-    const int kcap = (int)(kmin < KMAX ? kmin : KMAX);
-    const int64_t zwords = (m + 31) >> 5;
-    for (int64_t w = t; w < zwords; w += GS) Z[w] = 0u;
-    if (t < NCHUNK) S.chunk[t] = -1;
-    if (t == 0) S.fail = 0;
-    G.sync();
-
-    int kk = 0, status = 0;
-    int nalloc = 0;  // chunks allocated so far (same value in every thread)
-    int64_t nZ = 0, i = 0, entries = 0;
-    double normS2 = 0.0;
-    const double eps2 = eps * eps;
-    long long maxkey = 0, vkey = 0;  // largest pivot so far, and 1e-14 of it, as keys
-    auto Uat = [&](int l, int64_t r) -> T * {
-        return pool + S.chunk[l / KCHUNK] + (int64_t)(l % KCHUNK) * m + r;
-    };
-    auto Vat = [&](int l, int64_t j) -> T * {
-        return pool + S.chunk[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n + j;
-    };
-
-    for (;;) {
-        // factor storage for column kk; the decision uses only values that
-        // every thread of the group holds, so the barrier below is uniform
-        if (kk < kcap && kk / KCHUNK >= nalloc) {
-            if (t == 0) {
-                unsigned long long need = (unsigned long long)(m + n) * KCHUNK;
-                unsigned long long off = atomicAdd(&P->top, need);
-                if (off + need > P->cap) {
-                    P->overflow = 1;
-                    S.fail = 1;
-                } else {
-                    S.chunk[kk / KCHUNK] = (int64_t)off;
-                }
-            }
-            G.sync();
-            if (S.fail) {
-                status = 2;
-                break;
-            }
-            ++nalloc;
-        }
-        // selected row of R_{k-1}: a_{i,:} - sum_l (u_l)_i v_l
-        for (int l = t; l < kk; l += GS) S.cu[l] = *Uat(l, i);
-        G.sync();
-        typename E::Tri ti;
-        E::load(g, tb + i, ti);
-        long long bkey = -1;
-        int64_t bj = 0;
-        for (int64_t j = t; j < n; j += GS) {
-            typename E::Tri tj;
-            E::load(g, sb + j, tj);
-            T a = V::from(E::eval(ti, tj, R, k));
-            for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Vat(l, j), a);
-            if (kk < kcap) *Vat(kk, j) = a;
-            long long ky = V::key(a);
-            if (ky > bkey) {  // j increases, so ties keep the lowest index
-                bkey = ky;
-                bj = j;
-            }
-        }
-        entries += n;
-        G.argmax_key(bkey, bj);
-        if (t == 0) Z[i >> 5] |= 1u << (i & 31);
-        ++nZ;
-        if (bkey == 0 || bkey <= vkey) {
-            if (nZ == m) break;
-            G.sync();
-            if (t == 0) {
-                int64_t r = 0;
-                while (r < m && (Z[r >> 5] >> (r & 31)) & 1u) ++r;
-                S.scal = r;
-            }
-            G.sync();
-            i = S.scal;
-            continue;
-        }
-        if (kk == kcap) {
-            status = 1;
-            break;
-        }
-        if (bkey > maxkey) {
-            maxkey = bkey;
-            vkey = V::vanish_key(maxkey);
-        }
-        G.sync();
-        const T piv = *Vat(kk, bj);
-        const T pinv = V::inv(piv);
-        G.sync();
-        for (int64_t j = t; j < n; j += GS) *Vat(kk, j) = V::mul(*Vat(kk, j), pinv);
-        // selected column of R_{k-1}: a_{:,j} - sum_l (v_l)_j u_l
-        for (int l = t; l < kk; l += GS) S.cu[l] = *Vat(l, bj);
-        G.sync();
-        typename E::Tri tj;
-        E::load(g, sb + bj, tj);
-        long long ukey = -1;
-        int64_t br = m;
-        for (int64_t r = t; r < m; r += GS) {
-            typename E::Tri tr;
-            E::load(g, tb + r, tr);
-            T a = V::from(E::eval(tr, tj, R, k));
-            for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Uat(l, r), a);
-            *Uat(kk, r) = a;
-            if (!((Z[r >> 5] >> (r & 31)) & 1u)) {
-                long long ky = V::key(a);
-                if (ky > ukey) {
-                    ukey = ky;
-                    br = r;
-                }
-            }
-        }
-        entries += m;
-        G.argmax_key(ukey, br);
-        G.sync();
-        // ||S_k||_F^2 grows by 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> + ||u_k||^2 ||v_k||^2.
-        // Every thread forms the dot products of one column l <= k over one
-        // segment of the rows (and of v_l over one segment of the columns);
-        // the segments of each l are combined in shared memory, and one group
-        // sum gives the increment.  FP64 work: (k+1)(m+n) multiply-adds plus
-        // (k+1) * segments additions.
-        double incr = 0.0, uv2 = 0.0;
-        const int ncol = kk + 1;
-        if constexpr (std::is_same<Grp, WarpGroup>::value) {
-            // power-of-two segments per column, summed by shuffle trees
-            double uv2_lane = 0.0;
-            int last_l0 = 0;
-            for (int l0 = 0; l0 < ncol; l0 += 32) {
-                last_l0 = l0;
-                const int kc = (ncol - l0) < 32 ? (ncol - l0) : 32;
-                int nseg = 1;
-                while (nseg * 2 * kc <= 32) nseg *= 2;
-                T iu = V::zero(), iv = V::zero();
-                if (t < kc * nseg) {
-                    const int l = l0 + t % kc, sgi = t / kc;
-                    const T *ul = Uat(l, 0), *uk = Uat(kk, 0);
-                    const T *vl = Vat(l, 0), *vk = Vat(kk, 0);
-                    const int mi = (int)m, ni = (int)n;
-                    for (int r = (mi * sgi) / nseg, r1 = (mi * (sgi + 1)) / nseg; r < r1; ++r)
-                        iu = V::dotc(ul[r], uk[r], iu);
-                    for (int j = (ni * sgi) / nseg, j1 = (ni * (sgi + 1)) / nseg; j < j1; ++j)
-                        iv = V::dotc(vl[j], vk[j], iv);
-                }
-                for (int off = nseg / 2; off >= 1; off >>= 1) {
-                    iu = V::add(iu, V::shfl_down(iu, off * kc));
-                    iv = V::add(iv, V::shfl_down(iv, off * kc));
-                }
-                if (t < kc) {
-                    const double pr = V::re_mul(iu, iv);
-                    if (l0 + t == kk) {
-                        incr += pr;
-                        uv2_lane = pr;
-                    } else {
-                        incr += 2.0 * pr;
-                    }
-                }
-            }
-            incr = G.sum(incr);
-            uv2 = __shfl_sync(0xffffffffu, uv2_lane, kk - last_l0);
-        } else {
-            for (int l0 = 0; l0 < ncol; l0 += GS) {
-                const int kc = (ncol - l0) < GS ? (ncol - l0) : GS;
-                const int nseg = GS / kc;
-                T iu = V::zero(), iv = V::zero();
-                if (t < kc * nseg) {
-                    const int l = l0 + t % kc, sgi = t / kc;
-                    const T *ul = Uat(l, 0), *uk = Uat(kk, 0);
-                    const T *vl = Vat(l, 0), *vk = Vat(kk, 0);
-                    const int mi = (int)m, ni = (int)n;
-                    for (int r = (mi * sgi) / nseg, r1 = (mi * (sgi + 1)) / nseg; r < r1; ++r)
-                        iu = V::dotc(ul[r], uk[r], iu);
-                    for (int j = (ni * sgi) / nseg, j1 = (ni * (sgi + 1)) / nseg; j < j1; ++j)
-                        iv = V::dotc(vl[j], vk[j], iv);
-                }
-                part[t] = iu;
-                part[GS + t] = iv;
-                G.sync();
-                if (t < kc) {
-                    T su = part[t], sv = part[GS + t];
-                    for (int q = 1; q < nseg; ++q) {
-                        su = V::add(su, part[q * kc + t]);
-                        sv = V::add(sv, part[GS + q * kc + t]);
-                    }
-                    const double pr = V::re_mul(su, sv);
-                    if (l0 + t == kk) {
-                        incr += pr;          // ||u_k||^2 ||v_k||^2
-                        S.uv2 = pr;
-                    } else {
-                        incr += 2.0 * pr;
-                    }
-                }
-                G.sync();
-            }
-            incr = G.sum(incr);
-            uv2 = S.uv2;  // written before the last barrier above
-        }
-        normS2 += incr;
-        ++kk;
-        // ||u_k|| ||v_k|| <= eps ||S_k||_F, compared in squares
-        if (uv2 <= eps2 * normS2) break;
-        if (kk == kmin || nZ == m) break;
-        i = br;
-    }
-    G.sync();
-    if (t == 0) {
-        blk->rank = kk;
-        blk->status = status;
-        blk->entries = entries;
-        for (int c = 0; c < NCHUNK; ++c) chk->c[c] = S.chunk[c];
-    }
-    G.sync();
-}
-
-// One block per lane: the same algorithm, run sequentially by one thread for
-// a block with max(m, n) <= kTinyMax.  A warp takes 32 such blocks at once, so
-// every FP64 instruction of the (uniform-within-a-block) pivoting and norm
-// arithmetic serves 32 blocks, and no reductions are needed.
-constexpr int kTinyMax = 64;
-
-template <int OP, bool CPLX, int PREC>
-__device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double eps,
-                         FarBlock *blk, FarChunks *chk, typename VT<CPLX>::T *pool, Pool *P)
-{
-    using V = VT<CPLX>;
-    using T = typename V::T;
-    using E = RegularEntry<OP, CPLX, PREC>;
-    const int64_t tb = blk->tb, sb = blk->sb;
-    const int m = (int)(blk->te - tb), n = (int)(blk->se - sb);
-    const int kmin = m < n ? m : n;
-    const int kcap = kmin < KMAX ? kmin : KMAX;
-    int64_t chunk[NCHUNK];
-#pragma unroll
-    for (int c = 0; c < NCHUNK; ++c) chunk[c] = -1;
-    int kk = 0, nalloc = 0, status = 0, nZ = 0, i = 0;
-    int64_t entries = 0;
-    unsigned long long Z = 0ull;
-    double normS2 = 0.0, maxpiv = 0.0;
-    const double eps2 = eps * eps;
-    auto Uat = [&](int l, int r) -> T * {
-        return pool + chunk[l / KCHUNK] + (int64_t)(l % KCHUNK) * m + r;
-    };
-    auto Vat = [&](int l, int j) -> T * {
-        return pool + chunk[l / KCHUNK] + (int64_t)KCHUNK * m + (int64_t)(l % KCHUNK) * n + j;
-    };
-    for (;;) {
-        if (kk < kcap && kk / KCHUNK >= nalloc) {
-            unsigned long long need = (unsigned long long)(m + n) * KCHUNK;
-            unsigned long long off = atomicAdd(&P->top, need);
-            if (off + need > P->cap) {
-                P->overflow = 1;
-                status = 2;
-                break;
-            }
-            chunk[nalloc++] = (int64_t)off;
-        }
-        // selected row of R_{k-1}
-        typename E::Tri ti;
-        E::load_scattered(g, tb + i, ti);
-        long long bkey = -1;
-        int bj = 0;
-        for (int j = 0; j < n; ++j) {
-            typename E::Tri tj;
-            E::load_scattered(g, sb + j, tj);
-            T a = V::from(E::eval(ti, tj, R, k));
-            for (int l = 0; l < kk; ++l) a = V::fnma(*Uat(l, i), *Vat(l, j), a);
-            if (kk < kcap) *Vat(kk, j) = a;
-            long long ky = V::key(a);
-            if (ky > bkey) {
-                bkey = ky;
-                bj = j;
-            }
-        }
-        entries += n;
-        Z |= 1ull << i;
-        ++nZ;
-        const double vmax = V::mag_of_key(bkey);
-        if (vmax == 0.0 || vmax <= 1e-14 * maxpiv) {
-            if (nZ == m) break;
-            i = __ffsll((long long)~Z) - 1;  // smallest unused row
-            continue;
-        }
-        if (kk == kcap) {
-            status = 1;
-            break;
-        }
-        if (vmax > maxpiv) maxpiv = vmax;
-        const T pinv = V::inv(*Vat(kk, bj));
-        for (int j = 0; j < n; ++j) *Vat(kk, j) = V::mul(*Vat(kk, j), pinv);
-        // selected column of R_{k-1}
-        typename E::Tri tj;
-        E::load_scattered(g, sb + bj, tj);
-        long long ukey = -1;
-        int br = m;
-        for (int r = 0; r < m; ++r) {
-            typename E::Tri tr;
-            E::load_scattered(g, tb + r, tr);
-            T a = V::from(E::eval(tr, tj, R, k));
-            for (int l = 0; l < kk; ++l) a = V::fnma(*Vat(l, bj), *Uat(l, r), a);
-            *Uat(kk, r) = a;
-            if (!((Z >> r) & 1ull)) {
-                long long ky = V::key(a);
-                if (ky > ukey) {
-                    ukey = ky;
-                    br = r;
-                }
-            }
-        }
-        entries += m;
-        // ||S_k||_F^2 increment: 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> + ||u_k||^2 ||v_k||^2
-        double incr = 0.0, uv2 = 0.0;
-        const T *uk = Uat(kk, 0), *vk = Vat(kk, 0);
-        for (int l = 0; l <= kk; ++l) {
-            const T *ul = Uat(l, 0), *vl = Vat(l, 0);
-            T iu = V::zero(), iv = V::zero();
-            for (int r = 0; r < m; ++r) iu = V::dotc(ul[r], uk[r], iu);
-            for (int j = 0; j < n; ++j) iv = V::dotc(vl[j], vk[j], iv);
-            const double pr = V::re_mul(iu, iv);
-            if (l == kk) {
-                uv2 = pr;
-                incr += pr;
-            } else {
-                incr += 2.0 * pr;
-            }
-        }
-        normS2 += incr;
-        ++kk;
-        if (uv2 <= eps2 * normS2) break;
-        if (kk == kmin || nZ == m) break;
-        i = br;
-    }
-    blk->rank = kk;
-    blk->status = status;
-    blk->entries = entries;
-#pragma unroll
-    for (int c = 0; c < NCHUNK; ++c) chk->c[c] = chunk[c];
-}
-
-template <int OP, bool CPLX, int PREC>
-__global__ void __launch_bounds__(kAcaThreads, 2)
-k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, FarChunks *chunks,
-      int64_t n_big,
-      int64_t n_small, int64_t n_tiny, int zwords_small, typename VT<CPLX>::T *pool, Pool *P,
-      AcaQueue *Q)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ RedScratch red;
-    __shared__ GroupSmem<CPLX> gs[kWarps];
-    __shared__ typename VT<CPLX>::T part[2 * kAcaThreads];
-    __shared__ int64_t s_b;
-    // row bitmasks: the whole region for a CTA-wide block, then one slice of
-    // zwords_small words per warp for the small blocks
-    unsigned *zbig = reinterpret_cast<unsigned *>(smem_raw);
-    // phase 1: large blocks, one CTA each
-    CtaGroup cg{&red};
-    for (;;) {
-        if (threadIdx.x == 0) s_b = (int64_t)atomicAdd(&Q->next_big, 1u);
-        __syncthreads();
-        int64_t b = s_b;
-        __syncthreads();
-        if (b >= n_big) break;
-        aca_block<CtaGroup, OP, CPLX, PREC>(cg, g, R, k, eps, blocks + b, chunks + b, pool, P, gs[0],
-                                            zbig, part);
-    }
-    // phase 2: small blocks, one warp each
-    const int w = threadIdx.x >> 5;
-    WarpGroup wg{(int)(threadIdx.x & 31)};
-    for (;;) {
-        int64_t b = 0;
-        if (wg.lane == 0) b = (int64_t)atomicAdd(&Q->next_small, 1u);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (b >= n_small) break;
-        aca_block<WarpGroup, OP, CPLX, PREC>(wg, g, R, k, eps, blocks + n_big + b,
-                                             chunks + n_big + b, pool, P, gs[w],
-                                             zbig + (int64_t)w * zwords_small, part + 64 * w);
-    }
-    // phase 3: tiny blocks, 32 per warp, one per lane
-    FarBlock *tiny = blocks + n_big + n_small;
-    FarChunks *tiny_chk = chunks + n_big + n_small;
-    for (;;) {
-        int64_t b0 = 0;
-        if (wg.lane == 0) b0 = (int64_t)atomicAdd(&Q->next_tiny, 32u);
-        b0 = __shfl_sync(0xffffffffu, b0, 0);
-        if (b0 >= n_tiny) break;
-        const int64_t b = b0 + wg.lane;
-        if (b < n_tiny) aca_lane<OP, CPLX, PREC>(g, R, k, eps, tiny + b, tiny_chk + b, pool, P);
-        __syncwarp();
-    }
-}
-
-template <int OP, bool CPLX, int PREC>
-cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps,
-                       FarBlock *blocks, FarChunks *chunks, int64_t n_big, int64_t n_small,
-                       int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool,
-                       Pool *P, AcaQueue *Q,
-                       int num_sms, cudaStream_t st)
-{
-    const int64_t zw_big = (max_m_big + 31) / 32, zw_small = (max_m_small + 31) / 32;
-    int64_t words = zw_big > kWarps * zw_small ? zw_big : kWarps * zw_small;
-    size_t dyn = (size_t)(words > 0 ? words : 1) * sizeof(unsigned);
-    auto kern = k_aca<OP, CPLX, PREC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dyn);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAcaThreads, dyn);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)num_sms * per_sm;
-    kern<<<(unsigned)grid, kAcaThreads, dyn, st>>>(
-        g, R, k, eps, blocks, chunks, n_big, n_small, n_tiny, (int)zw_small,
-        reinterpret_cast<typename VT<CPLX>::T *>(pool), P, Q);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 int aca_small_cap() { return kSmallCap; }
@@ -852,13 +170,17 @@ cudaError_t launch_aca_finish(const FarBlock *far, const FarChunks *chunks, int6
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                        double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
                        int64_t n_small, int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
-                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st)
+                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st, int dofs)
 {
+    if (dofs == 3)
+        return launch_aca_dp1(g, rule, op, k, prec, eps, blocks, chunks, n_big, n_small,
+                              max_m_big, max_m_small, pool_data, pool, queue, num_sms, st);
+    if (dofs != 1) return cudaErrorInvalidValue;
     const bool cplx = k != 0.0;
 #define BEM_ACA(O, C, Pp)                                                                     \
     if (op == O && cplx == C && prec == Pp)                                                   \
-        return aca_launch<O, C, Pp>(g, rule, k, eps, blocks, chunks, n_big, n_small, n_tiny,          \
-                                    max_m_big, max_m_small, pool_data, pool, queue, num_sms, st);
+        return aca_launch<O, C, Pp, 1>(g, rule, k, eps, blocks, chunks, n_big, n_small, n_tiny,       \
+                                       max_m_big, max_m_small, pool_data, pool, queue, num_sms, st);
     BEM_ACA(0, false, 0) BEM_ACA(0, false, 1) BEM_ACA(0, true, 0) BEM_ACA(0, true, 1)
     BEM_ACA(1, false, 0) BEM_ACA(1, false, 1) BEM_ACA(1, true, 0) BEM_ACA(1, true, 1)
     BEM_ACA(2, false, 0) BEM_ACA(2, false, 1) BEM_ACA(2, true, 0) BEM_ACA(2, true, 1)

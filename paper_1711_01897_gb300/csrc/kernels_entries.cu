@@ -250,58 +250,7 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
 }
 
 // ---- Sauter-Schwab singular pairs (FP64) -----------------------------------
-// Vertex orders of the panel parametrisations chi(x^) = P0 + x1 (P1 - P0) +
-// x2 (P2 - P1):  identical - stored order for both; edge - test starts at the
-// shared edge in its cyclic order, trial takes the same two vertices first;
-// vertex - both start at the shared vertex and continue cyclically.
-template <int CASE>
-__device__ __forceinline__ void singular_order(const int ta[3], const int tb[3], int oa[3],
-                                               int ob[3])
-{
-    if (CASE == 3) {
-        for (int i = 0; i < 3; ++i) {
-            oa[i] = i;
-            ob[i] = 0;
-            for (int j = 0; j < 3; ++j)
-                if (tb[j] == ta[i]) ob[i] = j;
-        }
-    } else if (CASE == 2) {
-        int p = 0;
-        for (int q = 0; q < 3; ++q) {
-            bool s0 = false, s1 = false;
-            for (int j = 0; j < 3; ++j) {
-                s0 |= tb[j] == ta[q];
-                s1 |= tb[j] == ta[(q + 1) % 3];
-            }
-            if (s0 && s1) {
-                p = q;
-                break;
-            }
-        }
-        oa[0] = p;
-        oa[1] = (p + 1) % 3;
-        oa[2] = (p + 2) % 3;
-        ob[0] = ob[1] = ob[2] = 0;
-        for (int j = 0; j < 3; ++j) {
-            if (tb[j] == ta[oa[0]]) ob[0] = j;
-            else if (tb[j] == ta[oa[1]]) ob[1] = j;
-            else ob[2] = j;
-        }
-    } else {
-        int p = 0, q = 0;
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                if (ta[i] == tb[j]) {
-                    p = i;
-                    q = j;
-                }
-        for (int i = 0; i < 3; ++i) {
-            oa[i] = (p + i) % 3;
-            ob[i] = (q + i) % 3;
-        }
-    }
-}
-
+// (vertex orders: singular_order in bem_device.cuh)
 constexpr int kSingThreads = 128;
 constexpr int kSingMaxPts = 6 * NGL * NGL * NGL;  // largest table (identical, helm)
 
