@@ -599,6 +599,185 @@ def run_large(args, spec):
     return 0
 
 
+def run_p1(args):
+    """Continuous piecewise linear spaces (the paper's benchmark space, Sec.
+    5.2): Laplace single layer, double layer and hypersingular operator (Eq.
+    (9), through the DP1 single layer) on the jittered icosphere, as
+    H-matrices of the DP1 element-pair matrices with the P1 transforms in the
+    product.  One step = the three assemblies and one product each; the
+    integrals are DP1 entries (near field + every entry ACA requested).
+    Sampled exact rows of the P1 matrices (oracle, FP64) check the products."""
+    import torch
+    from paper_1711_01897_gb300 import bem, meshes
+    torch.cuda.set_device(0)
+    torch.cuda.init()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    V, T = meshes.icosphere_level(args.level)
+    V = meshes.jitter(V, T, 0.05, 1001)
+    nv, nt = V.shape[0], T.shape[0]
+    t0 = time.perf_counter()
+    mesh = bem.Mesh(V, T)
+    ops = {"SLP": bem.SLP, "DLP": bem.DLP, "HYPS": bem.HYPS}
+    hs = {name: bem.HMatrix(mesh, LEAF, ETA, space=bem.P1) for name in ops}
+    setup_s = time.perf_counter() - t0
+    rng = np.random.default_rng(11)
+    x_host = rng.normal(size=nv)
+    x = torch.from_numpy(x_host).to(dev)
+    ys = {name: torch.zeros(nv, dtype=torch.float64, device=dev) for name in ops}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(prec):
+        ent = 0
+        for name, h in hs.items():
+            bem.hmat_assemble(h.handle, ops[name], 0.0, EPS, prec, sptr)
+            bem.hmat_matvec(h.handle, x, ys[name], 1, sptr)
+        for h in hs.values():
+            st = h.stats()
+            ent += st["near_entries"] + st["far_entries"]
+        return ent
+
+    for _ in range(max(3, args.warmup)):
+        step(bem.MIXED)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ms, ents = [], 0
+    per_op = {name: {"assembly_ms": 0.0, "near_ms": 0.0, "aca_ms": 0.0} for name in ops}
+    for s_ in range(args.steps):
+        flush.fill_(s_ & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ents += step(bem.MIXED)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        for name, h in hs.items():
+            st = h.stats()
+            per_op[name]["assembly_ms"] += (st["time_near_ms"] + st["time_far_ms"]) / args.steps
+            per_op[name]["near_ms"] += st["time_near_ms"] / args.steps
+            per_op[name]["aca_ms"] += st["time_far_ms"] / args.steps
+    clk = clocks.stop()
+    stats = {name: h.stats() for name, h in hs.items()}
+    y_mixed = {name: ys[name].cpu().numpy().copy() for name in ops}
+    # FP64 comparison step
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    step(bem.FP64)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = a.elapsed_time(b)
+    # sampled exact rows (oracle) against the mixed products
+    import oracle
+    rows = np.sort(rng.choice(nv, 6, replace=False))
+    t1 = time.perf_counter()
+    errs = {}
+    for name, op in ops.items():
+        if name == "HYPS":
+            R = oracle.hypersingular_p1_rows(V, T, 0.0, rows).real
+            # D 1 = 0: its rows cancel, so the error is taken against |R| |x|
+            scale = np.linalg.norm(np.abs(R) @ np.abs(x_host))
+        else:
+            R = oracle.p1_rows(V, T, op, 0.0, rows).real
+            scale = np.linalg.norm(R @ x_host)
+        errs[name] = float(np.linalg.norm(y_mixed[name][rows] - R @ x_host) / scale)
+    t_or = time.perf_counter() - t1
+    tot = float(np.sum(ms))
+    line = {"metric": METRIC, "value": ents / (tot * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded jittered icosphere)",
+            "config": {"workload": f"laplace_p1_slp_dlp_hyps_icosphere_l{args.level}_jitter5pct",
+                       "n_vertices": nv, "n_triangles": nt, "dp1_dofs": 3 * nt, "leaf_size": LEAF,
+                       "eta": ETA, "aca_eps": EPS,
+                       "precision": "mixed (FP32 quadrature, float-float accumulation, FP64 ACA)",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "integrals_per_step": ents / args.steps, "per_operator": per_op,
+            "ranks": {n_: [st["rank_min"], st["rank_mean"], st["rank_max"]] for n_, st in stats.items()},
+            "memory_gb": {n_: (st["near_bytes"] + st["factor_bytes"]) / 2**30 for n_, st in stats.items()},
+            "mixed_vs_fp64": {"fp64_ms_per_step": fp64_ms, "mixed_ms_per_step": float(np.median(ms)),
+                              "speedup": fp64_ms / float(np.median(ms))},
+            "sampled_rows_rel_err": errs, "tolerance": 2 * EPS, "oracle_rows_s": t_or,
+            "tree_and_upload_s": setup_s, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_dense(args):
+    """Dense weak-form assembly (Sec. 3, Algorithm "Dense Assembly"): every
+    entry of the P0 Galerkin matrix of the unit sphere with about 103k
+    triangles (the size of the paper's largest dense Laplace case), regular
+    pairs by the tiled quadrature kernel and touching pairs by Sauter-Schwab,
+    single and double layer, mixed precision (FP64 for one comparison run).
+    Checks: sampled rows against the oracle, and the double-layer row sums
+    against -|T_i|/2 over all rows."""
+    import torch
+    from paper_1711_01897_gb300 import bem, meshes
+    torch.cuda.set_device(0)
+    torch.cuda.init()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    V, T = meshes.icosphere(args.nu)
+    nt = T.shape[0]
+    mesh = bem.Mesh(V, T)
+    ids = torch.arange(nt, dtype=torch.int32, device=dev)
+    out = torch.empty(nt * nt, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    clocks = Clocks(0)
+    for name, op in (("SLP", bem.SLP), ("DLP", bem.DLP)):
+        bem.bem_entries(mesh.handle, op, 0.0, bem.MIXED, ids, ids, out, stream.cuda_stream)
+        if name == "SLP":
+            clocks.start()
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bem.bem_entries(mesh.handle, op, 0.0, bem.MIXED, ids, ids, out, stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[name] = {"ms": float(np.median(ms)), "entries_per_s": nt * nt / (np.median(ms) * 1e-3)}
+        A = out.view(nt, nt)
+        rng = np.random.default_rng(3 + op)
+        rows = np.sort(rng.choice(nt, 4, replace=False)).astype(np.int32)
+        import oracle
+        ref = oracle.entries(V, T, op, 0.0, rows, np.arange(nt, dtype=np.int32)).real
+        got = A[torch.from_numpy(rows).long().to(dev)].cpu().numpy()
+        res[name]["sampled_rows_rel_err"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        if name == "DLP":
+            P = V[T]
+            area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+            rs = A.sum(dim=1).cpu().numpy()
+            res[name]["row_sum_vs_minus_half_area_max_rel"] = float(np.max(np.abs(rs + area / 2) / (area / 2)))
+    clk = clocks.stop()
+    # FP64 comparison, single layer
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    bem.bem_entries(mesh.handle, bem.SLP, 0.0, bem.FP64, ids, ids, out, stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = a.elapsed_time(b)
+    del out
+    tot_ms = res["SLP"]["ms"] + res["DLP"]["ms"]
+    line = {"metric": METRIC, "value": 2 * nt * nt / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": 1, "ms_per_step": tot_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (unit icosphere)",
+            "config": {"workload": f"laplace_slp_dlp_p0_dense_icosphere_nu{args.nu}",
+                       "n_triangles": nt, "entries_per_operator": nt * nt,
+                       "precision": "mixed (FP32 quadrature, float-float accumulation); touching pairs FP64",
+                       "l2": "flushed between timed launches (256 MiB write); output 8 n^2 bytes"},
+            "per_operator": res,
+            "mixed_vs_fp64": {"fp64_slp_ms": fp64_ms, "mixed_slp_ms": res["SLP"]["ms"],
+                              "speedup": fp64_ms / res["SLP"]["ms"]},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -608,7 +787,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serving"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serving", "p1", "dense"])
+    ap.add_argument("--nu", type=int, default=72,
+                    help="geodesic frequency of the dense workload's sphere (20 nu^2 triangles)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--slots", type=int, default=6)
     ap.add_argument("--hbm-budget-gb", type=float, default=96.0)
@@ -628,6 +809,10 @@ def main():
         return run_serving(args)
     if args.workload in LARGE:
         return run_large(args, LARGE[args.workload])
+    if args.workload == "p1":
+        return run_p1(args)
+    if args.workload == "dense":
+        return run_dense(args)
     return run_gpu(args)
 
 

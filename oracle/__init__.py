@@ -267,6 +267,60 @@ def hypersingular_p1(V, T, k: float, **kw) -> np.ndarray:
     return assemble_p1(T, V.shape[0], local)
 
 
+def _vertex_dofs(T, verts):
+    """For each vertex, the (triangle, local index) pairs of its DP1 dofs."""
+    T = np.asarray(T)
+    out = []
+    for v in verts:
+        t, a = np.nonzero(T == v)
+        out.append((t.astype(np.int32), a))
+    return out
+
+
+def p1_rows(V, T, op: int, k: float, verts, **kw) -> np.ndarray:
+    """Rows `verts` of the continuous P1 matrix of op (global assembly of the
+    local matrices, Sec. 3.2.3), [len(verts), n_vertices] complex128."""
+    V = np.asarray(V, dtype=np.float64)
+    T = np.asarray(T)
+    nt, nv = T.shape[0], V.shape[0]
+    allt = np.arange(nt, dtype=np.int32)
+    cols = T.reshape(-1)                      # DP1 dof 3t + b -> vertex
+    out = np.zeros((len(verts), nv), dtype=np.complex128)
+    for r, (tris, loc) in enumerate(_vertex_dofs(T, verts)):
+        A = entries_dp1(V, T, op, k, tris, allt, **kw)       # [3 len(tris), 3 nt]
+        row = A[3 * np.arange(tris.size) + loc].sum(axis=0)
+        np.add.at(out[r], cols, row)
+    return out
+
+
+def hypersingular_p1_rows(V, T, k: float, verts, **kw) -> np.ndarray:
+    """Rows `verts` of the hypersingular P1 matrix by the weak form, Eq. (4)
+    (as hypersingular_p1), [len(verts), n_vertices] complex128."""
+    V = np.asarray(V, dtype=np.float64)
+    T = np.asarray(T)
+    nt, nv = T.shape[0], V.shape[0]
+    allt = np.arange(nt, dtype=np.int32)
+    C = surface_curls(V, T)                                   # [nt, 3, 3]
+    P = V[T]
+    n = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    cols = T.reshape(-1)
+    out = np.zeros((len(verts), nv), dtype=np.complex128)
+    for r, (tris, loc) in enumerate(_vertex_dofs(T, verts)):
+        S0 = entries(V, T, SLP, k, tris, allt, **kw)          # [len(tris), nt]
+        row = np.zeros(3 * nt, dtype=np.complex128)
+        for q in range(tris.size):
+            cu = C[tris[q], loc[q]]                          # curl of phi_u on this triangle
+            row += (np.repeat(S0[q], 3) * (C.reshape(3 * nt, 3) @ cu))
+        if k != 0.0:
+            S1 = entries_dp1(V, T, SLP, k, tris, allt, **kw)
+            for q in range(tris.size):
+                nn = np.repeat(n @ n[tris[q]], 3)
+                row -= k * k * nn * S1[3 * q + loc[q]]
+        np.add.at(out[r], cols, row)
+    return out
+
+
 def mass_p1(V, T) -> np.ndarray:
     """P1 mass matrix M[u, v] = int phi_u phi_v (exact: |T|/12 (1 + delta_ab))."""
     V = np.asarray(V, dtype=np.float64)

@@ -179,3 +179,17 @@ def test_dp1_hmatrix_blocks_against_dense():
     y = hm.matvec(x)
     ref = A @ x
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-6
+
+
+def test_row_helpers_match_dense_matrices():
+    V, T = meshes.icosphere_level(2)
+    V = meshes.jitter(V, T, 0.05, 3)
+    rows = [0, 17, 100]
+    for k in (0.0, 1.5):
+        D = oracle.hypersingular_p1(V, T, k)
+        R = oracle.hypersingular_p1_rows(V, T, k, rows)
+        assert np.abs(R - D[rows]).max() <= 1e-13 * np.abs(D).max()
+        for op in (oracle.SLP, oracle.DLP):
+            A = oracle.dense_matrix_p1(V, T, op, k)
+            R = oracle.p1_rows(V, T, op, k, rows)
+            assert np.abs(R - A[rows]).max() <= 1e-13 * np.abs(A).max()
