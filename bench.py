@@ -644,7 +644,8 @@ def run_p1(args):
     clocks = Clocks(0)
     clocks.start()
     ms, ents = [], 0
-    per_op = {name: {"assembly_ms": 0.0, "near_ms": 0.0, "aca_ms": 0.0} for name in ops}
+    per_op = {name: {"assembly_ms": 0.0, "near_regular_ms": 0.0, "singular_ms": 0.0, "aca_ms": 0.0}
+              for name in ops}
     for s_ in range(args.steps):
         flush.fill_(s_ & 0xff)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -656,7 +657,8 @@ def run_p1(args):
         for name, h in hs.items():
             st = h.stats()
             per_op[name]["assembly_ms"] += (st["time_near_ms"] + st["time_far_ms"]) / args.steps
-            per_op[name]["near_ms"] += st["time_near_ms"] / args.steps
+            per_op[name]["near_regular_ms"] += st["time_near_regular_ms"] / args.steps
+            per_op[name]["singular_ms"] += st["time_singular_ms"] / args.steps
             per_op[name]["aca_ms"] += st["time_far_ms"] / args.steps
     clk = clocks.stop()
     stats = {name: h.stats() for name, h in hs.items()}

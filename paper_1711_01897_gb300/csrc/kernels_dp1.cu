@@ -195,7 +195,76 @@ k_singular_dp1(DevGeom g, SingTable tab, double k, const SingPairL *__restrict__
         // acc[i][j]: parametrisation vertices i (test) and j (trial)
         C2 acc[9];
         for (int o = 0; o < 9; ++o) acc[o] = {0.0, 0.0};
-        if (!flat_zero) {
+        if (!flat_zero && !CPLX) {
+            // Laplace: with lambda^x = e_0 + xi beta (beta = (-X1, X1 - X2, X2))
+            // and lambda^y = e_0 + xi beta' the xi integrand is a polynomial,
+            // xi^p (kernel weight W) times the product of the two affine
+            // factors (p = 2 single layer, 1 double layers), of degree <= p + 2,
+            // which the xi rule integrates exactly; so the xi sum is taken once
+            // through the moments M_p = sum_m w_m xi_m^p, and per eta node only
+            // the sums of W, W beta_a, W beta'_b and W beta_a beta'_b gather.
+            double S0 = 0.0, Sa[3] = {0.0, 0.0, 0.0}, Sb[3] = {0.0, 0.0, 0.0}, Sab[9];
+#pragma unroll
+            for (int o = 0; o < 9; ++o) Sab[o] = 0.0;
+            for (int q = 0; q < npts; ++q) {
+                double cf[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) cf[i] = s_tab[i * npts + q];
+                const double weta = s_tab[4 * npts + q];
+                const double X1 = s_tab[5 * npts + q], X2 = s_tab[6 * npts + q];
+                const double Y1 = s_tab[7 * npts + q], Y2 = s_tab[8 * npts + q];
+                double d[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double x = cf[0] * E[0][c];
+#pragma unroll
+                    for (int i = 1; i < NC; ++i) x = fma(cf[i], E[i][c], x);
+                    d[c] = x;
+                }
+                const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
+                const double ri = rsqrt(r2);
+                double W;
+                if (OP == 0) {
+                    W = weta * ri;
+                } else {
+                    double dn = 0.0;
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) dn = fma(cf[i], OP == 1 ? eny[i] : enx[i], dn);
+                    if (OP == 2) dn = -dn;  // ADLP kernel has -(x - y).n_x
+                    W = weta * dn * (ri * ri * ri);
+                }
+                const double ba[3] = {-X1, X1 - X2, X2}, bb[3] = {-Y1, Y1 - Y2, Y2};
+                S0 += W;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const double Wa = W * ba[a];
+                    Sa[a] += Wa;
+                    Sb[a] = fma(W, bb[a], Sb[a]);
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) Sab[3 * a + b] = fma(Wa, bb[b], Sab[3 * a + b]);
+                }
+            }
+            // moments of the xi rule
+            const int p0 = OP == 0 ? 2 : 1;
+            double M[3] = {0.0, 0.0, 0.0};
+            for (int m = 0; m < NGL; ++m) {
+                double xp = tab.wxi[m];
+                for (int e = 0; e < p0; ++e) xp *= tab.xi[m];
+                M[0] += xp;
+                M[1] += xp * tab.xi[m];
+                M[2] += xp * tab.xi[m] * tab.xi[m];
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    double v = Sab[3 * a + b] * M[2];
+                    if (a == 0) v = fma(Sb[b], M[1], v);
+                    if (b == 0) v = fma(Sa[a], M[1], v);
+                    if (a == 0 && b == 0) v = fma(S0, M[0], v);
+                    acc[3 * a + b].re = v;
+                }
+        } else if (!flat_zero) {
             for (int q = 0; q < npts; ++q) {
                 double cf[NC];
 #pragma unroll
