@@ -173,8 +173,8 @@ __device__ __forceinline__ int count_shared(const int a[3], const int b[3])
 // d.n_x on q only.  Each test point's 6-term FP32 sum is folded into a
 // float-float accumulator.
 template <int OP>
-__device__ __forceinline__ double entry_mixed_laplace(const TriF &a, const TriF &b,
-                                                      const float *__restrict__ w)
+__device__ __forceinline__ FF entry_mixed_laplace_ff(const TriF &a, const TriF &b,
+                                                     const float *__restrict__ w)
 {
     float D[3];
 #pragma unroll
@@ -203,10 +203,28 @@ __device__ __forceinline__ double entry_mixed_laplace(const TriF &a, const TriF 
         if (OP == 1) s *= Dp0 * b.n[0] + Dp1 * b.n[1] + Dp2 * b.n[2];
         ff_add(acc, w[p] * s);
     }
-    // (acc.hi + acc.lo) * |T_i||T_j|/(4 pi) in float-float, widened with one
-    // FP64 addition
-    FF r = ff_mul(acc, ff_mul(a.s, b.s));
+    // (acc.hi + acc.lo) * |T_i||T_j|/(4 pi) in float-float
+    return ff_mul(acc, ff_mul(a.s, b.s));
+}
+
+// The same entry widened to FP64 with one FP64 addition (the float halves are
+// widened on the integer pipe).
+template <int OP>
+__device__ __forceinline__ double entry_mixed_laplace(const TriF &a, const TriF &b,
+                                                      const float *__restrict__ w)
+{
+    const FF r = entry_mixed_laplace_ff<OP>(a, b, w);
     return f2d_exact(r.hi) + f2d_exact(r.lo);
+}
+
+// largest distance of a quadrature point from the centroid
+__device__ __forceinline__ float trif_rad(const TriF &a)
+{
+    float r2 = 0.f;
+#pragma unroll
+    for (int p = 0; p < NQ; ++p)
+        r2 = fmaxf(r2, fmaf(a.q[p][0], a.q[p][0], fmaf(a.q[p][1], a.q[p][1], a.q[p][2] * a.q[p][2])));
+    return sqrtf(r2);
 }
 
 // ---- regular entries, FP64 (Laplace and Helmholtz) -----------------------

@@ -164,8 +164,10 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
     using E = RegularEntry<OP, CPLX, 1>;
     __shared__ __align__(16) float rows_s[kTileRows][kTileFields];
     __shared__ int32_t rid_s[kTileRows];
+    __shared__ float box_s[2][6];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     constexpr int nw = kTileThreads / 32;
+    static_assert(kTileRows <= 2 * 32 && nw >= 2, "row boxes: warps 0 and 1");
     const int64_t ncb = (n_trial + 31) / 32, nrb = (n_test + kTileRows - 1) / kTileRows;
     const int64_t ntiles = ncb * nrb;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -209,6 +211,84 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
             load_ids_tile(g, j, vj);
         }
         __syncthreads();
+        bool far_tile = false;
+        // Single layer only (measured: the extra registers cost the double
+        // layers more than the skipped vertex tests save)
+        if constexpr (OP == 0 && !CPLX) {
+        // Bounding boxes of the tile's rows and columns: a vertex lies within
+        // rad / 0.7253 of its centroid (the rule's point nearest a vertex sits
+        // at 0.7253 of the way from the centroid), taken as 1.4 rad.  If the
+        // boxes are apart along some axis no pair of the tile shares a vertex.
+        {
+            float blo[3], bhi[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                blo[c] = INFINITY;
+                bhi[c] = -INFINITY;
+            }
+            if (w < 2) {
+                const int r = threadIdx.x;
+                if (r < nr && rid_s[r] >= 0) {
+                    float q2 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const float *e = &rows_s[r][kFQ + 3 * q];
+                        q2 = fmaxf(q2, fmaf(e[0], e[0], fmaf(e[1], e[1], e[2] * e[2])));
+                    }
+                    const float R = 1.4f * sqrtf(q2);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float cc = rows_s[r][kFCh + c] + rows_s[r][kFCl + c];
+                        blo[c] = cc - R;
+                        bhi[c] = cc + R;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        blo[c] = fminf(blo[c], __shfl_down_sync(0xffffffffu, blo[c], o));
+                        bhi[c] = fmaxf(bhi[c], __shfl_down_sync(0xffffffffu, bhi[c], o));
+                    }
+                if (lane == 0)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        box_s[w][c] = blo[c];
+                        box_s[w][3 + c] = bhi[c];
+                    }
+            }
+            // columns: every warp holds the same 32 trial triangles
+            float clo[3], chi[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                clo[c] = INFINITY;
+                chi[c] = -INFINITY;
+            }
+            if (j >= 0) {
+                const float R = 1.4f * trif_rad(tb);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float cc = tb.ch[c] + tb.cl[c];
+                    clo[c] = cc - R;
+                    chi[c] = cc + R;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    clo[c] = fminf(clo[c], __shfl_xor_sync(0xffffffffu, clo[c], o));
+                    chi[c] = fmaxf(chi[c], __shfl_xor_sync(0xffffffffu, chi[c], o));
+                }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float rlo = fminf(box_s[0][c], box_s[1][c]);
+                const float rhi = fmaxf(box_s[0][3 + c], box_s[1][3 + c]);
+                far_tile |= clo[c] > rhi || rlo > chi[c];
+            }
+        }
+        }
         if (j < 0) continue;
         for (int r = w; r < nr; r += nw) {
             const int32_t i = rid_s[r];
@@ -226,10 +306,12 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
             const int vi[3] = {__float_as_int(f[kFId]), __float_as_int(f[kFId + 1]),
                                __float_as_int(f[kFId + 2])};
             const int64_t dst = (a0 + r) * n_trial + b;
-            const int s = count_shared(vi, vj);
-            if (s > 0) {
-                push_singular(s, i, j, dst, l1, l2, l3, counts, cap, err);
-                continue;
+            if (!far_tile) {
+                const int s = count_shared(vi, vj);
+                if (s > 0) {
+                    push_singular(s, i, j, dst, l1, l2, l3, counts, cap, err);
+                    continue;
+                }
             }
             TriF ta;
 #pragma unroll
@@ -244,7 +326,18 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
                 for (int c = 0; c < 3; ++c) ta.q[q][c] = f[kFQ + 3 * q + c];
             ta.s.hi = f[kFS];
             ta.s.lo = f[kFS + 1];
-            store_val<CPLX>(out, dst, E::eval(ta, tb, R, k));
+            if constexpr (!CPLX) {
+                // widened with two conversions and one addition on the FP64
+                // pipe (idle in this kernel) for the single layer; on the
+                // integer pipe for the double layers (measured faster each)
+                const FF v = entry_mixed_laplace_ff<OP>(ta, tb, R.wf);
+                if (OP == 0)
+                    reinterpret_cast<double *>(out)[dst] = (double)v.hi + (double)v.lo;
+                else
+                    reinterpret_cast<double *>(out)[dst] = f2d_exact(v.hi) + f2d_exact(v.lo);
+            } else {
+                store_val<CPLX>(out, dst, E::eval(ta, tb, R, k));
+            }
         }
     }
 }
