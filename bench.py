@@ -47,6 +47,12 @@ LEAF, ETA, EPS = 32, 1.2, 1e-5
 N_SM, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, FP64_PER_SM_CLK, SM_MAX_MHZ = 152, 16, 128, 2, 2070.0
 FP64_TFLOPS_NOMINAL = 1.25
 
+# DRAM bytes (read + write) of the two k_aca launches of one step of the default
+# workload (icosphere level 6, SLP and DLP, mixed), from an ncu capture of this
+# build (dram__bytes_read.sum + dram__bytes_write.sum); re-capture when k_aca
+# changes.
+ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.717166080 + 1.938804992 + 10.725359872 + 2.943645184) * 1e9
+
 
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -369,7 +375,9 @@ def run_gpu(args):
         achieved = ops / (per_step[dom] * 1e-3) / 1e9
         roof = {"kernel": "k_aca (persistent ACA + far-field quadrature)", "bound": "alu",
                 "pipe": "FP64 (DFMA/DADD/DMUL)", "achieved": achieved, "peak": fp64_peak,
-                "unit": "Gop/s", "frac": achieved / fp64_peak, "traffic": None,
+                "unit": "Gop/s", "frac": achieved / fp64_peak,
+                "traffic": ACA_TRAFFIC_BYTES_PER_STEP_L6 if args.level == 6 else None,
+                "traffic_unit": "DRAM bytes per step (both k_aca launches, ncu capture)",
                 "secondary": {"pipe": "MUFU (rsqrt per Green's function evaluation)",
                               "achieved": evals_far / (per_step[dom] * 1e-3) / 1e9,
                               "peak": mufu_peak}}
