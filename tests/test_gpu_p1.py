@@ -178,3 +178,30 @@ def test_p1_batch_and_device_vectors(l2j, l2j_mesh):
     assert relf(Y[1], A @ X[1]) <= 2e-6
     with pytest.raises(bem.BemError):
         bem.HMatrix(l2j_mesh, 16, 1.2, space=bem.DP1).assemble(bem.HYPS, 0.0, 1e-4, bem.FP64)
+
+
+def test_p1_helmholtz_sampled_rows_l4(lib):
+    """A larger case: jittered L4 sphere (2,562 vertices), Helmholtz k = 3,
+    single layer and hypersingular operator in mixed precision, against exact
+    rows of the oracle's P1 matrices."""
+    V, T = meshes.icosphere_level(4)
+    V = meshes.jitter(V, T, 0.05, 77)
+    mesh = bem.Mesh(V, T)
+    k, eps = 3.0, 1e-5
+    rng = np.random.default_rng(9)
+    x = rng.normal(size=V.shape[0]) + 1j * rng.normal(size=V.shape[0])
+    rows = np.sort(rng.choice(V.shape[0], 6, replace=False))
+    for op in (bem.SLP, bem.HYPS):
+        h = bem.HMatrix(mesh, 32, 1.2, space=bem.P1)
+        h.assemble(op, k, eps, bem.MIXED)
+        y = h.matvec(x)
+        if op == bem.SLP:
+            R = oracle.p1_rows(V, T, oracle.SLP, k, rows)
+            scale = np.linalg.norm(R @ x)
+        else:
+            R = oracle.hypersingular_p1_rows(V, T, k, rows)
+            scale = np.linalg.norm(np.abs(R) @ np.abs(x))
+        err = np.linalg.norm(y[rows] - R @ x) / scale
+        assert err <= 2 * eps, (op, err)
+        h.close()
+    mesh.close()
