@@ -627,7 +627,8 @@ def run_p1(args):
     nv, nt = V.shape[0], T.shape[0]
     t0 = time.perf_counter()
     mesh = bem.Mesh(V, T)
-    ops = {"SLP": bem.SLP, "DLP": bem.DLP, "HYPS": bem.HYPS}
+    ops = {name: op for name, op in (("SLP", bem.SLP), ("DLP", bem.DLP), ("HYPS", bem.HYPS))
+           if name in args.ops.split(",")}
     hs = {name: bem.HMatrix(mesh, LEAF, ETA, space=bem.P1) for name in ops}
     setup_s = time.perf_counter() - t0
     rng = np.random.default_rng(11)
@@ -698,7 +699,7 @@ def run_p1(args):
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic (seeded jittered icosphere)",
-            "config": {"workload": f"laplace_p1_slp_dlp_hyps_icosphere_l{args.level}_jitter5pct",
+            "config": {"workload": f"laplace_p1_{'_'.join(n_.lower() for n_ in ops)}_icosphere_l{args.level}_jitter5pct",
                        "n_vertices": nv, "n_triangles": nt, "dp1_dofs": 3 * nt, "leaf_size": LEAF,
                        "eta": ETA, "aca_eps": EPS,
                        "precision": "mixed (FP32 quadrature, float-float accumulation, FP64 ACA)",
@@ -798,6 +799,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serving", "p1", "dense"])
+    ap.add_argument("--ops", default="SLP,DLP,HYPS",
+                    help="operators of the p1 workload (comma-separated SLP, DLP, HYPS)")
     ap.add_argument("--nu", type=int, default=72,
                     help="geodesic frequency of the dense workload's sphere (20 nu^2 triangles)")
     ap.add_argument("--requests", type=int, default=2000)
