@@ -205,3 +205,66 @@ def test_p1_helmholtz_sampled_rows_l4(lib):
         assert err <= 2 * eps, (op, err)
         h.close()
     mesh.close()
+
+
+def test_p1_icosahedron_all_near_field(lib):
+    """20 triangles: the H-matrix is (almost) all dense blocks."""
+    V, T = meshes.icosphere(1)
+    mesh = bem.Mesh(V, T)
+    for op, k in ((bem.SLP, 0.0), (bem.DLP, 1.0), (bem.HYPS, 0.0), (bem.HYPS, 1.0)):
+        h = bem.HMatrix(mesh, 4, 1.2, space=bem.P1)
+        h.assemble(op, k, 1e-12, bem.FP64)
+        x = np.arange(V.shape[0], dtype=np.float64) - 5.0
+        if k:
+            x = x + 0.5j
+        y = h.matvec(x)
+        A = oracle.hypersingular_p1(V, T, k) if op == bem.HYPS else oracle.dense_matrix_p1(V, T, op, k)
+        ref = A @ x if k else A.real @ x
+        assert np.linalg.norm(y - ref) <= 1e-9 * np.linalg.norm(np.abs(A) @ np.abs(x)), op
+        h.close()
+    mesh.close()
+
+
+def test_dp1_helmholtz_hmatrix_blocks(l2j, l2j_mesh):
+    V, T = l2j
+    k, eps = 2.0, 1e-6
+    h = bem.HMatrix(l2j_mesh, 16, 1.2, space=bem.DP1)
+    h.assemble(bem.SLP, k, eps, bem.MIXED)
+    A = oracle.dense_matrix_dp1(V, T, bem.SLP, k)
+    blocks, perm = h.blocks()
+    dperm = (3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)
+    Ap = A[np.ix_(dperm, dperm)]
+    for b, (tb, te, sb, se, adm) in enumerate(blocks):
+        ref = Ap[tb:te, sb:se]
+        got, _ = h.block_dense(b, (te - tb, se - sb))
+        err = relf(got, ref)
+        if adm:
+            U, Vv = oracle.aca_dense(ref, eps)
+            assert err <= 2 * relf(U @ Vv.T, ref) + 10 * eps + TOL[bem.MIXED], (b, err)
+        else:
+            assert err <= TOL[bem.MIXED], (b, err)
+    x = np.random.default_rng(4).normal(size=h.n) * (1 + 0.3j)
+    assert relf(h.matvec(x), A @ x) <= 2 * eps + TOL[bem.MIXED]
+    h.close()
+
+
+def test_p1_graph_replay_matches_eager(l2j, l2j_mesh):
+    """The DP1 assembly sequence captured into a CUDA graph and replayed gives
+    the eager result bit for bit (hypersingular, Helmholtz, mixed)."""
+    V, T = l2j
+    saved = bem.bem_get_tuning()
+    x = np.random.default_rng(8).normal(size=V.shape[0]) + 0.25j
+    try:
+        bem.bem_set_tuning(saved["warp_max_rows"], saved["lane_max_rows"], 0)
+        h0 = bem.HMatrix(l2j_mesh, 16, 1.2, space=bem.P1)
+        h0.assemble(bem.HYPS, 1.5, 1e-5, bem.MIXED)
+        y0 = h0.matvec(x)
+        bem.bem_set_tuning(saved["warp_max_rows"], saved["lane_max_rows"], 1)
+        h = bem.HMatrix(l2j_mesh, 16, 1.2, space=bem.P1)
+        for _ in range(3):          # eager, capture + launch, replay
+            h.assemble(bem.HYPS, 1.5, 1e-5, bem.MIXED)
+            assert np.array_equal(h.matvec(x), y0)
+        h.close()
+        h0.close()
+    finally:
+        bem.bem_set_tuning(saved["warp_max_rows"], saved["lane_max_rows"], saved["use_graphs"])
