@@ -54,6 +54,23 @@ FP64_TFLOPS_NOMINAL = 1.25
 ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.717166080 + 1.938804992 + 10.725359872 + 2.943645184) * 1e9
 
 
+def rank_jitter_seed(rank: int) -> int:
+    """Each rank solves its own problem: the workload's mesh with a
+    rank-dependent jitter seed (rank 0 is the single-GPU workload)."""
+    return 1001 + 7919 * rank
+
+
+def reduce_over_ranks(total_ms: float, integrals: float, dist, device):
+    """Whole-job figures of the weakly scaled run: the timed region lasts as
+    long as the slowest rank (max), and the integrals of all ranks add up."""
+    import torch
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(integrals)], device=device, dtype=torch.float64)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -174,7 +191,7 @@ def quadrature_roofline(bem, mesh, V, T, dev, stream, flush, reps: int = 3):
 # CPU oracle arm (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7):
+def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7, nthreads: int = 0):
     """Times the oracle's H-matrix assembly (Algorithm "H-Matrix Assembly":
     dense near blocks + ACA blocks, SLP and DLP) on a seeded sample of the
     workload's leaf blocks; returns integrals/s, threads, description."""
@@ -195,7 +212,7 @@ def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7):
         t0 = time.perf_counter()
         ent = 0
         for op in (oracle.SLP, oracle.DLP):
-            hm = oracle.hmat_assemble(V, T, op, 0.0, LEAF, ETA, EPS, block_ids=ids)
+            hm = oracle.hmat_assemble(V, T, op, 0.0, LEAF, ETA, EPS, block_ids=ids, nthreads=nthreads)
             ent += hm.entries_evaluated
         dt = time.perf_counter() - t0
         total_entries += ent
@@ -204,7 +221,7 @@ def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7):
         if total_t >= seconds_target or frac >= 0.5:
             break
         frac = min(0.5, frac * max(2.0, seconds_target / max(dt, 1e-3) * 0.7))
-    return (total_entries / total_t, oracle.num_threads(),
+    return (total_entries / total_t, nthreads if nthreads > 0 else oracle.num_threads(),
             f"{used} of {bl.shape[0]} leaf blocks (near and admissible, seeded stratified sample), "
             f"SLP+DLP, FP64 oracle, {total_entries} integrals in {total_t:.1f} s")
 
@@ -254,7 +271,7 @@ def run_gpu(args):
 
     # independent problems per rank: same workload, rank-dependent jitter seed
     V, T = meshes.icosphere_level(args.level)
-    V = meshes.jitter(V, T, 0.05, 1001 + 7919 * rank)
+    V = meshes.jitter(V, T, 0.05, rank_jitter_seed(rank))
     n = T.shape[0]
     mesh = bem.Mesh(V, T)
     hs = {op: bem.HMatrix(mesh, LEAF, ETA) for op in (bem.SLP, bem.DLP)}
@@ -304,12 +321,7 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(np.sum(step_ms))
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        e = torch.tensor([ents], device=dev, dtype=torch.float64)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        ents_all = float(e.item())
+        total_ms, ents_all = reduce_over_ranks(total_ms, ents, dist, dev)
     else:
         ents_all = float(ents)
     value = ents_all / (total_ms * 1e-3)
@@ -402,7 +414,10 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        rate1, _, sample1 = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds / 3, seed=8,
+                                               nthreads=1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "one_thread": {"value": rate1, "unit": UNIT, "cores": 1, "sample": sample1}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

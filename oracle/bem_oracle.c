@@ -468,8 +468,9 @@ int orc_entries(const double *V, const int32_t *Tr, int64_t nt, int op, double k
     if (!R) return 3;
     rule_init(R, regular_order);
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+    /* a per-call thread count that leaves the process default untouched */
+    const int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth)
 #endif
     for (int64_t a = 0; a < n_test; ++a)
         for (int64_t b = 0; b < n_trial; ++b)
@@ -611,8 +612,9 @@ int orc_entries_dp1(const double *V, const int32_t *Tr, int64_t nt, int op, doub
     rule_init(R, regular_order);
     const int64_t ld = 3 * n_trial;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+    /* a per-call thread count that leaves the process default untouched */
+    const int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth)
 #endif
     for (int64_t a = 0; a < n_test; ++a)
         for (int64_t b = 0; b < n_trial; ++b) {
@@ -1112,8 +1114,9 @@ int orc_aca_blocks(const double *V, const int32_t *Tr, const int32_t *perm, int 
                    int64_t *entries, int nthreads)
 {
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+    /* a per-call thread count that leaves the process default untouched */
+    const int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth)
 #endif
     for (int64_t b = 0; b < nblk; ++b) {
         int r = 0;
