@@ -347,27 +347,40 @@ def run_gpu(args):
             np.linalg.norm(y_mixed[op] - y_fp64[op]) / np.linalg.norm(y_fp64[op])) for op in hs},
         "tolerance": 2 * EPS}
 
-    # end to end through the C ABI from host buffers
-    e2e_ms = []
+    # end to end through the C ABI from host buffers: mesh, one tree for both
+    # operators (as for `value`), each assembly and its product from host x to
+    # host y
+    e2e_ms, parts = [], []
     h2d = V.nbytes + T.astype(np.int32).nbytes + 2 * x_host.nbytes
     d2h = 2 * x_host.nbytes
     for r in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m2 = bem.Mesh(V, T)
+        t1 = time.perf_counter()
+        h2 = bem.HMatrix(m2, LEAF, ETA)
+        t2 = time.perf_counter()
         ent2 = 0
         for op in (bem.SLP, bem.DLP):
-            h2 = bem.HMatrix(m2, LEAF, ETA)
             h2.assemble(op, 0.0, EPS, bem.MIXED, sptr)
             yh = np.zeros(n)
             bem.hmat_matvec(h2.handle, x_host, yh, 1, sptr)
             s2 = h2.stats()
             ent2 += s2["near_entries"] + s2["far_entries"]
-            h2.close()
+        t3 = time.perf_counter()
+        h2.close()
         m2.close()
         torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        t4 = time.perf_counter()
+        e2e_ms.append((t4 - t0) * 1e3)
+        parts.append({"mesh_ms": (t1 - t0) * 1e3, "tree_ms": (t2 - t1) * 1e3,
+                      "assemble_and_product_ms": (t3 - t2) * 1e3, "free_ms": (t4 - t3) * 1e3,
+                      "tree_clusters_ms": s2["time_tree_clusters_ms"],
+                      "tree_blocks_ms": s2["time_tree_blocks_ms"],
+                      "tree_lists_ms": s2["time_tree_lists_ms"],
+                      "tree_upload_ms": s2["time_tree_upload_ms"]})
     e2e_val = ent2 / (np.median(e2e_ms) * 1e-3) * ws
+    e2e_parts = parts[int(np.argsort(e2e_ms)[len(e2e_ms) // 2])]
 
     # roofline of the dominant kernel (device time share over the timed steps)
     steps = args.steps
@@ -436,7 +449,8 @@ def run_gpu(args):
                 "mixed_vs_fp64": mixed_vs_fp64,
                 "roofline": roof, "quadrature_roofline": quad, "cpu_baseline": cpu, "clocks": clk,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                        "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.median(e2e_ms))},
+                        "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.median(e2e_ms)),
+                        "parts_ms": e2e_parts},
                 "gpu_launches": int(launches), "step_ms": step_ms}
         print(json.dumps(line), flush=True)
     if ws > 1:

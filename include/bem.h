@@ -271,6 +271,10 @@ typedef struct {
     int32_t prec;
     int32_t space;               /* BEM_P0, BEM_DP1, BEM_P1 */
     int64_t n_dofs;              /* hmat_dofs() */
+    double time_tree_clusters_ms; /* parts of time_tree_ms: cluster tree, block tree, */
+    double time_tree_blocks_ms;   /* block lists and touching pairs (host), and the   */
+    double time_tree_lists_ms;    /* upload with the cluster-order geometry (device)  */
+    double time_tree_upload_ms;
 } bem_hmat_stats;
 
 /* Copies statistics of the handle into *out. */

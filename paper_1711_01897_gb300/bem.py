@@ -47,7 +47,9 @@ class HmatStats(ctypes.Structure):
                 ("aca_fp64_fma", ctypes.c_int64),
                 ("assembled", ctypes.c_int32), ("op", ctypes.c_int32), ("k", ctypes.c_double),
                 ("aca_eps", ctypes.c_double), ("prec", ctypes.c_int32),
-                ("space", ctypes.c_int32), ("n_dofs", ctypes.c_int64)]
+                ("space", ctypes.c_int32), ("n_dofs", ctypes.c_int64),
+                ("time_tree_clusters_ms", ctypes.c_double), ("time_tree_blocks_ms", ctypes.c_double),
+                ("time_tree_lists_ms", ctypes.c_double), ("time_tree_upload_ms", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):

@@ -21,6 +21,7 @@
 #include "bem_internal.h"
 
 #include <atomic>
+#include <thread>
 
 using namespace bem;
 
@@ -77,8 +78,51 @@ int guarded(F &&f)
     }
 }
 
+// The library's stream-ordered memory pool on the current device.  Freed
+// blocks up to kPoolKeep bytes stay in the pool across synchronisations, so
+// that meshes, trees and factor pools created one after another reuse them
+// instead of mapping fresh memory each time (the device's default pool
+// returns everything at every synchronisation).  pool_trim hands the cached
+// blocks back, before a large allocation is sized against the free memory.
+constexpr uint64_t kPoolKeep = uint64_t(16) << 30;
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaMemPool_t lib_pool()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        cudaDeviceGetDefaultMemPool(&pool, dev);
+    } else {
+        uint64_t keep = kPoolKeep;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    g_pools[dev] = pool;
+    return pool;
+}
+
+void pool_trim()
+{
+    cudaMemPoolTrimTo(lib_pool(), 0);
+}
+
+cudaError_t lib_malloc_async(void **p, size_t b, cudaStream_t st)
+{
+    return cudaMallocFromPoolAsync(p, b, lib_pool(), st);
+}
+
 // Device buffer owned by RAII, allocated stream-ordered on its home stream
-// and freed on that stream.
+// from the library's pool and freed on that stream.
 struct DBuf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -98,7 +142,7 @@ struct DBuf {
         release();
         if (b == 0) b = 16;
         home = st;
-        cudaError_t e = cudaMallocAsync(&p, b, st);
+        cudaError_t e = lib_malloc_async(&p, b, st);
         if (e != cudaSuccess) {
             p = nullptr;
             g_err = "device allocation of " + std::to_string(b) + " bytes failed: " +
@@ -456,6 +500,40 @@ struct bem_mesh_s {
 
 namespace {
 
+// Host threads for the mesh and tree builds: f(task) for task in [0, ntask), handed out
+// by an atomic counter to at most the hardware's thread count.  f must not
+// throw; the first error message is kept and rethrown after the join.
+template <class F>
+void parallel_tasks(int64_t ntask, F &&f)
+{
+    unsigned hw = std::thread::hardware_concurrency();
+    int64_t nth = std::min<int64_t>(std::min<int64_t>(hw ? hw : 1, 32), ntask);
+    std::atomic<int64_t> next{0};
+    std::mutex emu;
+    std::string err;
+    auto run = [&] {
+        for (;;) {
+            const int64_t t = next.fetch_add(1);
+            if (t >= ntask) return;
+            try {
+                f(t);
+            } catch (const std::exception &e) {
+                std::lock_guard<std::mutex> lk(emu);
+                if (err.empty()) err = e.what();
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int64_t i = 1; i < nth; ++i) th.emplace_back(run);
+    run();
+    for (auto &x : th) x.join();
+    if (!err.empty()) throw std::runtime_error(err);
+}
+
+// Touching triangles (sharing at least one vertex, itself included) of every
+// triangle, with the shared-vertex count, as CSR in increasing triangle order.
+// Triangles in chunks on the host threads; the chunks are concatenated in
+// order.
 void build_adjacency(bem_mesh_s &M)
 {
     const int64_t nt = M.nt, nv = M.nv;
@@ -467,26 +545,51 @@ void build_adjacency(bem_mesh_s &M)
     std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
     for (int64_t t = 0; t < nt; ++t)
         for (int a = 0; a < 3; ++a) vtri[fill[M.T[3 * t + a]]++] = (int32_t)t;
+    constexpr int64_t kChunk = 8192;
+    const int64_t nchunk = (nt + kChunk - 1) / kChunk;
+    struct Part {
+        std::vector<int64_t> len;
+        std::vector<int32_t> tri;
+        std::vector<int8_t> cs;
+        int64_t max_touch = 0;
+    };
+    std::vector<Part> parts(nchunk);
+    parallel_tasks(nchunk, [&](int64_t ck) {
+        Part &P = parts[ck];
+        std::vector<int32_t> loc;
+        for (int64_t t = ck * kChunk, te = std::min(nt, t + kChunk); t < te; ++t) {
+            loc.clear();
+            for (int a = 0; a < 3; ++a) {
+                const int32_t v = M.T[3 * t + a];
+                for (int64_t q = vptr[v]; q < vptr[v + 1]; ++q) loc.push_back(vtri[q]);
+            }
+            std::sort(loc.begin(), loc.end());
+            int64_t cnt = 0;
+            for (size_t q = 0; q < loc.size();) {
+                size_t e = q;
+                while (e < loc.size() && loc[e] == loc[q]) ++e;
+                P.tri.push_back(loc[q]);
+                P.cs.push_back((int8_t)(e - q));
+                ++cnt;
+                q = e;
+            }
+            P.len.push_back(cnt);
+            P.max_touch = std::max(P.max_touch, cnt);
+        }
+    });
     M.adj_ptr.assign(nt + 1, 0);
     M.adj_tri.clear();
     M.adj_case.clear();
-    std::vector<std::pair<int32_t, int>> loc;
-    for (int64_t t = 0; t < nt; ++t) {
-        loc.clear();
-        for (int a = 0; a < 3; ++a) {
-            int32_t v = M.T[3 * t + a];
-            for (int64_t q = vptr[v]; q < vptr[v + 1]; ++q) loc.push_back({vtri[q], 1});
+    M.max_touch = 0;
+    int64_t t = 0;
+    for (const Part &P : parts) {
+        for (int64_t c : P.len) {
+            M.adj_ptr[t + 1] = M.adj_ptr[t] + c;
+            ++t;
         }
-        std::sort(loc.begin(), loc.end());
-        for (size_t q = 0; q < loc.size();) {
-            size_t e = q;
-            while (e < loc.size() && loc[e].first == loc[q].first) ++e;
-            M.adj_tri.push_back(loc[q].first);
-            M.adj_case.push_back((int8_t)(e - q));
-            q = e;
-        }
-        M.adj_ptr[t + 1] = (int64_t)M.adj_tri.size();
-        M.max_touch = std::max<int64_t>(M.max_touch, M.adj_ptr[t + 1] - M.adj_ptr[t]);
+        M.adj_tri.insert(M.adj_tri.end(), P.tri.begin(), P.tri.end());
+        M.adj_case.insert(M.adj_case.end(), P.cs.begin(), P.cs.end());
+        M.max_touch = std::max(M.max_touch, P.max_touch);
     }
 }
 
@@ -690,7 +793,7 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
         size_t list_bytes = cap * sizeof(SingPair);
         size_t scratch = 3 * list_bytes + 64;
         void *ws = nullptr;
-        CU(cudaMallocAsync(&ws, scratch, st));
+        CU(lib_malloc_async(&ws, scratch, st));
         unsigned char *wb = (unsigned char *)ws;
         SingPair *lists[3] = {(SingPair *)wb, (SingPair *)(wb + list_bytes),
                               (SingPair *)(wb + 2 * list_bytes)};
@@ -765,7 +868,7 @@ int bem_entries_dp1(bem_mesh mesh, int32_t op, double k, int32_t prec, const int
             n_test * n_trial, n_test * std::max<int64_t>(mesh->max_touch, 1));
         const size_t list_bytes = cap * sizeof(SingPairL);
         void *ws = nullptr;
-        CU(cudaMallocAsync(&ws, 3 * list_bytes + 64, st));
+        CU(lib_malloc_async(&ws, 3 * list_bytes + 64, st));
         unsigned char *wb = (unsigned char *)ws;
         SingPairL *lists[3] = {(SingPairL *)wb, (SingPairL *)(wb + list_bytes),
                                (SingPairL *)(wb + 2 * list_bytes)};
@@ -857,6 +960,7 @@ struct bem_hmat_s {
     DBuf d_tiles, d_acastats;
     int64_t pool_elems = 0;
     double t_tree = 0, t_near = 0, t_far = 0, t_near_reg = 0;
+    double t_clusters = 0, t_blocks = 0, t_lists = 0, t_upload = 0;
     // CUDA graph of the assembly sequence and what it was captured for
     cudaGraphExec_t graph = nullptr;
     int g_op = -1, g_prec = -1;
@@ -886,55 +990,125 @@ namespace {
 // split along the longest axis of its vertex bounding box at the median of
 // the centroids ((v0 + v1) + v2) / 3, ties by triangle index; leaves list
 // their triangles in increasing index order.  Breadth-first numbering.
+// One cluster: its vertex box, and either its leaf order or its split (the
+// median of the centroids along the longest box axis).  Returns the split
+// point, or -1 for a leaf.
+int64_t split_cluster(Cluster &C, std::vector<int32_t> &perm, const std::vector<double> &cen,
+                      const std::vector<double> &tbox, int leaf)
+{
+    double box[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int64_t q = C.b; q < C.e; ++q) {
+        const double *tb = &tbox[6 * (int64_t)perm[q]];
+        for (int c = 0; c < 3; ++c) {
+            box[c] = std::min(box[c], tb[c]);
+            box[3 + c] = std::max(box[3 + c], tb[3 + c]);
+        }
+    }
+    std::memcpy(C.box, box, sizeof(box));
+    const int64_t n = C.e - C.b;
+    if (n <= leaf) {
+        std::sort(perm.begin() + C.b, perm.begin() + C.e);
+        return -1;
+    }
+    int axis = 0;
+    double ext = box[3] - box[0];
+    for (int a = 1; a < 3; ++a)
+        if (box[3 + a] - box[a] > ext) {
+            ext = box[3 + a] - box[a];
+            axis = a;
+        }
+    auto less = [&](int32_t x, int32_t y) {
+        double cx = cen[3 * (int64_t)x + axis], cy = cen[3 * (int64_t)y + axis];
+        return cx < cy || (cx == cy && x < y);
+    };
+    const int64_t mid = C.b + n / 2;
+    std::nth_element(perm.begin() + C.b, perm.begin() + mid, perm.begin() + C.e, less);
+    return mid;
+}
+
+// The tree is grown breadth-first until there are enough clusters to keep
+// the host threads busy; the subtrees below that frontier are grown on the
+// threads (each in its own list, depth-first) and appended in frontier order.
+// The splits, and so the partition, the block tree and every block list, are
+// those of the sequential breadth-first construction; only the cluster
+// numbering below the frontier differs.
 void build_clusters(bem_hmat_s &H)
 {
     const bem_mesh_s &M = *H.mesh;
     const int64_t nt = M.nt;
-    std::vector<double> cen(3 * nt);
-    for (int64_t t = 0; t < nt; ++t)
-        for (int c = 0; c < 3; ++c)
-            cen[3 * t + c] = ((M.V[3 * M.T[3 * t] + c] + M.V[3 * M.T[3 * t + 1] + c]) +
-                              M.V[3 * M.T[3 * t + 2] + c]) / 3.0;
+    std::vector<double> cen(3 * nt), tbox(6 * nt);
+    parallel_tasks((nt + 16383) / 16384, [&](int64_t task) {
+        for (int64_t t = task * 16384, te = std::min(nt, t + 16384); t < te; ++t)
+            for (int c = 0; c < 3; ++c) {
+                const double a = M.V[3 * (int64_t)M.T[3 * t] + c], b = M.V[3 * (int64_t)M.T[3 * t + 1] + c],
+                             d = M.V[3 * (int64_t)M.T[3 * t + 2] + c];
+                cen[3 * t + c] = ((a + b) + d) / 3.0;
+                tbox[6 * t + c] = std::min(std::min(a, b), d);
+                tbox[6 * t + 3 + c] = std::max(std::max(a, b), d);
+            }
+    });
     H.perm.resize(nt);
     std::iota(H.perm.begin(), H.perm.end(), 0);
     H.cl.clear();
     H.cl.push_back({0, nt, -1, -1, {0, 0, 0, 0, 0, 0}});
-    for (size_t head = 0; head < H.cl.size(); ++head) {
-        Cluster C = H.cl[head];
-        double box[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        for (int64_t q = C.b; q < C.e; ++q) {
-            const int32_t *tr = &M.T[3 * (int64_t)H.perm[q]];
-            for (int a = 0; a < 3; ++a)
-                for (int c = 0; c < 3; ++c) {
-                    double x = M.V[3 * (int64_t)tr[a] + c];
-                    box[c] = std::min(box[c], x);
-                    box[3 + c] = std::max(box[3 + c], x);
-                }
-        }
-        std::memcpy(H.cl[head].box, box, sizeof(box));
-        const int64_t n = C.e - C.b;
-        if (n <= H.leaf) {
-            std::sort(H.perm.begin() + C.b, H.perm.begin() + C.e);
-            continue;
-        }
-        int axis = 0;
-        double ext = box[3] - box[0];
-        for (int a = 1; a < 3; ++a)
-            if (box[3 + a] - box[a] > ext) {
-                ext = box[3 + a] - box[a];
-                axis = a;
+    unsigned hw = std::thread::hardware_concurrency();
+    const size_t want = 8 * (size_t)std::max(1u, std::min(hw, 32u));
+    // breadth-first top: the clusters of [head, size) are the frontier
+    size_t head = 0;
+    while (head < H.cl.size() && H.cl.size() - head < want) {
+        const size_t end = H.cl.size();
+        for (size_t q = head; q < end; ++q) {
+            Cluster C = H.cl[q];
+            const int64_t mid = split_cluster(C, H.perm, cen, tbox, H.leaf);
+            H.cl[q] = C;
+            if (mid >= 0) {
+                const int64_t L = (int64_t)H.cl.size();
+                H.cl[q].left = L;
+                H.cl[q].right = L + 1;
+                H.cl.push_back({C.b, mid, -1, -1, {0, 0, 0, 0, 0, 0}});
+                H.cl.push_back({mid, C.e, -1, -1, {0, 0, 0, 0, 0, 0}});
             }
-        auto less = [&](int32_t x, int32_t y) {
-            double cx = cen[3 * (int64_t)x + axis], cy = cen[3 * (int64_t)y + axis];
-            return cx < cy || (cx == cy && x < y);
-        };
-        int64_t mid = C.b + n / 2;
-        std::nth_element(H.perm.begin() + C.b, H.perm.begin() + mid, H.perm.begin() + C.e, less);
-        int64_t L = (int64_t)H.cl.size();
-        H.cl[head].left = L;
-        H.cl[head].right = L + 1;
-        H.cl.push_back({C.b, mid, -1, -1, {0, 0, 0, 0, 0, 0}});
-        H.cl.push_back({mid, C.e, -1, -1, {0, 0, 0, 0, 0, 0}});
+        }
+        head = end;
+        bool any_split = false;
+        for (size_t q = head; q < H.cl.size(); ++q) any_split |= H.cl[q].e - H.cl[q].b > H.leaf;
+        if (!any_split) break;
+    }
+    // subtrees of the frontier clusters, one task each (disjoint perm ranges)
+    const size_t nfront = H.cl.size() - head;
+    std::vector<std::vector<Cluster>> sub(nfront);
+    parallel_tasks((int64_t)nfront, [&](int64_t f) {
+        std::vector<Cluster> &S = sub[f];
+        S.push_back(H.cl[head + f]);
+        for (size_t q = 0; q < S.size(); ++q) {
+            Cluster C = S[q];
+            const int64_t mid = split_cluster(C, H.perm, cen, tbox, H.leaf);
+            if (mid >= 0) {
+                C.left = (int64_t)S.size();   // local index, fixed up below
+                C.right = C.left + 1;
+                S[q] = C;
+                S.push_back({C.b, mid, -1, -1, {0, 0, 0, 0, 0, 0}});
+                S.push_back({mid, C.e, -1, -1, {0, 0, 0, 0, 0, 0}});
+            } else {
+                S[q] = C;
+            }
+        }
+    });
+    // the frontier cluster keeps its index; its descendants follow in order
+    for (size_t f = 0; f < nfront; ++f) {
+        const int64_t base = (int64_t)H.cl.size() - 1;   // local index 1 -> base + 1
+        const std::vector<Cluster> &S = sub[f];
+        auto fix = [&](int64_t l) { return l < 0 ? l : base + l; };
+        Cluster root = S[0];
+        root.left = fix(root.left);
+        root.right = fix(root.right);
+        H.cl[head + f] = root;
+        for (size_t q = 1; q < S.size(); ++q) {
+            Cluster C = S[q];
+            C.left = fix(C.left);
+            C.right = fix(C.right);
+            H.cl.push_back(C);
+        }
     }
     H.iperm.resize(nt);
     for (int64_t p = 0; p < nt; ++p) H.iperm[H.perm[p]] = (int32_t)p;
@@ -958,25 +1132,76 @@ bool admissible(const double *bt, const double *bs, double eta)
     return (dt < ds ? dt : ds) <= eta * dist;
 }
 
+// Block tree: pairs (tau, sigma) from (root, root); an admissible pair, or one
+// with a leaf, is a block; otherwise its children pairs are visited in the
+// order (l,l), (l,r), (r,l), (r,r).  The blocks are listed depth-first ("tree
+// order").  The top of the tree is expanded level by level, which keeps that
+// order, until there are enough pairs for the host threads; the subtrees of
+// the remaining pairs are expanded depth-first on the threads and their
+// blocks concatenated in order.
 void build_blocks(bem_hmat_s &H)
 {
     H.blocks.clear();
-    std::vector<std::pair<int64_t, int64_t>> stack{{0, 0}};
-    while (!stack.empty()) {
-        auto [t, s] = stack.back();
-        stack.pop_back();
+    struct Item {
+        int64_t t, s;
+        int8_t state;  // 0 open, 1 admissible block, 2 dense block
+    };
+    auto classify = [&](int64_t t, int64_t s) -> int8_t {
         const Cluster &T = H.cl[t], &S = H.cl[s];
-        bool adm = admissible(T.box, S.box, H.eta);
-        if (adm || T.left < 0 || S.left < 0) {
-            H.blocks.push_back({t, s, adm});
-            continue;
+        const bool adm = admissible(T.box, S.box, H.eta);
+        if (adm) return 1;
+        if (T.left < 0 || S.left < 0) return 2;
+        return 0;
+    };
+    unsigned hw = std::thread::hardware_concurrency();
+    const size_t want = 8 * (size_t)std::max(1u, std::min(hw, 32u));
+    std::vector<Item> front{{0, 0, classify(0, 0)}};
+    for (;;) {
+        size_t open = 0;
+        for (const Item &it : front) open += it.state == 0;
+        if (open == 0 || open >= want) break;
+        std::vector<Item> next;
+        next.reserve(front.size() + 3 * open);
+        for (const Item &it : front) {
+            if (it.state != 0) {
+                next.push_back(it);
+                continue;
+            }
+            const Cluster &T = H.cl[it.t], &S = H.cl[it.s];
+            const int64_t ch[4][2] = {{T.left, S.left}, {T.left, S.right}, {T.right, S.left},
+                                      {T.right, S.right}};
+            for (auto &c : ch) next.push_back({c[0], c[1], classify(c[0], c[1])});
         }
-        // visit children in the order (l,l), (l,r), (r,l), (r,r)
-        stack.push_back({T.right, S.right});
-        stack.push_back({T.right, S.left});
-        stack.push_back({T.left, S.right});
-        stack.push_back({T.left, S.left});
+        front.swap(next);
     }
+    std::vector<std::vector<BlockH>> sub(front.size());
+    parallel_tasks((int64_t)front.size(), [&](int64_t f) {
+        const Item &it = front[f];
+        std::vector<BlockH> &out = sub[f];
+        if (it.state != 0) {
+            out.push_back({it.t, it.s, it.state == 1});
+            return;
+        }
+        std::vector<std::pair<int64_t, int64_t>> stack{{it.t, it.s}};
+        while (!stack.empty()) {
+            auto [t, s] = stack.back();
+            stack.pop_back();
+            const int8_t st = classify(t, s);
+            if (st != 0) {
+                out.push_back({t, s, st == 1});
+                continue;
+            }
+            const Cluster &T = H.cl[t], &S = H.cl[s];
+            stack.push_back({T.right, S.right});
+            stack.push_back({T.right, S.left});
+            stack.push_back({T.left, S.right});
+            stack.push_back({T.left, S.left});
+        }
+    });
+    size_t total = 0;
+    for (auto &v : sub) total += v.size();
+    H.blocks.reserve(total);
+    for (auto &v : sub) H.blocks.insert(H.blocks.end(), v.begin(), v.end());
 }
 
 // Block lists.  Near-field blocks keep tree order and get consecutive dense
@@ -1015,7 +1240,20 @@ void build_lists(bem_hmat_s &H)
         }
     }
     H.near_total = off;
-    std::sort(key.begin(), key.end());
+    // the keys were made in increasing block order, so a stable sort on the
+    // upper 32 bits (class, size) alone orders them fully: two 16-bit LSD
+    // counting passes
+    {
+        std::vector<uint64_t> tmp(key.size());
+        for (int pass = 0; pass < 2; ++pass) {
+            const int sh = 32 + 16 * pass;
+            std::vector<int64_t> cnt(65537, 0);
+            for (uint64_t k : key) ++cnt[((k >> sh) & 0xffffu) + 1];
+            for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
+            for (uint64_t k : key) tmp[cnt[(k >> sh) & 0xffffu]++] = k;
+            key.swap(tmp);
+        }
+    }
     H.far.resize(key.size());
     H.far_block_id.resize(key.size());
     H.max_m_big = H.max_m_small = 0;
@@ -1092,29 +1330,42 @@ void build_lists(bem_hmat_s &H)
         if (H.dofs == 1) H.sing[c].reserve(ncase[c]);
         else H.singl[c].reserve(ncase[c]);
     }
-    for (int64_t p = 0; p < nt; ++p) {
-        const int32_t t = H.perm[p];
-        const int64_t l = leaf_of[p];
-        const int64_t *b0 = nsb.data() + nptr[l], *b1 = nsb.data() + nptr[l + 1];
-        for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) {
-            const int32_t u = M.adj_tri[a];
-            const int64_t q = H.iperm[u];
-            // near block of this row leaf whose column range holds q
-            const int64_t *it = std::upper_bound(b0, b1, q);
-            if (it == b0) throw std::runtime_error("touching pair outside the near field");
-            const NearBlock &N = H.near[nq[nptr[l] + (it - 1 - b0)]];
-            if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
-            if (H.dofs == 1) {
-                const int64_t dest = N.off + (p - N.tb) * (N.se - N.sb) + (q - N.sb);
-                H.sing[M.adj_case[a] - 1].push_back({t, u, dest});
-            } else {
-                // local (0, 0) of the pair in the block of 3m x 3n dofs
-                const int64_t ld = 3 * (N.se - N.sb);
-                const int64_t dest = N.off + 3 * (p - N.tb) * ld + 3 * (q - N.sb);
-                H.singl[M.adj_case[a] - 1].push_back({t, u, dest, ld});
+    // rows in chunks on the host threads, each chunk's pairs in row order,
+    // concatenated in chunk order (the sequential order)
+    constexpr int64_t kRowChunk = 8192;
+    const int64_t nchunk = (nt + kRowChunk - 1) / kRowChunk;
+    std::vector<std::array<std::vector<SingPair>, 3>> cs(H.dofs == 1 ? nchunk : 0);
+    std::vector<std::array<std::vector<SingPairL>, 3>> csl(H.dofs == 3 ? nchunk : 0);
+    parallel_tasks(nchunk, [&](int64_t ck) {
+        for (int64_t p = ck * kRowChunk, pe = std::min(nt, p + kRowChunk); p < pe; ++p) {
+            const int32_t t = H.perm[p];
+            const int64_t l = leaf_of[p];
+            const int64_t *b0 = nsb.data() + nptr[l], *b1 = nsb.data() + nptr[l + 1];
+            for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) {
+                const int32_t u = M.adj_tri[a];
+                const int64_t q = H.iperm[u];
+                // near block of this row leaf whose column range holds q
+                const int64_t *it = std::upper_bound(b0, b1, q);
+                if (it == b0) throw std::runtime_error("touching pair outside the near field");
+                const NearBlock &N = H.near[nq[nptr[l] + (it - 1 - b0)]];
+                if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
+                if (H.dofs == 1) {
+                    const int64_t dest = N.off + (p - N.tb) * (N.se - N.sb) + (q - N.sb);
+                    cs[ck][M.adj_case[a] - 1].push_back({t, u, dest});
+                } else {
+                    // local (0, 0) of the pair in the block of 3m x 3n dofs
+                    const int64_t ld = 3 * (N.se - N.sb);
+                    const int64_t dest = N.off + 3 * (p - N.tb) * ld + 3 * (q - N.sb);
+                    csl[ck][M.adj_case[a] - 1].push_back({t, u, dest, ld});
+                }
             }
         }
-    }
+    });
+    for (int64_t ck = 0; ck < nchunk; ++ck)
+        for (int c = 0; c < 3; ++c) {
+            if (H.dofs == 1) H.sing[c].insert(H.sing[c].end(), cs[ck][c].begin(), cs[ck][c].end());
+            else H.singl[c].insert(H.singl[c].end(), csl[ck][c].begin(), csl[ck][c].end());
+        }
     if (H.dofs == 3) {
         // every list in dof units: ranges times three
         for (NearBlock &N : H.near) {
@@ -1217,10 +1468,17 @@ int hmat_build_tree_impl(bem_mesh mesh, int32_t leaf_size, double eta, cudaStrea
             H->tiny_max = H->dofs == 1 ? g_tuning.lane_max_rows : 0;
         }
         build_clusters(*H);
+        const double t1 = now_ms();
         build_blocks(*H);
+        const double t2 = now_ms();
         build_lists(*H);
+        const double t3 = now_ms();
         if (st != kHostOnly) upload_tree(*H, st);
         H->t_tree = now_ms() - t0;
+        H->t_clusters = t1 - t0;
+        H->t_blocks = t2 - t1;
+        H->t_lists = t3 - t2;
+        H->t_upload = H->t_tree - (t3 - t0);
         ++mesh->hmat_refs;
         *out = H.release();
         return BEM_OK;
@@ -1327,6 +1585,13 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         int64_t want = sum_mn * KCHUNK * 4 + 1024;
         {
             size_t fr = 0, tot = 0;
+            // blocks cached in the library's pool are not free to the sizing:
+            // give them back first when the wish would not fit otherwise
+            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess &&
+                (double)want * esz > (double)fr + (double)H->d_pool.bytes - 4.0 * (1 << 30)) {
+                CU(cudaStreamSynchronize(st));
+                pool_trim();
+            }
             if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
                 const double margin = 4.0 * (1 << 30) + 17.0 * H->ndof * esz;
                 const int64_t avail =
@@ -1580,6 +1845,10 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         s.prec = H->prec;
         s.space = H->space;
         s.n_dofs = H->space == BEM_P1 ? H->mesh->nv : H->ndof;
+        s.time_tree_clusters_ms = H->t_clusters;
+        s.time_tree_blocks_ms = H->t_blocks;
+        s.time_tree_lists_ms = H->t_lists;
+        s.time_tree_upload_ms = H->t_upload;
         for (int c = 0; c < 3; ++c)
             if (H->dofs == 3) s.singular_pairs[c] = (int64_t)H->singl[c].size();
         *out = s;
