@@ -1052,7 +1052,7 @@ void build_clusters(bem_hmat_s &H)
     H.cl.clear();
     H.cl.push_back({0, nt, -1, -1, {0, 0, 0, 0, 0, 0}});
     unsigned hw = std::thread::hardware_concurrency();
-    const size_t want = 8 * (size_t)std::max(1u, std::min(hw, 32u));
+    const size_t want = 2 * (size_t)std::max(1u, std::min(hw, 32u));
     // breadth-first top: the clusters of [head, size) are the frontier
     size_t head = 0;
     while (head < H.cl.size() && H.cl.size() - head < want) {
@@ -1216,28 +1216,55 @@ void build_lists(bem_hmat_s &H)
     if (nb >= (int64_t(1) << 32) || nt >= (int64_t(1) << 29))
         throw std::runtime_error("problem too large for the block-list keys");
     constexpr uint64_t kSizeMask = (uint64_t(1) << 30) - 1;
-    int64_t nnear = 0;
-    for (const BlockH &B : H.blocks) nnear += !B.adm;
+    // near blocks (tree order, consecutive dense storage) and keys of the
+    // admissible blocks, in block chunks on the host threads, joined in order
+    constexpr int64_t kBlkChunk = 16384;
+    const int64_t nbc = (nb + kBlkChunk - 1) / kBlkChunk;
+    struct BlkPart {
+        std::vector<NearBlock> near;
+        std::vector<int64_t> near_id;
+        std::vector<uint64_t> key;
+        int64_t elems = 0, ncls[3] = {0, 0, 0};
+    };
+    std::vector<BlkPart> bp(nbc);
+    parallel_tasks(nbc, [&](int64_t ck) {
+        BlkPart &P = bp[ck];
+        for (int64_t b = ck * kBlkChunk, be = std::min(nb, b + kBlkChunk); b < be; ++b) {
+            const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
+            const int64_t m = T.e - T.b, n = S.e - S.b;
+            if (!H.blocks[b].adm) {
+                P.near.push_back({T.b, T.e, S.b, S.e, P.elems});   // offset within the chunk
+                P.near_id.push_back(b);
+                P.elems += m * n * H.dofs * H.dofs;
+            } else {
+                const int64_t mx = std::max(m, n) * H.dofs;
+                const uint64_t cls = mx > H.small_max ? 0 : mx > H.tiny_max ? 1 : 2;
+                ++P.ncls[cls];
+                P.key.push_back(cls << 62 | (kSizeMask - (uint64_t)(m + n)) << 32 | (uint64_t)b);
+            }
+        }
+    });
+    int64_t nnear = 0, nkey = 0;
+    for (const BlkPart &P : bp) {
+        nnear += (int64_t)P.near.size();
+        nkey += (int64_t)P.key.size();
+    }
     H.near.clear();
     H.near.reserve(nnear);
     H.near_block_id.clear();
     H.near_block_id.reserve(nnear);
     std::vector<uint64_t> key;
-    key.reserve(nb - nnear);
+    key.reserve(nkey);
     int64_t off = 0, ncls[3] = {0, 0, 0};
-    for (int64_t b = 0; b < nb; ++b) {
-        const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
-        const int64_t m = T.e - T.b, n = S.e - S.b;
-        if (!H.blocks[b].adm) {
-            H.near.push_back({T.b, T.e, S.b, S.e, off});
-            H.near_block_id.push_back(b);
-            off += m * n * H.dofs * H.dofs;
-        } else {
-            const int64_t mx = std::max(m, n) * H.dofs;
-            const uint64_t cls = mx > H.small_max ? 0 : mx > H.tiny_max ? 1 : 2;
-            ++ncls[cls];
-            key.push_back(cls << 62 | (kSizeMask - (uint64_t)(m + n)) << 32 | (uint64_t)b);
+    for (const BlkPart &P : bp) {
+        for (NearBlock N : P.near) {
+            N.off += off;
+            H.near.push_back(N);
         }
+        H.near_block_id.insert(H.near_block_id.end(), P.near_id.begin(), P.near_id.end());
+        key.insert(key.end(), P.key.begin(), P.key.end());
+        off += P.elems;
+        for (int c = 0; c < 3; ++c) ncls[c] += P.ncls[c];
     }
     H.near_total = off;
     // the keys were made in increasing block order, so a stable sort on the
@@ -1257,18 +1284,27 @@ void build_lists(bem_hmat_s &H)
     H.far.resize(key.size());
     H.far_block_id.resize(key.size());
     H.max_m_big = H.max_m_small = 0;
-    for (size_t f = 0; f < key.size(); ++f) {
-        const int64_t b = (int64_t)(key[f] & 0xffffffffu);
-        const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
-        FarBlock &F = H.far[f];
-        std::memset(&F, 0, sizeof(F));
-        F.tb = T.b;
-        F.te = T.e;
-        F.sb = S.b;
-        F.se = S.e;
-        H.far_block_id[f] = b;
-        if ((int64_t)f < ncls[0]) H.max_m_big = std::max(H.max_m_big, T.e - T.b);
-        else if ((int64_t)f < ncls[0] + ncls[1]) H.max_m_small = std::max(H.max_m_small, T.e - T.b);
+    const int64_t nfar = (int64_t)key.size();
+    const int64_t nfc = (nfar + kBlkChunk - 1) / kBlkChunk;
+    std::vector<int64_t> mbig(nfc, 0), msmall(nfc, 0);
+    parallel_tasks(nfc, [&](int64_t ck) {
+        for (int64_t f = ck * kBlkChunk, fe = std::min(nfar, f + kBlkChunk); f < fe; ++f) {
+            const int64_t b = (int64_t)(key[f] & 0xffffffffu);
+            const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
+            FarBlock &F = H.far[f];
+            std::memset(&F, 0, sizeof(F));
+            F.tb = T.b;
+            F.te = T.e;
+            F.sb = S.b;
+            F.se = S.e;
+            H.far_block_id[f] = b;
+            if (f < ncls[0]) mbig[ck] = std::max(mbig[ck], T.e - T.b);
+            else if (f < ncls[0] + ncls[1]) msmall[ck] = std::max(msmall[ck], T.e - T.b);
+        }
+    });
+    for (int64_t ck = 0; ck < nfc; ++ck) {
+        H.max_m_big = std::max(H.max_m_big, mbig[ck]);
+        H.max_m_small = std::max(H.max_m_small, msmall[ck]);
     }
     H.n_big = ncls[0];
     H.n_small = ncls[1];
@@ -1327,8 +1363,7 @@ void build_lists(bem_hmat_s &H)
     for (int c = 0; c < 3; ++c) {
         H.sing[c].clear();
         H.singl[c].clear();
-        if (H.dofs == 1) H.sing[c].reserve(ncase[c]);
-        else H.singl[c].reserve(ncase[c]);
+        (void)ncase;
     }
     // rows in chunks on the host threads, each chunk's pairs in row order,
     // concatenated in chunk order (the sequential order)
@@ -1337,6 +1372,17 @@ void build_lists(bem_hmat_s &H)
     std::vector<std::array<std::vector<SingPair>, 3>> cs(H.dofs == 1 ? nchunk : 0);
     std::vector<std::array<std::vector<SingPairL>, 3>> csl(H.dofs == 3 ? nchunk : 0);
     parallel_tasks(nchunk, [&](int64_t ck) {
+        {
+            int64_t cnt[3] = {0, 0, 0};
+            for (int64_t p = ck * kRowChunk, pe = std::min(nt, p + kRowChunk); p < pe; ++p) {
+                const int32_t t = H.perm[p];
+                for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) ++cnt[M.adj_case[a] - 1];
+            }
+            for (int c = 0; c < 3; ++c) {
+                if (H.dofs == 1) cs[ck][c].reserve(cnt[c]);
+                else csl[ck][c].reserve(cnt[c]);
+            }
+        }
         for (int64_t p = ck * kRowChunk, pe = std::min(nt, p + kRowChunk); p < pe; ++p) {
             const int32_t t = H.perm[p];
             const int64_t l = leaf_of[p];
@@ -1361,11 +1407,18 @@ void build_lists(bem_hmat_s &H)
             }
         }
     });
-    for (int64_t ck = 0; ck < nchunk; ++ck)
-        for (int c = 0; c < 3; ++c) {
-            if (H.dofs == 1) H.sing[c].insert(H.sing[c].end(), cs[ck][c].begin(), cs[ck][c].end());
-            else H.singl[c].insert(H.singl[c].end(), csl[ck][c].begin(), csl[ck][c].end());
-        }
+    // join the chunks in order: offsets first, then the copies on the threads
+    for (int c = 0; c < 3; ++c) {
+        std::vector<int64_t> at(nchunk + 1, 0);
+        for (int64_t ck = 0; ck < nchunk; ++ck)
+            at[ck + 1] = at[ck] + (int64_t)(H.dofs == 1 ? cs[ck][c].size() : csl[ck][c].size());
+        if (H.dofs == 1) H.sing[c].resize(at[nchunk]);
+        else H.singl[c].resize(at[nchunk]);
+        parallel_tasks(nchunk, [&](int64_t ck) {
+            if (H.dofs == 1) std::copy(cs[ck][c].begin(), cs[ck][c].end(), H.sing[c].begin() + at[ck]);
+            else std::copy(csl[ck][c].begin(), csl[ck][c].end(), H.singl[c].begin() + at[ck]);
+        });
+    }
     if (H.dofs == 3) {
         // every list in dof units: ranges times three
         for (NearBlock &N : H.near) {
