@@ -126,6 +126,9 @@ k_entries(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int
 // triangle in registers for the whole tile, and a warp evaluates one row at a
 // time, reading the row's triangle with eight broadcast 128-bit loads.
 constexpr int kTileThreads = 128, kTileRows = 64;
+// CTAs per SM the single-layer instantiation is compiled for (measured: 7
+// is 1-2 % faster than the 6 the registers allow unbounded, 8 spills)
+constexpr int kSlpMinBlocks = 7;
 constexpr int kRowsPerWarp = kTileRows / (kTileThreads / 32);
 static_assert(kTileRows % (kTileThreads / 32) == 0 && kRowsPerWarp <= 32, "rows per warp");
 
@@ -155,19 +158,20 @@ __device__ __forceinline__ void push_singular(int s, int32_t i, int32_t j, int64
 }
 
 template <int OP, bool CPLX>
-__global__ void __launch_bounds__(kTileThreads)
-k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int64_t n_test,
-                const int32_t *__restrict__ trial, int64_t n_trial, void *out, SingPair *l1,
-                SingPair *l2, SingPair *l3, unsigned long long *counts, unsigned long long cap,
-                int *err)
+__device__ __forceinline__ void
+entries_tiled_body(const DevGeom &g, const QuadRule &R, double k, const int32_t *__restrict__ test,
+                   int64_t n_test, const int32_t *__restrict__ trial, int64_t n_trial, void *out,
+                   SingPair *l1, SingPair *l2, SingPair *l3, unsigned long long *counts,
+                   unsigned long long cap, int *err)
 {
     using E = RegularEntry<OP, CPLX, 1>;
     __shared__ __align__(16) float rows_s[kTileRows][kTileFields];
     __shared__ int32_t rid_s[kTileRows];
-    __shared__ float box_s[2][6];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     constexpr int nw = kTileThreads / 32;
-    static_assert(kTileRows <= 2 * 32 && nw >= 2, "row boxes: warps 0 and 1");
+    constexpr int kBoxWarps = (kTileRows + 31) / 32;
+    __shared__ float box_s[kBoxWarps][6];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    static_assert(kBoxWarps <= nw, "row boxes: one warp per 32 rows");
     const int64_t ncb = (n_trial + 31) / 32, nrb = (n_test + kTileRows - 1) / kTileRows;
     const int64_t ntiles = ncb * nrb;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -226,7 +230,7 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
                 blo[c] = INFINITY;
                 bhi[c] = -INFINITY;
             }
-            if (w < 2) {
+            if (w < kBoxWarps) {
                 const int r = threadIdx.x;
                 if (r < nr && rid_s[r] >= 0) {
                     float q2 = 0.f;
@@ -283,8 +287,12 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
             __syncthreads();
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float rlo = fminf(box_s[0][c], box_s[1][c]);
-                const float rhi = fmaxf(box_s[0][3 + c], box_s[1][3 + c]);
+                float rlo = box_s[0][c], rhi = box_s[0][3 + c];
+#pragma unroll
+                for (int q = 1; q < kBoxWarps; ++q) {
+                    rlo = fminf(rlo, box_s[q][c]);
+                    rhi = fmaxf(rhi, box_s[q][3 + c]);
+                }
                 far_tile |= clo[c] > rhi || rlo > chi[c];
             }
         }
@@ -340,6 +348,29 @@ k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ tes
             }
         }
     }
+}
+
+template <int OP, bool CPLX>
+__global__ void __launch_bounds__(kTileThreads)
+k_entries_tiled(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test, int64_t n_test,
+                const int32_t *__restrict__ trial, int64_t n_trial, void *out, SingPair *l1,
+                SingPair *l2, SingPair *l3, unsigned long long *counts, unsigned long long cap,
+                int *err)
+{
+    entries_tiled_body<OP, CPLX>(g, R, k, test, n_test, trial, n_trial, out, l1, l2, l3, counts,
+                                 cap, err);
+}
+
+// The Laplace single layer with a register bound that keeps kSlpMinBlocks
+// CTAs on an SM
+__global__ void __launch_bounds__(kTileThreads, kSlpMinBlocks)
+k_entries_tiled_slp(DevGeom g, QuadRule R, const int32_t *__restrict__ test, int64_t n_test,
+                    const int32_t *__restrict__ trial, int64_t n_trial, void *out, SingPair *l1,
+                    SingPair *l2, SingPair *l3, unsigned long long *counts, unsigned long long cap,
+                    int *err)
+{
+    entries_tiled_body<0, false>(g, R, 0.0, test, n_test, trial, n_trial, out, l1, l2, l3, counts,
+                                 cap, err);
 }
 
 // ---- Sauter-Schwab singular pairs (FP64) -----------------------------------
@@ -576,18 +607,28 @@ static void entries_launch(const DevGeom &g, const QuadRule &R, double k, const 
 {
     if constexpr (PREC == 1) {
         // persistent grid: every SM filled, tiles handed out round-robin
+        constexpr bool slp = OP == 0 && !CPLX;
         static int per_sm = 0;
         if (!per_sm) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_entries_tiled<OP, CPLX>,
-                                                          kTileThreads, 0);
+            if constexpr (slp)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_entries_tiled_slp,
+                                                              kTileThreads, 0);
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_entries_tiled<OP, CPLX>,
+                                                              kTileThreads, 0);
             if (per_sm < 1) per_sm = 1;
         }
         const int64_t ntiles = (n_trial + 31) / 32 * ((n_test + kTileRows - 1) / kTileRows);
         int64_t grid = (int64_t)num_sms_cached() * per_sm;
         if (grid > ntiles) grid = ntiles;
-        k_entries_tiled<OP, CPLX><<<(unsigned)grid, kTileThreads, 0, st>>>(
-            g, R, k, test, n_test, trial, n_trial, out, lists[0], lists[1], lists[2], counts, cap,
-            err);
+        if constexpr (slp)
+            k_entries_tiled_slp<<<(unsigned)grid, kTileThreads, 0, st>>>(
+                g, R, test, n_test, trial, n_trial, out, lists[0], lists[1], lists[2], counts, cap,
+                err);
+        else
+            k_entries_tiled<OP, CPLX><<<(unsigned)grid, kTileThreads, 0, st>>>(
+                g, R, k, test, n_test, trial, n_trial, out, lists[0], lists[1], lists[2], counts,
+                cap, err);
         count_launches(1);
     } else {
         int64_t gx = (n_trial + kEntBx - 1) / kEntBx;
