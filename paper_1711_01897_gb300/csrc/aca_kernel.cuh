@@ -408,7 +408,12 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 typename L::Tri tr;
                 L::load(g, tb / 3 + rt, tr);
                 C2 v[3];
-                L::template eval<1>(tr, tj, R, k, beta, v);
+                // the single-layer kernel is symmetric: column beta of the
+                // local matrix of (T_r, T_j) is row beta of (T_j, T_r), so the
+                // row evaluator serves both (one quadrature body in the
+                // kernel instead of two)
+                if constexpr (OP == 0) L::template eval<0>(tj, tr, R, k, beta, v);
+                else L::template eval<1>(tr, tj, R, k, beta, v);
 #pragma unroll
                 for (int al = 0; al < 3; ++al) {
                     const int64_t r = 3 * rt + al;
