@@ -191,7 +191,8 @@ def quadrature_roofline(bem, mesh, V, T, dev, stream, flush, reps: int = 3):
 # CPU oracle arm (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7, nthreads: int = 0):
+def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7, nthreads: int = 0,
+                       ops=None, k: float = 0.0, eps: float = EPS):
     """Times the oracle's H-matrix assembly (Algorithm "H-Matrix Assembly":
     dense near blocks + ACA blocks, SLP and DLP) on a seeded sample of the
     workload's leaf blocks; returns integrals/s, threads, description."""
@@ -211,8 +212,8 @@ def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7, nthrea
         ids = np.concatenate([rng.choice(far, nf, replace=False), rng.choice(near, nn, replace=False)])
         t0 = time.perf_counter()
         ent = 0
-        for op in (oracle.SLP, oracle.DLP):
-            hm = oracle.hmat_assemble(V, T, op, 0.0, LEAF, ETA, EPS, block_ids=ids, nthreads=nthreads)
+        for op in (ops if ops is not None else (oracle.SLP, oracle.DLP)):
+            hm = oracle.hmat_assemble(V, T, op, k, LEAF, ETA, eps, block_ids=ids, nthreads=nthreads)
             ent += hm.entries_evaluated
         dt = time.perf_counter() - t0
         total_entries += ent
@@ -221,9 +222,11 @@ def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7, nthrea
         if total_t >= seconds_target or frac >= 0.5:
             break
         frac = min(0.5, frac * max(2.0, seconds_target / max(dt, 1e-3) * 0.7))
+    names = "+".join({0: "SLP", 1: "DLP", 2: "ADLP"}[o] for o in (ops if ops is not None else (0, 1)))
     return (total_entries / total_t, nthreads if nthreads > 0 else oracle.num_threads(),
             f"{used} of {bl.shape[0]} leaf blocks (near and admissible, seeded stratified sample), "
-            f"SLP+DLP, FP64 oracle, {total_entries} integrals in {total_t:.1f} s")
+            f"{names}{', k = %g' % k if k else ''}, FP64 oracle, {total_entries} integrals in "
+            f"{total_t:.1f} s")
 
 
 def run_reference(args):
@@ -443,6 +446,11 @@ def run_gpu(args):
                             "far_blocks": st_slp["n_blocks_far"], "near_blocks": st_slp["n_blocks_near"]},
                 "h_assembly_ms": {"SLP": st_slp["time_near_ms"] + st_slp["time_far_ms"],
                                   "DLP": st_dlp["time_near_ms"] + st_dlp["time_far_ms"]},
+                "integrals_per_s_by_phase": {
+                    "far_field_aca": (st_slp["far_entries"] + st_dlp["far_entries"])
+                                     / (per_step["aca"] * 1e-3),
+                    "near_regular": near_reg / (per_step["near_regular"] * 1e-3),
+                    "singular": sum(sing) / (per_step["singular"] * 1e-3)},
                 "tree_ms": st_slp["time_tree_ms"],
                 "ranks": {"SLP": [st_slp["rank_min"], st_slp["rank_mean"], st_slp["rank_max"]],
                           "DLP": [st_dlp["rank_min"], st_dlp["rank_mean"], st_dlp["rank_max"]]},
@@ -612,6 +620,14 @@ def run_large(args, spec):
     A = oracle.entries(V, T, 0, k, rows, np.arange(n, dtype=np.int32))
     ref = A @ xh
     t_or = time.perf_counter() - t1
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's H-matrix assembly on a stratified sample of this mesh's
+        # leaf blocks, extrapolated to the whole assembly by its integrals
+        rate, cores, sample = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds,
+                                                 ops=(spec["op"],), k=k, eps=spec["eps"])
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "extrapolated_assembly_s": (ents / args.steps) / rate}
     got = y.cpu().numpy()[rows]
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     tot_ms = float(np.sum(asm_ms))
@@ -631,7 +647,7 @@ def run_large(args, spec):
                           "p99": float(np.percentile(mv_ms, 99)), "count": len(mv_ms)},
             "matvec_gbs": (st["near_bytes"] + st["factor_bytes"]) / (np.median(mv_ms) * 1e-3) / 1e9,
             "sampled_rows_rel_err": err, "tolerance": 2 * spec["eps"],
-            "oracle_rows_s": t_or, "clocks": clocks}
+            "oracle_rows_s": t_or, "cpu_baseline": cpu, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
