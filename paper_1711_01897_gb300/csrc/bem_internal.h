@@ -75,11 +75,12 @@ struct SingPair {
 };
 
 // A touching pair of a piecewise linear matrix: its 3 x 3 local matrix goes to
-// dest + alpha * ld + beta (alpha, beta: stored vertex indices).
+// dest + alpha * rs + beta * cs (alpha, beta: stored vertex indices; rs, cs:
+// the strides of the output's rows and columns).
 struct SingPairL {
     int32_t i, j;
     int64_t dest;
-    int64_t ld;
+    int32_t rs, cs;
 };
 
 struct FarBlock {
@@ -96,6 +97,9 @@ struct FarChunks {
     int64_t c[NCHUNK];
 };
 
+// A dense (near-field) block, stored column-major: entry (r, c) at
+// off + c * (te - tb) + r, so that the lanes that own consecutive rows in the
+// product read consecutive addresses.
 struct NearBlock {
     int64_t tb, te, sb, se;
     int64_t off;                    // element offset of the dense block

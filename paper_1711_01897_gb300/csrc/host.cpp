@@ -833,6 +833,7 @@ int bem_entries_dp1(bem_mesh mesh, int32_t op, double k, int32_t prec, const int
         if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
         if (n_test < 0 || n_trial < 0) return fail(BEM_E_ARG, "negative size");
         if (n_test == 0 || n_trial == 0) return BEM_OK;
+        if (3 * n_trial >= (int64_t(1) << 31)) return fail(BEM_E_ARG, "n_trial too large");
         if (!test_tris || !trial_tris || !out) return fail(BEM_E_ARG, "null array");
         cudaStream_t st = (cudaStream_t)cuda_stream;
         DeviceConsts &D = device_consts();
@@ -1396,13 +1397,15 @@ void build_lists(bem_hmat_s &H)
                 const NearBlock &N = H.near[nq[nptr[l] + (it - 1 - b0)]];
                 if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
                 if (H.dofs == 1) {
-                    const int64_t dest = N.off + (p - N.tb) * (N.se - N.sb) + (q - N.sb);
+                    // column-major block
+                    const int64_t dest = N.off + (q - N.sb) * (N.te - N.tb) + (p - N.tb);
                     cs[ck][M.adj_case[a] - 1].push_back({t, u, dest});
                 } else {
-                    // local (0, 0) of the pair in the block of 3m x 3n dofs
-                    const int64_t ld = 3 * (N.se - N.sb);
-                    const int64_t dest = N.off + 3 * (p - N.tb) * ld + 3 * (q - N.sb);
-                    csl[ck][M.adj_case[a] - 1].push_back({t, u, dest, ld});
+                    // local (0, 0) of the pair in the column-major block of
+                    // 3m x 3n dofs: rows step by 1, columns by 3m
+                    const int64_t ld = 3 * (N.te - N.tb);
+                    const int64_t dest = N.off + 3 * (q - N.sb) * ld + 3 * (p - N.tb);
+                    csl[ck][M.adj_case[a] - 1].push_back({t, u, dest, 1, (int32_t)ld});
                 }
             }
         }
@@ -1940,8 +1943,15 @@ int hmat_block_dense(bem_hmat H, int64_t block, void *out, int32_t *rank)
         if (!H->blocks[block].adm) {
             auto it = std::find(H->near_block_id.begin(), H->near_block_id.end(), block);
             const NearBlock &N = H->near[it - H->near_block_id.begin()];
-            size_t bytes = (N.te - N.tb) * (N.se - N.sb) * esz;
-            CU(cudaMemcpy(out, H->d_near_data.as<char>() + N.off * esz, bytes, cudaMemcpyDeviceToHost));
+            const int64_t m = N.te - N.tb, n = N.se - N.sb;
+            std::vector<char> colmajor((size_t)(m * n) * esz);
+            CU(cudaMemcpy(colmajor.data(), H->d_near_data.as<char>() + N.off * esz, colmajor.size(),
+                          cudaMemcpyDeviceToHost));
+            // the device keeps the block column-major; the caller gets rows
+            char *o = (char *)out;
+            for (int64_t i = 0; i < m; ++i)
+                for (int64_t j = 0; j < n; ++j)
+                    std::memcpy(o + (i * n + j) * esz, colmajor.data() + (j * m + i) * esz, esz);
             if (rank) *rank = -1;
             return BEM_OK;
         }

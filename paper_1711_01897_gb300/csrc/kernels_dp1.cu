@@ -17,12 +17,13 @@ __device__ __forceinline__ void store_val1(void *out, int64_t idx, C2 v)
 }
 
 template <bool CPLX>
-__device__ __forceinline__ void store_local(void *out, int64_t dest, int64_t ld, const C2 *v)
+__device__ __forceinline__ void store_local(void *out, int64_t dest, int64_t rs, int64_t cs,
+                                            const C2 *v)
 {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) store_val1<CPLX>(out, dest + a * ld + b, v[3 * a + b]);
+        for (int b = 0; b < 3; ++b) store_val1<CPLX>(out, dest + a * rs + b * cs, v[3 * a + b]);
 }
 
 int num_sms_dp1()
@@ -77,7 +78,7 @@ k_entries_dp1(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test,
             const unsigned long long slot = atomicAdd(&counts[s - 1], 1ull);
             if (slot < cap) {
                 SingPairL *L = s == 1 ? l1 : (s == 2 ? l2 : l3);
-                L[slot] = {i, j, dest, ld};
+                L[slot] = {i, j, dest, (int32_t)ld, 1};
             } else {
                 atomicExch(err, 2);
             }
@@ -87,14 +88,14 @@ k_entries_dp1(DevGeom g, QuadRule R, double k, const int32_t *__restrict__ test,
         E::load(g, i, ta);
         C2 v[9];
         E::template eval<2>(ta, tb, R, k, 0, v);
-        store_local<CPLX>(out, dest, ld, v);
+        store_local<CPLX>(out, dest, ld, 1, v);
     }
 }
 
 // Near-field blocks of a DP1 H-matrix: one warp per dense block, element
-// pairs flattened row-major over the lanes; every pair writes its 3 x 3
-// local matrix.  Touching pairs are overwritten by the singular kernel that
-// follows on the same stream.
+// pairs flattened over the lanes; every pair writes its 3 x 3 local matrix
+// into the column-major block.  Touching pairs are overwritten by the
+// singular kernel that follows on the same stream.
 constexpr int kNearDp1Threads = 128;
 
 template <int OP, bool CPLX, int PREC>
@@ -110,16 +111,16 @@ k_near_dp1(DevGeom g, QuadRule R, double k, const NearBlock *__restrict__ blocks
         const NearBlock B = blocks[bk];
         const int64_t t0 = B.tb / 3, s0 = B.sb / 3;
         const int mt = (int)((B.te - B.tb) / 3), nt = (int)((B.se - B.sb) / 3);
-        const int64_t ld = B.se - B.sb;
+        const int64_t ld = B.te - B.tb;   // column stride of the column-major block
         const int64_t tot = (int64_t)mt * nt;
         for (int64_t e = lane; e < tot; e += 32) {
-            const int r = (int)(e / nt), c = (int)(e - (int64_t)r * nt);
+            const int c = (int)(e / mt), r = (int)(e - (int64_t)c * mt);
             typename E::Tri ta, tb;
             E::load(g, t0 + r, ta);
             E::load(g, s0 + c, tb);
             C2 v[9];
             E::template eval<2>(ta, tb, R, k, 0, v);
-            store_local<CPLX>(out, B.off + 3 * r * ld + 3 * c, ld, v);
+            store_local<CPLX>(out, B.off + 3 * c * ld + 3 * r, 1, ld, v);
         }
     }
 }
@@ -325,7 +326,7 @@ k_singular_dp1(DevGeom g, SingTable tab, double k, const SingPairL *__restrict__
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
                 v[3 * oa[a] + ob[b]] = {acc[3 * a + b].re * sc, acc[3 * a + b].im * sc};
-        store_local<CPLX>(out, pr.dest, pr.ld, v);
+        store_local<CPLX>(out, pr.dest, pr.rs, pr.cs, v);
     }
 }
 

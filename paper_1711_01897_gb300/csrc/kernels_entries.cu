@@ -538,7 +538,8 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
 }
 
 // Near-field regular pairs: one warp per dense block, entries flattened
-// row-major over the lanes; pairs sharing a vertex are left to k_singular.
+// column-major over the lanes (the blocks' storage order); pairs sharing a
+// vertex are left to k_singular.
 constexpr int kNearThreads = 128;
 
 template <int OP, bool CPLX, int PREC>
@@ -553,9 +554,10 @@ k_near_regular(DevGeom g, QuadRule R, double k, const NearBlock *__restrict__ bl
     for (int64_t b = warp; b < nblocks; b += nwarps) {
         const NearBlock B = blocks[b];
         const int m = (int)(B.te - B.tb), nn = (int)(B.se - B.sb);
-        // entry e = r * nn + c of the block, stepped by 32 without division
-        int r = lane / nn, c = lane - r * nn;
-        const int dr = 32 / nn, dc = 32 - dr * nn;
+        // entry e = c * m + r of the column-major block, stepped by 32
+        // without division
+        int c = lane / m, r = lane - c * m;
+        const int dc = 32 / m, dr = 32 - dc * m;
         const int64_t tot = (int64_t)m * nn;
         for (int64_t e = lane; e < tot; e += 32) {
             // pairs that share a vertex get a value here that the singular
@@ -564,11 +566,11 @@ k_near_regular(DevGeom g, QuadRule R, double k, const NearBlock *__restrict__ bl
             E::load(g, B.tb + r, ta);
             E::load(g, B.sb + c, tb);
             store_val<CPLX>(out, B.off + e, E::eval(ta, tb, R, k));
-            r += dr;
             c += dc;
-            if (c >= nn) {
-                c -= nn;
-                ++r;
+            r += dr;
+            if (r >= m) {
+                r -= m;
+                ++c;
             }
         }
     }

@@ -182,10 +182,12 @@ __global__ void k_leaf_rows(const int64_t *__restrict__ leaf_rows, const int64_t
                     for (int l = 0; l < B.rank; ++l)
                         acc = madd(pool[ch[l / KCHUNK] + (int64_t)(l % KCHUNK) * m + rr], t[l], acc);
                 } else {
+                    // column-major: consecutive lanes (rows) read consecutive
+                    // entries of each column
                     const NearBlock &N = near[-1 - id];
-                    const int64_t nc = N.se - N.sb, rr = r - N.tb;
-                    const T *a = near_data + N.off + rr * nc;
-                    for (int64_t c = 0; c < nc; ++c) acc = madd(a[c], xt[N.sb + c], acc);
+                    const int64_t nc = N.se - N.sb, mr = N.te - N.tb, rr = r - N.tb;
+                    const T *a = near_data + N.off + rr;
+                    for (int64_t c = 0; c < nc; ++c) acc = madd(a[c * mr], xt[N.sb + c], acc);
                 }
             }
             yt[r] = acc;
