@@ -275,6 +275,7 @@ typedef struct {
     double time_tree_blocks_ms;   /* block lists and touching pairs (host), and the   */
     double time_tree_lists_ms;    /* upload with the cluster-order geometry (device)  */
     double time_tree_upload_ms;
+    int64_t factor_read_bytes;   /* bytes of U, V a product reads: sum of rank (m + n) */
 } bem_hmat_stats;
 
 /* Copies statistics of the handle into *out. */

@@ -49,7 +49,8 @@ class HmatStats(ctypes.Structure):
                 ("aca_eps", ctypes.c_double), ("prec", ctypes.c_int32),
                 ("space", ctypes.c_int32), ("n_dofs", ctypes.c_int64),
                 ("time_tree_clusters_ms", ctypes.c_double), ("time_tree_blocks_ms", ctypes.c_double),
-                ("time_tree_lists_ms", ctypes.c_double), ("time_tree_upload_ms", ctypes.c_double)]
+                ("time_tree_lists_ms", ctypes.c_double), ("time_tree_upload_ms", ctypes.c_double),
+                ("factor_read_bytes", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):

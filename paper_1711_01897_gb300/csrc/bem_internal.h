@@ -119,6 +119,8 @@ struct AcaStats {
     unsigned long long factor_elems;  // elements of all allocated chunks
     unsigned long long k2mn;          // sum over blocks of rank^2 (m + n): FP64 multiply-adds
                                       // of the residual updates and norm terms
+    unsigned long long rank_mn;       // sum over blocks of rank (m + n): factor elements a
+                                      // product reads
     int rank_min, rank_max;
     int capped, failed;
 };

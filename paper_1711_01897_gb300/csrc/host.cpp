@@ -957,7 +957,7 @@ struct bem_hmat_s {
     std::vector<int64_t> toff;
     std::vector<FarBlock> far_result;     // host copy of the factor descriptors, fetched lazily
     bool far_result_valid = false;
-    int64_t factor_elems = 0, k2mn = 0;
+    int64_t factor_elems = 0, k2mn = 0, rank_mn = 0;
     DBuf d_tiles, d_acastats;
     int64_t pool_elems = 0;
     double t_tree = 0, t_near = 0, t_far = 0, t_near_reg = 0;
@@ -1778,6 +1778,7 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         H->rank_max = ast.rank_max;
         H->factor_elems = (int64_t)ast.factor_elems;
         H->k2mn = (int64_t)ast.k2mn;
+        H->rank_mn = (int64_t)ast.rank_mn;
         H->far_result_valid = false;
         const int64_t nd = H->ndof;
         if (H->d_xt.bytes < nd * esz) {
@@ -1905,6 +1906,7 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         s.time_tree_blocks_ms = H->t_blocks;
         s.time_tree_lists_ms = H->t_lists;
         s.time_tree_upload_ms = H->t_upload;
+        s.factor_read_bytes = H->rank_mn * (int64_t)esz;
         for (int c = 0; c < 3; ++c)
             if (H->dofs == 3) s.singular_pairs[c] = (int64_t)H->singl[c].size();
         *out = s;

@@ -59,7 +59,7 @@ k_rank_tiles(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chu
 {
     __shared__ int64_t wt[32];
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    int64_t sum = 0, ent = 0, fe = 0, k2 = 0;
+    int64_t sum = 0, ent = 0, fe = 0, k2 = 0, kmn = 0;
     int rmin = 0x7fffffff, rmax = 0, capped = 0, failed = 0;
     for (int q = 0; q < kScanPer; ++q) {
         int64_t b = base + q;
@@ -68,6 +68,7 @@ k_rank_tiles(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chu
             sum += F.rank;
             ent += F.entries;
             k2 += (int64_t)F.rank * F.rank * ((F.te - F.tb) + (F.se - F.sb));
+            kmn += (int64_t)F.rank * ((F.te - F.tb) + (F.se - F.sb));
             rmin = min(rmin, F.rank);
             rmax = max(rmax, F.rank);
             capped += F.status == 1;
@@ -83,6 +84,7 @@ k_rank_tiles(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chu
     atomicAdd(&st->rank_sum, (unsigned long long)sum);
     atomicAdd(&st->factor_elems, (unsigned long long)fe);
     atomicAdd(&st->k2mn, (unsigned long long)k2);
+    atomicAdd(&st->rank_mn, (unsigned long long)kmn);
     atomicMin(&st->rank_min, rmin);
     atomicMax(&st->rank_max, rmax);
     if (capped) atomicAdd(&st->capped, capped);

@@ -44,14 +44,103 @@ __device__ __forceinline__ double2 shdown(double2 v, int o)
 __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
-// t_b[l] = sum_j (v_l)_j x~_{sigma_b + j}.  One lane per (block, column)
-// pair: the lane finds its block by binary search in the rank offsets and sums
-// the column sequentially, so every FP64 instruction of the warp is useful and
-// no reductions are needed.  Columns longer than kMatvecLongCol go to
+__device__ __forceinline__ double shxor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double2 shxor(double2 v, int o)
+{
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+// k_far_vtx: lanes per block, and columns of V summed per pass (two chunks)
+constexpr int kVtxGroup = 8;
+constexpr int kVtxCols = 2 * KCHUNK;
+
+// t_b[l] = sum_j (v_l)_j x~_{sigma_b + j}.  A group of kVtxGroup lanes per
+// admissible block with n <= kMatvecLongCol (longer columns go to
+// k_far_vtx_long), the groups striding over the block list.  A chunk stores
+// its KCHUNK columns of V contiguously, so the group's lanes read 64
+// consecutive bytes of each column per step; each pass sums kVtxCols columns
+// (eight loads in flight per lane, x~_j read once for all of them), and the
+// eight partial sums are reduced inside the group by a transposing butterfly:
+// the exchanges over lane bits 2, 1, 0 halve the values a lane holds (4, 2,
+// 1 of them), after which lane g of the group holds the sum of column g.
+template <typename T>
+__global__ void __launch_bounds__(kMvThreads)
+k_far_vtx(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks, int64_t nfar,
+          const int64_t *__restrict__ toff, const T *__restrict__ pool,
+          const T *__restrict__ xt, T *__restrict__ tbuf)
+{
+    const int g = threadIdx.x & (kVtxGroup - 1);
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kVtxGroup;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / kVtxGroup;
+    const bool h4 = g & 4, h2 = g & 2, h1 = g & 1;
+    // every lane of a warp runs the same number of iterations, so that the
+    // shuffles below always see the full warp
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / kVtxGroup;
+    const int64_t iters = nfar > gw ? (nfar - gw + ngrp - 1) / ngrp : 0;
+    for (int64_t k = 0; k < iters; ++k) {
+        const int64_t b = grp + k * ngrp;
+        int rank = 0;
+        int64_t m = 0, n = 0, sb = 0;
+        if (b < nfar) {
+            const FarBlock &B = far[b];
+            rank = B.rank;
+            m = B.te - B.tb;
+            n = B.se - B.sb;
+            sb = B.sb;
+            if (n > kMatvecLongCol) rank = 0;
+        }
+        const int64_t *ch = b < nfar ? chunks[b].c : nullptr;
+        T *t = b < nfar ? tbuf + toff[b] : nullptr;
+        const T *x = xt + sb;
+        // the group's largest rank is its own; passes run while any group of
+        // the warp has columns left
+        int wr = rank;
+#pragma unroll
+        for (int o = 8; o < 32; o <<= 1) wr = max(wr, __shfl_xor_sync(0xffffffffu, wr, o));
+        for (int l0 = 0; l0 < wr; l0 += kVtxCols) {
+            T s[kVtxCols];
+#pragma unroll
+            for (int q = 0; q < kVtxCols; ++q) s[q] = zero_of(T{});
+            if (l0 < rank) {
+                const T *v0 = pool + ch[l0 / KCHUNK] + KCHUNK * m;
+                const T *v1 = l0 + KCHUNK < rank ? pool + ch[l0 / KCHUNK + 1] + KCHUNK * m : v0;
+#pragma unroll 1
+                for (int64_t j = g; j < n; j += kVtxGroup) {
+                    const T xj = x[j];
+#pragma unroll
+                    for (int q = 0; q < KCHUNK; ++q) {
+                        if (l0 + q < rank) s[q] = madd(v0[q * n + j], xj, s[q]);
+                        if (l0 + KCHUNK + q < rank)
+                            s[KCHUNK + q] = madd(v1[q * n + j], xj, s[KCHUNK + q]);
+                    }
+                }
+            }
+            T r4[4], r2[2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const T keep = h4 ? s[4 + i] : s[i], send = h4 ? s[i] : s[4 + i];
+                r4[i] = add(keep, shxor(send, 4));
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const T keep = h2 ? r4[2 + i] : r4[i], send = h2 ? r4[i] : r4[2 + i];
+                r2[i] = add(keep, shxor(send, 2));
+            }
+            const T w = add(h1 ? r2[1] : r2[0], shxor(h1 ? r2[0] : r2[1], 1));
+            if (l0 + g < rank) t[l0 + g] = w;
+        }
+    }
+}
+
+// The same for complex factors, where the product is bound by the FP64 pipe
+// (four multiply-adds per 16 bytes): one lane per (block, column) pair; the
+// lane finds its block by binary search in the rank offsets and sums the
+// column sequentially, so every FP64 instruction of the warp is useful and no
+// reductions are needed.  Columns longer than kMatvecLongCol go to
 // k_far_vtx_long.  A block of rank 0 owns no item (it is skipped by the search).
 
 template <typename T>
-__global__ void k_far_vtx(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks,
+__global__ void k_far_vtx_cols(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks,
                           int64_t nfar,
                           const int64_t *__restrict__ toff, const T *__restrict__ pool,
                           const T *__restrict__ xt, T *__restrict__ tbuf)
@@ -211,7 +300,11 @@ cudaError_t matvec_t(int64_t n, const int32_t *perm, const T *x, T *y, T *xt, T 
         int dev = 0, nsm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        k_far_vtx<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(far, chunks, nfar, toff, pool, xt, tbuf);
+        if constexpr (sizeof(T) == sizeof(double))
+            k_far_vtx<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(far, chunks, nfar, toff, pool, xt, tbuf);
+        else
+            k_far_vtx_cols<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(far, chunks, nfar, toff, pool,
+                                                                          xt, tbuf);
         count_launches(1);
         if (nlong > 0) {
             k_far_vtx_long<T><<<(unsigned)(nsm * 8), kMvThreads, 0, st>>>(

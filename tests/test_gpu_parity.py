@@ -220,11 +220,13 @@ def test_hmatrix_blocks_and_matvec_l3(lib, l3, l3_oracle_dense, prec, op):
     Ap = A[np.ix_(perm, perm)]
     ohm = oracle.hmat_assemble(V, T, op, 0.0, 32, 1.2, eps)
     n_far = 0
+    rank_mn = 0
     for b, (tb, te, sb, se, adm) in enumerate(blocks):
         got, rank = h.block_dense(b, (te - tb, se - sb))
         truth = Ap[tb:te, sb:se]
         if adm:
             n_far += 1
+            rank_mn += rank * ((te - tb) + (se - sb))
             ob = next(i for i, r in enumerate(ohm.blocks) if tuple(r) == (tb, te, sb, se, 1))
             e_or = aca_yardstick(truth, eps, prec, extra=[relf(ohm.block_dense(ob), truth)], seed=b)
             e = relf(got, truth)
@@ -241,6 +243,11 @@ def test_hmatrix_blocks_and_matvec_l3(lib, l3, l3_oracle_dense, prec, op):
         assert relf(y[b], yd[b]) <= 2 * eps
     s = h.stats()
     assert s["assembled"] and s["far_entries"] > 0 and s["rank_capped_blocks"] == 0
+    # a product reads rank (m + n) factor entries per admissible block, at
+    # most the allocated 4-column chunks
+    assert s["factor_read_bytes"] == 8 * rank_mn
+    assert s["factor_read_bytes"] <= s["factor_bytes"] <= s["factor_read_bytes"] + 8 * 4 * sum(
+        (te - tb) + (se - sb) for tb, te, sb, se, adm in blocks if adm)
 
 
 def test_fp64_aca_matches_oracle_aca(lib, l3):
