@@ -26,6 +26,10 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
 SLP, DLP, ADLP = 0, 1, 2
+# regular-rule codes (``regular_order``): the 6-point degree-4 rule, the
+# 3-point degree-2 rule and the centroid rule; points per triangle of each
+RULE6, RULE3, RULE1 = 0, -3, -1
+RULE_POINTS = {RULE6: 6, RULE3: 3, RULE1: 1}
 P0, DP1, P1 = 0, 1, 2
 _lock = threading.Lock()
 _lib = None
@@ -68,7 +72,10 @@ def lib():
             L.orc_cluster_tree.argtypes = [P, P, i64, ctypes.c_int, P, P, P, P, P, P, P]
             L.orc_block_tree.argtypes = [P, P, P, dbl, P, P, P, i64, P]
             L.orc_aca_blocks.argtypes = [P, P, P, ctypes.c_int, i64, P, P, P, P, ctypes.c_int, dbl,
-                                         dbl, P, P, P, P, P, P, P, P, ctypes.c_int]
+                                         dbl, P, P, P, P, P, P, P, P, P, ctypes.c_int]
+            L.orc_block_rules.argtypes = [P, P, P, i64, P, P, P, P, P, P, dbl, dbl, P]
+            L.orc_triangle_rule_deg2.argtypes = [P, P, P]
+            L.orc_triangle_rule_deg1.argtypes = [P, P, P]
             L.orc_entries_dp1.argtypes = [P, P, i64, ctypes.c_int, dbl, P, i64, P, i64,
                                           ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
             L.orc_pair_local.argtypes = [P, P, P, P, ctypes.c_int, dbl, ctypes.c_int, ctypes.c_int,
@@ -103,6 +110,20 @@ def gauss_legendre01(n: int):
 def triangle_rule_deg4():
     s, t, w = np.zeros(6), np.zeros(6), np.zeros(6)
     lib().orc_triangle_rule_deg4(_p(s), _p(t), _p(w))
+    return s, t, w
+
+
+def triangle_rule_deg2():
+    """The 3-point degree-2 rule (s, t, w) of the middle distance class."""
+    s, t, w = (np.zeros(3) for _ in range(3))
+    lib().orc_triangle_rule_deg2(_p(s), _p(t), _p(w))
+    return s, t, w
+
+
+def triangle_rule_deg1():
+    """The centroid rule (s, t, w) of the farthest distance class."""
+    s, t, w = (np.zeros(1) for _ in range(3))
+    lib().orc_triangle_rule_deg1(_p(s), _p(t), _p(w))
     return s, t, w
 
 
@@ -448,6 +469,7 @@ class HMatrix:
     far: dict = field(default_factory=dict)
     ranks: dict = field(default_factory=dict)
     entries_evaluated: int = 0
+    rules: np.ndarray | None = None
 
     def matvec(self, x: np.ndarray) -> np.ndarray:
         """y = P (Near x~ + sum_b U_b (V_b^T x~_sigma)), x~ = x in cluster
@@ -479,9 +501,31 @@ def block_list(ct: ClusterTree, bt: BlockTree) -> np.ndarray:
                      bt.adm.astype(np.int64)], axis=1)
 
 
+def block_rules(V, T, ct: ClusterTree, bt: BlockTree, blocks: np.ndarray, rho3: float,
+                rho1: float) -> np.ndarray:
+    """Regular-rule code of every block (quadrature order per block distance
+    class): admissible blocks by rho = dist(tau, sigma) / h (box distance over
+    the longest triangle edge in tau or sigma) against the thresholds (0 =
+    class unused), near blocks RULE6."""
+    V, T = _mesh_arrays(V, T)
+    n = blocks.shape[0]
+    rules = np.zeros(n, dtype=np.int32)
+    adm = np.flatnonzero(blocks[:, 4])
+    if adm.size and (rho3 > 0 or rho1 > 0):
+        tb, te, sb, se = (np.ascontiguousarray(blocks[adm, c]) for c in range(4))
+        bx_t = np.ascontiguousarray(ct.box[bt.tau[adm]])
+        bx_s = np.ascontiguousarray(ct.box[bt.sigma[adm]])
+        out = np.zeros(adm.size, dtype=np.int32)
+        lib().orc_block_rules(_p(V), _p(T), _p(ct.perm), adm.size, _p(tb), _p(te), _p(sb), _p(se),
+                              _p(bx_t), _p(bx_s), float(rho3), float(rho1), _p(out))
+        rules[adm] = out
+    return rules
+
+
 def hmat_assemble(V, T, op: int, k: float, leaf_size: int, eta: float, eps: float,
                   n_gl: int = 4, kcap_max: int = 256, nthreads: int = 0,
-                  block_ids=None, space: int = P0) -> HMatrix:
+                  block_ids=None, space: int = P0, rho3: float = 0.0,
+                  rho1: float = 0.0) -> HMatrix:
     """Algorithm "H-Matrix Assembly" (Sec. 4.1): generate the block cluster
     tree, evaluate inadmissible blocks densely, approximate admissible blocks
     by ACA.  block_ids restricts the work to a subset of leaf blocks.
@@ -489,12 +533,19 @@ def hmat_assemble(V, T, op: int, k: float, leaf_size: int, eta: float, eps: floa
     space=DP1: the same triangle cluster and block trees, each triangle
     carrying its three local dofs (cluster position t -> dofs 3t, 3t+1,
     3t+2), so every block is the tripled dof block; ``perm`` and ``blocks``
-    are then in dof units."""
+    are then in dof units.
+
+    rho3, rho1 > 0 (P0 only): admissible blocks with dist / h >= rho1 use
+    the centroid rule, else >= rho3 the 3-point rule, else the 6-point rule
+    (``block_rules``); ``rules`` records the code of every block."""
     V, T = _mesh_arrays(V, T)
     ct = cluster_tree(V, T, leaf_size)
     bt = block_tree(ct, eta)
     blocks = block_list(ct, bt)
     perm = ct.perm
+    if space != P0 and (rho3 > 0 or rho1 > 0):
+        raise ValueError("per-class regular rules are defined for P0 only")
+    rules = block_rules(V, T, ct, bt, blocks, rho3, rho1)
     if space == DP1:
         dof_perm = (3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1).astype(np.int32)
         dblocks = blocks.copy()
@@ -502,6 +553,7 @@ def hmat_assemble(V, T, op: int, k: float, leaf_size: int, eta: float, eps: floa
         hm = HMatrix(n=3 * T.shape[0], perm=dof_perm, blocks=dblocks)
     else:
         hm = HMatrix(n=T.shape[0], perm=perm, blocks=blocks)
+    hm.rules = rules
     sel = np.arange(blocks.shape[0]) if block_ids is None else np.asarray(block_ids)
     far_ids = [b for b in sel if blocks[b, 4]]
     near_ids = [b for b in sel if not blocks[b, 4]]
@@ -528,8 +580,9 @@ def hmat_assemble(V, T, op: int, k: float, leaf_size: int, eta: float, eps: floa
         rank = np.zeros(ids.size, dtype=np.int32)
         status = np.zeros(ids.size, dtype=np.int32)
         ev = np.zeros(ids.size, dtype=np.int64)
+        rl = np.ascontiguousarray(rules[ids])
         lib().orc_aca_blocks(_p(V), _p(T), _p(perm), int(space), ids.size, _p(tb), _p(te), _p(sb), _p(se), op,
-                             float(k), float(eps), _p(kc), _p(uoff), _p(voff), _p(U), _p(Vf),
+                             float(k), float(eps), _p(kc), _p(rl), _p(uoff), _p(voff), _p(U), _p(Vf),
                              _p(rank), _p(status), _p(ev), nthreads)
         if np.any(status == 3):
             raise MemoryError("oracle ACA allocation failed")

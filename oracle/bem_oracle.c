@@ -152,6 +152,33 @@ int orc_triangle_rule_deg4(double *s, double *t, double *w)
     return 0;
 }
 
+/* Symmetric 3-point rule of degree 2 for the well-separated distance class
+ * of admissible blocks (the lower of the per-class orders; the paper's own
+ * rule is the 6-point one above).  One orbit (q,q,1-2q) with weights 1/3;
+ * the moment of e2 (1/4) gives 3 q^2 - 2 q + 1/4 = 0, whose smaller root
+ * q = 1/6 puts the points inside the triangle (the other, q = 1/2, at the
+ * edge midpoints).  Output as for orc_triangle_rule_deg4. */
+int orc_triangle_rule_deg2(double *s, double *t, double *w)
+{
+    const double a = 3.0, b = -2.0, c = 0.25;
+    const double q = (-b - sqrt(b * b - 4.0 * a * c)) / (2.0 * a), r = 1.0 - 2.0 * q;
+    const double L[3][3] = {{q, q, r}, {q, r, q}, {r, q, q}};
+    for (int m = 0; m < 3; ++m) {
+        s[m] = L[m][1];
+        t[m] = L[m][2];
+        w[m] = 1.0 / 3.0;
+    }
+    return 0;
+}
+
+/* Centroid rule (one point, degree 1) for the farthest distance class. */
+int orc_triangle_rule_deg1(double *s, double *t, double *w)
+{
+    s[0] = t[0] = 1.0 / 3.0;
+    w[0] = 1.0;
+    return 0;
+}
+
 /* Conical (collapsed) product rule with n*n points: s = u, t = v (1-u),
  * Jacobian (1-u), Gauss-Legendre in u and v.  Weights normalised to sum 1.
  * Exact for total degree <= 2n-2.  Used only by the pins' reference
@@ -432,9 +459,18 @@ static cplx entry_singular(const otri *Ti, const otri *Tj, const int32_t *ta, co
     return 4.0 * Ti->area * Tj->area * sum;
 }
 
+/* Regular rule by code: 0 (or any other value <= 0) the 6-point degree-4
+ * rule, -3 the 3-point degree-2 rule, -1 the centroid rule, n > 0 the
+ * conical n x n rule. */
 static void rule_init(orule *R, int regular_order)
 {
-    if (regular_order <= 0) {
+    if (regular_order == -3) {
+        R->np = 3;
+        orc_triangle_rule_deg2(R->s, R->t, R->w);
+    } else if (regular_order == -1) {
+        R->np = 1;
+        orc_triangle_rule_deg1(R->s, R->t, R->w);
+    } else if (regular_order <= 0) {
         R->np = 6;
         orc_triangle_rule_deg4(R->s, R->t, R->w);
     } else {
@@ -1017,6 +1053,54 @@ static cplx block_entry(const double *V, const int32_t *Tr, const int32_t *perm,
                      k, 4, R);
 }
 
+/* Regular-rule class of an admissible block (quadrature order per block
+ * distance class): rho = dist(tau, sigma) / h, with dist the distance between
+ * the cluster boxes (as in the admissibility test) and h the longest edge of
+ * any triangle of tau or sigma.  rho >= rho1 > 0 selects the centroid rule
+ * (code -1), else rho >= rho3 > 0 the 3-point rule (code -3), else the
+ * 6-point rule (code 0).  Boxes: 6 doubles (lo xyz, hi xyz) per block and
+ * side; ranges in cluster order through perm. */
+static double longest_edge(const double *V, const int32_t *Tr, const int32_t *perm, int64_t b,
+                           int64_t e)
+{
+    double h2 = 0.0;
+    for (int64_t p = b; p < e; ++p) {
+        const int32_t *tr = Tr + 3 * (int64_t)perm[p];
+        for (int a = 0; a < 3; ++a) {
+            const double *u = V + 3 * (int64_t)tr[a], *v = V + 3 * (int64_t)tr[(a + 1) % 3];
+            double l2 = 0.0;
+            for (int c = 0; c < 3; ++c) l2 += (u[c] - v[c]) * (u[c] - v[c]);
+            if (l2 > h2) h2 = l2;
+        }
+    }
+    return sqrt(h2);
+}
+
+int orc_block_rules(const double *V, const int32_t *Tr, const int32_t *perm, int64_t nblk,
+                    const int64_t *tb, const int64_t *te, const int64_t *sb, const int64_t *se,
+                    const double *box_t, const double *box_s, double rho3, double rho1,
+                    int32_t *rules)
+{
+    for (int64_t b = 0; b < nblk; ++b) {
+        const double *bt = box_t + 6 * b, *bs = box_s + 6 * b;
+        double g2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double g1 = bs[c] - bt[3 + c], gb = bt[c] - bs[3 + c];
+            double m = g1 > gb ? g1 : gb;
+            if (m > 0) g2 += m * m;
+        }
+        const double dist = sqrt(g2);
+        const double ht = longest_edge(V, Tr, perm, tb[b], te[b]);
+        const double hs = longest_edge(V, Tr, perm, sb[b], se[b]);
+        const double h = ht > hs ? ht : hs;
+        int r = 0;
+        if (rho1 > 0 && dist >= rho1 * h) r = -1;
+        else if (rho3 > 0 && dist >= rho3 * h) r = -3;
+        rules[b] = r;
+    }
+    return 0;
+}
+
 /* Readings where the paper defers or is silent:
  *  row pivot:  i_1 = 0; afterwards i_{k+1} = argmax_{i not in Z} |(u_k)_i|,
  *              lowest index on ties;
@@ -1032,7 +1116,7 @@ static cplx block_entry(const double *V, const int32_t *Tr, const int32_t *perm,
  * Returns 0, or 4 if kcap was reached before the criterion held. */
 int orc_aca_block(const double *V, const int32_t *Tr, const int32_t *perm, int space, int64_t tb,
                   int64_t te, int64_t sb, int64_t se, int op, double k, double eps, int kcap,
-                  cplx *U, cplx *Vf, int *rank, int64_t *entries_evaluated)
+                  int regular_order, cplx *U, cplx *Vf, int *rank, int64_t *entries_evaluated)
 {
     int64_t m = te - tb, n = se - sb;
     orule *R = (orule *)malloc(sizeof(orule));
@@ -1040,7 +1124,7 @@ int orc_aca_block(const double *V, const int32_t *Tr, const int32_t *perm, int s
     cplx *col = (cplx *)malloc(sizeof(cplx) * m);
     char *inZ = (char *)calloc((size_t)m, 1);
     if (!R || !row || !col || !inZ) { free(R); free(row); free(col); free(inZ); return 3; }
-    rule_init(R, 0);
+    rule_init(R, regular_order);
     int kk = 0, status = 0;
     int64_t nZ = 0, i = 0, evals = 0;
     double normS2 = 0, maxpiv = 0;
@@ -1109,9 +1193,9 @@ int orc_aca_block(const double *V, const int32_t *Tr, const int32_t *perm, int s
  * V + voff[b] with capacity kcap[b] columns.  Parallel over blocks. */
 int orc_aca_blocks(const double *V, const int32_t *Tr, const int32_t *perm, int space, int64_t nblk,
                    const int64_t *tb, const int64_t *te, const int64_t *sb, const int64_t *se,
-                   int op, double k, double eps, const int32_t *kcap, const int64_t *uoff,
-                   const int64_t *voff, cplx *U, cplx *Vf, int32_t *rank, int32_t *status,
-                   int64_t *entries, int nthreads)
+                   int op, double k, double eps, const int32_t *kcap, const int32_t *rules,
+                   const int64_t *uoff, const int64_t *voff, cplx *U, cplx *Vf, int32_t *rank,
+                   int32_t *status, int64_t *entries, int nthreads)
 {
 #ifdef _OPENMP
     /* a per-call thread count that leaves the process default untouched */
@@ -1122,7 +1206,7 @@ int orc_aca_blocks(const double *V, const int32_t *Tr, const int32_t *perm, int 
         int r = 0;
         int64_t ev = 0;
         status[b] = orc_aca_block(V, Tr, perm, space, tb[b], te[b], sb[b], se[b], op, k, eps, kcap[b],
-                                  U + uoff[b], Vf + voff[b], &r, &ev);
+                                  rules ? rules[b] : 0, U + uoff[b], Vf + voff[b], &r, &ev);
         rank[b] = r;
         entries[b] = ev;
     }
