@@ -51,7 +51,7 @@ FP64_TFLOPS_NOMINAL = 1.25
 # workload (icosphere level 6, SLP and DLP, mixed), from an ncu capture of this
 # build (dram__bytes_read.sum + dram__bytes_write.sum); re-capture when k_aca
 # changes.
-ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.717166080 + 1.938804992 + 10.725359872 + 2.943645184) * 1e9
+ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.707635968 + 1.940037376 + 10.711072512 + 2.945069056) * 1e9
 
 
 def rank_jitter_seed(rank: int) -> int:
@@ -460,6 +460,11 @@ def run_gpu(args):
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.median(e2e_ms)),
                         "parts_ms": e2e_parts},
                 "gpu_launches": int(launches), "step_ms": step_ms}
+        if args.rho3 > 0 or args.rho1 > 0:
+            line["quadrature_classes"] = {
+                "rho3": args.rho3, "rho1": args.rho1,
+                "blocks": {"rule3": st_slp["n_blocks_rule3"], "rule1": st_slp["n_blocks_rule1"],
+                           "all_far": st_slp["n_blocks_far"]}}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -652,6 +657,11 @@ def run_large(args, spec):
             "matvec_gbs": (st["near_bytes"] + st["factor_read_bytes"]) / (np.median(mv_ms) * 1e-3) / 1e9,
             "sampled_rows_rel_err": err, "tolerance": 2 * spec["eps"],
             "oracle_rows_s": t_or, "cpu_baseline": cpu, "clocks": clocks}
+    if args.rho3 > 0 or args.rho1 > 0:
+        line["quadrature_classes"] = {"rho3": args.rho3, "rho1": args.rho1,
+                                      "blocks": {"rule3": st["n_blocks_rule3"],
+                                                 "rule1": st["n_blocks_rule1"],
+                                                 "all_far": st["n_blocks_far"]}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -859,7 +869,16 @@ def main():
     ap.add_argument("--calib", type=int, default=24)
     ap.add_argument("--level", type=int, default=6,
                     help="icosphere level of the mesh (6 = the workload; smaller for profiling)")
+    ap.add_argument("--rho3", type=float, default=0.0,
+                    help="distance class of the 3-point regular rule (dist/h; 0 = the paper's "
+                         "6-point rule for every block)")
+    ap.add_argument("--rho1", type=float, default=0.0,
+                    help="distance class of the centroid rule (dist/h; 0 = off)")
     args = ap.parse_args()
+    if args.rho3 > 0 or args.rho1 > 0:
+        from paper_1711_01897_gb300 import bem
+        bem.bem_set_quadrature(args.rho3, args.rho1)
+        WORKLOAD["quadrature_classes"] = {"rho3": args.rho3, "rho1": args.rho1}
     if args.warmup < 3 and args.workload == "c2":
         args.warmup = 3
     if args.level != 6:

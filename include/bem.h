@@ -99,6 +99,31 @@ typedef struct {
 int bem_set_tuning(const bem_tuning *t);
 int bem_get_tuning(bem_tuning *t);
 
+/* Regular quadrature order per distance class of the admissible blocks
+ * (process-wide, read when a P0 tree is built).  The paper evaluates every
+ * regular pair with one symmetric 6-point rule of degree 4 (Sec. 3.2.1); a
+ * block far enough apart relative to its triangles may use a lower-order
+ * rule of the same family.  With rho = dist(tau, sigma) / h -- the distance
+ * between the two cluster boxes over the longest triangle edge in either
+ * cluster --
+ *   rho >= rho1 > 0            the centroid rule (1 point, degree 1),
+ *   else rho >= rho3 > 0       the 3-point rule of degree 2 (barycentric
+ *                              (2/3, 1/6, 1/6) and permutations),
+ *   else                       the 6-point rule.
+ * 0 switches a class off (the default: every block uses the 6-point rule).
+ * The classes apply to the mixed-precision assembly of the Laplace
+ * operators (k = 0) on P0 handles.  The Helmholtz entries (whose lower-order
+ * error is set by k h, not by the distance), the FP64 assembly (the plain
+ * form), the near field and the piecewise linear spaces keep the 6-point
+ * rule.  BEM_E_ARG for negative or non-finite thresholds. */
+typedef struct {
+    double rho3;
+    double rho1;
+} bem_quadrature;
+
+int bem_set_quadrature(const bem_quadrature *q);
+int bem_get_quadrature(bem_quadrature *q);
+
 /* Text of the calling thread's last error ("" if none).  The pointer stays
  * valid until the next library call on this thread. */
 const char *bem_last_error(void);
@@ -276,6 +301,10 @@ typedef struct {
     double time_tree_lists_ms;    /* upload with the cluster-order geometry (device)  */
     double time_tree_upload_ms;
     int64_t factor_read_bytes;   /* bytes of U, V a product reads: sum of rank (m + n) */
+    int64_t n_blocks_rule3;      /* admissible blocks of the 3-point and centroid classes */
+    int64_t n_blocks_rule1;
+    double rho3;                 /* the thresholds the tree was built with */
+    double rho1;
 } bem_hmat_stats;
 
 /* Copies statistics of the handle into *out. */
@@ -294,6 +323,11 @@ int hmat_blocks(bem_hmat hmat, int64_t *blocks, int64_t cap, int64_t *n_blocks, 
  * U V^T for an admissible block; *rank receives its ACA rank (-1 for a
  * dense block).  DP1 and P1 handles: DP1 dofs, as in hmat_blocks. */
 int hmat_block_dense(bem_hmat hmat, int64_t block, void *out, int32_t *rank);
+
+/* Points per triangle of the regular rule of every block (tree order, as in
+ * hmat_blocks): 6, 3 or 1 for admissible blocks (bem_set_quadrature), 0 for
+ * near-field blocks.  points: host, capacity cap >= number of blocks. */
+int hmat_block_rules(bem_hmat hmat, int32_t *points, int64_t cap);
 
 /* Frees the handle and its device memory. */
 int hmat_destroy(bem_hmat hmat);

@@ -1,4 +1,5 @@
-"""Autotuner for the assembly launch configuration.
+"""Autotuner for the assembly launch configuration and for the regular
+quadrature order per distance class of the admissible blocks.
 
 For a representative mesh it times hmat_assemble (device time of the near
 field plus the persistent ACA, from the library's own events) under each
@@ -9,7 +10,17 @@ baseline candidate's to 2 * aca_eps (the thresholds change no arithmetic, but
 ACA pivot near-ties may resolve differently).  The fastest admissible
 candidate is written to a JSON tuning table that `apply()` loads.
 
-    python -m paper_1711_01897_gb300.autotune [--level 5] [--out tuning.json]
+With --quadrature it also searches the distance classes (bem_set_quadrature):
+blocks with dist / h >= rho1 use the centroid rule, >= rho3 the 3-point
+degree-2 rule, the rest the paper's 6-point rule.  A candidate is admissible
+only if its H-matrix product stays within `accuracy` * aca_eps (default 0.5)
+of the product with the 6-point rule everywhere, so the product's error bound
+of 2 aca_eps against the dense matrix keeps its margin.  The fastest
+admissible candidate goes to a separate table (quadrature.json) that
+`apply_quadrature()` loads on request: the library's default stays the
+paper's rule.
+
+    python -m paper_1711_01897_gb300.autotune [--level 5] [--out tuning.json] [--quadrature]
 """
 from __future__ import annotations
 
@@ -21,9 +32,12 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_TABLE = os.path.join(HERE, "tuning.json")
+DEFAULT_QUAD_TABLE = os.path.join(HERE, "quadrature.json")
 
 WARP_CANDIDATES = (160, 320, 640, 1280, 2560, 8192)
 LANE_CANDIDATES = (0, 24, 48)
+RHO3_CANDIDATES = (0.0, 4.0, 6.0, 8.0, 12.0)
+RHO1_CANDIDATES = (0.0, 16.0, 24.0, 32.0, 48.0)
 
 
 def choose(results, eps):
@@ -71,6 +85,74 @@ def measure(V, T, ops=(0, 1), eps=1e-5, prec=1, reps=2, warp=WARP_CANDIDATES,
     return results
 
 
+def choose_quadrature(results, eps, accuracy=0.5):
+    """results: dicts with keys rho3, rho1, time_ms, rel_diff (product
+    against the 6-point product).  Returns the fastest admissible entry; the
+    6-point candidate (0, 0) is always admissible."""
+    ok = [r for r in results if r["rel_diff"] <= accuracy * eps]
+    if not ok:
+        raise RuntimeError("no candidate meets the accuracy constraint")
+    return min(ok, key=lambda r: (r["time_ms"], -r["rho3"] if r["rho3"] else 0.0,
+                                  -r["rho1"] if r["rho1"] else 0.0))
+
+
+def quadrature_candidates(rho3=RHO3_CANDIDATES, rho1=RHO1_CANDIDATES):
+    """(rho3, rho1) pairs with the centroid class beyond the 3-point class."""
+    return [(a, b) for a in rho3 for b in rho1 if b == 0.0 or a == 0.0 or b > a]
+
+
+def measure_quadrature(V, T, ops=(0, 1), eps=1e-5, reps=2, candidates=None, leaf=32, eta=1.2):
+    """Times the mixed Laplace assemblies (near field + ACA, from the
+    library's events) of trees built under each pair of class thresholds, and
+    the relative difference of their products from the 6-point products."""
+    from . import bem
+    cands = quadrature_candidates() if candidates is None else list(candidates)
+    if (0.0, 0.0) not in cands:
+        cands = [(0.0, 0.0)] + cands
+    cands.sort(key=lambda c: (c != (0.0, 0.0), c))
+    mesh = bem.Mesh(V, T)
+    x = np.random.default_rng(1).normal(size=T.shape[0])
+    base = {}
+    results = []
+    saved = bem.bem_get_quadrature()
+    try:
+        for r3, r1 in cands:
+            bem.bem_set_quadrature(r3, r1)
+            total, diffs, n3, n1 = 0.0, [], 0, 0
+            for op in ops:
+                h = bem.HMatrix(mesh, leaf, eta)
+                times = []
+                for _ in range(reps):
+                    h.assemble(op, 0.0, eps, bem.MIXED)
+                    st = h.stats()
+                    times.append(st["time_near_ms"] + st["time_far_ms"])
+                n3, n1 = st["n_blocks_rule3"], st["n_blocks_rule1"]
+                y = h.matvec(x)
+                h.close()
+                if op not in base:
+                    base[op] = y
+                diffs.append(float(np.linalg.norm(y - base[op]) / np.linalg.norm(base[op])))
+                total += min(times)
+            results.append({"rho3": r3, "rho1": r1, "time_ms": total, "rel_diff": max(diffs),
+                            "blocks_rule3": int(n3), "blocks_rule1": int(n1)})
+    finally:
+        bem.bem_set_quadrature(saved["rho3"], saved["rho1"])
+        mesh.close()
+    return results
+
+
+def apply_quadrature(path: str = DEFAULT_QUAD_TABLE) -> bool:
+    """Loads the distance classes of a quadrature table (if it exists); the
+    trees built afterwards use them."""
+    if not os.path.exists(path):
+        return False
+    from . import bem
+    with open(path) as f:
+        t = json.load(f)
+    bem.bem_set_quadrature(float(t["rho3"]), float(t["rho1"]))
+    return True
+
+
 def apply(path: str = DEFAULT_TABLE) -> bool:
     """Loads a tuning table (if it exists) into the library."""
     if not os.path.exists(path):
@@ -87,6 +169,9 @@ def main():
     ap.add_argument("--level", type=int, default=5)
     ap.add_argument("--eps", type=float, default=1e-5)
     ap.add_argument("--out", default=DEFAULT_TABLE)
+    ap.add_argument("--quadrature", action="store_true",
+                    help="also search the distance classes of the regular rule")
+    ap.add_argument("--quad-out", default=DEFAULT_QUAD_TABLE)
     args = ap.parse_args()
     import torch
     from . import meshes
@@ -102,6 +187,18 @@ def main():
     with open(args.out, "w") as f:
         json.dump(table, f, indent=1)
     print(json.dumps({k: table[k] for k in ("warp_max_rows", "lane_max_rows", "time_ms")}))
+    if args.quadrature:
+        apply(args.out)
+        qres = measure_quadrature(V, T, eps=args.eps)
+        qbest = choose_quadrature(qres, args.eps)
+        qtable = {"rho3": qbest["rho3"], "rho1": qbest["rho1"], "time_ms": qbest["time_ms"],
+                  "rel_diff": qbest["rel_diff"],
+                  "workload": f"Laplace SLP+DLP, jittered icosphere level {args.level}, "
+                              f"eps {args.eps}, mixed",
+                  "candidates": qres}
+        with open(args.quad_out, "w") as f:
+            json.dump(qtable, f, indent=1)
+        print(json.dumps({k: qtable[k] for k in ("rho3", "rho1", "time_ms", "rel_diff")}))
 
 
 if __name__ == "__main__":

@@ -50,12 +50,18 @@ class HmatStats(ctypes.Structure):
                 ("space", ctypes.c_int32), ("n_dofs", ctypes.c_int64),
                 ("time_tree_clusters_ms", ctypes.c_double), ("time_tree_blocks_ms", ctypes.c_double),
                 ("time_tree_lists_ms", ctypes.c_double), ("time_tree_upload_ms", ctypes.c_double),
-                ("factor_read_bytes", ctypes.c_int64)]
+                ("factor_read_bytes", ctypes.c_int64),
+                ("n_blocks_rule3", ctypes.c_int64), ("n_blocks_rule1", ctypes.c_int64),
+                ("rho3", ctypes.c_double), ("rho1", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("warp_max_rows", ctypes.c_int32), ("lane_max_rows", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32)]
+
+
+class Quadrature(ctypes.Structure):
+    _fields_ = [("rho3", ctypes.c_double), ("rho1", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -106,6 +112,8 @@ def load(path: str = LIB_PATH):
             "bem_kernel_launches": ([], ctypes.c_int64),
             "bem_set_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
             "bem_get_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
+            "bem_set_quadrature": ([ctypes.POINTER(Quadrature)], ctypes.c_int),
+            "bem_get_quadrature": ([ctypes.POINTER(Quadrature)], ctypes.c_int),
             "bem_last_error": ([], ctypes.c_char_p),
             "bem_mesh_create": ([P, i64, P, i64, P], ctypes.c_int),
             "bem_mesh_destroy": ([P], ctypes.c_int),
@@ -120,6 +128,7 @@ def load(path: str = LIB_PATH):
             "hmat_stats": ([P, ctypes.POINTER(HmatStats)], ctypes.c_int),
             "hmat_blocks": ([P, P, i64, P, P], ctypes.c_int),
             "hmat_block_dense": ([P, i64, P, P], ctypes.c_int),
+            "hmat_block_rules": ([P, P, i64], ctypes.c_int),
             "hmat_destroy": ([P], ctypes.c_int),
             "bem_server_create": ([i64, i32, i32, P], ctypes.c_int),
             "bem_server_submit": ([P, ctypes.POINTER(Request), P], ctypes.c_int),
@@ -195,6 +204,20 @@ def bem_get_tuning() -> dict:
     _check(load().bem_get_tuning(ctypes.byref(t)))
     return {"warp_max_rows": t.warp_max_rows, "lane_max_rows": t.lane_max_rows,
             "use_graphs": t.use_graphs}
+
+
+def bem_set_quadrature(rho3: float, rho1: float):
+    """Distance classes of the regular rule for trees built from now on:
+    admissible blocks with dist / h >= rho1 use the centroid rule, else >= rho3
+    the 3-point degree-2 rule, else the 6-point rule (0 = class off)."""
+    q = Quadrature(float(rho3), float(rho1))
+    _check(load().bem_set_quadrature(ctypes.byref(q)))
+
+
+def bem_get_quadrature() -> dict:
+    q = Quadrature()
+    _check(load().bem_get_quadrature(ctypes.byref(q)))
+    return {"rho3": q.rho3, "rho1": q.rho1}
 
 
 def bem_last_error() -> str:
@@ -296,6 +319,16 @@ def hmat_block_dense(hmat, block: int, shape, cplx: bool):
     return out, int(r.value)
 
 
+def hmat_block_rules(hmat) -> np.ndarray:
+    """Points per triangle of every block's regular rule (6, 3, 1; 0 near)."""
+    L = load()
+    n = ctypes.c_int64()
+    _check(L.hmat_blocks(hmat, None, 0, ctypes.byref(n), None))
+    out = np.zeros(n.value, dtype=np.int32)
+    _check(L.hmat_block_rules(hmat, out.ctypes.data, n.value))
+    return out
+
+
 def hmat_destroy(hmat):
     _check(load().hmat_destroy(hmat))
 
@@ -361,6 +394,9 @@ class HMatrix:
 
     def block_dense(self, b, shape):
         return hmat_block_dense(self.handle, b, shape, self.cplx)
+
+    def block_rules(self):
+        return hmat_block_rules(self.handle)
 
     def close(self):
         if self.handle is not None:

@@ -268,7 +268,18 @@ struct GroupSmem {
 // triangle (DP1); block ranges are dof ranges, dof 3 t + a of the cluster
 // order is local basis function a of triangle t, and one element pair gives a
 // requested row's (or column's) three entries of that triangle pair.
-template <class Grp, int OP, bool CPLX, int PREC, int DOF = 1>
+// One regular entry of a P0 block: with RULES the block's distance-class rule
+// (a separate instantiation, so that trees without lower-order classes run
+// the plain 6-point code), else the 6-point rule.
+template <bool RULES, class E>
+__device__ __forceinline__ C2 eval_entry(const typename E::Tri &a, const typename E::Tri &b,
+                                         const QuadRule &R, double k, int rule)
+{
+    if constexpr (RULES) return E::eval_rule(a, b, R, k, rule);
+    else return E::eval(a, b, R, k);
+}
+
+template <class Grp, int OP, bool CPLX, int PREC, int DOF = 1, bool RULES = false>
 __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, double k, double eps,
                           FarBlock *blk, FarChunks *chk, typename VT<CPLX>::T *pool, Pool *P,
                           GroupSmem<CPLX> &S, unsigned *Z, typename VT<CPLX>::T *part)
@@ -278,6 +289,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
     using E = RegularEntry<OP, CPLX, PREC>;
     const int64_t tb = blk->tb, sb = blk->sb;
     const int64_t m = blk->te - tb, n = blk->se - sb;
+    const int rule = blk->rule;  // the block's distance class (P0 Laplace entries)
     const int t = G.rank(), GS = G.size();
     const int64_t kmin = m < n ? m : n;
     const int kcap = (int)(kmin < KMAX ? kmin : KMAX);
@@ -355,7 +367,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             for (int64_t j = t; j < n; j += GS) {
                 typename E::Tri tj;
                 E::load(g, sb + j, tj);
-                T a = V::from(E::eval(ti, tj, R, k));
+                T a = V::from((eval_entry<RULES, E>(ti, tj, R, k, rule)));
                 for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Vat(l, j), a);
                 if (kk < kcap) *Vat(kk, j) = a;
                 long long ky = V::key(a);
@@ -435,7 +447,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             for (int64_t r = t; r < m; r += GS) {
                 typename E::Tri tr;
                 E::load(g, tb + r, tr);
-                T a = V::from(E::eval(tr, tj, R, k));
+                T a = V::from((eval_entry<RULES, E>(tr, tj, R, k, rule)));
                 for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Uat(l, r), a);
                 *Uat(kk, r) = a;
                 if (!((Z[r >> 5] >> (r & 31)) & 1u)) {
@@ -554,7 +566,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
 // arithmetic serves 32 blocks, and no reductions are needed.
 constexpr int kTinyMax = 64;
 
-template <int OP, bool CPLX, int PREC>
+template <int OP, bool CPLX, int PREC, bool RULES = false>
 __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double eps,
                          FarBlock *blk, FarChunks *chk, typename VT<CPLX>::T *pool, Pool *P)
 {
@@ -563,6 +575,7 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
     using E = RegularEntry<OP, CPLX, PREC>;
     const int64_t tb = blk->tb, sb = blk->sb;
     const int m = (int)(blk->te - tb), n = (int)(blk->se - sb);
+    const int rule = blk->rule;
     const int kmin = m < n ? m : n;
     const int kcap = kmin < KMAX ? kmin : KMAX;
     int64_t chunk[NCHUNK];
@@ -598,7 +611,7 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
         for (int j = 0; j < n; ++j) {
             typename E::Tri tj;
             E::load_scattered(g, sb + j, tj);
-            T a = V::from(E::eval(ti, tj, R, k));
+            T a = V::from((eval_entry<RULES, E>(ti, tj, R, k, rule)));
             for (int l = 0; l < kk; ++l) a = V::fnma(*Uat(l, i), *Vat(l, j), a);
             if (kk < kcap) *Vat(kk, j) = a;
             long long ky = V::key(a);
@@ -631,7 +644,7 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
         for (int r = 0; r < m; ++r) {
             typename E::Tri tr;
             E::load_scattered(g, tb + r, tr);
-            T a = V::from(E::eval(tr, tj, R, k));
+            T a = V::from((eval_entry<RULES, E>(tr, tj, R, k, rule)));
             for (int l = 0; l < kk; ++l) a = V::fnma(*Vat(l, bj), *Uat(l, r), a);
             *Uat(kk, r) = a;
             if (!((Z >> r) & 1ull)) {
@@ -672,7 +685,7 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
     for (int c = 0; c < NCHUNK; ++c) chk->c[c] = chunk[c];
 }
 
-template <int OP, bool CPLX, int PREC, int DOF>
+template <int OP, bool CPLX, int PREC, int DOF, bool RULES = false>
 __global__ void __launch_bounds__(kAcaThreads, 2)
 k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, FarChunks *chunks,
       int64_t n_big,
@@ -695,8 +708,8 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, FarChunks *
         int64_t b = s_b;
         __syncthreads();
         if (b >= n_big) break;
-        aca_block<CtaGroup, OP, CPLX, PREC, DOF>(cg, g, R, k, eps, blocks + b, chunks + b, pool, P,
-                                                 gs[0], zbig, part);
+        aca_block<CtaGroup, OP, CPLX, PREC, DOF, RULES>(cg, g, R, k, eps, blocks + b, chunks + b,
+                                                        pool, P, gs[0], zbig, part);
     }
     // phase 2: small blocks, one warp each
     const int w = threadIdx.x >> 5;
@@ -706,7 +719,7 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, FarChunks *
         if (wg.lane == 0) b = (int64_t)atomicAdd(&Q->next_small, 1u);
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= n_small) break;
-        aca_block<WarpGroup, OP, CPLX, PREC, DOF>(wg, g, R, k, eps, blocks + n_big + b,
+        aca_block<WarpGroup, OP, CPLX, PREC, DOF, RULES>(wg, g, R, k, eps, blocks + n_big + b,
                                                   chunks + n_big + b, pool, P, gs[w],
                                                   zbig + (int64_t)w * zwords_small, part + 64 * w);
     }
@@ -721,13 +734,14 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, FarChunks *
             b0 = __shfl_sync(0xffffffffu, b0, 0);
             if (b0 >= n_tiny) break;
             const int64_t b = b0 + wg.lane;
-            if (b < n_tiny) aca_lane<OP, CPLX, PREC>(g, R, k, eps, tiny + b, tiny_chk + b, pool, P);
+            if (b < n_tiny)
+                aca_lane<OP, CPLX, PREC, RULES>(g, R, k, eps, tiny + b, tiny_chk + b, pool, P);
             __syncwarp();
         }
     }
 }
 
-template <int OP, bool CPLX, int PREC, int DOF>
+template <int OP, bool CPLX, int PREC, int DOF, bool RULES = false>
 cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps,
                        FarBlock *blocks, FarChunks *chunks, int64_t n_big, int64_t n_small,
                        int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool,
@@ -737,7 +751,7 @@ cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps
     const int64_t zw_big = (max_m_big + 31) / 32, zw_small = (max_m_small + 31) / 32;
     int64_t words = zw_big > kWarps * zw_small ? zw_big : kWarps * zw_small;
     size_t dyn = (size_t)(words > 0 ? words : 1) * sizeof(unsigned);
-    auto kern = k_aca<OP, CPLX, PREC, DOF>;
+    auto kern = k_aca<OP, CPLX, PREC, DOF, RULES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dyn);
     if (e != cudaSuccess) return e;

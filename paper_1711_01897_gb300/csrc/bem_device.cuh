@@ -217,6 +217,58 @@ __device__ __forceinline__ double entry_mixed_laplace(const TriF &a, const TriF 
     return f2d_exact(r.hi) + f2d_exact(r.lo);
 }
 
+// ---- lower-order rules of the distance classes (Laplace) -----------------
+// Admissible blocks far enough apart for their class use NP = 3, the
+// symmetric degree-2 rule at barycentric (2/3, 1/6, 1/6) and permutations
+// (weights 1/3), or NP = 1, the centroid rule.  The degree-2 points are the
+// stored offsets of the degree-4 rule's second orbit scaled by beta3
+// (QuadRule), so the tiles need no new fields.
+template <int NP>
+__device__ __forceinline__ void low_points(const TriF &a, float beta, float q[NP][3])
+{
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[p][c] = NP == 1 ? 0.f : beta * a.q[3 + p][c];
+}
+
+template <int OP, int NP>
+__device__ __forceinline__ double entry_mixed_laplace_low(const TriF &a, const TriF &b, float beta)
+{
+    float aq[NP][3], bq[NP][3];
+    low_points<NP>(a, beta, aq);
+    low_points<NP>(b, beta, bq);
+    const float w = 1.f / (float)NP;
+    float D[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) D[c] = (a.ch[c] - b.ch[c]) + (a.cl[c] - b.cl[c]);
+    float cq[NP];
+    if (OP == 2) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            cq[q] = -w * ((D[0] - bq[q][0]) * a.n[0] + (D[1] - bq[q][1]) * a.n[1] +
+                          (D[2] - bq[q][2]) * a.n[2]);
+    }
+    FF acc = {0.f, 0.f};
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float Dp0 = D[0] + aq[p][0], Dp1 = D[1] + aq[p][1], Dp2 = D[2] + aq[p][2];
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float d0 = Dp0 - bq[q][0], d1 = Dp1 - bq[q][1], d2 = Dp2 - bq[q][2];
+            float ri = rsqrt_ftz(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+            if (OP == 0) s = fmaf(w, ri, s);
+            else if (OP == 1) s = fmaf(w, ri * ri * ri, s);
+            else s = fmaf(cq[q], ri * ri * ri, s);
+        }
+        if (OP == 1) s *= Dp0 * b.n[0] + Dp1 * b.n[1] + Dp2 * b.n[2];
+        ff_add(acc, w * s);
+    }
+    const FF r = ff_mul(acc, ff_mul(a.s, b.s));
+    return f2d_exact(r.hi) + f2d_exact(r.lo);
+}
+
 // largest distance of a quadrature point from the centroid
 __device__ __forceinline__ float trif_rad(const TriF &a)
 {
@@ -393,6 +445,12 @@ struct RegularEntry<OP, CPLX, 0> {  // FP64
     {
         return entry_fp64<OP, CPLX>(a, b, R.w, k);
     }
+    // the plain FP64 form keeps the 6-point rule for every block
+    static __device__ __forceinline__ C2 eval_rule(const Tri &a, const Tri &b, const QuadRule &R,
+                                                   double k, int)
+    {
+        return eval(a, b, R, k);
+    }
 };
 
 template <int OP, bool CPLX>
@@ -415,6 +473,17 @@ struct RegularEntry<OP, CPLX, 1> {  // mixed
     {
         if (!CPLX) return {entry_mixed_laplace<OP>(a, b, R.wf), 0.0};
         return entry_mixed_helmholtz<OP>(a, b, R.wf, (float)k, k);
+    }
+    // the block's distance-class rule (Laplace; Helmholtz keeps the 6-point
+    // rule, whose lower-order error is set by k h rather than by distance)
+    static __device__ __forceinline__ C2 eval_rule(const Tri &a, const Tri &b, const QuadRule &R,
+                                                   double k, int rule)
+    {
+        if constexpr (!CPLX) {
+            if (rule == kRule3) return {entry_mixed_laplace_low<OP, 3>(a, b, R.beta3f), 0.0};
+            if (rule == kRule1) return {entry_mixed_laplace_low<OP, 1>(a, b, R.beta3f), 0.0};
+        }
+        return eval(a, b, R, k);
     }
 };
 

@@ -41,12 +41,22 @@ static_assert(kFId + 3 == kTileFields, "tile fields");
 // Regular rule: reference points and weights (sum 1); wl[p][a] = w_p lambda_a(p)
 // with lambda = (1 - s - t, s, t) the barycentric coordinates of point p, the
 // weights of the piecewise linear local basis functions.
+// beta3: the scale that maps the stored points of the second orbit (indices
+// 3..5, barycentric (b, b, 1 - 2b) and permutations) onto the points of the
+// symmetric 3-point degree-2 rule (1/6, 1/6, 2/3): all lie on the medians, at
+// 1 - 3b and 1/2 of the vertex distance from the centroid.
 struct QuadRule {
     double s[NQ], t[NQ], w[NQ];
     float wf[NQ];
     double wl[NQ][3];
     float wlf[NQ][3];
+    double beta3;
+    float beta3f;
 };
+
+// Regular rule of an admissible block (distance classes, Laplace, P0): the
+// 6-point degree-4 rule, the 3-point degree-2 rule or the centroid rule.
+constexpr int kRule6 = 0, kRule3 = 1, kRule1 = 2;
 
 // Singular rule tables for one case (1 vertex-, 2 edge-adjacent, 3
 // identical).  Each 4D Gauss-Legendre node of the Sauter-Schwab maps gives
@@ -88,6 +98,8 @@ struct FarBlock {
     int32_t rank;
     int32_t status;                 // 0 ok, 1 rank cap, 2 pool overflow
     int64_t entries;                // entries evaluated by ACA
+    int32_t rule;                   // kRule6 / kRule3 / kRule1 (Laplace entries)
+    int32_t pad;
 };
 
 // Element offsets of a block's factor chunks (-1: not allocated), written by
@@ -202,7 +214,8 @@ cudaError_t launch_near_dp1(const DevGeom &g, const QuadRule &rule, int op, doub
 cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                        double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
                        int64_t n_small, int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
-                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st, int dofs = 1);
+                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st, int dofs = 1,
+                       bool rules = false);
 
 // the DP1 instantiations (kernels_aca_dp1.cu); no tiny-block class
 cudaError_t launch_aca_dp1(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,

@@ -31,6 +31,7 @@ int aca_tiny_max();
 
 static std::mutex g_tune_mu;
 static bem_tuning g_tuning{8192, 0, 1};
+static bem_quadrature g_quad{0.0, 0.0};
 
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -268,6 +269,8 @@ QuadRule make_rule6()
     double W1, W2;
     weights(a, b, W1, W2);
     QuadRule R{};
+    R.beta3 = 0.5 / (1.0 - 3.0 * b);
+    R.beta3f = (float)R.beta3;
     const double orb[2] = {a, b}, ow[2] = {W1 / 3.0, W2 / 3.0};
     int k = 0;
     for (int o = 0; o < 2; ++o) {
@@ -649,6 +652,24 @@ int bem_get_tuning(bem_tuning *t)
     return BEM_OK;
 }
 
+int bem_set_quadrature(const bem_quadrature *q)
+{
+    if (!q || !(q->rho3 >= 0.0) || !(q->rho1 >= 0.0) || !std::isfinite(q->rho3) ||
+        !std::isfinite(q->rho1))
+        return fail(BEM_E_ARG, "quadrature thresholds must be finite and >= 0");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_quad = *q;
+    return BEM_OK;
+}
+
+int bem_get_quadrature(bem_quadrature *q)
+{
+    if (!q) return BEM_E_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *q = g_quad;
+    return BEM_OK;
+}
+
 const char *bem_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
@@ -907,6 +928,7 @@ int bem_entries_dp1(bem_mesh mesh, int32_t op, double k, int32_t prec, const int
 struct Cluster {
     int64_t b, e, left, right;
     double box[6];
+    double h;       // longest edge of any of its triangles
 };
 
 struct BlockH {
@@ -929,6 +951,8 @@ struct bem_hmat_s {
     std::vector<SingPairL> singl[3];      // touching pairs of the DP1 near field
     std::vector<int64_t> vptr;            // P1: per vertex, its DP1 dofs (CSR, mesh order)
     std::vector<int32_t> vdof;
+    double rho3 = 0.0, rho1 = 0.0;        // distance-class thresholds of the regular rules
+    bool has_rules = false;               // some admissible block uses a lower-order rule
     int64_t small_max = 8192;             // blocks with max(m, n) <= this run on one warp
     int64_t tiny_max = 0;                 // ... and with max(m, n) <= this on one lane
     std::vector<int32_t> perm, iperm;
@@ -995,17 +1019,20 @@ namespace {
 // median of the centroids along the longest box axis).  Returns the split
 // point, or -1 for a leaf.
 int64_t split_cluster(Cluster &C, std::vector<int32_t> &perm, const std::vector<double> &cen,
-                      const std::vector<double> &tbox, int leaf)
+                      const std::vector<double> &tbox, const std::vector<double> &tlen, int leaf)
 {
     double box[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    double h = 0.0;
     for (int64_t q = C.b; q < C.e; ++q) {
         const double *tb = &tbox[6 * (int64_t)perm[q]];
         for (int c = 0; c < 3; ++c) {
             box[c] = std::min(box[c], tb[c]);
             box[3 + c] = std::max(box[3 + c], tb[3 + c]);
         }
+        h = std::max(h, tlen[perm[q]]);
     }
     std::memcpy(C.box, box, sizeof(box));
+    C.h = h;
     const int64_t n = C.e - C.b;
     if (n <= leaf) {
         std::sort(perm.begin() + C.b, perm.begin() + C.e);
@@ -1037,9 +1064,19 @@ void build_clusters(bem_hmat_s &H)
 {
     const bem_mesh_s &M = *H.mesh;
     const int64_t nt = M.nt;
-    std::vector<double> cen(3 * nt), tbox(6 * nt);
+    std::vector<double> cen(3 * nt), tbox(6 * nt), tlen(nt);
     parallel_tasks((nt + 16383) / 16384, [&](int64_t task) {
-        for (int64_t t = task * 16384, te = std::min(nt, t + 16384); t < te; ++t)
+        for (int64_t t = task * 16384, te = std::min(nt, t + 16384); t < te; ++t) {
+            // longest edge (squared lengths compared, one square root)
+            double h2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double *u = &M.V[3 * (int64_t)M.T[3 * t + a]];
+                const double *v = &M.V[3 * (int64_t)M.T[3 * t + (a + 1) % 3]];
+                double l2 = 0.0;
+                for (int c = 0; c < 3; ++c) l2 += (u[c] - v[c]) * (u[c] - v[c]);
+                h2 = std::max(h2, l2);
+            }
+            tlen[t] = std::sqrt(h2);
             for (int c = 0; c < 3; ++c) {
                 const double a = M.V[3 * (int64_t)M.T[3 * t] + c], b = M.V[3 * (int64_t)M.T[3 * t + 1] + c],
                              d = M.V[3 * (int64_t)M.T[3 * t + 2] + c];
@@ -1047,6 +1084,7 @@ void build_clusters(bem_hmat_s &H)
                 tbox[6 * t + c] = std::min(std::min(a, b), d);
                 tbox[6 * t + 3 + c] = std::max(std::max(a, b), d);
             }
+        }
     });
     H.perm.resize(nt);
     std::iota(H.perm.begin(), H.perm.end(), 0);
@@ -1060,7 +1098,7 @@ void build_clusters(bem_hmat_s &H)
         const size_t end = H.cl.size();
         for (size_t q = head; q < end; ++q) {
             Cluster C = H.cl[q];
-            const int64_t mid = split_cluster(C, H.perm, cen, tbox, H.leaf);
+            const int64_t mid = split_cluster(C, H.perm, cen, tbox, tlen, H.leaf);
             H.cl[q] = C;
             if (mid >= 0) {
                 const int64_t L = (int64_t)H.cl.size();
@@ -1083,7 +1121,7 @@ void build_clusters(bem_hmat_s &H)
         S.push_back(H.cl[head + f]);
         for (size_t q = 0; q < S.size(); ++q) {
             Cluster C = S[q];
-            const int64_t mid = split_cluster(C, H.perm, cen, tbox, H.leaf);
+            const int64_t mid = split_cluster(C, H.perm, cen, tbox, tlen, H.leaf);
             if (mid >= 0) {
                 C.left = (int64_t)S.size();   // local index, fixed up below
                 C.right = C.left + 1;
@@ -1131,6 +1169,27 @@ bool admissible(const double *bt, const double *bs, double eta)
     double dist = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
     if (!(dist > 0)) return false;
     return (dt < ds ? dt : ds) <= eta * dist;
+}
+
+// Regular rule of an admissible block by its distance class: rho = dist / h,
+// dist the distance between the cluster boxes (as in the admissibility test)
+// and h the longest triangle edge in either cluster; rho >= rho1 > 0 gives
+// the centroid rule, else rho >= rho3 > 0 the 3-point degree-2 rule, else the
+// 6-point degree-4 rule of Sec. 3.2.1.
+int block_rule(const Cluster &T, const Cluster &S, double rho3, double rho1)
+{
+    if (!(rho3 > 0) && !(rho1 > 0)) return kRule6;
+    const double *bt = T.box, *bs = S.box;
+    double g2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double g1 = bs[c] - bt[3 + c], gb = bt[c] - bs[3 + c];
+        const double m = g1 > gb ? g1 : gb;
+        if (m > 0) g2 += m * m;
+    }
+    const double dist = std::sqrt(g2), h = std::max(T.h, S.h);
+    if (rho1 > 0 && dist >= rho1 * h) return kRule1;
+    if (rho3 > 0 && dist >= rho3 * h) return kRule3;
+    return kRule6;
 }
 
 // Block tree: pairs (tau, sigma) from (root, root); an admissible pair, or one
@@ -1298,6 +1357,7 @@ void build_lists(bem_hmat_s &H)
             F.te = T.e;
             F.sb = S.b;
             F.se = S.e;
+            F.rule = H.dofs == 1 ? block_rule(T, S, H.rho3, H.rho1) : kRule6;
             H.far_block_id[f] = b;
             if (f < ncls[0]) mbig[ck] = std::max(mbig[ck], T.e - T.b);
             else if (f < ncls[0] + ncls[1]) msmall[ck] = std::max(msmall[ck], T.e - T.b);
@@ -1310,6 +1370,8 @@ void build_lists(bem_hmat_s &H)
     H.n_big = ncls[0];
     H.n_small = ncls[1];
     H.n_tiny = ncls[2];
+    H.has_rules = false;
+    for (const FarBlock &F : H.far) H.has_rules |= F.rule != kRule6;
 
     // leaves sorted by row start, and the leaf of every cluster-order row
     std::vector<std::pair<int64_t, int64_t>> lr;
@@ -1522,6 +1584,8 @@ int hmat_build_tree_impl(bem_mesh mesh, int32_t leaf_size, double eta, cudaStrea
             std::lock_guard<std::mutex> lk(g_tune_mu);
             H->small_max = g_tuning.warp_max_rows;
             H->tiny_max = H->dofs == 1 ? g_tuning.lane_max_rows : 0;
+            H->rho3 = H->dofs == 1 ? g_quad.rho3 : 0.0;
+            H->rho1 = H->dofs == 1 ? g_quad.rho1 : 0.0;
         }
         build_clusters(*H);
         const double t1 = now_ms();
@@ -1697,7 +1761,7 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
                 CU(launch_aca(H->geom.g, D.rule, aop, k, prec, aca_eps, H->d_far.as<FarBlock>(),
                               H->d_chunks.as<FarChunks>(), H->n_big, H->n_small, H->n_tiny, H->max_m_big, H->max_m_small,
                               H->d_pool.p, H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(),
-                              D.num_sms, st, H->dofs));
+                              D.num_sms, st, H->dofs, H->has_rules));
             rec(ev[2]);
             CU(launch_aca_finish(H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
                                  (int64_t)H->far.size(),
@@ -1879,6 +1943,12 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         s.n_clusters = (int64_t)H->cl.size();
         s.n_blocks_near = (int64_t)H->near.size();
         s.n_blocks_far = (int64_t)H->far.size();
+        for (const FarBlock &F : H->far) {
+            s.n_blocks_rule3 += F.rule == kRule3;
+            s.n_blocks_rule1 += F.rule == kRule1;
+        }
+        s.rho3 = H->rho3;
+        s.rho1 = H->rho1;
         s.near_entries = H->near_total;
         for (int c = 0; c < 3; ++c) s.singular_pairs[c] = (int64_t)H->sing[c].size();
         s.far_entries = H->far_entries;
@@ -1930,6 +2000,20 @@ int hmat_blocks(bem_hmat H, int64_t *blocks, int64_t cap, int64_t *n_blocks, int
             r[2] = S.b * H->dofs;
             r[3] = S.e * H->dofs;
             r[4] = H->blocks[b].adm ? 1 : 0;
+        }
+        return BEM_OK;
+    });
+}
+
+int hmat_block_rules(bem_hmat H, int32_t *points, int64_t cap)
+{
+    return guarded([&]() -> int {
+        if (!H || !points) return fail(BEM_E_ARG, "null argument");
+        if (cap < (int64_t)H->blocks.size()) return fail(BEM_E_ARG, "capacity too small");
+        for (size_t b = 0; b < H->blocks.size(); ++b) points[b] = 0;
+        for (size_t f = 0; f < H->far.size(); ++f) {
+            const int r = H->far[f].rule;
+            points[H->far_block_id[f]] = r == kRule1 ? 1 : (r == kRule3 ? 3 : 6);
         }
         return BEM_OK;
     });

@@ -40,3 +40,19 @@ def test_host_side_argument_validation(lib):
     assert lib.hmat_matvec(None, None, None, 1, None) == 1
     assert lib.hmat_destroy(None) == 1
     assert lib.hmat_stats(None, None) == 1
+
+
+def test_quadrature_class_arguments(lib):
+    """bem_set_quadrature rejects negative and non-finite thresholds and keeps
+    the previous ones; hmat_block_rules rejects null handles."""
+    saved = bem.bem_get_quadrature()
+    assert saved == {"rho3": 0.0, "rho1": 0.0}
+    for bad in ((-1.0, 0.0), (0.0, -2.0), (float("nan"), 0.0), (float("inf"), 0.0)):
+        with pytest.raises(bem.BemError):
+            bem.bem_set_quadrature(*bad)
+    assert bem.bem_get_quadrature() == saved
+    bem.bem_set_quadrature(4.0, 12.0)
+    assert bem.bem_get_quadrature() == {"rho3": 4.0, "rho1": 12.0}
+    bem.bem_set_quadrature(0.0, 0.0)
+    assert lib.bem_set_quadrature(None) == 1
+    assert lib.hmat_block_rules(None, None, 0) == 1

@@ -49,3 +49,11 @@ def test_thresholds_keep_results_and_autotuner_runs():
         assert r["rel_diff"] <= 2e-5 and r["time_ms"] > 0
     best = autotune.choose(res, 1e-5)
     assert best in res
+    q = autotune.measure_quadrature(V, T, ops=(bem.SLP,), eps=1e-5, reps=1,
+                                    candidates=[(0.0, 0.0), (6.0, 0.0), (6.0, 12.0)])
+    assert [(r["rho3"], r["rho1"]) for r in q] == [(0.0, 0.0), (6.0, 0.0), (6.0, 12.0)]
+    assert q[0]["rel_diff"] == 0.0 and q[0]["blocks_rule3"] == 0
+    assert q[1]["blocks_rule3"] > 0 and q[2]["blocks_rule1"] > 0
+    assert all(r["rel_diff"] < 1e-4 for r in q)
+    assert autotune.choose_quadrature(q, 1e-5) in q
+    assert bem.bem_get_quadrature() == {"rho3": 0.0, "rho1": 0.0}

@@ -33,3 +33,19 @@ def test_autotuner_picks_fastest_accurate_candidate():
     assert best["warp_max_rows"] == 2560 and best["lane_max_rows"] == 24
     with pytest.raises(RuntimeError):
         autotune.choose([dict(res[1])], eps=1e-5)
+
+
+def test_quadrature_autotuner_selection_rule():
+    res = [
+        {"rho3": 0.0, "rho1": 0.0, "time_ms": 10.0, "rel_diff": 0.0},
+        {"rho3": 4.0, "rho1": 0.0, "time_ms": 9.0, "rel_diff": 4e-6},
+        {"rho3": 4.0, "rho1": 16.0, "time_ms": 7.0, "rel_diff": 2e-5},   # beyond 0.5 eps
+        {"rho3": 6.0, "rho1": 32.0, "time_ms": 8.0, "rel_diff": 1e-6},
+    ]
+    best = autotune.choose_quadrature(res, eps=1e-5)
+    assert (best["rho3"], best["rho1"]) == (6.0, 32.0)
+    assert autotune.choose_quadrature(res[:3], eps=1e-5)["rho3"] == 4.0
+    with pytest.raises(RuntimeError):
+        autotune.choose_quadrature([dict(res[2])], eps=1e-5)
+    cands = autotune.quadrature_candidates((0.0, 4.0, 24.0), (0.0, 16.0))
+    assert (0.0, 0.0) in cands and (4.0, 16.0) in cands and (24.0, 16.0) not in cands
