@@ -94,7 +94,8 @@ class Clocks:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_gpu{gpu}.csv")
+        out_dir = os.environ.get("BEM_BENCH_OUT", os.path.join(ROOT, "bench_out"))
+        self.path = os.path.join(out_dir, f"clocks_bench_gpu{gpu}.csv")
 
     def start(self):
         try:
@@ -357,7 +358,7 @@ def run_gpu(args):
         "tolerance": 2 * EPS}
 
     # the same step on trees built with the autotuned distance classes of the
-    # regular rule (SURVEY A9), products against the FP64 6-point step above
+    # regular rule, products against the FP64 6-point step above
     auto_q = None
     if args.level == 6 and not (args.rho3 > 0 or args.rho1 > 0):
         saved_q = bem.bem_get_quadrature()
