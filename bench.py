@@ -198,6 +198,27 @@ def quadrature_roofline(bem, mesh, V, T, dev, stream, flush, reps: int = 3):
 # CPU oracle arm (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the ISA)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.split(":")[0].strip().lower() == "model name":
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def oracle_sample_rate(V, T, seconds_target: float = 15.0, seed: int = 7, nthreads: int = 0,
                        ops=None, k: float = 0.0, eps: float = EPS):
     """Times the oracle's H-matrix assembly (Algorithm "H-Matrix Assembly":
@@ -252,7 +273,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": WORKLOAD,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -494,7 +515,7 @@ def run_gpu(args):
         rate, cores, sample = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds)
         rate1, _, sample1 = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds / 3, seed=8,
                                                nthreads=1)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle", "sample": sample,
                "one_thread": {"value": rate1, "unit": UNIT, "cores": 1, "sample": sample1}}
 
     if rank == 0:
@@ -695,7 +716,7 @@ def run_large(args, spec):
         # leaf blocks, extrapolated to the whole assembly by its integrals
         rate, cores, sample = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds,
                                                  ops=(spec["op"],), k=k, eps=spec["eps"])
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle", "sample": sample,
                "extrapolated_assembly_s": (ents / args.steps) / rate}
     got = y.cpu().numpy()[rows]
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
@@ -720,7 +741,8 @@ def run_large(args, spec):
             # block's last 4-column chunk are not read)
             "matvec_gbs": (st["near_bytes"] + st["factor_read_bytes"]) / (np.median(mv_ms) * 1e-3) / 1e9,
             "sampled_rows_rel_err": err, "tolerance": 2 * spec["eps"],
-            "oracle_rows_s": t_or, "cpu_baseline": cpu, "clocks": clocks}
+            "oracle_rows_s": t_or, "cpu_baseline": cpu, "clocks": clocks,
+            "aca_work_shapes": bem.bem_get_tuning()}
     if args.rho3 > 0 or args.rho1 > 0:
         line["quadrature_classes"] = {"rho3": args.rho3, "rho1": args.rho1,
                                       "blocks": {"rule3": st["n_blocks_rule3"],
@@ -933,12 +955,23 @@ def main():
     ap.add_argument("--calib", type=int, default=24)
     ap.add_argument("--level", type=int, default=6,
                     help="icosphere level of the mesh (6 = the workload; smaller for profiling)")
+    ap.add_argument("--warp-max-rows", type=int, default=0,
+                    help="ACA work shapes (bem_set_tuning): blocks up to this many rows on one warp, "
+                         "larger ones on a CTA (0 = the library's setting)")
+    ap.add_argument("--lane-max-rows", type=int, default=-1,
+                    help="... and up to this many on one lane (-1 = the library's setting)")
     ap.add_argument("--rho3", type=float, default=0.0,
                     help="distance class of the 3-point regular rule (dist/h; 0 = the paper's "
                          "6-point rule for every block)")
     ap.add_argument("--rho1", type=float, default=0.0,
                     help="distance class of the centroid rule (dist/h; 0 = off)")
     args = ap.parse_args()
+    if args.warp_max_rows > 0 or args.lane_max_rows >= 0:
+        from paper_1711_01897_gb300 import bem
+        t = bem.bem_get_tuning()
+        bem.bem_set_tuning(args.warp_max_rows if args.warp_max_rows > 0 else t["warp_max_rows"],
+                           args.lane_max_rows if args.lane_max_rows >= 0 else t["lane_max_rows"],
+                           t["use_graphs"])
     if args.rho3 > 0 or args.rho1 > 0:
         from paper_1711_01897_gb300 import bem
         bem.bem_set_quadrature(args.rho3, args.rho1)

@@ -50,10 +50,13 @@ def choose(results, eps):
 
 
 def measure(V, T, ops=(0, 1), eps=1e-5, prec=1, reps=2, warp=WARP_CANDIDATES,
-            lane=LANE_CANDIDATES, leaf=32, eta=1.2):
+            lane=LANE_CANDIDATES, leaf=32, eta=1.2, k=0.0):
+    """k != 0: the Helmholtz operators (complex entries and factors)."""
     from . import bem
     mesh = bem.Mesh(V, T)
     x = np.random.default_rng(0).normal(size=T.shape[0])
+    if k != 0.0:
+        x = x + 0j
     base = {}
     results = []
     saved = bem.bem_get_tuning()
@@ -68,7 +71,7 @@ def measure(V, T, ops=(0, 1), eps=1e-5, prec=1, reps=2, warp=WARP_CANDIDATES,
                     h = bem.HMatrix(mesh, leaf, eta)
                     times = []
                     for _ in range(reps):
-                        h.assemble(op, 0.0, eps, prec)
+                        h.assemble(op, k, eps, prec)
                         st = h.stats()
                         times.append(st["time_near_ms"] + st["time_far_ms"])
                     y = h.matvec(x)
@@ -167,6 +170,9 @@ def apply(path: str = DEFAULT_TABLE) -> bool:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--level", type=int, default=5)
+    ap.add_argument("--ellipsoid-nu", type=int, default=0,
+                    help="tune on the 10 x 1 x 1 ellipsoid of this geodesic frequency instead of the "
+                         "jittered sphere, Helmholtz single layer at 10 elements per wavelength")
     ap.add_argument("--eps", type=float, default=1e-5)
     ap.add_argument("--out", default=DEFAULT_TABLE)
     ap.add_argument("--quadrature", action="store_true",
@@ -176,18 +182,24 @@ def main():
     import torch
     from . import meshes
     torch.cuda.init()
-    V, T = meshes.icosphere_level(args.level)
-    V = meshes.jitter(V, T, 0.05, 1001)
-    res = measure(V, T, eps=args.eps)
+    if args.ellipsoid_nu > 0:
+        V, T = meshes.ellipsoid(args.ellipsoid_nu)
+        k = meshes.helmholtz_k_10_per_wavelength(V, T)
+        res = measure(V, T, ops=(0,), eps=args.eps, reps=1, k=k)
+        what = (f"Helmholtz SLP, ellipsoid 10x1x1 nu {args.ellipsoid_nu} ({T.shape[0]} triangles), "
+                f"k {k:.4g}, eps {args.eps}, mixed")
+    else:
+        V, T = meshes.icosphere_level(args.level)
+        V = meshes.jitter(V, T, 0.05, 1001)
+        res = measure(V, T, eps=args.eps)
+        what = f"Laplace SLP+DLP, jittered icosphere level {args.level}, eps {args.eps}, mixed"
     best = choose(res, args.eps)
     table = {"warp_max_rows": best["warp_max_rows"], "lane_max_rows": best["lane_max_rows"],
-             "use_graphs": 1, "time_ms": best["time_ms"],
-             "workload": f"Laplace SLP+DLP, jittered icosphere level {args.level}, eps {args.eps}, mixed",
-             "candidates": res}
+             "use_graphs": 1, "time_ms": best["time_ms"], "workload": what, "candidates": res}
     with open(args.out, "w") as f:
         json.dump(table, f, indent=1)
     print(json.dumps({k: table[k] for k in ("warp_max_rows", "lane_max_rows", "time_ms")}))
-    if args.quadrature:
+    if args.quadrature and args.ellipsoid_nu == 0:
         apply(args.out)
         qres = measure_quadrature(V, T, eps=args.eps)
         qbest = choose_quadrature(qres, args.eps)
