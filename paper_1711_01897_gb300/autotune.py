@@ -49,9 +49,22 @@ def choose(results, eps):
     return min(ok, key=lambda r: (r["time_ms"], -r["warp_max_rows"], r["lane_max_rows"]))
 
 
+def shortlist(results, eps, n=3, default=(8192, 0)):
+    """The n fastest admissible candidates and the library default, as
+    (warp_max_rows, lane_max_rows) pairs, for a confirmation round with more
+    repetitions (a single timing of a persistent launch varies by several
+    percent between runs)."""
+    ok = sorted((r for r in results if r["rel_diff"] <= 2.0 * eps), key=lambda r: r["time_ms"])
+    pairs = [(r["warp_max_rows"], r["lane_max_rows"]) for r in ok[:n]]
+    if default not in pairs:
+        pairs.append(default)
+    return pairs
+
+
 def measure(V, T, ops=(0, 1), eps=1e-5, prec=1, reps=2, warp=WARP_CANDIDATES,
-            lane=LANE_CANDIDATES, leaf=32, eta=1.2, k=0.0):
-    """k != 0: the Helmholtz operators (complex entries and factors)."""
+            lane=LANE_CANDIDATES, leaf=32, eta=1.2, k=0.0, pairs=None):
+    """k != 0: the Helmholtz operators (complex entries and factors).  pairs:
+    explicit (warp, lane) candidates instead of the product of warp and lane."""
     from . import bem
     mesh = bem.Mesh(V, T)
     x = np.random.default_rng(0).normal(size=T.shape[0])
@@ -61,27 +74,27 @@ def measure(V, T, ops=(0, 1), eps=1e-5, prec=1, reps=2, warp=WARP_CANDIDATES,
     results = []
     saved = bem.bem_get_tuning()
     try:
-        for w in warp:
-            for l in lane:
-                if l > w:
-                    continue
-                bem.bem_set_tuning(w, l, 0)
-                total, diffs = 0.0, []
-                for op in ops:
-                    h = bem.HMatrix(mesh, leaf, eta)
-                    times = []
-                    for _ in range(reps):
-                        h.assemble(op, k, eps, prec)
-                        st = h.stats()
-                        times.append(st["time_near_ms"] + st["time_far_ms"])
-                    y = h.matvec(x)
-                    h.close()
-                    if op not in base:
-                        base[op] = y
-                    diffs.append(float(np.linalg.norm(y - base[op]) / np.linalg.norm(base[op])))
-                    total += min(times)
-                results.append({"warp_max_rows": w, "lane_max_rows": l, "time_ms": total,
-                                "rel_diff": max(diffs)})
+        cands = pairs if pairs is not None else [(w, l) for w in warp for l in lane]
+        for w, l in cands:
+            if l > w:
+                continue
+            bem.bem_set_tuning(w, l, 0)
+            total, diffs = 0.0, []
+            for op in ops:
+                h = bem.HMatrix(mesh, leaf, eta)
+                times = []
+                for _ in range(reps):
+                    h.assemble(op, k, eps, prec)
+                    st = h.stats()
+                    times.append(st["time_near_ms"] + st["time_far_ms"])
+                y = h.matvec(x)
+                h.close()
+                if op not in base:
+                    base[op] = y
+                diffs.append(float(np.linalg.norm(y - base[op]) / np.linalg.norm(base[op])))
+                total += min(times)
+            results.append({"warp_max_rows": w, "lane_max_rows": l, "time_ms": total,
+                            "rel_diff": max(diffs)})
     finally:
         bem.bem_set_tuning(saved["warp_max_rows"], saved["lane_max_rows"], saved["use_graphs"])
         mesh.close()
@@ -185,17 +198,21 @@ def main():
     if args.ellipsoid_nu > 0:
         V, T = meshes.ellipsoid(args.ellipsoid_nu)
         k = meshes.helmholtz_k_10_per_wavelength(V, T)
-        res = measure(V, T, ops=(0,), eps=args.eps, reps=1, k=k)
+        first = measure(V, T, ops=(0,), eps=args.eps, reps=1, k=k)
+        res = measure(V, T, ops=(0,), eps=args.eps, reps=3, k=k,
+                      pairs=shortlist(first, args.eps))
         what = (f"Helmholtz SLP, ellipsoid 10x1x1 nu {args.ellipsoid_nu} ({T.shape[0]} triangles), "
                 f"k {k:.4g}, eps {args.eps}, mixed")
     else:
         V, T = meshes.icosphere_level(args.level)
         V = meshes.jitter(V, T, 0.05, 1001)
-        res = measure(V, T, eps=args.eps)
+        first = measure(V, T, eps=args.eps)
+        res = measure(V, T, eps=args.eps, reps=5, pairs=shortlist(first, args.eps))
         what = f"Laplace SLP+DLP, jittered icosphere level {args.level}, eps {args.eps}, mixed"
     best = choose(res, args.eps)
     table = {"warp_max_rows": best["warp_max_rows"], "lane_max_rows": best["lane_max_rows"],
-             "use_graphs": 1, "time_ms": best["time_ms"], "workload": what, "candidates": res}
+             "use_graphs": 1, "time_ms": best["time_ms"], "workload": what, "candidates": first,
+             "confirmation": res}
     with open(args.out, "w") as f:
         json.dump(table, f, indent=1)
     print(json.dumps({k: table[k] for k in ("warp_max_rows", "lane_max_rows", "time_ms")}))

@@ -49,3 +49,14 @@ def test_quadrature_autotuner_selection_rule():
         autotune.choose_quadrature([dict(res[2])], eps=1e-5)
     cands = autotune.quadrature_candidates((0.0, 4.0, 24.0), (0.0, 16.0))
     assert (0.0, 0.0) in cands and (4.0, 16.0) in cands and (24.0, 16.0) not in cands
+
+
+def test_autotuner_shortlist_for_confirmation():
+    res = [
+        {"warp_max_rows": 160, "lane_max_rows": 0, "time_ms": 5.0, "rel_diff": 0.0},
+        {"warp_max_rows": 320, "lane_max_rows": 24, "time_ms": 4.0, "rel_diff": 1e-3},  # inaccurate
+        {"warp_max_rows": 640, "lane_max_rows": 0, "time_ms": 6.0, "rel_diff": 0.0},
+        {"warp_max_rows": 8192, "lane_max_rows": 0, "time_ms": 9.0, "rel_diff": 0.0},
+    ]
+    assert autotune.shortlist(res, 1e-5, n=2) == [(160, 0), (640, 0), (8192, 0)]
+    assert autotune.shortlist(res, 1e-5, n=3) == [(160, 0), (640, 0), (8192, 0)]
