@@ -56,6 +56,11 @@ FP64_TFLOPS_NOMINAL = 1.25
 # --level 6 --quadrature (eps 1e-5, products within 0.5 eps of the 6-point
 # products); the C2 line reports them beside the paper's 6-point rule
 AUTOTUNED_RHO_L6 = (4.0, 24.0)
+# ACA work shapes (bem_set_tuning: warp_max_rows, lane_max_rows) the autotuner
+# chose for the Helmholtz ellipsoid workload: python -m
+# paper_1711_01897_gb300.autotune --ellipsoid-nu 158 --eps 1e-4 (confirmation
+# round, three repetitions: 1321 ms against 1373 ms for the library default)
+AUTOTUNED_SHAPES_C3 = (160, 48)
 
 ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.707635968 + 1.940037376 + 10.711072512 + 2.945069056) * 1e9
 
@@ -671,6 +676,9 @@ def run_large(args, spec):
     V, T = meshes.workload_mesh(spec["mesh"])
     n = T.shape[0]
     k = meshes.helmholtz_k_10_per_wavelength(V, T) if spec["helmholtz"] else 0.0
+    if spec["helmholtz"] and args.warp_max_rows <= 0 and args.lane_max_rows < 0:
+        t = bem.bem_get_tuning()
+        bem.bem_set_tuning(AUTOTUNED_SHAPES_C3[0], AUTOTUNED_SHAPES_C3[1], t["use_graphs"])
     t0 = time.perf_counter()
     mesh = bem.Mesh(V, T)
     h = bem.HMatrix(mesh, LEAF, ETA)
