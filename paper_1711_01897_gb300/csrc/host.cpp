@@ -21,6 +21,9 @@
 #include "bem_internal.h"
 
 #include <atomic>
+#include <condition_variable>
+#include <unistd.h>
+#include <functional>
 #include <thread>
 
 using namespace bem;
@@ -503,34 +506,113 @@ struct bem_mesh_s {
 
 namespace {
 
-// Host threads for the mesh and tree builds: f(task) for task in [0, ntask), handed out
-// by an atomic counter to at most the hardware's thread count.  f must not
-// throw; the first error message is kept and rethrown after the join.
+// Helper threads of one calling thread, created on its first parallel call
+// and reused by the later ones (creating and joining threads for every call
+// cost more than the work of most tree-build phases).  Each calling thread
+// (the caller's own, a server slot's worker) has its own pool, joined when
+// that thread exits.
+class TaskPool {
+public:
+    const pid_t owner = getpid();   // a forked child inherits the object, not the threads
+    explicit TaskPool(int helpers)
+    {
+        for (int i = 0; i < helpers; ++i) workers_.emplace_back([this] { loop(); });
+    }
+    ~TaskPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        wake_.notify_all();
+        for (auto &t : workers_) t.join();
+    }
+    int helpers() const { return (int)workers_.size(); }
+    // runs f(task) for task in [0, ntask) on the caller and the helpers
+    void run(int64_t ntask, const std::function<void(int64_t)> &f)
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            job_ = &f;
+            ntask_ = ntask;
+            next_.store(0);
+            busy_ = (int)workers_.size();
+            err_.clear();
+            ++gen_;
+        }
+        wake_.notify_all();
+        work();
+        std::unique_lock<std::mutex> lk(mu_);
+        done_.wait(lk, [&] { return busy_ == 0; });
+        job_ = nullptr;
+        if (!err_.empty()) throw std::runtime_error(err_);
+    }
+
+private:
+    void work()
+    {
+        for (;;) {
+            const int64_t t = next_.fetch_add(1);
+            if (t >= ntask_) return;
+            try {
+                (*job_)(t);
+            } catch (const std::exception &e) {
+                std::lock_guard<std::mutex> lk(mu_);
+                if (err_.empty()) err_ = e.what();
+            }
+        }
+    }
+    void loop()
+    {
+        uint64_t seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                wake_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+            }
+            work();
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--busy_ == 0) done_.notify_all();
+        }
+    }
+    std::vector<std::thread> workers_;
+    std::mutex mu_;
+    std::condition_variable wake_, done_;
+    const std::function<void(int64_t)> *job_ = nullptr;
+    int64_t ntask_ = 0;
+    std::atomic<int64_t> next_{0};
+    int busy_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+    std::string err_;
+};
+
+// Host threads for the mesh and tree builds: f(task) for task in [0, ntask),
+// handed out by an atomic counter to the calling thread and its pool of
+// helpers (the hardware's thread count, at most 32, in all).  An exception
+// from f is kept and rethrown, as a runtime_error, after all tasks ran.
 template <class F>
 void parallel_tasks(int64_t ntask, F &&f)
 {
-    unsigned hw = std::thread::hardware_concurrency();
-    int64_t nth = std::min<int64_t>(std::min<int64_t>(hw ? hw : 1, 32), ntask);
-    std::atomic<int64_t> next{0};
-    std::mutex emu;
-    std::string err;
-    auto run = [&] {
-        for (;;) {
-            const int64_t t = next.fetch_add(1);
-            if (t >= ntask) return;
-            try {
-                f(t);
-            } catch (const std::exception &e) {
-                std::lock_guard<std::mutex> lk(emu);
-                if (err.empty()) err = e.what();
-            }
-        }
-    };
-    std::vector<std::thread> th;
-    for (int64_t i = 1; i < nth; ++i) th.emplace_back(run);
-    run();
-    for (auto &x : th) x.join();
-    if (!err.empty()) throw std::runtime_error(err);
+    if (ntask <= 0) return;
+    if (ntask == 1) {
+        f(0);
+        return;
+    }
+    thread_local std::unique_ptr<TaskPool> pool;
+    if (pool && pool->owner != getpid()) {
+        // in a forked child: the helpers stayed with the parent, so the
+        // object is dropped without joining them
+        (void)pool.release();
+    }
+    if (!pool) {
+        const unsigned hw = std::thread::hardware_concurrency();
+        pool.reset(new TaskPool((int)std::min<unsigned>(hw ? hw : 1, 32u) - 1));
+    }
+    const std::function<void(int64_t)> fn = [&](int64_t t) { f(t); };
+    pool->run(ntask, fn);
 }
 
 // Touching triangles (sharing at least one vertex, itself included) of every
@@ -1269,8 +1351,30 @@ void build_blocks(bem_hmat_s &H)
 // side (CTA, warp, lane ACA), each in longest-processing-time-first order
 // (m + n descending, tree order on ties); the order comes from one sort of
 // packed 64-bit keys so that each FarBlock is written once.
+// Sub-phase timings of build_lists on stderr when BEM_TRACE_TREE is set.
+struct PhaseTrace {
+    bool on;
+    double t0, last;
+    std::string text;
+    PhaseTrace() : on(std::getenv("BEM_TRACE_TREE") != nullptr), t0(now_ms()), last(t0) {}
+    void mark(const char *name)
+    {
+        if (!on) return;
+        const double t = now_ms();
+        char buf[96];
+        std::snprintf(buf, sizeof buf, " %s %.2f", name, t - last);
+        text += buf;
+        last = t;
+    }
+    ~PhaseTrace()
+    {
+        if (on) std::fprintf(stderr, "tree lists (ms):%s; total %.2f\n", text.c_str(), now_ms() - t0);
+    }
+};
+
 void build_lists(bem_hmat_s &H)
 {
+    PhaseTrace trace;
     const bem_mesh_s &M = *H.mesh;
     const int64_t nb = (int64_t)H.blocks.size(), nt = M.nt;
     if (nb >= (int64_t(1) << 32) || nt >= (int64_t(1) << 29))
@@ -1304,6 +1408,7 @@ void build_lists(bem_hmat_s &H)
             }
         }
     });
+    trace.mark("classify");
     int64_t nnear = 0, nkey = 0;
     for (const BlkPart &P : bp) {
         nnear += (int64_t)P.near.size();
@@ -1327,6 +1432,7 @@ void build_lists(bem_hmat_s &H)
         for (int c = 0; c < 3; ++c) ncls[c] += P.ncls[c];
     }
     H.near_total = off;
+    trace.mark("join");
     // the keys were made in increasing block order, so a stable sort on the
     // upper 32 bits (class, size) alone orders them fully: two 16-bit LSD
     // counting passes
@@ -1341,6 +1447,7 @@ void build_lists(bem_hmat_s &H)
             key.swap(tmp);
         }
     }
+    trace.mark("sort");
     H.far.resize(key.size());
     H.far_block_id.resize(key.size());
     H.max_m_big = H.max_m_small = 0;
@@ -1372,6 +1479,7 @@ void build_lists(bem_hmat_s &H)
     H.n_tiny = ncls[2];
     H.has_rules = false;
     for (const FarBlock &F : H.far) H.has_rules |= F.rule != kRule6;
+    trace.mark("far");
 
     // leaves sorted by row start, and the leaf of every cluster-order row
     std::vector<std::pair<int64_t, int64_t>> lr;
@@ -1386,40 +1494,96 @@ void build_lists(bem_hmat_s &H)
         H.leaf_rows[2 * l + 1] = lr[l].second;
         for (int64_t p = lr[l].first; p < lr[l].second; ++p) leaf_of[p] = l;
     }
+    trace.mark("leaves");
     // per leaf, the blocks whose row range contains it: far blocks in list
-    // order as f, then near blocks in tree order as -1 - q (CSR, two passes)
+    // order as f, then near blocks in tree order as -1 - q (CSR).  The far
+    // and near lists are cut into chunks; every chunk counts its items per
+    // leaf, a prefix over the chunks gives each chunk its slots in every
+    // leaf, and the chunks fill their slots in parallel, so each leaf's list
+    // keeps the sequential order.
+    const int64_t nfar_b = (int64_t)H.far.size(), nnear_b = (int64_t)H.near.size();
+    constexpr int64_t kItemChunks = 32;
+    const int64_t fch = std::max<int64_t>(1, (nfar_b + kItemChunks - 1) / kItemChunks);
+    const int64_t nch = std::max<int64_t>(1, (nnear_b + kItemChunks - 1) / kItemChunks);
+    const int64_t nfc_i = (nfar_b + fch - 1) / fch, nnc_i = (nnear_b + nch - 1) / nch;
+    const int64_t ncks = nfc_i + nnc_i;  // far chunks first, then near chunks
+    std::vector<std::vector<int32_t>> ccount(ncks, std::vector<int32_t>(nleaf, 0));
+    auto chunk_range = [&](int64_t ck, int64_t &b, int64_t &e, bool &is_far) {
+        is_far = ck < nfc_i;
+        if (is_far) {
+            b = ck * fch;
+            e = std::min(nfar_b, b + fch);
+        } else {
+            b = (ck - nfc_i) * nch;
+            e = std::min(nnear_b, b + nch);
+        }
+    };
+    auto leaves_of = [&](int64_t idx, bool is_far, int64_t &l0, int64_t &l1) {
+        const int64_t tb = is_far ? H.far[idx].tb : H.near[idx].tb;
+        const int64_t te = is_far ? H.far[idx].te : H.near[idx].te;
+        l0 = leaf_of[tb];
+        l1 = leaf_of[te - 1];
+    };
+    parallel_tasks(ncks, [&](int64_t ck) {
+        int64_t b, e, l0, l1;
+        bool is_far;
+        chunk_range(ck, b, e, is_far);
+        std::vector<int32_t> &c = ccount[ck];
+        for (int64_t x = b; x < e; ++x) {
+            leaves_of(x, is_far, l0, l1);
+            for (int64_t l = l0; l <= l1; ++l) ++c[l];
+        }
+    });
+    // per leaf: its total, and every chunk's first slot (counts become offsets)
     H.leaf_ptr.assign(nleaf + 1, 0);
-    for (const FarBlock &F : H.far)
-        for (int64_t l = leaf_of[F.tb]; l <= leaf_of[F.te - 1]; ++l) ++H.leaf_ptr[l + 1];
-    for (const NearBlock &N : H.near)
-        for (int64_t l = leaf_of[N.tb]; l <= leaf_of[N.te - 1]; ++l) ++H.leaf_ptr[l + 1];
+    parallel_tasks((nleaf + 4095) / 4096, [&](int64_t task) {
+        for (int64_t l = task * 4096, le = std::min(nleaf, l + 4096); l < le; ++l) {
+            int32_t run = 0;
+            for (int64_t ck = 0; ck < ncks; ++ck) {
+                const int32_t c = ccount[ck][l];
+                ccount[ck][l] = run;
+                run += c;
+            }
+            H.leaf_ptr[l + 1] = run;
+        }
+    });
     for (int64_t l = 0; l < nleaf; ++l) H.leaf_ptr[l + 1] += H.leaf_ptr[l];
     H.leaf_items.resize(H.leaf_ptr[nleaf]);
-    std::vector<int64_t> pos(H.leaf_ptr.begin(), H.leaf_ptr.end() - 1);
-    for (size_t f = 0; f < H.far.size(); ++f)
-        for (int64_t l = leaf_of[H.far[f].tb]; l <= leaf_of[H.far[f].te - 1]; ++l)
-            H.leaf_items[pos[l]++] = (int64_t)f;
+    parallel_tasks(ncks, [&](int64_t ck) {
+        int64_t b, e, l0, l1;
+        bool is_far;
+        chunk_range(ck, b, e, is_far);
+        std::vector<int32_t> &c = ccount[ck];
+        for (int64_t x = b; x < e; ++x) {
+            leaves_of(x, is_far, l0, l1);
+            for (int64_t l = l0; l <= l1; ++l)
+                H.leaf_items[H.leaf_ptr[l] + c[l]++] = is_far ? x : -1 - x;
+        }
+    });
+    trace.mark("leaf_far_items");
     // near blocks per row leaf, by column start (the columns of one leaf's
-    // blocks are disjoint, so the starts are distinct)
+    // blocks are disjoint, so the starts are distinct), for the touching pairs
     std::vector<int64_t> nptr(nleaf + 1, 0);
     for (size_t q = 0; q < H.near.size(); ++q)
-        for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l) {
-            H.leaf_items[pos[l]++] = -1 - (int64_t)q;
-            ++nptr[l + 1];
-        }
+        for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l) ++nptr[l + 1];
     for (int64_t l = 0; l < nleaf; ++l) nptr[l + 1] += nptr[l];
     std::vector<int64_t> nq(nptr[nleaf]);
-    std::copy(nptr.begin(), nptr.end() - 1, pos.begin());
-    for (size_t q = 0; q < H.near.size(); ++q)
-        for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l)
-            nq[pos[l]++] = (int64_t)q;
-    std::vector<int64_t> nsb(nq.size());
-    for (int64_t l = 0; l < nleaf; ++l) {
-        std::sort(nq.begin() + nptr[l], nq.begin() + nptr[l + 1],
-                  [&](int64_t a, int64_t b) { return H.near[a].sb < H.near[b].sb; });
-        for (int64_t i = nptr[l]; i < nptr[l + 1]; ++i) nsb[i] = H.near[nq[i]].sb;
+    {
+        std::vector<int64_t> pos(nptr.begin(), nptr.end() - 1);
+        for (size_t q = 0; q < H.near.size(); ++q)
+            for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l)
+                nq[pos[l]++] = (int64_t)q;
     }
+    std::vector<int64_t> nsb(nq.size());
+    parallel_tasks((nleaf + 1023) / 1024, [&](int64_t task) {
+        for (int64_t l = task * 1024, le = std::min(nleaf, l + 1024); l < le; ++l) {
+            std::sort(nq.begin() + nptr[l], nq.begin() + nptr[l + 1],
+                      [&](int64_t a, int64_t b) { return H.near[a].sb < H.near[b].sb; });
+            for (int64_t i = nptr[l]; i < nptr[l + 1]; ++i) nsb[i] = H.near[nq[i]].sb;
+        }
+    });
 
+    trace.mark("leaf_near_items");
     // singular pairs of the near field, with their place in the dense blocks
     int64_t ncase[3] = {0, 0, 0};
     for (int8_t c : M.adj_case) ++ncase[c - 1];
@@ -1472,6 +1636,7 @@ void build_lists(bem_hmat_s &H)
             }
         }
     });
+    trace.mark("singular");
     // join the chunks in order: offsets first, then the copies on the threads
     for (int c = 0; c < 3; ++c) {
         std::vector<int64_t> at(nchunk + 1, 0);
@@ -1484,6 +1649,7 @@ void build_lists(bem_hmat_s &H)
             else std::copy(csl[ck][c].begin(), csl[ck][c].end(), H.singl[c].begin() + at[ck]);
         });
     }
+    trace.mark("join_singular");
     if (H.dofs == 3) {
         // every list in dof units: ranges times three
         for (NearBlock &N : H.near) {
