@@ -1178,10 +1178,17 @@ void build_clusters(bem_hmat_s &H)
     size_t head = 0;
     while (head < H.cl.size() && H.cl.size() - head < want) {
         const size_t end = H.cl.size();
+        // the clusters of one level own disjoint ranges of perm: split them
+        // on the threads, then append their children in order
+        std::vector<int64_t> mids(end - head);
+        parallel_tasks((int64_t)(end - head), [&](int64_t i) {
+            Cluster C = H.cl[head + i];
+            mids[i] = split_cluster(C, H.perm, cen, tbox, tlen, H.leaf);
+            H.cl[head + i] = C;
+        });
         for (size_t q = head; q < end; ++q) {
-            Cluster C = H.cl[q];
-            const int64_t mid = split_cluster(C, H.perm, cen, tbox, tlen, H.leaf);
-            H.cl[q] = C;
+            const Cluster C = H.cl[q];
+            const int64_t mid = mids[q - head];
             if (mid >= 0) {
                 const int64_t L = (int64_t)H.cl.size();
                 H.cl[q].left = L;
