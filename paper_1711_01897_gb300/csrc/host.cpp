@@ -160,8 +160,8 @@ struct DBuf {
     {
         return reinterpret_cast<T *>(p);
     }
-    template <class T>
-    void upload(const std::vector<T> &v, cudaStream_t st = 0)
+    template <class T, class A>
+    void upload(const std::vector<T, A> &v, cudaStream_t st = 0)
     {
         alloc(v.size() * sizeof(T), st);
         if (!v.empty())
@@ -489,6 +489,30 @@ bool is_device_ptr(const void *p)
 // ---------------------------------------------------------------------------
 // meshes
 // ---------------------------------------------------------------------------
+// Allocator whose value-initialisation leaves elements uninitialised: for
+// host lists that are written in full right after they are sized.
+template <class T>
+struct NoInit : std::allocator<T> {
+    using value_type = T;
+    template <class U>
+    struct rebind {
+        using other = NoInit<U>;
+    };
+    NoInit() = default;
+    template <class U>
+    NoInit(const NoInit<U> &) noexcept {}
+    template <class U>
+    void construct(U *p) noexcept
+    {
+        ::new ((void *)p) U;
+    }
+    template <class U, class... A>
+    void construct(U *p, A &&...a)
+    {
+        ::new ((void *)p) U(std::forward<A>(a)...);
+    }
+};
+
 struct bem_mesh_s {
     int device = 0;
     int64_t nv = 0, nt = 0;
@@ -1030,7 +1054,7 @@ struct bem_hmat_s {
     int dofs = 1;
     int64_t ndof = 0;                     // length of the internal vectors
     std::vector<int32_t> dperm;           // dof permutation (DP1): cluster dof -> mesh dof
-    std::vector<SingPairL> singl[3];      // touching pairs of the DP1 near field
+    std::vector<SingPairL, NoInit<SingPairL>> singl[3];  // touching pairs of the DP1 near field
     std::vector<int64_t> vptr;            // P1: per vertex, its DP1 dofs (CSR, mesh order)
     std::vector<int32_t> vdof;
     double rho3 = 0.0, rho1 = 0.0;        // distance-class thresholds of the regular rules
@@ -1046,7 +1070,7 @@ struct bem_hmat_s {
     std::vector<int64_t> far_block_id;
     int64_t n_big = 0, n_small = 0, n_tiny = 0, max_m_big = 0, max_m_small = 0;
     int64_t near_total = 0;
-    std::vector<SingPair> sing[3];
+    std::vector<SingPair, NoInit<SingPair>> sing[3];
     // leaves (matvec)
     std::vector<int64_t> leaf_rows, leaf_ptr, leaf_items;
     // device
@@ -1592,31 +1616,34 @@ void build_lists(bem_hmat_s &H)
 
     trace.mark("leaf_near_items");
     // singular pairs of the near field, with their place in the dense blocks
-    int64_t ncase[3] = {0, 0, 0};
-    for (int8_t c : M.adj_case) ++ncase[c - 1];
     for (int c = 0; c < 3; ++c) {
         H.sing[c].clear();
         H.singl[c].clear();
-        (void)ncase;
     }
     // rows in chunks on the host threads, each chunk's pairs in row order,
-    // concatenated in chunk order (the sequential order)
+    // the chunks in order (the sequential order): the chunks count their
+    // pairs per case, the prefix over the chunks gives each its first slot,
+    // and the chunks write their pairs into the final lists
     constexpr int64_t kRowChunk = 8192;
     const int64_t nchunk = (nt + kRowChunk - 1) / kRowChunk;
-    std::vector<std::array<std::vector<SingPair>, 3>> cs(H.dofs == 1 ? nchunk : 0);
-    std::vector<std::array<std::vector<SingPairL>, 3>> csl(H.dofs == 3 ? nchunk : 0);
+    std::vector<std::array<int64_t, 3>> at(nchunk + 1, std::array<int64_t, 3>{0, 0, 0});
     parallel_tasks(nchunk, [&](int64_t ck) {
-        {
-            int64_t cnt[3] = {0, 0, 0};
-            for (int64_t p = ck * kRowChunk, pe = std::min(nt, p + kRowChunk); p < pe; ++p) {
-                const int32_t t = H.perm[p];
-                for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) ++cnt[M.adj_case[a] - 1];
-            }
-            for (int c = 0; c < 3; ++c) {
-                if (H.dofs == 1) cs[ck][c].reserve(cnt[c]);
-                else csl[ck][c].reserve(cnt[c]);
-            }
+        std::array<int64_t, 3> cnt{0, 0, 0};
+        for (int64_t p = ck * kRowChunk, pe = std::min(nt, p + kRowChunk); p < pe; ++p) {
+            const int32_t t = H.perm[p];
+            for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) ++cnt[M.adj_case[a] - 1];
         }
+        at[ck + 1] = cnt;
+    });
+    for (int64_t ck = 0; ck < nchunk; ++ck)
+        for (int c = 0; c < 3; ++c) at[ck + 1][c] += at[ck][c];
+    for (int c = 0; c < 3; ++c) {
+        if (H.dofs == 1) H.sing[c].resize(at[nchunk][c]);
+        else H.singl[c].resize(at[nchunk][c]);
+    }
+    trace.mark("singular_count");
+    parallel_tasks(nchunk, [&](int64_t ck) {
+        std::array<int64_t, 3> pos = at[ck];
         for (int64_t p = ck * kRowChunk, pe = std::min(nt, p + kRowChunk); p < pe; ++p) {
             const int32_t t = H.perm[p];
             const int64_t l = leaf_of[p];
@@ -1629,33 +1656,22 @@ void build_lists(bem_hmat_s &H)
                 if (it == b0) throw std::runtime_error("touching pair outside the near field");
                 const NearBlock &N = H.near[nq[nptr[l] + (it - 1 - b0)]];
                 if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
+                const int c = M.adj_case[a] - 1;
                 if (H.dofs == 1) {
                     // column-major block
                     const int64_t dest = N.off + (q - N.sb) * (N.te - N.tb) + (p - N.tb);
-                    cs[ck][M.adj_case[a] - 1].push_back({t, u, dest});
+                    H.sing[c][pos[c]++] = {t, u, dest};
                 } else {
                     // local (0, 0) of the pair in the column-major block of
                     // 3m x 3n dofs: rows step by 1, columns by 3m
                     const int64_t ld = 3 * (N.te - N.tb);
                     const int64_t dest = N.off + 3 * (q - N.sb) * ld + 3 * (p - N.tb);
-                    csl[ck][M.adj_case[a] - 1].push_back({t, u, dest, 1, (int32_t)ld});
+                    H.singl[c][pos[c]++] = {t, u, dest, 1, (int32_t)ld};
                 }
             }
         }
     });
     trace.mark("singular");
-    // join the chunks in order: offsets first, then the copies on the threads
-    for (int c = 0; c < 3; ++c) {
-        std::vector<int64_t> at(nchunk + 1, 0);
-        for (int64_t ck = 0; ck < nchunk; ++ck)
-            at[ck + 1] = at[ck] + (int64_t)(H.dofs == 1 ? cs[ck][c].size() : csl[ck][c].size());
-        if (H.dofs == 1) H.sing[c].resize(at[nchunk]);
-        else H.singl[c].resize(at[nchunk]);
-        parallel_tasks(nchunk, [&](int64_t ck) {
-            if (H.dofs == 1) std::copy(cs[ck][c].begin(), cs[ck][c].end(), H.sing[c].begin() + at[ck]);
-            else std::copy(csl[ck][c].begin(), csl[ck][c].end(), H.singl[c].begin() + at[ck]);
-        });
-    }
     trace.mark("join_singular");
     if (H.dofs == 3) {
         // every list in dof units: ranges times three
