@@ -1066,13 +1066,14 @@ struct bem_hmat_s {
     std::vector<BlockH> blocks;           // tree order
     std::vector<NearBlock> near;          // host copies
     std::vector<int64_t> near_block_id;   // index into blocks
-    std::vector<FarBlock> far;            // LPT order (big first, then small)
+    std::vector<FarBlock, NoInit<FarBlock>> far;  // LPT order (big first, then small)
     std::vector<int64_t> far_block_id;
     int64_t n_big = 0, n_small = 0, n_tiny = 0, max_m_big = 0, max_m_small = 0;
     int64_t near_total = 0;
     std::vector<SingPair, NoInit<SingPair>> sing[3];
     // leaves (matvec)
-    std::vector<int64_t> leaf_rows, leaf_ptr, leaf_items;
+    std::vector<int64_t> leaf_rows, leaf_ptr;
+    std::vector<int64_t, NoInit<int64_t>> leaf_items;
     // device
     DBuf d_perm, d_near, d_far, d_chunks, d_sing[3], d_leaf_rows, d_leaf_ptr, d_leaf_items, d_long, d_long_off;
     std::vector<int64_t> long_ids;        // admissible blocks with long columns (matvec)
