@@ -1566,6 +1566,7 @@ void build_lists(bem_hmat_s &H)
             for (int64_t l = l0; l <= l1; ++l) ++c[l];
         }
     });
+    trace.mark("items_count");
     // per leaf: its total, and every chunk's first slot (counts become offsets)
     H.leaf_ptr.assign(nleaf + 1, 0);
     parallel_tasks((nleaf + 4095) / 4096, [&](int64_t task) {
@@ -1581,6 +1582,7 @@ void build_lists(bem_hmat_s &H)
     });
     for (int64_t l = 0; l < nleaf; ++l) H.leaf_ptr[l + 1] += H.leaf_ptr[l];
     H.leaf_items.resize(H.leaf_ptr[nleaf]);
+    trace.mark("items_offsets");
     parallel_tasks(ncks, [&](int64_t ck) {
         int64_t b, e, l0, l1;
         bool is_far;
