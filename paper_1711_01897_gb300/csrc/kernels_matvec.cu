@@ -138,12 +138,11 @@ k_far_vtx(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks
 // column sequentially, so every FP64 instruction of the warp is useful and no
 // reductions are needed.  Columns longer than kMatvecLongCol go to
 // k_far_vtx_long.  A block of rank 0 owns no item (it is skipped by the search).
-
 template <typename T>
-__global__ void k_far_vtx_cols(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks,
-                          int64_t nfar,
-                          const int64_t *__restrict__ toff, const T *__restrict__ pool,
-                          const T *__restrict__ xt, T *__restrict__ tbuf)
+__global__ void k_far_vtx_cols(const FarBlock *__restrict__ far,
+                               const FarChunks *__restrict__ chunks, int64_t nfar,
+                               const int64_t *__restrict__ toff, const T *__restrict__ pool,
+                               const T *__restrict__ xt, T *__restrict__ tbuf)
 {
     const int64_t total = toff[nfar];
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
