@@ -613,6 +613,22 @@ private:
     std::string err_;
 };
 
+// The calling thread's pool (one per thread, shared by every parallel phase).
+TaskPool &thread_pool()
+{
+    thread_local std::unique_ptr<TaskPool> pool;
+    if (pool && pool->owner != getpid()) {
+        // in a forked child: the helpers stayed with the parent, so the
+        // object is dropped without joining them
+        (void)pool.release();
+    }
+    if (!pool) {
+        const unsigned hw = std::thread::hardware_concurrency();
+        pool.reset(new TaskPool((int)std::min<unsigned>(hw ? hw : 1, 32u) - 1));
+    }
+    return *pool;
+}
+
 // Host threads for the mesh and tree builds: f(task) for task in [0, ntask),
 // handed out by an atomic counter to the calling thread and its pool of
 // helpers (the hardware's thread count, at most 32, in all).  An exception
@@ -625,18 +641,8 @@ void parallel_tasks(int64_t ntask, F &&f)
         f(0);
         return;
     }
-    thread_local std::unique_ptr<TaskPool> pool;
-    if (pool && pool->owner != getpid()) {
-        // in a forked child: the helpers stayed with the parent, so the
-        // object is dropped without joining them
-        (void)pool.release();
-    }
-    if (!pool) {
-        const unsigned hw = std::thread::hardware_concurrency();
-        pool.reset(new TaskPool((int)std::min<unsigned>(hw ? hw : 1, 32u) - 1));
-    }
     const std::function<void(int64_t)> fn = [&](int64_t t) { f(t); };
-    pool->run(ntask, fn);
+    thread_pool().run(ntask, fn);
 }
 
 // Touching triangles (sharing at least one vertex, itself included) of every
