@@ -632,7 +632,8 @@ TaskPool &thread_pool()
 // Host threads for the mesh and tree builds: f(task) for task in [0, ntask),
 // handed out by an atomic counter to the calling thread and its pool of
 // helpers (the hardware's thread count, at most 32, in all).  An exception
-// from f is kept and rethrown, as a runtime_error, after all tasks ran.
+// from f is kept and rethrown, as a runtime_error, after all tasks ran.  f
+// must not call parallel_tasks itself (the pool runs one job at a time).
 template <class F>
 void parallel_tasks(int64_t ntask, F &&f)
 {
