@@ -1071,8 +1071,8 @@ struct bem_hmat_s {
     std::vector<int32_t> perm, iperm;
     std::vector<Cluster> cl;
     std::vector<BlockH> blocks;           // tree order
-    std::vector<NearBlock> near;          // host copies
-    std::vector<int64_t> near_block_id;   // index into blocks
+    std::vector<NearBlock, NoInit<NearBlock>> near;     // host copies
+    std::vector<int64_t, NoInit<int64_t>> near_block_id;  // index into blocks
     std::vector<FarBlock, NoInit<FarBlock>> far;  // LPT order (big first, then small)
     std::vector<int64_t> far_block_id;
     int64_t n_big = 0, n_small = 0, n_tiny = 0, max_m_big = 0, max_m_small = 0;
@@ -1448,41 +1448,70 @@ void build_lists(bem_hmat_s &H)
         }
     });
     trace.mark("classify");
-    int64_t nnear = 0, nkey = 0;
-    for (const BlkPart &P : bp) {
-        nnear += (int64_t)P.near.size();
-        nkey += (int64_t)P.key.size();
+    // the parts in order: their offsets first, then the copies on the threads
+    std::vector<int64_t> at_near(nbc + 1, 0), at_key(nbc + 1, 0), at_elems(nbc + 1, 0);
+    int64_t ncls[3] = {0, 0, 0};
+    for (int64_t ck = 0; ck < nbc; ++ck) {
+        at_near[ck + 1] = at_near[ck] + (int64_t)bp[ck].near.size();
+        at_key[ck + 1] = at_key[ck] + (int64_t)bp[ck].key.size();
+        at_elems[ck + 1] = at_elems[ck] + bp[ck].elems;
+        for (int c = 0; c < 3; ++c) ncls[c] += bp[ck].ncls[c];
     }
     H.near.clear();
-    H.near.reserve(nnear);
+    H.near.resize(at_near[nbc]);
     H.near_block_id.clear();
-    H.near_block_id.reserve(nnear);
-    std::vector<uint64_t> key;
-    key.reserve(nkey);
-    int64_t off = 0, ncls[3] = {0, 0, 0};
-    for (const BlkPart &P : bp) {
-        for (NearBlock N : P.near) {
-            N.off += off;
-            H.near.push_back(N);
+    H.near_block_id.resize(at_near[nbc]);
+    std::vector<uint64_t, NoInit<uint64_t>> key(at_key[nbc]);
+    parallel_tasks(nbc, [&](int64_t ck) {
+        const BlkPart &P = bp[ck];
+        for (size_t q = 0; q < P.near.size(); ++q) {
+            NearBlock N = P.near[q];
+            N.off += at_elems[ck];
+            H.near[at_near[ck] + q] = N;
+            H.near_block_id[at_near[ck] + q] = P.near_id[q];
         }
-        H.near_block_id.insert(H.near_block_id.end(), P.near_id.begin(), P.near_id.end());
-        key.insert(key.end(), P.key.begin(), P.key.end());
-        off += P.elems;
-        for (int c = 0; c < 3; ++c) ncls[c] += P.ncls[c];
-    }
-    H.near_total = off;
+        std::copy(P.key.begin(), P.key.end(), key.begin() + at_key[ck]);
+    });
+    H.near_total = at_elems[nbc];
     trace.mark("join");
     // the keys were made in increasing block order, so a stable sort on the
-    // upper 32 bits (class, size) alone orders them fully: two 16-bit LSD
-    // counting passes
+    // upper 32 bits (class, size) alone orders them fully: LSD passes of 8
+    // bits, each with digit counts per chunk on the threads, the offsets in
+    // (digit, chunk) order and a stable scatter per chunk; a pass whose keys
+    // all share their digit is skipped
     {
-        std::vector<uint64_t> tmp(key.size());
-        for (int pass = 0; pass < 2; ++pass) {
-            const int sh = 32 + 16 * pass;
-            std::vector<int64_t> cnt(65537, 0);
-            for (uint64_t k : key) ++cnt[((k >> sh) & 0xffffu) + 1];
-            for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
-            for (uint64_t k : key) tmp[cnt[(k >> sh) & 0xffffu]++] = k;
+        const int64_t nk = (int64_t)key.size();
+        const int64_t nck = std::max<int64_t>(1, std::min<int64_t>(64, nk / 16384));
+        const int64_t per = (nk + nck - 1) / nck;
+        std::vector<uint64_t, NoInit<uint64_t>> tmp(nk);
+        std::vector<std::array<int64_t, 256>> cnt(nck);
+        for (int pass = 0; pass < 4 && nk > 1; ++pass) {
+            const int sh = 32 + 8 * pass;
+            parallel_tasks(nck, [&](int64_t ck) {
+                std::array<int64_t, 256> &c = cnt[ck];
+                c.fill(0);
+                for (int64_t i = ck * per, ie = std::min(nk, i + per); i < ie; ++i)
+                    ++c[(key[i] >> sh) & 0xffu];
+            });
+            int used = 0;
+            for (int d = 0; d < 256; ++d) {
+                int64_t tot = 0;
+                for (int64_t ck = 0; ck < nck; ++ck) tot += cnt[ck][d];
+                used += tot > 0;
+            }
+            if (used <= 1) continue;
+            int64_t run = 0;
+            for (int d = 0; d < 256; ++d)
+                for (int64_t ck = 0; ck < nck; ++ck) {
+                    const int64_t v = cnt[ck][d];
+                    cnt[ck][d] = run;
+                    run += v;
+                }
+            parallel_tasks(nck, [&](int64_t ck) {
+                std::array<int64_t, 256> pos = cnt[ck];
+                for (int64_t i = ck * per, ie = std::min(nk, i + per); i < ie; ++i)
+                    tmp[pos[(key[i] >> sh) & 0xffu]++] = key[i];
+            });
             key.swap(tmp);
         }
     }
