@@ -1074,7 +1074,7 @@ struct bem_hmat_s {
     std::vector<NearBlock, NoInit<NearBlock>> near;     // host copies
     std::vector<int64_t, NoInit<int64_t>> near_block_id;  // index into blocks
     std::vector<FarBlock, NoInit<FarBlock>> far;  // LPT order (big first, then small)
-    std::vector<int64_t> far_block_id;
+    std::vector<int64_t, NoInit<int64_t>> far_block_id;
     int64_t n_big = 0, n_small = 0, n_tiny = 0, max_m_big = 0, max_m_small = 0;
     int64_t near_total = 0;
     std::vector<SingPair, NoInit<SingPair>> sing[3];
