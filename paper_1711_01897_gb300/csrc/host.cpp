@@ -1564,95 +1564,96 @@ void build_lists(bem_hmat_s &H)
     }
     trace.mark("leaves");
     // per leaf, the blocks whose row range contains it: far blocks in list
-    // order as f, then near blocks in tree order as -1 - q (CSR).  The far
-    // and near lists are cut into chunks; every chunk counts its items per
-    // leaf, a prefix over the chunks gives each chunk its slots in every
-    // leaf, and the chunks fill their slots in parallel, so each leaf's list
-    // keeps the sequential order.
+    // order as f, then near blocks in tree order as -1 - q (CSR).  A block
+    // covers a leaf exactly when its row cluster is the leaf's cluster or an
+    // ancestor of it: every cluster lists its own blocks, and each leaf (on
+    // the threads) copies the lists along its path to the root into its slot
+    // and sorts them there (the indices are distinct, so the sorted slot is
+    // the list order).
+    const int64_t ncl = (int64_t)H.cl.size();
     const int64_t nfar_b = (int64_t)H.far.size(), nnear_b = (int64_t)H.near.size();
-    constexpr int64_t kItemChunks = 32;
-    const int64_t fch = std::max<int64_t>(1, (nfar_b + kItemChunks - 1) / kItemChunks);
-    const int64_t nch = std::max<int64_t>(1, (nnear_b + kItemChunks - 1) / kItemChunks);
-    const int64_t nfc_i = (nfar_b + fch - 1) / fch, nnc_i = (nnear_b + nch - 1) / nch;
-    const int64_t ncks = nfc_i + nnc_i;  // far chunks first, then near chunks
-    std::vector<std::vector<int32_t>> ccount(ncks, std::vector<int32_t>(nleaf, 0));
-    auto chunk_range = [&](int64_t ck, int64_t &b, int64_t &e, bool &is_far) {
-        is_far = ck < nfc_i;
-        if (is_far) {
-            b = ck * fch;
-            e = std::min(nfar_b, b + fch);
+    std::vector<int64_t> parent(ncl, -1), leaf_cl(nleaf, -1);
+    for (int64_t c = 0; c < ncl; ++c) {
+        const Cluster &C = H.cl[c];
+        if (C.left >= 0) {
+            parent[C.left] = c;
+            parent[C.right] = c;
         } else {
-            b = (ck - nfc_i) * nch;
-            e = std::min(nnear_b, b + nch);
+            leaf_cl[leaf_of[C.b]] = c;
         }
-    };
-    auto leaves_of = [&](int64_t idx, bool is_far, int64_t &l0, int64_t &l1) {
-        const int64_t tb = is_far ? H.far[idx].tb : H.near[idx].tb;
-        const int64_t te = is_far ? H.far[idx].te : H.near[idx].te;
-        l0 = leaf_of[tb];
-        l1 = leaf_of[te - 1];
-    };
-    parallel_tasks(ncks, [&](int64_t ck) {
-        int64_t b, e, l0, l1;
-        bool is_far;
-        chunk_range(ck, b, e, is_far);
-        std::vector<int32_t> &c = ccount[ck];
-        for (int64_t x = b; x < e; ++x) {
-            leaves_of(x, is_far, l0, l1);
-            for (int64_t l = l0; l <= l1; ++l) ++c[l];
-        }
+    }
+    // row cluster of every far and near block, then a CSR per cluster
+    std::vector<int32_t, NoInit<int32_t>> tau_far(nfar_b), tau_near(nnear_b);
+    parallel_tasks((nfar_b + 65535) / 65536, [&](int64_t task) {
+        for (int64_t f = task * 65536, fe = std::min(nfar_b, f + 65536); f < fe; ++f)
+            tau_far[f] = (int32_t)H.blocks[H.far_block_id[f]].tau;
     });
+    parallel_tasks((nnear_b + 65535) / 65536, [&](int64_t task) {
+        for (int64_t q = task * 65536, qe = std::min(nnear_b, q + 65536); q < qe; ++q)
+            tau_near[q] = (int32_t)H.blocks[H.near_block_id[q]].tau;
+    });
+    auto cluster_lists = [&](const std::vector<int32_t, NoInit<int32_t>> &tau, std::vector<int64_t> &ptr,
+                             std::vector<int64_t, NoInit<int64_t>> &idx) {
+        const int64_t n = (int64_t)tau.size();
+        ptr.assign(ncl + 1, 0);
+        for (int64_t x = 0; x < n; ++x) ++ptr[tau[x] + 1];
+        for (int64_t c = 0; c < ncl; ++c) ptr[c + 1] += ptr[c];
+        idx.resize(n);
+        std::vector<int64_t> pos(ptr.begin(), ptr.end() - 1);
+        for (int64_t x = 0; x < n; ++x) idx[pos[tau[x]]++] = x;
+    };
+    std::vector<int64_t> cf_ptr, cn_ptr;
+    std::vector<int64_t, NoInit<int64_t>> cf_idx, cn_idx;
+    cluster_lists(tau_far, cf_ptr, cf_idx);
+    cluster_lists(tau_near, cn_ptr, cn_idx);
     trace.mark("items_count");
-    // per leaf: its total, and every chunk's first slot (counts become offsets)
     H.leaf_ptr.assign(nleaf + 1, 0);
-    parallel_tasks((nleaf + 4095) / 4096, [&](int64_t task) {
-        for (int64_t l = task * 4096, le = std::min(nleaf, l + 4096); l < le; ++l) {
-            int32_t run = 0;
-            for (int64_t ck = 0; ck < ncks; ++ck) {
-                const int32_t c = ccount[ck][l];
-                ccount[ck][l] = run;
-                run += c;
+    std::vector<int64_t> leaf_nfar(nleaf);
+    parallel_tasks((nleaf + 1023) / 1024, [&](int64_t task) {
+        for (int64_t l = task * 1024, le = std::min(nleaf, l + 1024); l < le; ++l) {
+            int64_t nf = 0, nn = 0;
+            for (int64_t c = leaf_cl[l]; c >= 0; c = parent[c]) {
+                nf += cf_ptr[c + 1] - cf_ptr[c];
+                nn += cn_ptr[c + 1] - cn_ptr[c];
             }
-            H.leaf_ptr[l + 1] = run;
+            leaf_nfar[l] = nf;
+            H.leaf_ptr[l + 1] = nf + nn;
         }
     });
     for (int64_t l = 0; l < nleaf; ++l) H.leaf_ptr[l + 1] += H.leaf_ptr[l];
     H.leaf_items.resize(H.leaf_ptr[nleaf]);
     trace.mark("items_offsets");
-    parallel_tasks(ncks, [&](int64_t ck) {
-        int64_t b, e, l0, l1;
-        bool is_far;
-        chunk_range(ck, b, e, is_far);
-        std::vector<int32_t> &c = ccount[ck];
-        for (int64_t x = b; x < e; ++x) {
-            leaves_of(x, is_far, l0, l1);
-            for (int64_t l = l0; l <= l1; ++l)
-                H.leaf_items[H.leaf_ptr[l] + c[l]++] = is_far ? x : -1 - x;
+    parallel_tasks((nleaf + 255) / 256, [&](int64_t task) {
+        for (int64_t l = task * 256, le = std::min(nleaf, l + 256); l < le; ++l) {
+            int64_t *const out = H.leaf_items.data() + H.leaf_ptr[l];
+            int64_t *w = out;
+            for (int64_t c = leaf_cl[l]; c >= 0; c = parent[c])
+                w = std::copy(cf_idx.begin() + cf_ptr[c], cf_idx.begin() + cf_ptr[c + 1], w);
+            std::sort(out, w);
+            int64_t *const nb = w;
+            for (int64_t c = leaf_cl[l]; c >= 0; c = parent[c])
+                w = std::copy(cn_idx.begin() + cn_ptr[c], cn_idx.begin() + cn_ptr[c + 1], w);
+            std::sort(nb, w);
+            for (int64_t *x = nb; x < w; ++x) *x = -1 - *x;
         }
     });
     trace.mark("leaf_far_items");
     // near blocks per row leaf, by column start (the columns of one leaf's
-    // blocks are disjoint, so the starts are distinct), for the touching pairs
+    // blocks are disjoint, so the starts are distinct), for the touching
+    // pairs: the near part of each leaf's item list, sorted by column start
     std::vector<int64_t> nptr(nleaf + 1, 0);
-    for (size_t q = 0; q < H.near.size(); ++q)
-        for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l) ++nptr[l + 1];
-    for (int64_t l = 0; l < nleaf; ++l) nptr[l + 1] += nptr[l];
-    std::vector<int64_t> nq(nptr[nleaf]);
-    {
-        std::vector<int64_t> pos(nptr.begin(), nptr.end() - 1);
-        for (size_t q = 0; q < H.near.size(); ++q)
-            for (int64_t l = leaf_of[H.near[q].tb]; l <= leaf_of[H.near[q].te - 1]; ++l)
-                nq[pos[l]++] = (int64_t)q;
-    }
-    std::vector<int64_t> nsb(nq.size());
+    for (int64_t l = 0; l < nleaf; ++l)
+        nptr[l + 1] = nptr[l] + (H.leaf_ptr[l + 1] - H.leaf_ptr[l] - leaf_nfar[l]);
+    std::vector<int64_t, NoInit<int64_t>> nq(nptr[nleaf]), nsb(nptr[nleaf]);
     parallel_tasks((nleaf + 1023) / 1024, [&](int64_t task) {
         for (int64_t l = task * 1024, le = std::min(nleaf, l + 1024); l < le; ++l) {
+            const int64_t *it = H.leaf_items.data() + H.leaf_ptr[l] + leaf_nfar[l];
+            for (int64_t i = nptr[l]; i < nptr[l + 1]; ++i) nq[i] = -1 - *it++;
             std::sort(nq.begin() + nptr[l], nq.begin() + nptr[l + 1],
                       [&](int64_t a, int64_t b) { return H.near[a].sb < H.near[b].sb; });
             for (int64_t i = nptr[l]; i < nptr[l + 1]; ++i) nsb[i] = H.near[nq[i]].sb;
         }
     });
-
     trace.mark("leaf_near_items");
     // singular pairs of the near field, with their place in the dense blocks
     for (int c = 0; c < 3; ++c) {
