@@ -1132,8 +1132,10 @@ namespace {
 // One cluster: its vertex box, and either its leaf order or its split (the
 // median of the centroids along the longest box axis).  Returns the split
 // point, or -1 for a leaf.
-int64_t split_cluster(Cluster &C, std::vector<int32_t> &perm, const std::vector<double> &cen,
-                      const std::vector<double> &tbox, const std::vector<double> &tlen, int leaf)
+int64_t split_cluster(Cluster &C, std::vector<int32_t> &perm,
+                      const std::vector<double, NoInit<double>> &cen,
+                      const std::vector<double, NoInit<double>> &tbox,
+                      const std::vector<double, NoInit<double>> &tlen, int leaf)
 {
     double box[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     double h = 0.0;
@@ -1168,6 +1170,31 @@ int64_t split_cluster(Cluster &C, std::vector<int32_t> &perm, const std::vector<
     return mid;
 }
 
+// Sub-phase timings of the tree build on stderr when BEM_TRACE_TREE is set.
+struct PhaseTrace {
+    bool on;
+    const char *label;
+    double t0, last;
+    std::string text;
+    explicit PhaseTrace(const char *what)
+        : on(std::getenv("BEM_TRACE_TREE") != nullptr), label(what), t0(now_ms()), last(t0)
+    {
+    }
+    void mark(const char *name)
+    {
+        if (!on) return;
+        const double t = now_ms();
+        char buf[96];
+        std::snprintf(buf, sizeof buf, " %s %.2f", name, t - last);
+        text += buf;
+        last = t;
+    }
+    ~PhaseTrace()
+    {
+        if (on) std::fprintf(stderr, "tree %s (ms):%s; total %.2f\n", label, text.c_str(), now_ms() - t0);
+    }
+};
+
 // The tree is grown breadth-first until there are enough clusters to keep
 // the host threads busy; the subtrees below that frontier are grown on the
 // threads (each in its own list, depth-first) and appended in frontier order.
@@ -1176,9 +1203,10 @@ int64_t split_cluster(Cluster &C, std::vector<int32_t> &perm, const std::vector<
 // numbering below the frontier differs.
 void build_clusters(bem_hmat_s &H)
 {
+    PhaseTrace trace("clusters");
     const bem_mesh_s &M = *H.mesh;
     const int64_t nt = M.nt;
-    std::vector<double> cen(3 * nt), tbox(6 * nt), tlen(nt);
+    std::vector<double, NoInit<double>> cen(3 * nt), tbox(6 * nt), tlen(nt);
     parallel_tasks((nt + 16383) / 16384, [&](int64_t task) {
         for (int64_t t = task * 16384, te = std::min(nt, t + 16384); t < te; ++t) {
             // longest edge (squared lengths compared, one square root)
@@ -1200,6 +1228,7 @@ void build_clusters(bem_hmat_s &H)
             }
         }
     });
+    trace.mark("triangles");
     H.perm.resize(nt);
     std::iota(H.perm.begin(), H.perm.end(), 0);
     H.cl.clear();
@@ -1234,6 +1263,7 @@ void build_clusters(bem_hmat_s &H)
         for (size_t q = head; q < H.cl.size(); ++q) any_split |= H.cl[q].e - H.cl[q].b > H.leaf;
         if (!any_split) break;
     }
+    trace.mark("top_levels");
     // subtrees of the frontier clusters, one task each (disjoint perm ranges)
     const size_t nfront = H.cl.size() - head;
     std::vector<std::vector<Cluster>> sub(nfront);
@@ -1254,6 +1284,7 @@ void build_clusters(bem_hmat_s &H)
             }
         }
     });
+    trace.mark("subtrees");
     // the frontier cluster keeps its index; its descendants follow in order
     for (size_t f = 0; f < nfront; ++f) {
         const int64_t base = (int64_t)H.cl.size() - 1;   // local index 1 -> base + 1
@@ -1270,8 +1301,12 @@ void build_clusters(bem_hmat_s &H)
             H.cl.push_back(C);
         }
     }
+    trace.mark("join");
     H.iperm.resize(nt);
-    for (int64_t p = 0; p < nt; ++p) H.iperm[H.perm[p]] = (int32_t)p;
+    parallel_tasks((nt + 65535) / 65536, [&](int64_t task) {
+        for (int64_t p = task * 65536, pe = std::min(nt, p + 65536); p < pe; ++p)
+            H.iperm[H.perm[p]] = (int32_t)p;
+    });
 }
 
 // Admissibility (Sec. 2.1): disjoint boxes and min(diam) <= eta * dist.
@@ -1390,30 +1425,10 @@ void build_blocks(bem_hmat_s &H)
 // side (CTA, warp, lane ACA), each in longest-processing-time-first order
 // (m + n descending, tree order on ties); the order comes from one sort of
 // packed 64-bit keys so that each FarBlock is written once.
-// Sub-phase timings of build_lists on stderr when BEM_TRACE_TREE is set.
-struct PhaseTrace {
-    bool on;
-    double t0, last;
-    std::string text;
-    PhaseTrace() : on(std::getenv("BEM_TRACE_TREE") != nullptr), t0(now_ms()), last(t0) {}
-    void mark(const char *name)
-    {
-        if (!on) return;
-        const double t = now_ms();
-        char buf[96];
-        std::snprintf(buf, sizeof buf, " %s %.2f", name, t - last);
-        text += buf;
-        last = t;
-    }
-    ~PhaseTrace()
-    {
-        if (on) std::fprintf(stderr, "tree lists (ms):%s; total %.2f\n", text.c_str(), now_ms() - t0);
-    }
-};
 
 void build_lists(bem_hmat_s &H)
 {
-    PhaseTrace trace;
+    PhaseTrace trace("lists");
     const bem_mesh_s &M = *H.mesh;
     const int64_t nb = (int64_t)H.blocks.size(), nt = M.nt;
     if (nb >= (int64_t(1) << 32) || nt >= (int64_t(1) << 29))
