@@ -132,3 +132,13 @@ def test_hmatrix_blocks_use_their_class_rule(l3, op):
         if len(seen) == 3:
             break
     assert seen == {oracle.RULE6, oracle.RULE3, oracle.RULE1}
+
+
+def test_classes_are_p0_only(l3):
+    """The distance classes are defined for P0 (the library's DP1 and P1
+    handles keep the 6-point rule); the oracle refuses them elsewhere."""
+    V, T = l3
+    with pytest.raises(ValueError):
+        oracle.hmat_assemble(V, T, oracle.SLP, 0.0, 32, 1.2, 1e-4, space=oracle.DP1, rho3=5.0)
+    hm = oracle.hmat_assemble(V, T, oracle.SLP, 0.0, 32, 1.2, 1e-4, block_ids=[0])
+    assert np.all(hm.rules == oracle.RULE6)
