@@ -115,7 +115,8 @@ int bem_get_tuning(bem_tuning *t);
  * operators (k = 0) on P0 handles.  The Helmholtz entries (whose lower-order
  * error is set by k h, not by the distance), the FP64 assembly (the plain
  * form), the near field and the piecewise linear spaces keep the 6-point
- * rule.  BEM_E_ARG for negative or non-finite thresholds. */
+ * rule.  q is copied (set) or filled (get); BEM_E_ARG for a null pointer or
+ * negative or non-finite thresholds, which leave the setting unchanged. */
 typedef struct {
     double rho3;
     double rho1;
@@ -325,8 +326,11 @@ int hmat_blocks(bem_hmat hmat, int64_t *blocks, int64_t cap, int64_t *n_blocks, 
 int hmat_block_dense(bem_hmat hmat, int64_t block, void *out, int32_t *rank);
 
 /* Points per triangle of the regular rule of every block (tree order, as in
- * hmat_blocks): 6, 3 or 1 for admissible blocks (bem_set_quadrature), 0 for
- * near-field blocks.  points: host, capacity cap >= number of blocks. */
+ * hmat_blocks): 6, 3 or 1 for admissible blocks (the distance classes of
+ * bem_set_quadrature at tree build; 6 = the 6-point rule of Sec. 3.2.1), 0
+ * for near-field blocks.  points: caller-owned host array, capacity cap >=
+ * the number of blocks (hmat_blocks gives it).  BEM_E_ARG for a null handle
+ * or array, or too small a capacity.  Needs no assembly and no device. */
 int hmat_block_rules(bem_hmat hmat, int32_t *points, int64_t cap);
 
 /* Frees the handle and its device memory. */
