@@ -284,9 +284,9 @@ QuadRule make_rule6()
             R.t[k] = bary[m][2];
             R.w[k] = ow[o];
             R.wf[k] = (float)ow[o];
-            for (int a = 0; a < 3; ++a) {
-                R.wl[k][a] = ow[o] * bary[m][a];
-                R.wlf[k][a] = (float)R.wl[k][a];
+            for (int v = 0; v < 3; ++v) {
+                R.wl[k][v] = ow[o] * bary[m][v];
+                R.wlf[k][v] = (float)R.wl[k][v];
             }
         }
     }
@@ -1041,7 +1041,7 @@ int bem_entries_dp1(bem_mesh mesh, int32_t op, double k, int32_t prec, const int
 struct Cluster {
     int64_t b, e, left, right;
     double box[6];
-    double h;       // longest edge of any of its triangles
+    double h = 0.0;  // longest edge of any of its triangles
 };
 
 struct BlockH {
@@ -1645,11 +1645,11 @@ void build_lists(bem_hmat_s &H)
             for (int64_t c = leaf_cl[l]; c >= 0; c = parent[c])
                 w = std::copy(cf_idx.begin() + cf_ptr[c], cf_idx.begin() + cf_ptr[c + 1], w);
             std::sort(out, w);
-            int64_t *const nb = w;
+            int64_t *const near0 = w;
             for (int64_t c = leaf_cl[l]; c >= 0; c = parent[c])
                 w = std::copy(cn_idx.begin() + cn_ptr[c], cn_idx.begin() + cn_ptr[c + 1], w);
-            std::sort(nb, w);
-            for (int64_t *x = nb; x < w; ++x) *x = -1 - *x;
+            std::sort(near0, w);
+            for (int64_t *x = near0; x < w; ++x) *x = -1 - *x;
         }
     });
     trace.mark("leaf_far_items");
