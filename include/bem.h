@@ -80,6 +80,22 @@ int bem_version(void);
  * devices, all handles); a monotone counter for launch accounting. */
 int64_t bem_kernel_launches(void);
 
+/* Bytes of the library's stream-ordered device memory pool on the current
+ * device: *reserved = memory the pool holds from the driver, *used = memory
+ * handed out and not yet freed.  Either pointer may be null.  The pool backs
+ * every device buffer of meshes, trees and assemblies, so the two numbers
+ * show whether a call allocated. */
+int bem_memory_usage(int64_t *reserved, int64_t *used);
+
+/* Diagnostic of the FP64 reciprocal that scales every ACA pivot (Eq. (7):
+ * v_k = v~_k / (v~_k)_{j_k}): y[i] = 1 / x[i] computed on the device by the
+ * routine the ACA kernels use (Newton-Raphson from a single-precision seed,
+ * correct to rounding level; IEEE division outside the seed's exponent
+ * range).  x, y: device arrays of n doubles on the current device (y may
+ * alias x); x[i] finite and nonzero.  Returns after the stream is
+ * synchronised. */
+int bem_debug_recip(const double *x, double *y, int64_t n, void *cuda_stream);
+
 /* Process-wide tuning, read when a tree is built (row thresholds) and when
  * an H-matrix is assembled (graphs).  The numerical results do not depend on
  * it (up to ACA pivot near-ties, which rounding decides).
@@ -163,7 +179,9 @@ int64_t bem_mesh_size(bem_mesh mesh);
  * return BEM_E_ARG at its next synchronisation (the call then waits for the
  * stream).  test_ids, trial_ids and out may each be host or device memory.
  * prec: BEM_FP64 or BEM_MIXED (regular pairs only; singular pairs are FP64).
- * Allocates stream-ordered device scratch for the list of singular pairs.
+ * Allocates stream-ordered device scratch for the list of singular pairs
+ * (sized by n_test times the most triangles touching one triangle; repeated
+ * trial ids that hold more touching pairs make a second, exactly sized pass).
  * Returns after the stream is synchronised. */
 int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t *test_ids,
                 int64_t n_test, const int32_t *trial_ids, int64_t n_trial, void *out,
@@ -179,12 +197,16 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
  *    allocating library routine.  The list of singular pairs lives in one
  *    file-scope device array of the library, 12 MiB plus counters, which
  *    every GPU that loads the library holds until the process exits.
- *  - test_ids, trial_ids and out must be device memory on the mesh's device,
- *    which must be current (BEM_E_ARG / BEM_E_STATE otherwise).
+ *  - test_ids, trial_ids and out must be device (or managed) memory of the
+ *    mesh's device, which must be current (BEM_E_ARG for host memory or
+ *    memory of another device, BEM_E_STATE for another current device).
  *  - Maximum size: the request may hold at most 262,144 singular pairs of
  *    each kind, counted as min(n_test * n_trial, n_test * T) with T the
  *    largest number of triangles that touch one triangle; larger requests
- *    return BEM_E_ARG without launching anything (use bem_entries).
+ *    return BEM_E_ARG without launching anything (use bem_entries).  Repeated
+ *    trial ids can hold more touching pairs than that count: if they exceed
+ *    the capacity, the call returns BEM_E_ARG after its launches and `out`
+ *    is undefined.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.
@@ -306,6 +328,9 @@ typedef struct {
     int64_t n_blocks_rule1;
     double rho3;                 /* the thresholds the tree was built with */
     double rho1;
+    int64_t n_blocks_cta;        /* admissible blocks by ACA work shape (bem_tuning at tree   */
+    int64_t n_blocks_warp;       /* build): a whole CTA per block, warps (a warp holds one or */
+    int64_t n_blocks_lane;       /* several blocks), one lane per block                       */
 } bem_hmat_stats;
 
 /* Copies statistics of the handle into *out. */

@@ -52,7 +52,9 @@ class HmatStats(ctypes.Structure):
                 ("time_tree_lists_ms", ctypes.c_double), ("time_tree_upload_ms", ctypes.c_double),
                 ("factor_read_bytes", ctypes.c_int64),
                 ("n_blocks_rule3", ctypes.c_int64), ("n_blocks_rule1", ctypes.c_int64),
-                ("rho3", ctypes.c_double), ("rho1", ctypes.c_double)]
+                ("rho3", ctypes.c_double), ("rho1", ctypes.c_double),
+                ("n_blocks_cta", ctypes.c_int64), ("n_blocks_warp", ctypes.c_int64),
+                ("n_blocks_lane", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
@@ -110,6 +112,8 @@ def load(path: str = LIB_PATH):
         sig = {
             "bem_version": ([], ctypes.c_int),
             "bem_kernel_launches": ([], ctypes.c_int64),
+            "bem_memory_usage": ([P, P], ctypes.c_int),
+            "bem_debug_recip": ([P, P, i64, P], ctypes.c_int),
             "bem_set_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
             "bem_get_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
             "bem_set_quadrature": ([ctypes.POINTER(Quadrature)], ctypes.c_int),
@@ -192,6 +196,20 @@ def bem_version() -> int:
 
 def bem_kernel_launches() -> int:
     return int(load().bem_kernel_launches())
+
+
+def bem_memory_usage() -> dict:
+    r, u = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().bem_memory_usage(ctypes.byref(r), ctypes.byref(u)))
+    return {"reserved": r.value, "used": u.value}
+
+
+def bem_debug_recip(x, y, stream=None):
+    """y = 1 / x on the device by the ACA pivot reciprocal; x, y device
+    tensors of float64 (same length)."""
+    n = x.numel()
+    assert y.numel() == n
+    _check(load().bem_debug_recip(_ptr(x)[0], _ptr(y)[0], n, _stream(stream)))
 
 
 def bem_set_tuning(warp_max_rows: int, lane_max_rows: int, use_graphs: int = 1):

@@ -174,9 +174,13 @@ cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int o
                                    SingPair *lists[3], unsigned long long *counts,
                                    unsigned long long cap, int *err, cudaStream_t st);
 
+// Touching pairs of each case: min(dev_counts[c], host_counts[c]) pairs
+// (dev_counts may be null); grid_counts[c], if given, sizes the grid instead
+// of host_counts[c] (the threads stride over every pair either way).
 cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k,
                             const SingPair *pairs[3], const unsigned long long *dev_counts,
-                            const int64_t host_counts[3], void *out, cudaStream_t st);
+                            const int64_t host_counts[3], void *out, cudaStream_t st,
+                            const int64_t *grid_counts = nullptr);
 
 cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                                 const NearBlock *blocks, int64_t nblocks, void *out,
@@ -223,6 +227,9 @@ cudaError_t launch_aca_dp1(const DevGeom &g, const QuadRule &rule, int op, doubl
                            int64_t n_small, int64_t max_m_big, int64_t max_m_small,
                            void *pool_data, Pool *pool, AcaQueue *queue, int num_sms,
                            cudaStream_t st);
+
+// y[i] = 1 / x[i] by the ACA's pivot reciprocal (diagnostic)
+cudaError_t launch_debug_recip(const double *x, double *y, int64_t n, cudaStream_t st);
 
 // After an ACA launch: toff[b] = sum of ranks of blocks < b (toff[n] = total)
 // and the totals in *st.  tile_sums needs aca_finish_tiles(n) entries.

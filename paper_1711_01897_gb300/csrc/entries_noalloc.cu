@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 
 #include "../../include/bem.h"
@@ -43,14 +44,18 @@ cudaError_t scratch_address(int device, unsigned char **out)
     return cudaSuccess;
 }
 
-bool on_device(const void *p)
+// True if p is device memory of `device` (or managed memory, which every
+// device can reach).  Device memory of another GPU is refused: without peer
+// access the kernels would fault on it.
+bool on_device(const void *p, int device)
 {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 int err(int code, const std::string &msg)
@@ -64,10 +69,11 @@ int err(int code, const std::string &msg)
 
 using namespace bem;
 
-extern "C" int bem_entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec,
-                                   const int32_t *test_ids, int64_t n_test,
-                                   const int32_t *trial_ids, int64_t n_trial, void *out,
-                                   void *cuda_stream)
+namespace {
+
+int entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t *test_ids,
+                    int64_t n_test, const int32_t *trial_ids, int64_t n_trial, void *out,
+                    void *cuda_stream)
 {
     set_last_error("");
     MeshView M;
@@ -81,8 +87,8 @@ extern "C" int bem_entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != M.device)
         return err(BEM_E_STATE, "the mesh's device must be the current device");
-    if (!on_device(test_ids) || !on_device(trial_ids) || !on_device(out))
-        return err(BEM_E_ARG, "bem_entries_noalloc takes device pointers only");
+    if (!on_device(test_ids, dev) || !on_device(trial_ids, dev) || !on_device(out, dev))
+        return err(BEM_E_ARG, "bem_entries_noalloc takes device pointers on the mesh's device only");
     const int64_t need = std::min<int64_t>(n_test * n_trial,
                                            n_test * std::max<int64_t>(M.max_touch, 1));
     if (need > kNoAllocPairs)
@@ -108,12 +114,39 @@ extern "C" int bem_entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t 
         e = launch_entries_regular(M.g, rule, op, k, prec, test_ids, n_test, trial_ids, n_trial,
                                    out, lists, counts, (unsigned long long)kNoAllocPairs, eflag, st);
     const SingPair *cl[3] = {lists[0], lists[1], lists[2]};
+    // the device counts, capped at the lists' capacity, say how many pairs
+    // there are; the host bound `need` only sizes the grids
     int64_t hc[3] = {kNoAllocPairs, kNoAllocPairs, kNoAllocPairs};
-    if (e == cudaSuccess) e = launch_singular(M.g, sing, op, k, cl, counts, hc, out, st);
+    int64_t gc[3] = {need, need, need};
+    if (e == cudaSuccess) e = launch_singular(M.g, sing, op, k, cl, counts, hc, out, st, gc);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, eflag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return err(BEM_E_CUDA, std::string("bem_entries_noalloc: ") + cudaGetErrorString(e));
     if (herr == 1) return err(BEM_E_ARG, "triangle id out of range");
-    if (herr == 2) return err(BEM_E_CUDA, "singular pair list overflow");
+    // repeated trial ids can make more touching pairs than the bound above
+    // counts; the lists stopped at their capacity and `out` is undefined
+    if (herr == 2)
+        return err(BEM_E_ARG, "request holds more than " + std::to_string(kNoAllocPairs) +
+                                  " singular pairs of one kind (repeated ids); the allocation-free "
+                                  "scratch is full (use bem_entries)");
     return BEM_OK;
+}
+
+}  // namespace
+
+extern "C" int bem_entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec,
+                                   const int32_t *test_ids, int64_t n_test,
+                                   const int32_t *trial_ids, int64_t n_trial, void *out,
+                                   void *cuda_stream)
+{
+    // no exception may cross the C boundary (std::map and std::string can
+    // throw on host allocation failure)
+    try {
+        return entries_noalloc(mesh, op, k, prec, test_ids, n_test, trial_ids, n_trial, out,
+                               cuda_stream);
+    } catch (const std::bad_alloc &) {
+        return err(BEM_E_OOM, "host allocation failed");
+    } catch (...) {
+        return err(BEM_E_CUDA, "bem_entries_noalloc: unexpected exception");
+    }
 }

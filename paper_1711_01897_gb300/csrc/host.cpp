@@ -744,6 +744,32 @@ int bem_version(void) { return 100; }
 
 int64_t bem_kernel_launches(void) { return launches_total(); }
 
+int bem_memory_usage(int64_t *reserved, int64_t *used)
+{
+    return guarded([&]() -> int {
+        cudaMemPool_t pool = lib_pool();
+        uint64_t r = 0, u = 0;
+        CU(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r));
+        CU(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+        if (reserved) *reserved = (int64_t)r;
+        if (used) *used = (int64_t)u;
+        return BEM_OK;
+    });
+}
+
+int bem_debug_recip(const double *x, double *y, int64_t n, void *cuda_stream)
+{
+    return guarded([&]() -> int {
+        if (n < 0) return fail(BEM_E_ARG, "negative size");
+        if (n == 0) return BEM_OK;
+        if (!x || !y) return fail(BEM_E_ARG, "null array");
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        CU(launch_debug_recip(x, y, n, st));
+        CU(cudaStreamSynchronize(st));
+        return BEM_OK;
+    });
+}
+
 int bem_set_tuning(const bem_tuning *t)
 {
     if (!t || t->warp_max_rows < 1 || t->warp_max_rows > aca_small_cap() || t->lane_max_rows < 0 ||
@@ -921,34 +947,47 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
             sto.alloc(nout * esz, st);
             dout = sto.p;
         }
-        // scratch: singular pair lists (one per case), counters, error flag
+        // scratch: singular pair lists (one per case), counters, error flag.
+        // The bound counts n_test * (most triangles touching one triangle);
+        // repeated trial ids can exceed it, and then the counters (which keep
+        // counting past the capacity) size a second pass
         unsigned long long cap =
             (unsigned long long)std::min<int64_t>(nout, n_test * std::max<int64_t>(mesh->max_touch, 1));
-        size_t list_bytes = cap * sizeof(SingPair);
-        size_t scratch = 3 * list_bytes + 64;
-        void *ws = nullptr;
-        CU(lib_malloc_async(&ws, scratch, st));
-        unsigned char *wb = (unsigned char *)ws;
-        SingPair *lists[3] = {(SingPair *)wb, (SingPair *)(wb + list_bytes),
-                              (SingPair *)(wb + 2 * list_bytes)};
-        unsigned long long *counts = (unsigned long long *)(wb + 3 * list_bytes);
-        int *err = (int *)(counts + 3);
-        cudaError_t e = cudaMemsetAsync(counts, 0, 64, st);
-        if (e == cudaSuccess)
-            e = launch_entries_regular(mesh->geom.g, D.rule, op, k, prec, dti, n_test, dtj,
-                                       n_trial, dout, lists, counts, cap, err, st);
-        const SingPair *cl[3] = {lists[0], lists[1], lists[2]};
-        int64_t hc[3] = {(int64_t)cap, (int64_t)cap, (int64_t)cap};
-        if (e == cudaSuccess) e = launch_singular(mesh->geom.g, D.sing, op, k, cl, counts, hc, dout, st);
         int herr = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && host_out)
-            e = cudaMemcpyAsync(out, dout, nout * esz, cudaMemcpyDeviceToHost, st);
-        cudaFreeAsync(ws, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            g_err = std::string("bem_entries: ") + cudaGetErrorString(e);
-            return e == cudaErrorMemoryAllocation ? BEM_E_OOM : BEM_E_CUDA;
+        for (int pass = 0; pass < 2; ++pass) {
+            size_t list_bytes = cap * sizeof(SingPair);
+            size_t scratch = 3 * list_bytes + 64;
+            void *ws = nullptr;
+            CU(lib_malloc_async(&ws, scratch, st));
+            unsigned char *wb = (unsigned char *)ws;
+            SingPair *lists[3] = {(SingPair *)wb, (SingPair *)(wb + list_bytes),
+                                  (SingPair *)(wb + 2 * list_bytes)};
+            unsigned long long *counts = (unsigned long long *)(wb + 3 * list_bytes);
+            int *err = (int *)(counts + 3);
+            unsigned long long hcount[3] = {0, 0, 0};
+            cudaError_t e = cudaMemsetAsync(counts, 0, 64, st);
+            if (e == cudaSuccess)
+                e = launch_entries_regular(mesh->geom.g, D.rule, op, k, prec, dti, n_test, dtj,
+                                           n_trial, dout, lists, counts, cap, err, st);
+            const SingPair *cl[3] = {lists[0], lists[1], lists[2]};
+            int64_t hc[3] = {(int64_t)cap, (int64_t)cap, (int64_t)cap};
+            if (e == cudaSuccess) e = launch_singular(mesh->geom.g, D.sing, op, k, cl, counts, hc, dout, st);
+            herr = 0;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hcount, counts, sizeof(hcount), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            cudaFreeAsync(ws, st);
+            if (e != cudaSuccess) {
+                g_err = std::string("bem_entries: ") + cudaGetErrorString(e);
+                return e == cudaErrorMemoryAllocation ? BEM_E_OOM : BEM_E_CUDA;
+            }
+            if (herr != 2) break;
+            cap = std::max({hcount[0], hcount[1], hcount[2]});
+        }
+        if (herr == 0 && host_out) {
+            CU(cudaMemcpyAsync(out, dout, nout * esz, cudaMemcpyDeviceToHost, st));
+            CU(cudaStreamSynchronize(st));
         }
         if (herr == 1) return fail(BEM_E_ARG, "triangle id out of range");
         if (herr == 2) return fail(BEM_E_CUDA, "singular pair list overflow");
@@ -2193,6 +2232,9 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         }
         s.rho3 = H->rho3;
         s.rho1 = H->rho1;
+        s.n_blocks_cta = H->n_big;
+        s.n_blocks_warp = H->n_small;
+        s.n_blocks_lane = H->n_tiny;
         s.near_entries = H->near_total;
         for (int c = 0; c < 3; ++c) s.singular_pairs[c] = (int64_t)H->sing[c].size();
         s.far_entries = H->far_entries;

@@ -12,12 +12,31 @@
 // vanishes if its maximum is 0 or <= 1e-14 * the largest pivot so far, and
 // then the smallest unused row is next; stop once ||u_k|| ||v_k|| <= eps
 // ||S_k||_F, or k = min(m, n), or all rows used, or k = KMAX (rank cap).
+#include <algorithm>
+
 #include "aca_kernel.cuh"
 
 namespace bem {
 
 namespace {
 }  // namespace
+
+namespace {
+__global__ void k_debug_recip(const double *__restrict__ x, double *__restrict__ y, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = recip(x[i]);
+}
+}  // namespace
+
+cudaError_t launch_debug_recip(const double *x, double *y, int64_t n, cudaStream_t st)
+{
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    k_debug_recip<<<(unsigned)blocks, 256, 0, st>>>(x, y, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 int aca_small_cap() { return kSmallCap; }
 int aca_tiny_max() { return kTinyMax; }

@@ -675,10 +675,12 @@ cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int o
 
 template <int CASE, int OP, bool CPLX>
 static void singular_launch(const DevGeom &g, const SingTable &tab, double k, const SingPair *p,
-                            const unsigned long long *dc, int64_t hc, void *out, cudaStream_t st)
+                            const unsigned long long *dc, int64_t hc, int64_t gc, void *out,
+                            cudaStream_t st)
 {
-    if (hc <= 0) return;
-    int64_t want = (hc + kSingThreads - 1) / kSingThreads;
+    if (hc <= 0 || gc <= 0) return;
+    // the grid covers gc pairs; its threads stride over all min(*dc, hc)
+    int64_t want = (gc + kSingThreads - 1) / kSingThreads;
     int64_t cap = (int64_t)num_sms_cached() * 16;
     unsigned grid = (unsigned)(want < cap ? want : cap);
     k_singular<CASE, OP, CPLX><<<grid, kSingThreads, 0, st>>>(g, tab, k, p, dc, hc, out);
@@ -687,19 +689,21 @@ static void singular_launch(const DevGeom &g, const SingTable &tab, double k, co
 
 cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k,
                             const SingPair *pairs[3], const unsigned long long *dev_counts,
-                            const int64_t host_counts[3], void *out, cudaStream_t st)
+                            const int64_t host_counts[3], void *out, cudaStream_t st,
+                            const int64_t *grid_counts)
 {
     const bool cplx = k != 0.0;
     for (int c = 1; c <= 3; ++c) {
         const unsigned long long *dc = dev_counts ? dev_counts + (c - 1) : nullptr;
         const SingTable &T = tabs[c - 1];
         int64_t hc = host_counts[c - 1];
+        int64_t gc = grid_counts ? grid_counts[c - 1] : hc;
         const SingPair *P = pairs[c - 1];
         BEM_DISPATCH(op, cplx, 0, ({
                          (void)PREC;
-                         if (c == 1) singular_launch<1, OP, CPLX>(g, T, k, P, dc, hc, out, st);
-                         else if (c == 2) singular_launch<2, OP, CPLX>(g, T, k, P, dc, hc, out, st);
-                         else singular_launch<3, OP, CPLX>(g, T, k, P, dc, hc, out, st);
+                         if (c == 1) singular_launch<1, OP, CPLX>(g, T, k, P, dc, hc, gc, out, st);
+                         else if (c == 2) singular_launch<2, OP, CPLX>(g, T, k, P, dc, hc, gc, out, st);
+                         else singular_launch<3, OP, CPLX>(g, T, k, P, dc, hc, gc, out, st);
                      }));
     }
     return cudaGetLastError();
