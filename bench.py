@@ -157,10 +157,11 @@ def measured_peaks():
 QUAD_FP32_PER_EVAL = {0: 7, 1: 12}
 
 
-def quadrature_roofline(bem, mesh, V, T, dev, stream, flush, reps: int = 3):
+def quadrature_roofline(bem, mesh, V, T, dev, stream, flush, reps: int = 3, peaks=None):
     """A3 alone: one bem_entries call over two opposite caps of the sphere
     (every pair regular and well separated), timed with CUDA events on the
-    launching stream, against the FP32 and MUFU pipe peaks."""
+    launching stream, against the FP32 and MUFU pipe peaks (measured on the
+    box by bem_measure_peaks when given, else derived from unit counts)."""
     import torch
     cen = V[T].mean(axis=1)
     test = np.nonzero(cen[:, 2] > 0.5)[0].astype(np.int32)
@@ -169,9 +170,14 @@ def quadrature_roofline(bem, mesh, V, T, dev, stream, flush, reps: int = 3):
     tj = torch.from_numpy(trial).to(dev)
     out = torch.empty(len(test) * len(trial), dtype=torch.float64, device=dev)
     ents = float(len(test)) * len(trial)
-    f_fp32 = N_SM * FP32_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9   # Gop/s
-    f_mufu = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+    f_fp32_d = N_SM * FP32_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9   # Gop/s
+    f_mufu_d = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+    f_fp32 = peaks["fp32_fma_per_s"] / 1e9 if peaks else f_fp32_d
+    f_mufu = peaks["mufu_rsqrt_per_s"] / 1e9 if peaks else f_mufu_d
     res = {"kernel": "k_entries (bem_entries, mixed precision, regular far pairs)",
+           "peak_source": ("measured on this box (bem_measure_peaks: FFMA and MUFU rsqrt "
+                           "throughput kernels)" if peaks else "derived from unit counts"),
+           "peaks_derived_gops": {"fp32": f_fp32_d, "mufu": f_mufu_d},
            "entries_per_launch": ents, "evals_per_entry": 36,
            "timing": "CUDA events around one bem_entries call (one k_entries launch, "
                      "3 empty singular launches); L2 flushed before each"}
@@ -305,23 +311,47 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
 
-    # independent problems per rank: same workload, rank-dependent jitter seed
+    # one problem (the workload's mesh); with N ranks each assembles and
+    # applies the block rows of its part of a cost-balanced row partition
+    # (hmat_build_tree_part), gathering x and the rows of y with all_gathers
+    # (no reduction)
     V, T = meshes.icosphere_level(args.level)
-    V = meshes.jitter(V, T, 0.05, rank_jitter_seed(rank))
+    V = meshes.jitter(V, T, 0.05, rank_jitter_seed(0))
     n = T.shape[0]
     mesh = bem.Mesh(V, T)
-    hs = {op: bem.HMatrix(mesh, LEAF, ETA) for op in (bem.SLP, bem.DLP)}
-    rng = np.random.default_rng(5 + rank)
+    hs = {op: bem.HMatrix(mesh, LEAF, ETA, parts=ws, part=rank) for op in (bem.SLP, bem.DLP)}
+    rng = np.random.default_rng(5)
     x_host = rng.normal(size=n)
     x = torch.from_numpy(x_host).to(dev)
     ys = {op: torch.zeros(n, dtype=torch.float64, device=dev) for op in hs}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    if ws > 1:
+        from paper_1711_01897_gb300 import sharding
+        _, perm_np = hs[bem.SLP].blocks()
+        perm_t = torch.from_numpy(perm_np.astype(np.int64)).to(dev)
+        rb, re = hs[bem.SLP].part_rows()
+        rows = torch.tensor([rb, re], dtype=torch.int64, device=dev)
+        allr = [torch.empty_like(rows) for _ in range(ws)]
+        dist.all_gather(allr, rows)
+        bounds = [int(r[0]) for r in allr] + [int(allr[-1][1])]
+        x_seg = x[perm_t][rb:re].contiguous()     # this rank's rows of x
+
+    def product(op, h):
+        if ws == 1:
+            bem.hmat_matvec(h.handle, x, ys[op], 1, sptr)
+            return
+        xc = sharding.gather_segments(x_seg, bounds, dist)
+        xf = torch.empty_like(xc)
+        xf[perm_t] = xc
+        bem.hmat_matvec(h.handle, xf, ys[op], 1, sptr)
+        yc = sharding.gather_segments(ys[op][perm_t][rb:re].contiguous(), bounds, dist)
+        ys[op][perm_t] = yc
 
     def step(prec):
         ent = 0
         for op, h in hs.items():
             bem.hmat_assemble(h.handle, op, 0.0, EPS, prec, sptr)
-            bem.hmat_matvec(h.handle, x, ys[op], 1, sptr)
+            product(op, h)
         for op, h in hs.items():
             st = h.stats()
             ent += st["near_entries"] + st["far_entries"]
@@ -449,7 +479,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         m2 = bem.Mesh(V, T)
         t1 = time.perf_counter()
-        h2 = bem.HMatrix(m2, LEAF, ETA)
+        h2 = bem.HMatrix(m2, LEAF, ETA, parts=ws, part=rank)
         t2 = time.perf_counter()
         ent2 = 0
         for op in (bem.SLP, bem.DLP):
@@ -470,7 +500,11 @@ def run_gpu(args):
                       "tree_blocks_ms": s2["time_tree_blocks_ms"],
                       "tree_lists_ms": s2["time_tree_lists_ms"],
                       "tree_upload_ms": s2["time_tree_upload_ms"]})
-    e2e_val = ent2 / (np.median(e2e_ms) * 1e-3) * ws
+    if ws > 1:
+        e2e_t, e2e_ents = reduce_over_ranks(float(np.median(e2e_ms)), ent2, dist, dev)
+        e2e_val = e2e_ents / (e2e_t * 1e-3)
+    else:
+        e2e_val = ent2 / (np.median(e2e_ms) * 1e-3)
     e2e_parts = parts[int(np.argsort(e2e_ms)[len(e2e_ms) // 2])]
 
     # roofline of the dominant kernel (device time share over the timed steps)
@@ -481,8 +515,12 @@ def run_gpu(args):
     near_reg = st_slp["near_entries"] + st_dlp["near_entries"] - sum(sing)
     per_step = {k: v / steps for k, v in phase.items()}
     dom = max(per_step, key=per_step.get)
-    fp64_peak = N_SM * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9          # Gop/s
-    mufu_peak = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9          # Gop/s
+    fp64_peak_d = N_SM * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9        # Gop/s
+    mufu_peak_d = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9        # Gop/s
+    # measured on this machine by the library's calibration kernels
+    peaks = bem.bem_measure_peaks(sptr)
+    fp64_peak = peaks["fp64_fma_per_s"] / 1e9
+    mufu_peak = peaks["mufu_rsqrt_per_s"] / 1e9
     if dom == "aca":
         # algorithmic FP64 work of the ACA: rank^2 (m+n) multiply-adds per block
         # (residual updates + norm terms) plus one addition per widened entry
@@ -509,11 +547,14 @@ def run_gpu(args):
         roof = {"kernel": "k_singular (Sauter-Schwab, FP64)", "bound": "alu", "pipe": "FP64",
                 "achieved": achieved, "peak": fp64_peak, "unit": "Gop/s",
                 "frac": achieved / fp64_peak, "traffic": None}
-    roof["peak_source"] = ("derived: 152 SMs x per-SM unit rate (FP64 2/clk, MUFU 16/clk) x 2070 MHz "
-                           "max SM clock; MEASURED_PEAKS.json holds no ALU peak")
+    roof["peak_source"] = ("measured on this box (bem_measure_peaks: DFMA and MUFU rsqrt throughput "
+                           "kernels, best of three launches); MEASURED_PEAKS.json holds no ALU peak")
+    roof["peaks_derived_gops"] = {"fp64": fp64_peak_d, "mufu": mufu_peak_d,
+                                  "how": "152 SMs x per-SM unit rate (FP64 2/clk, MUFU 16/clk) "
+                                         "x 2070 MHz max SM clock"}
     roof["phase_ms_per_step"] = per_step
 
-    quad = quadrature_roofline(bem, mesh, V, T, dev, stream, flush)
+    quad = quadrature_roofline(bem, mesh, V, T, dev, stream, flush, peaks=peaks)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -523,11 +564,29 @@ def run_gpu(args):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle", "sample": sample,
                "one_thread": {"value": rate1, "unit": UNIT, "cores": 1, "sample": sample1}}
 
+    extras = {}
+    if ws == 1:
+        # the remaining parts of the metric on this GPU, after the C2 step's
+        # buffers are released: serving latency (a short stream) and the
+        # largest single-GPU configuration (level 9, 100 products)
+        for h in hs.values():
+            h.close()
+        mesh.close()
+        del x, ys, flush
+        torch.cuda.empty_cache()
+        if args.serving_requests > 0:
+            extras["serving"] = serving_record(args, args.serving_requests, 8)
+        if not args.no_c4:
+            extras["c4"] = large_record(args, LARGE["c4"], steps=1, warmup=1, cpu_baseline=False)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-                "data": "synthetic (seeded jittered icosphere)", "config": WORKLOAD,
+                "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
+                "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic (seeded jittered icosphere)",
+                "config": dict(WORKLOAD, parallelism=(f"block-row sharding over {ws} GPUs" if ws > 1
+                                                      else "1 GPU")),
                 "integrals_per_step": ents_all / args.steps,
                 "entries": {"near": st_slp["near_entries"], "far_SLP": st_slp["far_entries"],
                             "far_DLP": st_dlp["far_entries"], "singular_pairs": st_slp["singular_pairs"],
@@ -550,6 +609,8 @@ def run_gpu(args):
                 "gpu_launches": int(launches), "step_ms": step_ms}
         if auto_q is not None:
             line["autotuned_quadrature"] = auto_q
+        line["measured_peaks"] = peaks
+        line.update(extras)
         if args.rho3 > 0 or args.rho1 > 0:
             line["quadrature_classes"] = {
                 "rho3": args.rho3, "rho1": args.rho1,
@@ -562,18 +623,20 @@ def run_gpu(args):
     return 0
 
 
-def run_serving(args):
+def serving_record(args, nreq: int, calib: int):
     """Serving workload: a Poisson stream of assembly-and-product requests
     (mesh size log-uniform in [1k, 200k] triangles, jittered spheres and
     ellipsoids, 50% Laplace / 50% Helmholtz SLP with k ~ U[1, 20], ACA eps in
-    {1e-4, 1e-6}), admitted by HBM budget; latency p50/p99 and throughput."""
+    {1e-4, 1e-6}), admitted by HBM budget and served with continuous batching
+    (each batch's assemblies share one persistent ACA launch per kind of
+    matrix); every tenth request is followed by a product-only request
+    against the matrix it left resident.  Latency p50/p99 and throughput."""
     import threading
     import torch
     from paper_1711_01897_gb300 import bem, meshes
     torch.cuda.set_device(0)
     torch.cuda.init()
     rng = np.random.default_rng(1004)
-    nreq = args.requests
     cache = {}
 
     def mesh_for(i):
@@ -600,13 +663,15 @@ def run_serving(args):
     srv = bem.Server(budget, max_slots=args.slots)
     # capacity: a closed-loop batch of the first requests
     t0 = time.perf_counter()
-    cal = [srv.submit(r["V"], r["T"], r["x"], k=r["k"], aca_eps=r["eps"]) for r in reqs[:args.calib]]
+    cal = [srv.submit(r["V"], r["T"], r["x"], k=r["k"], aca_eps=r["eps"]) for r in reqs[:calib]]
     for rid in cal:
         srv.wait(rid)
-    cap = args.calib / (time.perf_counter() - t0)
+    cap = calib / (time.perf_counter() - t0)
     rate = args.load * cap
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
     ids = [None] * nreq
+    prods = {}
+    st0 = srv.stats()
     clk = Clocks(0)
     clk.start()
     start = time.perf_counter()
@@ -617,39 +682,68 @@ def run_serving(args):
             if dt > 0:
                 time.sleep(dt)
             ids[i] = srv.submit(r["V"], r["T"], r["x"], k=r["k"], aca_eps=r["eps"])
+            if i % 10 == 5:
+                prods[i] = srv.submit_product(ids[i], r["x"])
 
     th = threading.Thread(target=submitter)
     th.start()
-    lat, ints, fails = [], 0, 0
+    lat, lat_prod, ints, fails, shared, mism = [], [], 0, 0, [], 0
     for i in range(nreq):
         while ids[i] is None:
             time.sleep(0.0005)
-        rc, info, _ = srv.wait(ids[i])
+        rc, info, y = srv.wait(ids[i])
         if rc != 0:
             fails += 1
             continue
         lat.append(info.t_done_ms - info.t_submit_ms)
         ints += info.integrals
+        shared.append(info.launch_requests)
+        if i % 10 == 5:
+            while i not in prods:
+                time.sleep(0.0005)
+            rc2, info2, y2 = srv.wait(prods[i])
+            if rc2 == 0:
+                lat_prod.append(info2.t_done_ms - info2.t_submit_ms)
+                mism += int(not np.array_equal(y, y2))
     th.join()
     span = time.perf_counter() - start
     st = srv.stats()
     srv.close()
     clocks = clk.stop()
     lat = np.array(lat)
-    line = {"metric": METRIC, "value": float(np.percentile(lat, 99)), "unit": "ms (p99 latency)",
-            "n_gpus": 1, "steps": nreq, "warmup": args.calib, "ms_per_step": None,
+    return {
+        "config": {"workload": "serving: Poisson stream, 1k-200k triangles, 50% Laplace / 50% "
+                               "Helmholtz SLP k~U[1,20], eps in {1e-4,1e-6}, assemble + 1 matvec; "
+                               "every 10th followed by a product on its resident matrix",
+                   "requests": nreq, "slots": args.slots, "hbm_budget_gb": args.hbm_budget_gb,
+                   "offered_load": args.load, "capacity_req_per_s": cap},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean()),
+                       "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50))},
+        "product_only_latency_ms": ({"p50": float(np.percentile(lat_prod, 50)),
+                                     "p99": float(np.percentile(lat_prod, 99)),
+                                     "count": len(lat_prod), "differ_from_assembly": mism}
+                                    if lat_prod else None),
+        "throughput": {"requests_per_s": len(lat) / span, "integrals_per_s": ints / span},
+        "batching": {"aca_launches": st["aca_launches"] - st0["aca_launches"],
+                     "requests_in_aca_launches": st["aca_launch_requests"] - st0["aca_launch_requests"],
+                     "max_requests_per_launch": st["max_launch_requests"],
+                     "mean_requests_per_launch_seen": float(np.mean(shared)) if shared else 0.0},
+        "residency": {"reuse_hits": st["reuse_hits"], "evictions": st["evictions"],
+                      "resident_at_end": st["resident"]},
+        "admission": {"peak_reserved_gb": st["peak_reserved_bytes"] / (1 << 30),
+                      "budget_gb": args.hbm_budget_gb, "failed": fails},
+        "clocks": clocks}
+
+
+def run_serving(args):
+    rec = serving_record(args, args.requests, args.calib)
+    lat = rec["latency_ms"]
+    line = {"metric": METRIC, "value": lat["p99"], "unit": "ms (p99 latency)",
+            "n_gpus": 1, "steps": args.requests, "warmup": args.calib, "ms_per_step": None,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic (seeded Poisson request stream)",
-            "config": {"workload": "serving: Poisson stream, 1k-200k triangles, 50% Laplace / 50% "
-                                   "Helmholtz SLP k~U[1,20], eps in {1e-4,1e-6}, assemble + 1 matvec",
-                       "requests": nreq, "slots": args.slots, "hbm_budget_gb": args.hbm_budget_gb,
-                       "offered_load": args.load, "capacity_req_per_s": cap},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "mean": float(lat.mean())},
-            "throughput": {"requests_per_s": len(lat) / span, "integrals_per_s": ints / span},
-            "admission": {"peak_reserved_gb": st["peak_reserved_bytes"] / (1 << 30),
-                          "budget_gb": args.hbm_budget_gb, "failed": fails},
-            "clocks": clocks}
+            "data": "synthetic (seeded Poisson request stream)"}
+    line.update(rec)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -663,7 +757,7 @@ LARGE = {
 }
 
 
-def run_large(args, spec):
+def large_record(args, spec, steps: int, warmup: int, cpu_baseline: bool = True):
     """Helmholtz ellipsoid (C3) and level-9 sphere (C4): one step = one mixed
     assembly (all blocks in one persistent launch) plus the products; sampled
     exact rows of the matrix (oracle) check the product."""
@@ -689,8 +783,8 @@ def run_large(args, spec):
     y = torch.zeros_like(x)
     clk = Clocks(0)
     asm_ms, mv_ms, ents = [], [], 0
-    for s in range(args.warmup + args.steps):
-        if s == args.warmup:
+    for s in range(warmup + steps):
+        if s == warmup:
             clk.start()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -706,7 +800,7 @@ def run_large(args, spec):
             d.record(stream)
             d.synchronize()
             mvs.append(c.elapsed_time(d))
-        if s >= args.warmup:
+        if s >= warmup:
             asm_ms.append(a.elapsed_time(b))
             mv_ms.extend(mvs)
             ents += st["near_entries"] + st["far_entries"]
@@ -719,24 +813,24 @@ def run_large(args, spec):
     ref = A @ xh
     t_or = time.perf_counter() - t1
     cpu = None
-    if not args.no_cpu_baseline:
+    if cpu_baseline and not args.no_cpu_baseline:
         # the oracle's H-matrix assembly on a stratified sample of this mesh's
         # leaf blocks, extrapolated to the whole assembly by its integrals
         rate, cores, sample = oracle_sample_rate(V, T, seconds_target=args.cpu_seconds,
                                                  ops=(spec["op"],), k=k, eps=spec["eps"])
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "cpu": cpu_model(), "kind": "oracle", "sample": sample,
-               "extrapolated_assembly_s": (ents / args.steps) / rate}
+               "extrapolated_assembly_s": (ents / steps) / rate}
     got = y.cpu().numpy()[rows]
     err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     tot_ms = float(np.sum(asm_ms))
     line = {"metric": METRIC, "value": ents / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": tot_ms / args.steps + float(np.sum(mv_ms)) / args.steps,
+            "steps": steps, "warmup": warmup,
+            "ms_per_step": tot_ms / steps + float(np.sum(mv_ms)) / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic", "config": {"workload": spec["workload"], "n_triangles": n, "k": k,
                                            "aca_eps": spec["eps"], "leaf_size": LEAF, "eta": ETA},
             "h_assembly_ms": float(np.median(asm_ms)), "tree_and_upload_s": setup_s,
-            "integrals_per_assembly": ents / args.steps,
+            "integrals_per_assembly": ents / steps,
             "phase_ms": {"near": st["time_near_ms"], "singular": st["time_singular_ms"],
                          "aca": st["time_far_ms"]},
             "ranks": [st["rank_min"], st["rank_mean"], st["rank_max"]],
@@ -756,7 +850,15 @@ def run_large(args, spec):
                                       "blocks": {"rule3": st["n_blocks_rule3"],
                                                  "rule1": st["n_blocks_rule1"],
                                                  "all_far": st["n_blocks_far"]}}
-    print(json.dumps(line), flush=True)
+    h.close()
+    mesh.close()
+    del x, y
+    torch.cuda.empty_cache()
+    return line
+
+
+def run_large(args, spec):
+    print(json.dumps(large_record(args, spec, args.steps, args.warmup)), flush=True)
     return 0
 
 
@@ -957,6 +1059,10 @@ def main():
     ap.add_argument("--nu", type=int, default=72,
                     help="geodesic frequency of the dense workload's sphere (20 nu^2 triangles)")
     ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="requests of the short serving stream in the default line (0: none)")
+    ap.add_argument("--no-c4", action="store_true",
+                    help="leave the level-9 record out of the default line")
     ap.add_argument("--slots", type=int, default=6)
     ap.add_argument("--hbm-budget-gb", type=float, default=96.0)
     ap.add_argument("--load", type=float, default=0.8)

@@ -87,6 +87,27 @@ int64_t bem_kernel_launches(void);
  * show whether a call allocated. */
 int bem_memory_usage(int64_t *reserved, int64_t *used);
 
+/* Throughputs measured on the current device by short calibration kernels
+ * (independent dependency chains in every thread, best of three timed
+ * launches after a warm-up, CUDA events on `cuda_stream`): the roofline
+ * denominators of the units the hot path is bound by.  The paper reports no
+ * such figures; this is an interface of this library only.  Rates are
+ * instructions per second (one fused multiply-add counts once) and bytes per
+ * second (read + write of a 1 GiB device copy).  Allocates and frees 2 GiB of
+ * device memory; takes a few tens of milliseconds. */
+typedef struct {
+    double fp32_fma_per_s;    /* FFMA */
+    double fp64_fma_per_s;    /* DFMA */
+    double mufu_rsqrt_per_s;  /* rsqrt.approx.ftz.f32 */
+    double mufu_sin_per_s;    /* sin.approx.ftz.f32 */
+    double copy_bytes_per_s;  /* device-to-device copy by a kernel */
+    int32_t sm_count;
+    double clock_mhz_nominal; /* the device's reported SM clock */
+    float ms[5];              /* best launch time of each kernel, in the order above */
+} bem_peaks;
+
+int bem_measure_peaks(bem_peaks *out, void *cuda_stream);
+
 /* Diagnostic of the FP64 reciprocal that scales every ACA pivot (Eq. (7):
  * v_k = v~_k / (v~_k)_{j_k}): y[i] = 1 / x[i] computed on the device by the
  * routine the ACA kernels use (Newton-Raphson from a single-precision seed,
@@ -358,15 +379,51 @@ int hmat_block_dense(bem_hmat hmat, int64_t block, void *out, int32_t *rank);
  * or array, or too small a capacity.  Needs no assembly and no device. */
 int hmat_block_rules(bem_hmat hmat, int32_t *points, int64_t cap);
 
+/* Row partition for assembling one H-matrix on several GPUs (the paper
+ * divides its block list evenly between two GPUs, Sec. 4.1; here every part
+ * owns whole block rows, balanced by estimated cost, so that no product
+ * needs a reduction).  The cluster-order rows [0, n_rows) are cut into
+ * n_parts ranges, only where no block's row range is cut, each range's cost
+ * as near as those cuts allow to 1/n_parts of the total: m n per dense
+ * block, (m + n) rank_est per admissible block, spread over its rows.
+ * blocks: n_blocks rows of 5 int64 (tau_begin, tau_end, sigma_begin,
+ * sigma_end, admissible) as hmat_blocks returns them; bounds: caller-owned,
+ * n_parts + 1 entries (bounds[0] = 0, bounds[n_parts] = n_rows; a part may
+ * be empty).  Host only; BEM_E_ARG for bad sizes or a block outside the
+ * rows. */
+int bem_partition_rows(const int64_t *blocks, int64_t n_blocks, int64_t n_rows, int32_t n_parts,
+                       double rank_est, int64_t *bounds);
+
+/* Part `part` (0 .. n_parts - 1) of the row partition of the P0 block tree
+ * that hmat_build_tree(mesh, leaf_size, eta) would build: the same clusters
+ * and blocks, keeping the blocks whose rows lie in the part's range (the
+ * bem_partition_rows split with rank_est = 10).  Assembly then evaluates
+ * only those blocks, and hmat_matvec returns the full-length product with
+ * the rows of other parts set to zero: the products of all parts add up to
+ * the product of the whole matrix, each row coming from exactly one part.
+ * hmat_part_rows gives the part's cluster-order row range (hmat_blocks gives
+ * the permutation).  BEM_E_ARG for a bad part. */
+int hmat_build_tree_part(bem_mesh mesh, int32_t leaf_size, double eta, int32_t n_parts,
+                         int32_t part, bem_hmat *out);
+int hmat_part_rows(bem_hmat hmat, int64_t *row_begin, int64_t *row_end);
+
 /* Frees the handle and its device memory. */
 int hmat_destroy(bem_hmat hmat);
 
 /* ---------------------------------------------------------------------- */
 /* Request server: assembly-and-product requests for meshes of different    */
-/* sizes and wavenumbers arrive over time; each is admitted when the HBM     */
-/* budget allows and runs on its own stream, so admitted requests overlap on */
-/* the device.  (The paper runs one problem at a time; this is the library's */
-/* serving interface.)                                                       */
+/* sizes and wavenumbers arrive over time and are served with continuous    */
+/* batching.  Host threads build each request's trees; an engine admits     */
+/* requests in arrival order as the HBM budget allows and runs everything   */
+/* admitted since its last launch as one batch: the near fields, then ONE   */
+/* persistent ACA launch over the admissible blocks of all the batch's      */
+/* requests of the same kind (Algorithm ACA, Sec. 2.1, across matrices), then */
+/* the products.  Requests that arrive meanwhile join the next batch, which   */
+/* overlaps the running one on a second stream.  Assembled matrices stay     */
+/* resident until the budget needs their bytes (least recently used first),  */
+/* and a request may apply a resident matrix instead of assembling one.      */
+/* (The paper runs one problem at a time; this is the library's serving      */
+/* interface.)                                                               */
 /* ---------------------------------------------------------------------- */
 
 typedef struct bem_server_s *bem_server;
@@ -378,7 +435,12 @@ enum bem_request_state {
 };
 
 /* One request: mesh (copied at submit), operator, ACA settings and the host
- * vector x of the product (n_triangles f64 for k == 0, complex128 otherwise). */
+ * vector x of the product (n_triangles f64 for k == 0, complex128 otherwise).
+ * reuse > 0 makes it a product-only request: apply the resident matrix that
+ * request `reuse` of this server assembled (its op, k, aca_eps and prec; the
+ * mesh fields are ignored except n_triangles, the length of x).  It waits
+ * while that request is still running, and fails with BEM_E_STATE if the
+ * matrix is no longer resident (evicted, or its request failed). */
 typedef struct {
     const double *vertices;
     int64_t n_vertices;
@@ -392,6 +454,7 @@ typedef struct {
     double eta;
     const void *x;
     double dry_run_ms;   /* duration of the simulated device work (dry-run servers) */
+    int64_t reuse;       /* 0: assemble; > 0: id of the request whose matrix to apply */
 } bem_request;
 
 typedef struct {
@@ -403,23 +466,34 @@ typedef struct {
     int64_t reserved_bytes;     /* HBM reserved for the request while it ran */
     int64_t integrals;          /* entries evaluated: near field + ACA requests */
     double assembly_ms;         /* device time of the assembly */
+    int32_t launch_requests;    /* requests whose blocks shared its ACA launch (0: none ran) */
+    int32_t reused;             /* 1: applied a resident matrix, nothing assembled */
 } bem_request_info;
 
 typedef struct {
     int64_t submitted, completed, failed, cancelled;
     int64_t queued, running;
-    int64_t reserved_bytes;      /* currently reserved */
+    int64_t reserved_bytes;      /* currently reserved: running requests + resident matrices */
     int64_t peak_reserved_bytes; /* never above the budget */
     int64_t budget_bytes;
+    int64_t resident;            /* matrices kept on the device, and their bytes */
+    int64_t resident_bytes;
+    int64_t evictions;           /* resident matrices freed for admissions */
+    int64_t reuse_hits;          /* product-only requests served from a resident matrix */
+    int64_t aca_launches;        /* ACA launches run, and the requests they held in all */
+    int64_t aca_launch_requests;
+    int64_t max_launch_requests; /* most requests in one ACA launch */
 } bem_server_stats;
 
-/* Creates a server on the current device with `max_slots` worker threads
- * (1..64), each with its own CUDA stream.  A request is admitted, in arrival
- * order, once its device bytes (geometry, tree, dense blocks, factor pool of
- * four 4-column chunks per admissible block, vectors) fit next to the
- * requests already running; one that alone exceeds the budget fails with
- * BEM_E_OOM.  flags: BEM_SERVER_DRY_RUN runs the host logic only (no CUDA
- * call; reserved bytes = 1024 per triangle; y = x after dry_run_ms). */
+/* Creates a server on the current device with `max_slots` host threads for
+ * the trees (1..64); at most max_slots requests run at once.  A request is
+ * admitted, in arrival order, once its device bytes (geometry, tree, dense
+ * blocks, factor pool of four 4-column chunks per admissible block, vectors)
+ * fit next to the running requests and resident matrices (idle resident
+ * matrices are evicted, least recently used first, to make room); one that
+ * alone exceeds the budget fails with BEM_E_OOM.  flags: BEM_SERVER_DRY_RUN
+ * runs the host logic only (no CUDA call; reserved bytes = 1024 per
+ * triangle; a batch takes the longest dry_run_ms of its requests; y = x). */
 int bem_server_create(int64_t hbm_budget_bytes, int32_t max_slots, int32_t flags,
                       bem_server *out);
 
@@ -436,12 +510,14 @@ int bem_server_poll(bem_server server, int64_t req_id, bem_request_info *info);
 int bem_server_wait(bem_server server, int64_t req_id, int64_t timeout_ms,
                     bem_request_info *info, void *y);
 
-/* Cancels a request that is still queued (BEM_E_STATE once it has started). */
+/* Cancels a request that has not been admitted yet (BEM_E_STATE once it
+ * has). */
 int bem_server_cancel(bem_server server, int64_t req_id);
 
 int bem_server_stats_get(bem_server server, bem_server_stats *out);
 
-/* Cancels queued requests, waits for running ones, joins the workers. */
+/* Cancels queued requests, waits for running ones, joins the threads and
+ * frees the resident matrices. */
 int bem_server_destroy(bem_server server);
 
 #ifdef __cplusplus

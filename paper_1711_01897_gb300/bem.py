@@ -57,6 +57,13 @@ class HmatStats(ctypes.Structure):
                 ("n_blocks_lane", ctypes.c_int64)]
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp64_fma_per_s", ctypes.c_double),
+                ("mufu_rsqrt_per_s", ctypes.c_double), ("mufu_sin_per_s", ctypes.c_double),
+                ("copy_bytes_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32),
+                ("clock_mhz_nominal", ctypes.c_double), ("ms", ctypes.c_float * 5)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("warp_max_rows", ctypes.c_int32), ("lane_max_rows", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32)]
@@ -71,20 +78,24 @@ class Request(ctypes.Structure):
                 ("triangles", ctypes.c_void_p), ("n_triangles", ctypes.c_int64),
                 ("op", ctypes.c_int32), ("k", ctypes.c_double), ("aca_eps", ctypes.c_double),
                 ("prec", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("eta", ctypes.c_double),
-                ("x", ctypes.c_void_p), ("dry_run_ms", ctypes.c_double)]
+                ("x", ctypes.c_void_p), ("dry_run_ms", ctypes.c_double),
+                ("reuse", ctypes.c_int64)]
 
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
                 ("t_done_ms", ctypes.c_double), ("reserved_bytes", ctypes.c_int64),
-                ("integrals", ctypes.c_int64), ("assembly_ms", ctypes.c_double)]
+                ("integrals", ctypes.c_int64), ("assembly_ms", ctypes.c_double),
+                ("launch_requests", ctypes.c_int32), ("reused", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("submitted", "completed", "failed", "cancelled", "queued", "running",
-                 "reserved_bytes", "peak_reserved_bytes", "budget_bytes")]
+                 "reserved_bytes", "peak_reserved_bytes", "budget_bytes", "resident",
+                 "resident_bytes", "evictions", "reuse_hits", "aca_launches",
+                 "aca_launch_requests", "max_launch_requests")]
 
 
 QUEUED, PREPARING, RUNNING, DONE, FAILED, CANCELLED = range(6)
@@ -114,6 +125,7 @@ def load(path: str = LIB_PATH):
             "bem_kernel_launches": ([], ctypes.c_int64),
             "bem_memory_usage": ([P, P], ctypes.c_int),
             "bem_debug_recip": ([P, P, i64, P], ctypes.c_int),
+            "bem_measure_peaks": ([ctypes.POINTER(Peaks), P], ctypes.c_int),
             "bem_set_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
             "bem_get_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
             "bem_set_quadrature": ([ctypes.POINTER(Quadrature)], ctypes.c_int),
@@ -127,6 +139,9 @@ def load(path: str = LIB_PATH):
             "hmat_build_tree": ([P, i32, dbl, P], ctypes.c_int),
             "hmat_build_tree_space": ([P, i32, dbl, i32, P], ctypes.c_int),
             "hmat_dofs": ([P], i64),
+            "bem_partition_rows": ([P, i64, i64, i32, dbl, P], ctypes.c_int),
+            "hmat_build_tree_part": ([P, i32, dbl, i32, i32, P], ctypes.c_int),
+            "hmat_part_rows": ([P, P, P], ctypes.c_int),
             "hmat_assemble": ([P, i32, dbl, dbl, i32, P], ctypes.c_int),
             "hmat_matvec": ([P, P, P, i32, P], ctypes.c_int),
             "hmat_stats": ([P, ctypes.POINTER(HmatStats)], ctypes.c_int),
@@ -202,6 +217,15 @@ def bem_memory_usage() -> dict:
     r, u = ctypes.c_int64(), ctypes.c_int64()
     _check(load().bem_memory_usage(ctypes.byref(r), ctypes.byref(u)))
     return {"reserved": r.value, "used": u.value}
+
+
+def bem_measure_peaks(stream=None) -> dict:
+    """Unit throughputs measured on the current device (see bem.h)."""
+    p = Peaks()
+    _check(load().bem_measure_peaks(ctypes.byref(p), _stream(stream)))
+    d = {n: getattr(p, n) for n, _ in Peaks._fields_ if n != "ms"}
+    d["ms"] = list(p.ms)
+    return d
 
 
 def bem_debug_recip(x, y, stream=None):
@@ -292,6 +316,29 @@ def hmat_build_tree_space(mesh, leaf_size: int, eta: float, space: int):
     _check(load().hmat_build_tree_space(mesh, int(leaf_size), float(eta), int(space),
                                         ctypes.byref(h)))
     return h
+
+
+def bem_partition_rows(blocks, n_rows: int, n_parts: int, rank_est: float = 10.0) -> np.ndarray:
+    """Cluster-order row bounds [n_parts + 1] of a cost-balanced block-row
+    partition of a block list (rows of 5 int64, as hmat_blocks returns)."""
+    B = np.ascontiguousarray(blocks, dtype=np.int64)
+    out = np.zeros(n_parts + 1, dtype=np.int64)
+    _check(load().bem_partition_rows(B.ctypes.data, B.shape[0], int(n_rows), int(n_parts),
+                                     float(rank_est), out.ctypes.data))
+    return out
+
+
+def hmat_build_tree_part(mesh, leaf_size: int, eta: float, n_parts: int, part: int):
+    h = ctypes.c_void_p()
+    _check(load().hmat_build_tree_part(mesh, int(leaf_size), float(eta), int(n_parts), int(part),
+                                       ctypes.byref(h)))
+    return h
+
+
+def hmat_part_rows(hmat):
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().hmat_part_rows(hmat, ctypes.byref(b), ctypes.byref(e)))
+    return b.value, e.value
 
 
 def hmat_dofs(hmat) -> int:
@@ -385,15 +432,23 @@ class Mesh:
 class HMatrix:
     """Owns a bem_hmat handle built on a Mesh."""
 
-    def __init__(self, mesh: Mesh, leaf_size: int = 32, eta: float = 1.2, space: int = P0):
+    def __init__(self, mesh: Mesh, leaf_size: int = 32, eta: float = 1.2, space: int = P0,
+                 parts: int = 1, part: int = 0):
+        """parts > 1: only block rows of part `part` of the row partition
+        (hmat_build_tree_part)."""
         self.mesh = mesh
         self.space = space
-        if space == P0:
+        if parts > 1:
+            self.handle = hmat_build_tree_part(mesh.handle, leaf_size, eta, parts, part)
+        elif space == P0:
             self.handle = hmat_build_tree(mesh.handle, leaf_size, eta)
         else:
             self.handle = hmat_build_tree_space(mesh.handle, leaf_size, eta, space)
         self.n = hmat_dofs(self.handle)
         self.cplx = False
+
+    def part_rows(self):
+        return hmat_part_rows(self.handle)
 
     def assemble(self, op, k, aca_eps, prec, stream=None):
         hmat_assemble(self.handle, op, k, aca_eps, prec, stream)
@@ -436,6 +491,7 @@ class Server:
         _check(load().bem_server_create(int(hbm_budget_bytes), int(max_slots),
                                         SERVER_DRY_RUN if dry_run else 0, ctypes.byref(self.handle)))
         self._keep = {}
+        self._shape = {}
 
     def submit(self, vertices, triangles, x, op=SLP, k=0.0, aca_eps=1e-4, prec=MIXED,
                leaf_size=32, eta=1.2, dry_run_ms=0.0) -> int:
@@ -443,10 +499,26 @@ class Server:
         T = np.ascontiguousarray(triangles, dtype=np.int32)
         X = np.ascontiguousarray(x, dtype=np.complex128 if k != 0 else np.float64)
         q = Request(V.ctypes.data, V.shape[0], T.ctypes.data, T.shape[0], op, float(k),
-                    float(aca_eps), prec, leaf_size, float(eta), X.ctypes.data, float(dry_run_ms))
+                    float(aca_eps), prec, leaf_size, float(eta), X.ctypes.data, float(dry_run_ms), 0)
         rid = ctypes.c_int64()
         _check(load().bem_server_submit(self.handle, ctypes.byref(q), ctypes.byref(rid)))
         self._keep[rid.value] = (T.shape[0], k != 0)
+        self._shape[rid.value] = (T.shape[0], k != 0)
+        return rid.value
+
+    def submit_product(self, reuse: int, x, dry_run_ms=0.0) -> int:
+        """A product-only request: y = A x with the resident matrix that
+        request `reuse` assembled."""
+        nt, cplx = self._shape[reuse]
+        X = np.ascontiguousarray(x, dtype=np.complex128 if cplx else np.float64)
+        if X.shape != (nt,):
+            raise ValueError("x must have one entry per triangle")
+        q = Request(None, 0, None, nt, 0, 1.0 if cplx else 0.0, 1e-4, MIXED, 32, 1.2,
+                    X.ctypes.data, float(dry_run_ms), int(reuse))
+        rid = ctypes.c_int64()
+        _check(load().bem_server_submit(self.handle, ctypes.byref(q), ctypes.byref(rid)))
+        self._keep[rid.value] = (nt, cplx)
+        self._shape[rid.value] = (nt, cplx)
         return rid.value
 
     def poll(self, rid: int) -> RequestInfo:

@@ -685,18 +685,29 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
     for (int c = 0; c < NCHUNK; ++c) chk->c[c] = chunk[c];
 }
 
+// The job of work item i and the block's index in that job's arrays.
+__device__ __forceinline__ const AcaJob *item_job(const AcaWork &w, int64_t i, int64_t &idx)
+{
+    if (!w.items) {
+        idx = i;
+        return w.jobs;
+    }
+    const int64_t it = w.items[i];
+    idx = it & ((int64_t(1) << kItemShift) - 1);
+    return w.jobs + (it >> kItemShift);
+}
+
 template <int OP, bool CPLX, int PREC, int DOF, bool RULES = false>
 __global__ void __launch_bounds__(kAcaThreads, 2)
-k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, FarChunks *chunks,
-      int64_t n_big,
-      int64_t n_small, int64_t n_tiny, int zwords_small, typename VT<CPLX>::T *pool, Pool *P,
-      AcaQueue *Q)
+k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
 {
+    using T = typename VT<CPLX>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ RedScratch red;
     __shared__ GroupSmem<CPLX> gs[kWarps];
-    __shared__ typename VT<CPLX>::T part[2 * kAcaThreads];
+    __shared__ T part[2 * kAcaThreads];
     __shared__ int64_t s_b;
+    const int64_t n_big = w.n_big, n_small = w.n_small, n_tiny = w.n_tiny;
     // row bitmasks: the whole region for a CTA-wide block, then one slice of
     // zwords_small words per warp for the small blocks
     unsigned *zbig = reinterpret_cast<unsigned *>(smem_raw);
@@ -708,47 +719,52 @@ k_aca(DevGeom g, QuadRule R, double k, double eps, FarBlock *blocks, FarChunks *
         int64_t b = s_b;
         __syncthreads();
         if (b >= n_big) break;
-        aca_block<CtaGroup, OP, CPLX, PREC, DOF, RULES>(cg, g, R, k, eps, blocks + b, chunks + b,
-                                                        pool, P, gs[0], zbig, part);
+        int64_t idx;
+        const AcaJob *J = item_job(w, b, idx);
+        aca_block<CtaGroup, OP, CPLX, PREC, DOF, RULES>(cg, J->g, R, J->k, J->eps, J->far + idx,
+                                                        J->chunks + idx, (T *)J->pool, J->P,
+                                                        gs[0], zbig, part);
     }
     // phase 2: small blocks, one warp each
-    const int w = threadIdx.x >> 5;
+    const int wi = threadIdx.x >> 5;
     WarpGroup wg{(int)(threadIdx.x & 31)};
     for (;;) {
         int64_t b = 0;
         if (wg.lane == 0) b = (int64_t)atomicAdd(&Q->next_small, 1u);
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= n_small) break;
-        aca_block<WarpGroup, OP, CPLX, PREC, DOF, RULES>(wg, g, R, k, eps, blocks + n_big + b,
-                                                  chunks + n_big + b, pool, P, gs[w],
-                                                  zbig + (int64_t)w * zwords_small, part + 64 * w);
+        int64_t idx;
+        const AcaJob *J = item_job(w, n_big + b, idx);
+        aca_block<WarpGroup, OP, CPLX, PREC, DOF, RULES>(wg, J->g, R, J->k, J->eps, J->far + idx,
+                                                         J->chunks + idx, (T *)J->pool, J->P,
+                                                         gs[wi], zbig + (int64_t)wi * zwords_small,
+                                                         part + 64 * wi);
     }
     // phase 3: tiny blocks, 32 per warp, one per lane (P0 only; the host
     // puts no DP1 block in this class)
     if constexpr (DOF == 1) {
-        FarBlock *tiny = blocks + n_big + n_small;
-        FarChunks *tiny_chk = chunks + n_big + n_small;
         for (;;) {
             int64_t b0 = 0;
             if (wg.lane == 0) b0 = (int64_t)atomicAdd(&Q->next_tiny, 32u);
             b0 = __shfl_sync(0xffffffffu, b0, 0);
             if (b0 >= n_tiny) break;
             const int64_t b = b0 + wg.lane;
-            if (b < n_tiny)
-                aca_lane<OP, CPLX, PREC, RULES>(g, R, k, eps, tiny + b, tiny_chk + b, pool, P);
+            if (b < n_tiny) {
+                int64_t idx;
+                const AcaJob *J = item_job(w, n_big + n_small + b, idx);
+                aca_lane<OP, CPLX, PREC, RULES>(J->g, R, J->k, J->eps, J->far + idx,
+                                                J->chunks + idx, (T *)J->pool, J->P);
+            }
             __syncwarp();
         }
     }
 }
 
 template <int OP, bool CPLX, int PREC, int DOF, bool RULES = false>
-cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps,
-                       FarBlock *blocks, FarChunks *chunks, int64_t n_big, int64_t n_small,
-                       int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool,
-                       Pool *P, AcaQueue *Q,
-                       int num_sms, cudaStream_t st)
+cudaError_t aca_launch(const AcaWork &w, const QuadRule &R, AcaQueue *Q, int num_sms,
+                       cudaStream_t st)
 {
-    const int64_t zw_big = (max_m_big + 31) / 32, zw_small = (max_m_small + 31) / 32;
+    const int64_t zw_big = (w.max_m_big + 31) / 32, zw_small = (w.max_m_small + 31) / 32;
     int64_t words = zw_big > kWarps * zw_small ? zw_big : kWarps * zw_small;
     size_t dyn = (size_t)(words > 0 ? words : 1) * sizeof(unsigned);
     auto kern = k_aca<OP, CPLX, PREC, DOF, RULES>;
@@ -760,9 +776,7 @@ cudaError_t aca_launch(const DevGeom &g, const QuadRule &R, double k, double eps
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
-    kern<<<(unsigned)grid, kAcaThreads, dyn, st>>>(
-        g, R, k, eps, blocks, chunks, n_big, n_small, n_tiny, (int)zw_small,
-        reinterpret_cast<typename VT<CPLX>::T *>(pool), P, Q);
+    kern<<<(unsigned)grid, kAcaThreads, dyn, st>>>(w, R, (int)zw_small, Q);
     count_launches(1);
     return cudaGetLastError();
 }

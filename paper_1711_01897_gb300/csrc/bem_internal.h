@@ -144,6 +144,31 @@ struct AcaQueue {
     unsigned int pad;
 };
 
+// One H-matrix's part of an ACA launch: its cluster-order geometry, its
+// admissible blocks and their chunk tables, its factor pool, k and eps.
+struct AcaJob {
+    DevGeom g;
+    FarBlock *far;
+    FarChunks *chunks;
+    void *pool;
+    Pool *P;
+    double k, eps;
+};
+
+// Work list of one ACA launch: n_big blocks for whole CTAs, then n_small
+// for warps, then n_tiny for single lanes, each class in descending size.
+// items == nullptr: item i is block i of jobs[0] (one H-matrix whose block
+// array is in that order); otherwise items[i] = (job << kItemShift) | the
+// block's index in that job's array (the request server's launches over
+// several H-matrices).
+constexpr int kItemShift = 40;
+struct AcaWork {
+    const AcaJob *jobs;      // device array
+    const int64_t *items;    // device array or null
+    int64_t n_big, n_small, n_tiny;
+    int64_t max_m_big, max_m_small;
+};
+
 // Read-only view of a mesh and of already-initialised per-device constants,
 // for entry points that must not allocate.  mesh_view fails (returns false)
 // for a null mesh; consts_peek returns false if the device has none yet.
@@ -214,19 +239,16 @@ cudaError_t launch_near_dp1(const DevGeom &g, const QuadRule &rule, int op, doub
                             const NearBlock *blocks, int64_t nblocks, void *out, cudaStream_t st);
 
 // dofs = 1: P0 (a dof per triangle); dofs = 3: DP1 (block ranges in dof
-// units, three local dofs per triangle)
-cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
-                       double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
-                       int64_t n_small, int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
-                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st, int dofs = 1,
+// units, three local dofs per triangle).  cplx: Helmholtz (k != 0) for every
+// job of the launch; rules: the mixed Laplace kernels that read each block's
+// distance class.
+cudaError_t launch_aca(const AcaWork &w, const QuadRule &rule, int op, bool cplx, int prec,
+                       AcaQueue *queue, int num_sms, cudaStream_t st, int dofs = 1,
                        bool rules = false);
 
 // the DP1 instantiations (kernels_aca_dp1.cu); no tiny-block class
-cudaError_t launch_aca_dp1(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
-                           double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
-                           int64_t n_small, int64_t max_m_big, int64_t max_m_small,
-                           void *pool_data, Pool *pool, AcaQueue *queue, int num_sms,
-                           cudaStream_t st);
+cudaError_t launch_aca_dp1(const AcaWork &w, const QuadRule &rule, int op, bool cplx, int prec,
+                           AcaQueue *queue, int num_sms, cudaStream_t st);
 
 // y[i] = 1 / x[i] by the ACA's pivot reciprocal (diagnostic)
 cudaError_t launch_debug_recip(const double *x, double *y, int64_t n, cudaStream_t st);

@@ -19,6 +19,7 @@
 
 #include "../../include/bem.h"
 #include "bem_internal.h"
+#include "bem_host_internal.h"
 
 #include <atomic>
 #include <condition_variable>
@@ -1099,6 +1100,7 @@ struct bem_hmat_s {
     int space = BEM_P0;
     int dofs = 1;
     int64_t ndof = 0;                     // length of the internal vectors
+    int64_t row_b = 0, row_e = -1;        // cluster-order rows kept (a part of a row partition)
     std::vector<int32_t> dperm;           // dof permutation (DP1): cluster dof -> mesh dof
     std::vector<SingPairL, NoInit<SingPairL>> singl[3];  // touching pairs of the DP1 near field
     std::vector<int64_t> vptr;            // P1: per vertex, its DP1 dofs (CSR, mesh order)
@@ -1135,8 +1137,8 @@ struct bem_hmat_s {
     std::vector<FarBlock> far_result;     // host copy of the factor descriptors, fetched lazily
     bool far_result_valid = false;
     int64_t factor_elems = 0, k2mn = 0, rank_mn = 0;
-    DBuf d_tiles, d_acastats;
-    int64_t pool_elems = 0;
+    DBuf d_tiles, d_acastats, d_job;
+    int64_t pool_elems = 0, pool_want = 0;
     double t_tree = 0, t_near = 0, t_far = 0, t_near_reg = 0;
     double t_clusters = 0, t_blocks = 0, t_lists = 0, t_upload = 0;
     // CUDA graph of the assembly sequence and what it was captured for
@@ -1149,8 +1151,10 @@ struct bem_hmat_s {
     cudaStream_t cap_stream = nullptr;
     Pool *pin_pool = nullptr;       // pinned readback slots
     AcaStats *pin_stats = nullptr;
+    AcaJob *pin_job = nullptr;      // pinned source of d_job (this matrix as one ACA job)
     ~bem_hmat_s()
     {
+        if (pin_job) cudaFreeHost(pin_job);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto &e : ev)
@@ -1465,6 +1469,80 @@ void build_blocks(bem_hmat_s &H)
 // (m + n descending, tree order on ties); the order comes from one sort of
 // packed 64-bit keys so that each FarBlock is written once.
 
+// Row partition of a block list (rows in cluster order): part boundaries
+// only where no block's row range is cut, each part's estimated cost as
+// close as the boundaries allow to 1/n_parts of the total.  Cost of a dense
+// block m n entries, of an admissible block (m + n) rank_est (the entries
+// its ACA requests at that rank); a block's cost is spread evenly over its
+// rows.  The paper's multi-GPU assembly splits the block list evenly between
+// its GPUs (Sec. 4.1); this generalises that to a cost-balanced split of the
+// block rows, so that each part owns whole rows of the matrix.
+constexpr double kPartRankEst = 10.0;  // typical ACA rank of the workloads (eps 1e-4 .. 1e-5)
+
+void partition_rows(const int64_t *blocks, int64_t nb, int64_t n, int32_t parts, double rank_est,
+                    int64_t *bounds)
+{
+    std::vector<int64_t> cross(n + 2, 0);
+    std::vector<double> cost(n + 1, 0.0);
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t *r = blocks + 5 * b;
+        const int64_t tb = r[0], te = r[1], m = r[1] - r[0], nn = r[3] - r[2];
+        if (m <= 0) continue;
+        if (te - tb > 1) {  // rows strictly inside (tb, te) may not be boundaries
+            cross[tb + 1] += 1;
+            cross[te] -= 1;
+        }
+        const double c = r[4] ? (double)(m + nn) * rank_est : (double)m * (double)nn;
+        cost[tb] += c / m;
+        cost[te] -= c / m;
+    }
+    // per-row cost and prefix sums
+    std::vector<double> pre(n + 1, 0.0);
+    double run = 0.0;
+    int64_t cr = 0;
+    std::vector<char> ok(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        run += cost[i];
+        pre[i + 1] = pre[i] + run;
+        cr += cross[i];
+        ok[i] = cr == 0;
+    }
+    ok[0] = ok[n] = 1;
+    bounds[0] = 0;
+    bounds[parts] = n;
+    const double total = pre[n];
+    int64_t prev = 0;
+    for (int32_t p = 1; p < parts; ++p) {
+        const double target = total * p / parts;
+        int64_t best = prev;
+        double bd = std::fabs(pre[prev] - target);
+        for (int64_t r = prev; r <= n; ++r) {
+            if (!ok[r]) continue;
+            const double d = std::fabs(pre[r] - target);
+            if (d < bd) {
+                bd = d;
+                best = r;
+            }
+            if (pre[r] > target) break;
+        }
+        bounds[p] = best;
+        prev = best;
+    }
+}
+
+// Keeps the blocks whose row cluster lies in [H.row_b, H.row_e).
+void restrict_rows(bem_hmat_s &H)
+{
+    std::vector<BlockH> keep;
+    for (const BlockH &B : H.blocks) {
+        const Cluster &T = H.cl[B.tau];
+        if (T.b >= H.row_b && T.e <= H.row_e) keep.push_back(B);
+        else if (T.e > H.row_b && T.b < H.row_e)
+            throw std::invalid_argument("the row range cuts the rows of a block");
+    }
+    H.blocks.swap(keep);
+}
+
 void build_lists(bem_hmat_s &H)
 {
     PhaseTrace trace("lists");
@@ -1723,7 +1801,9 @@ void build_lists(bem_hmat_s &H)
     std::vector<std::array<int64_t, 3>> at(nchunk + 1, std::array<int64_t, 3>{0, 0, 0});
     parallel_tasks(nchunk, [&](int64_t ck) {
         std::array<int64_t, 3> cnt{0, 0, 0};
-        for (int64_t p = ck * kRowChunk, pe = std::min(nt, p + kRowChunk); p < pe; ++p) {
+        for (int64_t p = std::max(ck * kRowChunk, H.row_b),
+                     pe = std::min({nt, ck * kRowChunk + kRowChunk, H.row_e});
+             p < pe; ++p) {
             const int32_t t = H.perm[p];
             for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) ++cnt[M.adj_case[a] - 1];
         }
@@ -1738,7 +1818,9 @@ void build_lists(bem_hmat_s &H)
     trace.mark("singular_count");
     parallel_tasks(nchunk, [&](int64_t ck) {
         std::array<int64_t, 3> pos = at[ck];
-        for (int64_t p = ck * kRowChunk, pe = std::min(nt, p + kRowChunk); p < pe; ++p) {
+        for (int64_t p = std::max(ck * kRowChunk, H.row_b),
+                     pe = std::min({nt, ck * kRowChunk + kRowChunk, H.row_e});
+             p < pe; ++p) {
             const int32_t t = H.perm[p];
             const int64_t l = leaf_of[p];
             const int64_t *b0 = nsb.data() + nptr[l], *b1 = nsb.data() + nptr[l + 1];
@@ -1832,6 +1914,7 @@ void upload_tree(bem_hmat_s &H, cudaStream_t st)
     H.d_toff.alloc((H.far.size() + 1) * sizeof(int64_t), st);
     H.d_tiles.alloc(aca_finish_tiles((int64_t)H.far.size()) * sizeof(int64_t), st);
     H.d_acastats.alloc(sizeof(AcaStats), st);
+    H.d_job.alloc(sizeof(AcaJob), st);
     CU(cudaStreamSynchronize(st));
 }
 
@@ -1846,7 +1929,7 @@ namespace bem {
 // Tree build on the host, uploads and geometry on stream st (none for
 // st == kHostOnly).
 int hmat_build_tree_impl(bem_mesh mesh, int32_t leaf_size, double eta, cudaStream_t st,
-                         bem_hmat *out, int32_t space)
+                         bem_hmat *out, int32_t space, int32_t n_parts, int32_t part)
 {
     return guarded([&]() -> int {
         if (!out) return fail(BEM_E_ARG, "out is null");
@@ -1870,9 +1953,33 @@ int hmat_build_tree_impl(bem_mesh mesh, int32_t leaf_size, double eta, cudaStrea
             H->rho3 = H->dofs == 1 ? g_quad.rho3 : 0.0;
             H->rho1 = H->dofs == 1 ? g_quad.rho1 : 0.0;
         }
+        if (n_parts < 1 || part < 0 || part >= n_parts)
+            return fail(BEM_E_ARG, "bad part of the row partition");
+        if (n_parts > 1 && space != BEM_P0)
+            return fail(BEM_E_ARG, "row partitions are for P0 handles");
         build_clusters(*H);
         const double t1 = now_ms();
         build_blocks(*H);
+        H->row_b = 0;
+        H->row_e = mesh->nt;
+        if (n_parts > 1) {
+            // this part's block rows: the partition of the whole block list
+            std::vector<int64_t> bl(5 * H->blocks.size()), bounds(n_parts + 1);
+            for (size_t b = 0; b < H->blocks.size(); ++b) {
+                const Cluster &T = H->cl[H->blocks[b].tau], &S = H->cl[H->blocks[b].sigma];
+                int64_t *r = bl.data() + 5 * b;
+                r[0] = T.b;
+                r[1] = T.e;
+                r[2] = S.b;
+                r[3] = S.e;
+                r[4] = H->blocks[b].adm ? 1 : 0;
+            }
+            partition_rows(bl.data(), (int64_t)H->blocks.size(), mesh->nt, n_parts, kPartRankEst,
+                           bounds.data());
+            H->row_b = bounds[part];
+            H->row_e = bounds[part + 1];
+            restrict_rows(*H);
+        }
         const double t2 = now_ms();
         build_lists(*H);
         const double t3 = now_ms();
@@ -1924,6 +2031,259 @@ void hmat_free_synced(bem_hmat H)
 
 }  // namespace bem
 
+namespace bem {
+
+// ---- stages of an assembly (hmat_assemble; the request server's launches
+// over several H-matrices) ---------------------------------------------------
+
+// Checks the arguments, records the key, allocates the near-field buffer and
+// sizes the factor pool (H->pool_want); nothing is launched.
+int assemble_begin(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec, cudaStream_t st)
+{
+    if (!H) return fail(BEM_E_ARG, "null hmat");
+    if (op < 0 || op > 3) return fail(BEM_E_ARG, "bad op");
+    if (op == BEM_HYPS && H->space != BEM_P1)
+        return fail(BEM_E_ARG, "the hypersingular operator needs a BEM_P1 handle");
+    if (prec != BEM_FP64 && prec != BEM_MIXED) return fail(BEM_E_ARG, "bad prec");
+    if (!(aca_eps > 0) || !std::isfinite(aca_eps)) return fail(BEM_E_ARG, "aca_eps must be > 0");
+    if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
+    const bool cplx = k != 0.0;
+    const size_t esz = cplx ? 16 : 8;
+    H->assembled = false;
+    H->op = op;
+    H->k = k;
+    H->eps = aca_eps;
+    H->prec = prec;
+    H->cplx = cplx;
+    if (!H->ev[0])
+        for (auto &e : H->ev) CU(cudaEventCreate(&e));
+    if (!H->pin_pool) {
+        CU(cudaMallocHost(&H->pin_pool, sizeof(Pool)));
+        CU(cudaMallocHost(&H->pin_stats, sizeof(AcaStats)));
+        CU(cudaMallocHost(&H->pin_job, sizeof(AcaJob)));
+    }
+    if (H->d_near_data.bytes < (size_t)H->near_total * esz)
+        H->d_near_data.alloc(H->near_total * esz, st);
+    int64_t sum_mn = 0;
+    for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
+    // factor pool: room for four chunks per admissible block, capped by
+    // what the device has free (less a margin for the product buffers);
+    // one chunk per block is the least that can work
+    int64_t want = sum_mn * KCHUNK * 4 + 1024;
+    {
+        size_t fr = 0, tot = 0;
+        // blocks cached in the library's pool are not free to the sizing:
+        // give them back first when the wish would not fit otherwise
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess &&
+            (double)want * esz > (double)fr + (double)H->d_pool.bytes - 4.0 * (1 << 30)) {
+            CU(cudaStreamSynchronize(st));
+            pool_trim();
+        }
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+            const double margin = 4.0 * (1 << 30) + 17.0 * H->ndof * esz;
+            const int64_t avail =
+                (int64_t)(((double)fr + (double)H->d_pool.bytes - margin) / (double)esz);
+            want = std::min(want, avail);
+            if (want < sum_mn * KCHUNK + 1024)
+                return fail(BEM_E_OOM, "not enough device memory for one " +
+                                           std::to_string(KCHUNK) + "-column chunk per block");
+        }
+    }
+    H->pool_want = std::max(want, H->pool_elems);
+    return BEM_OK;
+}
+
+// Allocates the factor pool at H->pool_want elements and uploads the
+// matrix's ACA job (stream-ordered before the launches that follow on st).
+void assemble_pool(bem_hmat H, cudaStream_t st)
+{
+    const size_t esz = H->cplx ? 16 : 8;
+    if (H->d_pool.bytes < (size_t)H->pool_want * esz) H->d_pool.alloc((size_t)H->pool_want * esz, st);
+    H->pool_elems = H->pool_want;
+    *H->pin_job = AcaJob{H->geom.g, H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
+                         H->d_pool.p, H->d_poolhdr.as<Pool>(), H->k, H->eps};
+    CU(cudaMemcpyAsync(H->d_job.p, H->pin_job, sizeof(AcaJob), cudaMemcpyHostToDevice, st));
+}
+
+static void record(cudaEvent_t e, cudaStream_t st, bool capturing)
+{
+    if (capturing) CU(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+    else CU(cudaEventRecord(e, st));
+}
+
+// Pool header, queue and totals reset; near field: regular pairs, then the
+// touching pairs (FP64).  Events 0 (start), 3 (after the regular pairs) and
+// 1 (end of the near field).
+void enqueue_near(bem_hmat H, cudaStream_t st, bool capturing)
+{
+    DeviceConsts &D = device_consts();
+    const int aop = H->op == BEM_HYPS ? BEM_SLP : H->op;
+    const double k = H->k;
+    const int prec = H->prec;
+    record(H->ev[0], st, capturing);
+    CU(launch_aca_reset(H->d_poolhdr.as<Pool>(), (unsigned long long)H->pool_elems,
+                        H->d_queue.as<AcaQueue>(), H->d_acastats.as<AcaStats>(), st));
+    if (H->dofs == 1) {
+        CU(launch_near_regular(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
+                               (int64_t)H->near.size(), H->d_near_data.p, st));
+        record(H->ev[3], st, capturing);
+        const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
+                                 H->d_sing[2].as<SingPair>()};
+        int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
+                         (int64_t)H->sing[2].size()};
+        CU(launch_singular(H->mesh->geom.g, D.sing, aop, k, sp, nullptr, hc, H->d_near_data.p, st));
+    } else {
+        CU(launch_near_dp1(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
+                           (int64_t)H->near.size(), H->d_near_data.p, st));
+        record(H->ev[3], st, capturing);
+        const SingPairL *sp[3] = {H->d_singl[0].as<SingPairL>(), H->d_singl[1].as<SingPairL>(),
+                                  H->d_singl[2].as<SingPairL>()};
+        int64_t hc[3] = {(int64_t)H->singl[0].size(), (int64_t)H->singl[1].size(),
+                         (int64_t)H->singl[2].size()};
+        CU(launch_singular_dp1(H->mesh->geom.g, D.sing, aop, k, sp, nullptr, hc, H->d_near_data.p,
+                               st));
+    }
+    record(H->ev[1], st, capturing);
+}
+
+// The persistent ACA over this matrix's admissible blocks alone.
+void enqueue_aca_own(bem_hmat H, cudaStream_t st)
+{
+    if (H->far.empty()) return;
+    DeviceConsts &D = device_consts();
+    const int aop = H->op == BEM_HYPS ? BEM_SLP : H->op;
+    AcaWork w{H->d_job.as<AcaJob>(), nullptr, H->n_big, H->n_small, H->n_tiny, H->max_m_big,
+              H->max_m_small};
+    CU(launch_aca(w, D.rule, aop, H->cplx, H->prec, H->d_queue.as<AcaQueue>(), D.num_sms, st,
+                  H->dofs, H->has_rules));
+}
+
+// Event 2 (end of the ACA), rank prefix sums and totals, and the readbacks
+// of the pool header and the totals.
+void enqueue_finish(bem_hmat H, cudaStream_t st, bool capturing)
+{
+    record(H->ev[2], st, capturing);
+    CU(launch_aca_finish(H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
+                         (int64_t)H->far.size(), H->d_toff.as<int64_t>(), H->d_tiles.as<int64_t>(),
+                         H->d_acastats.as<AcaStats>(), st));
+    CU(launch_long_offsets(H->d_far.as<FarBlock>(), H->d_long.as<int64_t>(),
+                           (int64_t)H->long_ids.size(), H->d_long_off.as<int64_t>(), st));
+    CU(cudaMemcpyAsync(H->pin_pool, H->d_poolhdr.p, sizeof(Pool), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(H->pin_stats, H->d_acastats.p, sizeof(AcaStats), cudaMemcpyDeviceToHost, st));
+}
+
+bool assemble_overflowed(bem_hmat H) { return H->pin_pool && H->pin_pool->overflow; }
+
+bool hmat_has_rules(bem_hmat H) { return H->has_rules; }
+
+int guarded_call(const std::function<int()> &f)
+{
+    return guarded([&]() -> int { return f(); });
+}
+
+// After the stream has synchronised without pool overflow: totals, phase
+// times, and the product's buffers.
+void assemble_end(bem_hmat H, cudaStream_t st)
+{
+    const size_t esz = H->cplx ? 16 : 8;
+    cudaEvent_t *ev = H->ev;
+    const AcaStats ast = *H->pin_stats;
+    float tn = 0, tf = 0, tr = 0;
+    CU(cudaEventElapsedTime(&tn, ev[0], ev[1]));
+    CU(cudaEventElapsedTime(&tf, ev[1], ev[2]));
+    CU(cudaEventElapsedTime(&tr, ev[0], ev[3]));
+    H->t_near = tn;
+    H->t_far = tf;
+    H->t_near_reg = tr;
+    H->far_entries = (int64_t)ast.entries;
+    H->rank_sum = (int64_t)ast.rank_sum;
+    H->capped = ast.capped;
+    H->rank_min = H->far.empty() ? 0 : ast.rank_min;
+    H->rank_max = ast.rank_max;
+    H->factor_elems = (int64_t)ast.factor_elems;
+    H->k2mn = (int64_t)ast.k2mn;
+    H->rank_mn = (int64_t)ast.rank_mn;
+    H->far_result_valid = false;
+    const int64_t nd = H->ndof;
+    if (H->d_xt.bytes < nd * esz) {
+        H->d_xt.alloc(nd * esz, st);
+        H->d_yt.alloc(nd * esz, st);
+    }
+    if (H->space == BEM_P1) {
+        // transformed vectors of the products: six DP1 vectors in and out
+        // (three curl components and three normal components, Eq. (9));
+        // one of each for SLP, DLP and ADLP
+        const size_t want_v = (size_t)(H->op == BEM_HYPS ? 6 : 1) * nd * esz;
+        if (H->d_xs.bytes < want_v) {
+            H->d_xs.alloc(want_v, st);
+            H->d_ys.alloc(want_v, st);
+        }
+    }
+    if (H->d_tbuf.bytes < (size_t)(H->rank_sum + 1) * esz)
+        H->d_tbuf.alloc((size_t)(H->rank_sum + 1) * esz * 5 / 4, st);
+    H->assembled = true;
+}
+
+// One persistent ACA launch over the admissible blocks of several
+// H-matrices (P0, the same operator, precision and number type, all past
+// assemble_pool and enqueue_near on st): the blocks of each work shape from
+// every matrix, merged longest first, each item naming its matrix's job.
+int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st)
+{
+    if (hs.empty()) return BEM_OK;
+    DeviceConsts &D = device_consts();
+    const bem_hmat H0 = hs[0];
+    const int aop = H0->op == BEM_HYPS ? BEM_SLP : H0->op;
+    std::vector<AcaJob> jobs;
+    struct It {
+        int64_t size, item;
+    };
+    std::vector<It> cls[3];
+    int64_t max_big = 0, max_small = 0;
+    for (size_t j = 0; j < hs.size(); ++j) {
+        const bem_hmat H = hs[j];
+        if (H->dofs != 1 || H->op != H0->op || H->cplx != H0->cplx || H->prec != H0->prec ||
+            H->has_rules != H0->has_rules)
+            return fail(BEM_E_ARG, "fused ACA launch over different kinds of matrices");
+        jobs.push_back(*H->pin_job);
+        const int64_t n[3] = {H->n_big, H->n_small, H->n_tiny};
+        int64_t f = 0;
+        for (int c = 0; c < 3; ++c)
+            for (int64_t e = f + n[c]; f < e; ++f) {
+                const FarBlock &F = H->far[f];
+                cls[c].push_back({(F.te - F.tb) + (F.se - F.sb), ((int64_t)j << kItemShift) | f});
+            }
+        max_big = std::max(max_big, H->max_m_big);
+        max_small = std::max(max_small, H->max_m_small);
+    }
+    std::vector<int64_t> items;
+    for (auto &c : cls) {
+        std::stable_sort(c.begin(), c.end(), [](const It &a, const It &b) { return a.size > b.size; });
+        for (const It &i : c) items.push_back(i.item);
+    }
+    if (items.empty()) return BEM_OK;
+    const size_t jb = (jobs.size() * sizeof(AcaJob) + 255) / 256 * 256;
+    const size_t ib = items.size() * sizeof(int64_t);
+    void *buf = nullptr;
+    CU(lib_malloc_async(&buf, jb + ib + sizeof(AcaQueue), st));
+    char *b = (char *)buf;
+    AcaQueue *Q = (AcaQueue *)(b + jb + ib);
+    cudaError_t e = cudaMemcpyAsync(b, jobs.data(), jobs.size() * sizeof(AcaJob),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + jb, items.data(), ib, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Q, 0, sizeof(AcaQueue), st);
+    if (e == cudaSuccess) {
+        AcaWork w{(const AcaJob *)b, (const int64_t *)(b + jb), (int64_t)cls[0].size(),
+                  (int64_t)cls[1].size(), (int64_t)cls[2].size(), max_big, max_small};
+        e = launch_aca(w, D.rule, aop, H0->cplx, H0->prec, Q, D.num_sms, st, 1, H0->has_rules);
+    }
+    cudaFreeAsync(buf, st);
+    CU(e);
+    return BEM_OK;
+}
+
+}  // namespace bem
+
 extern "C" {
 
 int hmat_build_tree(bem_mesh mesh, int32_t leaf_size, double eta, bem_hmat *out)
@@ -1937,6 +2297,36 @@ int hmat_build_tree_space(bem_mesh mesh, int32_t leaf_size, double eta, int32_t 
     return hmat_build_tree_impl(mesh, leaf_size, eta, 0, out, space);
 }
 
+int hmat_build_tree_part(bem_mesh mesh, int32_t leaf_size, double eta, int32_t n_parts,
+                         int32_t part, bem_hmat *out)
+{
+    return hmat_build_tree_impl(mesh, leaf_size, eta, 0, out, BEM_P0, n_parts, part);
+}
+
+int hmat_part_rows(bem_hmat H, int64_t *row_begin, int64_t *row_end)
+{
+    if (!H || !row_begin || !row_end) return fail(BEM_E_ARG, "null argument");
+    *row_begin = H->row_b * H->dofs;
+    *row_end = (H->row_e < 0 ? H->mesh->nt : H->row_e) * H->dofs;
+    return BEM_OK;
+}
+
+int bem_partition_rows(const int64_t *blocks, int64_t n_blocks, int64_t n_rows, int32_t n_parts,
+                       double rank_est, int64_t *bounds)
+{
+    return guarded([&]() -> int {
+        if (!blocks || !bounds || n_blocks < 0 || n_rows < 0 || n_parts < 1 || !(rank_est > 0))
+            return fail(BEM_E_ARG, "bad partition arguments");
+        for (int64_t b = 0; b < n_blocks; ++b) {
+            const int64_t *r = blocks + 5 * b;
+            if (r[0] < 0 || r[1] > n_rows || r[0] > r[1] || r[2] > r[3])
+                return fail(BEM_E_ARG, "block outside the rows");
+        }
+        partition_rows(blocks, n_blocks, n_rows, n_parts, rank_est, bounds);
+        return BEM_OK;
+    });
+}
+
 int64_t hmat_dofs(bem_hmat H)
 {
     if (!H) return -1;
@@ -1946,119 +2336,23 @@ int64_t hmat_dofs(bem_hmat H)
 int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec, void *cuda_stream)
 {
     return guarded([&]() -> int {
-        if (!H) return fail(BEM_E_ARG, "null hmat");
-        if (op < 0 || op > 3) return fail(BEM_E_ARG, "bad op");
-        if (op == BEM_HYPS && H->space != BEM_P1)
-            return fail(BEM_E_ARG, "the hypersingular operator needs a BEM_P1 handle");
-        if (prec != BEM_FP64 && prec != BEM_MIXED) return fail(BEM_E_ARG, "bad prec");
-        if (!(aca_eps > 0) || !std::isfinite(aca_eps)) return fail(BEM_E_ARG, "aca_eps must be > 0");
-        if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
         cudaStream_t st = (cudaStream_t)cuda_stream;
-        // the hypersingular operator is applied through the single layer on
-        // DP1 (Eq. (9)): that is the matrix assembled here
-        const int aop = op == BEM_HYPS ? BEM_SLP : op;
-        DeviceConsts &D = device_consts();
-        const bool cplx = k != 0.0;
-        const size_t esz = cplx ? 16 : 8;
-        H->assembled = false;
-        H->op = op;
-        H->k = k;
-        H->eps = aca_eps;
-        H->prec = prec;
-        H->cplx = cplx;
-        if (!H->ev[0])
-            for (auto &e : H->ev) CU(cudaEventCreate(&e));
-        if (!H->pin_pool) {
-            CU(cudaMallocHost(&H->pin_pool, sizeof(Pool)));
-            CU(cudaMallocHost(&H->pin_stats, sizeof(AcaStats)));
-        }
-        cudaEvent_t *ev = H->ev;
+        int rc = assemble_begin(H, op, k, aca_eps, prec, st);
+        if (rc != BEM_OK) return rc;
         bool use_graphs;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             use_graphs = g_tuning.use_graphs != 0;
         }
-        if (H->d_near_data.bytes < (size_t)H->near_total * esz)
-            H->d_near_data.alloc(H->near_total * esz, st);
-        int64_t sum_mn = 0;
-        for (const FarBlock &F : H->far) sum_mn += (F.te - F.tb) + (F.se - F.sb);
-        // factor pool: room for four chunks per admissible block, capped by
-        // what the device has free (less a margin for the product buffers);
-        // one chunk per block is the least that can work
-        int64_t want = sum_mn * KCHUNK * 4 + 1024;
-        {
-            size_t fr = 0, tot = 0;
-            // blocks cached in the library's pool are not free to the sizing:
-            // give them back first when the wish would not fit otherwise
-            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess &&
-                (double)want * esz > (double)fr + (double)H->d_pool.bytes - 4.0 * (1 << 30)) {
-                CU(cudaStreamSynchronize(st));
-                pool_trim();
-            }
-            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-                const double margin = 4.0 * (1 << 30) + 17.0 * H->ndof * esz;
-                const int64_t avail =
-                    (int64_t)(((double)fr + (double)H->d_pool.bytes - margin) / (double)esz);
-                want = std::min(want, avail);
-                if (want < sum_mn * KCHUNK + 1024)
-                    return fail(BEM_E_OOM, "not enough device memory for one " +
-                                               std::to_string(KCHUNK) + "-column chunk per block");
-            }
-        }
-        want = std::max(want, H->pool_elems);
         // the whole sequence: near field (regular, then singular pairs, FP64),
         // then the persistent ACA over all admissible blocks and its totals
-        // timing events become event-record nodes when the sequence is captured
-        auto enqueue = [&](cudaStream_t st, bool capturing) {
-            auto rec = [&](cudaEvent_t e) {
-                if (capturing) CU(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
-                else CU(cudaEventRecord(e, st));
-            };
-            rec(ev[0]);
-            CU(launch_aca_reset(H->d_poolhdr.as<Pool>(), (unsigned long long)H->pool_elems,
-                                H->d_queue.as<AcaQueue>(), H->d_acastats.as<AcaStats>(), st));
-            if (H->dofs == 1) {
-                CU(launch_near_regular(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
-                                       (int64_t)H->near.size(), H->d_near_data.p, st));
-                rec(ev[3]);
-                const SingPair *sp[3] = {H->d_sing[0].as<SingPair>(), H->d_sing[1].as<SingPair>(),
-                                         H->d_sing[2].as<SingPair>()};
-                int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
-                                 (int64_t)H->sing[2].size()};
-                CU(launch_singular(H->mesh->geom.g, D.sing, aop, k, sp, nullptr, hc,
-                                   H->d_near_data.p, st));
-            } else {
-                CU(launch_near_dp1(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
-                                   (int64_t)H->near.size(), H->d_near_data.p, st));
-                rec(ev[3]);
-                const SingPairL *sp[3] = {H->d_singl[0].as<SingPairL>(),
-                                          H->d_singl[1].as<SingPairL>(),
-                                          H->d_singl[2].as<SingPairL>()};
-                int64_t hc[3] = {(int64_t)H->singl[0].size(), (int64_t)H->singl[1].size(),
-                                 (int64_t)H->singl[2].size()};
-                CU(launch_singular_dp1(H->mesh->geom.g, D.sing, aop, k, sp, nullptr, hc,
-                                       H->d_near_data.p, st));
-            }
-            rec(ev[1]);
-            if (!H->far.empty())
-                CU(launch_aca(H->geom.g, D.rule, aop, k, prec, aca_eps, H->d_far.as<FarBlock>(),
-                              H->d_chunks.as<FarChunks>(), H->n_big, H->n_small, H->n_tiny, H->max_m_big, H->max_m_small,
-                              H->d_pool.p, H->d_poolhdr.as<Pool>(), H->d_queue.as<AcaQueue>(),
-                              D.num_sms, st, H->dofs, H->has_rules));
-            rec(ev[2]);
-            CU(launch_aca_finish(H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
-                                 (int64_t)H->far.size(),
-                                 H->d_toff.as<int64_t>(), H->d_tiles.as<int64_t>(),
-                                 H->d_acastats.as<AcaStats>(), st));
-            CU(launch_long_offsets(H->d_far.as<FarBlock>(), H->d_long.as<int64_t>(),
-                                   (int64_t)H->long_ids.size(), H->d_long_off.as<int64_t>(), st));
-            CU(cudaMemcpyAsync(H->pin_pool, H->d_poolhdr.p, sizeof(Pool), cudaMemcpyDeviceToHost, st));
-            CU(cudaMemcpyAsync(H->pin_stats, H->d_acastats.p, sizeof(AcaStats),
-                               cudaMemcpyDeviceToHost, st));
+        auto enqueue = [&](cudaStream_t s, bool capturing) {
+            enqueue_near(H, s, capturing);
+            enqueue_aca_own(H, s);
+            enqueue_finish(H, s, capturing);
         };
         for (int attempt = 0;; ++attempt) {
-            if (H->d_pool.bytes < (size_t)want * esz) H->d_pool.alloc((size_t)want * esz, st);
-            H->pool_elems = want;
+            assemble_pool(H, st);
             // the first assembly with a given key runs eagerly; the second
             // captures the sequence into a graph, later ones replay it
             const bool same = H->g_op == op && H->g_prec == prec && H->g_k == k &&
@@ -2108,43 +2402,9 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
             CU(cudaStreamSynchronize(st));
             if (!H->pin_pool->overflow) break;
             if (attempt >= 6) return fail(BEM_E_OOM, "ACA factor pool keeps overflowing");
-            want *= 2;
+            H->pool_want *= 2;
         }
-        const AcaStats ast = *H->pin_stats;
-        float tn = 0, tf = 0, tr = 0;
-        CU(cudaEventElapsedTime(&tn, ev[0], ev[1]));
-        CU(cudaEventElapsedTime(&tf, ev[1], ev[2]));
-        CU(cudaEventElapsedTime(&tr, ev[0], ev[3]));
-        H->t_near = tn;
-        H->t_far = tf;
-        H->t_near_reg = tr;
-        H->far_entries = (int64_t)ast.entries;
-        H->rank_sum = (int64_t)ast.rank_sum;
-        H->capped = ast.capped;
-        H->rank_min = H->far.empty() ? 0 : ast.rank_min;
-        H->rank_max = ast.rank_max;
-        H->factor_elems = (int64_t)ast.factor_elems;
-        H->k2mn = (int64_t)ast.k2mn;
-        H->rank_mn = (int64_t)ast.rank_mn;
-        H->far_result_valid = false;
-        const int64_t nd = H->ndof;
-        if (H->d_xt.bytes < nd * esz) {
-            H->d_xt.alloc(nd * esz, st);
-            H->d_yt.alloc(nd * esz, st);
-        }
-        if (H->space == BEM_P1) {
-            // transformed vectors of the products: six DP1 vectors in and out
-            // (three curl components and three normal components, Eq. (9));
-            // one of each for SLP, DLP and ADLP
-            const size_t want_v = (size_t)(op == BEM_HYPS ? 6 : 1) * nd * esz;
-            if (H->d_xs.bytes < want_v) {
-                H->d_xs.alloc(want_v, st);
-                H->d_ys.alloc(want_v, st);
-            }
-        }
-        if (H->d_tbuf.bytes < (size_t)(H->rank_sum + 1) * esz)
-            H->d_tbuf.alloc((size_t)(H->rank_sum + 1) * esz * 5 / 4, st);
-        H->assembled = true;
+        assemble_end(H, st);
         return BEM_OK;
     });
 }

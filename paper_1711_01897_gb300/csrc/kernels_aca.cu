@@ -188,37 +188,21 @@ cudaError_t launch_aca_finish(const FarBlock *far, const FarChunks *chunks, int6
     return cudaGetLastError();
 }
 
-cudaError_t launch_aca(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
-                       double eps, FarBlock *blocks, FarChunks *chunks, int64_t n_big,
-                       int64_t n_small, int64_t n_tiny, int64_t max_m_big, int64_t max_m_small, void *pool_data,
-                       Pool *pool, AcaQueue *queue, int num_sms, cudaStream_t st, int dofs,
-                       bool rules)
+cudaError_t launch_aca(const AcaWork &w, const QuadRule &rule, int op, bool cplx, int prec,
+                       AcaQueue *queue, int num_sms, cudaStream_t st, int dofs, bool rules)
 {
-    if (dofs == 3)
-        return launch_aca_dp1(g, rule, op, k, prec, eps, blocks, chunks, n_big, n_small,
-                              max_m_big, max_m_small, pool_data, pool, queue, num_sms, st);
+    if (dofs == 3) return launch_aca_dp1(w, rule, op, cplx, prec, queue, num_sms, st);
     if (dofs != 1) return cudaErrorInvalidValue;
-    const bool cplx = k != 0.0;
     // trees with lower-order distance classes: the mixed Laplace kernels that
     // read each block's rule
     if (rules && !cplx && prec == 1) {
-        if (op == 0)
-            return aca_launch<0, false, 1, 1, true>(g, rule, k, eps, blocks, chunks, n_big, n_small,
-                                                    n_tiny, max_m_big, max_m_small, pool_data, pool,
-                                                    queue, num_sms, st);
-        if (op == 1)
-            return aca_launch<1, false, 1, 1, true>(g, rule, k, eps, blocks, chunks, n_big, n_small,
-                                                    n_tiny, max_m_big, max_m_small, pool_data, pool,
-                                                    queue, num_sms, st);
-        if (op == 2)
-            return aca_launch<2, false, 1, 1, true>(g, rule, k, eps, blocks, chunks, n_big, n_small,
-                                                    n_tiny, max_m_big, max_m_small, pool_data, pool,
-                                                    queue, num_sms, st);
+        if (op == 0) return aca_launch<0, false, 1, 1, true>(w, rule, queue, num_sms, st);
+        if (op == 1) return aca_launch<1, false, 1, 1, true>(w, rule, queue, num_sms, st);
+        if (op == 2) return aca_launch<2, false, 1, 1, true>(w, rule, queue, num_sms, st);
     }
-#define BEM_ACA(O, C, Pp)                                                                     \
-    if (op == O && cplx == C && prec == Pp)                                                   \
-        return aca_launch<O, C, Pp, 1>(g, rule, k, eps, blocks, chunks, n_big, n_small, n_tiny,       \
-                                       max_m_big, max_m_small, pool_data, pool, queue, num_sms, st);
+#define BEM_ACA(O, C, Pp)                                   \
+    if (op == O && cplx == C && prec == Pp)                 \
+        return aca_launch<O, C, Pp, 1>(w, rule, queue, num_sms, st);
     BEM_ACA(0, false, 0) BEM_ACA(0, false, 1) BEM_ACA(0, true, 0) BEM_ACA(0, true, 1)
     BEM_ACA(1, false, 0) BEM_ACA(1, false, 1) BEM_ACA(1, true, 0) BEM_ACA(1, true, 1)
     BEM_ACA(2, false, 0) BEM_ACA(2, false, 1) BEM_ACA(2, true, 0) BEM_ACA(2, true, 1)

@@ -1,6 +1,9 @@
 """Request server on the GPU: results are identical alone and in a mix of
 concurrent requests (each request's arithmetic does not depend on what runs
-beside it), the HBM budget is respected, and products match the oracle."""
+beside it, even when its blocks share one persistent ACA launch with other
+requests' blocks), the HBM budget is respected, products match the oracle,
+and product-only requests against resident matrices give the same result
+as the assembly that left the matrix there."""
 import numpy as np
 import pytest
 
@@ -29,7 +32,7 @@ def _requests():
     return reqs
 
 
-def _run(reqs, slots, budget):
+def _run(reqs, slots, budget, reuse=False):
     srv = bem.Server(budget, max_slots=slots)
     ids = [srv.submit(r["V"], r["T"], r["x"], op=bem.SLP, k=r["k"], aca_eps=r["eps"],
                       prec=bem.MIXED, leaf_size=16, eta=1.2) for r in reqs]
@@ -38,9 +41,18 @@ def _run(reqs, slots, budget):
         rc, info, y = srv.wait(i)
         assert rc == 0, bem.bem_last_error()
         out.append((y, info))
+    again = []
+    if reuse:
+        # the same vectors again, as products against the resident matrices
+        for i, r in zip(ids, reqs):
+            p = srv.submit_product(i, r["x"])
+            rc, info, y = srv.wait(p)
+            assert rc == 0, bem.bem_last_error()
+            assert info.reused == 1
+            again.append(y)
     st = srv.stats()
     srv.close()
-    return out, st
+    return out, st, again
 
 
 def test_alone_and_mixed_identical_and_budget():
@@ -48,11 +60,17 @@ def test_alone_and_mixed_identical_and_budget():
     assert torch.cuda.is_available()
     torch.cuda.init()
     reqs = _requests()
-    alone, _ = _run(reqs, 1, 64 << 30)
+    alone, st1, again = _run(reqs, 1, 64 << 30, reuse=True)
+    assert st1["max_launch_requests"] == 1 and st1["reuse_hits"] == len(reqs)
+    for (ya, _), yr in zip(alone, again):
+        assert np.array_equal(ya, yr)
     budget = 3 * max(info.reserved_bytes for _, info in alone)
-    mixed, st = _run(reqs, 4, budget)
+    mixed, st, _ = _run(reqs, 4, budget)
     assert st["peak_reserved_bytes"] <= budget
     assert st["completed"] == len(reqs)
+    # requests of the same kind shared ACA launches
+    assert st["max_launch_requests"] >= 2, st
+    assert any(info.launch_requests >= 2 for _, info in mixed)
     for (ya, ia), (ym, im) in zip(alone, mixed):
         assert np.array_equal(ya, ym)
         assert ia.integrals == im.integrals and ia.integrals > 0

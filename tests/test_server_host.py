@@ -88,3 +88,62 @@ def test_bad_requests_rejected(lib):
     with pytest.raises(bem.BemError):
         srv.submit(V, T, np.zeros(T.shape[0]), op=5)
     srv.close()
+
+
+def test_batches_share_launches(lib):
+    """Requests admitted while a batch runs go into the next batch together:
+    one (simulated) ACA launch holds several requests."""
+    V, T = _mesh(8)
+    srv = bem.Server(16 * 1024 * 1280, max_slots=8, dry_run=True)
+    ids = [srv.submit(V, T, np.full(T.shape[0], float(i)), dry_run_ms=60) for i in range(8)]
+    for i, rid in enumerate(ids):
+        rc, info, y = srv.wait(rid)
+        assert rc == 0 and np.all(y == float(i))
+        assert info.launch_requests >= 1 and info.reused == 0
+    st = srv.stats()
+    assert st["max_launch_requests"] >= 2
+    assert st["aca_launch_requests"] == len(ids)
+    assert st["aca_launches"] < len(ids)
+    srv.close()
+
+
+def test_resident_reuse_and_eviction(lib):
+    """A finished request's matrix stays resident (its bytes stay reserved);
+    a product-only request naming it runs without assembling; admissions that
+    need the bytes evict it, after which naming it fails with BEM_E_STATE."""
+    V, T = _mesh(8)
+    per = 1024 * T.shape[0]
+    srv = bem.Server(2 * per, max_slots=2, dry_run=True)
+    a = srv.submit(V, T, np.ones(T.shape[0]), dry_run_ms=5)
+    rc, info, _ = srv.wait(a)
+    assert rc == 0
+    st = srv.stats()
+    assert st["resident"] == 1 and st["resident_bytes"] == per and st["reserved_bytes"] == per
+    p = srv.submit_product(a, np.arange(T.shape[0], dtype=float))
+    rc, info, y = srv.wait(p)
+    assert rc == 0 and info.reused == 1 and info.launch_requests == 0
+    assert np.array_equal(y, np.arange(T.shape[0], dtype=float))
+    assert srv.stats()["reuse_hits"] == 1
+    # two more requests need the whole budget: the idle resident one goes
+    b = srv.submit(V, T, np.zeros(T.shape[0]), dry_run_ms=5)
+    c = srv.submit(V, T, np.zeros(T.shape[0]), dry_run_ms=5)
+    assert srv.wait(b)[0] == 0 and srv.wait(c)[0] == 0
+    st = srv.stats()
+    assert st["evictions"] >= 1 and st["peak_reserved_bytes"] <= 2 * per
+    with pytest.raises(bem.BemError) as e:
+        srv.submit_product(a, np.zeros(T.shape[0]))
+    assert e.value.status == 6
+    srv.close()
+
+
+def test_product_waits_for_its_assembly(lib):
+    """A product request submitted while the assembly it names is still
+    running waits for it and then reuses it."""
+    V, T = _mesh(8)
+    srv = bem.Server(4 * 1024 * T.shape[0], max_slots=2, dry_run=True)
+    a = srv.submit(V, T, np.ones(T.shape[0]), dry_run_ms=80)
+    p = srv.submit_product(a, np.full(T.shape[0], 2.0))
+    rc, info, y = srv.wait(p)
+    assert rc == 0 and info.reused == 1 and np.all(y == 2.0)
+    assert srv.poll(a).state == bem.DONE
+    srv.close()
