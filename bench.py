@@ -670,7 +670,6 @@ def serving_record(args, nreq: int, calib: int):
     rate = args.load * cap
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
     ids = [None] * nreq
-    prods = {}
     st0 = srv.stats()
     clk = Clocks(0)
     clk.start()
@@ -682,12 +681,10 @@ def serving_record(args, nreq: int, calib: int):
             if dt > 0:
                 time.sleep(dt)
             ids[i] = srv.submit(r["V"], r["T"], r["x"], k=r["k"], aca_eps=r["eps"])
-            if i % 10 == 5:
-                prods[i] = srv.submit_product(ids[i], r["x"])
 
     th = threading.Thread(target=submitter)
     th.start()
-    lat, lat_prod, ints, fails, shared, mism = [], [], 0, 0, [], 0
+    lat, lat_prod, ints, fails, shared, mism, sizes = [], [], 0, 0, [], 0, []
     for i in range(nreq):
         while ids[i] is None:
             time.sleep(0.0005)
@@ -696,12 +693,13 @@ def serving_record(args, nreq: int, calib: int):
             fails += 1
             continue
         lat.append(info.t_done_ms - info.t_submit_ms)
+        sizes.append(reqs[i]["T"].shape[0])
         ints += info.integrals
         shared.append(info.launch_requests)
         if i % 10 == 5:
-            while i not in prods:
-                time.sleep(0.0005)
-            rc2, info2, y2 = srv.wait(prods[i])
+            # a product-only request against the matrix this one left resident
+            p = srv.submit_product(ids[i], reqs[i]["x"])
+            rc2, info2, y2 = srv.wait(p)
             if rc2 == 0:
                 lat_prod.append(info2.t_done_ms - info2.t_submit_ms)
                 mism += int(not np.array_equal(y, y2))
@@ -711,15 +709,23 @@ def serving_record(args, nreq: int, calib: int):
     srv.close()
     clocks = clk.stop()
     lat = np.array(lat)
+    sizes = np.array(sizes)
+    by_size = {}
+    for name, sel in (("below_40k_triangles", sizes < 40000), ("from_40k_triangles", sizes >= 40000)):
+        if sel.any():
+            by_size[name] = {"count": int(sel.sum()), "p50": float(np.percentile(lat[sel], 50)),
+                             "p99": float(np.percentile(lat[sel], 99))}
     return {
         "config": {"workload": "serving: Poisson stream, 1k-200k triangles, 50% Laplace / 50% "
                                "Helmholtz SLP k~U[1,20], eps in {1e-4,1e-6}, assemble + 1 matvec; "
-                               "every 10th followed by a product on its resident matrix",
+                               "after every 10th completes, a product-only request on its resident "
+                               "matrix",
                    "requests": nreq, "slots": args.slots, "hbm_budget_gb": args.hbm_budget_gb,
                    "offered_load": args.load, "capacity_req_per_s": cap},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(lat.mean()),
                        "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50))},
+        "latency_ms_by_size": by_size,
         "product_only_latency_ms": ({"p50": float(np.percentile(lat_prod, 50)),
                                      "p99": float(np.percentile(lat_prod, 99)),
                                      "count": len(lat_prod), "differ_from_assembly": mism}

@@ -121,7 +121,9 @@ int bem_debug_recip(const double *x, double *y, int64_t n, void *cuda_stream);
  * an H-matrix is assembled (graphs).  The numerical results do not depend on
  * it (up to ACA pivot near-ties, which rounding decides).
  *  warp_max_rows  admissible blocks with max(m, n) <= this are compressed by
- *                 one warp each, larger ones by a whole CTA (1..8192)
+ *                 warps, larger ones by a whole CTA (1..8192); a block of at
+ *                 most 80 rows takes half a warp (two blocks per warp), of at
+ *                 most 40 rows a quarter warp (four per warp)
  *  lane_max_rows  ... and those with max(m, n) <= this by one lane each,
  *                 32 blocks per warp (0 = off, at most 64)
  *  use_graphs     1: the kernel sequence of hmat_assemble is captured into a
@@ -352,6 +354,8 @@ typedef struct {
     int64_t n_blocks_cta;        /* admissible blocks by ACA work shape (bem_tuning at tree   */
     int64_t n_blocks_warp;       /* build): a whole CTA per block, warps (a warp holds one or */
     int64_t n_blocks_lane;       /* several blocks), one lane per block                       */
+    int64_t n_blocks_half_warp;  /* ... of n_blocks_warp: blocks of at most 80 rows on 16    */
+    int64_t n_blocks_quarter_warp; /* lanes (two per warp), of at most 40 on 8 (four per warp) */
 } bem_hmat_stats;
 
 /* Copies statistics of the handle into *out. */

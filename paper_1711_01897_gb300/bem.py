@@ -54,7 +54,8 @@ class HmatStats(ctypes.Structure):
                 ("n_blocks_rule3", ctypes.c_int64), ("n_blocks_rule1", ctypes.c_int64),
                 ("rho3", ctypes.c_double), ("rho1", ctypes.c_double),
                 ("n_blocks_cta", ctypes.c_int64), ("n_blocks_warp", ctypes.c_int64),
-                ("n_blocks_lane", ctypes.c_int64)]
+                ("n_blocks_lane", ctypes.c_int64), ("n_blocks_half_warp", ctypes.c_int64),
+                ("n_blocks_quarter_warp", ctypes.c_int64)]
 
 
 class Peaks(ctypes.Structure):

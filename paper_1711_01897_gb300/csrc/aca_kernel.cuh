@@ -3,6 +3,7 @@
 // kernels_aca.cu for the algorithm and its readings.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "bem_dp1.cuh"
@@ -63,9 +64,10 @@ struct VT<false> {
     static __device__ __forceinline__ T inv(T a) { return recip(a); }
     static __device__ __forceinline__ T dotc(T a, T b, T acc) { return fma(a, b, acc); }  // conj(a) b
     static __device__ __forceinline__ double re_mul(T a, T b) { return a * b; }
-    static __device__ __forceinline__ T shfl_down(T a, int o)
+    static __device__ __forceinline__ T shfl_down(T a, int o, unsigned mask = 0xffffffffu,
+                                                  int width = 32)
     {
-        return __shfl_down_sync(0xffffffffu, a, o);
+        return __shfl_down_sync(mask, a, o, width);
     }
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
 };
@@ -107,10 +109,11 @@ struct VT<true> {
         return make_double2(acc.x + fma(a.x, b.x, a.y * b.y), acc.y + fma(a.x, b.y, -a.y * b.x));
     }
     static __device__ __forceinline__ double re_mul(T a, T b) { return fma(a.x, b.x, -a.y * b.y); }
-    static __device__ __forceinline__ T shfl_down(T a, int o)
+    static __device__ __forceinline__ T shfl_down(T a, int o, unsigned mask = 0xffffffffu,
+                                                  int width = 32)
     {
-        return make_double2(__shfl_down_sync(0xffffffffu, a.x, o),
-                            __shfl_down_sync(0xffffffffu, a.y, o));
+        return make_double2(__shfl_down_sync(mask, a.x, o, width),
+                            __shfl_down_sync(mask, a.y, o, width));
     }
     static __device__ __forceinline__ T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
 };
@@ -162,24 +165,49 @@ __device__ __forceinline__ void warp_argmax_key(long long &key, int64_t &idx)
     idx = __shfl_sync(0xffffffffu, idx, 0);
 }
 
-struct WarpGroup {
-    int lane;
+// W consecutive lanes of a warp working on one block (W = 32: the whole
+// warp; 16 or 8: two or four blocks per warp).  Reductions are shuffle trees
+// within the group's lanes; mask names them, so that the groups of a warp may
+// part ways when their blocks need different numbers of steps.
+template <int W>
+struct SubGroup {
+    static constexpr bool kShuffle = true;
+    int lane;        // 0 .. W - 1
+    unsigned mask;   // the group's lanes in the warp
     __device__ int rank() const { return lane; }
-    __device__ int size() const { return 32; }
-    __device__ int warp() const { return 0; }
-    __device__ int nwarps() const { return 1; }
-    __device__ void sync() const { __syncwarp(); }
-    __device__ void argmax(double &v, int64_t &idx) const { warp_argmax(v, idx); }
-    __device__ void argmax_key(long long &key, int64_t &idx) const { warp_argmax_key(key, idx); }
-    __device__ void sum2(double &a, double &b) const
+    __device__ int size() const { return W; }
+    __device__ void sync() const { __syncwarp(mask); }
+    __device__ void argmax_key(long long &key, int64_t &idx) const
     {
-        a = warp_sum(a);
-        b = warp_sum(b);
+#pragma unroll
+        for (int o = W / 2; o > 0; o >>= 1) {
+            long long ok = __shfl_down_sync(mask, key, o, W);
+            int64_t oi = __shfl_down_sync(mask, idx, o, W);
+            if (ok > key || (ok == key && oi < idx)) {
+                key = ok;
+                idx = oi;
+            }
+        }
+        key = __shfl_sync(mask, key, 0, W);
+        idx = __shfl_sync(mask, idx, 0, W);
     }
-    __device__ double sum(double a) const { return warp_sum(a); }
+    __device__ double sum(double a) const
+    {
+#pragma unroll
+        for (int o = W / 2; o > 0; o >>= 1) a += __shfl_down_sync(mask, a, o, W);
+        return __shfl_sync(mask, a, 0, W);
+    }
+    template <class V>
+    __device__ typename V::T shfl_down(typename V::T a, int o) const
+    {
+        return V::shfl_down(a, o, mask, W);
+    }
+    __device__ double shfl_idx(double a, int src) const { return __shfl_sync(mask, a, src, W); }
 };
+using WarpGroup = SubGroup<32>;
 
 struct CtaGroup {
+    static constexpr bool kShuffle = false;
     RedScratch *red;
     __device__ int rank() const { return threadIdx.x; }
     __device__ int size() const { return blockDim.x; }
@@ -254,14 +282,26 @@ struct CtaGroup {
     }
 };
 
-// Per-group shared state.
-template <bool CPLX>
+// Per-group shared state, for blocks of rank at most CAP (the rank cap
+// min(m, n, KMAX) of the blocks the group takes).
+template <bool CPLX, int CAP = KMAX>
 struct GroupSmem {
-    typename VT<CPLX>::T cu[KMAX];   // (u_l)_i of the current row / (v_l)_j of the column
-    int64_t chunk[NCHUNK];
+    static constexpr int kCap = CAP, kChunks = (CAP + KCHUNK - 1) / KCHUNK;
+    typename VT<CPLX>::T cu[CAP];   // (u_l)_i of the current row / (v_l)_j of the column
+    int64_t chunk[kChunks];
     int64_t scal;                   // broadcast slot
     double uv2;                     // ||u_k||^2 ||v_k||^2 of the current step
     int fail;
+};
+
+// Shared bytes per warp: one full-rank group, or two groups for blocks of at
+// most kSub16Max rows, or four for at most kSub8Max rows.
+template <bool CPLX>
+struct GroupArea {
+    static constexpr size_t a = sizeof(GroupSmem<CPLX, KMAX>),
+                            b = 2 * sizeof(GroupSmem<CPLX, kSub16Max>),
+                            c = 4 * sizeof(GroupSmem<CPLX, kSub8Max>);
+    static constexpr size_t bytes = ((a > b ? (a > c ? a : c) : (b > c ? b : c)) + 15) / 16 * 16;
 };
 
 // DOF = 1: a dof per triangle (P0).  DOF = 3: the three local dofs of each
@@ -279,10 +319,10 @@ __device__ __forceinline__ C2 eval_entry(const typename E::Tri &a, const typenam
     else return E::eval(a, b, R, k);
 }
 
-template <class Grp, int OP, bool CPLX, int PREC, int DOF = 1, bool RULES = false>
+template <class Grp, int OP, bool CPLX, int PREC, int DOF = 1, bool RULES = false, class SM>
 __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, double k, double eps,
                           FarBlock *blk, FarChunks *chk, typename VT<CPLX>::T *pool, Pool *P,
-                          GroupSmem<CPLX> &S, unsigned *Z, typename VT<CPLX>::T *part)
+                          SM &S, unsigned *Z, typename VT<CPLX>::T *part)
 {
     using V = VT<CPLX>;
     using T = typename V::T;
@@ -292,10 +332,10 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
     const int rule = blk->rule;  // the block's distance class (P0 Laplace entries)
     const int t = G.rank(), GS = G.size();
     const int64_t kmin = m < n ? m : n;
-    const int kcap = (int)(kmin < KMAX ? kmin : KMAX);
+    const int kcap = (int)(kmin < SM::kCap ? kmin : SM::kCap);
     const int64_t zwords = (m + 31) >> 5;
     for (int64_t w = t; w < zwords; w += GS) Z[w] = 0u;
-    if (t < NCHUNK) S.chunk[t] = -1;
+    for (int c = t; c < SM::kChunks; c += GS) S.chunk[c] = -1;
     if (t == 0) S.fail = 0;
     G.sync();
 
@@ -470,15 +510,16 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         // (k+1) * segments additions.
         double incr = 0.0, uv2 = 0.0;
         const int ncol = kk + 1;
-        if constexpr (std::is_same<Grp, WarpGroup>::value) {
+        if constexpr (Grp::kShuffle) {
             // power-of-two segments per column, summed by shuffle trees
+            // within the group's lanes
             double uv2_lane = 0.0;
             int last_l0 = 0;
-            for (int l0 = 0; l0 < ncol; l0 += 32) {
+            for (int l0 = 0; l0 < ncol; l0 += GS) {
                 last_l0 = l0;
-                const int kc = (ncol - l0) < 32 ? (ncol - l0) : 32;
+                const int kc = (ncol - l0) < GS ? (ncol - l0) : GS;
                 int nseg = 1;
-                while (nseg * 2 * kc <= 32) nseg *= 2;
+                while (nseg * 2 * kc <= GS) nseg *= 2;
                 T iu = V::zero(), iv = V::zero();
                 if (t < kc * nseg) {
                     const int l = l0 + t % kc, sgi = t / kc;
@@ -491,8 +532,8 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                         iv = V::dotc(vl[j], vk[j], iv);
                 }
                 for (int off = nseg / 2; off >= 1; off >>= 1) {
-                    iu = V::add(iu, V::shfl_down(iu, off * kc));
-                    iv = V::add(iv, V::shfl_down(iv, off * kc));
+                    iu = V::add(iu, G.template shfl_down<V>(iu, off * kc));
+                    iv = V::add(iv, G.template shfl_down<V>(iv, off * kc));
                 }
                 if (t < kc) {
                     const double pr = V::re_mul(iu, iv);
@@ -505,7 +546,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 }
             }
             incr = G.sum(incr);
-            uv2 = __shfl_sync(0xffffffffu, uv2_lane, kk - last_l0);
+            uv2 = G.shfl_idx(uv2_lane, kk - last_l0);
         } else {
             for (int l0 = 0; l0 < ncol; l0 += GS) {
                 const int kc = (ncol - l0) < GS ? (ncol - l0) : GS;
@@ -555,8 +596,8 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         blk->rank = kk;
         blk->status = status;
         blk->entries = entries;
-        for (int c = 0; c < NCHUNK; ++c) chk->c[c] = S.chunk[c];
     }
+    for (int c = t; c < NCHUNK; c += GS) chk->c[c] = c < SM::kChunks ? S.chunk[c] : -1;
     G.sync();
 }
 
@@ -697,6 +738,38 @@ __device__ __forceinline__ const AcaJob *item_job(const AcaWork &w, int64_t i, i
     return w.jobs + (it >> kItemShift);
 }
 
+// Blocks of the half- and quarter-warp shapes, W lanes each, 32 / W per
+// warp: the warp takes that many consecutive blocks of the shape's queue.
+template <int W, int OP, bool CPLX, int PREC, int DOF, bool RULES>
+__device__ __forceinline__ void aca_subgroups(const AcaWork &w, const QuadRule &R, int64_t first,
+                                              int64_t count, unsigned *counter,
+                                              unsigned char *area, unsigned *zwarp)
+{
+    using SM = GroupSmem<CPLX, W == 16 ? kSub16Max : kSub8Max>;
+    SM *gs = reinterpret_cast<SM *>(area);
+    using T = typename VT<CPLX>::T;
+    constexpr int NG = 32 / W;
+    constexpr int ZW = (W == 16 ? kSub16Max : kSub8Max) / 32 + 1;  // row-mask words per block
+    static_assert(NG * ZW <= 8, "row masks of the groups of a warp");
+    const int lane = threadIdx.x & 31, gi = lane / W;
+    const SubGroup<W> sg{lane % W, (W == 32 ? 0xffffffffu : ((1u << W) - 1u)) << (W * gi)};
+    for (;;) {
+        int64_t b0 = 0;
+        if (lane == 0) b0 = (int64_t)atomicAdd(counter, (unsigned)NG);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (b0 >= count) break;
+        const int64_t b = b0 + gi;
+        if (b < count) {
+            int64_t idx;
+            const AcaJob *J = item_job(w, first + b, idx);
+            aca_block<SubGroup<W>, OP, CPLX, PREC, DOF, RULES>(
+                sg, J->g, R, J->k, J->eps, J->far + idx, J->chunks + idx, (T *)J->pool, J->P, gs[gi],
+                zwarp + gi * ZW, nullptr);
+        }
+        __syncwarp();
+    }
+}
+
 template <int OP, bool CPLX, int PREC, int DOF, bool RULES = false>
 __global__ void __launch_bounds__(kAcaThreads, 2)
 k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
@@ -704,12 +777,12 @@ k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
     using T = typename VT<CPLX>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ RedScratch red;
-    __shared__ GroupSmem<CPLX> gs[kWarps];
+    __shared__ __align__(16) unsigned char garea[kWarps][GroupArea<CPLX>::bytes];
     __shared__ T part[2 * kAcaThreads];
     __shared__ int64_t s_b;
-    const int64_t n_big = w.n_big, n_small = w.n_small, n_tiny = w.n_tiny;
+    const int64_t n_big = w.n[kShapeCta], n_small = w.n[kShapeWarp];
     // row bitmasks: the whole region for a CTA-wide block, then one slice of
-    // zwords_small words per warp for the small blocks
+    // zwords_small words per warp for the warp-sized and smaller blocks
     unsigned *zbig = reinterpret_cast<unsigned *>(smem_raw);
     // phase 1: large blocks, one CTA each
     CtaGroup cg{&red};
@@ -723,11 +796,13 @@ k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
         const AcaJob *J = item_job(w, b, idx);
         aca_block<CtaGroup, OP, CPLX, PREC, DOF, RULES>(cg, J->g, R, J->k, J->eps, J->far + idx,
                                                         J->chunks + idx, (T *)J->pool, J->P,
-                                                        gs[0], zbig, part);
+                                                        *reinterpret_cast<GroupSmem<CPLX> *>(garea[0]),
+                                                        zbig, part);
     }
-    // phase 2: small blocks, one warp each
+    // phase 2: blocks of a warp each
     const int wi = threadIdx.x >> 5;
-    WarpGroup wg{(int)(threadIdx.x & 31)};
+    unsigned *zwarp = zbig + (int64_t)wi * zwords_small;
+    WarpGroup wg{(int)(threadIdx.x & 31), 0xffffffffu};
     for (;;) {
         int64_t b = 0;
         if (wg.lane == 0) b = (int64_t)atomicAdd(&Q->next_small, 1u);
@@ -737,12 +812,22 @@ k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
         const AcaJob *J = item_job(w, n_big + b, idx);
         aca_block<WarpGroup, OP, CPLX, PREC, DOF, RULES>(wg, J->g, R, J->k, J->eps, J->far + idx,
                                                          J->chunks + idx, (T *)J->pool, J->P,
-                                                         gs[wi], zbig + (int64_t)wi * zwords_small,
-                                                         part + 64 * wi);
+                                                         *reinterpret_cast<GroupSmem<CPLX> *>(garea[wi]),
+                                                         zwarp, part + 64 * wi);
     }
-    // phase 3: tiny blocks, 32 per warp, one per lane (P0 only; the host
-    // puts no DP1 block in this class)
+    // phases 3 and 4: two blocks per warp on 16 lanes each, then four on 8
+    // lanes each (P0 only; the host puts no DP1 block in these shapes)
     if constexpr (DOF == 1) {
+        const int64_t f3 = n_big + n_small, f4 = f3 + w.n[kShapeHalf];
+        aca_subgroups<16, OP, CPLX, PREC, DOF, RULES>(w, R, f3, w.n[kShapeHalf], &Q->next_w16,
+                                                      garea[wi], zwarp);
+        aca_subgroups<8, OP, CPLX, PREC, DOF, RULES>(w, R, f4, w.n[kShapeQuarter], &Q->next_w8,
+                                                     garea[wi], zwarp);
+    }
+    // phase 5: tiny blocks, 32 per warp, one per lane (P0 only)
+    if constexpr (DOF == 1) {
+        const int64_t f5 = n_big + n_small + w.n[kShapeHalf] + w.n[kShapeQuarter];
+        const int64_t n_tiny = w.n[kShapeLane];
         for (;;) {
             int64_t b0 = 0;
             if (wg.lane == 0) b0 = (int64_t)atomicAdd(&Q->next_tiny, 32u);
@@ -751,7 +836,7 @@ k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
             const int64_t b = b0 + wg.lane;
             if (b < n_tiny) {
                 int64_t idx;
-                const AcaJob *J = item_job(w, n_big + n_small + b, idx);
+                const AcaJob *J = item_job(w, f5 + b, idx);
                 aca_lane<OP, CPLX, PREC, RULES>(J->g, R, J->k, J->eps, J->far + idx,
                                                 J->chunks + idx, (T *)J->pool, J->P);
             }
@@ -764,7 +849,10 @@ template <int OP, bool CPLX, int PREC, int DOF, bool RULES = false>
 cudaError_t aca_launch(const AcaWork &w, const QuadRule &R, AcaQueue *Q, int num_sms,
                        cudaStream_t st)
 {
-    const int64_t zw_big = (w.max_m_big + 31) / 32, zw_small = (w.max_m_small + 31) / 32;
+    // row masks: a CTA block's, or per warp a slice of at least 8 words (the
+    // sub-warp groups of a warp)
+    const int64_t zw_big = (w.max_m_big + 31) / 32;
+    const int64_t zw_small = std::max<int64_t>((w.max_m_small + 31) / 32, 8);
     int64_t words = zw_big > kWarps * zw_small ? zw_big : kWarps * zw_small;
     size_t dyn = (size_t)(words > 0 ? words : 1) * sizeof(unsigned);
     auto kern = k_aca<OP, CPLX, PREC, DOF, RULES>;
@@ -776,6 +864,7 @@ cudaError_t aca_launch(const AcaWork &w, const QuadRule &R, AcaQueue *Q, int num
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
+    if (w.max_ctas > 0 && grid > w.max_ctas) grid = w.max_ctas;
     kern<<<(unsigned)grid, kAcaThreads, dyn, st>>>(w, R, (int)zw_small, Q);
     count_launches(1);
     return cudaGetLastError();

@@ -141,8 +141,17 @@ struct AcaQueue {
     unsigned int next_big;
     unsigned int next_small;
     unsigned int next_tiny;
-    unsigned int pad;
+    unsigned int next_w16;
+    unsigned int next_w8;
+    unsigned int pad[3];
 };
+
+// Work shapes of admissible blocks (P0): a whole CTA, a warp, half a warp
+// (16 lanes, two blocks per warp), a quarter warp (8 lanes, four blocks per
+// warp), or one lane.  Blocks with max(m, n) <= kSub8Max rows take 8 lanes,
+// <= kSub16Max 16 lanes (unless bem_tuning sends them to a CTA or a lane).
+constexpr int kSub8Max = 40, kSub16Max = 80;
+enum AcaShape { kShapeCta = 0, kShapeWarp = 1, kShapeHalf = 2, kShapeQuarter = 3, kShapeLane = 4 };
 
 // One H-matrix's part of an ACA launch: its cluster-order geometry, its
 // admissible blocks and their chunk tables, its factor pool, k and eps.
@@ -155,8 +164,8 @@ struct AcaJob {
     double k, eps;
 };
 
-// Work list of one ACA launch: n_big blocks for whole CTAs, then n_small
-// for warps, then n_tiny for single lanes, each class in descending size.
+// Work list of one ACA launch: the blocks of each work shape (AcaShape
+// order), each shape's blocks in descending size.
 // items == nullptr: item i is block i of jobs[0] (one H-matrix whose block
 // array is in that order); otherwise items[i] = (job << kItemShift) | the
 // block's index in that job's array (the request server's launches over
@@ -165,8 +174,9 @@ constexpr int kItemShift = 40;
 struct AcaWork {
     const AcaJob *jobs;      // device array
     const int64_t *items;    // device array or null
-    int64_t n_big, n_small, n_tiny;
-    int64_t max_m_big, max_m_small;
+    int64_t n[5];            // blocks per work shape (AcaShape order; the items in that order)
+    int64_t max_m_big, max_m_small;  // most rows of a CTA block, of a warp block
+    int max_ctas = 0;        // > 0: at most this many CTAs (leaves SMs to other streams)
 };
 
 // Read-only view of a mesh and of already-initialised per-device constants,

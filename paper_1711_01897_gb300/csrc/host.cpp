@@ -1116,7 +1116,8 @@ struct bem_hmat_s {
     std::vector<int64_t, NoInit<int64_t>> near_block_id;  // index into blocks
     std::vector<FarBlock, NoInit<FarBlock>> far;  // LPT order (big first, then small)
     std::vector<int64_t, NoInit<int64_t>> far_block_id;
-    int64_t n_big = 0, n_small = 0, n_tiny = 0, max_m_big = 0, max_m_small = 0;
+    int64_t nshape[5] = {0, 0, 0, 0, 0};  // admissible blocks per work shape (AcaShape)
+    int64_t max_m_big = 0, max_m_small = 0;
     int64_t near_total = 0;
     std::vector<SingPair, NoInit<SingPair>> sing[3];
     // leaves (matvec)
@@ -1550,7 +1551,7 @@ void build_lists(bem_hmat_s &H)
     const int64_t nb = (int64_t)H.blocks.size(), nt = M.nt;
     if (nb >= (int64_t(1) << 32) || nt >= (int64_t(1) << 29))
         throw std::runtime_error("problem too large for the block-list keys");
-    constexpr uint64_t kSizeMask = (uint64_t(1) << 30) - 1;
+    constexpr uint64_t kSizeMask = (uint64_t(1) << 29) - 1;
     // near blocks (tree order, consecutive dense storage) and keys of the
     // admissible blocks, in block chunks on the host threads, joined in order
     constexpr int64_t kBlkChunk = 16384;
@@ -1559,7 +1560,7 @@ void build_lists(bem_hmat_s &H)
         std::vector<NearBlock> near;
         std::vector<int64_t> near_id;
         std::vector<uint64_t> key;
-        int64_t elems = 0, ncls[3] = {0, 0, 0};
+        int64_t elems = 0, ncls[5] = {0, 0, 0, 0, 0};
     };
     std::vector<BlkPart> bp(nbc);
     parallel_tasks(nbc, [&](int64_t ck) {
@@ -1572,22 +1573,29 @@ void build_lists(bem_hmat_s &H)
                 P.near_id.push_back(b);
                 P.elems += m * n * H.dofs * H.dofs;
             } else {
+                // work shape (AcaShape): CTA, warp, half warp, quarter warp,
+                // lane; piecewise linear blocks take CTAs and warps only
                 const int64_t mx = std::max(m, n) * H.dofs;
-                const uint64_t cls = mx > H.small_max ? 0 : mx > H.tiny_max ? 1 : 2;
+                uint64_t cls;
+                if (mx > H.small_max) cls = kShapeCta;
+                else if (mx <= H.tiny_max) cls = kShapeLane;
+                else if (H.dofs != 1 || mx > kSub16Max) cls = kShapeWarp;
+                else if (mx > kSub8Max) cls = kShapeHalf;
+                else cls = kShapeQuarter;
                 ++P.ncls[cls];
-                P.key.push_back(cls << 62 | (kSizeMask - (uint64_t)(m + n)) << 32 | (uint64_t)b);
+                P.key.push_back(cls << 61 | (kSizeMask - (uint64_t)(m + n)) << 32 | (uint64_t)b);
             }
         }
     });
     trace.mark("classify");
     // the parts in order: their offsets first, then the copies on the threads
     std::vector<int64_t> at_near(nbc + 1, 0), at_key(nbc + 1, 0), at_elems(nbc + 1, 0);
-    int64_t ncls[3] = {0, 0, 0};
+    int64_t ncls[5] = {0, 0, 0, 0, 0};
     for (int64_t ck = 0; ck < nbc; ++ck) {
         at_near[ck + 1] = at_near[ck] + (int64_t)bp[ck].near.size();
         at_key[ck + 1] = at_key[ck] + (int64_t)bp[ck].key.size();
         at_elems[ck + 1] = at_elems[ck] + bp[ck].elems;
-        for (int c = 0; c < 3; ++c) ncls[c] += bp[ck].ncls[c];
+        for (int c = 0; c < 5; ++c) ncls[c] += bp[ck].ncls[c];
     }
     H.near.clear();
     H.near.resize(at_near[nbc]);
@@ -1666,17 +1674,16 @@ void build_lists(bem_hmat_s &H)
             F.se = S.e;
             F.rule = H.dofs == 1 ? block_rule(T, S, H.rho3, H.rho1) : kRule6;
             H.far_block_id[f] = b;
-            if (f < ncls[0]) mbig[ck] = std::max(mbig[ck], T.e - T.b);
-            else if (f < ncls[0] + ncls[1]) msmall[ck] = std::max(msmall[ck], T.e - T.b);
+            if (f < ncls[kShapeCta]) mbig[ck] = std::max(mbig[ck], T.e - T.b);
+            else if (f < ncls[kShapeCta] + ncls[kShapeWarp])
+                msmall[ck] = std::max(msmall[ck], T.e - T.b);
         }
     });
     for (int64_t ck = 0; ck < nfc; ++ck) {
         H.max_m_big = std::max(H.max_m_big, mbig[ck]);
         H.max_m_small = std::max(H.max_m_small, msmall[ck]);
     }
-    H.n_big = ncls[0];
-    H.n_small = ncls[1];
-    H.n_tiny = ncls[2];
+    for (int c = 0; c < 5; ++c) H.nshape[c] = ncls[c];
     H.has_rules = false;
     for (const FarBlock &F : H.far) H.has_rules |= F.rule != kRule6;
     trace.mark("far");
@@ -2152,8 +2159,9 @@ void enqueue_aca_own(bem_hmat H, cudaStream_t st)
     if (H->far.empty()) return;
     DeviceConsts &D = device_consts();
     const int aop = H->op == BEM_HYPS ? BEM_SLP : H->op;
-    AcaWork w{H->d_job.as<AcaJob>(), nullptr, H->n_big, H->n_small, H->n_tiny, H->max_m_big,
-              H->max_m_small};
+    AcaWork w{H->d_job.as<AcaJob>(), nullptr,
+              {H->nshape[0], H->nshape[1], H->nshape[2], H->nshape[3], H->nshape[4]},
+              H->max_m_big, H->max_m_small};
     CU(launch_aca(w, D.rule, aop, H->cplx, H->prec, H->d_queue.as<AcaQueue>(), D.num_sms, st,
                   H->dofs, H->has_rules));
 }
@@ -2228,7 +2236,9 @@ void assemble_end(bem_hmat H, cudaStream_t st)
 // H-matrices (P0, the same operator, precision and number type, all past
 // assemble_pool and enqueue_near on st): the blocks of each work shape from
 // every matrix, merged longest first, each item naming its matrix's job.
-int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st)
+// sm_share < 1 caps the launch's CTAs at that share of the device, so that
+// launches on other streams find free SMs while it runs.
+int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st, double sm_share)
 {
     if (hs.empty()) return BEM_OK;
     DeviceConsts &D = device_consts();
@@ -2238,7 +2248,7 @@ int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st)
     struct It {
         int64_t size, item;
     };
-    std::vector<It> cls[3];
+    std::vector<It> cls[5];
     int64_t max_big = 0, max_small = 0;
     for (size_t j = 0; j < hs.size(); ++j) {
         const bem_hmat H = hs[j];
@@ -2246,10 +2256,9 @@ int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st)
             H->has_rules != H0->has_rules)
             return fail(BEM_E_ARG, "fused ACA launch over different kinds of matrices");
         jobs.push_back(*H->pin_job);
-        const int64_t n[3] = {H->n_big, H->n_small, H->n_tiny};
         int64_t f = 0;
-        for (int c = 0; c < 3; ++c)
-            for (int64_t e = f + n[c]; f < e; ++f) {
+        for (int c = 0; c < 5; ++c)
+            for (int64_t e = f + H->nshape[c]; f < e; ++f) {
                 const FarBlock &F = H->far[f];
                 cls[c].push_back({(F.te - F.tb) + (F.se - F.sb), ((int64_t)j << kItemShift) | f});
             }
@@ -2273,8 +2282,12 @@ int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st)
     if (e == cudaSuccess) e = cudaMemcpyAsync(b + jb, items.data(), ib, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(Q, 0, sizeof(AcaQueue), st);
     if (e == cudaSuccess) {
-        AcaWork w{(const AcaJob *)b, (const int64_t *)(b + jb), (int64_t)cls[0].size(),
-                  (int64_t)cls[1].size(), (int64_t)cls[2].size(), max_big, max_small};
+        AcaWork w{(const AcaJob *)b, (const int64_t *)(b + jb),
+                  {(int64_t)cls[0].size(), (int64_t)cls[1].size(), (int64_t)cls[2].size(),
+                   (int64_t)cls[3].size(), (int64_t)cls[4].size()},
+                  max_big, max_small};
+        // a share of the SMs: 2 CTAs of the ACA fit on an SM
+        if (sm_share < 1.0) w.max_ctas = std::max(1, (int)(sm_share * 2 * D.num_sms));
         e = launch_aca(w, D.rule, aop, H0->cplx, H0->prec, Q, D.num_sms, st, 1, H0->has_rules);
     }
     cudaFreeAsync(buf, st);
@@ -2492,9 +2505,11 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         }
         s.rho3 = H->rho3;
         s.rho1 = H->rho1;
-        s.n_blocks_cta = H->n_big;
-        s.n_blocks_warp = H->n_small;
-        s.n_blocks_lane = H->n_tiny;
+        s.n_blocks_cta = H->nshape[kShapeCta];
+        s.n_blocks_warp = H->nshape[kShapeWarp] + H->nshape[kShapeHalf] + H->nshape[kShapeQuarter];
+        s.n_blocks_lane = H->nshape[kShapeLane];
+        s.n_blocks_half_warp = H->nshape[kShapeHalf];
+        s.n_blocks_quarter_warp = H->nshape[kShapeQuarter];
         s.near_entries = H->near_total;
         for (int c = 0; c < 3; ++c) s.singular_pairs[c] = (int64_t)H->sing[c].size();
         s.far_entries = H->far_entries;

@@ -11,7 +11,7 @@ cudaError_t launch_aca_dp1(const AcaWork &w, const QuadRule &rule, int op, bool 
                            AcaQueue *queue, int num_sms, cudaStream_t st)
 {
     AcaWork w3 = w;
-    w3.n_tiny = 0;
+    w3.n[kShapeHalf] = w3.n[kShapeQuarter] = w3.n[kShapeLane] = 0;
 #define BEM_ACA3(O, C, Pp)                                  \
     if (op == O && cplx == C && prec == Pp)                 \
         return aca_launch<O, C, Pp, 3>(w3, rule, queue, num_sms, st);

@@ -44,6 +44,13 @@ constexpr int kBatchMax = 64;       // requests per batch
 // A free stream waits up to this long after the oldest admitted request for
 // requests still being prepared, so that they share the launch.
 constexpr double kBatchWindowMs = 2.0;
+// Requests with at least this many triangles are large: they are batched
+// apart from the small ones, at most one large batch runs at a time, and its
+// ACA launch leaves a quarter of the SMs to the small batches on the other
+// stream (so that a large assembly does not hold up small requests).
+constexpr int64_t kLargeTriangles = 40000;
+constexpr double kLargeSmShare = 0.75;
+constexpr double kLargeWaitMs = 50.0;
 
 // An assembled H-matrix kept on the device after its request finished.
 struct Resident {
@@ -81,9 +88,15 @@ struct Req {
 
 struct Batch {
     int slot = -1;
+    bool large = false;
     std::vector<Req *> reqs;
     double t_launch = 0;
 };
+
+bool is_large(const Req *r)
+{
+    return r->res == nullptr && (int64_t)r->T.size() / 3 >= kLargeTriangles;
+}
 
 }  // namespace
 
@@ -254,7 +267,9 @@ void bem_server_s::launch(Batch &b)
     for (auto &kv : kinds) {
         std::vector<bem_hmat> hs;
         for (Req *r : kv.second) hs.push_back(r->H);
-        int rc = guarded_call([&]() -> int { return enqueue_aca_fused(hs, st); });
+        int rc = guarded_call([&]() -> int {
+            return enqueue_aca_fused(hs, st, b.large ? kLargeSmShare : 1.0);
+        });
         for (Req *r : kv.second) {
             r->launch_reqs = (int32_t)kv.second.size();
             if (rc != BEM_OK) r->status = rc;
@@ -432,18 +447,40 @@ void bem_server_s::engine_loop()
         const bool more_coming = preparing > 0 || !queue.empty() || !prepared.empty();
         const bool window_over =
             !admitted.empty() && steady_ms() - admitted.front()->t_admit >= kBatchWindowMs;
+        bool large_inflight = false;
+        for (auto &b : inflight) large_inflight |= !b.reqs.empty() && b.large;
         if (!admitted.empty() && free_slot >= 0 &&
             (!more_coming || window_over || admitted.size() >= (size_t)kBatchMax ||
              running >= slots)) {
-            Batch &b = inflight[free_slot];
-            b.slot = free_slot;
-            const size_t n = std::min<size_t>(admitted.size(), kBatchMax);
-            b.reqs.assign(admitted.begin(), admitted.begin() + n);
-            admitted.erase(admitted.begin(), admitted.begin() + n);
-            lk.unlock();
-            launch(b);
-            lk.lock();
-            continue;
+            // a batch of one size class: the small requests, else (if no large
+            // batch is running) the large ones
+            bool any_small = false, any_large = false;
+            for (Req *r : admitted) (is_large(r) ? any_large : any_small) = true;
+            // small first, unless the oldest admitted request is a large one
+            // that has waited long enough (no starvation under a stream of
+            // small requests)
+            const bool large_overdue = is_large(admitted.front()) &&
+                                       steady_ms() - admitted.front()->t_admit > kLargeWaitMs;
+            const bool take_large = !any_small || (large_overdue && !large_inflight);
+            if (!take_large || !large_inflight) {
+                Batch &b = inflight[free_slot];
+                b.slot = free_slot;
+                b.large = take_large;
+                b.reqs.clear();
+                for (auto it = admitted.begin();
+                     it != admitted.end() && b.reqs.size() < (size_t)kBatchMax;) {
+                    if (is_large(*it) == take_large) {
+                        b.reqs.push_back(*it);
+                        it = admitted.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                lk.unlock();
+                launch(b);
+                lk.lock();
+                continue;
+            }
         }
         any_inflight = false;
         for (auto &b : inflight) any_inflight |= !b.reqs.empty();

@@ -27,12 +27,16 @@ TOL = {bem.FP64: 1e-6, bem.MIXED: 1e-5}
 NOISE = {bem.FP64: 1e-15, bem.MIXED: 1e-7}
 
 # (warp_max_rows, lane_max_rows): the shapes each puts blocks on, for the L3
-# mesh (blocks of 20 and 40 rows) and the L4 mesh (20 to 160 rows)
+# mesh (blocks of 20 and 40 rows) and the L4 mesh (20 to 160 rows).  "warp"
+# counts every block on warps; "quarter" (at most 40 rows, four blocks per
+# warp on 8 lanes each) and "half" (at most 80 rows, two per warp) are parts
+# of it, asserted where the mesh has such blocks
 SHAPES = {
-    "cta_warp": ((32, 0), {"cta", "warp"}),
-    "lane_warp": ((160, 24), {"lane", "warp"}),
+    "cta_warp": ((32, 0), {"cta", "warp", "quarter"}),
+    "lane_warp": ((160, 24), {"lane", "warp", "quarter"}),
     "lane_only": ((8192, 64), {"lane"}),
     "cta_only": ((16, 0), {"cta"}),
+    "default": ((8192, 0), {"warp", "quarter"}),
 }
 CASES = [(bem.SLP, 0.0), (bem.DLP, 0.0), (bem.SLP, 2.0)]
 
@@ -96,14 +100,19 @@ def _with_shape(shape, fn):
         bem.bem_set_tuning(saved["warp_max_rows"], saved["lane_max_rows"], saved["use_graphs"])
 
 
-def _check_shapes(stats, want):
+def _check_shapes(stats, want, l4=False):
     got = {"cta": stats["n_blocks_cta"], "warp": stats["n_blocks_warp"],
-           "lane": stats["n_blocks_lane"]}
-    assert sum(got.values()) == stats["n_blocks_far"]
-    for s in ("cta", "warp", "lane"):
+           "lane": stats["n_blocks_lane"], "half": stats["n_blocks_half_warp"],
+           "quarter": stats["n_blocks_quarter_warp"]}
+    assert got["cta"] + got["warp"] + got["lane"] == stats["n_blocks_far"]
+    assert got["half"] + got["quarter"] <= got["warp"]
+    want = set(want)
+    if l4 and "warp" in want and "lane" not in want:
+        want.add("half")          # the L4 mesh has 80-row blocks
+    for s in ("cta", "warp", "lane", "quarter", "half"):
         if s in want:
             assert got[s] > 0, (s, got)
-        else:
+        elif s in ("cta", "warp", "lane"):
             assert got[s] == 0, (s, got)
 
 
@@ -156,7 +165,7 @@ def test_every_block_every_shape_l3(lib, l3, l3_dense, shape, case, prec):
           f"shapes cta/warp/lane {s['n_blocks_cta']}/{s['n_blocks_warp']}/{s['n_blocks_lane']}")
 
 
-@pytest.mark.parametrize("shape", ["cta_warp", "lane_warp"])
+@pytest.mark.parametrize("shape", ["cta_warp", "lane_warp", "default"])
 @pytest.mark.parametrize("case", CASES, ids=["slp", "dlp", "helmholtz_slp_k2"])
 def test_sampled_blocks_every_shape_l4(lib, shape, case):
     """Jittered L4 (5,120 triangles; blocks of 20 to 160 rows), mixed: the
@@ -177,13 +186,15 @@ def test_sampled_blocks_every_shape_l4(lib, shape, case):
 
     h = _with_shape((wmax, lmax), build)
     s = h.stats()
-    _check_shapes(s, want)
+    _check_shapes(s, want, l4=shape != "cta_warp")
     blocks, perm = h.blocks()
     far = np.nonzero(blocks[:, 4] == 1)[0]
     mx = np.maximum(blocks[far, 1] - blocks[far, 0], blocks[far, 3] - blocks[far, 2])
     rng = np.random.default_rng(17 + op)
     pick = []
-    for lo, hi in ((0, lmax), (lmax, wmax), (wmax, 10 ** 9)):
+    # every shape's largest blocks and random ones: lane, quarter, half, warp, CTA
+    cuts = sorted({0, lmax, min(40, wmax), min(80, wmax), wmax, 10 ** 9})
+    for lo, hi in zip(cuts, cuts[1:]):
         cls = far[(mx > lo) & (mx <= hi)]
         if cls.size:
             order = cls[np.argsort(-mx[np.isin(far, cls)], kind="stable")]
