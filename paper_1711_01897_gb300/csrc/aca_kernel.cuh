@@ -373,12 +373,103 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             }
             ++nalloc;
         }
-        // selected row of R_{k-1}: a_{i,:} - sum_l (u_l)_i v_l
-        for (int l = t; l < kk; l += GS) S.cu[l] = *Uat(l, i);
-        G.sync();
-        long long bkey = -1;
-        int64_t bj = 0;
-        if constexpr (DOF == 3) {
+        long long ukey = -1;
+        int64_t br = m, bj = 0;
+        if constexpr (DOF == 1) {
+            // The selected row i of R_{k-1} (a_{i,:} - sum_l (u_l)_i v_l),
+            // then, after the pivot, the selected column bj (a_{:,bj} -
+            // sum_l (v_l)_bj u_l): two passes of one loop body, so that the
+            // quadrature is compiled once per work shape (a smaller hot code
+            // footprint); each entry loads both triangles, the fixed one by a
+            // load that is the same for every lane.
+            bool vanished = false, capped = false;
+            long long bkey = -1;
+#pragma unroll 1
+            for (int ph = 0; ph < 2; ++ph) {
+                const bool col = ph != 0;
+                if (!col) {
+                    for (int l = t; l < kk; l += GS) S.cu[l] = *Uat(l, i);
+                } else {
+                    G.sync();
+                    const T piv = *Vat(kk, bj);
+                    const T pinv = V::inv(piv);
+                    G.sync();
+                    for (int64_t j = t; j < n; j += GS) *Vat(kk, j) = V::mul(*Vat(kk, j), pinv);
+                    for (int l = t; l < kk; l += GS) S.cu[l] = *Vat(l, bj);
+                }
+                G.sync();
+                const int64_t len = col ? m : n;
+                const int64_t a0 = col ? tb : tb + i, da = col ? 1 : 0;
+                const int64_t b0 = col ? sb + bj : sb, db = col ? 0 : 1;
+                // factor column l of this pass: U_l (column pass) or V_l (row pass)
+                const int64_t xoff = col ? 0 : (int64_t)KCHUNK * m, xld = col ? m : n;
+                const bool store = col || kk < kcap;
+                long long best = -1;
+                int64_t bidx = col ? m : 0;
+                for (int64_t e = t; e < len; e += GS) {
+                    typename E::Tri ta, tq;
+                    E::load(g, a0 + da * e, ta);
+                    E::load(g, b0 + db * e, tq);
+                    T a = V::from((eval_entry<RULES, E>(ta, tq, R, k, rule)));
+                    for (int l = 0; l < kk; ++l)
+                        a = V::fnma(S.cu[l],
+                                    pool[S.chunk[l / KCHUNK] + xoff + (int64_t)(l % KCHUNK) * xld + e], a);
+                    if (store) pool[S.chunk[kk / KCHUNK] + xoff + (int64_t)(kk % KCHUNK) * xld + e] = a;
+                    // the column pass looks for the next row among the unused ones
+                    if (!col || !((Z[e >> 5] >> (e & 31)) & 1u)) {
+                        long long ky = V::key(a);
+                        if (ky > best) {  // e increases, so ties keep the lowest index
+                            best = ky;
+                            bidx = e;
+                        }
+                    }
+                }
+                entries += len;
+                G.argmax_key(best, bidx);
+                if (col) {
+                    ukey = best;
+                    br = bidx;
+                    break;
+                }
+                bkey = best;
+                bj = bidx;
+                if (t == 0) Z[i >> 5] |= 1u << (i & 31);
+                ++nZ;
+                if (bkey == 0 || bkey <= vkey) {
+                    vanished = true;
+                    break;
+                }
+                if (kk == kcap) {
+                    capped = true;
+                    break;
+                }
+                if (bkey > maxkey) {
+                    maxkey = bkey;
+                    vkey = V::vanish_key(maxkey);
+                }
+            }
+            if (vanished) {
+                if (nZ == m) break;
+                G.sync();
+                if (t == 0) {
+                    int64_t r = 0;
+                    while (r < m && (Z[r >> 5] >> (r & 31)) & 1u) ++r;
+                    S.scal = r;
+                }
+                G.sync();
+                i = S.scal;
+                continue;
+            }
+            if (capped) {
+                status = 1;
+                break;
+            }
+            G.sync();
+        } else {
+            // selected row of R_{k-1}: a_{i,:} - sum_l (u_l)_i v_l
+            for (int l = t; l < kk; l += GS) S.cu[l] = *Uat(l, i);
+            G.sync();
+            long long bkey = -1;
             using L = LocalEntry<OP, CPLX, PREC>;
             typename L::Tri ti;
             L::load(g, tb / 3 + i / 3, ti);
@@ -401,22 +492,6 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                     }
                 }
             }
-        } else {
-            typename E::Tri ti;
-            E::load(g, tb + i, ti);
-            for (int64_t j = t; j < n; j += GS) {
-                typename E::Tri tj;
-                E::load(g, sb + j, tj);
-                T a = V::from((eval_entry<RULES, E>(ti, tj, R, k, rule)));
-                for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Vat(l, j), a);
-                if (kk < kcap) *Vat(kk, j) = a;
-                long long ky = V::key(a);
-                if (ky > bkey) {  // j increases, so ties keep the lowest index
-                    bkey = ky;
-                    bj = j;
-                }
-            }
-        }
         entries += n;
         G.argmax_key(bkey, bj);
         if (t == 0) Z[i >> 5] |= 1u << (i & 31);
@@ -449,9 +524,6 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         // selected column of R_{k-1}: a_{:,j} - sum_l (v_l)_j u_l
         for (int l = t; l < kk; l += GS) S.cu[l] = *Vat(l, bj);
         G.sync();
-        long long ukey = -1;
-        int64_t br = m;
-        if constexpr (DOF == 3) {
             using L = LocalEntry<OP, CPLX, PREC>;
             typename L::Tri tj;
             L::load(g, sb / 3 + bj / 3, tj);
@@ -481,27 +553,10 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                     }
                 }
             }
-        } else {
-            typename E::Tri tj;
-            E::load(g, sb + bj, tj);
-            for (int64_t r = t; r < m; r += GS) {
-                typename E::Tri tr;
-                E::load(g, tb + r, tr);
-                T a = V::from((eval_entry<RULES, E>(tr, tj, R, k, rule)));
-                for (int l = 0; l < kk; ++l) a = V::fnma(S.cu[l], *Uat(l, r), a);
-                *Uat(kk, r) = a;
-                if (!((Z[r >> 5] >> (r & 31)) & 1u)) {
-                    long long ky = V::key(a);
-                    if (ky > ukey) {
-                        ukey = ky;
-                        br = r;
-                    }
-                }
-            }
+            entries += m;
+            G.argmax_key(ukey, br);
+            G.sync();
         }
-        entries += m;
-        G.argmax_key(ukey, br);
-        G.sync();
         // ||S_k||_F^2 grows by 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> + ||u_k||^2 ||v_k||^2.
         // Every thread forms the dot products of one column l <= k over one
         // segment of the rows (and of v_l over one segment of the columns);

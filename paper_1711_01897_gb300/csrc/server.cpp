@@ -51,6 +51,10 @@ constexpr double kBatchWindowMs = 2.0;
 constexpr int64_t kLargeTriangles = 40000;
 constexpr double kLargeSmShare = 0.75;
 constexpr double kLargeWaitMs = 50.0;
+// Admission: a request that cannot start lets younger ones pass for at most
+// this long; at most kMaxLargeRunning large requests run at once.
+constexpr double kBypassMs = 300.0;
+constexpr int64_t kMaxLargeRunning = 2;
 
 // An assembled H-matrix kept on the device after its request finished.
 struct Resident {
@@ -75,7 +79,7 @@ struct Req {
     int64_t reuse = 0;         // request whose resident matrix to apply (0: assemble)
     int state = BEM_REQ_QUEUED;
     int status = BEM_OK;
-    double t_submit = 0, t_admit = 0, t_done = 0, asm_ms = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0, asm_ms = 0, t_ready = 0;
     int64_t reserved = 0, integrals = 0;
     int32_t launch_reqs = 0;   // requests that shared its ACA launch
     int32_t reused = 0;        // 1: applied a resident matrix, no assembly
@@ -115,6 +119,7 @@ struct bem_server_s {
     int64_t next_id = 1;
     int64_t in_use = 0, peak = 0;
     int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, running = 0;
+    int64_t running_large = 0;
     int64_t evictions = 0, reuse_hits = 0, fused_launches = 0, fused_requests = 0;
     int64_t max_launch_requests = 0;
     int preparing = 0;
@@ -161,7 +166,10 @@ bool bem_server_s::evict_one()
 // Called with mu held.
 void bem_server_s::finish_locked(Req *r, int status)
 {
-    if (r->state == BEM_REQ_RUNNING) --running;
+    if (r->state == BEM_REQ_RUNNING) {
+        --running;
+        if (is_large(r)) --running_large;
+    }
     r->status = status;
     r->state = status == BEM_OK ? BEM_REQ_DONE : BEM_REQ_FAILED;
     r->t_done = steady_ms();
@@ -210,6 +218,7 @@ void bem_server_s::worker()
             if (r->state != BEM_REQ_CANCELLED) finish_locked(r, rc);
             continue;
         }
+        r->t_ready = steady_ms();
         prepared.push_back(r->id);
         std::sort(prepared.begin(), prepared.end());
         cv_engine.notify_all();
@@ -388,19 +397,34 @@ void bem_server_s::engine_loop()
                 lk.lock();
             }
         }
-        // admission in arrival order, evicting idle resident matrices
-        while (!prepared.empty() && running < slots) {
-            Req *r = reqs[prepared.front()].get();
+        // admission in arrival order, evicting idle resident matrices; a
+        // request that cannot start yet (budget, running limit, or the
+        // assembly it reuses still on the way) lets younger ones pass while
+        // it has waited less than kBypassMs, then holds the queue until it
+        // starts
+        for (size_t qi = 0; qi < prepared.size();) {
+            Req *r = reqs[prepared[qi]].get();
+            const bool lg = is_large(r);
+            auto hold = [&]() -> bool {   // true: stop scanning
+                return steady_ms() - r->t_ready >= kBypassMs;
+            };
+            if (running >= slots || (lg && running_large >= kMaxLargeRunning)) {
+                if (hold()) break;
+                ++qi;
+                continue;
+            }
             if (r->reuse > 0) {
                 Resident *R = find_resident(r->reuse);
                 if (!R) {
                     auto src = reqs.find(r->reuse);
                     if (src != reqs.end() && src->second->state != BEM_REQ_DONE &&
                         src->second->state != BEM_REQ_FAILED &&
-                        src->second->state != BEM_REQ_CANCELLED)
-                        break;   // its assembly is still on the way: wait for it
+                        src->second->state != BEM_REQ_CANCELLED) {
+                        ++qi;   // its assembly is still on the way: wait for it
+                        continue;
+                    }
                     // failed, cancelled or evicted
-                    prepared.pop_front();
+                    prepared.erase(prepared.begin() + qi);
                     set_last_error("the request to reuse has no resident matrix");
                     r->state = BEM_REQ_RUNNING;
                     ++running;
@@ -408,7 +432,7 @@ void bem_server_s::engine_loop()
                     continue;
                 }
                 if ((int64_t)r->x.size() != R->nt * (R->k != 0.0 ? 2 : 1)) {
-                    prepared.pop_front();
+                    prepared.erase(prepared.begin() + qi);
                     set_last_error("vector length does not match the resident matrix");
                     r->state = BEM_REQ_RUNNING;
                     ++running;
@@ -426,15 +450,20 @@ void bem_server_s::engine_loop()
             } else {
                 while (in_use + r->bytes > budget && evict_one()) {
                 }
-                if (in_use + r->bytes > budget) break;
+                if (in_use + r->bytes > budget) {
+                    if (hold()) break;
+                    ++qi;
+                    continue;
+                }
                 in_use += r->bytes;
                 peak = std::max(peak, in_use);
             }
-            prepared.pop_front();
+            prepared.erase(prepared.begin() + qi);
             r->reserved = r->bytes;
             r->state = BEM_REQ_RUNNING;
             r->t_admit = steady_ms();
             ++running;
+            if (lg) ++running_large;
             admitted.push_back(r);
         }
         // a batch of everything admitted, on a free stream

@@ -147,3 +147,25 @@ def test_product_waits_for_its_assembly(lib):
     assert rc == 0 and info.reused == 1 and np.all(y == 2.0)
     assert srv.poll(a).state == bem.DONE
     srv.close()
+
+
+def test_small_requests_pass_a_waiting_large_one(lib):
+    """A large request that must wait for budget lets small requests that
+    fit start before it (for a bounded time), so that they do not queue
+    behind it; it still starts once the budget allows."""
+    VL, TL = _mesh(45)                 # 40,500 triangles: a large request
+    VS, TS = _mesh(8)
+    per_large = 1024 * TL.shape[0]
+    srv = bem.Server(int(1.2 * per_large), max_slots=6, dry_run=True)
+    l1 = srv.submit(VL, TL, np.zeros(TL.shape[0]), dry_run_ms=250)
+    time.sleep(0.02)
+    l2 = srv.submit(VL, TL, np.zeros(TL.shape[0]), dry_run_ms=50)
+    time.sleep(0.02)
+    small = [srv.submit(VS, TS, np.zeros(TS.shape[0]), dry_run_ms=5) for _ in range(3)]
+    infos = {rid: srv.wait(rid)[1] for rid in [l1, l2] + small}
+    for rid in small:
+        assert infos[rid].t_done_ms < infos[l2].t_admit_ms        # passed the waiting one
+        assert infos[rid].t_done_ms - infos[rid].t_submit_ms < 200
+    assert infos[l2].t_admit_ms >= infos[l1].t_done_ms - 1e-6       # budget: one large at a time
+    assert srv.stats()["peak_reserved_bytes"] <= int(1.2 * per_large)
+    srv.close()
