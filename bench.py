@@ -62,7 +62,7 @@ AUTOTUNED_RHO_L6 = (4.0, 24.0)
 # round, three repetitions: 1321 ms against 1373 ms for the library default)
 AUTOTUNED_SHAPES_C3 = (160, 48)
 
-ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.707635968 + 1.940037376 + 10.711072512 + 2.945069056) * 1e9
+ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.708396288 + 1.940368640 + 10.743539200 + 2.975437056) * 1e9
 
 
 def rank_jitter_seed(rank: int) -> int:
@@ -684,7 +684,8 @@ def serving_record(args, nreq: int, calib: int):
 
     th = threading.Thread(target=submitter)
     th.start()
-    lat, lat_prod, ints, fails, shared, mism, sizes = [], [], 0, 0, [], 0, []
+    lat, lat_prod, ints, fails, shared, mism, sizes, phases = [], [], 0, 0, [], 0, [], []
+    prod_phases = []
     for i in range(nreq):
         while ids[i] is None:
             time.sleep(0.0005)
@@ -693,6 +694,8 @@ def serving_record(args, nreq: int, calib: int):
             fails += 1
             continue
         lat.append(info.t_done_ms - info.t_submit_ms)
+        phases.append((info.t_ready_ms - info.t_submit_ms, info.t_admit_ms - info.t_ready_ms,
+                       info.t_launch_ms - info.t_admit_ms, info.t_done_ms - info.t_launch_ms))
         sizes.append(reqs[i]["T"].shape[0])
         ints += info.integrals
         shared.append(info.launch_requests)
@@ -702,6 +705,10 @@ def serving_record(args, nreq: int, calib: int):
             rc2, info2, y2 = srv.wait(p)
             if rc2 == 0:
                 lat_prod.append(info2.t_done_ms - info2.t_submit_ms)
+                prod_phases.append((info2.t_ready_ms - info2.t_submit_ms,
+                                    info2.t_admit_ms - info2.t_ready_ms,
+                                    info2.t_launch_ms - info2.t_admit_ms,
+                                    info2.t_done_ms - info2.t_launch_ms))
                 mism += int(not np.array_equal(y, y2))
     th.join()
     span = time.perf_counter() - start
@@ -710,6 +717,16 @@ def serving_record(args, nreq: int, calib: int):
     clocks = clk.stop()
     lat = np.array(lat)
     sizes = np.array(sizes)
+    ph = np.array(phases) if phases else np.zeros((1, 4))
+    worst = np.argsort(-lat)[:5]
+    names = ("trees", "admission", "batch", "device")
+    phase_ms = {"median": {n: float(np.median(ph[:, c])) for c, n in enumerate(names)},
+                "p99": {n: float(np.percentile(ph[:, c], 99)) for c, n in enumerate(names)},
+                "slowest_requests": [{"triangles": int(sizes[w]), **{n: float(ph[w, c])
+                                                                    for c, n in enumerate(names)}}
+                                     for w in worst],
+                "slowest_products": [dict(zip(names, map(float, p_)))
+                                     for p_ in sorted(prod_phases, key=lambda q: -sum(q))[:3]]}
     by_size = {}
     for name, sel in (("below_40k_triangles", sizes < 40000), ("from_40k_triangles", sizes >= 40000)):
         if sel.any():
@@ -726,6 +743,7 @@ def serving_record(args, nreq: int, calib: int):
                        "mean": float(lat.mean()),
                        "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50))},
         "latency_ms_by_size": by_size,
+        "latency_parts_ms": phase_ms,
         "product_only_latency_ms": ({"p50": float(np.percentile(lat_prod, 50)),
                                      "p99": float(np.percentile(lat_prod, 99)),
                                      "count": len(lat_prod), "differ_from_assembly": mism}
