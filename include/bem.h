@@ -472,6 +472,8 @@ typedef struct {
     double assembly_ms;         /* device time of the assembly */
     int32_t launch_requests;    /* requests whose blocks shared its ACA launch (0: none ran) */
     int32_t reused;             /* 1: applied a resident matrix, nothing assembled */
+    double t_ready_ms;          /* host part (trees) done, waiting for admission */
+    double t_launch_ms;         /* its batch's device work enqueued */
 } bem_request_info;
 
 typedef struct {

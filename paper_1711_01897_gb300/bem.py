@@ -88,7 +88,8 @@ class RequestInfo(ctypes.Structure):
                 ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
                 ("t_done_ms", ctypes.c_double), ("reserved_bytes", ctypes.c_int64),
                 ("integrals", ctypes.c_int64), ("assembly_ms", ctypes.c_double),
-                ("launch_requests", ctypes.c_int32), ("reused", ctypes.c_int32)]
+                ("launch_requests", ctypes.c_int32), ("reused", ctypes.c_int32),
+                ("t_ready_ms", ctypes.c_double), ("t_launch_ms", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):

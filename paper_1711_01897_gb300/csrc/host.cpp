@@ -121,6 +121,35 @@ void pool_trim()
     cudaMemPoolTrimTo(lib_pool(), 0);
 }
 
+// Pinned host slots of up to kPinSlot bytes for the small readbacks and
+// uploads of an assembly (pool header, totals, the ACA job).  They come from
+// page-locked chunks that are never returned: freeing page-locked memory
+// synchronises the whole device, which would stall every stream (the request
+// server frees matrices while other batches run).
+constexpr size_t kPinSlot = 256, kPinChunk = 64 * 1024;
+std::mutex g_pin_mu;
+std::vector<void *> g_pin_free;
+
+void *pinned_slot()
+{
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        void *chunk = nullptr;
+        if (cudaMallocHost(&chunk, kPinChunk) != cudaSuccess) return nullptr;
+        for (size_t o = 0; o < kPinChunk; o += kPinSlot) g_pin_free.push_back((char *)chunk + o);
+    }
+    void *p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+
+void pinned_release(void *p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 cudaError_t lib_malloc_async(void **p, size_t b, cudaStream_t st)
 {
     return cudaMallocFromPoolAsync(p, b, lib_pool(), st);
@@ -1155,13 +1184,13 @@ struct bem_hmat_s {
     AcaJob *pin_job = nullptr;      // pinned source of d_job (this matrix as one ACA job)
     ~bem_hmat_s()
     {
-        if (pin_job) cudaFreeHost(pin_job);
+        pinned_release(pin_job);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
-        if (pin_pool) cudaFreeHost(pin_pool);
-        if (pin_stats) cudaFreeHost(pin_stats);
+        pinned_release(pin_pool);
+        pinned_release(pin_stats);
     }
     int64_t far_entries = 0, rank_sum = 0, capped = 0;
     int32_t rank_min = 0, rank_max = 0;
@@ -2065,9 +2094,13 @@ int assemble_begin(bem_hmat H, int32_t op, double k, double aca_eps, int32_t pre
     if (!H->ev[0])
         for (auto &e : H->ev) CU(cudaEventCreate(&e));
     if (!H->pin_pool) {
-        CU(cudaMallocHost(&H->pin_pool, sizeof(Pool)));
-        CU(cudaMallocHost(&H->pin_stats, sizeof(AcaStats)));
-        CU(cudaMallocHost(&H->pin_job, sizeof(AcaJob)));
+        static_assert(sizeof(Pool) <= kPinSlot && sizeof(AcaStats) <= kPinSlot &&
+                          sizeof(AcaJob) <= kPinSlot, "pinned slots");
+        H->pin_pool = (Pool *)pinned_slot();
+        H->pin_stats = (AcaStats *)pinned_slot();
+        H->pin_job = (AcaJob *)pinned_slot();
+        if (!H->pin_pool || !H->pin_stats || !H->pin_job)
+            return fail(BEM_E_OOM, "page-locked host memory for the readbacks");
     }
     if (H->d_near_data.bytes < (size_t)H->near_total * esz)
         H->d_near_data.alloc(H->near_total * esz, st);

@@ -79,7 +79,7 @@ struct Req {
     int64_t reuse = 0;         // request whose resident matrix to apply (0: assemble)
     int state = BEM_REQ_QUEUED;
     int status = BEM_OK;
-    double t_submit = 0, t_admit = 0, t_done = 0, asm_ms = 0, t_ready = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0, asm_ms = 0, t_ready = 0, t_launch = 0;
     int64_t reserved = 0, integrals = 0;
     int32_t launch_reqs = 0;   // requests that shared its ACA launch
     int32_t reused = 0;        // 1: applied a resident matrix, no assembly
@@ -232,6 +232,7 @@ void bem_server_s::launch(Batch &b)
     const bool dry = flags & BEM_SERVER_DRY_RUN;
     cudaStream_t st = streams[b.slot];
     b.t_launch = steady_ms();
+    for (Req *r : b.reqs) r->t_launch = b.t_launch;
     if (dry) {
         // one simulated ACA launch per kind of matrix among the assemblies
         std::map<std::tuple<int, int, int>, int> kinds;
@@ -633,6 +634,8 @@ static void fill_info(const Req &r, bem_request_info *info)
     info->assembly_ms = r.asm_ms;
     info->launch_requests = r.launch_reqs;
     info->reused = r.reused;
+    info->t_ready_ms = r.t_ready;
+    info->t_launch_ms = r.t_launch;
 }
 
 int bem_server_poll(bem_server S, int64_t id, bem_request_info *info)
