@@ -2270,8 +2270,11 @@ void assemble_end(bem_hmat H, cudaStream_t st)
 // assemble_pool and enqueue_near on st): the blocks of each work shape from
 // every matrix, merged longest first, each item naming its matrix's job.
 // sm_share < 1 caps the launch's CTAs at that share of the device, so that
-// launches on other streams find free SMs while it runs.
-int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st, double sm_share)
+// launches on other streams find free SMs while it runs.  pinned (optional):
+// page-locked staging of pinned_bytes for the work list, which must stay
+// untouched until the stream has run the copies.
+int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st, double sm_share,
+                      void *pinned, size_t pinned_bytes)
 {
     if (hs.empty()) return BEM_OK;
     DeviceConsts &D = device_consts();
@@ -2310,9 +2313,18 @@ int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st, double s
     CU(lib_malloc_async(&buf, jb + ib + sizeof(AcaQueue), st));
     char *b = (char *)buf;
     AcaQueue *Q = (AcaQueue *)(b + jb + ib);
-    cudaError_t e = cudaMemcpyAsync(b, jobs.data(), jobs.size() * sizeof(AcaJob),
+    // from page-locked staging if the caller has some (a copy from pageable
+    // memory first waits for the stream's pending work)
+    const void *src_jobs = jobs.data(), *src_items = items.data();
+    if (pinned && pinned_bytes >= jb + ib) {
+        std::memcpy(pinned, jobs.data(), jobs.size() * sizeof(AcaJob));
+        std::memcpy((char *)pinned + jb, items.data(), ib);
+        src_jobs = pinned;
+        src_items = (char *)pinned + jb;
+    }
+    cudaError_t e = cudaMemcpyAsync(b, src_jobs, jobs.size() * sizeof(AcaJob),
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b + jb, items.data(), ib, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + jb, src_items, ib, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(Q, 0, sizeof(AcaQueue), st);
     if (e == cudaSuccess) {
         AcaWork w{(const AcaJob *)b, (const int64_t *)(b + jb),

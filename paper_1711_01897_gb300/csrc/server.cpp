@@ -51,8 +51,9 @@ constexpr double kBatchWindowMs = 2.0;
 constexpr int64_t kLargeTriangles = 40000;
 constexpr double kLargeSmShare = 0.75;
 constexpr double kLargeWaitMs = 50.0;
-// Admission: a request that cannot start lets younger ones pass for at most
-// this long; at most kMaxLargeRunning large requests run at once.
+// Admission: a request that does not fit the budget lets younger ones pass;
+// after this long its bytes are held for it.  At most kMaxLargeRunning large
+// requests run at once.
 constexpr double kBypassMs = 300.0;
 constexpr int64_t kMaxLargeRunning = 2;
 
@@ -128,6 +129,8 @@ struct bem_server_s {
     std::thread engine;
     cudaStream_t streams[kEngineStreams] = {};
     cudaEvent_t events[kEngineStreams] = {};
+    void *staging[kEngineStreams] = {};     // page-locked work-list staging per stream
+    size_t staging_bytes[kEngineStreams] = {};
     Batch inflight[kEngineStreams];
 
     void worker();
@@ -277,8 +280,27 @@ void bem_server_s::launch(Batch &b)
     for (auto &kv : kinds) {
         std::vector<bem_hmat> hs;
         for (Req *r : kv.second) hs.push_back(r->H);
+        // the work list goes through this stream's page-locked staging,
+        // grown (rarely) before the stream has other work queued
+        size_t need = kv.second.size() * 256 + 4096;
+        for (Req *r : kv.second) need += (size_t)(r->T.size() / 3) * 4 * sizeof(int64_t);
+        if (staging_bytes[b.slot] < need) {
+            void *p = nullptr;
+            const size_t want = std::max<size_t>(need, size_t(32) << 20);
+            if (cudaHostAlloc(&p, want, cudaHostAllocDefault) == cudaSuccess) {
+                if (staging[b.slot]) {
+                    cudaStreamSynchronize(st);
+                    cudaFreeHost(staging[b.slot]);
+                }
+                staging[b.slot] = p;
+                staging_bytes[b.slot] = want;
+            } else {
+                cudaGetLastError();
+            }
+        }
         int rc = guarded_call([&]() -> int {
-            return enqueue_aca_fused(hs, st, b.large ? kLargeSmShare : 1.0);
+            return enqueue_aca_fused(hs, st, b.large ? kLargeSmShare : 1.0, staging[b.slot],
+                                     staging_bytes[b.slot]);
         });
         for (Req *r : kv.second) {
             r->launch_reqs = (int32_t)kv.second.size();
@@ -398,19 +420,17 @@ void bem_server_s::engine_loop()
                 lk.lock();
             }
         }
-        // admission in arrival order, evicting idle resident matrices; a
-        // request that cannot start yet (budget, running limit, or the
-        // assembly it reuses still on the way) lets younger ones pass while
-        // it has waited less than kBypassMs, then holds the queue until it
-        // starts
+        // admission in arrival order, evicting idle resident matrices.  A
+        // request that does not fit the budget lets younger ones pass; once it
+        // has waited kBypassMs its bytes are held for it, so that the younger
+        // ones only use what is left and it starts as soon as running requests
+        // give back enough.
+        int64_t held = 0;
         for (size_t qi = 0; qi < prepared.size();) {
+            if (running >= slots) break;
             Req *r = reqs[prepared[qi]].get();
             const bool lg = is_large(r);
-            auto hold = [&]() -> bool {   // true: stop scanning
-                return steady_ms() - r->t_ready >= kBypassMs;
-            };
-            if (running >= slots || (lg && running_large >= kMaxLargeRunning)) {
-                if (hold()) break;
+            if (lg && running_large >= kMaxLargeRunning) {
                 ++qi;
                 continue;
             }
@@ -449,10 +469,10 @@ void bem_server_s::engine_loop()
                 ++R->users;
                 ++reuse_hits;
             } else {
-                while (in_use + r->bytes > budget && evict_one()) {
+                while (in_use + r->bytes + held > budget && evict_one()) {
                 }
-                if (in_use + r->bytes > budget) {
-                    if (hold()) break;
+                if (in_use + r->bytes + held > budget) {
+                    if (steady_ms() - r->t_ready >= kBypassMs) held += r->bytes;
                     ++qi;
                     continue;
                 }
@@ -761,6 +781,7 @@ int bem_server_destroy(bem_server S)
     for (int s = 0; s < kEngineStreams; ++s) {
         if (S->streams[s]) cudaStreamDestroy(S->streams[s]);
         if (S->events[s]) cudaEventDestroy(S->events[s]);
+        if (S->staging[s]) cudaFreeHost(S->staging[s]);
     }
     delete S;
     return BEM_OK;
