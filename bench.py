@@ -854,6 +854,9 @@ def large_record(args, spec, steps: int, warmup: int, cpu_baseline: bool = True)
             "data": "synthetic", "config": {"workload": spec["workload"], "n_triangles": n, "k": k,
                                            "aca_eps": spec["eps"], "leaf_size": LEAF, "eta": ETA},
             "h_assembly_ms": float(np.median(asm_ms)), "tree_and_upload_s": setup_s,
+            "tree_parts_ms": {"clusters": st["time_tree_clusters_ms"], "blocks": st["time_tree_blocks_ms"],
+                              "lists": st["time_tree_lists_ms"], "upload": st["time_tree_upload_ms"],
+                              "tree_total": st["time_tree_ms"]},
             "integrals_per_assembly": ents / steps,
             "phase_ms": {"near": st["time_near_ms"], "singular": st["time_singular_ms"],
                          "aca": st["time_far_ms"]},

@@ -782,6 +782,7 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
 }
 
 // The job of work item i and the block's index in that job's arrays.
+// (nullptr for an item that names no block of the launch's jobs: skipped)
 __device__ __forceinline__ const AcaJob *item_job(const AcaWork &w, int64_t i, int64_t &idx)
 {
     if (!w.items) {
@@ -790,7 +791,10 @@ __device__ __forceinline__ const AcaJob *item_job(const AcaWork &w, int64_t i, i
     }
     const int64_t it = w.items[i];
     idx = it & ((int64_t(1) << kItemShift) - 1);
-    return w.jobs + (it >> kItemShift);
+    const int64_t j = it >> kItemShift;
+    if (j < 0 || j >= w.n_jobs) return nullptr;
+    const AcaJob *J = w.jobs + j;
+    return idx < J->n_far ? J : nullptr;
 }
 
 // Blocks of the half- and quarter-warp shapes, W lanes each, 32 / W per
@@ -814,9 +818,9 @@ __device__ __forceinline__ void aca_subgroups(const AcaWork &w, const QuadRule &
         b0 = __shfl_sync(0xffffffffu, b0, 0);
         if (b0 >= count) break;
         const int64_t b = b0 + gi;
-        if (b < count) {
-            int64_t idx;
-            const AcaJob *J = item_job(w, first + b, idx);
+        int64_t idx = 0;
+        const AcaJob *J = b < count ? item_job(w, first + b, idx) : nullptr;
+        if (J) {
             aca_block<SubGroup<W>, OP, CPLX, PREC, DOF, RULES>(
                 sg, J->g, R, J->k, J->eps, J->far + idx, J->chunks + idx, (T *)J->pool, J->P, gs[gi],
                 zwarp + gi * ZW, nullptr);
@@ -849,6 +853,7 @@ k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
         if (b >= n_big) break;
         int64_t idx;
         const AcaJob *J = item_job(w, b, idx);
+        if (!J) continue;
         aca_block<CtaGroup, OP, CPLX, PREC, DOF, RULES>(cg, J->g, R, J->k, J->eps, J->far + idx,
                                                         J->chunks + idx, (T *)J->pool, J->P,
                                                         *reinterpret_cast<GroupSmem<CPLX> *>(garea[0]),
@@ -865,6 +870,7 @@ k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
         if (b >= n_small) break;
         int64_t idx;
         const AcaJob *J = item_job(w, n_big + b, idx);
+        if (!J) continue;
         aca_block<WarpGroup, OP, CPLX, PREC, DOF, RULES>(wg, J->g, R, J->k, J->eps, J->far + idx,
                                                          J->chunks + idx, (T *)J->pool, J->P,
                                                          *reinterpret_cast<GroupSmem<CPLX> *>(garea[wi]),
@@ -889,9 +895,9 @@ k_aca(AcaWork w, QuadRule R, int zwords_small, AcaQueue *Q)
             b0 = __shfl_sync(0xffffffffu, b0, 0);
             if (b0 >= n_tiny) break;
             const int64_t b = b0 + wg.lane;
-            if (b < n_tiny) {
-                int64_t idx;
-                const AcaJob *J = item_job(w, f5 + b, idx);
+            int64_t idx = 0;
+            const AcaJob *J = b < n_tiny ? item_job(w, f5 + b, idx) : nullptr;
+            if (J) {
                 aca_lane<OP, CPLX, PREC, RULES>(J->g, R, J->k, J->eps, J->far + idx,
                                                 J->chunks + idx, (T *)J->pool, J->P);
             }

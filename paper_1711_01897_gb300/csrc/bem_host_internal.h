@@ -27,7 +27,7 @@ void hmat_free_synced(bem_hmat hmat);
 int assemble_begin(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec, cudaStream_t st);
 void assemble_pool(bem_hmat H, cudaStream_t st);
 void enqueue_near(bem_hmat H, cudaStream_t st, bool capturing);
-void enqueue_finish(bem_hmat H, cudaStream_t st, bool capturing);
+void enqueue_finish(bem_hmat H, cudaStream_t st, bool capturing, bool mark_aca_end = true);
 int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st, double sm_share = 1.0,
                       void *pinned = nullptr, size_t pinned_bytes = 0);
 // true if the last launch ran out of factor pool (then hmat_assemble alone

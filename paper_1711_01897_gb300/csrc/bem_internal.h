@@ -162,6 +162,7 @@ struct AcaJob {
     void *pool;
     Pool *P;
     double k, eps;
+    int64_t n_far;           // entries of far and chunks
 };
 
 // Work list of one ACA launch: the blocks of each work shape (AcaShape
@@ -177,6 +178,7 @@ struct AcaWork {
     int64_t n[5];            // blocks per work shape (AcaShape order; the items in that order)
     int64_t max_m_big, max_m_small;  // most rows of a CTA block, of a warp block
     int max_ctas = 0;        // > 0: at most this many CTAs (leaves SMs to other streams)
+    int64_t n_jobs = 1;      // entries of jobs (items naming another job are skipped)
 };
 
 // Read-only view of a mesh and of already-initialised per-device constants,

@@ -1177,8 +1177,11 @@ struct bem_hmat_s {
     double g_k = 0, g_eps = 0;
     void *g_pool = nullptr, *g_near = nullptr;
     int64_t g_nodes = 0, g_pool_elems = -1;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaStream_t cap_stream = nullptr;
+    // timing: 0 start, 1 end of the near field, 2 end of the ACA, 3 end of the
+    // regular near pairs, 4 start of the ACA
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // near field beside the ACA
+    cudaStream_t cap_stream = nullptr, side_stream = nullptr;
     Pool *pin_pool = nullptr;       // pinned readback slots
     AcaStats *pin_stats = nullptr;
     AcaJob *pin_job = nullptr;      // pinned source of d_job (this matrix as one ACA job)
@@ -1187,6 +1190,9 @@ struct bem_hmat_s {
         pinned_release(pin_job);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (side_stream) cudaStreamDestroy(side_stream);
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        if (join_ev) cudaEventDestroy(join_ev);
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
         pinned_release(pin_pool);
@@ -2141,7 +2147,8 @@ void assemble_pool(bem_hmat H, cudaStream_t st)
     if (H->d_pool.bytes < (size_t)H->pool_want * esz) H->d_pool.alloc((size_t)H->pool_want * esz, st);
     H->pool_elems = H->pool_want;
     *H->pin_job = AcaJob{H->geom.g, H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
-                         H->d_pool.p, H->d_poolhdr.as<Pool>(), H->k, H->eps};
+                         H->d_pool.p, H->d_poolhdr.as<Pool>(), H->k, H->eps,
+                         (int64_t)H->far.size()};
     CU(cudaMemcpyAsync(H->d_job.p, H->pin_job, sizeof(AcaJob), cudaMemcpyHostToDevice, st));
 }
 
@@ -2154,15 +2161,19 @@ static void record(cudaEvent_t e, cudaStream_t st, bool capturing)
 // Pool header, queue and totals reset; near field: regular pairs, then the
 // touching pairs (FP64).  Events 0 (start), 3 (after the regular pairs) and
 // 1 (end of the near field).
-void enqueue_near(bem_hmat H, cudaStream_t st, bool capturing)
+static void enqueue_reset(bem_hmat H, cudaStream_t st, bool capturing)
+{
+    record(H->ev[0], st, capturing);
+    CU(launch_aca_reset(H->d_poolhdr.as<Pool>(), (unsigned long long)H->pool_elems,
+                        H->d_queue.as<AcaQueue>(), H->d_acastats.as<AcaStats>(), st));
+}
+
+static void enqueue_near_field(bem_hmat H, cudaStream_t st, bool capturing)
 {
     DeviceConsts &D = device_consts();
     const int aop = H->op == BEM_HYPS ? BEM_SLP : H->op;
     const double k = H->k;
     const int prec = H->prec;
-    record(H->ev[0], st, capturing);
-    CU(launch_aca_reset(H->d_poolhdr.as<Pool>(), (unsigned long long)H->pool_elems,
-                        H->d_queue.as<AcaQueue>(), H->d_acastats.as<AcaStats>(), st));
     if (H->dofs == 1) {
         CU(launch_near_regular(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
                                (int64_t)H->near.size(), H->d_near_data.p, st));
@@ -2186,6 +2197,13 @@ void enqueue_near(bem_hmat H, cudaStream_t st, bool capturing)
     record(H->ev[1], st, capturing);
 }
 
+void enqueue_near(bem_hmat H, cudaStream_t st, bool capturing)
+{
+    enqueue_reset(H, st, capturing);
+    enqueue_near_field(H, st, capturing);
+    record(H->ev[4], st, capturing);
+}
+
 // The persistent ACA over this matrix's admissible blocks alone.
 void enqueue_aca_own(bem_hmat H, cudaStream_t st)
 {
@@ -2201,9 +2219,9 @@ void enqueue_aca_own(bem_hmat H, cudaStream_t st)
 
 // Event 2 (end of the ACA), rank prefix sums and totals, and the readbacks
 // of the pool header and the totals.
-void enqueue_finish(bem_hmat H, cudaStream_t st, bool capturing)
+void enqueue_finish(bem_hmat H, cudaStream_t st, bool capturing, bool mark_aca_end)
 {
-    record(H->ev[2], st, capturing);
+    if (mark_aca_end) record(H->ev[2], st, capturing);
     CU(launch_aca_finish(H->d_far.as<FarBlock>(), H->d_chunks.as<FarChunks>(),
                          (int64_t)H->far.size(), H->d_toff.as<int64_t>(), H->d_tiles.as<int64_t>(),
                          H->d_acastats.as<AcaStats>(), st));
@@ -2231,7 +2249,7 @@ void assemble_end(bem_hmat H, cudaStream_t st)
     const AcaStats ast = *H->pin_stats;
     float tn = 0, tf = 0, tr = 0;
     CU(cudaEventElapsedTime(&tn, ev[0], ev[1]));
-    CU(cudaEventElapsedTime(&tf, ev[1], ev[2]));
+    CU(cudaEventElapsedTime(&tf, ev[4], ev[2]));
     CU(cudaEventElapsedTime(&tr, ev[0], ev[3]));
     H->t_near = tn;
     H->t_far = tf;
@@ -2331,6 +2349,7 @@ int enqueue_aca_fused(const std::vector<bem_hmat> &hs, cudaStream_t st, double s
                   {(int64_t)cls[0].size(), (int64_t)cls[1].size(), (int64_t)cls[2].size(),
                    (int64_t)cls[3].size(), (int64_t)cls[4].size()},
                   max_big, max_small};
+        w.n_jobs = (int64_t)jobs.size();
         // a share of the SMs: 2 CTAs of the ACA fit on an SM
         if (sm_share < 1.0) w.max_ctas = std::max(1, (int)(sm_share * 2 * D.num_sms));
         e = launch_aca(w, D.rule, aop, H0->cplx, H0->prec, Q, D.num_sms, st, 1, H0->has_rules);
@@ -2404,10 +2423,25 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         }
         // the whole sequence: near field (regular, then singular pairs, FP64),
         // then the persistent ACA over all admissible blocks and its totals
+        if (!H->side_stream) {
+            CU(cudaStreamCreateWithFlags(&H->side_stream, cudaStreamNonBlocking));
+            CU(cudaEventCreateWithFlags(&H->fork_ev, cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&H->join_ev, cudaEventDisableTiming));
+        }
+        // the near field (regular, then touching pairs) on a side stream
+        // beside the persistent ACA, which needs only the reset: the regular
+        // pairs' FP32 and MUFU work overlaps the ACA's FP64 work
         auto enqueue = [&](cudaStream_t s, bool capturing) {
-            enqueue_near(H, s, capturing);
+            enqueue_reset(H, s, capturing);
+            CU(cudaEventRecord(H->fork_ev, s));
+            CU(cudaStreamWaitEvent(H->side_stream, H->fork_ev, 0));
+            enqueue_near_field(H, H->side_stream, capturing);
+            CU(cudaEventRecord(H->join_ev, H->side_stream));
+            record(H->ev[4], s, capturing);
             enqueue_aca_own(H, s);
-            enqueue_finish(H, s, capturing);
+            record(H->ev[2], s, capturing);
+            CU(cudaStreamWaitEvent(s, H->join_ev, 0));
+            enqueue_finish(H, s, capturing, false);
         };
         for (int attempt = 0;; ++attempt) {
             assemble_pool(H, st);

@@ -277,30 +277,40 @@ void bem_server_s::launch(Batch &b)
     std::map<std::tuple<int, int, int, int>, std::vector<Req *>> kinds;
     for (Req *r : ok)
         if (!r->res) kinds[{r->op, r->k != 0.0, r->prec, hmat_has_rules(r->H) ? 1 : 0}].push_back(r);
+    // each launch's work list goes through its own region of this stream's
+    // page-locked staging (the copies run later on the stream, so no region
+    // is reused within a batch); the staging grows (rarely) while the
+    // stream has no work queued
+    std::vector<size_t> bound;
+    size_t total = 0;
+    for (auto &kv : kinds) {
+        size_t need = kv.second.size() * sizeof(AcaJob) + 256 + 4096;
+        for (Req *r : kv.second) need += (size_t)(r->T.size() / 3) * 4 * sizeof(int64_t);
+        need = (need + 255) / 256 * 256;
+        bound.push_back(need);
+        total += need;
+    }
+    if (staging_bytes[b.slot] < total) {
+        void *p = nullptr;
+        const size_t want = std::max<size_t>(total, size_t(32) << 20);
+        if (cudaHostAlloc(&p, want, cudaHostAllocDefault) == cudaSuccess) {
+            if (staging[b.slot]) cudaFreeHost(staging[b.slot]);
+            staging[b.slot] = p;
+            staging_bytes[b.slot] = want;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    const bool staged = staging[b.slot] && staging_bytes[b.slot] >= total;
+    size_t at = 0, q = 0;
     for (auto &kv : kinds) {
         std::vector<bem_hmat> hs;
         for (Req *r : kv.second) hs.push_back(r->H);
-        // the work list goes through this stream's page-locked staging,
-        // grown (rarely) before the stream has other work queued
-        size_t need = kv.second.size() * 256 + 4096;
-        for (Req *r : kv.second) need += (size_t)(r->T.size() / 3) * 4 * sizeof(int64_t);
-        if (staging_bytes[b.slot] < need) {
-            void *p = nullptr;
-            const size_t want = std::max<size_t>(need, size_t(32) << 20);
-            if (cudaHostAlloc(&p, want, cudaHostAllocDefault) == cudaSuccess) {
-                if (staging[b.slot]) {
-                    cudaStreamSynchronize(st);
-                    cudaFreeHost(staging[b.slot]);
-                }
-                staging[b.slot] = p;
-                staging_bytes[b.slot] = want;
-            } else {
-                cudaGetLastError();
-            }
-        }
+        void *region = staged ? (char *)staging[b.slot] + at : nullptr;
+        const size_t region_bytes = staged ? bound[q] : 0;
+        at += bound[q++];
         int rc = guarded_call([&]() -> int {
-            return enqueue_aca_fused(hs, st, b.large ? kLargeSmShare : 1.0, staging[b.slot],
-                                     staging_bytes[b.slot]);
+            return enqueue_aca_fused(hs, st, b.large ? kLargeSmShare : 1.0, region, region_bytes);
         });
         for (Req *r : kv.second) {
             r->launch_reqs = (int32_t)kv.second.size();
