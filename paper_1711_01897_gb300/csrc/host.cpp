@@ -1180,8 +1180,7 @@ struct bem_hmat_s {
     // timing: 0 start, 1 end of the near field, 2 end of the ACA, 3 end of the
     // regular near pairs, 4 start of the ACA
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // near field beside the ACA
-    cudaStream_t cap_stream = nullptr, side_stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
     Pool *pin_pool = nullptr;       // pinned readback slots
     AcaStats *pin_stats = nullptr;
     AcaJob *pin_job = nullptr;      // pinned source of d_job (this matrix as one ACA job)
@@ -1190,9 +1189,6 @@ struct bem_hmat_s {
         pinned_release(pin_job);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
-        if (side_stream) cudaStreamDestroy(side_stream);
-        if (fork_ev) cudaEventDestroy(fork_ev);
-        if (join_ev) cudaEventDestroy(join_ev);
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
         pinned_release(pin_pool);
@@ -2423,25 +2419,15 @@ int hmat_assemble(bem_hmat H, int32_t op, double k, double aca_eps, int32_t prec
         }
         // the whole sequence: near field (regular, then singular pairs, FP64),
         // then the persistent ACA over all admissible blocks and its totals
-        if (!H->side_stream) {
-            CU(cudaStreamCreateWithFlags(&H->side_stream, cudaStreamNonBlocking));
-            CU(cudaEventCreateWithFlags(&H->fork_ev, cudaEventDisableTiming));
-            CU(cudaEventCreateWithFlags(&H->join_ev, cudaEventDisableTiming));
-        }
-        // the near field (regular, then touching pairs) on a side stream
-        // beside the persistent ACA, which needs only the reset: the regular
-        // pairs' FP32 and MUFU work overlaps the ACA's FP64 work
+        // the whole sequence: near field (regular, then singular pairs, FP64),
+        // then the persistent ACA over all admissible blocks and its totals.
+        // (Running the near field on a second stream beside the ACA was
+        // measured: the step took as long, the ACA slowing by what the near
+        // field saved.)
         auto enqueue = [&](cudaStream_t s, bool capturing) {
-            enqueue_reset(H, s, capturing);
-            CU(cudaEventRecord(H->fork_ev, s));
-            CU(cudaStreamWaitEvent(H->side_stream, H->fork_ev, 0));
-            enqueue_near_field(H, H->side_stream, capturing);
-            CU(cudaEventRecord(H->join_ev, H->side_stream));
-            record(H->ev[4], s, capturing);
+            enqueue_near(H, s, capturing);
             enqueue_aca_own(H, s);
-            record(H->ev[2], s, capturing);
-            CU(cudaStreamWaitEvent(s, H->join_ev, 0));
-            enqueue_finish(H, s, capturing, false);
+            enqueue_finish(H, s, capturing);
         };
         for (int attempt = 0;; ++attempt) {
             assemble_pool(H, st);

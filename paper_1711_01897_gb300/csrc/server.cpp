@@ -56,6 +56,9 @@ constexpr double kLargeWaitMs = 50.0;
 // requests run at once.
 constexpr double kBypassMs = 300.0;
 constexpr int64_t kMaxLargeRunning = 2;
+// Large requests may hold at most this share of the budget (running and
+// admitted), so that small requests always find room.
+constexpr double kLargeBudgetShare = 0.7;
 
 // An assembled H-matrix kept on the device after its request finished.
 struct Resident {
@@ -120,7 +123,7 @@ struct bem_server_s {
     int64_t next_id = 1;
     int64_t in_use = 0, peak = 0;
     int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, running = 0;
-    int64_t running_large = 0;
+    int64_t running_large = 0, in_use_large = 0;
     int64_t evictions = 0, reuse_hits = 0, fused_launches = 0, fused_requests = 0;
     int64_t max_launch_requests = 0;
     int preparing = 0;
@@ -171,7 +174,10 @@ void bem_server_s::finish_locked(Req *r, int status)
 {
     if (r->state == BEM_REQ_RUNNING) {
         --running;
-        if (is_large(r)) --running_large;
+        if (is_large(r)) {
+            --running_large;
+            in_use_large -= r->bytes;
+        }
     }
     r->status = status;
     r->state = status == BEM_OK ? BEM_REQ_DONE : BEM_REQ_FAILED;
@@ -435,7 +441,7 @@ void bem_server_s::engine_loop()
         // has waited kBypassMs its bytes are held for it, so that the younger
         // ones only use what is left and it starts as soon as running requests
         // give back enough.
-        int64_t held = 0;
+        int64_t held[2] = {0, 0};   // bytes held for waiting small / large requests
         for (size_t qi = 0; qi < prepared.size();) {
             if (running >= slots) break;
             Req *r = reqs[prepared[qi]].get();
@@ -479,14 +485,20 @@ void bem_server_s::engine_loop()
                 ++R->users;
                 ++reuse_hits;
             } else {
-                while (in_use + r->bytes + held > budget && evict_one()) {
+                const int64_t h = held[lg ? 1 : 0];
+                // (a large request alone may exceed the share: it then runs by itself)
+                const bool large_room =
+                    !lg || in_use_large == 0 ||
+                    (double)(in_use_large + r->bytes + h) <= kLargeBudgetShare * (double)budget;
+                while (large_room && in_use + r->bytes + h > budget && evict_one()) {
                 }
-                if (in_use + r->bytes + held > budget) {
-                    if (steady_ms() - r->t_ready >= kBypassMs) held += r->bytes;
+                if (!large_room || in_use + r->bytes + h > budget) {
+                    if (steady_ms() - r->t_ready >= kBypassMs) held[lg ? 1 : 0] += r->bytes;
                     ++qi;
                     continue;
                 }
                 in_use += r->bytes;
+                if (lg) in_use_large += r->bytes;
                 peak = std::max(peak, in_use);
             }
             prepared.erase(prepared.begin() + qi);
