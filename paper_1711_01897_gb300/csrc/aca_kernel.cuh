@@ -406,11 +406,22 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 const bool store = col || kk < kcap;
                 long long best = -1;
                 int64_t bidx = col ? m : 0;
+                // the single layer is symmetric (A_rj = A_jr): both passes
+                // evaluate (fixed triangle, varying triangle), the fixed one
+                // loaded once into registers; the other operators load both
+                // triangles of every entry in their own roles
+                constexpr bool kSym = OP == 0;
+                typename E::Tri tf;
+                if constexpr (kSym) E::load_compact(g, col ? b0 : a0, tf, R);
                 for (int64_t e = t; e < len; e += GS) {
                     typename E::Tri ta, tq;
-                    E::load(g, a0 + da * e, ta);
-                    E::load(g, b0 + db * e, tq);
-                    T a = V::from((eval_entry<RULES, E>(ta, tq, R, k, rule)));
+                    if constexpr (kSym) {
+                        E::load_compact(g, col ? a0 + e : b0 + e, tq, R);
+                    } else {
+                        E::load_compact(g, a0 + da * e, ta, R);
+                        E::load_compact(g, b0 + db * e, tq, R);
+                    }
+                    T a = V::from((eval_entry<RULES, E>(kSym ? tf : ta, tq, R, k, rule)));
                     for (int l = 0; l < kk; ++l)
                         a = V::fnma(S.cu[l],
                                     pool[S.chunk[l / KCHUNK] + xoff + (int64_t)(l % KCHUNK) * xld + e], a);

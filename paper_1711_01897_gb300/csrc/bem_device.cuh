@@ -129,6 +129,29 @@ __device__ __forceinline__ void load_trif(const DevGeom &g, int64_t p, TriF &t)
     t.s.lo = __ldg(f + 32 * (kFS + 1));
 }
 
+// The same view from 20 of the tile's fields: the second orbit's points are
+// rho21 times the first orbit's (QuadRule::rho21f), which saves a third of
+// the loads of a triangle where loads, not arithmetic, are scarce.
+__device__ __forceinline__ void load_trif_compact(const DevGeom &g, int64_t p, TriF &t, float rho)
+{
+    const float *f = tile_of(g, p);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        t.ch[c] = __ldg(f + 32 * (kFCh + c));
+        t.cl[c] = __ldg(f + 32 * (kFCl + c));
+        t.n[c] = __ldg(f + 32 * (kFN + c));
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            t.q[q][c] = __ldg(f + 32 * (kFQ + 3 * q + c));
+            t.q[3 + q][c] = rho * t.q[q][c];
+        }
+    t.s.hi = __ldg(f + 32 * kFS);
+    t.s.lo = __ldg(f + 32 * (kFS + 1));
+}
+
 __device__ __forceinline__ void load_ids_tile(const DevGeom &g, int64_t p, int v[3])
 {
     const float *f = tile_of(g, p);
@@ -452,6 +475,11 @@ struct RegularEntry<OP, CPLX, 0> {  // FP64
     {
         load_trid(g, p, t);
     }
+    static __device__ __forceinline__ void load_compact(const DevGeom &g, int64_t p, Tri &t,
+                                                        const QuadRule &)
+    {
+        load_trid(g, p, t);
+    }
     static __device__ __forceinline__ void load_scattered(const DevGeom &g, int64_t p, Tri &t)
     {
         load_trid(g, p, t);
@@ -479,6 +507,11 @@ struct RegularEntry<OP, CPLX, 1> {  // mixed
     static __device__ __forceinline__ void load(const DevGeom &g, int64_t p, Tri &t)
     {
         load_trif(g, p, t);
+    }
+    static __device__ __forceinline__ void load_compact(const DevGeom &g, int64_t p, Tri &t,
+                                                        const QuadRule &R)
+    {
+        load_trif_compact(g, p, t, R.rho21f);
     }
     static __device__ __forceinline__ void load_scattered(const DevGeom &g, int64_t p, Tri &t)
     {

@@ -52,6 +52,12 @@ struct QuadRule {
     float wlf[NQ][3];
     double beta3;
     float beta3f;
+    // The two orbits lie on the medians: the point of orbit t with dominant
+    // vertex v sits at (1 - 3 t)(v - centroid), so point 3 + m is
+    // rho21 times point m ((1 - 3 b) / (1 - 3 a), points m and 3 + m sharing
+    // their dominant vertex)
+    double rho21;
+    float rho21f;
 };
 
 // Regular rule of an admissible block (distance classes, Laplace, P0): the

@@ -304,6 +304,8 @@ QuadRule make_rule6()
     QuadRule R{};
     R.beta3 = 0.5 / (1.0 - 3.0 * b);
     R.beta3f = (float)R.beta3;
+    R.rho21 = (1.0 - 3.0 * b) / (1.0 - 3.0 * a);
+    R.rho21f = (float)R.rho21;
     const double orb[2] = {a, b}, ow[2] = {W1 / 3.0, W2 / 3.0};
     int k = 0;
     for (int o = 0; o < 2; ++o) {
