@@ -35,6 +35,19 @@ __device__ __forceinline__ double recip(double a)
     return r;
 }
 
+// A float from the high word of a double, scaled by 2^-E on the integer
+// pipe (the FP64 pipe, conversions included, is the scarce unit on this
+// part): the exponent is rebased by B = (896 + E) << 20 and the 20 mantissa
+// bits of the high word kept (relative error below 2^-20); magnitudes below
+// the float range flush to zero and above it saturate near 2^127.
+__device__ __forceinline__ float hi_to_float(double a, unsigned B)
+{
+    const unsigned h = (unsigned)__double2hiint(a);
+    const unsigned x = h & 0x7fffffffu;
+    const unsigned y = (min(max(x, B), B + (254u << 20)) - B) << 3;
+    return __uint_as_float(y | (h & 0x80000000u));
+}
+
 template <bool CPLX>
 struct VT;
 
@@ -70,6 +83,16 @@ struct VT<false> {
         return __shfl_down_sync(mask, a, o, width);
     }
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    // floor(log2 |a|) from a key
+    static __device__ __forceinline__ int key_exp2(long long k) { return (int)((k >> 52) & 0x7ff) - 1023; }
+    // conj(a) b accumulated in FP32, both factors scaled by 2^-E (B of hi_to_float)
+    using F = float;
+    static __device__ __forceinline__ F zerof() { return 0.f; }
+    static __device__ __forceinline__ F dotf(T a, T b, unsigned B, F acc)
+    {
+        return fmaf(hi_to_float(a, B), hi_to_float(b, B), acc);
+    }
+    static __device__ __forceinline__ T fromf(F a) { return (double)a; }
 };
 
 template <>
@@ -116,6 +139,20 @@ struct VT<true> {
                             __shfl_down_sync(mask, a.y, o, width));
     }
     static __device__ __forceinline__ T add(T a, T b) { return make_double2(a.x + b.x, a.y + b.y); }
+    // the key is |a|^2
+    static __device__ __forceinline__ int key_exp2(long long k)
+    {
+        return ((int)((k >> 52) & 0x7ff) - 1023) >> 1;
+    }
+    using F = float2;
+    static __device__ __forceinline__ F zerof() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ F dotf(T a, T b, unsigned B, F acc)
+    {
+        const float ax = hi_to_float(a.x, B), ay = hi_to_float(a.y, B);
+        const float bx = hi_to_float(b.x, B), by = hi_to_float(b.y, B);
+        return make_float2(fmaf(ax, bx, fmaf(ay, by, acc.x)), fmaf(ax, by, fmaf(-ay, bx, acc.y)));
+    }
+    static __device__ __forceinline__ T fromf(F a) { return make_double2(a.x, a.y); }
 };
 
 // ---- groups: a whole CTA or a single warp ---------------------------------
@@ -576,6 +613,39 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         // (k+1) * segments additions.
         double incr = 0.0, uv2 = 0.0;
         const int ncol = kk + 1;
+        // Mixed precision: the dot products in FP32 from floats formed on the
+        // integer pipe (hi_to_float), u scaled by 2^-E with 2^E the largest
+        // pivot so far, so that its squares and products stay in the float
+        // range (|v| <= 1: each row is divided by its largest entry); each
+        // product is rescaled by 2^2E in FP64.  The norm feeds only the
+        // stopping test, whose threshold a relative error of ~1e-6 moves by
+        // as much.  FP64 dot products in the FP64 path.
+        unsigned Bu = 0u;
+        double unscale = 1.0;
+        if constexpr (PREC == 1) {
+            int E = V::key_exp2(maxkey);
+            E = E < -500 ? -500 : (E > 500 ? 500 : E);
+            Bu = (unsigned)(896 + E) << 20;
+            unscale = __longlong_as_double((long long)(1023 + 2 * E) << 52);
+        }
+        // <u_l, u_k> and <v_l, v_k> over segment sgi of nseg
+        auto seg_dots = [&](int l, int sgi, int nseg, T &iu, T &iv) {
+            const T *ul = Uat(l, 0), *uk = Uat(kk, 0);
+            const T *vl = Vat(l, 0), *vk = Vat(kk, 0);
+            const int mi = (int)m, ni = (int)n;
+            const int r0 = (mi * sgi) / nseg, r1 = (mi * (sgi + 1)) / nseg;
+            const int j0 = (ni * sgi) / nseg, j1 = (ni * (sgi + 1)) / nseg;
+            if constexpr (PREC == 1) {
+                typename V::F fu = V::zerof(), fv = V::zerof();
+                for (int r = r0; r < r1; ++r) fu = V::dotf(ul[r], uk[r], Bu, fu);
+                for (int j = j0; j < j1; ++j) fv = V::dotf(vl[j], vk[j], 896u << 20, fv);
+                iu = V::fromf(fu);
+                iv = V::fromf(fv);
+            } else {
+                for (int r = r0; r < r1; ++r) iu = V::dotc(ul[r], uk[r], iu);
+                for (int j = j0; j < j1; ++j) iv = V::dotc(vl[j], vk[j], iv);
+            }
+        };
         if constexpr (Grp::kShuffle) {
             // power-of-two segments per column, summed by shuffle trees
             // within the group's lanes
@@ -587,22 +657,13 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 int nseg = 1;
                 while (nseg * 2 * kc <= GS) nseg *= 2;
                 T iu = V::zero(), iv = V::zero();
-                if (t < kc * nseg) {
-                    const int l = l0 + t % kc, sgi = t / kc;
-                    const T *ul = Uat(l, 0), *uk = Uat(kk, 0);
-                    const T *vl = Vat(l, 0), *vk = Vat(kk, 0);
-                    const int mi = (int)m, ni = (int)n;
-                    for (int r = (mi * sgi) / nseg, r1 = (mi * (sgi + 1)) / nseg; r < r1; ++r)
-                        iu = V::dotc(ul[r], uk[r], iu);
-                    for (int j = (ni * sgi) / nseg, j1 = (ni * (sgi + 1)) / nseg; j < j1; ++j)
-                        iv = V::dotc(vl[j], vk[j], iv);
-                }
+                if (t < kc * nseg) seg_dots(l0 + t % kc, t / kc, nseg, iu, iv);
                 for (int off = nseg / 2; off >= 1; off >>= 1) {
                     iu = V::add(iu, G.template shfl_down<V>(iu, off * kc));
                     iv = V::add(iv, G.template shfl_down<V>(iv, off * kc));
                 }
                 if (t < kc) {
-                    const double pr = V::re_mul(iu, iv);
+                    const double pr = V::re_mul(iu, iv) * unscale;
                     if (l0 + t == kk) {
                         incr += pr;
                         uv2_lane = pr;
@@ -618,16 +679,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 const int kc = (ncol - l0) < GS ? (ncol - l0) : GS;
                 const int nseg = GS / kc;
                 T iu = V::zero(), iv = V::zero();
-                if (t < kc * nseg) {
-                    const int l = l0 + t % kc, sgi = t / kc;
-                    const T *ul = Uat(l, 0), *uk = Uat(kk, 0);
-                    const T *vl = Vat(l, 0), *vk = Vat(kk, 0);
-                    const int mi = (int)m, ni = (int)n;
-                    for (int r = (mi * sgi) / nseg, r1 = (mi * (sgi + 1)) / nseg; r < r1; ++r)
-                        iu = V::dotc(ul[r], uk[r], iu);
-                    for (int j = (ni * sgi) / nseg, j1 = (ni * (sgi + 1)) / nseg; j < j1; ++j)
-                        iv = V::dotc(vl[j], vk[j], iv);
-                }
+                if (t < kc * nseg) seg_dots(l0 + t % kc, t / kc, nseg, iu, iv);
                 part[t] = iu;
                 part[GS + t] = iv;
                 G.sync();
@@ -637,7 +689,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                         su = V::add(su, part[q * kc + t]);
                         sv = V::add(sv, part[GS + q * kc + t]);
                     }
-                    const double pr = V::re_mul(su, sv);
+                    const double pr = V::re_mul(su, sv) * unscale;
                     if (l0 + t == kk) {
                         incr += pr;          // ||u_k||^2 ||v_k||^2
                         S.uv2 = pr;
@@ -764,14 +816,31 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
         }
         entries += m;
         // ||S_k||_F^2 increment: 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> + ||u_k||^2 ||v_k||^2
+        // (mixed precision: FP32 dot products as in aca_block)
         double incr = 0.0, uv2 = 0.0;
+        unsigned Bu = 0u;
+        double unscale = 1.0;
+        if constexpr (PREC == 1) {
+            int E = (int)((__double_as_longlong(maxpiv) >> 52) & 0x7ff) - 1023;
+            E = E < -500 ? -500 : (E > 500 ? 500 : E);
+            Bu = (unsigned)(896 + E) << 20;
+            unscale = __longlong_as_double((long long)(1023 + 2 * E) << 52);
+        }
         const T *uk = Uat(kk, 0), *vk = Vat(kk, 0);
         for (int l = 0; l <= kk; ++l) {
             const T *ul = Uat(l, 0), *vl = Vat(l, 0);
             T iu = V::zero(), iv = V::zero();
-            for (int r = 0; r < m; ++r) iu = V::dotc(ul[r], uk[r], iu);
-            for (int j = 0; j < n; ++j) iv = V::dotc(vl[j], vk[j], iv);
-            const double pr = V::re_mul(iu, iv);
+            if constexpr (PREC == 1) {
+                typename V::F fu = V::zerof(), fv = V::zerof();
+                for (int r = 0; r < m; ++r) fu = V::dotf(ul[r], uk[r], Bu, fu);
+                for (int j = 0; j < n; ++j) fv = V::dotf(vl[j], vk[j], 896u << 20, fv);
+                iu = V::fromf(fu);
+                iv = V::fromf(fv);
+            } else {
+                for (int r = 0; r < m; ++r) iu = V::dotc(ul[r], uk[r], iu);
+                for (int j = 0; j < n; ++j) iv = V::dotc(vl[j], vk[j], iv);
+            }
+            const double pr = V::re_mul(iu, iv) * unscale;
             if (l == kk) {
                 uv2 = pr;
                 incr += pr;
