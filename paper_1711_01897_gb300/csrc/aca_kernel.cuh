@@ -419,8 +419,13 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             // quadrature is compiled once per work shape (a smaller hot code
             // footprint); each entry loads both triangles, the fixed one by a
             // load that is the same for every lane.
+            // The pivot's reciprocal scales u_k as the column pass stores it
+            // (u_k v_k^T is the same rank-one term as with v_k scaled, and
+            // no separate pass over the row is needed); the keys that pick
+            // the next row are taken before the scaling.
             bool vanished = false, capped = false;
             long long bkey = -1;
+            T pinv = V::zero();
 #pragma unroll 1
             for (int ph = 0; ph < 2; ++ph) {
                 const bool col = ph != 0;
@@ -428,10 +433,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                     for (int l = t; l < kk; l += GS) S.cu[l] = *Uat(l, i);
                 } else {
                     G.sync();
-                    const T piv = *Vat(kk, bj);
-                    const T pinv = V::inv(piv);
-                    G.sync();
-                    for (int64_t j = t; j < n; j += GS) *Vat(kk, j) = V::mul(*Vat(kk, j), pinv);
+                    pinv = V::inv(*Vat(kk, bj));
                     for (int l = t; l < kk; l += GS) S.cu[l] = *Vat(l, bj);
                 }
                 G.sync();
@@ -462,7 +464,9 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                     for (int l = 0; l < kk; ++l)
                         a = V::fnma(S.cu[l],
                                     pool[S.chunk[l / KCHUNK] + xoff + (int64_t)(l % KCHUNK) * xld + e], a);
-                    if (store) pool[S.chunk[kk / KCHUNK] + xoff + (int64_t)(kk % KCHUNK) * xld + e] = a;
+                    if (store)
+                        pool[S.chunk[kk / KCHUNK] + xoff + (int64_t)(kk % KCHUNK) * xld + e] =
+                            col ? V::mul(a, pinv) : a;
                     // the column pass looks for the next row among the unused ones
                     if (!col || !((Z[e >> 5] >> (e & 31)) & 1u)) {
                         long long ky = V::key(a);
@@ -614,18 +618,22 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         double incr = 0.0, uv2 = 0.0;
         const int ncol = kk + 1;
         // Mixed precision: the dot products in FP32 from floats formed on the
-        // integer pipe (hi_to_float), u scaled by 2^-E with 2^E the largest
-        // pivot so far, so that its squares and products stay in the float
-        // range (|v| <= 1: each row is divided by its largest entry); each
-        // product is rescaled by 2^2E in FP64.  The norm feeds only the
+        // integer pipe (hi_to_float), the factor that carries the pivots'
+        // magnitude scaled by 2^-E with 2^E the largest pivot so far, so that
+        // its squares and products stay in the float range (the other factor
+        // is divided by its pivot, the largest entry of its row, and is
+        // O(1)); each product is rescaled by 2^2E in FP64.  The norm feeds only the
         // stopping test, whose threshold a relative error of ~1e-6 moves by
         // as much.  FP64 dot products in the FP64 path.
-        unsigned Bu = 0u;
+        unsigned Bu = 896u << 20, Bv = 896u << 20;
         double unscale = 1.0;
         if constexpr (PREC == 1) {
             int E = V::key_exp2(maxkey);
             E = E < -500 ? -500 : (E > 500 ? 500 : E);
-            Bu = (unsigned)(896 + E) << 20;
+            // P0: u_k carries 1/pivot (|u| = O(1)), v_k the pivot's scale;
+            // DP1: v_k is divided by the pivot (|v| <= 1), u_k is not
+            if constexpr (DOF == 1) Bv = (unsigned)(896 + E) << 20;
+            else Bu = (unsigned)(896 + E) << 20;
             unscale = __longlong_as_double((long long)(1023 + 2 * E) << 52);
         }
         // <u_l, u_k> and <v_l, v_k> over segment sgi of nseg
@@ -638,7 +646,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             if constexpr (PREC == 1) {
                 typename V::F fu = V::zerof(), fv = V::zerof();
                 for (int r = r0; r < r1; ++r) fu = V::dotf(ul[r], uk[r], Bu, fu);
-                for (int j = j0; j < j1; ++j) fv = V::dotf(vl[j], vk[j], 896u << 20, fv);
+                for (int j = j0; j < j1; ++j) fv = V::dotf(vl[j], vk[j], Bv, fv);
                 iu = V::fromf(fu);
                 iv = V::fromf(fv);
             } else {
