@@ -93,6 +93,14 @@ struct VT<false> {
         return fmaf(hi_to_float(a, B), hi_to_float(b, B), acc);
     }
     static __device__ __forceinline__ T fromf(F a) { return (double)a; }
+    static __device__ __forceinline__ F tof(T a, unsigned B) { return hi_to_float(a, B); }
+    static __device__ __forceinline__ F fdot(F a, F b, F acc) { return fmaf(a, b, acc); }  // conj(a) b
+    static __device__ __forceinline__ F addf(F a, F b) { return a + b; }
+    static __device__ __forceinline__ float re_mulf(F a, F b) { return a * b; }
+    static __device__ __forceinline__ F shfl_xorf(F a, int d, unsigned mask)
+    {
+        return __shfl_xor_sync(mask, a, d);
+    }
 };
 
 template <>
@@ -153,6 +161,20 @@ struct VT<true> {
         return make_float2(fmaf(ax, bx, fmaf(ay, by, acc.x)), fmaf(ax, by, fmaf(-ay, bx, acc.y)));
     }
     static __device__ __forceinline__ T fromf(F a) { return make_double2(a.x, a.y); }
+    static __device__ __forceinline__ F tof(T a, unsigned B)
+    {
+        return make_float2(hi_to_float(a.x, B), hi_to_float(a.y, B));
+    }
+    static __device__ __forceinline__ F fdot(F a, F b, F acc)  // conj(a) b + acc
+    {
+        return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+    }
+    static __device__ __forceinline__ F addf(F a, F b) { return make_float2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ float re_mulf(F a, F b) { return fmaf(a.x, b.x, -a.y * b.y); }
+    static __device__ __forceinline__ F shfl_xorf(F a, int d, unsigned mask)
+    {
+        return make_float2(__shfl_xor_sync(mask, a.x, d), __shfl_xor_sync(mask, a.y, d));
+    }
 };
 
 // ---- groups: a whole CTA or a single warp ---------------------------------
@@ -209,6 +231,7 @@ __device__ __forceinline__ void warp_argmax_key(long long &key, int64_t &idx)
 template <int W>
 struct SubGroup {
     static constexpr bool kShuffle = true;
+    static constexpr int kWidth = W;
     int lane;        // 0 .. W - 1
     unsigned mask;   // the group's lanes in the warp
     __device__ int rank() const { return lane; }
@@ -240,7 +263,65 @@ struct SubGroup {
         return V::shfl_down(a, o, mask, W);
     }
     __device__ double shfl_idx(double a, int src) const { return __shfl_sync(mask, a, src, W); }
+    // butterfly sum: every lane gets the same bits
+    __device__ float sumf(float a) const
+    {
+#pragma unroll
+        for (int o = W / 2; o > 0; o >>= 1) a += __shfl_xor_sync(mask, a, o);
+        return a;
+    }
 };
+
+// Dot products <x_l, x_k> for the NC factor columns l0 .. l0 + NC - 1 (those
+// below ncol) of a group of W lanes: lanes stride over the rows (coalesced),
+// each holding NC accumulators and forming the float of x_k[r] once; a
+// butterfly reduce-scatter over the low log2(NC) lane bits leaves lane t
+// with column l0 + bitrev(t mod NC), summed over the lanes of its NC-lane
+// set, and xor rounds over the higher bits complete the group sum.  cols:
+// the first column of the chunk that holds l0 and of the next chunk (stride
+// ld between the columns of a chunk); xk: column k.
+template <class V, int NC, int W>
+__device__ __forceinline__ typename V::F group_col_dots(const typename V::T *c0, const typename V::T *c1,
+                                                        int64_t ld, const typename V::T *xk, int len,
+                                                        int nvalid, unsigned B, int t, unsigned mask)
+{
+    using F = typename V::F;
+    F acc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) acc[q] = V::zerof();
+    for (int r = t; r < len; r += W) {
+        const F x = V::tof(xk[r], B);
+#pragma unroll
+        for (int q = 0; q < NC; ++q)
+            if (q < nvalid) {
+                const typename V::T *c = (q < KCHUNK ? c0 : c1) + (int64_t)(q % KCHUNK) * ld;
+                acc[q] = V::fdot(V::tof(c[r], B), x, acc[q]);
+            }
+    }
+#pragma unroll
+    for (int d = 1, n = NC / 2; n >= 1; d <<= 1, n >>= 1) {
+        const bool up = (t & d) != 0;
+#pragma unroll
+        for (int q = 0; q < n; ++q) {
+            const F send = up ? acc[q] : acc[q + n];
+            const F keep = up ? acc[q + n] : acc[q];
+            acc[q] = V::addf(keep, V::shfl_xorf(send, d, mask));
+        }
+    }
+#pragma unroll
+    for (int d = NC; d < W; d <<= 1) acc[0] = V::addf(acc[0], V::shfl_xorf(acc[0], d, mask));
+    return acc[0];
+}
+
+template <int NC>
+__device__ __forceinline__ int bitrev_low(int t)
+{
+    int c = 0;
+#pragma unroll
+    for (int b = 1, v = NC / 2; v >= 1; b <<= 1, v >>= 1)
+        if (t & b) c += v;
+    return c;
+}
 using WarpGroup = SubGroup<32>;
 
 struct CtaGroup {
@@ -654,7 +735,36 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 for (int j = j0; j < j1; ++j) iv = V::dotc(vl[j], vk[j], iv);
             }
         };
-        if constexpr (Grp::kShuffle) {
+        if constexpr (Grp::kShuffle && PREC == 1) {
+            // columns in register groups of NC (group_col_dots); the
+            // increment summed in FP32 (scaled), then rescaled once
+            constexpr int NC = CPLX ? 4 : 8;
+            constexpr int W = Grp::kWidth;
+            static_assert(KCHUNK == 4 && NC <= 2 * KCHUNK && NC <= W, "column groups span two chunks");
+            float incr_f = 0.f, uv2_f = 0.f;
+            const T *uk = Uat(kk, 0), *vk = Vat(kk, 0);
+            for (int l0 = 0; l0 < ncol; l0 += NC) {
+                const int nv = ncol - l0 < NC ? ncol - l0 : NC;
+                const T *u0 = pool + S.chunk[l0 / KCHUNK];
+                const T *u1 = nv > KCHUNK ? pool + S.chunk[l0 / KCHUNK + 1] : u0;
+                const typename V::F su =
+                    group_col_dots<V, NC, W>(u0, u1, m, uk, (int)m, nv, Bu, t, G.mask);
+                const typename V::F sv = group_col_dots<V, NC, W>(
+                    u0 + (int64_t)KCHUNK * m, u1 + (int64_t)KCHUNK * m, n, vk, (int)n, nv, Bv, t, G.mask);
+                const int c = l0 + bitrev_low<NC>(t % NC);
+                if (t < NC && c < ncol) {
+                    const float pr = V::re_mulf(su, sv);
+                    if (c == kk) {
+                        incr_f += pr;
+                        uv2_f = pr;
+                    } else {
+                        incr_f += 2.f * pr;
+                    }
+                }
+            }
+            incr = (double)G.sumf(incr_f) * unscale;
+            uv2 = (double)G.sumf(uv2_f) * unscale;
+        } else if constexpr (Grp::kShuffle) {
             // power-of-two segments per column, summed by shuffle trees
             // within the group's lanes
             double uv2_lane = 0.0;
