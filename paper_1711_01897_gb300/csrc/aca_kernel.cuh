@@ -40,6 +40,13 @@ __device__ __forceinline__ double recip(double a)
 // part): the exponent is rebased by B = (896 + E) << 20 and the 20 mantissa
 // bits of the high word kept (relative error below 2^-20); magnitudes below
 // the float range flush to zero and above it saturate near 2^127.
+__device__ __forceinline__ float hiword_to_float(unsigned h, unsigned B)
+{
+    const unsigned x = h & 0x7fffffffu;
+    const unsigned y = (min(max(x, B), B + (254u << 20)) - B) << 3;
+    return __uint_as_float(y | (h & 0x80000000u));
+}
+
 __device__ __forceinline__ float hi_to_float(double a, unsigned B)
 {
     const unsigned h = (unsigned)__double2hiint(a);
@@ -94,6 +101,11 @@ struct VT<false> {
     }
     static __device__ __forceinline__ T fromf(F a) { return (double)a; }
     static __device__ __forceinline__ F tof(T a, unsigned B) { return hi_to_float(a, B); }
+    // from memory: only the high word is loaded
+    static __device__ __forceinline__ F tofp(const T *p, unsigned B)
+    {
+        return hiword_to_float(reinterpret_cast<const unsigned *>(p)[1], B);
+    }
     static __device__ __forceinline__ F fdot(F a, F b, F acc) { return fmaf(a, b, acc); }  // conj(a) b
     static __device__ __forceinline__ F addf(F a, F b) { return a + b; }
     static __device__ __forceinline__ float re_mulf(F a, F b) { return a * b; }
@@ -164,6 +176,11 @@ struct VT<true> {
     static __device__ __forceinline__ F tof(T a, unsigned B)
     {
         return make_float2(hi_to_float(a.x, B), hi_to_float(a.y, B));
+    }
+    static __device__ __forceinline__ F tofp(const T *p, unsigned B)
+    {
+        const unsigned *w = reinterpret_cast<const unsigned *>(p);
+        return make_float2(hiword_to_float(w[1], B), hiword_to_float(w[3], B));
     }
     static __device__ __forceinline__ F fdot(F a, F b, F acc)  // conj(a) b + acc
     {
@@ -289,13 +306,14 @@ __device__ __forceinline__ typename V::F group_col_dots(const typename V::T *c0,
     F acc[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) acc[q] = V::zerof();
+#pragma unroll 2
     for (int r = t; r < len; r += W) {
-        const F x = V::tof(xk[r], B);
+        const F x = V::tofp(xk + r, B);
 #pragma unroll
         for (int q = 0; q < NC; ++q)
             if (q < nvalid) {
                 const typename V::T *c = (q < KCHUNK ? c0 : c1) + (int64_t)(q % KCHUNK) * ld;
-                acc[q] = V::fdot(V::tof(c[r], B), x, acc[q]);
+                acc[q] = V::fdot(V::tofp(c + r, B), x, acc[q]);
             }
     }
 #pragma unroll
