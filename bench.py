@@ -62,7 +62,10 @@ AUTOTUNED_RHO_L6 = (4.0, 24.0)
 # round, three repetitions: 1321 ms against 1373 ms for the library default)
 AUTOTUNED_SHAPES_C3 = (160, 48)
 
-ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.708396288 + 1.940368640 + 10.743539200 + 2.975437056) * 1e9
+# DRAM bytes of the two k_aca launches of one level-6 step (SLP read, write;
+# DLP read, write), dram__bytes_read.sum + dram__bytes_write.sum from one ncu
+# capture of the current kernel
+ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.480550400 + 1.825745152 + 10.497422592 + 2.730348288) * 1e9
 
 
 def rank_jitter_seed(rank: int) -> int:
@@ -522,19 +525,39 @@ def run_gpu(args):
     fp64_peak = peaks["fp64_fma_per_s"] / 1e9
     mufu_peak = peaks["mufu_rsqrt_per_s"] / 1e9
     if dom == "aca":
-        # algorithmic FP64 work of the ACA: rank^2 (m+n) multiply-adds per block
-        # (residual updates + norm terms) plus one addition per widened entry
-        ops = (st_slp["aca_fp64_fma"] + st_dlp["aca_fp64_fma"]
-               + st_slp["far_entries"] + st_dlp["far_entries"])
-        achieved = ops / (per_step[dom] * 1e-3) / 1e9
+        # algorithmic work of the mixed ACA per step.  rank^2 (m+n) per block
+        # (aca_fp64_fma) counts the residual updates (about half) and the
+        # norm's dot products (the other half, FP32 on this path).  FP64: the
+        # residual updates, one addition per entry (widening the float-float
+        # quadrature sum) and one multiplication per column entry (1/pivot).
+        # FP32: 7 (SLP) / 9 (DLP) operations per point pair, 36 pairs per
+        # entry, plus the norm's multiply-adds.  MUFU: one rsqrt per pair.
+        k2 = st_slp["aca_fp64_fma"] + st_dlp["aca_fp64_fma"]
+        far = st_slp["far_entries"] + st_dlp["far_entries"]
+        t_s = per_step[dom] * 1e-3
+        ops = 0.5 * k2 + 1.5 * far
+        achieved = ops / t_s / 1e9
+        fp32_ops = 36.0 * (7 * st_slp["far_entries"] + 9 * st_dlp["far_entries"]) + 0.5 * k2
+        fp32_peak = peaks["fp32_fma_per_s"] / 1e9
         roof = {"kernel": "k_aca (persistent ACA + far-field quadrature)", "bound": "alu",
-                "pipe": "FP64 (DFMA/DADD/DMUL)", "achieved": achieved, "peak": fp64_peak,
+                "pipe": "FP64 (DFMA/DADD/DMUL): the largest single-pipe demand per step",
+                "achieved": achieved, "peak": fp64_peak,
                 "unit": "Gop/s", "frac": achieved / fp64_peak,
                 "traffic": ACA_TRAFFIC_BYTES_PER_STEP_L6 if args.level == 6 else None,
                 "traffic_unit": "DRAM bytes per step (both k_aca launches, ncu capture)",
-                "secondary": {"pipe": "MUFU (rsqrt per Green's function evaluation)",
-                              "achieved": evals_far / (per_step[dom] * 1e-3) / 1e9,
-                              "peak": mufu_peak}}
+                "algorithmic": {"fp64_ops": ops, "fp32_ops": fp32_ops, "mufu_ops": evals_far,
+                                "how": "FP64 = rank^2(m+n)/2 residual multiply-adds + 1.5 per entry; "
+                                       "FP32 = 36 x (7 SLP | 9 DLP) per entry + rank^2(m+n)/2 norm "
+                                       "multiply-adds; MUFU = 36 rsqrt per entry"},
+                "pipe_ms_at_peak": {"fp64": ops / (fp64_peak * 1e9) * 1e3,
+                                    "fp32": fp32_ops / (fp32_peak * 1e9) * 1e3,
+                                    "mufu": evals_far / (mufu_peak * 1e9) * 1e3},
+                "secondary": [{"pipe": "MUFU (rsqrt per Green's function evaluation)",
+                               "achieved": evals_far / t_s / 1e9, "peak": mufu_peak,
+                               "frac": evals_far / t_s / 1e9 / mufu_peak},
+                              {"pipe": "FP32 (quadrature + norm dot products)",
+                               "achieved": fp32_ops / t_s / 1e9, "peak": fp32_peak,
+                               "frac": fp32_ops / t_s / 1e9 / fp32_peak}]}
     elif dom == "near_regular":
         achieved = 36.0 * near_reg / (per_step[dom] * 1e-3) / 1e9
         roof = {"kernel": "k_near_regular", "bound": "alu", "pipe": "MUFU",

@@ -333,8 +333,10 @@ typedef struct {
     double time_far_ms;          /* last assembly: ACA (device) */
     double time_near_regular_ms; /* part of time_near_ms: regular pairs */
     double time_singular_ms;     /* part of time_near_ms: singular pairs */
-    int64_t aca_fp64_fma;        /* sum over admissible blocks of rank^2 (m + n): the FP64
-                                    multiply-adds of the ACA residual updates and norms */
+    int64_t aca_fp64_fma;        /* sum over admissible blocks of rank^2 (m + n): the
+                                    multiply-adds of the ACA residual updates (about half,
+                                    FP64) and of the norm's dot products (the other half:
+                                    FP64 in BEM_FP64, FP32 in BEM_MIXED) */
     int32_t assembled;
     int32_t op;
     double k;
