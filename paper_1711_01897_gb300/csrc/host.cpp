@@ -553,9 +553,9 @@ struct bem_mesh_s {
     DBuf dV, dT;
     GeomStore geom;
     // touching triangles (sharing >= 1 vertex, itself included): CSR
-    std::vector<int64_t> adj_ptr;
-    std::vector<int32_t> adj_tri;
-    std::vector<int8_t> adj_case;   // shared vertex count 1..3
+    std::vector<int64_t, NoInit<int64_t>> adj_ptr;
+    std::vector<int32_t, NoInit<int32_t>> adj_tri;
+    std::vector<int8_t, NoInit<int8_t>> adj_case;   // shared vertex count 1..3
     int64_t max_touch = 0;
     int hmat_refs = 0;
 };
@@ -680,21 +680,28 @@ void parallel_tasks(int64_t ntask, F &&f)
 
 // Touching triangles (sharing at least one vertex, itself included) of every
 // triangle, with the shared-vertex count, as CSR in increasing triangle order.
-// Triangles in chunks on the host threads; the chunks are concatenated in
-// order.
+// All phases on the host threads: the vertex -> triangle lists by atomic
+// counts and cursors (their order is not kept: each triangle's list is
+// sorted below), the triangles in chunks, and the chunks written into their
+// final slots after a prefix sum of their sizes.
 void build_adjacency(bem_mesh_s &M)
 {
     const int64_t nt = M.nt, nv = M.nv;
-    std::vector<int64_t> vptr(nv + 1, 0);
-    for (int64_t t = 0; t < nt; ++t)
-        for (int a = 0; a < 3; ++a) ++vptr[M.T[3 * t + a] + 1];
-    for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
-    std::vector<int32_t> vtri(vptr[nv]);
-    std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
-    for (int64_t t = 0; t < nt; ++t)
-        for (int a = 0; a < 3; ++a) vtri[fill[M.T[3 * t + a]]++] = (int32_t)t;
     constexpr int64_t kChunk = 8192;
     const int64_t nchunk = (nt + kChunk - 1) / kChunk;
+    std::vector<int64_t> vptr(nv + 1, 0);
+    parallel_tasks(nchunk, [&](int64_t ck) {
+        for (int64_t t = ck * kChunk, te = std::min(nt, t + kChunk); t < te; ++t)
+            for (int a = 0; a < 3; ++a) __atomic_fetch_add(&vptr[M.T[3 * t + a] + 1], 1, __ATOMIC_RELAXED);
+    });
+    for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
+    std::vector<int32_t, NoInit<int32_t>> vtri(vptr[nv]);
+    std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
+    parallel_tasks(nchunk, [&](int64_t ck) {
+        for (int64_t t = ck * kChunk, te = std::min(nt, t + kChunk); t < te; ++t)
+            for (int a = 0; a < 3; ++a)
+                vtri[__atomic_fetch_add(&fill[M.T[3 * t + a]], 1, __ATOMIC_RELAXED)] = (int32_t)t;
+    });
     struct Part {
         std::vector<int64_t> len;
         std::vector<int32_t> tri;
@@ -725,20 +732,26 @@ void build_adjacency(bem_mesh_s &M)
             P.max_touch = std::max(P.max_touch, cnt);
         }
     });
-    M.adj_ptr.assign(nt + 1, 0);
-    M.adj_tri.clear();
-    M.adj_case.clear();
+    std::vector<int64_t> off(nchunk + 1, 0);
     M.max_touch = 0;
-    int64_t t = 0;
-    for (const Part &P : parts) {
-        for (int64_t c : P.len) {
-            M.adj_ptr[t + 1] = M.adj_ptr[t] + c;
-            ++t;
-        }
-        M.adj_tri.insert(M.adj_tri.end(), P.tri.begin(), P.tri.end());
-        M.adj_case.insert(M.adj_case.end(), P.cs.begin(), P.cs.end());
-        M.max_touch = std::max(M.max_touch, P.max_touch);
+    for (int64_t ck = 0; ck < nchunk; ++ck) {
+        off[ck + 1] = off[ck] + (int64_t)parts[ck].tri.size();
+        M.max_touch = std::max(M.max_touch, parts[ck].max_touch);
     }
+    M.adj_ptr.resize(nt + 1);
+    M.adj_tri.resize(off[nchunk]);
+    M.adj_case.resize(off[nchunk]);
+    parallel_tasks(nchunk, [&](int64_t ck) {
+        const Part &P = parts[ck];
+        std::copy(P.tri.begin(), P.tri.end(), M.adj_tri.begin() + off[ck]);
+        std::copy(P.cs.begin(), P.cs.end(), M.adj_case.begin() + off[ck]);
+        int64_t o = off[ck];
+        for (size_t q = 0; q < P.len.size(); ++q) {
+            M.adj_ptr[ck * kChunk + (int64_t)q] = o;
+            o += P.len[q];
+        }
+    });
+    M.adj_ptr[nt] = off[nchunk];
 }
 
 }  // namespace
@@ -866,26 +879,56 @@ int mesh_create_impl(const double *vertices, int64_t n_vertices, const int32_t *
         M->nt = n_triangles;
         M->V.assign(vertices, vertices + 3 * n_vertices);
         M->T.assign(triangles, triangles + 3 * n_triangles);
-        for (int64_t i = 0; i < 3 * n_vertices; ++i)
-            if (!std::isfinite(M->V[i]))
+        // validation in chunks on the host threads; each chunk keeps its first
+        // failure, and the smallest index over the chunks is reported (the
+        // one a sequential scan finds first)
+        constexpr int64_t kVal = 65536;
+        const int64_t nvc = (3 * n_vertices + kVal - 1) / kVal;
+        std::vector<int64_t> bad_v(nvc, -1);
+        parallel_tasks(nvc, [&](int64_t ck) {
+            for (int64_t i = ck * kVal, ie = std::min(3 * n_vertices, i + kVal); i < ie; ++i)
+                if (!std::isfinite(M->V[i])) {
+                    bad_v[ck] = i;
+                    return;
+                }
+        });
+        for (int64_t i : bad_v)
+            if (i >= 0)
                 return fail(BEM_E_MESH, "non-finite coordinate at vertex " + std::to_string(i / 3));
-        for (int64_t t = 0; t < n_triangles; ++t) {
-            const int32_t *tr = &M->T[3 * t];
-            for (int a = 0; a < 3; ++a)
-                if (tr[a] < 0 || tr[a] >= n_vertices)
-                    return fail(BEM_E_MESH, "vertex index out of range in triangle " + std::to_string(t));
-            if (tr[0] == tr[1] || tr[1] == tr[2] || tr[0] == tr[2])
-                return fail(BEM_E_MESH, "repeated vertex in triangle " + std::to_string(t));
-            const double *a = &M->V[3 * tr[0]], *b = &M->V[3 * tr[1]], *c = &M->V[3 * tr[2]];
-            double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-            double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-            double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                           e1[0] * e2[1] - e1[1] * e2[0]};
-            double n2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
-            double s2 = (e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]) *
-                        (e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
-            if (!(n2 > 1e-24 * s2) || n2 == 0.0)
-                return fail(BEM_E_MESH, "zero-area triangle " + std::to_string(t));
+        const int64_t ntc = (n_triangles + kVal - 1) / kVal;
+        std::vector<int64_t> bad_t(ntc, -1);
+        std::vector<int> bad_kind(ntc, 0);
+        parallel_tasks(ntc, [&](int64_t ck) {
+            for (int64_t t = ck * kVal, te = std::min(n_triangles, t + kVal); t < te; ++t) {
+                const int32_t *tr = &M->T[3 * t];
+                int kind = 0;
+                for (int a = 0; a < 3; ++a)
+                    if (tr[a] < 0 || tr[a] >= n_vertices) kind = 1;
+                if (!kind && (tr[0] == tr[1] || tr[1] == tr[2] || tr[0] == tr[2])) kind = 2;
+                if (!kind) {
+                    const double *a = &M->V[3 * tr[0]], *b = &M->V[3 * tr[1]], *c = &M->V[3 * tr[2]];
+                    double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+                    double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+                    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                   e1[0] * e2[1] - e1[1] * e2[0]};
+                    double n2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+                    double s2 = (e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]) *
+                                (e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
+                    if (!(n2 > 1e-24 * s2) || n2 == 0.0) kind = 3;
+                }
+                if (kind) {
+                    bad_t[ck] = t;
+                    bad_kind[ck] = kind;
+                    return;
+                }
+            }
+        });
+        for (int64_t ck = 0; ck < ntc; ++ck) {
+            if (bad_t[ck] < 0) continue;
+            const std::string ts = std::to_string(bad_t[ck]);
+            if (bad_kind[ck] == 1) return fail(BEM_E_MESH, "vertex index out of range in triangle " + ts);
+            if (bad_kind[ck] == 2) return fail(BEM_E_MESH, "repeated vertex in triangle " + ts);
+            return fail(BEM_E_MESH, "zero-area triangle " + ts);
         }
         build_adjacency(*M);
         if (st != kHostOnly) {
