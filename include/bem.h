@@ -117,6 +117,16 @@ int bem_measure_peaks(bem_peaks *out, void *cuda_stream);
  * synchronised. */
 int bem_debug_recip(const double *x, double *y, int64_t n, void *cuda_stream);
 
+/* Diagnostic of the FP64 reciprocal square root of the FP64 quadratures
+ * (the singular pairs of Sec. 3.2.3 and the FP64 regular pairs, where the
+ * kernels of Eq. (5) take 1/|x - y|): y[i] = 1 / sqrt(x[i]) by the routine
+ * those kernels use (one Newton step in FP64 from a single-precision seed of
+ * the mantissa reduced to [1, 4); relative error below 7e-14).  x, y: device
+ * arrays of n doubles on the current device (y may alias x); x[i] positive
+ * and normal (other values give unspecified results).  Returns after the
+ * stream is synchronised. */
+int bem_debug_rsqrt(const double *x, double *y, int64_t n, void *cuda_stream);
+
 /* Process-wide tuning, read when a tree is built (row thresholds) and when
  * an H-matrix is assembled (graphs).  The numerical results do not depend on
  * it (up to ACA pivot near-ties, which rounding decides).

@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
             "bem_kernel_launches": ([], ctypes.c_int64),
             "bem_memory_usage": ([P, P], ctypes.c_int),
             "bem_debug_recip": ([P, P, i64, P], ctypes.c_int),
+            "bem_debug_rsqrt": ([P, P, i64, P], ctypes.c_int),
             "bem_measure_peaks": ([ctypes.POINTER(Peaks), P], ctypes.c_int),
             "bem_set_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
             "bem_get_tuning": ([ctypes.POINTER(Tuning)], ctypes.c_int),
@@ -236,6 +237,14 @@ def bem_debug_recip(x, y, stream=None):
     n = x.numel()
     assert y.numel() == n
     _check(load().bem_debug_recip(_ptr(x)[0], _ptr(y)[0], n, _stream(stream)))
+
+
+def bem_debug_rsqrt(x, y, stream=None):
+    """y = 1 / sqrt(x) on the device by the FP64 quadratures' reciprocal
+    square root; x, y device tensors of float64 (same length), x > 0."""
+    n = x.numel()
+    assert y.numel() == n
+    _check(load().bem_debug_rsqrt(_ptr(x)[0], _ptr(y)[0], n, _stream(stream)))
 
 
 def bem_set_tuning(warp_max_rows: int, lane_max_rows: int, use_graphs: int = 1):

@@ -90,6 +90,29 @@ __device__ __forceinline__ double f2d_exact(float f)
 
 __device__ __forceinline__ double ff_to_double(FF a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
 
+// 1/sqrt(q) in FP64 for a positive normal q (the FP64 quadratures: r^2 of a
+// regular pair or of a Sauter-Schwab node, never zero).  Newton's iteration
+// y <- y + y (1/2 - (q/2) y^2) from an FP32 seed: q is reduced exactly to
+// q' = q 2^-2k in [1, 4), the float of q' built from its fields (23 mantissa
+// bits, truncated) on the integer pipe, the seed taken by rsqrt.approx.f32
+// (relative error at most 2^-22.9, PTX ISA), so the seed's relative error is
+// below 2^-22.3, and one step in FP64 leaves 1.5 e^2 + rounding < 2^-43.7
+// (about 7e-14); the result is scaled back by 2^-k in its exponent.  Three
+// FP64 operations.
+__device__ __forceinline__ double rsqrt_fp64(double q)
+{
+    const long long b = __double_as_longlong(q);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const int k = e >> 1;  // floor(e / 2)
+    const long long bq = b - ((long long)(2 * k) << 52);
+    const unsigned hi = (unsigned)(bq >> 32), lo = (unsigned)bq;
+    const unsigned fb = ((unsigned)(127 + e - 2 * k) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    double y = f2d_exact(rsqrt_ftz(__uint_as_float(fb)));
+    const double h = __longlong_as_double(bq - (1ll << 52));  // q' / 2
+    y = fma(y, fma(-h, y * y, 0.5), y);
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));
+}
+
 // ---- triangle views -------------------------------------------------------
 struct TriF {           // mixed-precision view
     float ch[3], cl[3];
@@ -336,7 +359,7 @@ __device__ __forceinline__ C2 entry_fp64(const TriD &a, const TriD &b, const dou
             double d0 = a.q[p][0] - b.q[q][0], d1 = a.q[p][1] - b.q[q][1],
                    d2 = a.q[p][2] - b.q[q][2];
             double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
-            double ri = rsqrt(r2);
+            double ri = rsqrt_fp64(r2);
             double amp;  // real factor multiplying exp(ikr)
             if (OP == 0) amp = ri;
             else if (OP == 1) amp = (d0 * b.n[0] + d1 * b.n[1] + d2 * b.n[2]) * ri * ri * ri;

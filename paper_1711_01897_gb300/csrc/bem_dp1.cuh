@@ -47,7 +47,7 @@ __device__ __forceinline__ void dp1_fp64(const TriD &a, const TriD &b, const Qua
             const double d0 = a.q[p][0] - b.q[q][0], d1 = a.q[p][1] - b.q[q][1],
                          d2 = a.q[p][2] - b.q[q][2];
             const double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
-            const double ri = rsqrt(r2);
+            const double ri = rsqrt_fp64(r2);
             double amp;
             if (OP == 0) amp = ri;
             else if (OP == 1) amp = (d0 * b.n[0] + d1 * b.n[1] + d2 * b.n[2]) * ri * ri * ri;

@@ -270,6 +270,7 @@ cudaError_t launch_aca_dp1(const AcaWork &w, const QuadRule &rule, int op, bool 
 
 // y[i] = 1 / x[i] by the ACA's pivot reciprocal (diagnostic)
 cudaError_t launch_debug_recip(const double *x, double *y, int64_t n, cudaStream_t st);
+cudaError_t launch_debug_rsqrt(const double *x, double *y, int64_t n, cudaStream_t st);
 
 // After an ACA launch: toff[b] = sum of ranks of blocks < b (toff[n] = total)
 // and the totals in *st.  tile_sums needs aca_finish_tiles(n) entries.

@@ -815,6 +815,19 @@ int bem_debug_recip(const double *x, double *y, int64_t n, void *cuda_stream)
     });
 }
 
+int bem_debug_rsqrt(const double *x, double *y, int64_t n, void *cuda_stream)
+{
+    return guarded([&]() -> int {
+        if (n < 0) return fail(BEM_E_ARG, "negative size");
+        if (n == 0) return BEM_OK;
+        if (!x || !y) return fail(BEM_E_ARG, "null array");
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        CU(launch_debug_rsqrt(x, y, n, st));
+        CU(cudaStreamSynchronize(st));
+        return BEM_OK;
+    });
+}
+
 int bem_set_tuning(const bem_tuning *t)
 {
     if (!t || t->warp_max_rows < 1 || t->warp_max_rows > aca_small_cap() || t->lane_max_rows < 0 ||

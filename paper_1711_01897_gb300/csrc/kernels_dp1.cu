@@ -223,7 +223,7 @@ k_singular_dp1(DevGeom g, SingTable tab, double k, const SingPairL *__restrict__
                     d[c] = x;
                 }
                 const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
-                const double ri = rsqrt(r2);
+                const double ri = rsqrt_fp64(r2);
                 double W;
                 if (OP == 0) {
                     W = weta * ri;
@@ -282,7 +282,7 @@ k_singular_dp1(DevGeom g, SingTable tab, double k, const SingPairL *__restrict__
                     d[c] = x;
                 }
                 const double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
-                const double ri = rsqrt(r2), rt = r2 * ri;
+                const double ri = rsqrt_fp64(r2), rt = r2 * ri;
                 double dn = 0.0;
                 if (OP != 0) {
 #pragma unroll

@@ -472,7 +472,7 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
                         const double w = tab.wxi[a] * tab.wxi[b] * tab.wxi[c] * e2;
                         const double q0 = fma(q2, Cc[b], fma(m2, B[a][b], A[a]));
                         const double q1 = fma(q2, A[b], fma(m2, B[b][a], Cc[a]));
-                        const double r0 = rsqrt(q0), r1 = rsqrt(q1);
+                        const double r0 = rsqrt_fp64(q0), r1 = rsqrt_fp64(q1);
                         if (OP == 0) {
                             s = fma(w, r0 + r1, s);
                         } else if (OP == 1) {
@@ -499,7 +499,7 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
                     d[c] = x;
                 }
                 double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
-                double ri = rsqrt(r2);
+                double ri = rsqrt_fp64(r2);
                 double dn = 0.0;
                 if (OP != 0) {
 #pragma unroll
@@ -726,4 +726,23 @@ cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, 
     return cudaGetLastError();
 }
 
+}  // namespace bem
+
+namespace bem {
+namespace {
+__global__ void k_debug_rsqrt(const double *__restrict__ x, double *__restrict__ y, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = rsqrt_fp64(x[i]);
+}
+}  // namespace
+
+cudaError_t launch_debug_rsqrt(const double *x, double *y, int64_t n, cudaStream_t st)
+{
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    k_debug_rsqrt<<<(unsigned)blocks, 256, 0, st>>>(x, y, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
 }  // namespace bem
