@@ -464,25 +464,43 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
             for (int a = 0; a < NGL; ++a)
                 for (int b = 0; b < NGL; ++b)
                     B[a][b] = u[a][0] * up[b][0] + u[a][1] * up[b][1] + u[a][2] * up[b][2];
+            // nested sums: s = sum_c w_c e2_c sum_a w_a sum_b w_b (...); the
+            // double layers' per-node factors (w_b u_b.n_y, w_b u'_b.n_x) are
+            // formed once
+            double wny[NGL], wnx[NGL];
+            for (int b = 0; b < NGL; ++b) {
+                wny[b] = tab.wxi[b] * uny[b];
+                wnx[b] = tab.wxi[b] * upnx[b];
+            }
             double s = 0.0;
             for (int c = 0; c < NGL; ++c) {
                 const double e2 = tab.xi[c], m2 = -2.0 * e2, q2 = e2 * e2;
-                for (int a = 0; a < NGL; ++a)      // eta1 node
+                double sc = 0.0;
+                for (int a = 0; a < NGL; ++a) {      // eta1 node
+                    double s0 = 0.0, s1 = 0.0;
                     for (int b = 0; b < NGL; ++b) {  // eta3 node
-                        const double w = tab.wxi[a] * tab.wxi[b] * tab.wxi[c] * e2;
                         const double q0 = fma(q2, Cc[b], fma(m2, B[a][b], A[a]));
                         const double q1 = fma(q2, A[b], fma(m2, B[b][a], Cc[a]));
                         const double r0 = rsqrt_fp64(q0), r1 = rsqrt_fp64(q1);
                         if (OP == 0) {
-                            s = fma(w, r0 + r1, s);
+                            s0 = fma(tab.wxi[b], r0 + r1, s0);
                         } else if (OP == 1) {
                             // d.n_y / r^3: region 0 xi u_a.n_y, region 1 xi eta2 u_b.n_y
-                            s = fma(w, uny[a] * r0 * r0 * r0 + e2 * uny[b] * r1 * r1 * r1, s);
+                            s0 = fma(tab.wxi[b], r0 * r0 * r0, s0);
+                            s1 = fma(wny[b], r1 * r1 * r1, s1);
                         } else {
                             // -d.n_x / r^3: region 0 xi eta2 u'_b.n_x, region 1 xi u'_a.n_x
-                            s = fma(w, e2 * upnx[b] * r0 * r0 * r0 + upnx[a] * r1 * r1 * r1, s);
+                            s0 = fma(wnx[b], r0 * r0 * r0, s0);
+                            s1 = fma(tab.wxi[b], r1 * r1 * r1, s1);
                         }
                     }
+                    double sa;
+                    if (OP == 0) sa = s0;
+                    else if (OP == 1) sa = fma(uny[a], s0, e2 * s1);
+                    else sa = fma(e2, s0, upnx[a] * s1);
+                    sc = fma(tab.wxi[a], sa, sc);
+                }
+                s = fma(tab.wxi[c] * e2, sc, s);
             }
             acc.re = s * (OP == 0 ? sx2 : sx1);
         } else if (!flat_zero) {
