@@ -90,6 +90,46 @@ __device__ __forceinline__ double f2d_exact(float f)
 
 __device__ __forceinline__ double ff_to_double(FF a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
 
+// ---- packed pairs of FP32 values ---------------------------------------
+// PTX .f32x2 arithmetic (sm_100-family parts): one instruction applies the
+// operation to both 32-bit halves, each rounded as the scalar form (.rn), so
+// two quadrature terms take the issue slot of one.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 x2_pack(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void x2_unpack(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float x2_sum(f32x2 v)
+{
+    float lo, hi;
+    x2_unpack(v, lo, hi);
+    return lo + hi;
+}
+
 // 1/sqrt(q) in FP64 for a positive normal q (the FP64 quadratures: r^2 of a
 // regular pair or of a Sauter-Schwab node, never zero).  Newton's iteration
 // y <- y + y (1/2 - (q/2) y^2) from an FP32 seed: q is reduced exactly to
@@ -233,38 +273,54 @@ __device__ __forceinline__ FF entry_mixed_laplace_ff(const TriF &a, const TriF &
                              (D[2] - b.q[q][2]) * a.n[2]);
     }
     FF acc = {0.f, 0.f};
+    // the trial points (and their weights) as packed pairs (q, q + 1): two
+    // Green's-function evaluations per packed instruction, one rsqrt each;
+    // each sum is kept in two lanes (even and odd q) and joined at its end
+    f32x2 bq[NQ / 2][3], wq[NQ / 2];
+#pragma unroll
+    for (int h = 0; h < NQ / 2; ++h) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bq[h][c] = x2_pack(b.q[2 * h][c], b.q[2 * h + 1][c]);
+        wq[h] = OP == 2 ? x2_pack(cq[2 * h], cq[2 * h + 1]) : x2_pack(w[2 * h], w[2 * h + 1]);
+    }
     if constexpr (OP == 0) {
         // Single layer: every term is positive, and the three test points of
         // an orbit of the rule share one weight, so each orbit's 18 terms are
         // summed in FP32 (relative error at most 17 u, u = 2^-24), scaled
         // once, and the two orbit sums joined in float-float
-        float so[2] = {0.f, 0.f};
+        f32x2 so[2] = {0ull, 0ull};
 #pragma unroll
         for (int p = 0; p < NQ; ++p) {
-            float Dp0 = D[0] + a.q[p][0], Dp1 = D[1] + a.q[p][1], Dp2 = D[2] + a.q[p][2];
-            float s = so[p / 3];
+            const f32x2 P0 = x2_pack(D[0] + a.q[p][0], D[0] + a.q[p][0]);
+            const f32x2 P1 = x2_pack(D[1] + a.q[p][1], D[1] + a.q[p][1]);
+            const f32x2 P2 = x2_pack(D[2] + a.q[p][2], D[2] + a.q[p][2]);
+            f32x2 s = so[p / 3];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                float d0 = Dp0 - b.q[q][0], d1 = Dp1 - b.q[q][1], d2 = Dp2 - b.q[q][2];
-                s = fmaf(w[q], rsqrt_ftz(fmaf(d0, d0, fmaf(d1, d1, d2 * d2))), s);
+            for (int h = 0; h < NQ / 2; ++h) {
+                const f32x2 d0 = x2_sub(P0, bq[h][0]), d1 = x2_sub(P1, bq[h][1]), d2 = x2_sub(P2, bq[h][2]);
+                float r0, r1;
+                x2_unpack(x2_fma(d0, d0, x2_fma(d1, d1, x2_mul(d2, d2))), r0, r1);
+                s = x2_fma(wq[h], x2_pack(rsqrt_ftz(r0), rsqrt_ftz(r1)), s);
             }
             so[p / 3] = s;
         }
-        acc.hi = w[0] * so[0];
-        ff_add(acc, w[3] * so[1]);
+        acc.hi = w[0] * x2_sum(so[0]);
+        ff_add(acc, w[3] * x2_sum(so[1]));
     } else {
 #pragma unroll
         for (int p = 0; p < NQ; ++p) {
             float Dp0 = D[0] + a.q[p][0], Dp1 = D[1] + a.q[p][1], Dp2 = D[2] + a.q[p][2];
-            float s = 0.f;
+            const f32x2 P0 = x2_pack(Dp0, Dp0), P1 = x2_pack(Dp1, Dp1), P2 = x2_pack(Dp2, Dp2);
+            f32x2 s2 = 0ull;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                float d0 = Dp0 - b.q[q][0], d1 = Dp1 - b.q[q][1], d2 = Dp2 - b.q[q][2];
-                float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-                float ri = rsqrt_ftz(r2);
-                if (OP == 1) s = fmaf(w[q], ri * ri * ri, s);
-                else s = fmaf(cq[q], ri * ri * ri, s);
+            for (int h = 0; h < NQ / 2; ++h) {
+                const f32x2 d0 = x2_sub(P0, bq[h][0]), d1 = x2_sub(P1, bq[h][1]), d2 = x2_sub(P2, bq[h][2]);
+                float r0, r1;
+                x2_unpack(x2_fma(d0, d0, x2_fma(d1, d1, x2_mul(d2, d2))), r0, r1);
+                const f32x2 ri = x2_pack(rsqrt_ftz(r0), rsqrt_ftz(r1));
+                s2 = x2_fma(wq[h], x2_mul(x2_mul(ri, ri), ri), s2);
             }
+            float s = x2_sum(s2);
             if (OP == 1) s *= Dp0 * b.n[0] + Dp1 * b.n[1] + Dp2 * b.n[2];
             ff_add(acc, w[p] * s);
         }
