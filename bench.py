@@ -530,14 +530,16 @@ def run_gpu(args):
         # norm's dot products (the other half, FP32 on this path).  FP64: the
         # residual updates, one addition per entry (widening the float-float
         # quadrature sum) and one multiplication per column entry (1/pivot).
-        # FP32: 7 (SLP) / 9 (DLP) operations per point pair, 36 pairs per
-        # entry, plus the norm's multiply-adds.  MUFU: one rsqrt per pair.
+        # FP32: 7 (SLP) / 12 (DLP) operations per point pair (the per-unit
+        # figures of the quadrature roofline), 36 pairs per entry, plus the
+        # norm's multiply-adds.  MUFU: one rsqrt per pair.
         k2 = st_slp["aca_fp64_fma"] + st_dlp["aca_fp64_fma"]
         far = st_slp["far_entries"] + st_dlp["far_entries"]
         t_s = per_step[dom] * 1e-3
         ops = 0.5 * k2 + 1.5 * far
         achieved = ops / t_s / 1e9
-        fp32_ops = 36.0 * (7 * st_slp["far_entries"] + 9 * st_dlp["far_entries"]) + 0.5 * k2
+        fp32_ops = (36.0 * (QUAD_FP32_PER_EVAL[0] * st_slp["far_entries"]
+                            + QUAD_FP32_PER_EVAL[1] * st_dlp["far_entries"]) + 0.5 * k2)
         fp32_peak = peaks["fp32_fma_per_s"] / 1e9
         roof = {"kernel": "k_aca (persistent ACA + far-field quadrature)", "bound": "alu",
                 "pipe": "FP64 (DFMA/DADD/DMUL): the largest single-pipe demand per step",
@@ -547,7 +549,7 @@ def run_gpu(args):
                 "traffic_unit": "DRAM bytes per step (both k_aca launches, ncu capture)",
                 "algorithmic": {"fp64_ops": ops, "fp32_ops": fp32_ops, "mufu_ops": evals_far,
                                 "how": "FP64 = rank^2(m+n)/2 residual multiply-adds + 1.5 per entry; "
-                                       "FP32 = 36 x (7 SLP | 9 DLP) per entry + rank^2(m+n)/2 norm "
+                                       "FP32 = 36 x (7 SLP | 12 DLP) per entry + rank^2(m+n)/2 norm "
                                        "multiply-adds; MUFU = 36 rsqrt per entry"},
                 "pipe_ms_at_peak": {"fp64": ops / (fp64_peak * 1e9) * 1e3,
                                     "fp32": fp32_ops / (fp32_peak * 1e9) * 1e3,
