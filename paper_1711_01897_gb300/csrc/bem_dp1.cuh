@@ -125,26 +125,44 @@ __device__ __forceinline__ void dp1_mixed_laplace(const TriF &a, const TriF &b, 
     FF acc[NO];
 #pragma unroll
     for (int o = 0; o < NO; ++o) acc[o] = {0.f, 0.f};
+    // trial points and their basis weights as packed pairs (q, q + 1): two
+    // evaluations per packed instruction (as entry_mixed_laplace_ff); each
+    // partial sum in two lanes, joined after the trial points
+    constexpr int NS = MODE == 1 ? 1 : 3;
+    f32x2 bq[NQ / 2][3], wq[NQ / 2][NS], cq2[NQ / 2];
+#pragma unroll
+    for (int h = 0; h < NQ / 2; ++h) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bq[h][c] = x2_pack(b.q[2 * h][c], b.q[2 * h + 1][c]);
+        if (MODE == 1) {
+            wq[h][0] = x2_pack(wlf_at(R, 2 * h, fix), wlf_at(R, 2 * h + 1, fix));
+        } else {
+#pragma unroll
+            for (int be = 0; be < NS; ++be) wq[h][be] = x2_pack(R.wlf[2 * h][be], R.wlf[2 * h + 1][be]);
+        }
+        cq2[h] = OP == 2 ? x2_pack(cq[2 * h], cq[2 * h + 1]) : 0ull;
+    }
 #pragma unroll
     for (int p = 0; p < NQ; ++p) {
         const float Dp0 = D[0] + a.q[p][0], Dp1 = D[1] + a.q[p][1], Dp2 = D[2] + a.q[p][2];
+        const f32x2 P0 = x2_pack(Dp0, Dp0), P1 = x2_pack(Dp1, Dp1), P2 = x2_pack(Dp2, Dp2);
+        f32x2 s2[NS];
+#pragma unroll
+        for (int be = 0; be < NS; ++be) s2[be] = 0ull;
+#pragma unroll
+        for (int h = 0; h < NQ / 2; ++h) {
+            const f32x2 d0 = x2_sub(P0, bq[h][0]), d1 = x2_sub(P1, bq[h][1]), d2 = x2_sub(P2, bq[h][2]);
+            float r0, r1;
+            x2_unpack(x2_fma(d0, d0, x2_fma(d1, d1, x2_mul(d2, d2))), r0, r1);
+            f32x2 G = x2_pack(rsqrt_ftz(r0), rsqrt_ftz(r1));
+            if (OP != 0) G = x2_mul(x2_mul(G, G), G);
+            if (OP == 2) G = x2_mul(cq2[h], G);
+#pragma unroll
+            for (int be = 0; be < NS; ++be) s2[be] = x2_fma(wq[h][be], G, s2[be]);
+        }
         float s[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const float d0 = Dp0 - b.q[q][0], d1 = Dp1 - b.q[q][1], d2 = Dp2 - b.q[q][2];
-            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            const float ri = rsqrt_ftz(r2);
-            float G;
-            if (OP == 0) G = ri;
-            else if (OP == 1) G = ri * ri * ri;
-            else G = cq[q] * (ri * ri * ri);
-            if (MODE == 1) {
-                s[0] = fmaf(wlf_at(R, q, fix), G, s[0]);
-            } else {
-#pragma unroll
-                for (int be = 0; be < 3; ++be) s[be] = fmaf(R.wlf[q][be], G, s[be]);
-            }
-        }
+        for (int be = 0; be < NS; ++be) s[be] = x2_sum(s2[be]);
         if (OP == 1) {
             const float dn = Dp0 * b.n[0] + Dp1 * b.n[1] + Dp2 * b.n[2];
 #pragma unroll
