@@ -43,7 +43,7 @@ int aca_tiny_max() { return kTinyMax; }
 
 // ---- after the launch: prefix sums of the ranks and device-side totals ----
 namespace {
-constexpr int kScanThreads = 1024, kScanPer = 4, kScanTile = kScanThreads * kScanPer;
+constexpr int kScanThreads = 1024, kScanPer = 1, kScanTile = kScanThreads * kScanPer;
 
 __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *warp_tot, int64_t &total)
 {
@@ -92,22 +92,76 @@ k_rank_tiles(const FarBlock *__restrict__ far, const FarChunks *__restrict__ chu
             rmax = max(rmax, F.rank);
             capped += F.status == 1;
             failed += F.status == 2;
-            for (int c = 0; c < NCHUNK; ++c)
-                if (chunks[b].c[c] >= 0) fe += ((F.te - F.tb) + (F.se - F.sb)) * KCHUNK;
+            // a block's chunks are allocated in order: the allocated ones
+            // are a prefix of its list, the rest -1
+            for (int c = 0; c < NCHUNK && chunks[b].c[c] >= 0; ++c)
+                fe += ((F.te - F.tb) + (F.se - F.sb)) * KCHUNK;
         }
     }
     int64_t tot = 0;
     block_exclusive_scan(sum, wt, tot);
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
-    atomicAdd(&st->entries, (unsigned long long)ent);
-    atomicAdd(&st->rank_sum, (unsigned long long)sum);
-    atomicAdd(&st->factor_elems, (unsigned long long)fe);
-    atomicAdd(&st->k2mn, (unsigned long long)k2);
-    atomicAdd(&st->rank_mn, (unsigned long long)kmn);
-    atomicMin(&st->rank_min, rmin);
-    atomicMax(&st->rank_max, rmax);
-    if (capped) atomicAdd(&st->capped, capped);
-    if (failed) atomicAdd(&st->failed, failed);
+    // the CTA's totals (warp shuffles, then one warp over the warps' sums),
+    // so that each CTA adds to the device totals once
+    __shared__ int64_t red64[4][32];
+    __shared__ int red32[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int nw = kScanThreads / 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ent += __shfl_xor_sync(0xffffffffu, ent, o);
+        fe += __shfl_xor_sync(0xffffffffu, fe, o);
+        k2 += __shfl_xor_sync(0xffffffffu, k2, o);
+        kmn += __shfl_xor_sync(0xffffffffu, kmn, o);
+        rmin = min(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+        rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        capped += __shfl_xor_sync(0xffffffffu, capped, o);
+        failed += __shfl_xor_sync(0xffffffffu, failed, o);
+    }
+    if (lane == 0) {
+        red64[0][w] = ent;
+        red64[1][w] = fe;
+        red64[2][w] = k2;
+        red64[3][w] = kmn;
+        red32[0][w] = rmin;
+        red32[1][w] = rmax;
+        red32[2][w] = capped;
+        red32[3][w] = failed;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const bool on = lane < nw;
+        ent = on ? red64[0][lane] : 0;
+        fe = on ? red64[1][lane] : 0;
+        k2 = on ? red64[2][lane] : 0;
+        kmn = on ? red64[3][lane] : 0;
+        rmin = on ? red32[0][lane] : 0x7fffffff;
+        rmax = on ? red32[1][lane] : 0;
+        capped = on ? red32[2][lane] : 0;
+        failed = on ? red32[3][lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ent += __shfl_xor_sync(0xffffffffu, ent, o);
+            fe += __shfl_xor_sync(0xffffffffu, fe, o);
+            k2 += __shfl_xor_sync(0xffffffffu, k2, o);
+            kmn += __shfl_xor_sync(0xffffffffu, kmn, o);
+            rmin = min(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+            rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+            capped += __shfl_xor_sync(0xffffffffu, capped, o);
+            failed += __shfl_xor_sync(0xffffffffu, failed, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&st->entries, (unsigned long long)ent);
+            atomicAdd(&st->rank_sum, (unsigned long long)tot);
+            atomicAdd(&st->factor_elems, (unsigned long long)fe);
+            atomicAdd(&st->k2mn, (unsigned long long)k2);
+            atomicAdd(&st->rank_mn, (unsigned long long)kmn);
+            atomicMin(&st->rank_min, rmin);
+            atomicMax(&st->rank_max, rmax);
+            if (capped) atomicAdd(&st->capped, capped);
+            if (failed) atomicAdd(&st->failed, failed);
+        }
+    }
 }
 
 // exclusive scan of the tile sums in place, one CTA
