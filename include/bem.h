@@ -40,13 +40,16 @@
  *    degree-4 triangle rule in both triangles (Sec. 3.2.1, Sec. 3.2.3);
  *    pairs that share a vertex, an edge or the whole triangle use the
  *    Sauter-Schwab transformations of [0,1]^4 with 4 Gauss-Legendre points
- *    per axis (the Erichsen-Sauter scheme cited in Sec. 3.2.3), always in
- *    FP64.
+ *    per axis (the Erichsen-Sauter scheme cited in Sec. 3.2.3): in FP64 for
+ *    BEM_FP64 and for Helmholtz; for Laplace in BEM_MIXED the transformed
+ *    (smooth) integrands are evaluated in FP32 and summed in float-float.
  *  - Precision (Sec. 3.2.4): BEM_FP64 evaluates every regular pair in FP64;
  *    BEM_MIXED evaluates regular pairs in FP32 (centroid-relative geometry)
  *    and accumulates each entry's quadrature sum in float-float (about 48
  *    significant bits) before it is stored in FP64.  ACA pivoting, residual
- *    updates and norms are FP64 in both modes.
+ *    updates and the norm's accumulation are FP64 in both modes; in
+ *    BEM_MIXED the norm's dot products, which feed only the stopping test,
+ *    are FP32.
  */
 #ifndef BEM_H
 #define BEM_H

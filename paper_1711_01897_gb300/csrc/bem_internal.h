@@ -220,7 +220,7 @@ cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int o
 // Touching pairs of each case: min(dev_counts[c], host_counts[c]) pairs
 // (dev_counts may be null); grid_counts[c], if given, sizes the grid instead
 // of host_counts[c] (the threads stride over every pair either way).
-cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k,
+cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k, int prec,
                             const SingPair *pairs[3], const unsigned long long *dev_counts,
                             const int64_t host_counts[3], void *out, cudaStream_t st,
                             const int64_t *grid_counts = nullptr);

@@ -118,7 +118,7 @@ int entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec, const int
     // there are; the host bound `need` only sizes the grids
     int64_t hc[3] = {kNoAllocPairs, kNoAllocPairs, kNoAllocPairs};
     int64_t gc[3] = {need, need, need};
-    if (e == cudaSuccess) e = launch_singular(M.g, sing, op, k, cl, counts, hc, out, st, gc);
+    if (e == cudaSuccess) e = launch_singular(M.g, sing, op, k, prec, cl, counts, hc, out, st, gc);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, eflag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return err(BEM_E_CUDA, std::string("bem_entries_noalloc: ") + cudaGetErrorString(e));

@@ -1059,7 +1059,7 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
                                            n_trial, dout, lists, counts, cap, err, st);
             const SingPair *cl[3] = {lists[0], lists[1], lists[2]};
             int64_t hc[3] = {(int64_t)cap, (int64_t)cap, (int64_t)cap};
-            if (e == cudaSuccess) e = launch_singular(mesh->geom.g, D.sing, op, k, cl, counts, hc, dout, st);
+            if (e == cudaSuccess) e = launch_singular(mesh->geom.g, D.sing, op, k, prec, cl, counts, hc, dout, st);
             herr = 0;
             if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess)
@@ -2236,7 +2236,7 @@ static void enqueue_near_field(bem_hmat H, cudaStream_t st, bool capturing)
                                  H->d_sing[2].as<SingPair>()};
         int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
                          (int64_t)H->sing[2].size()};
-        CU(launch_singular(H->mesh->geom.g, D.sing, aop, k, sp, nullptr, hc, H->d_near_data.p, st));
+        CU(launch_singular(H->mesh->geom.g, D.sing, aop, k, prec, sp, nullptr, hc, H->d_near_data.p, st));
     } else {
         CU(launch_near_dp1(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
                            (int64_t)H->near.size(), H->d_near_data.p, st));

@@ -378,18 +378,40 @@ k_entries_tiled_slp(DevGeom g, QuadRule R, const int32_t *__restrict__ test, int
 constexpr int kSingThreads = 128;
 constexpr int kSingMaxPts = 6 * NGL * NGL * NGL;  // largest table (identical, helm)
 
-template <int CASE, int OP, bool CPLX>
+// PREC 1 with real k (mixed Laplace): the evaluations after the Sauter-Schwab
+// transformation in FP32 (smooth integrands, the reduced distance bounded
+// away from zero), summed in FP32 within a node row and in float-float
+// outside it; the pair's geometry, its edge basis and the final scaling in
+// FP64.  Otherwise every step in FP64.
+template <int CASE, int OP, bool CPLX, int PREC = 0>
 __global__ void __launch_bounds__(kSingThreads)
 k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pairs,
            const unsigned long long *__restrict__ dev_count, int64_t max_count, void *out)
 {
     constexpr int NC = CASE == 3 ? 2 : (CASE == 2 ? 3 : 4);
     constexpr int ROWS = CPLX ? 5 : 6;
+    constexpr bool kMix = PREC == 1 && !CPLX;
     __shared__ double s_tab[6 * kSingMaxPts];
+    __shared__ float s_tabf[kMix ? 6 * kSingMaxPts : 1];
     const int npts = CPLX ? tab.n_helm : tab.n_lap;
     const double *src = CPLX ? tab.helm : tab.lap;
-    for (int e = threadIdx.x; e < ROWS * npts; e += blockDim.x) s_tab[e] = src[e];
+    for (int e = threadIdx.x; e < ROWS * npts; e += blockDim.x) {
+        s_tab[e] = src[e];
+        if constexpr (kMix) s_tabf[e] = (float)src[e];
+    }
     __syncthreads();
+    // the xi rule in FP32 and its moments (vertex case of the mixed path)
+    float xf[NGL], wf[NGL];
+    double sx1m = 0.0, sx2m = 0.0;
+    if constexpr (kMix && CASE == 1) {
+#pragma unroll
+        for (int a = 0; a < NGL; ++a) {
+            xf[a] = (float)tab.xi[a];
+            wf[a] = (float)tab.wxi[a];
+            sx1m = fma(tab.wxi[a], tab.xi[a], sx1m);
+            sx2m = fma(tab.wxi[a] * tab.xi[a], tab.xi[a], sx2m);
+        }
+    }
     int64_t count = max_count;
     if (dev_count) {
         unsigned long long c = *dev_count;
@@ -438,7 +460,67 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
         }
         C2 acc = {0.0, 0.0};
         const bool flat_zero = (CASE == 3 && OP != 0);  // d.n = 0 on one flat panel
-        if (CASE == 1 && !CPLX) {
+        if constexpr (kMix && CASE == 1) {
+            // the factorised vertex-adjacent rule below in FP32, with x - y
+            // formed per node pair (d0 = u_a - eta2 u'_b, d1 = eta2 u_b - u'_a)
+            // instead of through the expanded quadratic
+            float Ef[4][3], nxf[3], nyf[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) Ef[i][c] = (float)E[i][c];
+                nxf[c] = (float)nx[c];
+                nyf[c] = (float)ny[c];
+            }
+            float u[NGL][3], up[NGL][3], uny[NGL], upnx[NGL], wny[NGL], wnx[NGL];
+#pragma unroll
+            for (int a = 0; a < NGL; ++a) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    u[a][c] = fmaf(xf[a], Ef[1][c], Ef[0][c]);
+                    up[a][c] = fmaf(xf[a], Ef[3][c], Ef[2][c]);
+                }
+                uny[a] = u[a][0] * nyf[0] + u[a][1] * nyf[1] + u[a][2] * nyf[2];
+                upnx[a] = up[a][0] * nxf[0] + up[a][1] * nxf[1] + up[a][2] * nxf[2];
+                wny[a] = wf[a] * uny[a];
+                wnx[a] = wf[a] * upnx[a];
+            }
+            FF s = {0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < NGL; ++c) {
+                const float e2 = xf[c];
+#pragma unroll
+                for (int a = 0; a < NGL; ++a) {
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NGL; ++b) {
+                        float d0[3], d1[3];
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            d0[m] = fmaf(-e2, up[b][m], u[a][m]);
+                            d1[m] = fmaf(e2, u[b][m], -up[a][m]);
+                        }
+                        const float r0 = rsqrt_ftz(fmaf(d0[0], d0[0], fmaf(d0[1], d0[1], d0[2] * d0[2])));
+                        const float r1 = rsqrt_ftz(fmaf(d1[0], d1[0], fmaf(d1[1], d1[1], d1[2] * d1[2])));
+                        if (OP == 0) {
+                            s0 = fmaf(wf[b], r0 + r1, s0);
+                        } else if (OP == 1) {
+                            s0 = fmaf(wf[b], r0 * r0 * r0, s0);
+                            s1 = fmaf(wny[b], r1 * r1 * r1, s1);
+                        } else {
+                            s0 = fmaf(wnx[b], r0 * r0 * r0, s0);
+                            s1 = fmaf(wf[b], r1 * r1 * r1, s1);
+                        }
+                    }
+                    float sa;
+                    if (OP == 0) sa = s0;
+                    else if (OP == 1) sa = fmaf(uny[a], s0, e2 * s1);
+                    else sa = fmaf(e2, s0, upnx[a] * s1);
+                    ff_add(s, (wf[c] * e2) * (wf[a] * sa));
+                }
+            }
+            acc.re = ff_to_double(s) * (OP == 0 ? sx2m : sx1m);
+        } else if (CASE == 1 && !CPLX) {
             // Vertex-adjacent Laplace pair, factorised.  Region 0 maps to
             // x - y = xi (u(eta1) - eta2 u'(eta3)), region 1 to
             // x - y = xi (eta2 u(eta3) - u'(eta1)), with u(t) = E0 + t E1 and
@@ -503,6 +585,42 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
                 s = fma(tab.wxi[c] * e2, sc, s);
             }
             acc.re = s * (OP == 0 ? sx2 : sx1);
+        } else if (!flat_zero && kMix) {
+            // the merged directions in FP32, summed in float-float
+            float Ef[NC][3], enf[NC];
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Ef[i][c] = (float)E[i][c];
+                enf[i] = OP == 0 ? 0.f : (float)(OP == 1 ? eny[i] : enx[i]);
+            }
+            FF s = {0.f, 0.f};
+            for (int q = 0; q < npts; ++q) {
+                float cf[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) cf[i] = s_tabf[i * npts + q];
+                float d[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float x = cf[0] * Ef[0][c];
+#pragma unroll
+                    for (int i = 1; i < NC; ++i) x = fmaf(cf[i], Ef[i][c], x);
+                    d[c] = x;
+                }
+                const float ri = rsqrt_ftz(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+                float term;
+                if (OP == 0) {
+                    term = s_tabf[4 * npts + q] * ri;
+                } else {
+                    float dn = 0.f;
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) dn = fmaf(cf[i], enf[i], dn);
+                    if (OP == 2) dn = -dn;  // ADLP kernel has -(x - y).n_x
+                    term = s_tabf[5 * npts + q] * dn * (ri * ri * ri);
+                }
+                ff_add(s, term);
+            }
+            acc.re = ff_to_double(s);
         } else if (!flat_zero) {
             for (int q = 0; q < npts; ++q) {
                 double cf[NC];
@@ -691,7 +809,7 @@ cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int o
     return cudaGetLastError();
 }
 
-template <int CASE, int OP, bool CPLX>
+template <int CASE, int OP, bool CPLX, int PREC>
 static void singular_launch(const DevGeom &g, const SingTable &tab, double k, const SingPair *p,
                             const unsigned long long *dc, int64_t hc, int64_t gc, void *out,
                             cudaStream_t st)
@@ -701,11 +819,11 @@ static void singular_launch(const DevGeom &g, const SingTable &tab, double k, co
     int64_t want = (gc + kSingThreads - 1) / kSingThreads;
     int64_t cap = (int64_t)num_sms_cached() * 16;
     unsigned grid = (unsigned)(want < cap ? want : cap);
-    k_singular<CASE, OP, CPLX><<<grid, kSingThreads, 0, st>>>(g, tab, k, p, dc, hc, out);
+    k_singular<CASE, OP, CPLX, PREC><<<grid, kSingThreads, 0, st>>>(g, tab, k, p, dc, hc, out);
     count_launches(1);
 }
 
-cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k,
+cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k, int prec,
                             const SingPair *pairs[3], const unsigned long long *dev_counts,
                             const int64_t host_counts[3], void *out, cudaStream_t st,
                             const int64_t *grid_counts)
@@ -717,11 +835,11 @@ cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, dou
         int64_t hc = host_counts[c - 1];
         int64_t gc = grid_counts ? grid_counts[c - 1] : hc;
         const SingPair *P = pairs[c - 1];
-        BEM_DISPATCH(op, cplx, 0, ({
-                         (void)PREC;
-                         if (c == 1) singular_launch<1, OP, CPLX>(g, T, k, P, dc, hc, gc, out, st);
-                         else if (c == 2) singular_launch<2, OP, CPLX>(g, T, k, P, dc, hc, gc, out, st);
-                         else singular_launch<3, OP, CPLX>(g, T, k, P, dc, hc, gc, out, st);
+        // mixed precision applies to the Laplace kernels (Helmholtz pairs stay FP64)
+        BEM_DISPATCH(op, cplx, (cplx ? 0 : prec), ({
+                         if (c == 1) singular_launch<1, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
+                         else if (c == 2) singular_launch<2, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
+                         else singular_launch<3, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
                      }));
     }
     return cudaGetLastError();

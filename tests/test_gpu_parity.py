@@ -4,7 +4,9 @@ on the same seeded meshes.
 Tolerances (relative Frobenius norm per entry set / block):
   FP64 path   <= 1e-6 (expected ~1e-13)
   mixed path  <= 1e-5 (expected ~1e-7)
-  singular pairs are FP64 in both modes: elementwise <= 1e-11
+  singular pairs: FP64 path and Helmholtz elementwise <= 1e-11; mixed Laplace
+    (FP32 evaluations after the Sauter-Schwab transformation, float-float
+    sums) elementwise <= 1e-6 of the largest singular entry (expected ~1e-7)
   ACA block vs dense truth: <= 2 e_oracle,b + 1e-6 (FP64) / + 1e-5 (mixed)
   H-matrix product vs dense product: <= 2 aca_eps
 """
@@ -17,6 +19,11 @@ from paper_1711_01897_gb300 import bem, meshes
 pytestmark = pytest.mark.gpu
 
 TOL = {bem.FP64: 1e-6, bem.MIXED: 1e-5}
+
+
+def sing_tol(prec, k):
+    """Elementwise bound on touching pairs, relative to the largest of them."""
+    return 1e-6 if (prec == bem.MIXED and k == 0) else 1e-11
 
 
 def relf(a, b):
@@ -83,11 +90,12 @@ def test_entries_against_oracle(l3, l3_mesh, op, k, prec):
     assert err <= TOL[prec], err
     if prec == bem.FP64:
         assert err < 1e-11, err
-    # singular pairs are FP64 in both modes and follow the same rule
+    # singular pairs: FP64 in the FP64 path and for Helmholtz, FP32
+    # evaluations with float-float sums in the mixed Laplace path
     sing = (T[test][:, None, :, None] == T[trial][None, :, None, :]).any(axis=(2, 3))
     assert sing.sum() > 20
     scale = np.abs(ref[sing]).max()
-    assert np.max(np.abs(got[sing] - ref[sing])) <= 1e-11 * scale
+    assert np.max(np.abs(got[sing] - ref[sing])) <= sing_tol(prec, k) * scale
 
 
 def test_entries_full_matrix_small_meshes(lib):
@@ -137,7 +145,7 @@ def test_entries_mixed_tiles_ragged(lib, l3, l3_mesh, op, k):
     assert relf(got, ref) <= TOL[bem.MIXED]
     sing = (T[test][:, None, :, None] == T[trial][None, :, None, :]).any(axis=(2, 3))
     assert sing.sum() > 20
-    assert np.max(np.abs(got[sing] - ref[sing])) <= 1e-11 * np.abs(ref[sing]).max()
+    assert np.max(np.abs(got[sing] - ref[sing])) <= sing_tol(bem.MIXED, k) * np.abs(ref[sing]).max()
     # a bad id inside a tile is reported, not evaluated
     bad = test.copy()
     bad[70] = T.shape[0] + 5
