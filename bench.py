@@ -39,7 +39,7 @@ UNIT = "integrals/s"
 WORKLOAD = {"workload": "laplace_slp_dlp_p0_icosphere_l6_jitter5pct", "n_triangles": 81920,
             "leaf_size": 32, "eta": 1.2, "aca_eps": 1e-5, "operators": ["SLP", "DLP"],
             "quadrature": "6-pt degree-4 regular, Sauter-Schwab 4^4 GL singular",
-            "precision": "mixed (FP32 quadrature, float-float accumulation, FP64 ACA)",
+            "precision": "BEM_MIXED: FP32 regular quadrature with float-float accumulation; FP64 singular pairs, ACA pivots, residual updates and norms",
             "l2": "flushed between timed steps (256 MiB write)"}
 LEAF, ETA, EPS = 32, 1.2, 1e-5
 
@@ -425,6 +425,42 @@ def run_gpu(args):
             np.linalg.norm(y_mixed[op] - y_fp64[op]) / np.linalg.norm(y_fp64[op])) for op in hs},
         "tolerance": 2 * EPS}
 
+    # the same step in BEM_MIXED_SP (the norm's dot products and the Laplace
+    # singular integrands in single precision as well), products against the
+    # FP64 step above
+    sp_ms, sp_ents, sp_phase = [], 0, {"singular": 0.0, "aca": 0.0}
+    for _ in range(args.warmup):
+        step(bem.MIXED_SP)
+        flush.fill_(1)
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.fill_(s & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sp_ents += step(bem.MIXED_SP)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sp_ms.append(a.elapsed_time(b))
+        for h in hs.values():
+            st = h.stats()
+            sp_phase["singular"] += st["time_singular_ms"]
+            sp_phase["aca"] += st["time_far_ms"]
+    sp_total = float(np.sum(sp_ms))
+    if ws > 1:
+        sp_total, sp_ents_all = reduce_over_ranks(sp_total, sp_ents, dist, dev)
+    else:
+        sp_ents_all = float(sp_ents)
+    y_sp = {op: ys[op].cpu().numpy().copy() for op in hs}
+    mixed_sp = {
+        "precision": "BEM_MIXED_SP: as BEM_MIXED, plus FP32 dot products in the ACA norm "
+                     "and FP32 Sauter-Schwab integrands (float-float sums) for the singular pairs",
+        "value": sp_ents_all / (sp_total * 1e-3), "unit": UNIT,
+        "ms_per_step": sp_total / args.steps,
+        "phase_ms_per_step": {k_: v / args.steps for k_, v in sp_phase.items()},
+        "matvec_rel_diff_vs_fp64": {("SLP" if op == 0 else "DLP"): float(
+            np.linalg.norm(y_sp[op] - y_fp64[op]) / np.linalg.norm(y_fp64[op])) for op in hs},
+        "tolerance": 2 * EPS}
+
     # the same step on trees built with the autotuned distance classes of the
     # regular rule, products against the FP64 6-point step above
     auto_q = None
@@ -536,19 +572,19 @@ def run_gpu(args):
     if dom == "aca":
         # algorithmic work of the mixed ACA per step.  rank^2 (m+n) per block
         # (aca_fp64_fma) counts the residual updates (about half) and the
-        # norm's dot products (the other half, FP32 on this path).  FP64: the
-        # residual updates, one addition per entry (widening the float-float
+        # norm's dot products (the other half), both FP64 in BEM_MIXED.
+        # FP64: those, one addition per entry (widening the float-float
         # quadrature sum) and one multiplication per column entry (1/pivot).
         # FP32: 7 (SLP) / 12 (DLP) operations per point pair (the per-unit
-        # figures of the quadrature roofline), 36 pairs per entry, plus the
-        # norm's multiply-adds.  MUFU: one rsqrt per pair.
+        # figures of the quadrature roofline), 36 pairs per entry.  MUFU: one
+        # rsqrt per pair.
         k2 = st_slp["aca_fp64_fma"] + st_dlp["aca_fp64_fma"]
         far = st_slp["far_entries"] + st_dlp["far_entries"]
         t_s = per_step[dom] * 1e-3
-        ops = 0.5 * k2 + 1.5 * far
+        ops = k2 + 1.5 * far
         achieved = ops / t_s / 1e9
-        fp32_ops = (36.0 * (QUAD_FP32_PER_EVAL[0] * st_slp["far_entries"]
-                            + QUAD_FP32_PER_EVAL[1] * st_dlp["far_entries"]) + 0.5 * k2)
+        fp32_ops = 36.0 * (QUAD_FP32_PER_EVAL[0] * st_slp["far_entries"]
+                           + QUAD_FP32_PER_EVAL[1] * st_dlp["far_entries"])
         fp32_peak = peaks["fp32_fma_per_s"] / 1e9
         roof = {"kernel": "k_aca (persistent ACA + far-field quadrature)", "bound": "alu",
                 "pipe": "FP64 (DFMA/DADD/DMUL): the largest single-pipe demand per step",
@@ -557,9 +593,9 @@ def run_gpu(args):
                 "traffic": ACA_TRAFFIC_BYTES_PER_STEP_L6 if args.level == 6 else None,
                 "traffic_unit": "DRAM bytes per step (both k_aca launches, ncu capture)",
                 "algorithmic": {"fp64_ops": ops, "fp32_ops": fp32_ops, "mufu_ops": evals_far,
-                                "how": "FP64 = rank^2(m+n)/2 residual multiply-adds + 1.5 per entry; "
-                                       "FP32 = 36 x (7 SLP | 12 DLP) per entry + rank^2(m+n)/2 norm "
-                                       "multiply-adds; MUFU = 36 rsqrt per entry"},
+                                "how": "FP64 = rank^2(m+n)/2 residual multiply-adds + rank^2(m+n)/2 "
+                                       "norm multiply-adds + 1.5 per entry; FP32 = 36 x (7 SLP | 12 DLP) "
+                                       "per entry; MUFU = 36 rsqrt per entry"},
                 "pipe_ms_at_peak": {"fp64": ops / (fp64_peak * 1e9) * 1e3,
                                     "fp32": fp32_ops / (fp32_peak * 1e9) * 1e3,
                                     "mufu": evals_far / (mufu_peak * 1e9) * 1e3},
@@ -639,6 +675,7 @@ def run_gpu(args):
                 "gpu_launches": int(launches), "step_ms": step_ms}
         if auto_q is not None:
             line["autotuned_quadrature"] = auto_q
+        line["mixed_sp"] = mixed_sp
         line["measured_peaks"] = peaks
         line.update(extras)
         if args.rho3 > 0 or args.rho1 > 0:

@@ -40,16 +40,24 @@
  *    degree-4 triangle rule in both triangles (Sec. 3.2.1, Sec. 3.2.3);
  *    pairs that share a vertex, an edge or the whole triangle use the
  *    Sauter-Schwab transformations of [0,1]^4 with 4 Gauss-Legendre points
- *    per axis (the Erichsen-Sauter scheme cited in Sec. 3.2.3): in FP64 for
- *    BEM_FP64 and for Helmholtz; for Laplace in BEM_MIXED the transformed
- *    (smooth) integrands are evaluated in FP32 and summed in float-float.
- *  - Precision (Sec. 3.2.4): BEM_FP64 evaluates every regular pair in FP64;
- *    BEM_MIXED evaluates regular pairs in FP32 (centroid-relative geometry)
- *    and accumulates each entry's quadrature sum in float-float (about 48
- *    significant bits) before it is stored in FP64.  ACA pivoting, residual
- *    updates and the norm's accumulation are FP64 in both modes; in
- *    BEM_MIXED the norm's dot products, which feed only the stopping test,
- *    are FP32.
+ *    per axis (the Erichsen-Sauter scheme cited in Sec. 3.2.3), in FP64
+ *    (BEM_MIXED_SP excepted, below).
+ *  - Precision (Sec. 3.2.4):
+ *      BEM_FP64      every quadrature, pivot, residual update and norm in FP64.
+ *      BEM_MIXED     regular pairs (far field and the non-touching near
+ *                    field) in FP32 with centroid-relative geometry, each
+ *                    entry's quadrature sum accumulated in float-float (about
+ *                    48 significant bits) and stored in FP64; FP64 for the
+ *                    singular pairs, the ACA pivot search, the residual
+ *                    updates and the norms of the stopping test.
+ *      BEM_MIXED_SP  BEM_MIXED, plus single precision in two more places:
+ *                    the dot products of the norm of S_k (they feed only the
+ *                    stopping test; its accumulation stays FP64), and, for
+ *                    Laplace, the Sauter-Schwab integrands after the
+ *                    transformation (FP32 evaluations, float-float sums; the
+ *                    pair's geometry and final scaling FP64).  P0 only
+ *                    (hmat_assemble on DP1 / P1 handles returns BEM_E_ARG);
+ *                    not for bem_entries_dp1.
  */
 #ifndef BEM_H
 #define BEM_H
@@ -65,7 +73,7 @@ typedef struct bem_hmat_s *bem_hmat;
 
 enum bem_op { BEM_SLP = 0, BEM_DLP = 1, BEM_ADLP = 2, BEM_HYPS = 3 };
 enum bem_space { BEM_P0 = 0, BEM_DP1 = 1, BEM_P1 = 2 };
-enum bem_prec { BEM_FP64 = 0, BEM_MIXED = 1 };
+enum bem_prec { BEM_FP64 = 0, BEM_MIXED = 1, BEM_MIXED_SP = 2 };
 enum bem_status {
     BEM_OK = 0,
     BEM_E_ARG = 1,     /* invalid argument (null handle, size, enum, index) */
@@ -214,7 +222,8 @@ int64_t bem_mesh_size(bem_mesh mesh);
  * device-resident ids are checked on the device and a bad id makes the call
  * return BEM_E_ARG at its next synchronisation (the call then waits for the
  * stream).  test_ids, trial_ids and out may each be host or device memory.
- * prec: BEM_FP64 or BEM_MIXED (regular pairs only; singular pairs are FP64).
+ * prec: BEM_FP64, BEM_MIXED (regular pairs in FP32, singular pairs FP64) or
+ * BEM_MIXED_SP (Laplace singular pairs with FP32 integrands as well).
  * Allocates stream-ordered device scratch for the list of singular pairs
  * (sized by n_test times the most triangles touching one triangle; repeated
  * trial ids that hold more touching pairs make a second, exactly sized pass).
@@ -259,8 +268,9 @@ int bem_entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec,
  *   out[3 a + alpha][3 b + beta] = int_{T_i} int_{T_j} lambda_alpha g' lambda_beta,
  *   i = test_tris[a], j = trial_tris[b], row-major [3 n_test][3 n_trial],
  * with lambda the barycentric coordinates of the stored vertices and g' the
- * kernel of op (BEM_SLP, BEM_DLP or BEM_ADLP).  Same quadrature, precision,
- * argument rules, scratch and synchronisation as bem_entries; touching pairs
+ * kernel of op (BEM_SLP, BEM_DLP or BEM_ADLP).  Same quadrature, precision
+ * (BEM_FP64 or BEM_MIXED; BEM_MIXED_SP gives BEM_E_ARG), argument rules,
+ * scratch and synchronisation as bem_entries; touching pairs
  * use the Sauter-Schwab rule with the basis functions at the mapped points. */
 int bem_entries_dp1(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t *test_tris,
                     int64_t n_test, const int32_t *trial_tris, int64_t n_trial, void *out,
@@ -311,7 +321,8 @@ int64_t hmat_dofs(bem_hmat hmat);
  *  op       BEM_SLP, BEM_DLP, BEM_ADLP; BEM_HYPS on BEM_P1 handles (the
  *           single layer on DP1 is assembled, the rest is applied in products)
  *  aca_eps  > 0
- *  prec     BEM_FP64 or BEM_MIXED (see the top of this file)
+ *  prec     BEM_FP64, BEM_MIXED, or (P0 handles) BEM_MIXED_SP (see the top
+ *           of this file)
  * May be called again on the same handle (the previous matrix is replaced).
  * Synchronous: it reads back the device status word; a bounded device wait
  * that runs out gives BEM_E_TIMEOUT. */
@@ -349,7 +360,8 @@ typedef struct {
     int64_t aca_fp64_fma;        /* sum over admissible blocks of rank^2 (m + n): the
                                     multiply-adds of the ACA residual updates (about half,
                                     FP64) and of the norm's dot products (the other half:
-                                    FP64 in BEM_FP64, FP32 in BEM_MIXED) */
+                                    FP64 in BEM_FP64 and BEM_MIXED, FP32 in
+                                    BEM_MIXED_SP) */
     int32_t assembled;
     int32_t op;
     double k;

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libbem.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "bem.h")
 
 SLP, DLP, ADLP, HYPS = 0, 1, 2, 3
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_SP = 0, 1, 2
 P0, DP1, P1 = 0, 1, 2
 STATUS = {0: "BEM_OK", 1: "BEM_E_ARG", 2: "BEM_E_MESH", 3: "BEM_E_OOM", 4: "BEM_E_CUDA",
           5: "BEM_E_TIMEOUT", 6: "BEM_E_STATE"}

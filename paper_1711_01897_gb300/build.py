@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libbem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 SOURCES = ["host.cpp", "server.cpp", "kernels_entries.cu", "kernels_aca.cu",
-           "kernels_aca_dp1.cu", "kernels_dp1.cu", "kernels_matvec.cu", "entries_noalloc.cu",
+           "kernels_aca_dp1.cu", "kernels_aca_sp.cu", "kernels_dp1.cu", "kernels_matvec.cu", "entries_noalloc.cu",
            "kernels_calib.cu"]
 
 

@@ -289,6 +289,44 @@ struct SubGroup {
     }
 };
 
+// The FP64 form of the dot-product members of VT (the interface
+// group_col_dots reads: F, zerof, tofp, fdot, addf, shfl_xorf, re_mulf), for
+// the norm of the mixed path when its dot products stay FP64 (BEM_MIXED):
+// values are loaded whole, B is unused.
+template <bool CPLX>
+struct DotF64;
+
+template <>
+struct DotF64<false> {
+    using F = double;
+    static __device__ __forceinline__ F zerof() { return 0.0; }
+    static __device__ __forceinline__ F tofp(const double *p, unsigned) { return *p; }
+    static __device__ __forceinline__ F fdot(F a, F b, F acc) { return fma(a, b, acc); }
+    static __device__ __forceinline__ F addf(F a, F b) { return a + b; }
+    static __device__ __forceinline__ double re_mulf(F a, F b) { return a * b; }
+    static __device__ __forceinline__ F shfl_xorf(F a, int d, unsigned mask)
+    {
+        return __shfl_xor_sync(mask, a, d);
+    }
+};
+
+template <>
+struct DotF64<true> {
+    using F = double2;
+    static __device__ __forceinline__ F zerof() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ F tofp(const double2 *p, unsigned) { return *p; }
+    static __device__ __forceinline__ F fdot(F a, F b, F acc)  // conj(a) b + acc
+    {
+        return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+    }
+    static __device__ __forceinline__ F addf(F a, F b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ double re_mulf(F a, F b) { return fma(a.x, b.x, -a.y * b.y); }
+    static __device__ __forceinline__ F shfl_xorf(F a, int d, unsigned mask)
+    {
+        return make_double2(__shfl_xor_sync(mask, a.x, d), __shfl_xor_sync(mask, a.y, d));
+    }
+};
+
 // Dot products <x_l, x_k> for the NC factor columns l0 .. l0 + NC - 1 (those
 // below ncol) of a group of W lanes: lanes stride over the rows (coalesced),
 // each holding NC accumulators and forming the float of x_k[r] once; a
@@ -296,24 +334,27 @@ struct SubGroup {
 // with column l0 + bitrev(t mod NC), summed over the lanes of its NC-lane
 // set, and xor rounds over the higher bits complete the group sum.  cols:
 // the first column of the chunk that holds l0 and of the next chunk (stride
-// ld between the columns of a chunk); xk: column k.
-template <class V, int NC, int W>
-__device__ __forceinline__ typename V::F group_col_dots(const typename V::T *c0, const typename V::T *c1,
+// ld between the columns of a chunk), q0 = l0 mod KCHUNK (nonzero only when
+// NC < KCHUNK); xk: column k.
+template <class V, class D, int NC, int W>
+__device__ __forceinline__ typename D::F group_col_dots(const typename V::T *c0, const typename V::T *c1,
                                                         int64_t ld, const typename V::T *xk, int len,
-                                                        int nvalid, unsigned B, int t, unsigned mask)
+                                                        int nvalid, unsigned B, int t, unsigned mask,
+                                                        int q0)
 {
-    using F = typename V::F;
+    using F = typename D::F;
     F acc[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) acc[q] = V::zerof();
+    for (int q = 0; q < NC; ++q) acc[q] = D::zerof();
 #pragma unroll 2
     for (int r = t; r < len; r += W) {
-        const F x = V::tofp(xk + r, B);
+        const F x = D::tofp(xk + r, B);
 #pragma unroll
         for (int q = 0; q < NC; ++q)
             if (q < nvalid) {
-                const typename V::T *c = (q < KCHUNK ? c0 : c1) + (int64_t)(q % KCHUNK) * ld;
-                acc[q] = V::fdot(V::tofp(c + r, B), x, acc[q]);
+                const int qc = q0 + q;  // column within the chunk pair
+                const typename V::T *c = (qc < KCHUNK ? c0 : c1) + (int64_t)(qc % KCHUNK) * ld;
+                acc[q] = D::fdot(D::tofp(c + r, B), x, acc[q]);
             }
     }
 #pragma unroll
@@ -323,11 +364,11 @@ __device__ __forceinline__ typename V::F group_col_dots(const typename V::T *c0,
         for (int q = 0; q < n; ++q) {
             const F send = up ? acc[q] : acc[q + n];
             const F keep = up ? acc[q + n] : acc[q];
-            acc[q] = V::addf(keep, V::shfl_xorf(send, d, mask));
+            acc[q] = D::addf(keep, D::shfl_xorf(send, d, mask));
         }
     }
 #pragma unroll
-    for (int d = NC; d < W; d <<= 1) acc[0] = V::addf(acc[0], V::shfl_xorf(acc[0], d, mask));
+    for (int d = NC; d < W; d <<= 1) acc[0] = D::addf(acc[0], D::shfl_xorf(acc[0], d, mask));
     return acc[0];
 }
 
@@ -462,7 +503,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
 {
     using V = VT<CPLX>;
     using T = typename V::T;
-    using E = RegularEntry<OP, CPLX, PREC>;
+    using E = RegularEntry<OP, CPLX, (PREC != 0 ? 1 : 0)>;
     const int64_t tb = blk->tb, sb = blk->sb;
     const int64_t m = blk->te - tb, n = blk->se - sb;
     const int rule = blk->rule;  // the block's distance class (P0 Laplace entries)
@@ -621,7 +662,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             for (int l = t; l < kk; l += GS) S.cu[l] = *Uat(l, i);
             G.sync();
             long long bkey = -1;
-            using L = LocalEntry<OP, CPLX, PREC>;
+            using L = LocalEntry<OP, CPLX, (PREC != 0 ? 1 : 0)>;
             typename L::Tri ti;
             L::load(g, tb / 3 + i / 3, ti);
             const int alpha = (int)(i % 3);
@@ -675,7 +716,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         // selected column of R_{k-1}: a_{:,j} - sum_l (v_l)_j u_l
         for (int l = t; l < kk; l += GS) S.cu[l] = *Vat(l, bj);
         G.sync();
-            using L = LocalEntry<OP, CPLX, PREC>;
+            using L = LocalEntry<OP, CPLX, (PREC != 0 ? 1 : 0)>;
             typename L::Tri tj;
             L::load(g, sb / 3 + bj / 3, tj);
             const int beta = (int)(bj % 3);
@@ -716,17 +757,17 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
         // (k+1) * segments additions.
         double incr = 0.0, uv2 = 0.0;
         const int ncol = kk + 1;
-        // Mixed precision: the dot products in FP32 from floats formed on the
-        // integer pipe (hi_to_float), the factor that carries the pivots'
-        // magnitude scaled by 2^-E with 2^E the largest pivot so far, so that
-        // its squares and products stay in the float range (the other factor
-        // is divided by its pivot, the largest entry of its row, and is
-        // O(1)); each product is rescaled by 2^2E in FP64.  The norm feeds only the
-        // stopping test, whose threshold a relative error of ~1e-6 moves by
-        // as much.  FP64 dot products in the FP64 path.
+        // BEM_MIXED_SP (PREC 2): the dot products in FP32 from floats formed
+        // on the integer pipe (hi_to_float), the factor that carries the
+        // pivots' magnitude scaled by 2^-E with 2^E the largest pivot so far,
+        // so that its squares and products stay in the float range (the
+        // other factor is divided by its pivot, the largest entry of its row,
+        // and is O(1)); each product is rescaled by 2^2E in FP64.  The norm
+        // feeds only the stopping test, whose threshold a relative error of
+        // ~1e-6 moves by as much.  FP64 dot products in BEM_MIXED and BEM_FP64.
         unsigned Bu = 896u << 20, Bv = 896u << 20;
         double unscale = 1.0;
-        if constexpr (PREC == 1) {
+        if constexpr (PREC == 2) {
             int E = V::key_exp2(maxkey);
             E = E < -500 ? -500 : (E > 500 ? 500 : E);
             // P0: u_k carries 1/pivot (|u| = O(1)), v_k the pivot's scale;
@@ -742,7 +783,7 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
             const int mi = (int)m, ni = (int)n;
             const int r0 = (mi * sgi) / nseg, r1 = (mi * (sgi + 1)) / nseg;
             const int j0 = (ni * sgi) / nseg, j1 = (ni * (sgi + 1)) / nseg;
-            if constexpr (PREC == 1) {
+            if constexpr (PREC == 2) {
                 typename V::F fu = V::zerof(), fv = V::zerof();
                 for (int r = r0; r < r1; ++r) fu = V::dotf(ul[r], uk[r], Bu, fu);
                 for (int j = j0; j < j1; ++j) fv = V::dotf(vl[j], vk[j], Bv, fv);
@@ -753,35 +794,47 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 for (int j = j0; j < j1; ++j) iv = V::dotc(vl[j], vk[j], iv);
             }
         };
-        if constexpr (Grp::kShuffle && PREC == 1) {
-            // columns in register groups of NC (group_col_dots); the
-            // increment summed in FP32 (scaled), then rescaled once
-            constexpr int NC = CPLX ? 4 : 8;
+        if constexpr (Grp::kShuffle && PREC != 0) {
+            // columns in register groups of NC (group_col_dots), the same
+            // register footprint in both forms: BEM_MIXED_SP sums FP32
+            // products (scaled) and rescales the increment once; BEM_MIXED
+            // keeps the dot products and their sums in FP64
+            constexpr bool kF32 = PREC == 2;
+            using D = std::conditional_t<kF32, V, DotF64<CPLX>>;
+            using S_t = std::conditional_t<kF32, float, double>;
+            constexpr int NC = kF32 ? (CPLX ? 4 : 8) : (CPLX ? 2 : 4);
             constexpr int W = Grp::kWidth;
-            static_assert(KCHUNK == 4 && NC <= 2 * KCHUNK && NC <= W, "column groups span two chunks");
-            float incr_f = 0.f, uv2_f = 0.f;
+            static_assert(KCHUNK == 4 && NC <= 2 * KCHUNK && NC <= W &&
+                              (NC % KCHUNK == 0 || KCHUNK % NC == 0), "column groups span two chunks");
+            S_t incr_s = 0, uv2_s = 0;
             const T *uk = Uat(kk, 0), *vk = Vat(kk, 0);
             for (int l0 = 0; l0 < ncol; l0 += NC) {
                 const int nv = ncol - l0 < NC ? ncol - l0 : NC;
+                const int q0 = NC < KCHUNK ? l0 % KCHUNK : 0;
                 const T *u0 = pool + S.chunk[l0 / KCHUNK];
-                const T *u1 = nv > KCHUNK ? pool + S.chunk[l0 / KCHUNK + 1] : u0;
-                const typename V::F su =
-                    group_col_dots<V, NC, W>(u0, u1, m, uk, (int)m, nv, Bu, t, G.mask);
-                const typename V::F sv = group_col_dots<V, NC, W>(
-                    u0 + (int64_t)KCHUNK * m, u1 + (int64_t)KCHUNK * m, n, vk, (int)n, nv, Bv, t, G.mask);
+                const T *u1 = q0 + nv > KCHUNK ? pool + S.chunk[l0 / KCHUNK + 1] : u0;
+                const typename D::F su =
+                    group_col_dots<V, D, NC, W>(u0, u1, m, uk, (int)m, nv, Bu, t, G.mask, q0);
+                const typename D::F sv = group_col_dots<V, D, NC, W>(
+                    u0 + (int64_t)KCHUNK * m, u1 + (int64_t)KCHUNK * m, n, vk, (int)n, nv, Bv, t, G.mask, q0);
                 const int c = l0 + bitrev_low<NC>(t % NC);
                 if (t < NC && c < ncol) {
-                    const float pr = V::re_mulf(su, sv);
+                    const S_t pr = D::re_mulf(su, sv);
                     if (c == kk) {
-                        incr_f += pr;
-                        uv2_f = pr;
+                        incr_s += pr;
+                        uv2_s = pr;
                     } else {
-                        incr_f += 2.f * pr;
+                        incr_s += S_t(2) * pr;
                     }
                 }
             }
-            incr = (double)G.sumf(incr_f) * unscale;
-            uv2 = (double)G.sumf(uv2_f) * unscale;
+            if constexpr (kF32) {
+                incr = (double)G.sumf(incr_s) * unscale;
+                uv2 = (double)G.sumf(uv2_s) * unscale;
+            } else {
+                incr = G.sum(incr_s);
+                uv2 = G.sum(uv2_s);
+            }
         } else if constexpr (Grp::kShuffle) {
             // power-of-two segments per column, summed by shuffle trees
             // within the group's lanes
@@ -867,7 +920,7 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
 {
     using V = VT<CPLX>;
     using T = typename V::T;
-    using E = RegularEntry<OP, CPLX, PREC>;
+    using E = RegularEntry<OP, CPLX, (PREC != 0 ? 1 : 0)>;
     const int64_t tb = blk->tb, sb = blk->sb;
     const int m = (int)(blk->te - tb), n = (int)(blk->se - sb);
     const int rule = blk->rule;
@@ -952,11 +1005,11 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
         }
         entries += m;
         // ||S_k||_F^2 increment: 2 Re sum_{l<k} <u_k,u_l><v_k,v_l> + ||u_k||^2 ||v_k||^2
-        // (mixed precision: FP32 dot products as in aca_block)
+        // (BEM_MIXED_SP: FP32 dot products as in aca_block)
         double incr = 0.0, uv2 = 0.0;
         unsigned Bu = 0u;
         double unscale = 1.0;
-        if constexpr (PREC == 1) {
+        if constexpr (PREC == 2) {
             int E = (int)((__double_as_longlong(maxpiv) >> 52) & 0x7ff) - 1023;
             E = E < -500 ? -500 : (E > 500 ? 500 : E);
             Bu = (unsigned)(896 + E) << 20;
@@ -966,7 +1019,7 @@ __device__ void aca_lane(const DevGeom &g, const QuadRule &R, double k, double e
         for (int l = 0; l <= kk; ++l) {
             const T *ul = Uat(l, 0), *vl = Vat(l, 0);
             T iu = V::zero(), iv = V::zero();
-            if constexpr (PREC == 1) {
+            if constexpr (PREC == 2) {
                 typename V::F fu = V::zerof(), fv = V::zerof();
                 for (int r = 0; r < m; ++r) fu = V::dotf(ul[r], uk[r], Bu, fu);
                 for (int j = 0; j < n; ++j) fv = V::dotf(vl[j], vk[j], 896u << 20, fv);

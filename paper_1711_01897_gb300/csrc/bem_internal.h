@@ -264,6 +264,11 @@ cudaError_t launch_aca(const AcaWork &w, const QuadRule &rule, int op, bool cplx
                        AcaQueue *queue, int num_sms, cudaStream_t st, int dofs = 1,
                        bool rules = false);
 
+// the P0 instantiations of BEM_MIXED_SP (kernels_aca_sp.cu: FP32 dot
+// products in the norm of S_k)
+cudaError_t launch_aca_sp(const AcaWork &w, const QuadRule &rule, int op, bool cplx,
+                          AcaQueue *queue, int num_sms, cudaStream_t st, bool rules);
+
 // the DP1 instantiations (kernels_aca_dp1.cu); no tiny-block class
 cudaError_t launch_aca_dp1(const AcaWork &w, const QuadRule &rule, int op, bool cplx, int prec,
                            AcaQueue *queue, int num_sms, cudaStream_t st);

@@ -79,7 +79,7 @@ int entries_noalloc(bem_mesh mesh, int32_t op, double k, int32_t prec, const int
     MeshView M;
     if (!mesh_view(mesh, &M)) return err(BEM_E_ARG, "null mesh");
     if (op < 0 || op > 2) return err(BEM_E_ARG, "bad op");
-    if (prec != BEM_FP64 && prec != BEM_MIXED) return err(BEM_E_ARG, "bad prec");
+    if (prec != BEM_FP64 && prec != BEM_MIXED && prec != BEM_MIXED_SP) return err(BEM_E_ARG, "bad prec");
     if (!(k == k) || k - k != 0.0) return err(BEM_E_ARG, "bad k");
     if (n_test < 0 || n_trial < 0) return err(BEM_E_ARG, "negative size");
     if (n_test == 0 || n_trial == 0) return BEM_OK;

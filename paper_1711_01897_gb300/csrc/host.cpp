@@ -1000,7 +1000,7 @@ int bem_entries(bem_mesh mesh, int32_t op, double k, int32_t prec, const int32_t
     return guarded([&]() -> int {
         if (!mesh) return fail(BEM_E_ARG, "null mesh");
         if (op < 0 || op > 2) return fail(BEM_E_ARG, "bad op");
-        if (prec != BEM_FP64 && prec != BEM_MIXED) return fail(BEM_E_ARG, "bad prec");
+        if (prec != BEM_FP64 && prec != BEM_MIXED && prec != BEM_MIXED_SP) return fail(BEM_E_ARG, "bad prec");
         if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
         if (n_test < 0 || n_trial < 0) return fail(BEM_E_ARG, "negative size");
         if (n_test == 0 || n_trial == 0) return BEM_OK;
@@ -2140,7 +2140,9 @@ int assemble_begin(bem_hmat H, int32_t op, double k, double aca_eps, int32_t pre
     if (op < 0 || op > 3) return fail(BEM_E_ARG, "bad op");
     if (op == BEM_HYPS && H->space != BEM_P1)
         return fail(BEM_E_ARG, "the hypersingular operator needs a BEM_P1 handle");
-    if (prec != BEM_FP64 && prec != BEM_MIXED) return fail(BEM_E_ARG, "bad prec");
+    if (prec != BEM_FP64 && prec != BEM_MIXED && prec != BEM_MIXED_SP) return fail(BEM_E_ARG, "bad prec");
+    if (prec == BEM_MIXED_SP && H->dofs != 1)
+        return fail(BEM_E_ARG, "BEM_MIXED_SP applies to P0 handles only");
     if (!(aca_eps > 0) || !std::isfinite(aca_eps)) return fail(BEM_E_ARG, "aca_eps must be > 0");
     if (!std::isfinite(k)) return fail(BEM_E_ARG, "bad k");
     const bool cplx = k != 0.0;

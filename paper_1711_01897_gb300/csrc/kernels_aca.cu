@@ -247,6 +247,7 @@ cudaError_t launch_aca(const AcaWork &w, const QuadRule &rule, int op, bool cplx
 {
     if (dofs == 3) return launch_aca_dp1(w, rule, op, cplx, prec, queue, num_sms, st);
     if (dofs != 1) return cudaErrorInvalidValue;
+    if (prec == 2) return launch_aca_sp(w, rule, op, cplx, queue, num_sms, st, rules);
     // trees with lower-order distance classes: the mixed Laplace kernels that
     // read each block's rule
     if (rules && !cplx && prec == 1) {

@@ -378,11 +378,12 @@ k_entries_tiled_slp(DevGeom g, QuadRule R, const int32_t *__restrict__ test, int
 constexpr int kSingThreads = 128;
 constexpr int kSingMaxPts = 6 * NGL * NGL * NGL;  // largest table (identical, helm)
 
-// PREC 1 with real k (mixed Laplace): the evaluations after the Sauter-Schwab
-// transformation in FP32 (smooth integrands, the reduced distance bounded
-// away from zero), summed in FP32 within a node row and in float-float
-// outside it; the pair's geometry, its edge basis and the final scaling in
-// FP64.  Otherwise every step in FP64.
+// PREC 1 with real k (Laplace in BEM_MIXED_SP): the evaluations after the
+// Sauter-Schwab transformation in FP32 (smooth integrands, the reduced
+// distance bounded away from zero), summed in FP32 within a node row and in
+// float-float outside it; the pair's geometry, its edge basis and the final
+// scaling in FP64.  Otherwise (BEM_FP64, BEM_MIXED, Helmholtz) every step in
+// FP64.
 template <int CASE, int OP, bool CPLX, int PREC = 0>
 __global__ void __launch_bounds__(kSingThreads)
 k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pairs,
@@ -803,7 +804,7 @@ cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int o
                                    unsigned long long cap, int *err, cudaStream_t st)
 {
     const bool cplx = k != 0.0;
-    BEM_DISPATCH(op, cplx, prec,
+    BEM_DISPATCH(op, cplx, (prec != 0 ? 1 : 0),
                  (entries_launch<OP, CPLX, PREC>(g, rule, k, test, n_test, trial, n_trial, out,
                                                  lists, counts, cap, err, st)));
     return cudaGetLastError();
@@ -835,8 +836,9 @@ cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, dou
         int64_t hc = host_counts[c - 1];
         int64_t gc = grid_counts ? grid_counts[c - 1] : hc;
         const SingPair *P = pairs[c - 1];
-        // mixed precision applies to the Laplace kernels (Helmholtz pairs stay FP64)
-        BEM_DISPATCH(op, cplx, (cplx ? 0 : prec), ({
+        // FP32 integrands only for Laplace in BEM_MIXED_SP; BEM_FP64,
+        // BEM_MIXED and Helmholtz pairs stay FP64
+        BEM_DISPATCH(op, cplx, (!cplx && prec == 2 ? 1 : 0), ({
                          if (c == 1) singular_launch<1, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
                          else if (c == 2) singular_launch<2, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
                          else singular_launch<3, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
@@ -855,7 +857,7 @@ cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, 
     int64_t grid = (warps * 32 + kNearThreads - 1) / kNearThreads;
     int64_t cap = (int64_t)num_sms_cached() * 64;
     if (grid > cap) grid = cap;
-    BEM_DISPATCH(op, cplx, prec,
+    BEM_DISPATCH(op, cplx, (prec != 0 ? 1 : 0),
                  (k_near_regular<OP, CPLX, PREC>
                   <<<(unsigned)grid, kNearThreads, 0, st>>>(g, rule, k, blocks, nblocks, out)));
     count_launches(1);

@@ -625,7 +625,7 @@ int bem_server_submit(bem_server S, const bem_request *q, int64_t *req_id)
     const bool product = q->reuse > 0;
     if (!q->x || (!product && (!q->vertices || !q->triangles || q->n_vertices < 3 ||
                                q->n_triangles < 1 || q->op < 0 || q->op > 2 ||
-                               (q->prec != BEM_FP64 && q->prec != BEM_MIXED) ||
+                               (q->prec != BEM_FP64 && q->prec != BEM_MIXED && q->prec != BEM_MIXED_SP) ||
                                !(q->aca_eps > 0) || q->leaf_size < 1 || !(q->eta > 0))) ||
         (product && q->n_triangles < 1)) {
         set_last_error("bad request");

@@ -23,8 +23,8 @@ from paper_1711_01897_gb300 import bem, meshes
 
 pytestmark = pytest.mark.gpu
 
-TOL = {bem.FP64: 1e-6, bem.MIXED: 1e-5}
-NOISE = {bem.FP64: 1e-15, bem.MIXED: 1e-7}
+TOL = {bem.FP64: 1e-6, bem.MIXED: 1e-5, bem.MIXED_SP: 1e-5}
+NOISE = {bem.FP64: 1e-15, bem.MIXED: 1e-7, bem.MIXED_SP: 1e-7}
 
 # (warp_max_rows, lane_max_rows): the shapes each puts blocks on, for the L3
 # mesh (blocks of 20 and 40 rows) and the L4 mesh (20 to 160 rows).  "warp"
@@ -118,7 +118,7 @@ def _check_shapes(stats, want, l4=False):
 
 @pytest.mark.parametrize("shape", sorted(SHAPES))
 @pytest.mark.parametrize("case", CASES, ids=["slp", "dlp", "helmholtz_slp_k2"])
-@pytest.mark.parametrize("prec", [bem.FP64, bem.MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("prec", [bem.FP64, bem.MIXED, bem.MIXED_SP], ids=["fp64", "mixed", "mixed_sp"])
 def test_every_block_every_shape_l3(lib, l3, l3_dense, shape, case, prec):
     """Jittered L3 (1,280 triangles), leaf 32, eta 1.2, eps 1e-5: every
     admissible block and the product."""
@@ -165,17 +165,17 @@ def test_every_block_every_shape_l3(lib, l3, l3_dense, shape, case, prec):
           f"shapes cta/warp/lane {s['n_blocks_cta']}/{s['n_blocks_warp']}/{s['n_blocks_lane']}")
 
 
+@pytest.mark.parametrize("prec", [bem.MIXED, bem.MIXED_SP], ids=["mixed", "mixed_sp"])
 @pytest.mark.parametrize("shape", ["cta_warp", "lane_warp", "default"])
 @pytest.mark.parametrize("case", CASES, ids=["slp", "dlp", "helmholtz_slp_k2"])
-def test_sampled_blocks_every_shape_l4(lib, shape, case):
-    """Jittered L4 (5,120 triangles; blocks of 20 to 160 rows), mixed: the
-    largest blocks of every shape plus random ones against the oracle's dense
-    blocks, and 24 exact rows of the product."""
+def test_sampled_blocks_every_shape_l4(lib, shape, case, prec):
+    """Jittered L4 (5,120 triangles; blocks of 20 to 160 rows), both mixed
+    modes: the largest blocks of every shape plus random ones against the
+    oracle's dense blocks, and 24 exact rows of the product."""
     V, T = meshes.icosphere_level(4)
     V = meshes.jitter(V, T, 0.05, 41)
     op, k = case
     eps = 1e-5
-    prec = bem.MIXED
     (wmax, lmax), want = SHAPES[shape]
     m = bem.Mesh(V, T)
 
@@ -247,7 +247,7 @@ def test_entries_repeated_trial_ids(lib):
     m = bem.Mesh(V, T)
     test = np.array([0, 7], dtype=np.int32)
     trial = np.array([0] * 40 + [1, 2, 3] * 10 + [7] * 25, dtype=np.int32)
-    for prec in (bem.FP64, bem.MIXED):
+    for prec in (bem.FP64, bem.MIXED, bem.MIXED_SP):
         got = m.entries(bem.SLP, 0.0, prec, test, trial)
         ref = oracle.entries(V, T, bem.SLP, 0.0, test, trial).real
         assert relf(got, ref) < (1e-11 if prec == bem.FP64 else 1e-5)

@@ -4,9 +4,10 @@ on the same seeded meshes.
 Tolerances (relative Frobenius norm per entry set / block):
   FP64 path   <= 1e-6 (expected ~1e-13)
   mixed path  <= 1e-5 (expected ~1e-7)
-  singular pairs: FP64 path and Helmholtz elementwise <= 1e-11; mixed Laplace
-    (FP32 evaluations after the Sauter-Schwab transformation, float-float
-    sums) elementwise <= 1e-6 of the largest singular entry (expected ~1e-7)
+  singular pairs: FP64 in BEM_FP64, BEM_MIXED and for Helmholtz,
+    elementwise <= 1e-11; Laplace in BEM_MIXED_SP (FP32 evaluations after the
+    Sauter-Schwab transformation, float-float sums) elementwise <= 1e-6 of
+    the largest singular entry (expected ~1e-7)
   ACA block vs dense truth: <= 2 e_oracle,b + 1e-6 (FP64) / + 1e-5 (mixed)
   H-matrix product vs dense product: <= 2 aca_eps
 """
@@ -18,19 +19,19 @@ from paper_1711_01897_gb300 import bem, meshes
 
 pytestmark = pytest.mark.gpu
 
-TOL = {bem.FP64: 1e-6, bem.MIXED: 1e-5}
+TOL = {bem.FP64: 1e-6, bem.MIXED: 1e-5, bem.MIXED_SP: 1e-5}
 
 
 def sing_tol(prec, k):
     """Elementwise bound on touching pairs, relative to the largest of them."""
-    return 1e-6 if (prec == bem.MIXED and k == 0) else 1e-11
+    return 1e-6 if (prec == bem.MIXED_SP and k == 0) else 1e-11
 
 
 def relf(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-NOISE = {bem.FP64: 1e-15, bem.MIXED: 1e-7}
+NOISE = {bem.FP64: 1e-15, bem.MIXED: 1e-7, bem.MIXED_SP: 1e-7}
 
 
 def aca_yardstick(truth, eps, prec, extra=(), draws=4, seed=0):
@@ -74,7 +75,7 @@ def _touching_ids(T, seeds):
 
 @pytest.mark.parametrize("op", [bem.SLP, bem.DLP, bem.ADLP])
 @pytest.mark.parametrize("k", [0.0, 2.0])
-@pytest.mark.parametrize("prec", [bem.FP64, bem.MIXED])
+@pytest.mark.parametrize("prec", [bem.FP64, bem.MIXED, bem.MIXED_SP])
 def test_entries_against_oracle(l3, l3_mesh, op, k, prec):
     V, T = l3
     rng = np.random.default_rng(100 + op + 10 * int(k) + 100 * prec)
@@ -90,8 +91,8 @@ def test_entries_against_oracle(l3, l3_mesh, op, k, prec):
     assert err <= TOL[prec], err
     if prec == bem.FP64:
         assert err < 1e-11, err
-    # singular pairs: FP64 in the FP64 path and for Helmholtz, FP32
-    # evaluations with float-float sums in the mixed Laplace path
+    # singular pairs: FP64 in BEM_FP64, BEM_MIXED and for Helmholtz, FP32
+    # evaluations with float-float sums for Laplace in BEM_MIXED_SP
     sing = (T[test][:, None, :, None] == T[trial][None, :, None, :]).any(axis=(2, 3))
     assert sing.sum() > 20
     scale = np.abs(ref[sing]).max()
@@ -126,10 +127,11 @@ def test_entries_device_pointers_and_ragged(lib, l3):
     assert relf(outc.cpu().numpy(), refc) < 1e-11
 
 
+@pytest.mark.parametrize("prec", [bem.MIXED, bem.MIXED_SP])
 @pytest.mark.parametrize("op", [bem.SLP, bem.DLP, bem.ADLP])
 @pytest.mark.parametrize("k", [0.0, 2.0])
-def test_entries_mixed_tiles_ragged(lib, l3, l3_mesh, op, k):
-    """Mixed path over several 64-row x 32-column tiles with ragged tails in
+def test_entries_mixed_tiles_ragged(lib, l3, l3_mesh, op, k, prec):
+    """Mixed paths over several 64-row x 32-column tiles with ragged tails in
     both directions, repeated ids and touching pairs inside tiles."""
     V, T = l3
     rng = np.random.default_rng(7 + op + int(10 * k))
@@ -138,19 +140,19 @@ def test_entries_mixed_tiles_ragged(lib, l3, l3_mesh, op, k):
     trial = np.concatenate([rng.choice(T.shape[0], 150, replace=False),
                             _touching_ids(T, [11, 701])]).astype(np.int32)
     assert len(test) % 64 and len(trial) % 32 and len(test) > 3 * 64 and len(trial) > 5 * 32
-    got = l3_mesh.entries(op, k, bem.MIXED, test, trial)
+    got = l3_mesh.entries(op, k, prec, test, trial)
     ref = oracle.entries(V, T, op, k, test, trial)
     if k == 0:
         ref = ref.real
-    assert relf(got, ref) <= TOL[bem.MIXED]
+    assert relf(got, ref) <= TOL[prec]
     sing = (T[test][:, None, :, None] == T[trial][None, :, None, :]).any(axis=(2, 3))
     assert sing.sum() > 20
-    assert np.max(np.abs(got[sing] - ref[sing])) <= sing_tol(bem.MIXED, k) * np.abs(ref[sing]).max()
+    assert np.max(np.abs(got[sing] - ref[sing])) <= sing_tol(prec, k) * np.abs(ref[sing]).max()
     # a bad id inside a tile is reported, not evaluated
     bad = test.copy()
     bad[70] = T.shape[0] + 5
     with pytest.raises(bem.BemError) as e:
-        l3_mesh.entries(op, k, bem.MIXED, bad, trial)
+        l3_mesh.entries(op, k, prec, bad, trial)
     assert e.value.status == 1
 
 
@@ -213,7 +215,7 @@ def test_block_tree_matches_oracle(lib, l3):
         (T[:, None, :, None] == T[None, :, None, :]).any(axis=(2, 3)).sum())
 
 
-@pytest.mark.parametrize("prec", [bem.FP64, bem.MIXED])
+@pytest.mark.parametrize("prec", [bem.FP64, bem.MIXED, bem.MIXED_SP])
 @pytest.mark.parametrize("op", [bem.SLP, bem.DLP])
 def test_hmatrix_blocks_and_matvec_l3(lib, l3, l3_oracle_dense, prec, op):
     """Workload: Laplace P0 on icosphere L3 (1,280 triangles), leaf 32,
@@ -241,7 +243,7 @@ def test_hmatrix_blocks_and_matvec_l3(lib, l3, l3_oracle_dense, prec, op):
             assert e <= 2 * e_or + TOL[prec], (b, e, e_or, rank)
             assert 0 < rank < min(te - tb, se - sb)
         else:
-            assert relf(got, truth) <= TOL[prec] if prec == bem.MIXED else relf(got, truth) < 1e-12
+            assert relf(got, truth) <= TOL[prec] if prec != bem.FP64 else relf(got, truth) < 1e-12
     assert n_far > 0
     rng = np.random.default_rng(7)
     x = rng.normal(size=(2, T.shape[0]))
@@ -316,6 +318,26 @@ def test_hmatrix_state_and_degenerate(lib):
     h.close()
 
 
+def test_mixed_sp_is_p0_only(lib):
+    """BEM_MIXED_SP exists for P0 matrices and P0 entries; a DP1 or P1 handle
+    and bem_entries_dp1 refuse it with BEM_E_ARG and launch nothing."""
+    V, T = meshes.icosphere(1)
+    m = bem.Mesh(V, T)
+    for space in (bem.DP1, bem.P1):
+        h = bem.HMatrix(m, 16, 1.2, space=space)
+        with pytest.raises(bem.BemError) as e:
+            h.assemble(bem.SLP, 0.0, 1e-4, bem.MIXED_SP)
+        assert e.value.status == 1
+        h.close()
+    ids = np.arange(4, dtype=np.int32)
+    with pytest.raises(bem.BemError) as e:
+        m.entries_dp1(bem.SLP, 0.0, bem.MIXED_SP, ids, ids)
+    assert e.value.status == 1
+    with pytest.raises(bem.BemError) as e:
+        m.entries(bem.SLP, 0.0, 3, ids, ids)
+    assert e.value.status == 1
+
+
 # ---- full-size workload: icosphere L6, jittered (81,920 triangles) ---------
 
 @pytest.fixture(scope="module")
@@ -344,7 +366,7 @@ def test_workload_l6_sampled(lib, l6, op):
     allc = np.arange(T.shape[0], dtype=np.int32)
     Arows = oracle.entries(V, T, op, 0.0, rows, allc).real
     x = rng.normal(size=T.shape[0])
-    for prec in (bem.MIXED, bem.FP64):
+    for prec in (bem.MIXED, bem.MIXED_SP, bem.FP64):
         h.assemble(op, 0.0, eps, prec)
         for b in pick_far:
             tb, te, sb, se, _ = blocks[b]
