@@ -818,7 +818,12 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 const typename D::F sv = group_col_dots<V, D, NC, W>(
                     u0 + (int64_t)KCHUNK * m, u1 + (int64_t)KCHUNK * m, n, vk, (int)n, nv, Bv, t, G.mask, q0);
                 const int c = l0 + bitrev_low<NC>(t % NC);
-                if (t < NC && c < ncol) {
+                // FP32: lanes below NC hold the group's columns once, and a
+                // group sum follows.  FP64 (the scarce pipe): every NC-lane set
+                // holds all NC columns, so a butterfly over the low log2(NC)
+                // lane bits completes the sum in each lane, and ||u_k||^2
+                // ||v_k||^2 is read from a lane that holds column k
+                if ((!kF32 || t < NC) && c < ncol) {
                     const S_t pr = D::re_mulf(su, sv);
                     if (c == kk) {
                         incr_s += pr;
@@ -832,8 +837,11 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 incr = (double)G.sumf(incr_s) * unscale;
                 uv2 = (double)G.sumf(uv2_s) * unscale;
             } else {
-                incr = G.sum(incr_s);
-                uv2 = G.sum(uv2_s);
+#pragma unroll
+                for (int d = 1; d < NC; d <<= 1) incr_s += __shfl_xor_sync(G.mask, incr_s, d);
+                incr = incr_s;
+                const int last_l0 = (ncol - 1) / NC * NC;
+                uv2 = G.shfl_idx(uv2_s, bitrev_low<NC>(kk - last_l0));
             }
         } else if constexpr (Grp::kShuffle) {
             // power-of-two segments per column, summed by shuffle trees

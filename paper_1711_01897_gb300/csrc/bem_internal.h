@@ -220,10 +220,13 @@ cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int o
 // Touching pairs of each case: min(dev_counts[c], host_counts[c]) pairs
 // (dev_counts may be null); grid_counts[c], if given, sizes the grid instead
 // of host_counts[c] (the threads stride over every pair either way).
+// vertex_dest2, if given, holds per vertex-adjacent pair the offset of the
+// transposed entry A_ji (or -1 for none), evaluated by the same quadrature.
 cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k, int prec,
                             const SingPair *pairs[3], const unsigned long long *dev_counts,
                             const int64_t host_counts[3], void *out, cudaStream_t st,
-                            const int64_t *grid_counts = nullptr);
+                            const int64_t *grid_counts = nullptr,
+                            const int64_t *vertex_dest2 = nullptr);
 
 cudaError_t launch_near_regular(const DevGeom &g, const QuadRule &rule, int op, double k, int prec,
                                 const NearBlock *blocks, int64_t nblocks, void *out,

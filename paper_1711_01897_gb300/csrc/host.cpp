@@ -1207,11 +1207,15 @@ struct bem_hmat_s {
     int64_t max_m_big = 0, max_m_small = 0;
     int64_t near_total = 0;
     std::vector<SingPair, NoInit<SingPair>> sing[3];
+    // per vertex-adjacent pair of sing[0] (P0): the offset of the transposed
+    // entry, evaluated by the same quadrature, or -1
+    std::vector<int64_t, NoInit<int64_t>> sing_t;
+    int64_t sing_entries[3] = {0, 0, 0};  // entries the pair lists write
     // leaves (matvec)
     std::vector<int64_t> leaf_rows, leaf_ptr;
     std::vector<int64_t, NoInit<int64_t>> leaf_items;
     // device
-    DBuf d_perm, d_near, d_far, d_chunks, d_sing[3], d_leaf_rows, d_leaf_ptr, d_leaf_items, d_long, d_long_off;
+    DBuf d_perm, d_near, d_far, d_chunks, d_sing[3], d_sing_t, d_leaf_rows, d_leaf_ptr, d_leaf_items, d_long, d_long_off;
     std::vector<int64_t> long_ids;        // admissible blocks with long columns (matvec)
     DBuf d_near_data, d_pool, d_poolhdr, d_queue, d_toff, d_xt, d_yt, d_tbuf, d_x, d_y;
     DBuf d_dperm, d_singl[3], d_vptr, d_vdof, d_xs, d_ys;
@@ -1891,7 +1895,14 @@ void build_lists(bem_hmat_s &H)
     // rows in chunks on the host threads, each chunk's pairs in row order,
     // the chunks in order (the sequential order): the chunks count their
     // pairs per case, the prefix over the chunks gives each its first slot,
-    // and the chunks write their pairs into the final lists
+    // and the chunks write their pairs into the final lists.
+    // P0 vertex-adjacent pairs are listed once, as (lower, higher) cluster
+    // position, with the offsets of both entries (-1 for an entry whose row
+    // another part of a row partition holds): the two share the rule's
+    // nodes (k_singular, SYM), and each entry's value is the same whatever
+    // the partition.
+    const bool vsym = H.dofs == 1;
+    auto mirrored = [&](int64_t p, int64_t q) { return q >= H.row_b && q < H.row_e && q < p; };
     constexpr int64_t kRowChunk = 8192;
     const int64_t nchunk = (nt + kRowChunk - 1) / kRowChunk;
     std::vector<std::array<int64_t, 3>> at(nchunk + 1, std::array<int64_t, 3>{0, 0, 0});
@@ -1901,7 +1912,11 @@ void build_lists(bem_hmat_s &H)
                      pe = std::min({nt, ck * kRowChunk + kRowChunk, H.row_e});
              p < pe; ++p) {
             const int32_t t = H.perm[p];
-            for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) ++cnt[M.adj_case[a] - 1];
+            for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) {
+                const int c = M.adj_case[a] - 1;
+                if (vsym && c == 0 && mirrored(p, H.iperm[M.adj_tri[a]])) continue;
+                ++cnt[c];
+            }
         }
         at[ck + 1] = cnt;
     });
@@ -1911,7 +1926,17 @@ void build_lists(bem_hmat_s &H)
         if (H.dofs == 1) H.sing[c].resize(at[nchunk][c]);
         else H.singl[c].resize(at[nchunk][c]);
     }
+    H.sing_t.resize(vsym ? at[nchunk][0] : 0);
     trace.mark("singular_count");
+    // the near block of row leaf l whose column range holds column q
+    auto near_of = [&](int64_t l, int64_t q) -> const NearBlock & {
+        const int64_t *b0 = nsb.data() + nptr[l], *b1 = nsb.data() + nptr[l + 1];
+        const int64_t *it = std::upper_bound(b0, b1, q);
+        if (it == b0) throw std::runtime_error("touching pair outside the near field");
+        const NearBlock &N = H.near[nq[nptr[l] + (it - 1 - b0)]];
+        if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
+        return N;
+    };
     parallel_tasks(nchunk, [&](int64_t ck) {
         std::array<int64_t, 3> pos = at[ck];
         for (int64_t p = std::max(ck * kRowChunk, H.row_b),
@@ -1919,19 +1944,31 @@ void build_lists(bem_hmat_s &H)
              p < pe; ++p) {
             const int32_t t = H.perm[p];
             const int64_t l = leaf_of[p];
-            const int64_t *b0 = nsb.data() + nptr[l], *b1 = nsb.data() + nptr[l + 1];
             for (int64_t a = M.adj_ptr[t]; a < M.adj_ptr[t + 1]; ++a) {
                 const int32_t u = M.adj_tri[a];
                 const int64_t q = H.iperm[u];
-                // near block of this row leaf whose column range holds q
-                const int64_t *it = std::upper_bound(b0, b1, q);
-                if (it == b0) throw std::runtime_error("touching pair outside the near field");
-                const NearBlock &N = H.near[nq[nptr[l] + (it - 1 - b0)]];
-                if (q >= N.se) throw std::runtime_error("touching pair outside the near field");
                 const int c = M.adj_case[a] - 1;
+                if (vsym && c == 0 && mirrored(p, q)) continue;  // listed from row q
+                // near block of this row leaf whose column range holds q
+                const NearBlock &N = near_of(l, q);
                 if (H.dofs == 1) {
                     // column-major block
                     const int64_t dest = N.off + (q - N.sb) * (N.te - N.tb) + (p - N.tb);
+                    if (c == 0 && q < p) {
+                        // row q lies in another part: the pair (q, p) writes
+                        // only its transposed entry, this row's
+                        H.sing_t[pos[c]] = dest;
+                        H.sing[c][pos[c]++] = {u, t, -1};
+                        continue;
+                    }
+                    if (c == 0) {
+                        int64_t d2 = -1;
+                        if (q >= H.row_b && q < H.row_e) {  // (q, p) is a row of this matrix
+                            const NearBlock &N2 = near_of(leaf_of[q], p);
+                            d2 = N2.off + (p - N2.sb) * (N2.te - N2.tb) + (q - N2.tb);
+                        }
+                        H.sing_t[pos[c]] = d2;
+                    }
                     H.sing[c][pos[c]++] = {t, u, dest};
                 } else {
                     // local (0, 0) of the pair in the column-major block of
@@ -1943,6 +1980,13 @@ void build_lists(bem_hmat_s &H)
             }
         }
     });
+    for (int c = 0; c < 3; ++c)
+        H.sing_entries[c] = H.dofs == 1 ? (int64_t)H.sing[c].size() : (int64_t)H.singl[c].size();
+    if (vsym) {
+        H.sing_entries[0] = 0;
+        for (size_t i = 0; i < H.sing_t.size(); ++i)
+            H.sing_entries[0] += (H.sing[0][i].dest >= 0) + (H.sing_t[i] >= 0);
+    }
     trace.mark("singular");
     trace.mark("join_singular");
     if (H.dofs == 3) {
@@ -1986,6 +2030,7 @@ void upload_tree(bem_hmat_s &H, cudaStream_t st)
     H.d_far.upload(H.far, st);
     H.d_chunks.alloc(H.far.size() * sizeof(FarChunks), st);
     for (int c = 0; c < 3; ++c) H.d_sing[c].upload(H.sing[c], st);
+    H.d_sing_t.upload(H.sing_t, st);
     if (H.dofs == 3) {
         H.d_dperm.upload(H.dperm, st);
         for (int c = 0; c < 3; ++c) H.d_singl[c].upload(H.singl[c], st);
@@ -2112,6 +2157,7 @@ int64_t hmat_device_bytes(bem_hmat H, bool cplx)
     int64_t tree = (int64_t)(H->near.size() * sizeof(NearBlock) +
                              H->far.size() * (sizeof(FarBlock) + sizeof(FarChunks))) +
                    (int64_t)(H->sing[0].size() + H->sing[1].size() + H->sing[2].size()) * 16 +
+                   (int64_t)H->sing_t.size() * 8 +
                    (int64_t)(H->leaf_items.size() + H->leaf_ptr.size() + H->leaf_rows.size()) * 8 +
                    nt * 4 + (int64_t)H->far.size() * 8 * 2;
     int64_t pool = (sum_mn * KCHUNK * 4 + 1024) * esz;
@@ -2238,7 +2284,8 @@ static void enqueue_near_field(bem_hmat H, cudaStream_t st, bool capturing)
                                  H->d_sing[2].as<SingPair>()};
         int64_t hc[3] = {(int64_t)H->sing[0].size(), (int64_t)H->sing[1].size(),
                          (int64_t)H->sing[2].size()};
-        CU(launch_singular(H->mesh->geom.g, D.sing, aop, k, prec, sp, nullptr, hc, H->d_near_data.p, st));
+        CU(launch_singular(H->mesh->geom.g, D.sing, aop, k, prec, sp, nullptr, hc, H->d_near_data.p, st,
+                           nullptr, H->sing_t.empty() ? nullptr : H->d_sing_t.as<int64_t>()));
     } else {
         CU(launch_near_dp1(H->geom.g, D.rule, aop, k, prec, H->d_near.as<NearBlock>(),
                            (int64_t)H->near.size(), H->d_near_data.p, st));
@@ -2638,7 +2685,7 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         s.n_blocks_half_warp = H->nshape[kShapeHalf];
         s.n_blocks_quarter_warp = H->nshape[kShapeQuarter];
         s.near_entries = H->near_total;
-        for (int c = 0; c < 3; ++c) s.singular_pairs[c] = (int64_t)H->sing[c].size();
+        for (int c = 0; c < 3; ++c) s.singular_pairs[c] = H->sing_entries[c];
         s.far_entries = H->far_entries;
         const size_t esz = H->cplx ? 16 : 8;
         s.factor_bytes = H->factor_elems * (int64_t)esz;
@@ -2665,8 +2712,6 @@ int hmat_stats(bem_hmat H, bem_hmat_stats *out)
         s.time_tree_lists_ms = H->t_lists;
         s.time_tree_upload_ms = H->t_upload;
         s.factor_read_bytes = H->rank_mn * (int64_t)esz;
-        for (int c = 0; c < 3; ++c)
-            if (H->dofs == 3) s.singular_pairs[c] = (int64_t)H->singl[c].size();
         *out = s;
         return BEM_OK;
     });

@@ -384,11 +384,23 @@ constexpr int kSingMaxPts = 6 * NGL * NGL * NGL;  // largest table (identical, h
 // float-float outside it; the pair's geometry, its edge basis and the final
 // scaling in FP64.  Otherwise (BEM_FP64, BEM_MIXED, Helmholtz) every step in
 // FP64.
-template <int CASE, int OP, bool CPLX, int PREC = 0>
+//
+// SYM (vertex-adjacent pairs only): the rule's node set for (T_j, T_i) is that
+// of (T_i, T_j) with x and y exchanged (both triangles start at the shared
+// vertex, Sec. 3.2.3), so one quadrature gives A_ij and A_ji: the single
+// layer is the same value (g(x, y) = g(y, x)); the double layer's transposed
+// entry has the adjoint kernel's numerator (x - y).n_x over the same nodes,
+// and the reverse for the adjoint double layer.  A_ij goes to pairs[pid].dest
+// and A_ji to dest2[pid], each only when its offset is >= 0.
+template <int CASE, int OP, bool CPLX, int PREC = 0, bool SYM = false>
 __global__ void __launch_bounds__(kSingThreads)
 k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pairs,
-           const unsigned long long *__restrict__ dev_count, int64_t max_count, void *out)
+           const unsigned long long *__restrict__ dev_count, int64_t max_count, void *out,
+           const int64_t *__restrict__ dest2)
 {
+    static_assert(!SYM || CASE == 1, "transposed pairs share nodes in the vertex case only");
+    // the operator whose kernel gives the transposed entry
+    constexpr int OPT = OP == 1 ? 2 : (OP == 2 ? 1 : 0);
     constexpr int NC = CASE == 3 ? 2 : (CASE == 2 ? 3 : 4);
     constexpr int ROWS = CPLX ? 5 : 6;
     constexpr bool kMix = PREC == 1 && !CPLX;
@@ -459,7 +471,7 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
             eny[i] = E[i][0] * ny[0] + E[i][1] * ny[1] + E[i][2] * ny[2];
             enx[i] = E[i][0] * nx[0] + E[i][1] * nx[1] + E[i][2] * nx[2];
         }
-        C2 acc = {0.0, 0.0};
+        C2 acc = {0.0, 0.0}, acc2 = {0.0, 0.0};
         const bool flat_zero = (CASE == 3 && OP != 0);  // d.n = 0 on one flat panel
         if constexpr (kMix && CASE == 1) {
             // the factorised vertex-adjacent rule below in FP32, with x - y
@@ -486,13 +498,16 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
                 wny[a] = wf[a] * uny[a];
                 wnx[a] = wf[a] * upnx[a];
             }
-            FF s = {0.f, 0.f};
+            // double layers: w r0^3, w r1^3 (DLP and ADLP forms share them),
+            // w_b u_b.n_y r1^3 (DLP) and w_b u'_b.n_x r0^3 (ADLP)
+            constexpr bool kD = OP == 1 || (SYM && OP == 2), kA = OP == 2 || (SYM && OP == 1);
+            FF s = {0.f, 0.f}, s2 = {0.f, 0.f};
 #pragma unroll
             for (int c = 0; c < NGL; ++c) {
                 const float e2 = xf[c];
 #pragma unroll
                 for (int a = 0; a < NGL; ++a) {
-                    float s0 = 0.f, s1 = 0.f;
+                    float s0 = 0.f, w0 = 0.f, w1 = 0.f, d1s = 0.f, a0s = 0.f;
 #pragma unroll
                     for (int b = 0; b < NGL; ++b) {
                         float d0[3], d1[3];
@@ -505,22 +520,28 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
                         const float r1 = rsqrt_ftz(fmaf(d1[0], d1[0], fmaf(d1[1], d1[1], d1[2] * d1[2])));
                         if (OP == 0) {
                             s0 = fmaf(wf[b], r0 + r1, s0);
-                        } else if (OP == 1) {
-                            s0 = fmaf(wf[b], r0 * r0 * r0, s0);
-                            s1 = fmaf(wny[b], r1 * r1 * r1, s1);
                         } else {
-                            s0 = fmaf(wnx[b], r0 * r0 * r0, s0);
-                            s1 = fmaf(wf[b], r1 * r1 * r1, s1);
+                            const float c0 = r0 * r0 * r0, c1 = r1 * r1 * r1;
+                            if (kD) {
+                                w0 = fmaf(wf[b], c0, w0);
+                                d1s = fmaf(wny[b], c1, d1s);
+                            }
+                            if (kA) {
+                                a0s = fmaf(wnx[b], c0, a0s);
+                                w1 = fmaf(wf[b], c1, w1);
+                            }
                         }
                     }
-                    float sa;
-                    if (OP == 0) sa = s0;
-                    else if (OP == 1) sa = fmaf(uny[a], s0, e2 * s1);
-                    else sa = fmaf(e2, s0, upnx[a] * s1);
-                    ff_add(s, (wf[c] * e2) * (wf[a] * sa));
+                    const float sd = kD ? fmaf(uny[a], w0, e2 * d1s) : 0.f;  // DLP form
+                    const float sA = kA ? fmaf(e2, a0s, upnx[a] * w1) : 0.f;  // ADLP form
+                    const float sa = OP == 0 ? s0 : (OP == 1 ? sd : sA);
+                    const float wq = (wf[c] * e2) * wf[a];
+                    ff_add(s, wq * sa);
+                    if (SYM && OP != 0) ff_add(s2, wq * (OP == 1 ? sA : sd));
                 }
             }
             acc.re = ff_to_double(s) * (OP == 0 ? sx2m : sx1m);
+            acc2.re = OP == 0 ? acc.re : ff_to_double(s2) * sx1m;
         } else if (CASE == 1 && !CPLX) {
             // Vertex-adjacent Laplace pair, factorised.  Region 0 maps to
             // x - y = xi (u(eta1) - eta2 u'(eta3)), region 1 to
@@ -555,37 +576,46 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
                 wny[b] = tab.wxi[b] * uny[b];
                 wnx[b] = tab.wxi[b] * upnx[b];
             }
-            double s = 0.0;
+            // the DLP form (d.n_y / r^3: region 0 xi u_a.n_y, region 1 xi
+            // eta2 u_b.n_y) and the ADLP form (-d.n_x / r^3: region 0 xi eta2
+            // u'_b.n_x, region 1 xi u'_a.n_x); with SYM a double layer takes
+            // both, one for each of the two entries
+            constexpr bool kD = OP == 1 || (SYM && OP == 2), kA = OP == 2 || (SYM && OP == 1);
+            double s = 0.0, s2 = 0.0;
             for (int c = 0; c < NGL; ++c) {
                 const double e2 = tab.xi[c], m2 = -2.0 * e2, q2 = e2 * e2;
-                double sc = 0.0;
+                double sc = 0.0, sc2 = 0.0;
                 for (int a = 0; a < NGL; ++a) {      // eta1 node
-                    double s0 = 0.0, s1 = 0.0;
+                    double s0 = 0.0, w0 = 0.0, w1 = 0.0, d1s = 0.0, a0s = 0.0;
                     for (int b = 0; b < NGL; ++b) {  // eta3 node
                         const double q0 = fma(q2, Cc[b], fma(m2, B[a][b], A[a]));
                         const double q1 = fma(q2, A[b], fma(m2, B[b][a], Cc[a]));
                         const double r0 = rsqrt_fp64(q0), r1 = rsqrt_fp64(q1);
                         if (OP == 0) {
                             s0 = fma(tab.wxi[b], r0 + r1, s0);
-                        } else if (OP == 1) {
-                            // d.n_y / r^3: region 0 xi u_a.n_y, region 1 xi eta2 u_b.n_y
-                            s0 = fma(tab.wxi[b], r0 * r0 * r0, s0);
-                            s1 = fma(wny[b], r1 * r1 * r1, s1);
                         } else {
-                            // -d.n_x / r^3: region 0 xi eta2 u'_b.n_x, region 1 xi u'_a.n_x
-                            s0 = fma(wnx[b], r0 * r0 * r0, s0);
-                            s1 = fma(tab.wxi[b], r1 * r1 * r1, s1);
+                            const double c0 = r0 * r0 * r0, c1 = r1 * r1 * r1;
+                            if (kD) {
+                                w0 = fma(tab.wxi[b], c0, w0);
+                                d1s = fma(wny[b], c1, d1s);
+                            }
+                            if (kA) {
+                                a0s = fma(wnx[b], c0, a0s);
+                                w1 = fma(tab.wxi[b], c1, w1);
+                            }
                         }
                     }
-                    double sa;
-                    if (OP == 0) sa = s0;
-                    else if (OP == 1) sa = fma(uny[a], s0, e2 * s1);
-                    else sa = fma(e2, s0, upnx[a] * s1);
+                    const double sd = kD ? fma(uny[a], w0, e2 * d1s) : 0.0;
+                    const double sA = kA ? fma(e2, a0s, upnx[a] * w1) : 0.0;
+                    const double sa = OP == 0 ? s0 : (OP == 1 ? sd : sA);
                     sc = fma(tab.wxi[a], sa, sc);
+                    if (SYM && OP != 0) sc2 = fma(tab.wxi[a], OP == 1 ? sA : sd, sc2);
                 }
                 s = fma(tab.wxi[c] * e2, sc, s);
+                if (SYM && OP != 0) s2 = fma(tab.wxi[c] * e2, sc2, s2);
             }
             acc.re = s * (OP == 0 ? sx2 : sx1);
+            acc2.re = OP == 0 ? acc.re : s2 * sx1;
         } else if (!flat_zero && kMix) {
             // the merged directions in FP32, summed in float-float
             float Ef[NC][3], enf[NC];
@@ -637,11 +667,17 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
                 }
                 double r2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]));
                 double ri = rsqrt_fp64(r2);
-                double dn = 0.0;
+                double dn = 0.0, dn2 = 0.0;
                 if (OP != 0) {
 #pragma unroll
                     for (int i = 0; i < NC; ++i) dn = fma(cf[i], OP == 1 ? eny[i] : enx[i], dn);
                     if (OP == 2) dn = -dn;  // ADLP kernel has -(x - y).n_x
+                    if (SYM) {
+                        // the transposed entry's numerator (the other form)
+#pragma unroll
+                        for (int i = 0; i < NC; ++i) dn2 = fma(cf[i], OPT == 1 ? eny[i] : enx[i], dn2);
+                        if (OPT == 2) dn2 = -dn2;
+                    }
                 }
                 if (!CPLX) {
                     if (OP == 0) acc.re = fma(s_tab[4 * npts + q], ri, acc.re);
@@ -660,17 +696,31 @@ k_singular(DevGeom g, SingTable tab, double k, const SingPair *__restrict__ pair
                             acc.im = fma(f, sn, acc.im);
                         } else {
                             // xi^3 J_eta exp(ikr)(1 - ikr) xi dn / (xi rt)^3
-                            double f = tab.wxi[m] * xi * weta * dn * ri * ri * ri;
-                            double kr = k * r;
-                            acc.re = fma(f, fma(kr, sn, cs), acc.re);
-                            acc.im = fma(f, fma(-kr, cs, sn), acc.im);
+                            const double f0 = tab.wxi[m] * xi * weta * ri * ri * ri;
+                            const double kr = k * r;
+                            const double er = fma(kr, sn, cs), ei = fma(-kr, cs, sn);
+                            const double f = f0 * dn;
+                            acc.re = fma(f, er, acc.re);
+                            acc.im = fma(f, ei, acc.im);
+                            if (SYM) {
+                                const double f2 = f0 * dn2;
+                                acc2.re = fma(f2, er, acc2.re);
+                                acc2.im = fma(f2, ei, acc2.im);
+                            }
                         }
                     }
                 }
             }
         }
         double sc = 4.0 * g.area[pr.i] * g.area[pr.j] * kInv4Pi;
-        store_val<CPLX>(out, pr.dest, {acc.re * sc, acc.im * sc});
+        if (!SYM || pr.dest >= 0) store_val<CPLX>(out, pr.dest, {acc.re * sc, acc.im * sc});
+        if constexpr (SYM) {
+            const int64_t d2 = dest2[pid];
+            if (d2 >= 0) {
+                if (OP == 0) acc2 = acc;
+                store_val<CPLX>(out, d2, {acc2.re * sc, acc2.im * sc});
+            }
+        }
     }
 }
 
@@ -813,21 +863,29 @@ cudaError_t launch_entries_regular(const DevGeom &g, const QuadRule &rule, int o
 template <int CASE, int OP, bool CPLX, int PREC>
 static void singular_launch(const DevGeom &g, const SingTable &tab, double k, const SingPair *p,
                             const unsigned long long *dc, int64_t hc, int64_t gc, void *out,
-                            cudaStream_t st)
+                            cudaStream_t st, const int64_t *dest2)
 {
     if (hc <= 0 || gc <= 0) return;
     // the grid covers gc pairs; its threads stride over all min(*dc, hc)
     int64_t want = (gc + kSingThreads - 1) / kSingThreads;
     int64_t cap = (int64_t)num_sms_cached() * 16;
     unsigned grid = (unsigned)(want < cap ? want : cap);
-    k_singular<CASE, OP, CPLX, PREC><<<grid, kSingThreads, 0, st>>>(g, tab, k, p, dc, hc, out);
+    if constexpr (CASE == 1) {
+        if (dest2) {
+            k_singular<CASE, OP, CPLX, PREC, true>
+                <<<grid, kSingThreads, 0, st>>>(g, tab, k, p, dc, hc, out, dest2);
+            count_launches(1);
+            return;
+        }
+    }
+    k_singular<CASE, OP, CPLX, PREC><<<grid, kSingThreads, 0, st>>>(g, tab, k, p, dc, hc, out, nullptr);
     count_launches(1);
 }
 
 cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, double k, int prec,
                             const SingPair *pairs[3], const unsigned long long *dev_counts,
                             const int64_t host_counts[3], void *out, cudaStream_t st,
-                            const int64_t *grid_counts)
+                            const int64_t *grid_counts, const int64_t *vertex_dest2)
 {
     const bool cplx = k != 0.0;
     for (int c = 1; c <= 3; ++c) {
@@ -839,9 +897,9 @@ cudaError_t launch_singular(const DevGeom &g, const SingTable *tabs, int op, dou
         // FP32 integrands only for Laplace in BEM_MIXED_SP; BEM_FP64,
         // BEM_MIXED and Helmholtz pairs stay FP64
         BEM_DISPATCH(op, cplx, (!cplx && prec == 2 ? 1 : 0), ({
-                         if (c == 1) singular_launch<1, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
-                         else if (c == 2) singular_launch<2, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
-                         else singular_launch<3, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st);
+                         if (c == 1) singular_launch<1, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st, vertex_dest2);
+                         else if (c == 2) singular_launch<2, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st, nullptr);
+                         else singular_launch<3, OP, CPLX, PREC>(g, T, k, P, dc, hc, gc, out, st, nullptr);
                      }));
     }
     return cudaGetLastError();
