@@ -244,41 +244,109 @@ k_long_offsets(const FarBlock *__restrict__ far, const int64_t *__restrict__ ids
 
 // Rows of one leaf cluster: items >= 0 are admissible blocks, items < 0 are
 // dense blocks (-1 - id); every listed block's row range contains the leaf.
+// The product costs one FP64 multiply-add per 8 bytes (real), more than this
+// part's FP64 rate sustains at HBM speed, so the kernel is built to keep the
+// FP64 lanes full: a warp per leaf, its lanes kLeafRowLanes rows x
+// kLeafSlices column slices.  The leaf's columns (the rank columns of its
+// admissible blocks and the columns of its dense blocks, in list order) are
+// dealt round-robin to the slices; each lane keeps NS rows (rows q, q + 4,
+// ...) in registers, so a leaf of 20 rows uses every lane; a butterfly over
+// the slice bits adds the slices in a fixed order (deterministic, no
+// atomics).  Leaves above 32 rows are taken in 32-row chunks.
+constexpr int kLeafRowLanes = 4, kLeafSlices = 32 / kLeafRowLanes, kLeafChunk = 32;
+
+template <typename T, int NS>
+__device__ __forceinline__ void leaf_chunk(int64_t rb, int mrow, int64_t i0, int64_t i1,
+                                           const int64_t *__restrict__ items,
+                                           const FarBlock *__restrict__ far,
+                                           const FarChunks *__restrict__ chunks,
+                                           const int64_t *__restrict__ toff,
+                                           const T *__restrict__ pool, const T *__restrict__ tbuf,
+                                           const NearBlock *__restrict__ near,
+                                           const T *__restrict__ near_data,
+                                           const T *__restrict__ xt, T *__restrict__ yt, int lane)
+{
+    const int q = lane % kLeafRowLanes, sl = lane / kLeafRowLanes;
+    T acc[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) acc[i] = zero_of(T{});
+    bool row_ok[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) row_ok[i] = q + kLeafRowLanes * i < mrow;
+    int64_t before = 0;  // columns of the leaf's earlier items
+    for (int64_t it = i0; it < i1; ++it) {
+        const int64_t id = items[it];
+        // this slice's first column of the item
+        int c = (int)((sl - before) % kLeafSlices);
+        if (c < 0) c += kLeafSlices;
+        if (id >= 0) {
+            const FarBlock &B = far[id];
+            const int64_t m = B.te - B.tb, rr = rb - B.tb + q;
+            const T *t = tbuf + toff[id];
+            const int64_t *ch = chunks[id].c;
+            const int nc = B.rank;
+            for (; c < nc; c += kLeafSlices) {
+                const T *col = pool + ch[c / KCHUNK] + (int64_t)(c % KCHUNK) * m + rr;
+                const T tv = t[c];
+#pragma unroll
+                for (int i = 0; i < NS; ++i)
+                    if (row_ok[i]) acc[i] = madd(col[kLeafRowLanes * i], tv, acc[i]);
+            }
+            before += nc;
+        } else {
+            // column-major: the row lanes read consecutive entries of a column
+            const NearBlock &N = near[-1 - id];
+            const int64_t nc = N.se - N.sb, mr = N.te - N.tb;
+            const T *a = near_data + N.off + (rb - N.tb) + q;
+            for (int64_t cc = c; cc < nc; cc += kLeafSlices) {
+                const T *col = a + cc * mr;
+                const T xv = xt[N.sb + cc];
+#pragma unroll
+                for (int i = 0; i < NS; ++i)
+                    if (row_ok[i]) acc[i] = madd(col[kLeafRowLanes * i], xv, acc[i]);
+            }
+            before += nc;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+        for (int d = kLeafRowLanes; d < 32; d <<= 1) acc[i] = add(acc[i], shxor(acc[i], d));
+    if (sl == 0) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            if (row_ok[i]) yt[rb + q + kLeafRowLanes * i] = acc[i];
+    }
+}
+
 template <typename T>
-__global__ void k_leaf_rows(const int64_t *__restrict__ leaf_rows, const int64_t *__restrict__ ptr,
-                            const int64_t *__restrict__ items, int64_t nleaf,
-                            const FarBlock *__restrict__ far, const FarChunks *__restrict__ chunks,
-                            const int64_t *__restrict__ toff,
-                            const T *__restrict__ pool, const T *__restrict__ tbuf,
-                            const NearBlock *__restrict__ near, const T *__restrict__ near_data,
-                            const T *__restrict__ xt, T *__restrict__ yt)
+__global__ void __launch_bounds__(kMvThreads)
+k_leaf_rows(const int64_t *__restrict__ leaf_rows, const int64_t *__restrict__ ptr,
+            const int64_t *__restrict__ items, int64_t nleaf, const FarBlock *__restrict__ far,
+            const FarChunks *__restrict__ chunks, const int64_t *__restrict__ toff,
+            const T *__restrict__ pool, const T *__restrict__ tbuf,
+            const NearBlock *__restrict__ near, const T *__restrict__ near_data,
+            const T *__restrict__ xt, T *__restrict__ yt)
 {
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t lf = warp; lf < nleaf; lf += nw) {
         const int64_t r0 = leaf_rows[2 * lf], r1 = leaf_rows[2 * lf + 1];
-        for (int64_t r = r0 + lane; r < r1; r += 32) {
-            T acc = zero_of(T{});
-            for (int64_t it = ptr[lf]; it < ptr[lf + 1]; ++it) {
-                int64_t id = items[it];
-                if (id >= 0) {
-                    const FarBlock &B = far[id];
-                    const int64_t m = B.te - B.tb, rr = r - B.tb;
-                    const T *t = tbuf + toff[id];
-                    const int64_t *ch = chunks[id].c;
-                    for (int l = 0; l < B.rank; ++l)
-                        acc = madd(pool[ch[l / KCHUNK] + (int64_t)(l % KCHUNK) * m + rr], t[l], acc);
-                } else {
-                    // column-major: consecutive lanes (rows) read consecutive
-                    // entries of each column
-                    const NearBlock &N = near[-1 - id];
-                    const int64_t nc = N.se - N.sb, mr = N.te - N.tb, rr = r - N.tb;
-                    const T *a = near_data + N.off + rr;
-                    for (int64_t c = 0; c < nc; ++c) acc = madd(a[c * mr], xt[N.sb + c], acc);
-                }
+        const int64_t i0 = ptr[lf], i1 = ptr[lf + 1];
+        for (int64_t rb = r0; rb < r1; rb += kLeafChunk) {
+            const int mrow = (int)(r1 - rb < kLeafChunk ? r1 - rb : kLeafChunk);
+            // rows per lane, the same in every lane of the warp
+            switch ((mrow + kLeafRowLanes - 1) / kLeafRowLanes) {
+#define BEM_LEAF(NS)                                                                              \
+    case NS:                                                                                      \
+        leaf_chunk<T, NS>(rb, mrow, i0, i1, items, far, chunks, toff, pool, tbuf, near, near_data, \
+                          xt, yt, lane);                                                          \
+        break;
+                BEM_LEAF(1) BEM_LEAF(2) BEM_LEAF(3) BEM_LEAF(4)
+                BEM_LEAF(5) BEM_LEAF(6) BEM_LEAF(7) BEM_LEAF(8)
+#undef BEM_LEAF
+                default: break;
             }
-            yt[r] = acc;
         }
     }
 }
