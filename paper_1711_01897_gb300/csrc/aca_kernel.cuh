@@ -372,6 +372,61 @@ __device__ __forceinline__ typename D::F group_col_dots(const typename V::T *c0,
     return acc[0];
 }
 
+// The FP64 form (BEM_MIXED) with the group's lanes split in two halves: the
+// lower W/2 lanes form <u_l, u_k> over the m rows, the upper W/2 lanes
+// <v_l, v_k> over the n columns, each half striding over its own vector with
+// NC accumulators.  The reduce-scatter and the xor rounds stay within a half,
+// so each lane reduces one set of NC sums over W/2 lanes instead of two sets
+// over W (fewer FP64 additions, the scarce pipe, and no idle lanes in the
+// tails of short columns); one shuffle across the halves then pairs each
+// column's two dot products.  Every NC-lane set of the group returns
+// re <u_l,u_k><v_l,v_k> of column l = l0 + bitrev(t mod NC) (bitwise the same
+// in both halves).  u0 / u1: first column of the chunk holding l0 and of the
+// next chunk (U columns at stride m, V columns at KCHUNK * m + stride n).
+template <class V, class D, int NC, int W>
+__device__ __forceinline__ double group_col_dots_split(const typename V::T *u0, const typename V::T *u1,
+                                                      const typename V::T *uk, const typename V::T *vk,
+                                                      int64_t m, int64_t n, int nvalid, int t, unsigned mask,
+                                                      int q0)
+{
+    using F = typename D::F;
+    constexpr int H = W / 2;
+    static_assert(NC <= H, "a half holds every column of the set");
+    const bool vside = t >= H;
+    const int64_t ld = vside ? n : m;
+    const typename V::T *c0 = vside ? u0 + (int64_t)KCHUNK * m : u0;
+    const typename V::T *c1 = vside ? u1 + (int64_t)KCHUNK * m : u1;
+    const typename V::T *xk = vside ? vk : uk;
+    const int len = (int)ld, h = t & (H - 1);
+    F acc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) acc[q] = D::zerof();
+#pragma unroll 2
+    for (int r = h; r < len; r += H) {
+        const F x = D::tofp(xk + r, 0u);
+#pragma unroll
+        for (int q = 0; q < NC; ++q)
+            if (q < nvalid) {
+                const int qc = q0 + q;
+                const typename V::T *c = (qc < KCHUNK ? c0 : c1) + (int64_t)(qc % KCHUNK) * ld;
+                acc[q] = D::fdot(D::tofp(c + r, 0u), x, acc[q]);
+            }
+    }
+#pragma unroll
+    for (int d = 1, nh = NC / 2; nh >= 1; d <<= 1, nh >>= 1) {
+        const bool up = (t & d) != 0;
+#pragma unroll
+        for (int q = 0; q < nh; ++q) {
+            const F send = up ? acc[q] : acc[q + nh];
+            const F keep = up ? acc[q + nh] : acc[q];
+            acc[q] = D::addf(keep, D::shfl_xorf(send, d, mask));
+        }
+    }
+#pragma unroll
+    for (int d = NC; d < H; d <<= 1) acc[0] = D::addf(acc[0], D::shfl_xorf(acc[0], d, mask));
+    return D::re_mulf(acc[0], D::shfl_xorf(acc[0], H, mask));
+}
+
 template <int NC>
 __device__ __forceinline__ int bitrev_low(int t)
 {
@@ -813,10 +868,17 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 const int q0 = NC < KCHUNK ? l0 % KCHUNK : 0;
                 const T *u0 = pool + S.chunk[l0 / KCHUNK];
                 const T *u1 = q0 + nv > KCHUNK ? pool + S.chunk[l0 / KCHUNK + 1] : u0;
-                const typename D::F su =
-                    group_col_dots<V, D, NC, W>(u0, u1, m, uk, (int)m, nv, Bu, t, G.mask, q0);
-                const typename D::F sv = group_col_dots<V, D, NC, W>(
-                    u0 + (int64_t)KCHUNK * m, u1 + (int64_t)KCHUNK * m, n, vk, (int)n, nv, Bv, t, G.mask, q0);
+                S_t pr;
+                if constexpr (kF32) {
+                    const typename D::F su =
+                        group_col_dots<V, D, NC, W>(u0, u1, m, uk, (int)m, nv, Bu, t, G.mask, q0);
+                    const typename D::F sv =
+                        group_col_dots<V, D, NC, W>(u0 + (int64_t)KCHUNK * m, u1 + (int64_t)KCHUNK * m, n, vk,
+                                                    (int)n, nv, Bv, t, G.mask, q0);
+                    pr = D::re_mulf(su, sv);
+                } else {
+                    pr = group_col_dots_split<V, D, NC, W>(u0, u1, uk, vk, m, n, nv, t, G.mask, q0);
+                }
                 const int c = l0 + bitrev_low<NC>(t % NC);
                 // FP32: lanes below NC hold the group's columns once, and a
                 // group sum follows.  FP64 (the scarce pipe): every NC-lane set
@@ -824,7 +886,6 @@ __device__ void aca_block(const Grp &G, const DevGeom &g, const QuadRule &R, dou
                 // lane bits completes the sum in each lane, and ||u_k||^2
                 // ||v_k||^2 is read from a lane that holds column k
                 if ((!kF32 || t < NC) && c < ncol) {
-                    const S_t pr = D::re_mulf(su, sv);
                     if (c == kk) {
                         incr_s += pr;
                         uv2_s = pr;
