@@ -47,10 +47,6 @@ LEAF, ETA, EPS = 32, 1.2, 1e-5
 N_SM, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, FP64_PER_SM_CLK, SM_MAX_MHZ = 152, 16, 128, 2, 2070.0
 FP64_TFLOPS_NOMINAL = 1.25
 
-# DRAM bytes (read + write) of the two k_aca launches of one step of the default
-# workload (icosphere level 6, SLP and DLP, mixed), from an ncu capture of this
-# build (dram__bytes_read.sum + dram__bytes_write.sum); re-capture when k_aca
-# changes.
 # distance classes of the regular rule (bem_set_quadrature) that the autotuner
 # chose for the default workload: python -m paper_1711_01897_gb300.autotune
 # --level 6 --quadrature (eps 1e-5, products within 0.5 eps of the 6-point
@@ -64,8 +60,8 @@ AUTOTUNED_SHAPES_C3 = (160, 48)
 
 # DRAM bytes of the two k_aca launches of one level-6 step (SLP read, write;
 # DLP read, write), dram__bytes_read.sum + dram__bytes_write.sum from one ncu
-# capture of the current kernel
-ACA_TRAFFIC_BYTES_PER_STEP_L6 = (4.482555136 + 1.825327872 + 10.779501568 + 2.851700224) * 1e9
+# capture of the current kernel (re-capture when k_aca changes)
+ACA_TRAFFIC_BYTES_PER_STEP_L6 = (5.115825920 + 1.825319168 + 11.720610816 + 2.815915008) * 1e9
 
 
 def rank_jitter_seed(rank: int) -> int:
