@@ -1558,10 +1558,11 @@ void build_blocks(bem_hmat_s &H)
 }
 
 // Block lists.  Near-field blocks keep tree order and get consecutive dense
-// storage.  Admissible blocks are split into three classes by their longer
-// side (CTA, warp, lane ACA), each in longest-processing-time-first order
-// (m + n descending, tree order on ties); the order comes from one sort of
-// packed 64-bit keys so that each FarBlock is written once.
+// storage.  Admissible blocks are split into classes by their longer side
+// (the ACA's work shapes), each in longest-processing-time-first order (m + n
+// descending; in the half- and quarter-warp shapes then by rank_order; tree
+// order on ties); the order comes from one sort of packed 64-bit keys so that
+// each FarBlock is written once.
 
 // Row partition of a block list (rows in cluster order): part boundaries
 // only where no block's row range is cut, each part's estimated cost as
@@ -1637,6 +1638,28 @@ void restrict_rows(bem_hmat_s &H)
     H.blocks.swap(keep);
 }
 
+// Order of an admissible block among those of its size in the half- and
+// quarter-warp shapes, whose 2 or 4 blocks per warp run in step until the
+// highest-rank one ends: a 12-bit bucket of the centre distance of the two
+// cluster boxes over the sum of their diameters, which falls as the ACA rank
+// grows (on the L6 sphere, correlation -0.57 to -0.72 with the ranks of SLP
+// and DLP blocks), so that blocks of like rank share a warp, the likely
+// higher ranks first.
+static uint64_t rank_order(const Cluster &T, const Cluster &S)
+{
+    double c2 = 0.0, dt = 0.0, ds = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double c = 0.5 * ((T.box[a] + T.box[a + 3]) - (S.box[a] + S.box[a + 3]));
+        const double et = T.box[a + 3] - T.box[a], es = S.box[a + 3] - S.box[a];
+        c2 += c * c;
+        dt += et * et;
+        ds += es * es;
+    }
+    const double den = std::sqrt(dt) + std::sqrt(ds);
+    const double r = den > 0.0 ? std::sqrt(c2) / den : 8.0;
+    return (uint64_t)std::min(4095.0, std::floor(r * 512.0));
+}
+
 void build_lists(bem_hmat_s &H)
 {
     PhaseTrace trace("lists");
@@ -1676,7 +1699,9 @@ void build_lists(bem_hmat_s &H)
                 else if (mx > kSub8Max) cls = kShapeHalf;
                 else cls = kShapeQuarter;
                 ++P.ncls[cls];
-                P.key.push_back(cls << 61 | (kSizeMask - (uint64_t)(m + n)) << 32 | (uint64_t)b);
+                uint64_t sz = kSizeMask - (uint64_t)(m + n);
+                if (cls == kShapeHalf || cls == kShapeQuarter) sz = (uint64_t)(255 - (m + n)) << 12 | rank_order(T, S);
+                P.key.push_back(cls << 61 | sz << 32 | (uint64_t)b);
             }
         }
     });
@@ -1708,7 +1733,7 @@ void build_lists(bem_hmat_s &H)
     H.near_total = at_elems[nbc];
     trace.mark("join");
     // the keys were made in increasing block order, so a stable sort on the
-    // upper 32 bits (class, size) alone orders them fully: LSD passes of 8
+    // upper 32 bits (class, size, rank order) alone orders them fully: LSD passes of 8
     // bits, each with digit counts per chunk on the threads, the offsets in
     // (digit, chunk) order and a stable scatter per chunk; a pass whose keys
     // all share their digit is skipped
