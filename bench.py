@@ -15,7 +15,10 @@ the end-to-end figure `e2e` rebuilds everything from host arrays every step.
 
 Metric: Galerkin integrals/s = entries evaluated per step (all near-field
 entries + every entry the ACA requested) / step time.  The FP64 path of the
-same step is timed after the run for the mixed-vs-FP64 comparison.
+same step is timed after the run for the mixed-vs-FP64 comparison.  On one
+GPU the line also carries records of the level-9 sphere (`c4`: 5.24 M
+triangles, assembly and 100 products), the Helmholtz ellipsoid (`c3`: 499,280
+triangles, complex ACA) and a short request stream (`serving`: p50 / p99).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -317,6 +320,16 @@ def run_gpu(args):
         # gigabytes of fresh host memory, and measured 0.75 s in a fresh
         # process against 1.06 s after the legs below (same library)
         extras["c4"] = large_record(args, LARGE["c4"], steps=1, warmup=1, cpu_baseline=False)
+        torch.cuda.empty_cache()
+    if ws == 1 and not args.no_c3:
+        # the Helmholtz ellipsoid (complex ACA on the autotuned work shapes);
+        # the library's work shapes are put back for the legs below
+        from paper_1711_01897_gb300 import bem as _bem
+        saved = _bem.bem_get_tuning()
+        try:
+            extras["c3"] = large_record(args, LARGE["c3"], steps=2, warmup=1, cpu_baseline=False)
+        finally:
+            _bem.bem_set_tuning(saved["warp_max_rows"], saved["lane_max_rows"], saved["use_graphs"])
         torch.cuda.empty_cache()
 
     # one problem (the workload's mesh); with N ranks each assembles and
@@ -1153,6 +1166,8 @@ def main():
                     help="requests of the short serving stream in the default line (0: none)")
     ap.add_argument("--no-c4", action="store_true",
                     help="leave the level-9 record out of the default line")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="leave the Helmholtz ellipsoid record out of the default line")
     ap.add_argument("--slots", type=int, default=6)
     ap.add_argument("--hbm-budget-gb", type=float, default=96.0)
     ap.add_argument("--load", type=float, default=0.8)
