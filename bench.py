@@ -65,7 +65,7 @@ AUTOTUNED_SHAPES_C3 = (1280, 48)
 # DRAM bytes of the two k_aca launches of one level-6 step (SLP read, write;
 # DLP read, write), dram__bytes_read.sum + dram__bytes_write.sum from one ncu
 # capture of the current kernel (re-capture when k_aca changes)
-ACA_TRAFFIC_BYTES_PER_STEP_L6 = (5.115825920 + 1.825319168 + 11.720610816 + 2.815915008) * 1e9
+ACA_TRAFFIC_BYTES_PER_STEP_L6 = (5.093048832 + 1.826512640 + 11.758856704 + 2.819681024) * 1e9
 
 
 def rank_jitter_seed(rank: int) -> int:
