@@ -809,6 +809,9 @@ def serving_record(args, nreq: int, calib: int):
         if sel.any():
             by_size[name] = {"count": int(sel.sum()), "p50": float(np.percentile(lat[sel], 50)),
                              "p99": float(np.percentile(lat[sel], 99))}
+            if len(phases) == len(lat):
+                by_size[name]["parts_p99_ms"] = {n: float(np.percentile(ph[sel, c], 99))
+                                                 for c, n in enumerate(names)}
     return {
         "config": {"workload": "serving: Poisson stream, 1k-200k triangles, 50% Laplace / 50% "
                                "Helmholtz SLP k~U[1,20], eps in {1e-4,1e-6}, assemble + 1 matvec; "
