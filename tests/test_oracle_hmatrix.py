@@ -103,6 +103,33 @@ def test_aca_zero_block_and_pivot_rule():
     assert np.isclose(Vv[1, 0], 1.0)
 
 
+def _rows_reproduced(A, kcap):
+    U, Vv = oracle.aca_dense(A, 1e-14, kcap=kcap)
+    R = U @ Vv.T
+    return [i for i in range(A.shape[0]) if np.allclose(R[i], A[i], rtol=0.0, atol=1e-13)]
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_aca_row_pivot_rule(cplx):
+    """Reading R1 (the paper leaves the row pivot to Bebendorf's rule): the
+    first row is row 0, the next the unused row with the largest modulus in
+    the last column of the residual, the lowest index on ties.  A cross
+    approximation reproduces its pivot rows exactly, so the rows that the
+    rank-2 approximant reproduces name the two row pivots."""
+    rng = np.random.default_rng(21 + cplx)
+    m, n = 7, 6
+    A = rng.uniform(0.1, 0.5, size=(m, n)) + (1j * rng.uniform(0.1, 0.5, size=(m, n)) if cplx else 0)
+    # j1 = 3, the largest modulus of row 0; the first column of the residual
+    # is column 3 itself, whose largest modulus outside row 0 is in row 4
+    A[:, 3] = np.array([2.0, 0.2, 0.3, 0.1, 0.9, 0.4, 0.25]) * (1j if cplx else 1.0)
+    assert _rows_reproduced(A, 2) == [0, 4]
+    # a tie in modulus between rows 2 and 4: the lower index
+    A[2, 3] = -A[4, 3]
+    assert _rows_reproduced(A, 2) == [0, 2]
+    # one step reproduces row 0 alone
+    assert _rows_reproduced(A, 1) == [0]
+
+
 def test_aca_error_decreases_with_eps():
     """Smooth kernel matrix: the ACA error tracks the requested accuracy."""
     x = np.linspace(0, 1, 60)
