@@ -130,6 +130,32 @@ def test_aca_row_pivot_rule(cplx):
     assert _rows_reproduced(A, 1) == [0]
 
 
+@pytest.mark.parametrize("k", [0.0, 25.0])
+def test_aca_stopping_rule(k):
+    """Reading R3: ACA stops after the first step k with ||u_k|| ||v_k|| <=
+    eps ||S_k||_F, where the oracle updates ||S_k||_F^2 incrementally (cross
+    terms 2 Re <u_k, u_l><v_k, v_l>).  Here ||S_l||_F is recomputed from the
+    returned factors by numpy for every prefix, so the run must stop at the
+    first step that meets the criterion.  On this kernel matrix a missing
+    cross term, a wrong sign of the cross terms or unconjugated inner
+    products (k = 25) move the stopping step for some of the tolerances."""
+    x = np.linspace(0.0, 1.0, 50)
+    y = np.linspace(1.3, 2.2, 40)
+    r = np.abs(x[:, None] - y[None, :])
+    A = np.exp(1j * k * r) / r if k else 1.0 / r
+    for eps in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
+        U, Vv = oracle.aca_dense(A, eps)
+        rank = U.shape[1]
+        assert 0 < rank < min(A.shape)
+
+        def ratio(l):
+            uv = np.linalg.norm(U[:, l - 1]) * np.linalg.norm(Vv[:, l - 1])
+            return uv / (eps * np.linalg.norm(U[:, :l] @ Vv[:, :l].T))
+
+        assert ratio(rank) <= 1.0 + 1e-9, (eps, rank)
+        assert all(ratio(l) > 1.0 - 1e-9 for l in range(1, rank)), (eps, rank)
+
+
 def test_aca_error_decreases_with_eps():
     """Smooth kernel matrix: the ACA error tracks the requested accuracy."""
     x = np.linspace(0, 1, 60)
