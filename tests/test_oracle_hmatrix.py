@@ -130,6 +130,18 @@ def test_aca_row_pivot_rule(cplx):
     assert _rows_reproduced(A, 1) == [0]
 
 
+@pytest.mark.parametrize("scale", [1.0, 1e10, 1e-10])
+def test_aca_vanishing_row_threshold(scale):
+    """Reading R2: a residual row counts as vanished when its largest modulus
+    is at most 1e-14 of the largest pivot so far.  On diag(1, d) the second
+    row's residual is (0, d): d = 1e-13 is a second pivot (rank 2), d = 1e-15
+    vanishes (rank 1), whatever the matrix's scale."""
+    for d, rank in ((1e-13, 2), (1e-15, 1)):
+        A = scale * np.diag([1.0, d])
+        U, Vv = oracle.aca_dense(A, 1e-30)
+        assert U.shape[1] == rank, (d, scale)
+
+
 @pytest.mark.parametrize("k", [0.0, 25.0])
 def test_aca_stopping_rule(k):
     """Reading R3: ACA stops after the first step k with ||u_k|| ||v_k|| <=
