@@ -6,6 +6,7 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -708,25 +709,49 @@ void build_adjacency(bem_mesh_s &M)
         std::vector<int8_t> cs;
         int64_t max_touch = 0;
     };
+    // each vertex's triangles in increasing order (the atomic fill leaves
+    // them in any order)
+    const int64_t nvchunk = (nv + kChunk - 1) / kChunk;
+    parallel_tasks(nvchunk, [&](int64_t ck) {
+        for (int64_t v = ck * kChunk, ve = std::min(nv, v + kChunk); v < ve; ++v)
+            std::sort(vtri.begin() + vptr[v], vtri.begin() + vptr[v + 1]);
+    });
+    // the triangles touching t: a three-way merge of its vertices' sorted
+    // lists, each triangle once, with the number of lists that hold it (the
+    // vertices it shares with t: 1 vertex, 2 edge, 3 t itself)
     std::vector<Part> parts(nchunk);
     parallel_tasks(nchunk, [&](int64_t ck) {
         Part &P = parts[ck];
-        std::vector<int32_t> loc;
-        for (int64_t t = ck * kChunk, te = std::min(nt, t + kChunk); t < te; ++t) {
-            loc.clear();
+        const int64_t t0 = ck * kChunk, t1 = std::min(nt, t0 + kChunk);
+        P.len.reserve(t1 - t0);
+        P.tri.reserve(16 * (t1 - t0));
+        P.cs.reserve(16 * (t1 - t0));
+        for (int64_t t = t0; t < t1; ++t) {
+            const int32_t *l[3], *le[3];
             for (int a = 0; a < 3; ++a) {
                 const int32_t v = M.T[3 * t + a];
-                for (int64_t q = vptr[v]; q < vptr[v + 1]; ++q) loc.push_back(vtri[q]);
+                l[a] = vtri.data() + vptr[v];
+                le[a] = vtri.data() + vptr[v + 1];
             }
-            std::sort(loc.begin(), loc.end());
             int64_t cnt = 0;
-            for (size_t q = 0; q < loc.size();) {
-                size_t e = q;
-                while (e < loc.size() && loc[e] == loc[q]) ++e;
-                P.tri.push_back(loc[q]);
-                P.cs.push_back((int8_t)(e - q));
+            for (;;) {
+                int32_t m = INT32_MAX;
+                bool any = false;
+                for (int a = 0; a < 3; ++a)
+                    if (l[a] < le[a] && (!any || *l[a] < m)) {
+                        m = *l[a];
+                        any = true;
+                    }
+                if (!any) break;
+                int8_t k = 0;
+                for (int a = 0; a < 3; ++a)
+                    if (l[a] < le[a] && *l[a] == m) {
+                        ++l[a];
+                        ++k;
+                    }
+                P.tri.push_back(m);
+                P.cs.push_back(k);
                 ++cnt;
-                q = e;
             }
             P.len.push_back(cnt);
             P.max_touch = std::max(P.max_touch, cnt);
