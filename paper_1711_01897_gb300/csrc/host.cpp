@@ -1874,15 +1874,36 @@ void build_lists(bem_hmat_s &H)
         for (int64_t q = task * 65536, qe = std::min(nnear_b, q + 65536); q < qe; ++q)
             tau_near[q] = (int32_t)H.blocks[H.near_block_id[q]].tau;
     });
+    // a stable counting sort of the blocks by row cluster, in chunks of the
+    // blocks on the host threads: per-chunk counts, offsets in (cluster,
+    // chunk) order, and each chunk's blocks scattered in order
     auto cluster_lists = [&](const std::vector<int32_t, NoInit<int32_t>> &tau, std::vector<int64_t> &ptr,
                              std::vector<int64_t, NoInit<int64_t>> &idx) {
         const int64_t n = (int64_t)tau.size();
+        const int64_t nck = std::max<int64_t>(1, std::min<int64_t>(8, n / 262144));
+        const int64_t per = (n + nck - 1) / nck;
+        std::vector<std::vector<int64_t>> cnt(nck);
+        parallel_tasks(nck, [&](int64_t ck) {
+            std::vector<int64_t> &c = cnt[ck];
+            c.assign(ncl, 0);
+            for (int64_t x = ck * per, xe = std::min(n, x + per); x < xe; ++x) ++c[tau[x]];
+        });
         ptr.assign(ncl + 1, 0);
-        for (int64_t x = 0; x < n; ++x) ++ptr[tau[x] + 1];
-        for (int64_t c = 0; c < ncl; ++c) ptr[c + 1] += ptr[c];
+        int64_t run = 0;
+        for (int64_t c = 0; c < ncl; ++c) {
+            ptr[c] = run;
+            for (int64_t ck = 0; ck < nck; ++ck) {
+                const int64_t v = cnt[ck][c];
+                cnt[ck][c] = run;
+                run += v;
+            }
+        }
+        ptr[ncl] = run;
         idx.resize(n);
-        std::vector<int64_t> pos(ptr.begin(), ptr.end() - 1);
-        for (int64_t x = 0; x < n; ++x) idx[pos[tau[x]]++] = x;
+        parallel_tasks(nck, [&](int64_t ck) {
+            std::vector<int64_t> &pos = cnt[ck];
+            for (int64_t x = ck * per, xe = std::min(n, x + per); x < xe; ++x) idx[pos[tau[x]]++] = x;
+        });
     };
     std::vector<int64_t> cf_ptr, cn_ptr;
     std::vector<int64_t, NoInit<int64_t>> cf_idx, cn_idx;
