@@ -721,7 +721,7 @@ void build_adjacency(bem_mesh_s &M)
     // vertices it shares with t: 1 vertex, 2 edge, 3 t itself)
     std::vector<Part> parts(nchunk);
     parallel_tasks(nchunk, [&](int64_t ck) {
-        Part &P = parts[ck];
+        Part P;  // moved in at the end: neighbouring chunks' parts share cache lines
         const int64_t t0 = ck * kChunk, t1 = std::min(nt, t0 + kChunk);
         P.len.reserve(t1 - t0);
         P.tri.reserve(16 * (t1 - t0));
@@ -756,6 +756,7 @@ void build_adjacency(bem_mesh_s &M)
             P.len.push_back(cnt);
             P.max_touch = std::max(P.max_touch, cnt);
         }
+        parts[ck] = std::move(P);
     });
     std::vector<int64_t> off(nchunk + 1, 0);
     M.max_touch = 0;
@@ -1430,7 +1431,7 @@ void build_clusters(bem_hmat_s &H)
     const size_t nfront = H.cl.size() - head;
     std::vector<std::vector<Cluster>> sub(nfront);
     parallel_tasks((int64_t)nfront, [&](int64_t f) {
-        std::vector<Cluster> &S = sub[f];
+        std::vector<Cluster> S;  // moved in at the end (neighbouring headers share cache lines)
         S.push_back(H.cl[head + f]);
         for (size_t q = 0; q < S.size(); ++q) {
             Cluster C = S[q];
@@ -1445,6 +1446,7 @@ void build_clusters(bem_hmat_s &H)
                 S[q] = C;
             }
         }
+        sub[f] = std::move(S);
     });
     trace.mark("subtrees");
     // the frontier cluster keeps its index; its descendants follow in order
@@ -1555,9 +1557,10 @@ void build_blocks(bem_hmat_s &H)
     std::vector<std::vector<BlockH>> sub(front.size());
     parallel_tasks((int64_t)front.size(), [&](int64_t f) {
         const Item &it = front[f];
-        std::vector<BlockH> &out = sub[f];
+        std::vector<BlockH> out;  // moved in at the end (neighbouring headers share cache lines)
         if (it.state != 0) {
             out.push_back({it.t, it.s, it.state == 1});
+            sub[f] = std::move(out);
             return;
         }
         std::vector<std::pair<int64_t, int64_t>> stack{{it.t, it.s}};
@@ -1575,6 +1578,7 @@ void build_blocks(bem_hmat_s &H)
             stack.push_back({T.left, S.right});
             stack.push_back({T.left, S.left});
         }
+        sub[f] = std::move(out);
     });
     size_t total = 0;
     for (auto &v : sub) total += v.size();
@@ -1705,7 +1709,9 @@ void build_lists(bem_hmat_s &H)
     };
     std::vector<BlkPart> bp(nbc);
     parallel_tasks(nbc, [&](int64_t ck) {
-        BlkPart &P = bp[ck];
+        // built in locals and moved in at the end: the parts of neighbouring
+        // chunks share cache lines
+        BlkPart P;
         for (int64_t b = ck * kBlkChunk, be = std::min(nb, b + kBlkChunk); b < be; ++b) {
             const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
             const int64_t m = T.e - T.b, n = S.e - S.b;
@@ -1729,6 +1735,7 @@ void build_lists(bem_hmat_s &H)
                 P.key.push_back(cls << 61 | sz << 32 | (uint64_t)b);
             }
         }
+        bp[ck] = std::move(P);
     });
     trace.mark("classify");
     // the parts in order: their offsets first, then the copies on the threads
@@ -1805,7 +1812,10 @@ void build_lists(bem_hmat_s &H)
     const int64_t nfar = (int64_t)key.size();
     const int64_t nfc = (nfar + kBlkChunk - 1) / kBlkChunk;
     std::vector<int64_t> mbig(nfc, 0), msmall(nfc, 0);
+    std::vector<char> low_rule(nfc, 0);  // some block of the chunk has a lower-order rule
     parallel_tasks(nfc, [&](int64_t ck) {
+        bool low = false;
+        int64_t mb = 0, ms = 0;
         for (int64_t f = ck * kBlkChunk, fe = std::min(nfar, f + kBlkChunk); f < fe; ++f) {
             const int64_t b = (int64_t)(key[f] & 0xffffffffu);
             const Cluster &T = H.cl[H.blocks[b].tau], &S = H.cl[H.blocks[b].sigma];
@@ -1816,11 +1826,14 @@ void build_lists(bem_hmat_s &H)
             F.sb = S.b;
             F.se = S.e;
             F.rule = H.dofs == 1 ? block_rule(T, S, H.rho3, H.rho1) : kRule6;
+            low |= F.rule != kRule6;
             H.far_block_id[f] = b;
-            if (f < ncls[kShapeCta]) mbig[ck] = std::max(mbig[ck], T.e - T.b);
-            else if (f < ncls[kShapeCta] + ncls[kShapeWarp])
-                msmall[ck] = std::max(msmall[ck], T.e - T.b);
+            if (f < ncls[kShapeCta]) mb = std::max(mb, T.e - T.b);
+            else if (f < ncls[kShapeCta] + ncls[kShapeWarp]) ms = std::max(ms, T.e - T.b);
         }
+        mbig[ck] = mb;
+        msmall[ck] = ms;
+        low_rule[ck] = low;
     });
     for (int64_t ck = 0; ck < nfc; ++ck) {
         H.max_m_big = std::max(H.max_m_big, mbig[ck]);
@@ -1828,7 +1841,7 @@ void build_lists(bem_hmat_s &H)
     }
     for (int c = 0; c < 5; ++c) H.nshape[c] = ncls[c];
     H.has_rules = false;
-    for (const FarBlock &F : H.far) H.has_rules |= F.rule != kRule6;
+    for (char c : low_rule) H.has_rules |= c != 0;
     trace.mark("far");
 
     // leaves sorted by row start, and the leaf of every cluster-order row
