@@ -1893,7 +1893,7 @@ void build_lists(bem_hmat_s &H)
     auto cluster_lists = [&](const std::vector<int32_t, NoInit<int32_t>> &tau, std::vector<int64_t> &ptr,
                              std::vector<int64_t, NoInit<int64_t>> &idx) {
         const int64_t n = (int64_t)tau.size();
-        const int64_t nck = std::max<int64_t>(1, std::min<int64_t>(8, n / 262144));
+        const int64_t nck = std::max<int64_t>(1, std::min<int64_t>(8, n / 32768));
         const int64_t per = (n + nck - 1) / nck;
         std::vector<std::vector<int64_t>> cnt(nck);
         parallel_tasks(nck, [&](int64_t ck) {
@@ -2013,7 +2013,21 @@ void build_lists(bem_hmat_s &H)
     H.sing_t.resize(vsym ? at[nchunk][0] : 0);
     trace.mark("singular_count");
     // the near block of row leaf l whose column range holds column q
+    // each leaf's own block (columns the leaf's rows), where most touching
+    // pairs lie: found without a search when the column falls in the leaf
+    std::vector<int64_t> diag(nleaf, -1);
+    parallel_tasks((nleaf + 1023) / 1024, [&](int64_t task) {
+        for (int64_t l = task * 1024, le = std::min(nleaf, l + 1024); l < le; ++l) {
+            const int64_t *b0 = nsb.data() + nptr[l], *b1 = nsb.data() + nptr[l + 1];
+            const int64_t *it = std::lower_bound(b0, b1, H.leaf_rows[2 * l]);
+            if (it != b1 && *it == H.leaf_rows[2 * l]) {
+                const int64_t id = nq[nptr[l] + (it - b0)];
+                if (H.near[id].se == H.leaf_rows[2 * l + 1]) diag[l] = id;
+            }
+        }
+    });
     auto near_of = [&](int64_t l, int64_t q) -> const NearBlock & {
+        if (diag[l] >= 0 && q >= H.leaf_rows[2 * l] && q < H.leaf_rows[2 * l + 1]) return H.near[diag[l]];
         const int64_t *b0 = nsb.data() + nptr[l], *b1 = nsb.data() + nptr[l + 1];
         const int64_t *it = std::upper_bound(b0, b1, q);
         if (it == b0) throw std::runtime_error("touching pair outside the near field");
